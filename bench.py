@@ -1,0 +1,353 @@
+"""Benchmark of the coupled LB phase-field step on GB300.
+
+Default workload: 2D 1024 x 1024, flow D2Q9 BGK tau_f = 0.6 coupled to the
+phase-field and solute D2Q9 lattices, inflow u = 0.01 on the left,
+zero-gradient outflow, periodic y, seed of radius 16 at x = 300, U0 = 0.4,
+5-fold anisotropy of strength 0.03, FP32.  One benchmark step is one LB time
+step over the whole grid; the metric is MLUPS (million node updates per
+second) with the HBM roofline of the step kernel beside it.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload c2|c1|c3|c3_fp16|c3_bf16|c2_fp16]
+
+Multi-GPU: the path does not shard in this build (one grid per GPU), so N
+GPUs run N independent replicas ("replicas only", weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+# bytes each node moves through HBM per step (populations read + written,
+# phi(t-1) read, phi(t) written)
+WORKLOADS = {
+    "c2": dict(desc="2D 1024x1024 coupled LB (D2Q9 flow + solute + phase field), inflow 0.01, "
+                    "seed R=16 at x=300, U0=0.4, 5-fold eps 0.03",
+               dim=2, nx=1024, ny=1024, nz=1, flow=1, fold=5, eps=0.03, bc=(1, 0, 0),
+               u_in=0.01, U_in=0.4, seed=(300.0, 512.0, 0.0, 16.0, 0.4, 0.01, 1),
+               storage="fp32", kernel="step2d_kernel", src="step2d.cu",
+               sample=dict(nx=256, ny=256, seed=(75.0, 128.0, 0.0, 16.0, 0.4, 0.01, 1))),
+    "c2_fp16": dict(base="c2", storage="fp16"),
+    "c1": dict(desc="2D 128x128 periodic, no flow (phase field + solute D2Q9), U0=0.3, R=8, "
+                    "4-fold eps 0.05",
+               dim=2, nx=128, ny=128, nz=1, flow=0, fold=4, eps=0.05, bc=(0, 0, 0), u_in=0.0,
+               U_in=0.0, seed=(64.0, 64.0, 0.0, 8.0, 0.3, 0.01, 1), storage="fp32",
+               kernel="step2d_kernel", src="step2d.cu",
+               sample=dict(nx=128, ny=128, seed=(64.0, 64.0, 0.0, 8.0, 0.3, 0.01, 1))),
+    "c3": dict(desc="3D 256^3 coupled LB (D3Q19 flow, D3Q7 solute and phase field), cubic eps "
+                    "0.04, sphere R=12, U0=0.3, inflow 0.005",
+               dim=3, nx=256, ny=256, nz=256, flow=1, fold=0, eps=0.04, bc=(1, 0, 0),
+               u_in=0.005, U_in=0.3, seed=(128.0, 128.0, 128.0, 12.0, 0.3, 0.01, 1),
+               storage="fp32", kernel="step3d_kernel", src="step3d.cu",
+               sample=dict(nx=48, ny=48, nz=48, seed=(24.0, 24.0, 24.0, 12.0, 0.3, 0.01, 1))),
+    "c3_fp16": dict(base="c3", storage="fp16"),
+    "c3_bf16": dict(base="c3", storage="bf16"),
+}
+ELEM = {"fp32": 4, "fp64": 8, "fp16": 2, "bf16": 2}
+
+
+def workload(name):
+    w = dict(WORKLOADS[name])
+    if "base" in w:
+        b = dict(WORKLOADS[w.pop("base")])
+        b.update(w)
+        b["desc"] = b["desc"] + f", {b['storage'].upper()} shifted storage"
+        w = b
+    q = (9 if w["dim"] == 2 else 19) * w["flow"] + 2 * (9 if w["dim"] == 2 else 7)
+    ring = 8 if w["storage"] == "fp64" else 4
+    w["bytes_per_lup"] = 2 * q * ELEM[w["storage"]] + 2 * ring
+    w["nodes"] = w["nx"] * w["ny"] * w["nz"]
+    return w
+
+
+def lib_params(w, L, storage=None):
+    return dict(dim=w["dim"], nx=w["nx"], ny=w["ny"], nz=w["nz"], bc=w["bc"], flow=w["flow"],
+                storage={"fp32": L.FP32, "fp64": L.FP64, "fp16": L.FP16_SHIFTED,
+                         "bf16": L.BF16_SHIFTED}[storage or w["storage"]],
+                fold=w["fold"], eps_aniso=w["eps"], u_inlet=w["u_in"], u0_inlet=w["U_in"])
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        try:
+            d = json.load(open(path))
+            flat = {}
+
+            def walk(o, pre=""):
+                if isinstance(o, dict):
+                    for k, v in o.items():
+                        walk(v, pre + k + ".")
+                else:
+                    flat[pre[:-1]] = o
+            walk(d)
+            for k, v in flat.items():
+                if re.search(r"hbm.*(gbs|gb_s|gbps)", k, re.I) and isinstance(v, (int, float)):
+                    return float(v), "measured"
+        except Exception:
+            pass
+    return 6800.0, "fallback"
+
+
+def profiled_traffic(w):
+    """Per-launch DRAM bytes from the committed ncu summary of this kernel, or
+    None when the kernel source changed since the counters were taken."""
+    prof = os.path.join(ROOT, "profiles", f"{w['kernel']}_{w['nx']}_{w['storage']}.md")
+    src = os.path.join(ROOT, "paper_2206_02145_gb300", "csrc", w["src"])
+    if not os.path.exists(prof):
+        return None
+    text = open(prof).read()
+    mh = re.search(r"source_sha256:\s*([0-9a-f]+)", text)
+    mt = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    if not (mh and mt):
+        return None
+    if hashlib.sha256(open(src, "rb").read()).hexdigest() != mh.group(1):
+        return None
+    return float(mt.group(1))
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    Q = ("clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) == 6:
+                self.rows.append(parts)
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = sorted(float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit())
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4)
+                          if r[2 + i].lower() == "active"})
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(self.rows)}
+
+
+def oracle_sample(w, seconds: float, threads: int):
+    """The FP64 CPU oracle, as it stands, on a bounded sample of the workload."""
+    import oracle
+    s = w["sample"]
+    p = oracle.Params(dim=w["dim"], nx=s["nx"], ny=s["ny"], nz=s.get("nz", 1), bc=w["bc"],
+                      flow=w["flow"], fold=w["fold"], eps=w["eps"], u_inlet=w["u_in"],
+                      u0_inlet=w["U_in"])
+    o = oracle.Oracle(p)
+    o.init_seed(*s["seed"])
+    o.step(1, threads)
+    steps, t0 = 0, time.perf_counter()
+    while time.perf_counter() - t0 < seconds:
+        o.step(1, threads)
+        steps += 1
+    dt = time.perf_counter() - t0
+    return p.nodes * steps / dt / 1e6, steps, p.nodes, dt
+
+
+def run_reference(args, w):
+    """The oracle on the host cores: each step advances a bounded sample."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    threads = os.cpu_count() or 1
+    s = w["sample"]
+    p = oracle.Params(dim=w["dim"], nx=s["nx"], ny=s["ny"], nz=s.get("nz", 1), bc=w["bc"],
+                      flow=w["flow"], fold=w["fold"], eps=w["eps"], u_inlet=w["u_in"],
+                      u0_inlet=w["U_in"])
+    o = oracle.Oracle(p)
+    o.init_seed(*s["seed"])
+    for _ in range(args.warmup):
+        o.step(1, threads)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        o.step(1, threads)
+    dt = time.perf_counter() - t0
+    v = p.nodes * args.steps / dt / 1e6
+    sample = (f"{s['nx']}x{s['ny']}" + (f"x{s['nz']}" if w['dim'] == 3 else "") +
+              " nodes of the same workload per step (FP64 oracle, OpenMP)")
+    print(json.dumps({
+        "impl": "reference", "metric": "coupled-LB MLUPS", "value": v, "unit": "MLUPS",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": w["desc"], "sample_grid": [s["nx"], s["ny"], s.get("nz", 1)]},
+        "cpu_baseline": {"value": v, "unit": "MLUPS", "cores": threads, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": v, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=4000)
+    ap.add_argument("--warmup", type=int, default=200)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="c2", choices=sorted(WORKLOADS))
+    ap.add_argument("--e2e-steps", type=int, default=50)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    w = workload(args.workload)
+    if args.impl == "reference":
+        return run_reference(args, w)
+
+    import numpy as np
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    import paper_2206_02145_gb300 as L
+    stream = torch.cuda.current_stream()
+    sim = L.Sim(stream=stream.cuda_stream, **lib_params(w, L))
+    sim.init_seed(*w["seed"])
+
+    # warm-up (also builds the step graph)
+    sim.step(args.warmup)
+    torch.cuda.synchronize()
+
+    # --- device-resident timed region: K steps, inputs already in HBM ----------
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        barrier()
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        sim.step(args.steps)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+    ms = ev0.elapsed_time(ev1)
+    t = torch.tensor([ms], device="cuda")
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    per_step_ms = ms_max / args.steps
+    value = w["nodes"] * world * args.steps / (ms_max * 1e-3) / 1e6
+    d = sim.diagnostics()  # also surfaces any sticky device error
+
+    # --- end to end through the C ABI with host buffers -------------------------
+    # every step: H2D of the full state from pinned memory (lbpf_write_state),
+    # one coupled step, D2H of phi and U (lbpf_read_fields)
+    state = sim.state()
+    host_state = torch.from_numpy(state).pin_memory()
+    nf = 2
+    host_out = torch.empty(nf * w["nodes"], dtype=torch.float32).pin_memory()
+    mask = L.FIELD_PHI | L.FIELD_U
+    for _ in range(3):
+        L.lbpf_write_state(sim.h, host_state.data_ptr(), host_state.numel())
+        sim.step(1)
+        L.lbpf_read_fields(sim.h, mask, host_out.data_ptr(), host_out.numel() * 4, 0)
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        L.lbpf_write_state(sim.h, host_state.data_ptr(), host_state.numel())
+        sim.step(1)
+        L.lbpf_read_fields(sim.h, mask, host_out.data_ptr(), host_out.numel() * 4, 0)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    te = torch.tensor([e2e_s], device="cuda")
+    if dist is not None:
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    e2e_value = w["nodes"] * world * args.e2e_steps / float(te.item()) / 1e6
+
+    peak, peak_kind = measured_peaks()
+    achieved = w["bytes_per_lup"] * w["nodes"] / (per_step_ms * 1e-3) / 1e9
+    traffic = profiled_traffic(w)
+
+    if rank == 0:
+        cpu = None
+        if not args.no_cpu_baseline:
+            threads = os.cpu_count() or 1
+            v, steps, n, dt = oracle_sample(w, args.cpu_seconds, threads)
+            s = w["sample"]
+            cpu = {"value": v, "unit": "MLUPS", "cores": threads, "kind": "oracle",
+                   "sample": f"{steps} steps of a {s['nx']}x{s['ny']}"
+                             + (f"x{s['nz']}" if w['dim'] == 3 else "")
+                             + f" grid of the same workload ({n} nodes), {dt:.1f} s, FP64"}
+        out = {
+            "metric": "coupled-LB MLUPS", "value": value, "unit": "MLUPS", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_step_ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if w["storage"] == "fp32" else (
+                "f64" if w["storage"] == "fp64" else f"f32 ({w['storage']} storage)"),
+            "data": "synthetic (seeded tanh seed + SplitMix64 noise)",
+            "config": {"workload": w["desc"], "grid": [w["nx"], w["ny"], w["nz"]],
+                       "storage": w["storage"], "bytes_per_lup": w["bytes_per_lup"],
+                       "l2": f"inputs larger than L2: {w['bytes_per_lup'] * w['nodes'] / 1e6:.0f}"
+                             " MB moved per step vs 129 MB L2",
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "peak_source": peak_kind,
+                         "traffic": traffic,
+                         "algorithmic_bytes_per_launch": w["bytes_per_lup"] * w["nodes"]},
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": "MLUPS",
+                    "h2d_bytes_per_step": int(host_state.numel()),
+                    "d2h_bytes_per_step": int(host_out.numel() * 4)},
+            "gpu_launches": args.steps,
+            "clocks": clk.summary(),
+            "diag": {"step": d["step"], "solute_drift_rel": d["solute_drift_rel"],
+                     "r_eq": d["r_eq"]},
+        }
+        print(json.dumps(out), flush=True)
+    sim.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,201 @@
+/*
+ * lbpf — coupled lattice-Boltzmann phase-field crystal-growth step on one
+ * NVIDIA GB300 (sm_103a).  C ABI of liblbpf.so.
+ *
+ * The model is the one of Sec. 2 of Tan, Hosseini, Seidel-Morgenstern,
+ * Thevenin and Lorenz, "Mandelic acid single-crystal growth: experiments vs
+ * numerical simulations":
+ *   - phase field phi (solid +1, liquid -1) on the modified LB scheme of
+ *     Eq. 19 with source Eq. 20, equilibrium Eq. 21, moment Eq. 22 and
+ *     relaxation Eq. 23, anisotropy a_s(n) of Eq. 3 with n = -grad phi/|grad phi|;
+ *   - supersaturation U on the advection-diffusion LB of Eqs. 13-18 with the
+ *     growth source of Eq. 14;
+ *   - flow on the BGK LB of Eqs. 4-12 with Guo forcing (Eq. 5), the solid drag
+ *     of Eq. 6 and the velocity mask of Eq. 7.
+ * 2D uses D2Q9 for all three lattices; 3D uses D3Q19 for the flow and D3Q7
+ * for U and phi.
+ *
+ * Conventions of every call:
+ *   - returns LBPF_OK (0) or a negative lbpf_status; never aborts;
+ *   - a NULL or destroyed handle gives LBPF_EINVAL;
+ *   - errors are sticky per handle: after a CUDA error or a device-detected
+ *     non-finite value every later call returns that status, and
+ *     lbpf_last_error() gives a one-line description;
+ *   - the library owns all device memory of a handle; host buffers passed in
+ *     are owned by the caller and are not retained after the call returns;
+ *   - work is issued on the CUDA stream given at creation (NULL = legacy
+ *     default stream); calls documented as synchronising wait for that
+ *     stream, the others return as soon as the work is queued.
+ * Node order of every field and state array: x fastest, then y, then z;
+ * no padding.
+ */
+#ifndef LBPF_H
+#define LBPF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbpf lbpf_t;
+
+typedef enum {
+  LBPF_OK = 0,
+  LBPF_EINVAL = -1,      /* invalid argument, parameter or buffer size */
+  LBPF_ECUDA = -2,       /* a CUDA runtime call failed */
+  LBPF_ENOMEM = -3,      /* device or host allocation failed */
+  LBPF_ESTATE = -4,      /* call out of order (e.g. step before init) */
+  LBPF_ENONFINITE = -5,  /* a NaN/Inf appeared in the fields */
+  LBPF_ETIMEDOUT = -6    /* a bounded device wait gave up */
+} lbpf_status;
+
+/* Boundary condition per axis. */
+enum {
+  LBPF_BC_PERIODIC = 0,
+  /* x only: inflow ghost at x = -1 in equilibrium with rho = 1,
+   * u = (u_inlet, 0, 0), U = u0_inlet, phi = -1; outflow ghost at x = nx that
+   * repeats the post-collision state of the last column (zero gradient). */
+  LBPF_BC_INLET_OUTLET = 1,
+  /* half-way bounce-back for f, g and h (zero flux; no-slip for the flow) */
+  LBPF_BC_WALL = 2
+};
+
+/* Population storage.  Arithmetic is FP32 except for LBPF_FP64. */
+enum {
+  LBPF_FP32 = 0,
+  LBPF_FP64 = 1,
+  LBPF_FP16_SHIFTED = 2, /* binary16 deviation from the lattice weight times a reference moment */
+  LBPF_BF16_SHIFTED = 3  /* bfloat16, same shift */
+};
+
+/* Field selection bits of lbpf_read_fields. */
+enum {
+  LBPF_FIELD_PHI = 1u << 0,      /* phi = sum h (Eq. 22) */
+  LBPF_FIELD_U = 1u << 1,        /* U = sum g (Eq. 17) */
+  LBPF_FIELD_RHO = 1u << 2,      /* rho = sum f (Eq. 11); 1 without flow */
+  LBPF_FIELD_UX = 1u << 3,       /* fluid velocity (Eq. 12 with the Guo half force) */
+  LBPF_FIELD_UY = 1u << 4,
+  LBPF_FIELD_UZ = 1u << 5,
+  LBPF_FIELD_PHI_PREV = 1u << 6, /* phi at the previous time level */
+  LBPF_FIELD_STATE = 1u << 8     /* the full restartable state (see below) */
+};
+
+/* Model and run parameters.  Lattice units: dx = dt = 1. */
+typedef struct {
+  int dim;            /* 2 or 3 */
+  int nx, ny, nz;     /* grid; nz is ignored (taken as 1) in 2D */
+  int bc[3];          /* LBPF_BC_* for x, y, z; INLET_OUTLET only on x */
+  int flow;           /* 0: phase field + solute only; 1: coupled flow lattice */
+  int storage;        /* LBPF_FP32, LBPF_FP64, LBPF_FP16_SHIFTED, LBPF_BF16_SHIFTED */
+  int fold;           /* k of a_s = 1 + eps cos(k (theta - theta0)) (Eq. 3), 1..12;
+                         0 = cubic a_s = 1 - 3 eps + 4 eps sum n_i^4 (required in 3D) */
+  int aniso_literal;  /* 0: N = |grad phi|^2 a_s d(a_s)/d(grad phi) (Eq. 21 read in
+                         its variational form); 1: twice that (the literal factor) */
+  double tau_phi0;    /* tau_phi at a_s = 1 (Eq. 23); sets tau0 = W0^2/(cs^2 (tau_phi0 - 1/2)) */
+  double tau_u_liquid;/* tau_U in the liquid (Eq. 18); D = cs^2 (tau_u_liquid - 1/2) */
+  double tau_f;       /* flow relaxation time (Eq. 10); nu = (tau_f - 1/2)/3 */
+  double w0;          /* interface width W0 (Eqs. 1, 6, 21, 23) */
+  double lambda;      /* coupling constant (Eq. 20); < 0 selects D tau0 / (0.6267 W0^2) */
+  double eps_aniso;   /* anisotropy strength eps (Eq. 3), 0 <= eps < 1 */
+  double theta0;      /* anisotropy orientation (radians) */
+  double h_drag;      /* drag constant h of Eq. 6 (2.757) */
+  double u_inlet;     /* inflow velocity along +x (|u| <= 0.1) */
+  double u0_inlet;    /* supersaturation of the inflow */
+  double body_force[3]; /* constant body force density (test flows); usually 0 */
+} lbpf_params;
+
+/* Circular (2D) / spherical (3D) seed: phi0 = tanh((radius - r)/(sqrt(2) W0))
+ * + noise_amp * xi, xi in [-1, 1) from SplitMix64 of (seed XOR
+ * (node_index * 0x9E3779B97F4A7C15)); U = u0; rho = 1;
+ * u = (u_inlet, 0, 0) when flow is on; all populations at equilibrium. */
+typedef struct {
+  double cx, cy, cz;  /* centre in node units */
+  double radius;
+  double u0;          /* initial supersaturation */
+  double noise_amp;
+  uint64_t seed;
+} lbpf_seed;
+
+/* FP64 diagnostics of the current state. */
+typedef struct {
+  int64_t step;
+  double solute_total;      /* sum over nodes of U(t) + phi(t-1); conserved without inflow */
+  double solute_drift_rel;  /* (solute_total - value at init) / |value at init| */
+  double mass_total;        /* sum rho */
+  double solid_volume;      /* sum (1 + clamp(phi, -1, 1)) / 2 */
+  double r_eq;              /* equivalent radius of solid_volume (circle / sphere) */
+  double iface_pos[6];      /* distance of the phi = 0 crossing from the seed-centre
+                               node along +x, -x, +y, -y, +z, -z; -1 if none */
+  double max_u;             /* max |u| */
+  int64_t nonfinite;        /* nodes with a non-finite phi, U or rho */
+} lbpf_diag;
+
+/* Fill *p with the defaults: 2D 128 x 128 periodic, no flow, FP32, fold 4,
+ * eps 0.05, tau_phi0 = tau_u_liquid = 0.8, tau_f = 0.6, W0 = 2, default
+ * lambda, h_drag = 2.757. */
+int lbpf_params_default(lbpf_params* p);
+
+/* Validate *p, allocate the device state and return a handle in *out.
+ * stream: a cudaStream_t (NULL = legacy default stream).  EINVAL cases:
+ * tau <= 1/2, W0 <= 0, eps outside [0, 1), fold outside 0..12 (or != 0 in
+ * 3D), grid dimension < 4, INLET_OUTLET on y or z, |u_inlet| > 0.1. */
+int lbpf_create(const lbpf_params* p, void* stream, lbpf_t** out);
+
+/* Initial state from a seed (computed on the device in FP64, stored in the
+ * population type); resets the step counter to 0.  Asynchronous. */
+int lbpf_init_seed(lbpf_t* h, const lbpf_seed* s);
+
+/* Initial state from host FP64 fields of nx*ny*nz values each: every
+ * population at the equilibrium of (rho, u* = (1 - clamp(phi))/2 u, U, phi);
+ * phi(t-1) = phi.  rho, ux, uy, uz may be NULL (1, 0).  Synchronising. */
+int lbpf_init_fields(lbpf_t* h, const double* phi, const double* U, const double* rho,
+                     const double* ux, const double* uy, const double* uz);
+
+/* Advance n >= 0 coupled steps (Eqs. 4-23, pull-equivalent push streaming).
+ * Asynchronous; n = 0 is a no-op. */
+int lbpf_step(lbpf_t* h, int n);
+
+/* Copy fields to host_dst (caller-owned).  Without LBPF_FIELD_STATE: the
+ * selected fields one after another in bit order, nx*ny*nz values each, as
+ * double if as_fp64 else float; bytes must equal that total.  With
+ * LBPF_FIELD_STATE alone: the restartable state of lbpf_state_bytes() bytes.
+ * Synchronising. */
+int lbpf_read_fields(lbpf_t* h, unsigned field_mask, void* host_dst, size_t bytes,
+                     int as_fp64);
+
+/* Size of the restartable state: a 64-byte header (magic "LBPFST01", int64
+ * step, int32 dim, nx, ny, nz, storage, flow, populations per node, element
+ * bytes), then the populations direction-major in the storage type (f, then
+ * g, then h; directions in the order: D2Q9 (0,0) (1,0) (0,1) (-1,0) (0,-1)
+ * (1,1) (-1,1) (-1,-1) (1,-1); D3Q19 rest, +x, -x, +y, -y, +z, -z,
+ * (1,1,0) (-1,-1,0) (1,-1,0) (-1,1,0) (1,0,1) (-1,0,-1) (1,0,-1) (-1,0,1)
+ * (0,1,1) (0,-1,-1) (0,1,-1) (0,-1,1); D3Q7 the first seven of those), then
+ * phi(t-1) in FP64 for LBPF_FP64 storage and FP32 otherwise. */
+size_t lbpf_state_bytes(const lbpf_t* h);
+
+/* Restore a state written by lbpf_read_fields(LBPF_FIELD_STATE) of a handle
+ * with the same grid, flow and storage.  Synchronising. */
+int lbpf_write_state(lbpf_t* h, const void* host_src, size_t bytes);
+
+/* FP64 reductions of the current state (deterministic two-pass sums).
+ * Synchronising; reports a non-finite state as LBPF_ENONFINITE. */
+int lbpf_diagnostics(lbpf_t* h, lbpf_diag* out);
+
+/* Rebind the handle to another stream (e.g. the caller's current stream). */
+int lbpf_set_stream(lbpf_t* h, void* stream);
+
+/* Bytes of device memory the handle owns. */
+size_t lbpf_device_bytes(const lbpf_t* h);
+
+/* Human-readable description of the last error of h ("" if none). */
+const char* lbpf_last_error(const lbpf_t* h);
+
+/* Release everything the handle owns; NULL is a no-op. */
+void lbpf_destroy(lbpf_t* h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LBPF_H */

@@ -1,0 +1,265 @@
+"""Python binding of liblbpf.so — the coupled lattice-Boltzmann phase-field
+crystal-growth step (Sec. 2 of Tan et al., "Mandelic acid single-crystal
+growth: experiments vs numerical simulations") on one GB300.
+
+The functions here carry the C ABI names of ``include/lbpf.h`` and only
+marshal arguments through ctypes; every step of the method runs in the CUDA
+kernels of the library.  There is no CPU fallback: importing the package
+without the built library raises.  Build it with
+``python -c "import __graft_entry__ as g; g.build()"``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "liblbpf.so")
+
+OK, EINVAL, ECUDA, ENOMEM, ESTATE, ENONFINITE, ETIMEDOUT = 0, -1, -2, -3, -4, -5, -6
+BC_PERIODIC, BC_INLET_OUTLET, BC_WALL = 0, 1, 2
+FP32, FP64, FP16_SHIFTED, BF16_SHIFTED = 0, 1, 2, 3
+FIELD_PHI, FIELD_U, FIELD_RHO, FIELD_UX, FIELD_UY, FIELD_UZ, FIELD_PHI_PREV = (
+    1, 2, 4, 8, 16, 32, 64)
+FIELD_STATE = 256
+FIELD_NAMES = ("phi", "U", "rho", "ux", "uy", "uz", "phi_prev")
+_STATUS = {OK: "OK", EINVAL: "EINVAL", ECUDA: "ECUDA", ENOMEM: "ENOMEM", ESTATE: "ESTATE",
+           ENONFINITE: "ENONFINITE", ETIMEDOUT: "ETIMEDOUT"}
+
+
+class LbpfError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{_STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class lbpf_params(ctypes.Structure):
+    _fields_ = [
+        ("dim", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+        ("bc", ctypes.c_int * 3), ("flow", ctypes.c_int), ("storage", ctypes.c_int),
+        ("fold", ctypes.c_int), ("aniso_literal", ctypes.c_int),
+        ("tau_phi0", ctypes.c_double), ("tau_u_liquid", ctypes.c_double),
+        ("tau_f", ctypes.c_double), ("w0", ctypes.c_double), ("lambda_", ctypes.c_double),
+        ("eps_aniso", ctypes.c_double), ("theta0", ctypes.c_double),
+        ("h_drag", ctypes.c_double), ("u_inlet", ctypes.c_double),
+        ("u0_inlet", ctypes.c_double), ("body_force", ctypes.c_double * 3),
+    ]
+
+
+class lbpf_seed(ctypes.Structure):
+    _fields_ = [("cx", ctypes.c_double), ("cy", ctypes.c_double), ("cz", ctypes.c_double),
+                ("radius", ctypes.c_double), ("u0", ctypes.c_double),
+                ("noise_amp", ctypes.c_double), ("seed", ctypes.c_uint64)]
+
+
+class lbpf_diag(ctypes.Structure):
+    _fields_ = [("step", ctypes.c_int64), ("solute_total", ctypes.c_double),
+                ("solute_drift_rel", ctypes.c_double), ("mass_total", ctypes.c_double),
+                ("solid_volume", ctypes.c_double), ("r_eq", ctypes.c_double),
+                ("iface_pos", ctypes.c_double * 6), ("max_u", ctypes.c_double),
+                ("nonfinite", ctypes.c_int64)]
+
+
+EXPORTED = ("lbpf_params_default", "lbpf_create", "lbpf_init_seed", "lbpf_init_fields",
+            "lbpf_step", "lbpf_read_fields", "lbpf_state_bytes", "lbpf_write_state",
+            "lbpf_diagnostics", "lbpf_set_stream", "lbpf_device_bytes", "lbpf_last_error",
+            "lbpf_destroy")
+
+
+def _load_library():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(
+            f"liblbpf.so is not built ({LIB_PATH}); run __graft_entry__.build() first — "
+            "there is no CPU fallback")
+    lib = ctypes.CDLL(LIB_PATH)
+    vp, dp, sz = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_size_t
+    P = ctypes.POINTER(lbpf_params)
+    lib.lbpf_params_default.argtypes = [P]
+    lib.lbpf_create.argtypes = [P, vp, ctypes.POINTER(vp)]
+    lib.lbpf_init_seed.argtypes = [vp, ctypes.POINTER(lbpf_seed)]
+    lib.lbpf_init_fields.argtypes = [vp, dp, dp, dp, dp, dp, dp]
+    lib.lbpf_step.argtypes = [vp, ctypes.c_int]
+    lib.lbpf_read_fields.argtypes = [vp, ctypes.c_uint, vp, sz, ctypes.c_int]
+    lib.lbpf_state_bytes.argtypes = [vp]
+    lib.lbpf_state_bytes.restype = sz
+    lib.lbpf_write_state.argtypes = [vp, vp, sz]
+    lib.lbpf_diagnostics.argtypes = [vp, ctypes.POINTER(lbpf_diag)]
+    lib.lbpf_set_stream.argtypes = [vp, vp]
+    lib.lbpf_device_bytes.argtypes = [vp]
+    lib.lbpf_device_bytes.restype = sz
+    lib.lbpf_last_error.argtypes = [vp]
+    lib.lbpf_last_error.restype = ctypes.c_char_p
+    lib.lbpf_destroy.argtypes = [vp]
+    lib.lbpf_destroy.restype = None
+    for name in EXPORTED:
+        getattr(lib, name).restype = getattr(lib, name).restype if name in (
+            "lbpf_state_bytes", "lbpf_device_bytes", "lbpf_last_error", "lbpf_destroy") \
+            else ctypes.c_int
+    return lib
+
+
+_lib = _load_library()
+
+
+def _check(h, rc: int):
+    if rc != OK:
+        msg = _lib.lbpf_last_error(h).decode() if h else ""
+        raise LbpfError(rc, msg or "see stderr")
+
+
+def _dptr(a):
+    if a is None:
+        return None
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+# ---- C ABI, one function each --------------------------------------------------
+def lbpf_params_default(**overrides) -> lbpf_params:
+    p = lbpf_params()
+    _check(None, _lib.lbpf_params_default(ctypes.byref(p)))
+    for k, v in overrides.items():
+        if k == "lambda":
+            k = "lambda_"
+        if k in ("bc", "body_force"):
+            arr = getattr(p, k)
+            for i in range(3):
+                arr[i] = v[i]
+        else:
+            setattr(p, k, v)
+    return p
+
+
+def lbpf_create(params: lbpf_params, stream: int | None = None) -> int:
+    h = ctypes.c_void_p()
+    rc = _lib.lbpf_create(ctypes.byref(params), ctypes.c_void_p(stream or 0), ctypes.byref(h))
+    if rc != OK:
+        raise LbpfError(rc, "lbpf_create rejected the parameters (reason on stderr)")
+    return h.value
+
+
+def lbpf_init_seed(h: int, cx, cy, cz, radius, u0, noise_amp, seed) -> None:
+    s = lbpf_seed(cx, cy, cz, radius, u0, noise_amp, seed)
+    _check(h, _lib.lbpf_init_seed(h, ctypes.byref(s)))
+
+
+def lbpf_init_fields(h: int, phi, U, rho=None, ux=None, uy=None, uz=None) -> None:
+    arrs = [None if a is None else np.ascontiguousarray(np.asarray(a, np.float64).reshape(-1))
+            for a in (phi, U, rho, ux, uy, uz)]
+    _check(h, _lib.lbpf_init_fields(h, *[_dptr(a) for a in arrs]))
+
+
+def lbpf_step(h: int, n: int = 1) -> None:
+    _check(h, _lib.lbpf_step(h, int(n)))
+
+
+def lbpf_state_bytes(h: int) -> int:
+    return int(_lib.lbpf_state_bytes(h))
+
+
+def lbpf_read_fields(h: int, mask: int, host_dst_ptr: int, nbytes: int, as_fp64: int) -> None:
+    """Raw form: copy into caller-owned host memory at ``host_dst_ptr``."""
+    _check(h, _lib.lbpf_read_fields(h, mask, ctypes.c_void_p(host_dst_ptr), nbytes, as_fp64))
+
+
+def lbpf_write_state(h: int, host_src_ptr: int, nbytes: int) -> None:
+    _check(h, _lib.lbpf_write_state(h, ctypes.c_void_p(host_src_ptr), nbytes))
+
+
+def lbpf_diagnostics(h: int) -> dict:
+    d = lbpf_diag()
+    _check(h, _lib.lbpf_diagnostics(h, ctypes.byref(d)))
+    return {"step": d.step, "solute_total": d.solute_total,
+            "solute_drift_rel": d.solute_drift_rel, "mass_total": d.mass_total,
+            "solid_volume": d.solid_volume, "r_eq": d.r_eq,
+            "iface_pos": np.array(d.iface_pos[:]), "max_u": d.max_u, "nonfinite": d.nonfinite}
+
+
+def lbpf_set_stream(h: int, stream: int | None) -> None:
+    _check(h, _lib.lbpf_set_stream(h, ctypes.c_void_p(stream or 0)))
+
+
+def lbpf_device_bytes(h: int) -> int:
+    return int(_lib.lbpf_device_bytes(h))
+
+
+def lbpf_last_error(h: int) -> str:
+    return _lib.lbpf_last_error(h).decode()
+
+
+def lbpf_destroy(h: int) -> None:
+    _lib.lbpf_destroy(h)
+
+
+# ---- convenience wrapper -------------------------------------------------------------
+def current_stream() -> int:
+    """The calling thread's current torch CUDA stream (PyTorch supplies streams)."""
+    import torch
+    return torch.cuda.current_stream().cuda_stream
+
+
+class Sim:
+    """One simulation handle: owns its device state, runs on a CUDA stream."""
+
+    def __init__(self, stream: int | None = None, **params):
+        self.params = lbpf_params_default(**params)
+        self.h = lbpf_create(self.params, stream)
+        p = self.params
+        self.shape = (p.nz, p.ny, p.nx) if p.dim == 3 else (p.ny, p.nx)
+        self.nodes = int(np.prod(self.shape))
+
+    def close(self):
+        if getattr(self, "h", None):
+            lbpf_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def init_seed(self, cx, cy, cz=0.0, radius=8.0, u0=0.3, noise_amp=0.0, seed=1):
+        lbpf_init_seed(self.h, cx, cy, cz, radius, u0, noise_amp, seed)
+
+    def init_fields(self, phi, U, rho=None, ux=None, uy=None, uz=None):
+        lbpf_init_fields(self.h, phi, U, rho, ux, uy, uz)
+
+    def step(self, n: int = 1):
+        lbpf_step(self.h, n)
+
+    def fields(self, names=("phi", "U", "rho", "ux", "uy"), fp64: bool = True) -> dict:
+        mask = 0
+        for nm in names:
+            mask |= 1 << FIELD_NAMES.index(nm)
+        order = [nm for nm in FIELD_NAMES if mask & (1 << FIELD_NAMES.index(nm))]
+        out = np.empty((len(order), self.nodes), np.float64 if fp64 else np.float32)
+        lbpf_read_fields(self.h, mask, out.ctypes.data, out.nbytes, 1 if fp64 else 0)
+        return {nm: out[i].reshape(self.shape) for i, nm in enumerate(order)}
+
+    def state(self) -> np.ndarray:
+        buf = np.empty(lbpf_state_bytes(self.h), np.uint8)
+        lbpf_read_fields(self.h, FIELD_STATE, buf.ctypes.data, buf.nbytes, 0)
+        return buf
+
+    def load_state(self, buf: np.ndarray):
+        buf = np.ascontiguousarray(buf, dtype=np.uint8)
+        lbpf_write_state(self.h, buf.ctypes.data, buf.nbytes)
+
+    def pops(self, buf: np.ndarray | None = None) -> dict:
+        """Populations from the exported state: {'f','g','h'} arrays [q, ...]."""
+        if buf is None:
+            buf = self.state()
+        hdr = np.frombuffer(buf[:64].tobytes(), dtype=np.int32, count=12, offset=16)
+        q, elem, flow, dim = int(hdr[6]), int(hdr[7]), int(hdr[5]), int(hdr[0])
+        dt = {8: np.float64, 4: np.float32, 2: np.float16}[elem]
+        n = self.nodes
+        raw = np.frombuffer(buf[64:64 + q * n * elem].tobytes(), dtype=dt).reshape((q,) + self.shape)
+        qf = (9 if dim == 2 else 19) if flow else 0
+        qs = 9 if dim == 2 else 7
+        return {"f": raw[:qf], "g": raw[qf:qf + qs], "h": raw[qf + qs:]}
+
+    def diagnostics(self) -> dict:
+        return lbpf_diagnostics(self.h)

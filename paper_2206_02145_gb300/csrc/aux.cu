@@ -1,0 +1,339 @@
+// Initial state, moment read-out and FP64 diagnostics of liblbpf.so.
+#include "lbpf_device.cuh"
+
+namespace lbk {
+namespace {
+
+__device__ __forceinline__ void node_xyz(const Model& m, long long i, int& x, int& y, int& z) {
+  x = int(i % m.nx);
+  long long r = i / m.nx;
+  y = int(r % m.ny);
+  z = int(r / m.ny);
+}
+__device__ __forceinline__ long long pitched(const Model& m, int x, int y, int z) {
+  return ((long long)z * m.ny + y) * m.px + x;
+}
+
+// SplitMix64 (Steele, Lea and Flood, OOPSLA 2014): Weyl increment
+// 0x9E3779B97F4A7C15 followed by the two xor-shift-multiply rounds.
+__device__ __forceinline__ unsigned long long splitmix64(unsigned long long z) {
+  z += 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+// Equilibrium populations of (rho, u*, U, phi) in FP64 (Eq. 9 at second
+// order, Eq. 16, Eq. 21 with N = 0), stored in the population type.
+template <typename T>
+__device__ void store_equilibrium(const Model& m, T* pops, long long j, double phi, double U,
+                                  double rho, double ux, double uy, double uz) {
+  const long long P = m.plane;
+  const double ph = phi < -1.0 ? -1.0 : (phi > 1.0 ? 1.0 : phi);
+  const double mask = m.flow ? 0.5 * (1.0 - ph) : 0.0;
+  const double us[3] = {mask * ux, mask * uy, mask * uz};
+  const double uu = us[0] * us[0] + us[1] * us[1] + us[2] * us[2];
+  T* pf = pops;
+  T* pg = pops + (long long)m.qf * P;
+  T* ph_ = pops + (long long)(m.qf + m.qs) * P;
+  if (m.dim == 2) {
+    for (int a = 0; a < 9; ++a) {
+      const double w = d2_w<double>(a);
+      const double cu = D2_CX[a] * us[0] + D2_CY[a] * us[1];
+      if (m.flow)
+        Pop<T>::st(pf + a * P + j, rho * w * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * uu),
+                   w * m.ref_f);
+      Pop<T>::st(pg + a * P + j, w * U * (1.0 + 3.0 * cu), w * m.ref_g);
+      Pop<T>::st(ph_ + a * P + j, w * phi, w * m.ref_h);
+    }
+  } else {
+    if (m.flow)
+      for (int a = 0; a < 19; ++a) {
+        const double w = d3q19_w<double>(a);
+        const double cu = D3_CX[a] * us[0] + D3_CY[a] * us[1] + D3_CZ[a] * us[2];
+        Pop<T>::st(pf + a * P + j, rho * w * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * uu),
+                   w * m.ref_f);
+      }
+    for (int a = 0; a < 7; ++a) {
+      const double w = d3q7_w<double>(a);
+      const double cu = D3_CX[a] * us[0] + D3_CY[a] * us[1] + D3_CZ[a] * us[2];
+      Pop<T>::st(pg + a * P + j, w * U * (1.0 + 4.0 * cu), w * m.ref_g);  // cs^2 = 1/4
+      Pop<T>::st(ph_ + a * P + j, w * phi, w * m.ref_h);
+    }
+  }
+}
+
+template <typename T, typename R>
+__global__ void init_seed_kernel(const Model m, const SeedArgs s, T* pops, R* phi_prev) {
+  const long long n = (long long)m.nx * m.ny * m.nz;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    int x, y, z;
+    node_xyz(m, i, x, y, z);
+    const double dx = x - s.cx, dy = y - s.cy, dz = m.dim == 3 ? z - s.cz : 0.0;
+    const double r = sqrt(dx * dx + dy * dy + dz * dz);
+    double phi = tanh((s.radius - r) / (sqrt(2.0) * m.w0));
+    const unsigned long long bits =
+        splitmix64(s.seed ^ ((unsigned long long)i * 0x9E3779B97F4A7C15ull));
+    const double xi = double(bits >> 11) * 0x1.0p-52 - 1.0;  // [-1, 1)
+    phi += s.noise_amp * xi;
+    const long long j = pitched(m, x, y, z);
+    store_equilibrium<T>(m, pops, j, phi, s.u0, 1.0, m.flow ? m.u_in : 0.0, 0.0, 0.0);
+    phi_prev[j] = R(phi);
+  }
+}
+
+template <typename T, typename R>
+__global__ void init_fields_kernel(const Model m, const double* phi, const double* U,
+                                   const double* rho, const double* ux, const double* uy,
+                                   const double* uz, T* pops, R* phi_prev) {
+  const long long n = (long long)m.nx * m.ny * m.nz;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    int x, y, z;
+    node_xyz(m, i, x, y, z);
+    const long long j = pitched(m, x, y, z);
+    store_equilibrium<T>(m, pops, j, phi[i], U[i], rho ? rho[i] : 1.0, ux ? ux[i] : 0.0,
+                         uy ? uy[i] : 0.0, uz ? uz[i] : 0.0);
+    phi_prev[j] = R(phi[i]);
+  }
+}
+
+// Moments of one node in FP64 from the stored populations.
+template <typename T>
+__device__ void node_moments(const Model& m, const T* pops, long long j, double& phi, double& U,
+                             double& rho, double u[3]) {
+  const long long P = m.plane;
+  const T* pf = pops;
+  const T* pg = pops + (long long)m.qf * P;
+  const T* ph_ = pops + (long long)(m.qf + m.qs) * P;
+  phi = U = 0.0;
+  rho = 1.0;
+  double mo[3] = {0.0, 0.0, 0.0};
+  if (m.dim == 2) {
+    for (int a = 0; a < 9; ++a) {
+      const double w = d2_w<double>(a);
+      U += Pop<T>::ld(pg + a * P + j, w * m.ref_g);
+      phi += Pop<T>::ld(ph_ + a * P + j, w * m.ref_h);
+    }
+    if (m.flow) {
+      rho = 0.0;
+      for (int a = 0; a < 9; ++a) {
+        const double v = Pop<T>::ld(pf + a * P + j, d2_w<double>(a) * m.ref_f);
+        rho += v;
+        mo[0] += D2_CX[a] * v;
+        mo[1] += D2_CY[a] * v;
+      }
+    }
+  } else {
+    for (int a = 0; a < 7; ++a) {
+      const double w = d3q7_w<double>(a);
+      U += Pop<T>::ld(pg + a * P + j, w * m.ref_g);
+      phi += Pop<T>::ld(ph_ + a * P + j, w * m.ref_h);
+    }
+    if (m.flow) {
+      rho = 0.0;
+      for (int a = 0; a < 19; ++a) {
+        const double v = Pop<T>::ld(pf + a * P + j, d3q19_w<double>(a) * m.ref_f);
+        rho += v;
+        mo[0] += D3_CX[a] * v;
+        mo[1] += D3_CY[a] * v;
+        mo[2] += D3_CZ[a] * v;
+      }
+    }
+  }
+  const double ph = phi < -1.0 ? -1.0 : (phi > 1.0 ? 1.0 : phi);
+  const double K = m.flow ? m.kdrag * (1.0 + ph) * (1.0 + ph) * (1.0 - ph) : 0.0;
+  for (int d = 0; d < 3; ++d)
+    u[d] = m.flow ? (mo[d] + 0.5 * m.body[d]) / (rho + 0.5 * K) : 0.0;
+}
+
+template <typename T, typename R, typename O>
+__global__ void fields_kernel(const Model m, const T* pops, const R* phi_prev, unsigned mask,
+                              O* out) {
+  const long long n = (long long)m.nx * m.ny * m.nz;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    int x, y, z;
+    node_xyz(m, i, x, y, z);
+    const long long j = pitched(m, x, y, z);
+    double phi, U, rho, u[3];
+    node_moments<T>(m, pops, j, phi, U, rho, u);
+    const double vals[7] = {phi, U, rho, u[0], u[1], u[2], double(phi_prev[j])};
+    int slot = 0;
+    for (int b = 0; b < 7; ++b)
+      if (mask & (1u << b)) out[(long long)(slot++) * n + i] = O(vals[b]);
+  }
+}
+
+constexpr int kDiagBlocks = 152 * 4;
+constexpr int kDiagThreads = 256;
+constexpr int kDiagSlots = 5;  // sum(U + phi_prev), sum(rho), solid, max|u|, nonfinite
+
+template <typename T, typename R>
+__global__ void __launch_bounds__(kDiagThreads)
+    diag_partial_kernel(const Model m, const T* pops, const R* phi_prev, double* partials) {
+  const long long n = (long long)m.nx * m.ny * m.nz;
+  double acc[kDiagSlots] = {0.0, 0.0, 0.0, 0.0, 0.0};
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    int x, y, z;
+    node_xyz(m, i, x, y, z);
+    const long long j = pitched(m, x, y, z);
+    double phi, U, rho, u[3];
+    node_moments<T>(m, pops, j, phi, U, rho, u);
+    const double pp = double(phi_prev[j]);
+    const double ph = phi < -1.0 ? -1.0 : (phi > 1.0 ? 1.0 : phi);
+    acc[0] += U + pp;
+    acc[1] += rho;
+    acc[2] += 0.5 * (1.0 + ph);
+    const double um = sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+    acc[3] = um > acc[3] ? um : acc[3];
+    if (!(isfinite(phi) && isfinite(U) && isfinite(rho))) acc[4] += 1.0;
+  }
+  __shared__ double sh[kDiagSlots][kDiagThreads];
+  for (int k = 0; k < kDiagSlots; ++k) sh[k][threadIdx.x] = acc[k];
+  __syncthreads();
+  for (int w = kDiagThreads / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w)
+      for (int k = 0; k < kDiagSlots; ++k) {
+        const double o = sh[k][threadIdx.x + w];
+        sh[k][threadIdx.x] = k == 3 ? (o > sh[k][threadIdx.x] ? o : sh[k][threadIdx.x])
+                                    : sh[k][threadIdx.x] + o;
+      }
+    __syncthreads();
+  }
+  if (threadIdx.x < kDiagSlots) partials[blockIdx.x * kDiagSlots + threadIdx.x] = sh[threadIdx.x][0];
+}
+
+__global__ void __launch_bounds__(kDiagThreads)
+    diag_final_kernel(const double* partials, int nblocks, double* out) {
+  __shared__ double sh[kDiagSlots][kDiagThreads];
+  double acc[kDiagSlots] = {0.0, 0.0, 0.0, 0.0, 0.0};
+  for (int b = threadIdx.x; b < nblocks; b += blockDim.x)
+    for (int k = 0; k < kDiagSlots; ++k) {
+      const double v = partials[b * kDiagSlots + k];
+      acc[k] = k == 3 ? (v > acc[k] ? v : acc[k]) : acc[k] + v;
+    }
+  for (int k = 0; k < kDiagSlots; ++k) sh[k][threadIdx.x] = acc[k];
+  __syncthreads();
+  for (int w = kDiagThreads / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w)
+      for (int k = 0; k < kDiagSlots; ++k) {
+        const double o = sh[k][threadIdx.x + w];
+        sh[k][threadIdx.x] = k == 3 ? (o > sh[k][threadIdx.x] ? o : sh[k][threadIdx.x])
+                                    : sh[k][threadIdx.x] + o;
+      }
+    __syncthreads();
+  }
+  if (threadIdx.x < kDiagSlots) out[threadIdx.x] = sh[threadIdx.x][0];
+}
+
+// phi = 0 crossing along the six axis rays from (icx, icy, icz): the first
+// sign change from phi >= 0 to phi < 0, linearly interpolated; -1 if none.
+template <typename T>
+__global__ void crossing_kernel(const Model m, const T* pops, int icx, int icy, int icz,
+                                double* out) {
+  const int r = threadIdx.x;
+  if (r >= 6) return;
+  const int axis = r / 2, dir = (r & 1) ? -1 : 1;
+  double res = -1.0;
+  if (axis < m.dim) {
+    const int n = axis == 0 ? m.nx : (axis == 1 ? m.ny : m.nz);
+    int c[3] = {icx, icy, m.dim == 3 ? icz : 0};
+    double phi, U, rho, u[3];
+    node_moments<T>(m, pops, pitched(m, c[0], c[1], c[2]), phi, U, rho, u);
+    double prev = phi;
+    if (prev >= 0.0) {
+      const int limit = m.bc[axis] == BC_PERIODIC ? n / 2 : n;
+      const int start = c[axis];
+      for (int d = 1; d < limit; ++d) {
+        int v = start + dir * d;
+        if (m.bc[axis] == BC_PERIODIC) v = ((v % n) + n) % n;
+        else if (v < 0 || v >= n) break;
+        c[axis] = v;
+        node_moments<T>(m, pops, pitched(m, c[0], c[1], c[2]), phi, U, rho, u);
+        if (phi < 0.0) {
+          res = double(d - 1) + prev / (prev - phi);
+          break;
+        }
+        prev = phi;
+      }
+    }
+  }
+  out[5 + r] = res;
+}
+
+int grid_for(long long n) {
+  long long b = (n + 255) / 256;
+  return int(b < 152 * 16 ? (b < 1 ? 1 : b) : 152 * 16);
+}
+
+template <typename T, typename R>
+cudaError_t init_seed_t(const Model& m, const SeedArgs& a, void* pops, void* pp, cudaStream_t s) {
+  const long long n = (long long)m.nx * m.ny * m.nz;
+  init_seed_kernel<T, R><<<grid_for(n), 256, 0, s>>>(m, a, static_cast<T*>(pops),
+                                                     static_cast<R*>(pp));
+  return cudaGetLastError();
+}
+template <typename T, typename R>
+cudaError_t init_fields_t(const Model& m, const double* phi, const double* U, const double* rho,
+                          const double* ux, const double* uy, const double* uz, void* pops,
+                          void* pp, cudaStream_t s) {
+  const long long n = (long long)m.nx * m.ny * m.nz;
+  init_fields_kernel<T, R><<<grid_for(n), 256, 0, s>>>(m, phi, U, rho, ux, uy, uz,
+                                                       static_cast<T*>(pops), static_cast<R*>(pp));
+  return cudaGetLastError();
+}
+template <typename T, typename R>
+cudaError_t fields_t(const Model& m, const void* pops, const void* pp, unsigned mask, int fp64,
+                     void* out, cudaStream_t s) {
+  const long long n = (long long)m.nx * m.ny * m.nz;
+  if (fp64)
+    fields_kernel<T, R, double><<<grid_for(n), 256, 0, s>>>(
+        m, static_cast<const T*>(pops), static_cast<const R*>(pp), mask, static_cast<double*>(out));
+  else
+    fields_kernel<T, R, float><<<grid_for(n), 256, 0, s>>>(
+        m, static_cast<const T*>(pops), static_cast<const R*>(pp), mask, static_cast<float*>(out));
+  return cudaGetLastError();
+}
+template <typename T, typename R>
+cudaError_t diag_t(const Model& m, const void* pops, const void* pp, double* partials,
+                   double* out, int icx, int icy, int icz, cudaStream_t s) {
+  diag_partial_kernel<T, R><<<kDiagBlocks, kDiagThreads, 0, s>>>(
+      m, static_cast<const T*>(pops), static_cast<const R*>(pp), partials);
+  diag_final_kernel<<<1, kDiagThreads, 0, s>>>(partials, kDiagBlocks, out);
+  crossing_kernel<T><<<1, 32, 0, s>>>(m, static_cast<const T*>(pops), icx, icy, icz, out);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+#define LBPF_DISPATCH(FN, ...)                                          \
+  switch (m.storage) {                                                  \
+    case ST_FP64: return FN<double, double>(__VA_ARGS__);               \
+    case ST_FP16: return FN<__half, float>(__VA_ARGS__);                \
+    case ST_BF16: return FN<__nv_bfloat16, float>(__VA_ARGS__);         \
+    default: return FN<float, float>(__VA_ARGS__);                      \
+  }
+
+cudaError_t launch_init_seed(const Model& m, const SeedArgs& a, void* pops, void* phi_prev,
+                             cudaStream_t s) {
+  LBPF_DISPATCH(init_seed_t, m, a, pops, phi_prev, s)
+}
+cudaError_t launch_init_fields(const Model& m, const double* phi, const double* U,
+                               const double* rho, const double* ux, const double* uy,
+                               const double* uz, void* pops, void* phi_prev, cudaStream_t s) {
+  LBPF_DISPATCH(init_fields_t, m, phi, U, rho, ux, uy, uz, pops, phi_prev, s)
+}
+cudaError_t launch_fields(const Model& m, const void* pops, const void* phi_prev, unsigned mask,
+                          int fp64, void* out, cudaStream_t s) {
+  LBPF_DISPATCH(fields_t, m, pops, phi_prev, mask, fp64, out, s)
+}
+size_t diag_partials_bytes(const Model&) { return sizeof(double) * kDiagBlocks * kDiagSlots; }
+cudaError_t launch_diag(const Model& m, const void* pops, const void* phi_prev, double* partials,
+                        double* out, int icx, int icy, int icz, cudaStream_t s) {
+  LBPF_DISPATCH(diag_t, m, pops, phi_prev, partials, out, icx, icy, icz, s)
+}
+
+}  // namespace lbk

@@ -1,0 +1,523 @@
+// Host side of the C ABI declared in include/lbpf.h: parameter validation,
+// device memory, the step loop with its CUDA-graph replay, state export and
+// restore, field read-out and FP64 diagnostics.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+#include "../../include/lbpf.h"
+#include "lbpf_internal.cuh"
+
+using lbk::Model;
+
+struct lbpf {
+  lbpf_params p;
+  Model m;
+  cudaStream_t stream = nullptr;
+  cudaStream_t cap_stream = nullptr;  // private stream used only to capture graphs
+  void* pops[2] = {nullptr, nullptr};
+  void* phi[2] = {nullptr, nullptr};  // phi[cur] holds phi(t-1)
+  int cur = 0;
+  long long step = 0;
+  bool initialized = false;
+  unsigned* d_err = nullptr;
+  double* d_partials = nullptr;
+  double* d_diag = nullptr;  // [0..10] diag outputs, [16] solute total at init
+  void* d_fields = nullptr;
+  size_t fields_cap = 0;
+  int icx = 0, icy = 0, icz = 0;
+  size_t dev_bytes = 0;
+  size_t es = 4;  // population element bytes
+  size_t rs = 4;  // phi ring element bytes
+  cudaGraphExec_t graph = nullptr;
+  int graph_steps = 0;
+  int status = LBPF_OK;
+  char msg[256] = {0};
+};
+
+namespace {
+
+constexpr int kGraphSteps = 64;  // even, so a replay keeps the buffer parity
+
+int fail(lbpf* h, int code, const char* fmt, ...) {
+  if (!h) return code;
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(h->msg, sizeof(h->msg), fmt, ap);
+  va_end(ap);
+  if (code == LBPF_ECUDA || code == LBPF_ENONFINITE || code == LBPF_ETIMEDOUT) h->status = code;
+  return code;
+}
+
+#define CK(h, call)                                                                     \
+  do {                                                                                  \
+    cudaError_t e_ = (call);                                                            \
+    if (e_ != cudaSuccess)                                                              \
+      return fail(h, LBPF_ECUDA, "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, \
+                  __LINE__);                                                            \
+  } while (0)
+
+long long nodes(const lbpf_params& p) {
+  return (long long)p.nx * p.ny * (p.dim == 3 ? p.nz : 1);
+}
+
+int validate(const lbpf_params* p, char* why, size_t n) {
+  auto bad = [&](const char* s) {
+    snprintf(why, n, "%s", s);
+    return LBPF_EINVAL;
+  };
+  if (p->dim != 2 && p->dim != 3) return bad("dim must be 2 or 3");
+  if (p->nx < 4 || p->ny < 4 || (p->dim == 3 && p->nz < 4)) return bad("every grid dimension must be >= 4");
+  if ((double)p->nx * p->ny * (p->dim == 3 ? p->nz : 1) > 4.0e9) return bad("grid too large");
+  for (int d = 0; d < 3; ++d)
+    if (p->bc[d] < 0 || p->bc[d] > 2) return bad("unknown boundary condition");
+  if (p->bc[1] == LBPF_BC_INLET_OUTLET || p->bc[2] == LBPF_BC_INLET_OUTLET)
+    return bad("INLET_OUTLET is only available on x");
+  if (p->storage < 0 || p->storage > 3) return bad("unknown storage");
+  if (!(p->tau_phi0 > 0.5) || !(p->tau_u_liquid > 0.5)) return bad("relaxation times must exceed 1/2");
+  if (p->flow && !(p->tau_f > 0.5)) return bad("tau_f must exceed 1/2");
+  if (!(p->w0 > 0.0)) return bad("W0 must be positive");
+  if (!(p->eps_aniso >= 0.0 && p->eps_aniso < 1.0)) return bad("eps must be in [0, 1)");
+  if (p->fold < 0 || p->fold > 12) return bad("fold must be 0..12");
+  if (p->dim == 3 && p->fold != 0) return bad("3D supports the cubic form only (fold = 0)");
+  if (!(std::fabs(p->u_inlet) <= 0.1)) return bad("|u_inlet| must be <= 0.1 (low Mach)");
+  if (!std::isfinite(p->lambda) || !std::isfinite(p->theta0) || !std::isfinite(p->h_drag) ||
+      !std::isfinite(p->u0_inlet))
+    return bad("non-finite parameter");
+  for (int d = 0; d < 3; ++d)
+    if (!std::isfinite(p->body_force[d])) return bad("non-finite body force");
+  return LBPF_OK;
+}
+
+Model derive(const lbpf_params& p) {
+  Model m{};
+  m.dim = p.dim;
+  m.nx = p.nx;
+  m.ny = p.ny;
+  m.nz = p.dim == 3 ? p.nz : 1;
+  m.px = (p.nx + 31) / 32 * 32;
+  m.plane = (long long)m.px * m.ny * m.nz;
+  for (int d = 0; d < 3; ++d) m.bc[d] = p.bc[d];
+  if (p.dim == 2) m.bc[2] = LBPF_BC_PERIODIC;
+  m.flow = p.flow ? 1 : 0;
+  m.fold = p.fold;
+  m.storage = p.storage;
+  m.qf = p.flow ? (p.dim == 2 ? 9 : 19) : 0;
+  m.qs = p.dim == 2 ? 9 : 7;
+  const double cs2 = p.dim == 2 ? 1.0 / 3.0 : 0.25;  // lattice of g and h
+  const double tau0 = p.w0 * p.w0 / (cs2 * (p.tau_phi0 - 0.5));  // Eq. 23 at a_s = 1
+  m.omega_f = p.flow ? 1.0 / p.tau_f : 0.0;
+  m.guo = p.flow ? 1.0 - 0.5 / p.tau_f : 0.0;
+  m.tauU_slope = p.tau_u_liquid - 0.5;
+  m.inv_tau0 = 1.0 / tau0;
+  m.tpc = p.w0 * p.w0 / (cs2 * tau0);
+  if (p.lambda >= 0.0) {
+    m.lambda = p.lambda;
+  } else {
+    const double D = cs2 * (p.tau_u_liquid - 0.5);
+    m.lambda = D * tau0 / (0.6267 * p.w0 * p.w0);  // thin-interface value, a2 = 0.6267
+  }
+  m.eps = p.eps_aniso;
+  m.ck0 = std::cos(p.fold * p.theta0);
+  m.sk0 = std::sin(p.fold * p.theta0);
+  m.aniso_fac = p.aniso_literal ? 2.0 : 1.0;
+  m.kdrag = p.flow ? p.h_drag * p.tau_f / (4.0 * p.w0 * p.w0) : 0.0;
+  m.w0 = p.w0;
+  for (int d = 0; d < 3; ++d) m.body[d] = p.flow ? p.body_force[d] : 0.0;
+  m.u_in = p.flow ? p.u_inlet : 0.0;
+  m.U_in = p.u0_inlet;
+  m.ref_f = 1.0;
+  m.ref_g = 0.0;
+  m.ref_h = 0.0;
+  return m;
+}
+
+bool is16(const Model& m) { return m.storage == lbk::ST_FP16 || m.storage == lbk::ST_BF16; }
+
+int check_handle(lbpf* h) {
+  if (!h) return LBPF_EINVAL;
+  if (h->status != LBPF_OK) return h->status;
+  return LBPF_OK;
+}
+
+int check_device_error(lbpf* h) {
+  unsigned e = 0;
+  CK(h, cudaMemcpyAsync(&e, h->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost, h->stream));
+  CK(h, cudaStreamSynchronize(h->stream));
+  if (e & 1u) return fail(h, LBPF_ENONFINITE, "a non-finite phi, U or rho appeared in the step");
+  return LBPF_OK;
+}
+
+int launch_one(lbpf* h, cudaStream_t s) {
+  const int c = h->cur;
+  cudaError_t e = h->m.dim == 2
+                      ? lbk::launch_step2d(h->m, h->pops[c], h->pops[c ^ 1], h->phi[c],
+                                            h->phi[c ^ 1], h->d_err, s)
+                      : lbk::launch_step3d(h->m, h->pops[c], h->pops[c ^ 1], h->phi[c],
+                                            h->phi[c ^ 1], h->d_err, s);
+  if (e != cudaSuccess) return fail(h, LBPF_ECUDA, "step launch: %s", cudaGetErrorString(e));
+  h->cur ^= 1;
+  return LBPF_OK;
+}
+
+// Capture kGraphSteps launches starting from buffer parity 0.
+int build_graph(lbpf* h) {
+  if (h->graph) return LBPF_OK;
+  if (!h->cap_stream) CK(h, cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+  const int saved = h->cur;
+  h->cur = 0;
+  cudaGraph_t g = nullptr;
+  CK(h, cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+  int rc = LBPF_OK;
+  for (int i = 0; i < kGraphSteps && rc == LBPF_OK; ++i) rc = launch_one(h, h->cap_stream);
+  cudaError_t e = cudaStreamEndCapture(h->cap_stream, &g);
+  h->cur = saved;
+  if (rc != LBPF_OK) {
+    if (g) cudaGraphDestroy(g);
+    return rc;
+  }
+  if (e != cudaSuccess) return fail(h, LBPF_ECUDA, "graph capture: %s", cudaGetErrorString(e));
+  e = cudaGraphInstantiate(&h->graph, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return fail(h, LBPF_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
+  h->graph_steps = kGraphSteps;
+  return LBPF_OK;
+}
+
+// The graph bakes the model constants in; drop it when they change.
+void drop_graph(lbpf* h) {
+  if (h->graph) cudaGraphExecDestroy(h->graph);
+  h->graph = nullptr;
+  h->graph_steps = 0;
+}
+
+int ensure_fields_buffer(lbpf* h, size_t bytes) {
+  if (h->fields_cap >= bytes) return LBPF_OK;
+  if (h->d_fields) {
+    cudaFree(h->d_fields);
+    h->dev_bytes -= h->fields_cap;
+    h->d_fields = nullptr;
+    h->fields_cap = 0;
+  }
+  cudaError_t e = cudaMalloc(&h->d_fields, bytes);
+  if (e != cudaSuccess) return fail(h, LBPF_ENOMEM, "field buffer: %s", cudaGetErrorString(e));
+  h->fields_cap = bytes;
+  h->dev_bytes += bytes;
+  return LBPF_OK;
+}
+
+void store_I0(lbpf* h) {
+  // solute total at init, kept on the device for the drift of lbpf_diagnostics
+  lbk::launch_diag(h->m, h->pops[h->cur], h->phi[h->cur], h->d_partials, h->d_diag, h->icx,
+                    h->icy, h->icz, h->stream);
+  cudaMemcpyAsync(h->d_diag + 16, h->d_diag, sizeof(double), cudaMemcpyDeviceToDevice, h->stream);
+}
+
+constexpr char kMagic[8] = {'L', 'B', 'P', 'F', 'S', 'T', '0', '1'};
+
+struct StateHeader {
+  char magic[8];
+  int64_t step;
+  int32_t dim, nx, ny, nz, storage, flow, q, elem;
+  double ref_g;  // equilibrium shift of g in 16-bit storage
+  char pad[8];
+};
+static_assert(sizeof(StateHeader) == 64, "state header must be 64 bytes");
+
+}  // namespace
+
+extern "C" {
+
+int lbpf_params_default(lbpf_params* p) {
+  if (!p) return LBPF_EINVAL;
+  std::memset(p, 0, sizeof(*p));
+  p->dim = 2;
+  p->nx = p->ny = 128;
+  p->nz = 1;
+  p->fold = 4;
+  p->tau_phi0 = 0.8;
+  p->tau_u_liquid = 0.8;
+  p->tau_f = 0.6;
+  p->w0 = 2.0;
+  p->lambda = -1.0;
+  p->eps_aniso = 0.05;
+  p->h_drag = 2.757;
+  return LBPF_OK;
+}
+
+int lbpf_create(const lbpf_params* p, void* stream, lbpf_t** out) {
+  if (!p || !out) return LBPF_EINVAL;
+  *out = nullptr;
+  char why[160];
+  if (validate(p, why, sizeof(why)) != LBPF_OK) {
+    fprintf(stderr, "lbpf_create: %s\n", why);
+    return LBPF_EINVAL;
+  }
+  lbpf* h = new (std::nothrow) lbpf();
+  if (!h) return LBPF_ENOMEM;
+  h->p = *p;
+  if (h->p.dim == 2) h->p.nz = 1;
+  h->m = derive(h->p);
+  h->stream = static_cast<cudaStream_t>(stream);
+  h->es = h->m.storage == lbk::ST_FP64 ? 8 : (is16(h->m) ? 2 : 4);
+  h->rs = h->m.storage == lbk::ST_FP64 ? 8 : 4;
+  const size_t q = size_t(h->m.qf + 2 * h->m.qs);
+  const size_t pop_bytes = q * size_t(h->m.plane) * h->es;
+  const size_t ring_bytes = size_t(h->m.plane) * h->rs;
+  cudaError_t e = cudaSuccess;
+  for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = cudaMalloc(&h->pops[i], pop_bytes);
+  for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = cudaMalloc(&h->phi[i], ring_bytes);
+  if (e == cudaSuccess) e = cudaMalloc(&h->d_err, 256);
+  if (e == cudaSuccess) e = cudaMalloc(&h->d_partials, lbk::diag_partials_bytes(h->m));
+  if (e == cudaSuccess) e = cudaMalloc(&h->d_diag, 32 * sizeof(double));
+  if (e != cudaSuccess) {
+    fprintf(stderr, "lbpf_create: %s\n", cudaGetErrorString(e));
+    lbpf_destroy(h);
+    return LBPF_ENOMEM;
+  }
+  h->dev_bytes = 2 * pop_bytes + 2 * ring_bytes + 256 + lbk::diag_partials_bytes(h->m) +
+                 32 * sizeof(double);
+  e = cudaMemsetAsync(h->d_err, 0, 256, h->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->d_diag, 0, 32 * sizeof(double), h->stream);
+  if (e != cudaSuccess) {
+    fprintf(stderr, "lbpf_create: %s\n", cudaGetErrorString(e));
+    lbpf_destroy(h);
+    return LBPF_ECUDA;
+  }
+  h->icx = h->m.nx / 2;
+  h->icy = h->m.ny / 2;
+  h->icz = h->m.nz / 2;
+  *out = h;
+  return LBPF_OK;
+}
+
+int lbpf_init_seed(lbpf_t* h, const lbpf_seed* s) {
+  int rc = check_handle(h);
+  if (rc) return rc;
+  if (!s || !(s->radius >= 0.0) || !std::isfinite(s->u0) || !std::isfinite(s->noise_amp) ||
+      !std::isfinite(s->cx) || !std::isfinite(s->cy) || !std::isfinite(s->cz))
+    return fail(h, LBPF_EINVAL, "invalid seed");
+  h->m.ref_g = is16(h->m) ? s->u0 : 0.0;
+  h->m.ref_h = 0.0;
+  drop_graph(h);
+  lbk::SeedArgs a{s->cx, s->cy, s->cz, s->radius, s->u0, s->noise_amp, s->seed};
+  h->cur = 0;
+  h->step = 0;
+  CK(h, lbk::launch_init_seed(h->m, a, h->pops[0], h->phi[0], h->stream));
+  auto clampi = [](double v, int n) {
+    long long i = std::llround(v);
+    return int(i < 0 ? 0 : (i >= n ? n - 1 : i));
+  };
+  h->icx = clampi(s->cx, h->m.nx);
+  h->icy = clampi(s->cy, h->m.ny);
+  h->icz = h->m.dim == 3 ? clampi(s->cz, h->m.nz) : 0;
+  h->initialized = true;
+  store_I0(h);
+  CK(h, cudaGetLastError());
+  return LBPF_OK;
+}
+
+int lbpf_init_fields(lbpf_t* h, const double* phi, const double* U, const double* rho,
+                     const double* ux, const double* uy, const double* uz) {
+  int rc = check_handle(h);
+  if (rc) return rc;
+  if (!phi || !U) return fail(h, LBPF_EINVAL, "phi and U are required");
+  const size_t n = size_t(nodes(h->p));
+  const double* src[6] = {phi, U, rho, ux, uy, uz};
+  double* dev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  double* block = nullptr;
+  CK(h, cudaMalloc(&block, 6 * n * sizeof(double)));
+  for (int k = 0; k < 6; ++k) {
+    if (!src[k]) continue;
+    dev[k] = block + k * n;
+    cudaError_t e = cudaMemcpyAsync(dev[k], src[k], n * sizeof(double), cudaMemcpyHostToDevice,
+                                    h->stream);
+    if (e != cudaSuccess) {
+      cudaFree(block);
+      return fail(h, LBPF_ECUDA, "init_fields copy: %s", cudaGetErrorString(e));
+    }
+  }
+  // 16-bit storage shifts g by the mean initial U
+  if (is16(h->m)) {
+    double mean = 0.0;
+    for (size_t i = 0; i < n; ++i) mean += U[i];
+    h->m.ref_g = mean / double(n);
+  }
+  drop_graph(h);
+  h->cur = 0;
+  h->step = 0;
+  cudaError_t e = lbk::launch_init_fields(h->m, dev[0], dev[1], dev[2], dev[3], dev[4], dev[5],
+                                           h->pops[0], h->phi[0], h->stream);
+  cudaError_t e2 = cudaStreamSynchronize(h->stream);
+  cudaFree(block);
+  if (e != cudaSuccess || e2 != cudaSuccess)
+    return fail(h, LBPF_ECUDA, "init_fields: %s",
+                cudaGetErrorString(e != cudaSuccess ? e : e2));
+  h->initialized = true;
+  store_I0(h);
+  CK(h, cudaGetLastError());
+  return LBPF_OK;
+}
+
+int lbpf_step(lbpf_t* h, int n) {
+  int rc = check_handle(h);
+  if (rc) return rc;
+  if (n < 0) return fail(h, LBPF_EINVAL, "n must be >= 0");
+  if (!h->initialized) return fail(h, LBPF_ESTATE, "step before init");
+  int left = n;
+  if (left >= kGraphSteps) {
+    if (h->cur == 1) {
+      if ((rc = launch_one(h, h->stream))) return rc;
+      --left;
+    }
+    if (left >= kGraphSteps) {
+      if ((rc = build_graph(h))) return rc;
+      while (left >= h->graph_steps) {
+        CK(h, cudaGraphLaunch(h->graph, h->stream));
+        left -= h->graph_steps;
+      }
+    }
+  }
+  for (; left > 0; --left)
+    if ((rc = launch_one(h, h->stream))) return rc;
+  h->step += n;
+  return LBPF_OK;
+}
+
+size_t lbpf_state_bytes(const lbpf_t* h) {
+  if (!h) return 0;
+  const size_t n = size_t(nodes(h->p));
+  const size_t q = size_t(h->m.qf + 2 * h->m.qs);
+  return sizeof(StateHeader) + q * n * h->es + n * h->rs;
+}
+
+int lbpf_read_fields(lbpf_t* h, unsigned mask, void* host_dst, size_t bytes, int as_fp64) {
+  int rc = check_handle(h);
+  if (rc) return rc;
+  if (!host_dst) return fail(h, LBPF_EINVAL, "null destination");
+  if (!h->initialized) return fail(h, LBPF_ESTATE, "read before init");
+  const size_t n = size_t(nodes(h->p));
+  if (mask & LBPF_FIELD_STATE) {
+    if (mask != LBPF_FIELD_STATE) return fail(h, LBPF_EINVAL, "STATE must be requested alone");
+    if (bytes != lbpf_state_bytes(h)) return fail(h, LBPF_EINVAL, "state buffer size mismatch");
+    StateHeader hd{};
+    std::memcpy(hd.magic, kMagic, 8);
+    hd.step = h->step;
+    hd.dim = h->m.dim;
+    hd.nx = h->m.nx;
+    hd.ny = h->m.ny;
+    hd.nz = h->m.nz;
+    hd.storage = h->m.storage;
+    hd.flow = h->m.flow;
+    hd.q = h->m.qf + 2 * h->m.qs;
+    hd.elem = int32_t(h->es);
+    hd.ref_g = h->m.ref_g;
+    char* dst = static_cast<char*>(host_dst);
+    std::memcpy(dst, &hd, sizeof(hd));
+    const size_t rows = size_t(hd.q) * h->m.ny * h->m.nz;
+    CK(h, cudaMemcpy2DAsync(dst + sizeof(hd), h->m.nx * h->es, h->pops[h->cur],
+                            h->m.px * h->es, h->m.nx * h->es, rows, cudaMemcpyDeviceToHost,
+                            h->stream));
+    CK(h, cudaMemcpy2DAsync(dst + sizeof(hd) + size_t(hd.q) * n * h->es, h->m.nx * h->rs,
+                            h->phi[h->cur], h->m.px * h->rs, h->m.nx * h->rs,
+                            size_t(h->m.ny) * h->m.nz, cudaMemcpyDeviceToHost, h->stream));
+    return check_device_error(h);
+  }
+  const unsigned fm = mask & 0x7Fu;
+  if (fm == 0 || mask != fm) return fail(h, LBPF_EINVAL, "unknown field bits");
+  const int nf = __builtin_popcount(fm);
+  const size_t es = as_fp64 ? 8 : 4;
+  if (bytes != size_t(nf) * n * es) return fail(h, LBPF_EINVAL, "field buffer size mismatch");
+  if ((rc = ensure_fields_buffer(h, bytes))) return rc;
+  CK(h, lbk::launch_fields(h->m, h->pops[h->cur], h->phi[h->cur], fm, as_fp64, h->d_fields,
+                            h->stream));
+  CK(h, cudaMemcpyAsync(host_dst, h->d_fields, bytes, cudaMemcpyDeviceToHost, h->stream));
+  return check_device_error(h);
+}
+
+int lbpf_write_state(lbpf_t* h, const void* host_src, size_t bytes) {
+  int rc = check_handle(h);
+  if (rc) return rc;
+  if (!host_src || bytes != lbpf_state_bytes(h))
+    return fail(h, LBPF_EINVAL, "state buffer size mismatch");
+  StateHeader hd;
+  std::memcpy(&hd, host_src, sizeof(hd));
+  if (std::memcmp(hd.magic, kMagic, 8) != 0 || hd.dim != h->m.dim || hd.nx != h->m.nx ||
+      hd.ny != h->m.ny || hd.nz != h->m.nz || hd.storage != h->m.storage || hd.flow != h->m.flow ||
+      hd.q != h->m.qf + 2 * h->m.qs || hd.elem != int32_t(h->es) || hd.step < 0)
+    return fail(h, LBPF_EINVAL, "state does not match this handle");
+  const size_t n = size_t(nodes(h->p));
+  const char* src = static_cast<const char*>(host_src);
+  h->cur = 0;
+  const size_t rows = size_t(hd.q) * h->m.ny * h->m.nz;
+  CK(h, cudaMemcpy2DAsync(h->pops[0], h->m.px * h->es, src + sizeof(hd), h->m.nx * h->es,
+                          h->m.nx * h->es, rows, cudaMemcpyHostToDevice, h->stream));
+  CK(h, cudaMemcpy2DAsync(h->phi[0], h->m.px * h->rs, src + sizeof(hd) + size_t(hd.q) * n * h->es,
+                          h->m.nx * h->rs, h->m.nx * h->rs, size_t(h->m.ny) * h->m.nz,
+                          cudaMemcpyHostToDevice, h->stream));
+  h->step = hd.step;
+  if (h->m.ref_g != hd.ref_g) drop_graph(h);
+  h->m.ref_g = hd.ref_g;
+  if (!h->initialized) {
+    h->initialized = true;
+    store_I0(h);
+  }
+  CK(h, cudaStreamSynchronize(h->stream));
+  return LBPF_OK;
+}
+
+int lbpf_diagnostics(lbpf_t* h, lbpf_diag* out) {
+  int rc = check_handle(h);
+  if (rc) return rc;
+  if (!out) return fail(h, LBPF_EINVAL, "null output");
+  if (!h->initialized) return fail(h, LBPF_ESTATE, "diagnostics before init");
+  CK(h, lbk::launch_diag(h->m, h->pops[h->cur], h->phi[h->cur], h->d_partials, h->d_diag, h->icx,
+                          h->icy, h->icz, h->stream));
+  double v[17];
+  CK(h, cudaMemcpyAsync(v, h->d_diag, sizeof(v), cudaMemcpyDeviceToHost, h->stream));
+  if ((rc = check_device_error(h))) return rc;
+  std::memset(out, 0, sizeof(*out));
+  out->step = h->step;
+  out->solute_total = v[0];
+  out->mass_total = v[1];
+  out->solid_volume = v[2];
+  out->max_u = v[3];
+  out->nonfinite = (int64_t)v[4];
+  out->solute_drift_rel = v[16] != 0.0 ? (v[0] - v[16]) / std::fabs(v[16]) : 0.0;
+  out->r_eq = h->m.dim == 3 ? std::cbrt(3.0 * v[2] / (4.0 * M_PI)) : std::sqrt(v[2] / M_PI);
+  for (int k = 0; k < 6; ++k) out->iface_pos[k] = v[5 + k];
+  if (out->nonfinite > 0)
+    return fail(h, LBPF_ENONFINITE, "%lld nodes hold non-finite values", (long long)out->nonfinite);
+  return LBPF_OK;
+}
+
+int lbpf_set_stream(lbpf_t* h, void* stream) {
+  if (!h) return LBPF_EINVAL;
+  h->stream = static_cast<cudaStream_t>(stream);
+  return LBPF_OK;
+}
+
+size_t lbpf_device_bytes(const lbpf_t* h) { return h ? h->dev_bytes : 0; }
+
+const char* lbpf_last_error(const lbpf_t* h) { return h ? h->msg : "null handle"; }
+
+void lbpf_destroy(lbpf_t* h) {
+  if (!h) return;
+  cudaStreamSynchronize(h->stream);
+  if (h->graph) cudaGraphExecDestroy(h->graph);
+  if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+  for (int i = 0; i < 2; ++i) {
+    if (h->pops[i]) cudaFree(h->pops[i]);
+    if (h->phi[i]) cudaFree(h->phi[i]);
+  }
+  if (h->d_err) cudaFree(h->d_err);
+  if (h->d_partials) cudaFree(h->d_partials);
+  if (h->d_diag) cudaFree(h->d_diag);
+  if (h->d_fields) cudaFree(h->d_fields);
+  delete h;
+}
+
+}  // extern "C"

@@ -1,0 +1,137 @@
+// Device helpers of liblbpf.so: lattice constants, population storage
+// codecs and the anisotropy function.  Internal to the CUDA library.
+#pragma once
+
+#include "lbpf_internal.cuh"
+
+namespace lbk {
+
+// ---- lattices (direction order of the exported state) ----------------------
+// D2Q9: (0,0) (1,0) (0,1) (-1,0) (0,-1) (1,1) (-1,1) (-1,-1) (1,-1)
+__device__ constexpr int D2_CX[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+__device__ constexpr int D2_CY[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+__device__ constexpr int D2_OPP[9] = {0, 3, 4, 1, 2, 7, 8, 5, 6};
+template <typename R>
+__device__ __forceinline__ R d2_w(int a) {
+  return a == 0 ? R(4.0 / 9.0) : (a < 5 ? R(1.0 / 9.0) : R(1.0 / 36.0));
+}
+
+// D3Q19: rest, +x, -x, +y, -y, +z, -z, then the 12 edge links; D3Q7 is the
+// first seven of these.
+__device__ constexpr int D3_CX[19] = {0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 0, 0, 0, 0};
+__device__ constexpr int D3_CY[19] = {0, 0, 0, 1, -1, 0, 0, 1, -1, -1, 1, 0, 0, 0, 0, 1, -1, 1, -1};
+__device__ constexpr int D3_CZ[19] = {0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, -1, -1, 1, 1, -1, -1, 1};
+__device__ constexpr int D3_OPP[19] = {0, 2, 1, 4, 3, 6, 5, 8, 7, 10, 9, 12, 11, 14, 13, 16, 15, 18, 17};
+template <typename R>
+__device__ __forceinline__ R d3q19_w(int a) {
+  return a == 0 ? R(1.0 / 3.0) : (a < 7 ? R(1.0 / 18.0) : R(1.0 / 36.0));
+}
+template <typename R>
+__device__ __forceinline__ R d3q7_w(int a) {
+  return a == 0 ? R(0.25) : R(0.125);
+}
+
+// ---- arithmetic helpers -------------------------------------------------------
+__device__ __forceinline__ float rsqrt_r(float v) { return rsqrtf(v); }
+__device__ __forceinline__ double rsqrt_r(double v) { return rsqrt(v); }
+template <typename R>
+__device__ __forceinline__ R clamp1(R v) {
+  return v < R(-1) ? R(-1) : (v > R(1) ? R(1) : v);
+}
+__device__ __forceinline__ bool finite_r(float v) { return isfinite(v); }
+__device__ __forceinline__ bool finite_r(double v) { return isfinite(v); }
+
+// ---- population storage ---------------------------------------------------------
+// FP32/FP64 hold the population itself.  16-bit storage holds the deviation
+// from shift = w_a * reference moment (rho_ref = 1 for f, U_ref for g,
+// phi_ref for h), which keeps the stored magnitudes small.
+template <typename T>
+struct Pop;
+template <>
+struct Pop<float> {
+  template <typename R>
+  __device__ static __forceinline__ R ld(const float* p, R) { return R(*p); }
+  template <typename R>
+  __device__ static __forceinline__ void st(float* p, R v, R) { *p = float(v); }
+};
+template <>
+struct Pop<double> {
+  template <typename R>
+  __device__ static __forceinline__ R ld(const double* p, R) { return R(*p); }
+  template <typename R>
+  __device__ static __forceinline__ void st(double* p, R v, R) { *p = double(v); }
+};
+template <>
+struct Pop<__half> {
+  template <typename R>
+  __device__ static __forceinline__ R ld(const __half* p, R shift) {
+    return R(__half2float(*p)) + shift;
+  }
+  template <typename R>
+  __device__ static __forceinline__ void st(__half* p, R v, R shift) {
+    *p = __float2half_rn(float(v - shift));
+  }
+};
+template <>
+struct Pop<__nv_bfloat16> {
+  template <typename R>
+  __device__ static __forceinline__ R ld(const __nv_bfloat16* p, R shift) {
+    return R(__bfloat162float(*p)) + shift;
+  }
+  template <typename R>
+  __device__ static __forceinline__ void st(__nv_bfloat16* p, R v, R shift) {
+    *p = __float2bfloat16_rn(float(v - shift));
+  }
+};
+
+// ---- anisotropy (Eq. 3) and flux vector N (Eq. 21) ----------------------------
+// n = -grad/|grad| (solid -> liquid).  k-fold: cos/sin(k theta) are the real and
+// imaginary parts of (n_x + i n_y)^k, rotated by k theta0, so no atan2 is needed.
+// N = fac |grad|^2 a_s d(a_s)/d(grad):
+//   k-fold: N = fac k eps a_s sin(k(theta - theta0)) (g_y, -g_x)
+//   cubic : N_i = fac 16 eps a_s |grad| (n_i S - n_i^3), S = sum n_j^4
+template <typename R>
+__device__ __forceinline__ void aniso(const Model& m, R gx, R gy, R gz, R& as, R& Nx, R& Ny,
+                                      R& Nz) {
+  as = R(1);
+  Nx = Ny = Nz = R(0);
+  R g2 = gx * gx + gy * gy + gz * gz;
+  if (!(g2 > R(1e-12)) || m.eps == 0.0) return;
+  const R ig = rsqrt_r(g2);
+  const R nx = -gx * ig, ny = -gy * ig, nz = -gz * ig;
+  const R eps = R(m.eps), fac = R(m.aniso_fac);
+  if (m.fold > 0) {
+    R c = nx, s = ny;
+    for (int j = 1; j < m.fold; ++j) {
+      const R c2 = c * nx - s * ny;
+      s = c * ny + s * nx;
+      c = c2;
+    }
+    const R ck0 = R(m.ck0), sk0 = R(m.sk0);
+    const R cosd = c * ck0 + s * sk0;
+    const R sind = s * ck0 - c * sk0;
+    as = R(1) + eps * cosd;
+    const R amp = fac * R(m.fold) * eps * as * sind;
+    Nx = amp * gy;
+    Ny = -amp * gx;
+  } else {
+    const R nx2 = nx * nx, ny2 = ny * ny, nz2 = nz * nz;
+    const R S = nx2 * nx2 + ny2 * ny2 + nz2 * nz2;
+    as = R(1) - R(3) * eps + R(4) * eps * S;
+    const R amp = fac * R(16) * eps * as * (g2 * ig);
+    Nx = amp * nx * (S - nx2);
+    Ny = amp * ny * (S - ny2);
+    Nz = amp * nz * (S - nz2);
+  }
+}
+
+// periodic wrap of a coordinate that is at most one period out of range
+__device__ __forceinline__ int wrap1(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
+// neighbour coordinate for the gradient stencil: periodic wrap, else copy the
+// nearest node (zero normal derivative)
+__device__ __forceinline__ int grad_coord(int v, int n, int bc) {
+  if (bc == BC_PERIODIC) return wrap1(v, n);
+  return v < 0 ? 0 : (v >= n ? n - 1 : v);
+}
+
+}  // namespace lbk

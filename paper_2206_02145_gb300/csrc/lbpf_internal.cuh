@@ -1,0 +1,75 @@
+// Internal declarations shared by the translation units of liblbpf.so.
+// Nothing here is part of the C ABI (include/lbpf.h is).
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+namespace lbk {
+
+enum { BC_PERIODIC = 0, BC_INOUT = 1, BC_WALL = 2 };
+enum { ST_FP32 = 0, ST_FP64 = 1, ST_FP16 = 2, ST_BF16 = 3 };
+
+// Derived model constants (FP64 on the host; each kernel casts to its
+// arithmetic type).  Device layout: every population is its own array of
+// `plane` elements, node (x, y, z) at (z * ny + y) * px + x, px a multiple
+// of 32 elements so that every row starts 128-byte aligned.  Population
+// arrays of one buffer are consecutive: f (qf of them, 0 without flow),
+// then g (qs), then h (qs).
+struct Model {
+  int dim, nx, ny, nz;
+  int px;
+  long long plane;
+  int bc[3];
+  int flow, fold, storage, qf, qs;
+  double omega_f;      // 1 / tau_f                                   (Eq. 8)
+  double guo;          // 1 - 1/(2 tau_f)                              (Eq. 5)
+  double tauU_slope;   // tau_U(liquid) - 1/2                          (Eq. 18)
+  double inv_tau0;     // 1 / tau0                                     (Eq. 19)
+  double tpc;          // W0^2 / (cs^2 tau0), the a_s^2 slope of tau_phi (Eq. 23)
+                       // and the c.N coefficient of h^eq (Eq. 21)
+  double lambda;       //                                              (Eq. 20)
+  double eps;          //                                              (Eq. 3)
+  double ck0, sk0;     // cos(k theta0), sin(k theta0)
+  double aniso_fac;    // 1 (variational N) or 2 (literal factor)
+  double kdrag;        // h tau_f / (4 W0^2)                           (Eq. 6)
+  double w0;           // interface width W0
+  double body[3];
+  double u_in, U_in;   // inflow ghost state
+  double ref_f, ref_g, ref_h;  // equilibrium shifts of 16-bit storage
+};
+
+// Launchers (each returns the launch error).
+cudaError_t launch_step2d(const Model& m, const void* src, void* dst, const void* phi_prev,
+                          void* phi_cur, unsigned* err, cudaStream_t s);
+cudaError_t launch_step3d(const Model& m, const void* src, void* dst, const void* phi_prev,
+                          void* phi_cur, unsigned* err, cudaStream_t s);
+
+// Seeded initial state (FP64 arithmetic, stored in the population type).
+struct SeedArgs {
+  double cx, cy, cz, radius, u0, noise_amp;
+  unsigned long long seed;
+};
+cudaError_t launch_init_seed(const Model& m, const SeedArgs& a, void* pops, void* phi_prev,
+                             cudaStream_t s);
+// Equilibrium state from device FP64 fields (rho/ux/uy/uz may be null).
+cudaError_t launch_init_fields(const Model& m, const double* phi, const double* U,
+                               const double* rho, const double* ux, const double* uy,
+                               const double* uz, void* pops, void* phi_prev, cudaStream_t s);
+// Moments of the state into a packed device buffer: the fields selected by
+// `mask` (LBPF_FIELD_* bits 0..6) one after another, N values each, as
+// double (fp64) or float.
+cudaError_t launch_fields(const Model& m, const void* pops, const void* phi_prev,
+                          unsigned mask, int fp64, void* out, cudaStream_t s);
+
+// FP64 diagnostics.  partials: scratch of diag_partials_bytes(m) bytes.
+// out[0..4] = sum(U + phi_prev), sum(rho), sum((1+phihat)/2), max|u|,
+// nonfinite count; out[5..10] = interface crossings from (icx, icy, icz).
+size_t diag_partials_bytes(const Model& m);
+cudaError_t launch_diag(const Model& m, const void* pops, const void* phi_prev, double* partials,
+                        double* out, int icx, int icy, int icz, cudaStream_t s);
+
+}  // namespace lbk

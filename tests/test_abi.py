@@ -1,0 +1,85 @@
+"""CPU checks of the C ABI boundary: the library builds, loads, exports every
+symbol include/lbpf.h declares, and rejects invalid parameters before it
+touches the GPU."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2206_02145_gb300 import build as B
+    path = B.build()
+    import paper_2206_02145_gb300 as L
+    assert os.path.samefile(L.LIB_PATH, path)
+    return L
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "lbpf.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(lbpf_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("lbpf_create", "lbpf_init_seed", "lbpf_step", "lbpf_read_fields",
+                     "lbpf_diagnostics"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    so = ctypes.CDLL(lib.LIB_PATH)
+    for name in declared_functions():
+        assert hasattr(so, name), name
+    assert set(lib.EXPORTED) <= set(declared_functions())
+
+
+def test_struct_layouts_match_header(lib, tmp_path):
+    # the C compiler's sizeof/offsetof of the header structs against ctypes
+    prog = tmp_path / "layout.c"
+    fields = {"lbpf_params": [f for f, _ in lib.lbpf_params._fields_],
+              "lbpf_seed": [f for f, _ in lib.lbpf_seed._fields_],
+              "lbpf_diag": [f for f, _ in lib.lbpf_diag._fields_]}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "lbpf.h"', "int main(void){"]
+    for st, fs in fields.items():
+        lines.append(f'printf("{st} %zu\\n", sizeof({st}));')
+        for f in fs:
+            cf = "lambda" if f == "lambda_" else f
+            lines.append(f'printf("{st}.{f} %zu\\n", offsetof({st}, {cf}));')
+    lines.append("return 0;}")
+    prog.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), "-o", str(exe), str(prog)])
+    out = dict(l.split() for l in subprocess.check_output([str(exe)], text=True).splitlines())
+    for st, fs in fields.items():
+        cls = getattr(lib, st)
+        assert int(out[st]) == ctypes.sizeof(cls), st
+        for f in fs:
+            assert int(out[f"{st}.{f}"]) == getattr(cls, f).offset, (st, f)
+
+
+@pytest.mark.parametrize("bad", [
+    dict(tau_phi0=0.5), dict(tau_u_liquid=0.4), dict(flow=1, tau_f=0.5), dict(w0=0.0),
+    dict(eps_aniso=1.0), dict(eps_aniso=-0.1), dict(fold=13), dict(dim=3, nz=8, fold=4),
+    dict(nx=3), dict(dim=4), dict(bc=(0, 1, 0)), dict(u_inlet=0.2), dict(storage=7),
+    dict(lambda_=float("nan")),
+])
+def test_invalid_parameters_are_rejected_without_a_gpu(lib, bad):
+    p = lib.lbpf_params_default(**bad)
+    with pytest.raises(lib.LbpfError) as e:
+        lib.lbpf_create(p)
+    assert e.value.code == lib.EINVAL
+
+
+def test_null_handle_calls_return_einval(lib):
+    so = lib._lib
+    assert so.lbpf_step(None, 1) == lib.EINVAL
+    assert so.lbpf_diagnostics(None, None) == lib.EINVAL
+    assert so.lbpf_state_bytes(None) == 0
+    so.lbpf_destroy(None)
