@@ -13,8 +13,8 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 @pytest.fixture(scope="module")
 def lib():
-    from paper_2206_02145_gb300 import build as B
-    path = B.build()
+    import __graft_entry__
+    path = __graft_entry__._builder().build()
     import paper_2206_02145_gb300 as L
     assert os.path.samefile(L.LIB_PATH, path)
     return L
