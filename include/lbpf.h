@@ -167,12 +167,14 @@ int lbpf_read_fields(lbpf_t* h, unsigned field_mask, void* host_dst, size_t byte
 
 /* Size of the restartable state: a 64-byte header (magic "LBPFST01", int64
  * step, int32 dim, nx, ny, nz, storage, flow, populations per node, element
- * bytes), then the populations direction-major in the storage type (f, then
- * g, then h; directions in the order: D2Q9 (0,0) (1,0) (0,1) (-1,0) (0,-1)
- * (1,1) (-1,1) (-1,-1) (1,-1); D3Q19 rest, +x, -x, +y, -y, +z, -z,
- * (1,1,0) (-1,-1,0) (1,-1,0) (-1,1,0) (1,0,1) (-1,0,-1) (1,0,-1) (-1,0,1)
- * (0,1,1) (0,-1,-1) (0,1,-1) (0,-1,1); D3Q7 the first seven of those), then
- * phi(t-1) in FP64 for LBPF_FP64 storage and FP32 otherwise. */
+ * bytes, then at byte 48 the double U_ref), then the populations
+ * direction-major in the storage type (f, then g, then h; directions in the
+ * order: D2Q9 (0,0) (1,0) (0,1) (-1,0) (0,-1) (1,1) (-1,1) (-1,-1) (1,-1);
+ * D3Q19 rest, +x, -x, +y, -y, +z, -z, (1,1,0) (-1,-1,0) (1,-1,0) (-1,1,0)
+ * (1,0,1) (-1,0,-1) (1,0,-1) (-1,0,1) (0,1,1) (0,-1,-1) (0,1,-1) (0,-1,1);
+ * D3Q7 the first seven of those), each stored as its deviation
+ * d_a = p_a - w_a M_ref with M_ref = 1 for f, U_ref for g and -1 for h; then
+ * phi(t-1) + 1 in FP64 for LBPF_FP64 storage and FP32 otherwise. */
 size_t lbpf_state_bytes(const lbpf_t* h);
 
 /* Restore a state written by lbpf_read_fields(LBPF_FIELD_STATE) of a handle

@@ -248,18 +248,5 @@ class Sim:
         buf = np.ascontiguousarray(buf, dtype=np.uint8)
         lbpf_write_state(self.h, buf.ctypes.data, buf.nbytes)
 
-    def pops(self, buf: np.ndarray | None = None) -> dict:
-        """Populations from the exported state: {'f','g','h'} arrays [q, ...]."""
-        if buf is None:
-            buf = self.state()
-        hdr = np.frombuffer(buf[:64].tobytes(), dtype=np.int32, count=12, offset=16)
-        q, elem, flow, dim = int(hdr[6]), int(hdr[7]), int(hdr[5]), int(hdr[0])
-        dt = {8: np.float64, 4: np.float32, 2: np.float16}[elem]
-        n = self.nodes
-        raw = np.frombuffer(buf[64:64 + q * n * elem].tobytes(), dtype=dt).reshape((q,) + self.shape)
-        qf = (9 if dim == 2 else 19) if flow else 0
-        qs = 9 if dim == 2 else 7
-        return {"f": raw[:qf], "g": raw[qf:qf + qs], "h": raw[qf + qs:]}
-
     def diagnostics(self) -> dict:
         return lbpf_diagnostics(self.h)

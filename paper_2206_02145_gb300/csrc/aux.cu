@@ -24,7 +24,8 @@ __device__ __forceinline__ unsigned long long splitmix64(unsigned long long z) {
 }
 
 // Equilibrium populations of (rho, u*, U, phi) in FP64 (Eq. 9 at second
-// order, Eq. 16, Eq. 21 with N = 0), stored in the population type.
+// order, Eq. 16, Eq. 21 with N = 0), stored as deviations from w_a M_ref
+// (M_ref = 1, U_ref, -1) in the population type.
 template <typename T>
 __device__ void store_equilibrium(const Model& m, T* pops, long long j, double phi, double U,
                                   double rho, double ux, double uy, double uz) {
@@ -41,24 +42,24 @@ __device__ void store_equilibrium(const Model& m, T* pops, long long j, double p
       const double w = d2_w<double>(a);
       const double cu = D2_CX[a] * us[0] + D2_CY[a] * us[1];
       if (m.flow)
-        Pop<T>::st(pf + a * P + j, rho * w * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * uu),
-                   w * m.ref_f);
-      Pop<T>::st(pg + a * P + j, w * U * (1.0 + 3.0 * cu), w * m.ref_g);
-      Pop<T>::st(ph_ + a * P + j, w * phi, w * m.ref_h);
+        Pop<T>::st(pf + a * P + j,
+                   w * ((rho - m.ref_f) + rho * (3.0 * cu + 4.5 * cu * cu - 1.5 * uu)));
+      Pop<T>::st(pg + a * P + j, w * ((U - m.ref_g) + U * 3.0 * cu));
+      Pop<T>::st(ph_ + a * P + j, w * (phi - m.ref_h));
     }
   } else {
     if (m.flow)
       for (int a = 0; a < 19; ++a) {
         const double w = d3q19_w<double>(a);
         const double cu = D3_CX[a] * us[0] + D3_CY[a] * us[1] + D3_CZ[a] * us[2];
-        Pop<T>::st(pf + a * P + j, rho * w * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * uu),
-                   w * m.ref_f);
+        Pop<T>::st(pf + a * P + j,
+                   w * ((rho - m.ref_f) + rho * (3.0 * cu + 4.5 * cu * cu - 1.5 * uu)));
       }
     for (int a = 0; a < 7; ++a) {
       const double w = d3q7_w<double>(a);
       const double cu = D3_CX[a] * us[0] + D3_CY[a] * us[1] + D3_CZ[a] * us[2];
-      Pop<T>::st(pg + a * P + j, w * U * (1.0 + 4.0 * cu), w * m.ref_g);  // cs^2 = 1/4
-      Pop<T>::st(ph_ + a * P + j, w * phi, w * m.ref_h);
+      Pop<T>::st(pg + a * P + j, w * ((U - m.ref_g) + U * 4.0 * cu));  // cs^2 = 1/4
+      Pop<T>::st(ph_ + a * P + j, w * (phi - m.ref_h));
     }
   }
 }
@@ -79,7 +80,7 @@ __global__ void init_seed_kernel(const Model m, const SeedArgs s, T* pops, R* ph
     phi += s.noise_amp * xi;
     const long long j = pitched(m, x, y, z);
     store_equilibrium<T>(m, pops, j, phi, s.u0, 1.0, m.flow ? m.u_in : 0.0, 0.0, 0.0);
-    phi_prev[j] = R(phi);
+    phi_prev[j] = R(phi - m.ref_h);  // the ring holds phi + 1
   }
 }
 
@@ -95,7 +96,7 @@ __global__ void init_fields_kernel(const Model m, const double* phi, const doubl
     const long long j = pitched(m, x, y, z);
     store_equilibrium<T>(m, pops, j, phi[i], U[i], rho ? rho[i] : 1.0, ux ? ux[i] : 0.0,
                          uy ? uy[i] : 0.0, uz ? uz[i] : 0.0);
-    phi_prev[j] = R(phi[i]);
+    phi_prev[j] = R(phi[i] - m.ref_h);
   }
 }
 
@@ -107,41 +108,39 @@ __device__ void node_moments(const Model& m, const T* pops, long long j, double&
   const T* pf = pops;
   const T* pg = pops + (long long)m.qf * P;
   const T* ph_ = pops + (long long)(m.qf + m.qs) * P;
-  phi = U = 0.0;
-  rho = 1.0;
+  double dphi = 0.0, dU = 0.0, drho = 0.0;
   double mo[3] = {0.0, 0.0, 0.0};
   if (m.dim == 2) {
     for (int a = 0; a < 9; ++a) {
-      const double w = d2_w<double>(a);
-      U += Pop<T>::ld(pg + a * P + j, w * m.ref_g);
-      phi += Pop<T>::ld(ph_ + a * P + j, w * m.ref_h);
+      dU += Pop<T>::template ld<double>(pg + a * P + j);
+      dphi += Pop<T>::template ld<double>(ph_ + a * P + j);
     }
     if (m.flow) {
-      rho = 0.0;
       for (int a = 0; a < 9; ++a) {
-        const double v = Pop<T>::ld(pf + a * P + j, d2_w<double>(a) * m.ref_f);
-        rho += v;
+        const double v = Pop<T>::template ld<double>(pf + a * P + j);
+        drho += v;
         mo[0] += D2_CX[a] * v;
         mo[1] += D2_CY[a] * v;
       }
     }
   } else {
     for (int a = 0; a < 7; ++a) {
-      const double w = d3q7_w<double>(a);
-      U += Pop<T>::ld(pg + a * P + j, w * m.ref_g);
-      phi += Pop<T>::ld(ph_ + a * P + j, w * m.ref_h);
+      dU += Pop<T>::template ld<double>(pg + a * P + j);
+      dphi += Pop<T>::template ld<double>(ph_ + a * P + j);
     }
     if (m.flow) {
-      rho = 0.0;
       for (int a = 0; a < 19; ++a) {
-        const double v = Pop<T>::ld(pf + a * P + j, d3q19_w<double>(a) * m.ref_f);
-        rho += v;
+        const double v = Pop<T>::template ld<double>(pf + a * P + j);
+        drho += v;
         mo[0] += D3_CX[a] * v;
         mo[1] += D3_CY[a] * v;
         mo[2] += D3_CZ[a] * v;
       }
     }
   }
+  phi = m.ref_h + dphi;
+  U = m.ref_g + dU;
+  rho = m.ref_f + drho;
   const double ph = phi < -1.0 ? -1.0 : (phi > 1.0 ? 1.0 : phi);
   const double K = m.flow ? m.kdrag * (1.0 + ph) * (1.0 + ph) * (1.0 - ph) : 0.0;
   for (int d = 0; d < 3; ++d)
@@ -159,7 +158,7 @@ __global__ void fields_kernel(const Model m, const T* pops, const R* phi_prev, u
     const long long j = pitched(m, x, y, z);
     double phi, U, rho, u[3];
     node_moments<T>(m, pops, j, phi, U, rho, u);
-    const double vals[7] = {phi, U, rho, u[0], u[1], u[2], double(phi_prev[j])};
+    const double vals[7] = {phi, U, rho, u[0], u[1], u[2], m.ref_h + double(phi_prev[j])};
     int slot = 0;
     for (int b = 0; b < 7; ++b)
       if (mask & (1u << b)) out[(long long)(slot++) * n + i] = O(vals[b]);
@@ -182,7 +181,7 @@ __global__ void __launch_bounds__(kDiagThreads)
     const long long j = pitched(m, x, y, z);
     double phi, U, rho, u[3];
     node_moments<T>(m, pops, j, phi, U, rho, u);
-    const double pp = double(phi_prev[j]);
+    const double pp = m.ref_h + double(phi_prev[j]);
     const double ph = phi < -1.0 ? -1.0 : (phi > 1.0 ? 1.0 : phi);
     acc[0] += U + pp;
     acc[1] += rho;

@@ -131,7 +131,7 @@ Model derive(const lbpf_params& p) {
   m.U_in = p.u0_inlet;
   m.ref_f = 1.0;
   m.ref_g = 0.0;
-  m.ref_h = 0.0;
+  m.ref_h = -1.0;
   return m;
 }
 
@@ -222,7 +222,7 @@ struct StateHeader {
   char magic[8];
   int64_t step;
   int32_t dim, nx, ny, nz, storage, flow, q, elem;
-  double ref_g;  // equilibrium shift of g in 16-bit storage
+  double ref_g;  // reference U of the stored g deviations
   char pad[8];
 };
 static_assert(sizeof(StateHeader) == 64, "state header must be 64 bytes");
@@ -300,8 +300,7 @@ int lbpf_init_seed(lbpf_t* h, const lbpf_seed* s) {
   if (!s || !(s->radius >= 0.0) || !std::isfinite(s->u0) || !std::isfinite(s->noise_amp) ||
       !std::isfinite(s->cx) || !std::isfinite(s->cy) || !std::isfinite(s->cz))
     return fail(h, LBPF_EINVAL, "invalid seed");
-  h->m.ref_g = is16(h->m) ? s->u0 : 0.0;
-  h->m.ref_h = 0.0;
+  h->m.ref_g = s->u0;
   drop_graph(h);
   lbk::SeedArgs a{s->cx, s->cy, s->cz, s->radius, s->u0, s->noise_amp, s->seed};
   h->cur = 0;
@@ -340,8 +339,8 @@ int lbpf_init_fields(lbpf_t* h, const double* phi, const double* U, const double
       return fail(h, LBPF_ECUDA, "init_fields copy: %s", cudaGetErrorString(e));
     }
   }
-  // 16-bit storage shifts g by the mean initial U
-  if (is16(h->m)) {
+  // g is stored as the deviation from w_a times the mean initial U
+  {
     double mean = 0.0;
     for (size_t i = 0; i < n; ++i) mean += U[i];
     h->m.ref_g = mean / double(n);

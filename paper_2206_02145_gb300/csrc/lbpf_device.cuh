@@ -11,9 +11,20 @@ namespace lbk {
 __device__ constexpr int D2_CX[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
 __device__ constexpr int D2_CY[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
 __device__ constexpr int D2_OPP[9] = {0, 3, 4, 1, 2, 7, 8, 5, 6};
+// Weights.  In FP32 the three values are chosen so that their exact sum
+// (w0 + 4 w1 + 4 w2, resp. w0 + 6 w1 + 12 w2) is 1: with the rounded 4/9, 1/9,
+// 1/36 the sum is 1 + 7.4e-9, which biases every zeroth moment by that much
+// per collision (sum of U + phi(t-1) drifts; phi drifts by ~1e-8 per step).
+// FP64 uses the plain fractions.
 template <typename R>
-__device__ __forceinline__ R d2_w(int a) {
-  return a == 0 ? R(4.0 / 9.0) : (a < 5 ? R(1.0 / 9.0) : R(1.0 / 36.0));
+__device__ __forceinline__ R d2_w(int a);
+template <>
+__device__ __forceinline__ double d2_w<double>(int a) {
+  return a == 0 ? 4.0 / 9.0 : (a < 5 ? 1.0 / 9.0 : 1.0 / 36.0);
+}
+template <>
+__device__ __forceinline__ float d2_w<float>(int a) {
+  return a == 0 ? 0x1.c71c72p-2f : (a < 5 ? 0x1.c71c72p-4f : 0x1.c71c70p-6f);
 }
 
 // D3Q19: rest, +x, -x, +y, -y, +z, -z, then the 12 edge links; D3Q7 is the
@@ -23,8 +34,14 @@ __device__ constexpr int D3_CY[19] = {0, 0, 0, 1, -1, 0, 0, 1, -1, -1, 1, 0, 0, 
 __device__ constexpr int D3_CZ[19] = {0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, -1, -1, 1, 1, -1, -1, 1};
 __device__ constexpr int D3_OPP[19] = {0, 2, 1, 4, 3, 6, 5, 8, 7, 10, 9, 12, 11, 14, 13, 16, 15, 18, 17};
 template <typename R>
-__device__ __forceinline__ R d3q19_w(int a) {
-  return a == 0 ? R(1.0 / 3.0) : (a < 7 ? R(1.0 / 18.0) : R(1.0 / 36.0));
+__device__ __forceinline__ R d3q19_w(int a);
+template <>
+__device__ __forceinline__ double d3q19_w<double>(int a) {
+  return a == 0 ? 1.0 / 3.0 : (a < 7 ? 1.0 / 18.0 : 1.0 / 36.0);
+}
+template <>
+__device__ __forceinline__ float d3q19_w<float>(int a) {
+  return a == 0 ? 0x1.555558p-2f : (a < 7 ? 0x1.c71c72p-5f : 0x1.c71c6ep-6f);
 }
 template <typename R>
 __device__ __forceinline__ R d3q7_w(int a) {
@@ -42,45 +59,44 @@ __device__ __forceinline__ bool finite_r(float v) { return isfinite(v); }
 __device__ __forceinline__ bool finite_r(double v) { return isfinite(v); }
 
 // ---- population storage ---------------------------------------------------------
-// FP32/FP64 hold the population itself.  16-bit storage holds the deviation
-// from shift = w_a * reference moment (rho_ref = 1 for f, U_ref for g,
-// phi_ref for h), which keeps the stored magnitudes small.
+// Every lattice stores and updates the deviation of its populations from the
+// weights times a reference moment, d_a = p_a - w_a M_ref (M_ref = 1 for f,
+// U_ref for g, -1 for h), so that rounding acts on small numbers: the moments
+// are M = M_ref + sum d and the equilibria are written as deviations too.
+// FP32/FP64 store d as is; the 16-bit modes store d rounded to binary16 or
+// bfloat16 and compute in FP32.
 template <typename T>
 struct Pop;
 template <>
 struct Pop<float> {
   template <typename R>
-  __device__ static __forceinline__ R ld(const float* p, R) { return R(*p); }
+  __device__ static __forceinline__ R ld(const float* p) { return R(*p); }
   template <typename R>
-  __device__ static __forceinline__ void st(float* p, R v, R) { *p = float(v); }
+  __device__ static __forceinline__ void st(float* p, R v) { *p = float(v); }
 };
 template <>
 struct Pop<double> {
   template <typename R>
-  __device__ static __forceinline__ R ld(const double* p, R) { return R(*p); }
+  __device__ static __forceinline__ R ld(const double* p) { return R(*p); }
   template <typename R>
-  __device__ static __forceinline__ void st(double* p, R v, R) { *p = double(v); }
+  __device__ static __forceinline__ void st(double* p, R v) { *p = double(v); }
 };
 template <>
 struct Pop<__half> {
   template <typename R>
-  __device__ static __forceinline__ R ld(const __half* p, R shift) {
-    return R(__half2float(*p)) + shift;
-  }
+  __device__ static __forceinline__ R ld(const __half* p) { return R(__half2float(*p)); }
   template <typename R>
-  __device__ static __forceinline__ void st(__half* p, R v, R shift) {
-    *p = __float2half_rn(float(v - shift));
-  }
+  __device__ static __forceinline__ void st(__half* p, R v) { *p = __float2half_rn(float(v)); }
 };
 template <>
 struct Pop<__nv_bfloat16> {
   template <typename R>
-  __device__ static __forceinline__ R ld(const __nv_bfloat16* p, R shift) {
-    return R(__bfloat162float(*p)) + shift;
+  __device__ static __forceinline__ R ld(const __nv_bfloat16* p) {
+    return R(__bfloat162float(*p));
   }
   template <typename R>
-  __device__ static __forceinline__ void st(__nv_bfloat16* p, R v, R shift) {
-    *p = __float2bfloat16_rn(float(v - shift));
+  __device__ static __forceinline__ void st(__nv_bfloat16* p, R v) {
+    *p = __float2bfloat16_rn(float(v));
   }
 };
 

@@ -39,7 +39,7 @@ struct Model {
   double w0;           // interface width W0
   double body[3];
   double u_in, U_in;   // inflow ghost state
-  double ref_f, ref_g, ref_h;  // equilibrium shifts of 16-bit storage
+  double ref_f, ref_g, ref_h;  // reference moments of the stored deviations (1, U_ref, -1)
 };
 
 // Launchers (each returns the launch error).

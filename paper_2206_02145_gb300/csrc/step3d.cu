@@ -1,3 +1,4 @@
+// Populations are deviations d_a = p_a - w_a M_ref as in 2D; the ring holds phi + 1.
 // Fused coupled LB step in 3D: D3Q19 flow f (Eqs. 4-12), D3Q7 solute g
 // (Eqs. 13-18) and D3Q7 phase field h (Eqs. 19-23), one thread per node,
 // push streaming (same update as the pull form of the equations).  Per node
@@ -13,7 +14,7 @@ namespace {
 template <typename T, typename R, bool FLOW, int TX, int TY, int TZ>
 __global__ void __launch_bounds__(TX* TY* TZ)
     step3d_kernel(const Model m, const T* __restrict__ src, T* __restrict__ dst,
-                  const R* __restrict__ phi_prev, R* __restrict__ phi_cur,
+                  const R* __restrict__ ring_prev, R* __restrict__ ring_cur,
                   unsigned* __restrict__ err) {
   constexpr int SX = TX + 2, SY = TY + 2, SZ = TZ + 2;
   constexpr int QF = FLOW ? 19 : 0;
@@ -30,29 +31,28 @@ __global__ void __launch_bounds__(TX* TY* TZ)
   const bool active = x < nx && y < ny && z < nz;
   const long long idx = z * rowz + (long long)y * px + x;
 
-  const R ref_f = R(m.ref_f), ref_g = R(m.ref_g), ref_h = R(m.ref_h);
   const T* sf = src;
   const T* sg = src + (long long)QF * P;
   const T* shp = src + (long long)(QF + 7) * P;
 
   R f[FLOW ? 19 : 1], g[7], h[7];
-  R phi = R(0);
+  R dphi = R(0);
   if (active) {
     if (FLOW) {
 #pragma unroll
-      for (int a = 0; a < 19; ++a) f[a] = Pop<T>::ld(sf + a * P + idx, d3q19_w<R>(a) * ref_f);
+      for (int a = 0; a < 19; ++a) f[a] = Pop<T>::template ld<R>(sf + a * P + idx);
     }
 #pragma unroll
     for (int a = 0; a < 7; ++a) {
-      g[a] = Pop<T>::ld(sg + a * P + idx, d3q7_w<R>(a) * ref_g);
-      h[a] = Pop<T>::ld(shp + a * P + idx, d3q7_w<R>(a) * ref_h);
+      g[a] = Pop<T>::template ld<R>(sg + a * P + idx);
+      h[a] = Pop<T>::template ld<R>(shp + a * P + idx);
     }
 #pragma unroll
     for (int a = 0; a < 7; ++a) {
-      phi += h[a];  // Eq. 22
+      dphi += h[a];  // Eq. 22: phi = -1 + sum d_h
       sh_h[a][tz + 1][ty + 1][tx + 1] = h[a];
     }
-    sh_phi[tz + 1][ty + 1][tx + 1] = phi;
+    sh_phi[tz + 1][ty + 1][tx + 1] = dphi;
   }
   const int tid = (tz * TY + ty) * TX + tx;
   for (int i = tid; i < SX * SY * SZ; i += NT) {
@@ -68,7 +68,7 @@ __global__ void __launch_bounds__(TX* TY* TZ)
     R s = R(0);
 #pragma unroll
     for (int a = 0; a < 7; ++a) {
-      const R v = Pop<T>::ld(shp + a * P + j, d3q7_w<R>(a) * ref_h);
+      const R v = Pop<T>::template ld<R>(shp + a * P + j);
       sh_h[a][lz][ly][lx] = v;
       s += v;
     }
@@ -77,20 +77,22 @@ __global__ void __launch_bounds__(TX* TY* TZ)
   __syncthreads();
   if (!active) return;
 
-  R U = R(0);
+  const R phi = dphi - R(1);
+  R dU = R(0);
 #pragma unroll
-  for (int a = 0; a < 7; ++a) U += g[a];
-  R rho = R(1), mo[3] = {R(0), R(0), R(0)};
+  for (int a = 0; a < 7; ++a) dU += g[a];
+  const R U = R(m.ref_g) + dU;
+  R drho = R(0), mo[3] = {R(0), R(0), R(0)};
   if (FLOW) {
-    rho = R(0);
 #pragma unroll
     for (int a = 0; a < 19; ++a) {
-      rho += f[a];
+      drho += f[a];
       if (D3_CX[a]) mo[0] += R(D3_CX[a]) * f[a];
       if (D3_CY[a]) mo[1] += R(D3_CY[a]) * f[a];
       if (D3_CZ[a]) mo[2] += R(D3_CZ[a]) * f[a];
     }
   }
+  const R rho = R(1) + drho;
   const R ph = clamp1(phi);
   const R mask = R(0.5) * (R(1) - ph);
   R u[3] = {R(0), R(0), R(0)}, F[3] = {R(0), R(0), R(0)};
@@ -105,8 +107,8 @@ __global__ void __launch_bounds__(TX* TY* TZ)
   }
   const R us[3] = {mask * u[0], mask * u[1], mask * u[2]};  // Eq. 7
   const R omega_U = R(1) / (R(0.5) + R(m.tauU_slope) * mask);  // Eq. 18
-  const R dphidt = phi - phi_prev[idx];
-  phi_cur[idx] = phi;
+  const R dphidt = dphi - ring_prev[idx];
+  ring_cur[idx] = dphi;
   if (!(finite_r(phi) && finite_r(U) && finite_r(rho))) atomicOr(err, 1u);
 
   // grad = 3 sum_a w_a c_a phi(x + c_a) over D3Q19
@@ -144,15 +146,15 @@ __global__ void __launch_bounds__(TX* TY* TZ)
     const R wf = d3q19_w<R>(a);
     if (FLOW) {
       const R cF = R(cx) * F[0] + R(cy) * F[1] + R(cz) * F[2];
-      const R feq = rho * wf * (R(1) + R(3) * cu + R(4.5) * cu * cu - R(1.5) * uu);  // Eq. 9
+      const R feq = wf * (drho + rho * (R(3) * cu + R(4.5) * cu * cu - R(1.5) * uu));  // Eq. 9
       const R G = wf * R(m.guo) * (R(3) * cF + R(9) * cu * cF - R(3) * uF);           // Eq. 5
       fp = f[a] - R(m.omega_f) * (f[a] - feq) + G;
     }
     const bool sc = a < 7;  // direction of the D3Q7 lattices too
     const R ws = d3q7_w<R>(a);
     if (sc) {
-      gp = g[a] - omega_U * (g[a] - ws * U * (R(1) + R(4) * cu)) - ws * dphidt;  // Eqs. 13-16
-      const R heq = ws * (phi - tpc * (R(cx) * N[0] + R(cy) * N[1] + R(cz) * N[2]));  // Eq. 21
+      gp = g[a] - omega_U * (g[a] - ws * (dU + U * R(4) * cu)) - ws * dphidt;  // Eqs. 13-16
+      const R heq = ws * (dphi - tpc * (R(cx) * N[0] + R(cy) * N[1] + R(cz) * N[2]));  // Eq. 21
       hp = h[a] - omega_phi * (h[a] - heq) + ws * Qs;                                 // Eq. 19
     }
     int xd = x + cx, yd = y + cy, zd = z + cz;
@@ -172,19 +174,18 @@ __global__ void __launch_bounds__(TX* TY* TZ)
     }
     if (bounce) {
       const int b = D3_OPP[a];
-      if (FLOW) Pop<T>::st(df + b * P + idx, fp, d3q19_w<R>(b) * ref_f);
+      if (FLOW) Pop<T>::st(df + b * P + idx, fp);
       if (sc) {
-        const R wb = d3q7_w<R>(b);
-        Pop<T>::st(dg + b * P + idx, gp, wb * ref_g);
-        Pop<T>::st(dh + b * P + idx, hp * inv_a2 - (inv_a2 - R(1)) * h[b], wb * ref_h);
+        Pop<T>::st(dg + b * P + idx, gp);
+        Pop<T>::st(dh + b * P + idx, hp * inv_a2 - (inv_a2 - R(1)) * h[b]);
       }
     } else if (!drop) {
       const long long jd = zd * rowz + (long long)yd * px + xd;
-      if (FLOW) Pop<T>::st(df + a * P + jd, fp, wf * ref_f);
+      if (FLOW) Pop<T>::st(df + a * P + jd, fp);
       if (sc) {
         const R hold = sh_h[a][lz + cz][ly + cy][lx + cx];
-        Pop<T>::st(dg + a * P + jd, gp, ws * ref_g);
-        Pop<T>::st(dh + a * P + jd, hp * inv_a2 - (inv_a2 - R(1)) * hold, ws * ref_h);
+        Pop<T>::st(dg + a * P + jd, gp);
+        Pop<T>::st(dh + a * P + jd, hp * inv_a2 - (inv_a2 - R(1)) * hold);
       }
     }
     if (bcx == BC_INOUT) {
@@ -201,11 +202,11 @@ __global__ void __launch_bounds__(TX* TY* TZ)
         }
         if (ok) {
           const long long jo = zo * rowz + (long long)yo * px + x;
-          if (FLOW) Pop<T>::st(df + a * P + jo, fp, wf * ref_f);
+          if (FLOW) Pop<T>::st(df + a * P + jo, fp);
           if (sc) {
             const R hold = sh_h[a][lz + cz][ly + cy][lx];
-            Pop<T>::st(dg + a * P + jo, gp, ws * ref_g);
-            Pop<T>::st(dh + a * P + jo, hp * inv_a2 - (inv_a2 - R(1)) * hold, ws * ref_h);
+            Pop<T>::st(dg + a * P + jo, gp);
+            Pop<T>::st(dh + a * P + jo, hp * inv_a2 - (inv_a2 - R(1)) * hold);
           }
         }
       }
@@ -217,12 +218,12 @@ __global__ void __launch_bounds__(TX* TY* TZ)
           const R uin = R(m.u_in), cui = uin;
           if (FLOW)
             Pop<T>::st(df + a * P + idx,
-                       wf * (R(1) + R(3) * cui + R(4.5) * cui * cui - R(1.5) * uin * uin),
-                       wf * ref_f);
+                       wf * (R(3) * cui + R(4.5) * cui * cui - R(1.5) * uin * uin));
           if (sc) {
             const R gu = FLOW ? cui : R(0);
-            Pop<T>::st(dg + a * P + idx, ws * R(m.U_in) * (R(1) + R(4) * gu), ws * ref_g);
-            Pop<T>::st(dh + a * P + idx, -ws, ws * ref_h);
+            const R Uin = R(m.U_in);
+            Pop<T>::st(dg + a * P + idx, ws * ((Uin - R(m.ref_g)) + Uin * R(4) * gu));
+            Pop<T>::st(dh + a * P + idx, R(0));  // phi = -1: zero deviation
           }
         }
       }

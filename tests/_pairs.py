@@ -72,3 +72,37 @@ def max_errors(a, b, fields=("phi", "U", "rho", "ux", "uy")):
     got = a.fields(fields)
     want = b.fields()
     return {k: float(np.abs(got[k] - want[k]).max()) for k in fields}
+
+
+# lattice weights of the exported state's direction order (for decoding the
+# stored deviations d_a = p_a - w_a M_ref back to populations)
+_W = {9: [4 / 9] + [1 / 9] * 4 + [1 / 36] * 4,
+      19: [1 / 3] + [1 / 18] * 6 + [1 / 36] * 12,
+      7: [1 / 4] + [1 / 8] * 6}
+
+
+def decode_pops(sim, buf=None):
+    """Populations {'f','g','h'} [q, ...] of a library handle's exported state."""
+    if buf is None:
+        buf = sim.state()
+    hdr = np.frombuffer(buf[:48].tobytes(), dtype=np.int32, count=8, offset=16)
+    dim, flow, q, elem = int(hdr[0]), int(hdr[5]), int(hdr[6]), int(hdr[7])
+    u_ref = float(np.frombuffer(buf[48:56].tobytes(), dtype=np.float64)[0])
+    storage = int(hdr[4])
+    dt = {8: np.float64, 4: np.float32}.get(elem)
+    n = sim.nodes
+    raw = np.frombuffer(buf[64:64 + q * n * elem].tobytes(),
+                        dtype=dt if dt else np.uint16).reshape((q, n))
+    if elem == 2:
+        if storage == L.FP16_SHIFTED:
+            raw = raw.view(np.float16).astype(np.float64)
+        else:  # bfloat16: the upper half of a float32
+            raw = (raw.astype(np.uint32) << 16).view(np.float32).astype(np.float64)
+    raw = raw.astype(np.float64)
+    qf = (9 if dim == 2 else 19) if flow else 0
+    qs = 9 if dim == 2 else 7
+    out = {}
+    for name, lo, qq, ref in (("f", 0, qf, 1.0), ("g", qf, qs, u_ref), ("h", qf + qs, qs, -1.0)):
+        w = np.array(_W[qq]) if qq else np.zeros(0)
+        out[name] = (raw[lo:lo + qq] + w[:, None] * ref).reshape((qq,) + sim.shape)
+    return out
