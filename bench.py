@@ -35,14 +35,14 @@ WORKLOADS = {
                     "seed R=16 at x=300, U0=0.4, 5-fold eps 0.03",
                dim=2, nx=1024, ny=1024, nz=1, flow=1, fold=5, eps=0.03, bc=(1, 0, 0),
                u_in=0.01, U_in=0.4, seed=(300.0, 512.0, 0.0, 16.0, 0.4, 0.01, 1),
-               storage="fp32", kernel="step2d_kernel", src="step2d.cu",
+               storage="fp32", kernel="step2d_tma_kernel", src="step2d.cu",
                sample=dict(nx=256, ny=256, seed=(75.0, 128.0, 0.0, 16.0, 0.4, 0.01, 1))),
     "c2_fp16": dict(base="c2", storage="fp16"),
     "c1": dict(desc="2D 128x128 periodic, no flow (phase field + solute D2Q9), U0=0.3, R=8, "
                     "4-fold eps 0.05",
                dim=2, nx=128, ny=128, nz=1, flow=0, fold=4, eps=0.05, bc=(0, 0, 0), u_in=0.0,
                U_in=0.0, seed=(64.0, 64.0, 0.0, 8.0, 0.3, 0.01, 1), storage="fp32",
-               kernel="step2d_kernel", src="step2d.cu",
+               kernel="step2d_tma_kernel", src="step2d.cu",
                sample=dict(nx=128, ny=128, seed=(64.0, 64.0, 0.0, 8.0, 0.3, 0.01, 1))),
     "c3": dict(desc="3D 256^3 coupled LB (D3Q19 flow, D3Q7 solute and phase field), cubic eps "
                     "0.04, sphere R=12, U0=0.3, inflow 0.005",
@@ -131,7 +131,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
-                 "--format=csv,noheader,nounits", "-lms", "100"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -221,7 +221,7 @@ def run_reference(args, w):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=4000)
+    ap.add_argument("--steps", type=int, default=20000)
     ap.add_argument("--warmup", type=int, default=200)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="c2", choices=sorted(WORKLOADS))

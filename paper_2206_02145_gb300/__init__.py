@@ -17,7 +17,7 @@ from dataclasses import dataclass
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "_build", "liblbpf.so")
+LIB_PATH = os.environ.get("LBPF_LIB") or os.path.join(_HERE, "_build", "liblbpf.so")
 
 OK, EINVAL, ECUDA, ENOMEM, ESTATE, ENONFINITE, ETIMEDOUT = 0, -1, -2, -3, -4, -5, -6
 BC_PERIODIC, BC_INLET_OUTLET, BC_WALL = 0, 1, 2

@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "liblbpf.so")
 SOURCES = ["lbpf_api.cu", "step2d.cu", "step3d.cu", "aux.cu"]
-HEADERS = ["lbpf_internal.cuh", "lbpf_device.cuh"]
+HEADERS = ["lbpf_internal.cuh", "lbpf_device.cuh", "step2d_core.cuh", "tma.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2",
               "--expt-relaxed-constexpr"]

@@ -100,51 +100,53 @@ __global__ void init_fields_kernel(const Model m, const double* phi, const doubl
   }
 }
 
-// Moments of one node in FP64 from the stored populations.
-template <typename T>
-__device__ void node_moments(const Model& m, const T* pops, long long j, double& phi, double& U,
-                             double& rho, double u[3]) {
+// Moments of one node from the stored populations, in the arithmetic type R
+// of the step (FP32, or FP64 for FP64 storage).
+template <typename T, typename R>
+__device__ void node_moments(const Model& m, const T* pops, long long j, R& phi, R& U, R& rho,
+                             R u[3]) {
   const long long P = m.plane;
   const T* pf = pops;
   const T* pg = pops + (long long)m.qf * P;
   const T* ph_ = pops + (long long)(m.qf + m.qs) * P;
-  double dphi = 0.0, dU = 0.0, drho = 0.0;
-  double mo[3] = {0.0, 0.0, 0.0};
+  R dphi = R(0), dU = R(0), drho = R(0);
+  R mo[3] = {R(0), R(0), R(0)};
   if (m.dim == 2) {
     for (int a = 0; a < 9; ++a) {
-      dU += Pop<T>::template ld<double>(pg + a * P + j);
-      dphi += Pop<T>::template ld<double>(ph_ + a * P + j);
+      dU += Pop<T>::template ld<R>(pg + a * P + j);
+      dphi += Pop<T>::template ld<R>(ph_ + a * P + j);
     }
     if (m.flow) {
       for (int a = 0; a < 9; ++a) {
-        const double v = Pop<T>::template ld<double>(pf + a * P + j);
+        const R v = Pop<T>::template ld<R>(pf + a * P + j);
         drho += v;
-        mo[0] += D2_CX[a] * v;
-        mo[1] += D2_CY[a] * v;
+        mo[0] += R(D2_CX[a]) * v;
+        mo[1] += R(D2_CY[a]) * v;
       }
     }
   } else {
     for (int a = 0; a < 7; ++a) {
-      dU += Pop<T>::template ld<double>(pg + a * P + j);
-      dphi += Pop<T>::template ld<double>(ph_ + a * P + j);
+      dU += Pop<T>::template ld<R>(pg + a * P + j);
+      dphi += Pop<T>::template ld<R>(ph_ + a * P + j);
     }
     if (m.flow) {
       for (int a = 0; a < 19; ++a) {
-        const double v = Pop<T>::template ld<double>(pf + a * P + j);
+        const R v = Pop<T>::template ld<R>(pf + a * P + j);
         drho += v;
-        mo[0] += D3_CX[a] * v;
-        mo[1] += D3_CY[a] * v;
-        mo[2] += D3_CZ[a] * v;
+        mo[0] += R(D3_CX[a]) * v;
+        mo[1] += R(D3_CY[a]) * v;
+        mo[2] += R(D3_CZ[a]) * v;
       }
     }
   }
-  phi = m.ref_h + dphi;
-  U = m.ref_g + dU;
-  rho = m.ref_f + drho;
-  const double ph = phi < -1.0 ? -1.0 : (phi > 1.0 ? 1.0 : phi);
-  const double K = m.flow ? m.kdrag * (1.0 + ph) * (1.0 + ph) * (1.0 - ph) : 0.0;
-  for (int d = 0; d < 3; ++d)
-    u[d] = m.flow ? (mo[d] + 0.5 * m.body[d]) / (rho + 0.5 * K) : 0.0;
+  const Coef<R>& c = coef<R>(m);
+  phi = c.ref_h + dphi;
+  U = c.ref_g + dU;
+  rho = c.ref_f + drho;
+  const R ph = phi < R(-1) ? R(-1) : (phi > R(1) ? R(1) : phi);
+  const R K = m.flow ? c.kdrag * (R(1) + ph) * (R(1) + ph) * (R(1) - ph) : R(0);
+  const R inv = R(1) / (rho + R(0.5) * K);
+  for (int d = 0; d < 3; ++d) u[d] = m.flow ? (mo[d] + R(0.5) * c.body[d]) * inv : R(0);
 }
 
 template <typename T, typename R, typename O>
@@ -156,9 +158,9 @@ __global__ void fields_kernel(const Model m, const T* pops, const R* phi_prev, u
     int x, y, z;
     node_xyz(m, i, x, y, z);
     const long long j = pitched(m, x, y, z);
-    double phi, U, rho, u[3];
-    node_moments<T>(m, pops, j, phi, U, rho, u);
-    const double vals[7] = {phi, U, rho, u[0], u[1], u[2], m.ref_h + double(phi_prev[j])};
+    R phi, U, rho, u[3];
+    node_moments<T, R>(m, pops, j, phi, U, rho, u);
+    const R vals[7] = {phi, U, rho, u[0], u[1], u[2], coef<R>(m).ref_h + phi_prev[j]};
     int slot = 0;
     for (int b = 0; b < 7; ++b)
       if (mask & (1u << b)) out[(long long)(slot++) * n + i] = O(vals[b]);
@@ -179,16 +181,17 @@ __global__ void __launch_bounds__(kDiagThreads)
     int x, y, z;
     node_xyz(m, i, x, y, z);
     const long long j = pitched(m, x, y, z);
-    double phi, U, rho, u[3];
-    node_moments<T>(m, pops, j, phi, U, rho, u);
+    R phi, U, rho, u[3];
+    node_moments<T, R>(m, pops, j, phi, U, rho, u);
+    // FP64 accumulation of per-node values formed in the step's arithmetic
     const double pp = m.ref_h + double(phi_prev[j]);
-    const double ph = phi < -1.0 ? -1.0 : (phi > 1.0 ? 1.0 : phi);
-    acc[0] += U + pp;
-    acc[1] += rho;
-    acc[2] += 0.5 * (1.0 + ph);
-    const double um = sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+    const R ph = phi < R(-1) ? R(-1) : (phi > R(1) ? R(1) : phi);
+    acc[0] += double(U) + pp;
+    acc[1] += double(rho);
+    acc[2] += 0.5 * (1.0 + double(ph));
+    const double um = double(sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]));
     acc[3] = um > acc[3] ? um : acc[3];
-    if (!(isfinite(phi) && isfinite(U) && isfinite(rho))) acc[4] += 1.0;
+    if (!(finite_r(phi) && finite_r(U) && finite_r(rho))) acc[4] += 1.0;
   }
   __shared__ double sh[kDiagSlots][kDiagThreads];
   for (int k = 0; k < kDiagSlots; ++k) sh[k][threadIdx.x] = acc[k];
@@ -230,7 +233,7 @@ __global__ void __launch_bounds__(kDiagThreads)
 
 // phi = 0 crossing along the six axis rays from (icx, icy, icz): the first
 // sign change from phi >= 0 to phi < 0, linearly interpolated; -1 if none.
-template <typename T>
+template <typename T, typename R>
 __global__ void crossing_kernel(const Model m, const T* pops, int icx, int icy, int icz,
                                 double* out) {
   const int r = threadIdx.x;
@@ -240,9 +243,9 @@ __global__ void crossing_kernel(const Model m, const T* pops, int icx, int icy, 
   if (axis < m.dim) {
     const int n = axis == 0 ? m.nx : (axis == 1 ? m.ny : m.nz);
     int c[3] = {icx, icy, m.dim == 3 ? icz : 0};
-    double phi, U, rho, u[3];
-    node_moments<T>(m, pops, pitched(m, c[0], c[1], c[2]), phi, U, rho, u);
-    double prev = phi;
+    R phi, U, rho, u[3];
+    node_moments<T, R>(m, pops, pitched(m, c[0], c[1], c[2]), phi, U, rho, u);
+    double prev = double(phi);
     if (prev >= 0.0) {
       const int limit = m.bc[axis] == BC_PERIODIC ? n / 2 : n;
       const int start = c[axis];
@@ -251,12 +254,12 @@ __global__ void crossing_kernel(const Model m, const T* pops, int icx, int icy, 
         if (m.bc[axis] == BC_PERIODIC) v = ((v % n) + n) % n;
         else if (v < 0 || v >= n) break;
         c[axis] = v;
-        node_moments<T>(m, pops, pitched(m, c[0], c[1], c[2]), phi, U, rho, u);
-        if (phi < 0.0) {
-          res = double(d - 1) + prev / (prev - phi);
+        node_moments<T, R>(m, pops, pitched(m, c[0], c[1], c[2]), phi, U, rho, u);
+        if (double(phi) < 0.0) {
+          res = double(d - 1) + prev / (prev - double(phi));
           break;
         }
-        prev = phi;
+        prev = double(phi);
       }
     }
   }
@@ -302,7 +305,7 @@ cudaError_t diag_t(const Model& m, const void* pops, const void* pp, double* par
   diag_partial_kernel<T, R><<<kDiagBlocks, kDiagThreads, 0, s>>>(
       m, static_cast<const T*>(pops), static_cast<const R*>(pp), partials);
   diag_final_kernel<<<1, kDiagThreads, 0, s>>>(partials, kDiagBlocks, out);
-  crossing_kernel<T><<<1, 32, 0, s>>>(m, static_cast<const T*>(pops), icx, icy, icz, out);
+  crossing_kernel<T, R><<<1, 32, 0, s>>>(m, static_cast<const T*>(pops), icx, icy, icz, out);
   return cudaGetLastError();
 }
 

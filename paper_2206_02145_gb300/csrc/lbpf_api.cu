@@ -32,6 +32,7 @@ struct lbpf {
   size_t dev_bytes = 0;
   size_t es = 4;  // population element bytes
   size_t rs = 4;  // phi ring element bytes
+  lbk::StepMaps maps;
   cudaGraphExec_t graph = nullptr;
   int graph_steps = 0;
   int status = LBPF_OK;
@@ -71,7 +72,9 @@ int validate(const lbpf_params* p, char* why, size_t n) {
   };
   if (p->dim != 2 && p->dim != 3) return bad("dim must be 2 or 3");
   if (p->nx < 4 || p->ny < 4 || (p->dim == 3 && p->nz < 4)) return bad("every grid dimension must be >= 4");
-  if ((double)p->nx * p->ny * (p->dim == 3 ? p->nz : 1) > 4.0e9) return bad("grid too large");
+  // node offsets are 32-bit: at most 2^31 - 1 (padded) nodes per array
+  if ((double)((p->nx + 31) / 32 * 32) * p->ny * (p->dim == 3 ? p->nz : 1) > 2147483647.0)
+    return bad("grid too large (more than 2^31 nodes per population array)");
   for (int d = 0; d < 3; ++d)
     if (p->bc[d] < 0 || p->bc[d] > 2) return bad("unknown boundary condition");
   if (p->bc[1] == LBPF_BC_INLET_OUTLET || p->bc[2] == LBPF_BC_INLET_OUTLET)
@@ -132,6 +135,7 @@ Model derive(const lbpf_params& p) {
   m.ref_f = 1.0;
   m.ref_g = 0.0;
   m.ref_h = -1.0;
+  lbk::finalize(m);
   return m;
 }
 
@@ -147,6 +151,7 @@ int check_device_error(lbpf* h) {
   unsigned e = 0;
   CK(h, cudaMemcpyAsync(&e, h->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost, h->stream));
   CK(h, cudaStreamSynchronize(h->stream));
+  if (e & 2u) return fail(h, LBPF_ETIMEDOUT, "a step kernel gave up waiting for its tile loads");
   if (e & 1u) return fail(h, LBPF_ENONFINITE, "a non-finite phi, U or rho appeared in the step");
   return LBPF_OK;
 }
@@ -154,8 +159,8 @@ int check_device_error(lbpf* h) {
 int launch_one(lbpf* h, cudaStream_t s) {
   const int c = h->cur;
   cudaError_t e = h->m.dim == 2
-                      ? lbk::launch_step2d(h->m, h->pops[c], h->pops[c ^ 1], h->phi[c],
-                                            h->phi[c ^ 1], h->d_err, s)
+                      ? lbk::launch_step2d(h->m, h->maps, c, h->pops[c], h->pops[c ^ 1],
+                                           h->phi[c], h->phi[c ^ 1], h->d_err, s)
                       : lbk::launch_step3d(h->m, h->pops[c], h->pops[c ^ 1], h->phi[c],
                                             h->phi[c ^ 1], h->d_err, s);
   if (e != cudaSuccess) return fail(h, LBPF_ECUDA, "step launch: %s", cudaGetErrorString(e));
@@ -287,6 +292,14 @@ int lbpf_create(const lbpf_params* p, void* stream, lbpf_t** out) {
     lbpf_destroy(h);
     return LBPF_ECUDA;
   }
+  if (h->m.dim == 2) {
+    e = lbk::prepare_step2d(h->m, h->pops, h->phi, &h->maps);
+    if (e != cudaSuccess) {
+      fprintf(stderr, "lbpf_create: step setup: %s\n", cudaGetErrorString(e));
+      lbpf_destroy(h);
+      return LBPF_ECUDA;
+    }
+  }
   h->icx = h->m.nx / 2;
   h->icy = h->m.ny / 2;
   h->icz = h->m.nz / 2;
@@ -301,6 +314,7 @@ int lbpf_init_seed(lbpf_t* h, const lbpf_seed* s) {
       !std::isfinite(s->cx) || !std::isfinite(s->cy) || !std::isfinite(s->cz))
     return fail(h, LBPF_EINVAL, "invalid seed");
   h->m.ref_g = s->u0;
+  lbk::finalize(h->m);
   drop_graph(h);
   lbk::SeedArgs a{s->cx, s->cy, s->cz, s->radius, s->u0, s->noise_amp, s->seed};
   h->cur = 0;
@@ -345,6 +359,7 @@ int lbpf_init_fields(lbpf_t* h, const double* phi, const double* U, const double
     for (size_t i = 0; i < n; ++i) mean += U[i];
     h->m.ref_g = mean / double(n);
   }
+  lbk::finalize(h->m);
   drop_graph(h);
   h->cur = 0;
   h->step = 0;
@@ -460,6 +475,7 @@ int lbpf_write_state(lbpf_t* h, const void* host_src, size_t bytes) {
   h->step = hd.step;
   if (h->m.ref_g != hd.ref_g) drop_graph(h);
   h->m.ref_g = hd.ref_g;
+  lbk::finalize(h->m);
   if (!h->initialized) {
     h->initialized = true;
     store_I0(h);

@@ -112,20 +112,20 @@ __device__ __forceinline__ void aniso(const Model& m, R gx, R gy, R gz, R& as, R
   as = R(1);
   Nx = Ny = Nz = R(0);
   R g2 = gx * gx + gy * gy + gz * gz;
-  if (!(g2 > R(1e-12)) || m.eps == 0.0) return;
+  const Coef<R>& c = coef<R>(m);
+  if (!(g2 > R(1e-12)) || c.eps == R(0)) return;
   const R ig = rsqrt_r(g2);
   const R nx = -gx * ig, ny = -gy * ig, nz = -gz * ig;
-  const R eps = R(m.eps), fac = R(m.aniso_fac);
+  const R eps = c.eps, fac = c.aniso_fac;
   if (m.fold > 0) {
-    R c = nx, s = ny;
+    R ck = nx, sk = ny;
     for (int j = 1; j < m.fold; ++j) {
-      const R c2 = c * nx - s * ny;
-      s = c * ny + s * nx;
-      c = c2;
+      const R c2 = ck * nx - sk * ny;
+      sk = ck * ny + sk * nx;
+      ck = c2;
     }
-    const R ck0 = R(m.ck0), sk0 = R(m.sk0);
-    const R cosd = c * ck0 + s * sk0;
-    const R sind = s * ck0 - c * sk0;
+    const R cosd = ck * c.ck0 + sk * c.sk0;
+    const R sind = sk * c.ck0 - ck * c.sk0;
     as = R(1) + eps * cosd;
     const R amp = fac * R(m.fold) * eps * as * sind;
     Nx = amp * gy;

@@ -2,19 +2,30 @@
 // Nothing here is part of the C ABI (include/lbpf.h is).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <type_traits>
 
 namespace lbk {
 
 enum { BC_PERIODIC = 0, BC_INOUT = 1, BC_WALL = 2 };
 enum { ST_FP32 = 0, ST_FP64 = 1, ST_FP16 = 2, ST_BF16 = 3 };
 
-// Derived model constants (FP64 on the host; each kernel casts to its
-// arithmetic type).  Device layout: every population is its own array of
+// Model constants in one arithmetic type.  The kernels read the copy in their
+// own type: converting a double constant inside the per-node code would run
+// on the FP64 pipe, which on GB300 is narrow enough to bound the whole step.
+template <typename R>
+struct Coef {
+  R omega_f, guo, tauU_slope, inv_tau0, tpc, lambda, eps, ck0, sk0, aniso_fac, kdrag;
+  R body[3];
+  R u_in, U_in, ref_f, ref_g, ref_h;
+};
+
+// Derived model constants (FP64 on the host; the kernels use cf / cd).  Device layout: every population is its own array of
 // `plane` elements, node (x, y, z) at (z * ny + y) * px + x, px a multiple
 // of 32 elements so that every row starts 128-byte aligned.  Population
 // arrays of one buffer are consecutive: f (qf of them, 0 without flow),
@@ -40,11 +51,72 @@ struct Model {
   double body[3];
   double u_in, U_in;   // inflow ghost state
   double ref_f, ref_g, ref_h;  // reference moments of the stored deviations (1, U_ref, -1)
+  Coef<float> cf;   // the constants above in FP32 ...
+  Coef<double> cd;  // ... and in FP64 (filled by finalize())
+};
+
+// Fill m.cf and m.cd from the FP64 fields; call after every change of those.
+inline void finalize(Model& m) {
+  auto fill = [&](auto& c) {
+    using R = std::remove_reference_t<decltype(c.omega_f)>;
+    c.omega_f = R(m.omega_f);
+    c.guo = R(m.guo);
+    c.tauU_slope = R(m.tauU_slope);
+    c.inv_tau0 = R(m.inv_tau0);
+    c.tpc = R(m.tpc);
+    c.lambda = R(m.lambda);
+    c.eps = R(m.eps);
+    c.ck0 = R(m.ck0);
+    c.sk0 = R(m.sk0);
+    c.aniso_fac = R(m.aniso_fac);
+    c.kdrag = R(m.kdrag);
+    for (int d = 0; d < 3; ++d) c.body[d] = R(m.body[d]);
+    c.u_in = R(m.u_in);
+    c.U_in = R(m.U_in);
+    c.ref_f = R(m.ref_f);
+    c.ref_g = R(m.ref_g);
+    c.ref_h = R(m.ref_h);
+  };
+  fill(m.cf);
+  fill(m.cd);
+}
+
+template <typename R>
+__host__ __device__ __forceinline__ const Coef<R>& coef(const Model& m);
+template <>
+__host__ __device__ __forceinline__ const Coef<float>& coef<float>(const Model& m) {
+  return m.cf;
+}
+template <>
+__host__ __device__ __forceinline__ const Coef<double>& coef<double>(const Model& m) {
+  return m.cd;
+}
+
+// Base pointer of every population array of one buffer (f, then g, then h).
+// Passed by value as a kernel parameter, so that each access is one
+// constant-bank base plus a 32-bit node offset.
+struct PopPtrs {
+  void* p[27];
+};
+// TMA descriptors of the 2D step for both population buffers (index = the
+// parity of the source buffer) and the launch shape of the persistent kernel.
+struct StepMaps {
+  CUtensorMap fg[2], h[2], ring[2];
+  int ctas = 0, smem = 0, ready = 0;
 };
 
 // Launchers (each returns the launch error).
-cudaError_t launch_step2d(const Model& m, const void* src, void* dst, const void* phi_prev,
-                          void* phi_cur, unsigned* err, cudaStream_t s);
+cudaError_t prepare_step2d(const Model& m, void* const pops[2], void* const rings[2],
+                           StepMaps* out);
+cudaError_t launch_step2d(const Model& m, const StepMaps& maps, int c, const void* src, void* dst,
+                          const void* ring_prev, void* ring_cur, unsigned* err, cudaStream_t s);
+inline PopPtrs pop_ptrs(const Model& m, void* buf, size_t elem_bytes) {
+  PopPtrs r{};
+  const int q = m.qf + 2 * m.qs;
+  for (int a = 0; a < q && a < 27; ++a)
+    r.p[a] = static_cast<char*>(buf) + size_t(a) * size_t(m.plane) * elem_bytes;
+  return r;
+}
 cudaError_t launch_step3d(const Model& m, const void* src, void* dst, const void* phi_prev,
                           void* phi_cur, unsigned* err, cudaStream_t s);
 

@@ -1,298 +1,384 @@
 // Fused coupled LB step in 2D: D2Q9 flow f (Eqs. 4-12), D2Q9 solute g
-// (Eqs. 13-18) and D2Q9 phase field h (Eqs. 19-23), one thread per node.
+// (Eqs. 13-18) and D2Q9 phase field h (Eqs. 19-23).
 //
-// Streaming is done in push form: the thread of node s loads its own
-// populations (aligned, coalesced), forms every moment locally, collides and
-// writes the post-collision value of direction a to s + c_a.  That is the
-// same update as the pull form of the paper's equations; it needs no stored
-// macroscopic fields, only phi(t-1) for d(phi)/dt.  Per node and step the
-// HBM traffic is 27 populations read + 27 written + phi(t-1) read + phi(t)
-// written (224 B in FP32 with flow, 152 B without).
+// Streaming is done in push form: the thread of node s holds its own
+// populations, forms every moment locally, collides and writes the
+// post-collision value of direction a to s + c_a.  That is the same update
+// as the pull form of the paper's equations; it needs no stored macroscopic
+// fields, only phi(t-1) for d(phi)/dt.  Per node and step the HBM traffic is
+// 27 populations read + 27 written + phi(t-1) read + phi(t) written (224 B in
+// FP32 with flow, 152 B without, 116 B with 16-bit populations).
 //
-// Populations are handled as deviations d_a = p_a - w_a M_ref (M_ref = 1 for
-// f, U_ref for g, -1 for h); the phi ring holds phi + 1.
+// Populations are deviations d_a = p_a - w_a M_ref (M_ref = 1 for f, U_ref
+// for g, -1 for h); the phi ring holds phi + 1.
 //
 // Two parts of the step need neighbour data, both served from shared memory:
-//   - grad(phi) for the normal and anisotropy (Eq. 3, Eq. 21, Eq. 23): phi(t)
-//     of the tile plus a one-node halo, summed from the h populations;
-//   - Eq. 19 writes a_s^2 h(r + c, t+1) = h*(r) - (1 - a_s^2(r)) h(r + c, t):
-//     the old h of the destination node, which is the tile's own h or the
-//     halo's, staged in shared memory next to phi.
-// The halo ring is loaded in the same round trip as the tile's own
-// populations (one ring node per thread of the first 2 (TX + TY) + 4).
-#include "lbpf_device.cuh"
+// grad(phi) (Eq. 3, 21, 23) needs phi(t) of a one-node halo, summed from the
+// halo's h populations, and Eq. 19 writes
+// a_s^2 h(r + c, t+1) = h*(r) - (1 - a_s^2(r)) h(r + c, t), i.e. needs the old
+// h of the destination node.
+//
+// step2d_tma_kernel (FP32 and 16-bit storage): persistent CTAs stream 32 x 4
+// tiles through a 2-stage shared-memory pipeline, 4 CTAs of 128 threads per SM
+// (tile, depth and CTAs per SM chosen by a sweep on GB300).  Per tile one thread issues
+// three TMA tensor loads on one mbarrier: f and g of the tile, h of the tile
+// plus halo (box starting 16 bytes left of the tile so that its innermost
+// coordinate stays aligned), and the phi ring of the tile.  While a tile is
+// computed and pushed, the next one is in flight.  Halo positions outside
+// the domain (the TMA fills them with zeros) are patched with the mapped
+// periodic / zero-gradient values on edge tiles only.
+//
+// step2d_kernel (FP64 storage): one thread per node, one tile per CTA, the
+// same per-node code.
+#include <cudaTypedefs.h>
+
+#include "step2d_core.cuh"
+#include "tma.cuh"
 
 namespace lbk {
 namespace {
 
+constexpr int kSpin = 1 << 22;  // bound on mbarrier polls before giving up
+
+// ---- FP64 (and reference) kernel: one tile per CTA ------------------------------
 template <typename T, typename R, bool FLOW, int TX, int TY>
 __global__ void __launch_bounds__(TX* TY)
-    step2d_kernel(const Model m, const T* __restrict__ src, T* __restrict__ dst,
+    step2d_kernel(const Model m, const PopPtrs sp, const PopPtrs dp,
                   const R* __restrict__ ring_prev, R* __restrict__ ring_cur,
                   unsigned* __restrict__ err) {
   constexpr int SX = TX + 2, SY = TY + 2;
   constexpr int QF = FLOW ? 9 : 0;
   constexpr int NT = TX * TY;
-  constexpr int RING = 2 * SX + 2 * TY;
-  static_assert(RING <= NT, "one ring node per thread");
-  __shared__ R sh_phi[SY][SX];  // phi + 1 of tile and halo
-  __shared__ R sh_h[9][SY][SX];  // h deviations of tile and halo
+  __shared__ R sh_phi[SY][SX];
+  __shared__ R sh_h[9][SY][SX];
 
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int tid = ty * TX + tx;
   const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
   const int x = x0 + tx, y = y0 + ty;
   const int nx = m.nx, ny = m.ny, px = m.px;
-  const long long P = m.plane;
   const bool active = x < nx && y < ny;
-  const bool full = x0 + TX <= nx && y0 + TY <= ny;
-  const long long idx = (long long)y * px + x;
+  const int idx = y * px + x;
 
-  const T* sf = src;
-  const T* sg = src + (long long)QF * P;
-  const T* shp = src + (long long)(QF + 9) * P;
-
-  // ---- one round trip: own populations, phi ring, and (full tiles) the halo
   R f[9], g[9], h[9];
   R dphi_prev = R(0);
   if (active) {
 #pragma unroll
     for (int a = 0; a < 9; ++a) {
-      if (FLOW) f[a] = Pop<T>::template ld<R>(sf + a * P + idx);
-      g[a] = Pop<T>::template ld<R>(sg + a * P + idx);
-      h[a] = Pop<T>::template ld<R>(shp + a * P + idx);
+      if (FLOW) f[a] = Pop<T>::template ld<R>(static_cast<const T*>(sp.p[a]) + idx);
+      g[a] = Pop<T>::template ld<R>(static_cast<const T*>(sp.p[QF + a]) + idx);
+      h[a] = Pop<T>::template ld<R>(static_cast<const T*>(sp.p[QF + 9 + a]) + idx);
     }
     dphi_prev = ring_prev[idx];
   }
-  R hv[9];
-  int rlx = 0, rly = 0;
-  const bool ring_thread = full && tid < RING;
-  if (ring_thread) {
-    if (tid < SX) {
-      rlx = tid;
-      rly = 0;
-    } else if (tid < 2 * SX) {
-      rlx = tid - SX;
-      rly = SY - 1;
-    } else if (tid < 2 * SX + TY) {
-      rlx = 0;
-      rly = 1 + tid - 2 * SX;
-    } else {
-      rlx = SX - 1;
-      rly = 1 + tid - 2 * SX - TY;
-    }
-    const int gx = grad_coord(x0 + rlx - 1, nx, m.bc[0]);
-    const int gy = grad_coord(y0 + rly - 1, ny, m.bc[1]);
-    const long long j = (long long)gy * px + gx;
-#pragma unroll
-    for (int a = 0; a < 9; ++a) hv[a] = Pop<T>::template ld<R>(shp + a * P + j);
-  }
-  R dphi = R(0);
   if (active) {
-#pragma unroll
-    for (int a = 0; a < 9; ++a) {
-      dphi += h[a];  // Eq. 22: phi = -1 + sum d_h
-      sh_h[a][ty + 1][tx + 1] = h[a];
-    }
-    sh_phi[ty + 1][tx + 1] = dphi;
-  }
-  if (ring_thread) {
     R s = R(0);
 #pragma unroll
     for (int a = 0; a < 9; ++a) {
-      s += hv[a];
-      sh_h[a][rly][rlx] = hv[a];
+      s += h[a];
+      sh_h[a][ty + 1][tx + 1] = h[a];
     }
-    sh_phi[rly][rlx] = s;
+    sh_phi[ty + 1][tx + 1] = s;
   }
-  if (!full) {
-    // edge tile: every position not owned by an active thread, mapped
-    for (int i = tid; i < SX * SY; i += NT) {
-      const int lx = i % SX, ly = i / SX;
-      int gx = x0 + lx - 1, gy = y0 + ly - 1;
-      if (lx >= 1 && lx <= TX && ly >= 1 && ly <= TY && gx < nx && gy < ny) continue;
-      gx = grad_coord(gx, nx, m.bc[0]);
-      gy = grad_coord(gy, ny, m.bc[1]);
-      const long long j = (long long)gy * px + gx;
-      R s = R(0);
+  // halo ring (and positions of a partial tile): phi and h of the mapped node
+  for (int i = tid; i < SX * SY; i += NT) {
+    const int lx = i % SX, ly = i / SX;
+    int gx = x0 + lx - 1, gy = y0 + ly - 1;
+    if (lx >= 1 && lx <= TX && ly >= 1 && ly <= TY && gx < nx && gy < ny) continue;
+    gx = grad_coord(gx, nx, m.bc[0]);
+    gy = grad_coord(gy, ny, m.bc[1]);
+    const int j = gy * px + gx;
+    R s = R(0);
 #pragma unroll
-      for (int a = 0; a < 9; ++a) {
-        const R v = Pop<T>::template ld<R>(shp + a * P + j);
-        sh_h[a][ly][lx] = v;
-        s += v;
-      }
-      sh_phi[ly][lx] = s;
+    for (int a = 0; a < 9; ++a) {
+      const R v = Pop<T>::template ld<R>(static_cast<const T*>(sp.p[QF + 9 + a]) + j);
+      sh_h[a][ly][lx] = v;
+      s += v;
     }
+    sh_phi[ly][lx] = s;
   }
   __syncthreads();
   if (!active) return;
+  TileView<R, R, SX, SX * SY, 0> hs{&sh_h[0][0][0]};
+  if (x0 >= 1 && x0 + TX <= nx - 1 && y0 >= 1 && y0 + TY <= ny - 1)
+    collide_push_2d<T, R, FLOW, true, SX>(m, x, y, tx + 1, ty + 1, f, g, h,
+                                          sh_phi[ty + 1][tx + 1], dphi_prev, &sh_phi[0][0], hs,
+                                          static_cast<T*>(dp.p[0]), ring_cur, err);
+  else
+    collide_push_2d<T, R, FLOW, false, SX>(m, x, y, tx + 1, ty + 1, f, g, h,
+                                           sh_phi[ty + 1][tx + 1], dphi_prev, &sh_phi[0][0], hs,
+                                           static_cast<T*>(dp.p[0]), ring_cur, err);
+}
 
-  // ---- local moments (Eqs. 11, 12, 17, 22) ----------------------------------
-  const R phi = dphi - R(1);
-  R dU = R(0);
-#pragma unroll
-  for (int a = 0; a < 9; ++a) dU += g[a];
-  const R U = R(m.ref_g) + dU;
-  R drho = R(0), mx = R(0), my = R(0);
-  if (FLOW) {
-#pragma unroll
-    for (int a = 0; a < 9; ++a) drho += f[a];
-    mx = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
-    my = (f[2] - f[4]) + (f[5] + f[6]) - (f[7] + f[8]);
+// ---- TMA-pipelined persistent kernel ------------------------------------------
+template <typename T, bool FLOW, int TX, int TY>
+struct Tiles2D {
+  static constexpr int QFG = (FLOW ? 9 : 0) + 9;   // f and g arrays
+  static constexpr int HX = 16 / int(sizeof(T));   // halo box starts HX left of the tile
+  static constexpr int BXH = TX + 2 * HX;          // h box width
+  static constexpr int FG_BYTES = QFG * TY * TX * int(sizeof(T));
+  static constexpr int H_BYTES = 9 * (TY + 2) * BXH * int(sizeof(T));
+  static constexpr int RING_BYTES = TY * TX * 4;
+  static constexpr int al(int b) { return (b + 127) / 128 * 128; }
+  static constexpr int OFF_H = al(FG_BYTES);
+  static constexpr int OFF_RING = OFF_H + al(H_BYTES);
+  static constexpr int STAGE = OFF_RING + al(RING_BYTES);
+  static constexpr int TX_BYTES = FG_BYTES + H_BYTES + RING_BYTES;
+};
+
+// Pipeline depth and resident CTAs per SM of the persistent kernel.
+#ifndef LBPF_2D_STAGES
+#define LBPF_2D_STAGES 2
+#endif
+#ifndef LBPF_2D_MIN_CTAS
+#define LBPF_2D_MIN_CTAS 4
+#endif
+#ifndef LBPF_2D_TY
+#define LBPF_2D_TY 4
+#endif
+
+template <typename T, bool FLOW, int TX, int TY, int S>
+__global__ void __launch_bounds__(TX* TY, LBPF_2D_MIN_CTAS)
+    step2d_tma_kernel(const __grid_constant__ CUtensorMap tm_fg,
+                      const __grid_constant__ CUtensorMap tm_h,
+                      const __grid_constant__ CUtensorMap tm_ring, const Model m,
+                      const T* __restrict__ src, T* __restrict__ dst,
+                      float* __restrict__ ring_cur, unsigned* __restrict__ err, int ntx,
+                      int ntiles) {
+  using R = float;
+  using L = Tiles2D<T, FLOW, TX, TY>;
+  constexpr int NT = TX * TY, SX = TX + 2, SY = TY + 2;
+  constexpr int QF = FLOW ? 9 : 0;
+  extern __shared__ unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t full[S];
+  __shared__ R sh_phi[SY][SX];
+  unsigned char* smem = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+
+  const int tid = threadIdx.x;
+  const int tx = tid % TX, ty = tid / TX;
+  const int nx = m.nx, ny = m.ny, px = m.px;
+  const int first = blockIdx.x, G = gridDim.x;
+
+  auto issue = [&](int tile, int s) {
+    const int x0 = (tile % ntx) * TX, y0 = (tile / ntx) * TY;
+    unsigned char* st = smem + s * L::STAGE;
+    mbar_arrive_expect_tx(&full[s], L::TX_BYTES);
+    tma_load_3d(st, &tm_fg, &full[s], x0, y0, 0);
+    tma_load_3d(st + L::OFF_H, &tm_h, &full[s], x0 - L::HX, y0 - 1, L::QFG);
+    tma_load_2d(st + L::OFF_RING, &tm_ring, &full[s], x0, y0);
+  };
+
+  if (tid == 0) {
+    for (int s = 0; s < S; ++s) mbar_init(&full[s], 1);
+    fence_barrier_init();
   }
-  const R rho = R(1) + drho;
-  const R ph = clamp1(phi);
-  const R mask = R(0.5) * (R(1) - ph);  // (1 - phi)/2 of Eq. 7 and q(phi) of Eq. 18
-  R ux = R(0), uy = R(0), Fx = R(0), Fy = R(0);
-  if (FLOW) {
-    // Eq. 6: F = b - K u, K = h tau_f (1+phi)^2 (1-phi) / (4 W0^2); the Guo
-    // half-force velocity u = (m + F/2)/rho solved in closed form.
-    const R K = R(m.kdrag) * (R(1) + ph) * (R(1) + ph) * (R(1) - ph);
-    const R inv = R(1) / (rho + R(0.5) * K);
-    ux = (mx + R(0.5) * R(m.body[0])) * inv;
-    uy = (my + R(0.5) * R(m.body[1])) * inv;
-    Fx = R(m.body[0]) - K * ux;
-    Fy = R(m.body[1]) - K * uy;
-  }
-  const R usx = mask * ux, usy = mask * uy;  // u* (Eq. 7)
-  const R omega_U = R(1) / (R(0.5) + R(m.tauU_slope) * mask);  // Eq. 18
-  const R dphidt = dphi - dphi_prev;
-  ring_cur[idx] = dphi;
-  if (!(finite_r(phi) && finite_r(U) && finite_r(rho))) atomicOr(err, 1u);
+  __syncthreads();
+  if (tid == 0)
+    for (int k = 0; k < S; ++k)
+      if (first + k * G < ntiles) issue(first + k * G, k);
 
-  // ---- gradient, anisotropy, phase-field coefficients (Eqs. 3, 20, 21, 23) --
-  const int lx = tx + 1, ly = ty + 1;
-  const R pE = sh_phi[ly][lx + 1], pW = sh_phi[ly][lx - 1];
-  const R pN = sh_phi[ly + 1][lx], pS = sh_phi[ly - 1][lx];
-  const R pNE = sh_phi[ly + 1][lx + 1], pNW = sh_phi[ly + 1][lx - 1];
-  const R pSE = sh_phi[ly - 1][lx + 1], pSW = sh_phi[ly - 1][lx - 1];
-  // grad = 3 sum_a w_a c_a phi(x + c_a) over D2Q9
-  const R gxv = R(1.0 / 3.0) * (pE - pW) + R(1.0 / 12.0) * ((pNE + pSE) - (pNW + pSW));
-  const R gyv = R(1.0 / 3.0) * (pN - pS) + R(1.0 / 12.0) * ((pNE + pNW) - (pSE + pSW));
-  R as, Nx, Ny, Nz;
-  aniso<R>(m, gxv, gyv, R(0), as, Nx, Ny, Nz);
-  const R a2 = as * as;
-  const R inv_a2 = R(1) / a2;
-  const R omega_phi = R(1) / (a2 * R(m.tpc) + R(0.5));  // Eq. 23
-  const R phi2m = R(1) - phi * phi;
-  const R Qs = (phi - phi * phi * phi + R(m.lambda) * U * phi2m * phi2m) * R(m.inv_tau0);  // Eq. 20
-  const R tpc = R(m.tpc);
-  const R uu = usx * usx + usy * usy, uF = usx * Fx + usy * Fy;
-  const R omega_f = R(m.omega_f), guo = R(m.guo);
-
-  T* df = dst;
-  T* dg = dst + (long long)QF * P;
-  T* dh = dst + (long long)(QF + 9) * P;
-  const int bcx = m.bc[0], bcy = m.bc[1];
-
-#pragma unroll
-  for (int a = 0; a < 9; ++a) {
-    const int cx = D2_CX[a], cy = D2_CY[a];
-    const R w = d2_w<R>(a);
-    const R cu = R(cx) * usx + R(cy) * usy;
-    // post-collision deviations at this node
-    R fp = R(0);
-    if (FLOW) {
-      const R cF = R(cx) * Fx + R(cy) * Fy;
-      const R feq = w * (drho + rho * (R(3) * cu + R(4.5) * cu * cu - R(1.5) * uu));  // Eq. 9
-      const R G = w * guo * (R(3) * cF + R(9) * cu * cF - R(3) * uF);               // Eq. 5
-      fp = f[a] - omega_f * (f[a] - feq) + G;                                       // Eq. 4, 8
-    }
-    const R geq = w * (dU + U * R(3) * cu);                    // Eq. 16
-    const R gp = g[a] - omega_U * (g[a] - geq) - w * dphidt;   // Eqs. 13-15
-    const R heq = w * (dphi - tpc * (R(cx) * Nx + R(cy) * Ny)); // Eq. 21
-    const R hp = h[a] - omega_phi * (h[a] - heq) + w * Qs;     // Eq. 19 (right side)
-
-    // destination s + c_a
-    int xd = x + cx, yd = y + cy;
-    bool bounce = false, drop = false;
-    if (yd < 0 || yd >= ny) {
-      if (bcy == BC_PERIODIC) yd = wrap1(yd, ny);
-      else bounce = true;
-    }
-    if (xd < 0 || xd >= nx) {
-      if (bcx == BC_PERIODIC) xd = wrap1(xd, nx);
-      else if (bcx == BC_WALL) bounce = true;
-      else drop = true;
-    }
-    if (bounce) {
-      // half-way bounce-back: comes back to this node reversed
-      const int b = D2_OPP[a];
-      if (FLOW) Pop<T>::st(df + b * P + idx, fp);
-      Pop<T>::st(dg + b * P + idx, gp);
-      Pop<T>::st(dh + b * P + idx, hp * inv_a2 - (inv_a2 - R(1)) * h[b]);
-    } else if (!drop) {
-      const long long jd = (long long)yd * px + xd;
-      const R hold = sh_h[a][ly + cy][lx + cx];  // h_a(s + c_a, t)
-      if (FLOW) Pop<T>::st(df + a * P + jd, fp);
-      Pop<T>::st(dg + a * P + jd, gp);
-      Pop<T>::st(dh + a * P + jd, hp * inv_a2 - (inv_a2 - R(1)) * hold);  // Eq. 19
-    }
-    if (bcx == BC_INOUT) {
-      if (cx == -1 && x == nx - 1) {
-        // outflow ghost x = nx repeats this column: its post-collision value
-        // arrives at (nx - 1, y + c_y)
-        int yo = y + cy;
-        bool ok = true;
-        if (yo < 0 || yo >= ny) {
-          if (bcy == BC_PERIODIC) yo = wrap1(yo, ny);
-          else ok = false;
-        }
-        if (ok) {
-          const long long jo = (long long)yo * px + x;
-          const R hold = sh_h[a][ly + cy][lx];
-          if (FLOW) Pop<T>::st(df + a * P + jo, fp);
-          Pop<T>::st(dg + a * P + jo, gp);
-          Pop<T>::st(dh + a * P + jo, hp * inv_a2 - (inv_a2 - R(1)) * hold);
+  for (int k = 0;; ++k) {
+    const int tile = first + k * G;
+    if (tile >= ntiles) break;
+    const int s = k % S;
+    const bool ok = mbar_wait_bounded(&full[s], uint32_t((k / S) & 1), kSpin);
+    if (__syncthreads_or(!ok)) {
+      // a tile never arrived: report, let the copies in flight land, stop
+      if (tid == 0) {
+        atomicOr(err, 2u);
+        for (int j = 1; j < S; ++j) {
+          const int kk = k + j;
+          if (first + kk * G < ntiles)
+            mbar_wait_bounded(&full[kk % S], uint32_t((kk / S) & 1), kSpin);
         }
       }
-      if (cx == 1 && x == 0) {
-        // inflow ghost x = -1: equilibrium at rho = 1, u = u_in e_x, U = U_in,
-        // phi = -1 (a_s = 1; its h deviation is 0), unless behind a wall
-        const int ys = y - cy;
-        if (!((ys < 0 || ys >= ny) && bcy == BC_WALL)) {
-          const R uin = R(m.u_in), cui = uin;
-          if (FLOW)
-            Pop<T>::st(df + a * P + idx,
-                       w * (R(3) * cui + R(4.5) * cui * cui - R(1.5) * uin * uin));
-          const R gu = FLOW ? cui : R(0);
-          const R Uin = R(m.U_in);
-          Pop<T>::st(dg + a * P + idx, w * ((Uin - R(m.ref_g)) + Uin * R(3) * gu));
-          Pop<T>::st(dh + a * P + idx, R(0));
-        }
+      __syncthreads();
+      return;
+    }
+    const int x0 = (tile % ntx) * TX, y0 = (tile / ntx) * TY;
+    unsigned char* st = smem + s * L::STAGE;
+    const T* fgs = reinterpret_cast<const T*>(st);
+    T* hsm = reinterpret_cast<T*>(st + L::OFF_H);
+    const float* rings = reinterpret_cast<const float*>(st + L::OFF_RING);
+    constexpr int HPLANE = SY * L::BXH;
+
+    if (x0 == 0 || y0 == 0 || x0 + TX >= nx || y0 + TY >= ny) {
+      // halo positions outside the domain: periodic wrap or nearest node
+      for (int i = tid; i < SX * SY; i += NT) {
+        const int lx = i % SX, ly = i / SX;
+        int gx = x0 + lx - 1, gy = y0 + ly - 1;
+        if (gx >= 0 && gx < nx && gy >= 0 && gy < ny) continue;
+        gx = grad_coord(gx, nx, m.bc[0]);
+        gy = grad_coord(gy, ny, m.bc[1]);
+        const int j = gy * px + gx;
+        const int P = int(m.plane);
+#pragma unroll
+        for (int a = 0; a < 9; ++a)
+          hsm[a * HPLANE + ly * L::BXH + lx + L::HX - 1] = src[(QF + 9 + a) * P + j];
       }
+      __syncthreads();
+    }
+    // phi + 1 of the halo-extended tile
+    for (int i = tid; i < SX * SY; i += NT) {
+      const int lx = i % SX, ly = i / SX;
+      const T* hp = hsm + ly * L::BXH + lx + L::HX - 1;
+      R sum = R(0);
+#pragma unroll
+      for (int a = 0; a < 9; ++a) sum += Pop<T>::template ld<R>(hp + a * HPLANE);
+      sh_phi[ly][lx] = sum;
+    }
+    __syncthreads();
+
+    const int x = x0 + tx, y = y0 + ty;
+    if (x < nx && y < ny) {
+      R f[9], g[9], h[9];
+      const int o = ty * TX + tx;
+#pragma unroll
+      for (int a = 0; a < 9; ++a) {
+        if (FLOW) f[a] = Pop<T>::template ld<R>(fgs + a * (TY * TX) + o);
+        g[a] = Pop<T>::template ld<R>(fgs + (QF + a) * (TY * TX) + o);
+        h[a] = Pop<T>::template ld<R>(hsm + a * HPLANE + (ty + 1) * L::BXH + tx + L::HX);
+      }
+      TileView<T, R, L::BXH, HPLANE, L::HX - 1> hs{hsm};
+      if (x0 >= 1 && x0 + TX <= nx - 1 && y0 >= 1 && y0 + TY <= ny - 1)
+        collide_push_2d<T, R, FLOW, true, SX>(m, x, y, tx + 1, ty + 1, f, g, h,
+                                              sh_phi[ty + 1][tx + 1], rings[o], &sh_phi[0][0], hs,
+                                              dst, ring_cur, err);
+      else
+        collide_push_2d<T, R, FLOW, false, SX>(m, x, y, tx + 1, ty + 1, f, g, h,
+                                               sh_phi[ty + 1][tx + 1], rings[o], &sh_phi[0][0],
+                                               hs, dst, ring_cur, err);
+    }
+    __syncthreads();  // stage s and sh_phi are free again
+    if (tid == 0 && tile + S * G < ntiles) {
+      fence_proxy_async_smem();
+      issue(tile + S * G, s);
     }
   }
 }
 
-template <typename T, typename R, bool FLOW>
-cudaError_t launch_t(const Model& m, const void* src, void* dst, const void* ring_prev,
-                     void* ring_cur, unsigned* err, cudaStream_t s) {
-  constexpr int TX = 32, TY = 8;
-  dim3 block(TX, TY);
-  dim3 grid((m.nx + TX - 1) / TX, (m.ny + TY - 1) / TY);
-  step2d_kernel<T, R, FLOW, TX, TY><<<grid, block, 0, s>>>(
-      m, static_cast<const T*>(src), static_cast<T*>(dst), static_cast<const R*>(ring_prev),
-      static_cast<R*>(ring_cur), err);
+// ---- host side: tensor maps and launches -------------------------------------------
+constexpr int kTX = 32, kTY = LBPF_2D_TY, kStages = LBPF_2D_STAGES;
+
+PFN_cuTensorMapEncodeTiled_v12000 encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+bool encode(CUtensorMap* map, CUtensorMapDataType dt, int rank, void* base, const uint64_t* dims,
+            const uint64_t* strides_bytes, const uint32_t* box) {
+  auto fn = encoder();
+  if (!fn) return false;
+  const uint32_t es[3] = {1, 1, 1};
+  return fn(map, dt, rank, base, dims, strides_bytes, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <typename T, bool FLOW>
+cudaError_t prepare_t(const Model& m, void* const pops[2], void* const rings[2], StepMaps* out) {
+  using L = Tiles2D<T, FLOW, kTX, kTY>;
+  const CUtensorMapDataType dt = sizeof(T) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                : (m.storage == ST_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                                                        : CU_TENSOR_MAP_DATA_TYPE_FLOAT16);
+  const uint64_t q = uint64_t(L::QFG + 9);
+  for (int b = 0; b < 2; ++b) {
+    const uint64_t dims3[3] = {uint64_t(m.nx), uint64_t(m.ny), q};
+    const uint64_t str3[2] = {uint64_t(m.px) * sizeof(T), uint64_t(m.plane) * sizeof(T)};
+    const uint32_t box_fg[3] = {kTX, kTY, uint32_t(L::QFG)};
+    const uint32_t box_h[3] = {uint32_t(L::BXH), kTY + 2, 9};
+    const uint64_t dims2[2] = {uint64_t(m.nx), uint64_t(m.ny)};
+    const uint64_t str2[1] = {uint64_t(m.px) * 4};
+    const uint32_t box_r[2] = {kTX, kTY};
+    if (!encode(&out->fg[b], dt, 3, pops[b], dims3, str3, box_fg) ||
+        !encode(&out->h[b], dt, 3, pops[b], dims3, str3, box_h) ||
+        !encode(&out->ring[b], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, rings[b], dims2, str2, box_r))
+      return cudaErrorInvalidValue;
+  }
+  auto kern = step2d_tma_kernel<T, FLOW, kTX, kTY, kStages>;
+  const int smem = kStages * L::STAGE + 128;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 0, per_sm = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+    return e;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kTX * kTY, smem)) !=
+      cudaSuccess)
+    return e;
+  out->ctas = sms * (per_sm > 0 ? per_sm : 1);
+  out->smem = smem;
+  out->ready = 1;
+  return cudaSuccess;
+}
+
+template <typename T, bool FLOW>
+cudaError_t launch_tma_t(const Model& m, const StepMaps& maps, int c, const void* src, void* dst,
+                         void* ring_cur, unsigned* err, cudaStream_t s) {
+  const int ntx = (m.nx + kTX - 1) / kTX, nty = (m.ny + kTY - 1) / kTY;
+  const int ntiles = ntx * nty;
+  const int grid = ntiles < maps.ctas ? ntiles : maps.ctas;
+  step2d_tma_kernel<T, FLOW, kTX, kTY, kStages><<<grid, kTX * kTY, maps.smem, s>>>(
+      maps.fg[c], maps.h[c], maps.ring[c], m, static_cast<const T*>(src), static_cast<T*>(dst),
+      static_cast<float*>(ring_cur), err, ntx, ntiles);
   return cudaGetLastError();
 }
 
-template <typename T, typename R>
-cudaError_t launch_flow(const Model& m, const void* src, void* dst, const void* pp, void* pc,
-                        unsigned* err, cudaStream_t s) {
-  return m.flow ? launch_t<T, R, true>(m, src, dst, pp, pc, err, s)
-                : launch_t<T, R, false>(m, src, dst, pp, pc, err, s);
+template <typename T, typename R, bool FLOW>
+cudaError_t launch_plain_t(const Model& m, const void* src, void* dst, const void* ring_prev,
+                           void* ring_cur, unsigned* err, cudaStream_t s) {
+  dim3 block(kTX, kTY);
+  dim3 grid((m.nx + kTX - 1) / kTX, (m.ny + kTY - 1) / kTY);
+  step2d_kernel<T, R, FLOW, kTX, kTY><<<grid, block, 0, s>>>(
+      m, pop_ptrs(m, const_cast<void*>(src), sizeof(T)), pop_ptrs(m, dst, sizeof(T)),
+      static_cast<const R*>(ring_prev), static_cast<R*>(ring_cur), err);
+  return cudaGetLastError();
 }
 
 }  // namespace
 
-cudaError_t launch_step2d(const Model& m, const void* src, void* dst, const void* ring_prev,
-                          void* ring_cur, unsigned* err, cudaStream_t s) {
+cudaError_t prepare_step2d(const Model& m, void* const pops[2], void* const rings[2],
+                           StepMaps* out) {
+  out->ready = 0;
+  if (m.storage == ST_FP64) return cudaSuccess;  // one-tile kernel, no maps
   switch (m.storage) {
-    case ST_FP64: return launch_flow<double, double>(m, src, dst, ring_prev, ring_cur, err, s);
-    case ST_FP16: return launch_flow<__half, float>(m, src, dst, ring_prev, ring_cur, err, s);
-    case ST_BF16: return launch_flow<__nv_bfloat16, float>(m, src, dst, ring_prev, ring_cur, err, s);
-    default: return launch_flow<float, float>(m, src, dst, ring_prev, ring_cur, err, s);
+    case ST_FP16:
+      return m.flow ? prepare_t<__half, true>(m, pops, rings, out)
+                    : prepare_t<__half, false>(m, pops, rings, out);
+    case ST_BF16:
+      return m.flow ? prepare_t<__nv_bfloat16, true>(m, pops, rings, out)
+                    : prepare_t<__nv_bfloat16, false>(m, pops, rings, out);
+    default:
+      return m.flow ? prepare_t<float, true>(m, pops, rings, out)
+                    : prepare_t<float, false>(m, pops, rings, out);
+  }
+}
+
+cudaError_t launch_step2d(const Model& m, const StepMaps& maps, int c, const void* src, void* dst,
+                          const void* ring_prev, void* ring_cur, unsigned* err, cudaStream_t s) {
+  if (m.storage == ST_FP64)
+    return m.flow ? launch_plain_t<double, double, true>(m, src, dst, ring_prev, ring_cur, err, s)
+                  : launch_plain_t<double, double, false>(m, src, dst, ring_prev, ring_cur, err, s);
+  if (!maps.ready) return cudaErrorNotReady;
+  switch (m.storage) {
+    case ST_FP16:
+      return m.flow ? launch_tma_t<__half, true>(m, maps, c, src, dst, ring_cur, err, s)
+                    : launch_tma_t<__half, false>(m, maps, c, src, dst, ring_cur, err, s);
+    case ST_BF16:
+      return m.flow ? launch_tma_t<__nv_bfloat16, true>(m, maps, c, src, dst, ring_cur, err, s)
+                    : launch_tma_t<__nv_bfloat16, false>(m, maps, c, src, dst, ring_cur, err, s);
+    default:
+      return m.flow ? launch_tma_t<float, true>(m, maps, c, src, dst, ring_cur, err, s)
+                    : launch_tma_t<float, false>(m, maps, c, src, dst, ring_cur, err, s);
   }
 }
 

@@ -1,0 +1,200 @@
+// Per-node part of the 2D coupled step, shared by the step kernels: moments,
+// anisotropy, collisions of f, g and h, and the push of every direction to
+// its destination (Eqs. 3-23).  The caller has the node's own population
+// deviations in registers and the tile's phi + 1 and h deviations (with a
+// one-node halo) in shared memory.
+#pragma once
+
+#include "lbpf_device.cuh"
+
+namespace lbk {
+
+// Shared-memory view of the halo-extended tile: value of lattice direction a
+// at local position (lx, ly) (lx, ly in [0, TX + 1] x [0, TY + 1]).  The
+// shape is compile-time, so every access is one load with an immediate
+// offset from a per-thread base.
+template <typename T, typename R, int ROW, int PLANE, int XOFF>
+struct TileView {
+  const T* base;
+  __device__ __forceinline__ R at(int a, int ly, int lx) const {
+    return Pop<T>::template ld<R>(base + a * PLANE + ly * ROW + lx + XOFF);
+  }
+};
+
+// dphi_prev: phi(t-1) + 1 of this node; ring_cur: where phi(t) + 1 goes.
+// phi_s: the tile's phi + 1 with halo ([ly][lx], row pitch PROW).
+// dst: the destination population buffer (array a at dst + a * plane).
+// INTERIOR: the caller guarantees 1 <= x <= nx - 2 and 1 <= y <= ny - 2 for
+// every node of the tile, so every destination is an ordinary node (no wrap,
+// wall or ghost) and the push needs no boundary logic.
+template <typename T, typename R, bool FLOW, bool INTERIOR, int PROW, typename HV>
+__device__ __forceinline__ void collide_push_2d(const Model& m, int x, int y, int lx, int ly,
+                                                const R (&f)[9], const R (&g)[9],
+                                                const R (&h)[9], R dphi, R dphi_prev,
+                                                const R* phi_s, const HV& hs,
+                                                T* __restrict__ dst, R* __restrict__ ring_cur,
+                                                unsigned* __restrict__ err) {
+  constexpr int QF = FLOW ? 9 : 0;
+  const int nx = m.nx, ny = m.ny, px = m.px;
+  const int P = int(m.plane);  // fits: checked at creation
+  const int idx = y * px + x;
+  T* const pd = dst + idx;  // this node in array 0; the offsets below are uniform
+  const Coef<R>& c = coef<R>(m);
+
+  // ---- local moments (Eqs. 11, 12, 17, 22) ----------------------------------
+  const R phi = dphi - R(1);
+  R dU = R(0);
+#pragma unroll
+  for (int a = 0; a < 9; ++a) dU += g[a];
+  const R U = c.ref_g + dU;
+  R drho = R(0), mx = R(0), my = R(0);
+  if (FLOW) {
+#pragma unroll
+    for (int a = 0; a < 9; ++a) drho += f[a];
+    mx = (f[1] - f[3]) + (f[5] - f[6]) + (f[8] - f[7]);
+    my = (f[2] - f[4]) + (f[5] + f[6]) - (f[7] + f[8]);
+  }
+  const R rho = R(1) + drho;
+  const R ph = clamp1(phi);
+  const R mask = R(0.5) * (R(1) - ph);  // (1 - phi)/2 of Eq. 7 and q(phi) of Eq. 18
+  R ux = R(0), uy = R(0), Fx = R(0), Fy = R(0);
+  if (FLOW) {
+    // Eq. 6: F = b - K u, K = h tau_f (1+phi)^2 (1-phi) / (4 W0^2); the Guo
+    // half-force velocity u = (m + F/2)/rho solved in closed form.
+    const R K = c.kdrag * (R(1) + ph) * (R(1) + ph) * (R(1) - ph);
+    const R inv = R(1) / (rho + R(0.5) * K);
+    ux = (mx + R(0.5) * c.body[0]) * inv;
+    uy = (my + R(0.5) * c.body[1]) * inv;
+    Fx = c.body[0] - K * ux;
+    Fy = c.body[1] - K * uy;
+  }
+  const R usx = mask * ux, usy = mask * uy;  // u* (Eq. 7)
+  const R omega_U = R(1) / (R(0.5) + c.tauU_slope * mask);  // Eq. 18
+  const R dphidt = dphi - dphi_prev;
+  ring_cur[idx] = dphi;
+  if (!(finite_r(phi) && finite_r(U) && finite_r(rho))) atomicOr(err, 1u);
+
+  // ---- gradient, anisotropy, phase-field coefficients (Eqs. 3, 20, 21, 23) --
+  const R* pc = phi_s + ly * PROW + lx;
+  const R pE = pc[1], pW = pc[-1], pN = pc[PROW], pS = pc[-PROW];
+  const R pNE = pc[PROW + 1], pNW = pc[PROW - 1], pSE = pc[-PROW + 1], pSW = pc[-PROW - 1];
+  // grad = 3 sum_a w_a c_a phi(x + c_a) over D2Q9
+  const R gxv = R(1.0 / 3.0) * (pE - pW) + R(1.0 / 12.0) * ((pNE + pSE) - (pNW + pSW));
+  const R gyv = R(1.0 / 3.0) * (pN - pS) + R(1.0 / 12.0) * ((pNE + pNW) - (pSE + pSW));
+  R as, Nx, Ny, Nz;
+  aniso<R>(m, gxv, gyv, R(0), as, Nx, Ny, Nz);
+  const R a2 = as * as;
+  const R inv_a2 = R(1) / a2;
+  const R omega_phi = R(1) / (a2 * c.tpc + R(0.5));  // Eq. 23
+  const R phi2m = R(1) - phi * phi;
+  const R Qs = (phi - phi * phi * phi + c.lambda * U * phi2m * phi2m) * c.inv_tau0;  // Eq. 20
+  // Node constants of the collisions, so that each direction costs a few FMAs:
+  //   f*: (1 - w_f) d + w_f w [E0 + cu (E1 + E2 cu)] + guo w [cF (3 + 9 cu) - 3 u*.F]
+  //       (Eq. 4, 5, 8, 9 with c_s^2 = 1/3, d = f - w)
+  //   g*: (1 - w_U) d + w (K0 + K1 cu)            (Eqs. 13-16, d = g - w U_ref)
+  //   h*: (1 - w_phi) d + w (H0 - c.H)            (Eqs. 19-21, d = h + w)
+  const R uu = usx * usx + usy * usy, uF = usx * Fx + usy * Fy;
+  const R omega_f = c.omega_f, keep_f = R(1) - c.omega_f, guo = c.guo;
+  const R E0 = omega_f * (drho - R(1.5) * rho * uu);
+  const R E1 = omega_f * R(3) * rho, E2 = omega_f * R(4.5) * rho;
+  const R G0 = -R(3) * uF;
+  const R keep_U = R(1) - omega_U;
+  const R K0 = omega_U * dU - dphidt, K1 = R(3) * omega_U * U;
+  const R keep_phi = R(1) - omega_phi;
+  const R H0 = omega_phi * dphi + Qs;
+  const R Hx = omega_phi * c.tpc * Nx, Hy = omega_phi * c.tpc * Ny;
+  const R keep_old = R(1) - inv_a2;  // Eq. 19: h_new = h* / a_s^2 + (1 - 1/a_s^2) h_old
+
+  // array of direction a: f at a * P, g at (QF + a) * P, h at (QF + 9 + a) * P
+#define LBPF_DF(a) (dst + (a) * P)
+#define LBPF_DG(a) (dst + (QF + (a)) * P)
+#define LBPF_DH(a) (dst + (QF + 9 + (a)) * P)
+  const int bcx = m.bc[0], bcy = m.bc[1];
+
+#pragma unroll
+  for (int a = 0; a < 9; ++a) {
+    const int cx = D2_CX[a], cy = D2_CY[a];
+    const R w = d2_w<R>(a);
+    const R cu = R(cx) * usx + R(cy) * usy;
+    // post-collision deviations at this node
+    R fp = R(0);
+    if (FLOW) {
+      const R cF = R(cx) * Fx + R(cy) * Fy;
+      fp = keep_f * f[a] + w * ((E0 + cu * (E1 + E2 * cu)) + guo * (cF * (R(3) + R(9) * cu) + G0));
+    }
+    const R gp = keep_U * g[a] + w * (K0 + K1 * cu);
+    const R hp = keep_phi * h[a] + w * (H0 - (R(cx) * Hx + R(cy) * Hy));
+    if (INTERIOR) {
+      const int off = cy * px + cx;  // uniform
+      const R hold = hs.at(a, ly + cy, lx + cx);  // h_a(s + c_a, t)
+      if (FLOW) Pop<T>::st(pd + (a * P + off), fp);
+      Pop<T>::st(pd + ((QF + a) * P + off), gp);
+      Pop<T>::st(pd + ((QF + 9 + a) * P + off), inv_a2 * hp + keep_old * hold);  // Eq. 19
+      continue;
+    }
+    // destination s + c_a
+    int xd = x + cx, yd = y + cy;
+    bool bounce = false, drop = false;
+    if (yd < 0 || yd >= ny) {
+      if (bcy == BC_PERIODIC) yd = wrap1(yd, ny);
+      else bounce = true;
+    }
+    if (xd < 0 || xd >= nx) {
+      if (bcx == BC_PERIODIC) xd = wrap1(xd, nx);
+      else if (bcx == BC_WALL) bounce = true;
+      else drop = true;
+    }
+    if (bounce) {
+      // half-way bounce-back: comes back to this node reversed
+      const int b = D2_OPP[a];
+      if (FLOW) Pop<T>::st(LBPF_DF(b) + idx, fp);
+      Pop<T>::st(LBPF_DG(b) + idx, gp);
+      Pop<T>::st(LBPF_DH(b) + idx, inv_a2 * hp + keep_old * h[b]);
+    } else if (!drop) {
+      const int jd = yd * px + xd;
+      const R hold = hs.at(a, ly + cy, lx + cx);  // h_a(s + c_a, t)
+      if (FLOW) Pop<T>::st(LBPF_DF(a) + jd, fp);
+      Pop<T>::st(LBPF_DG(a) + jd, gp);
+      Pop<T>::st(LBPF_DH(a) + jd, inv_a2 * hp + keep_old * hold);  // Eq. 19
+    }
+    if (bcx == BC_INOUT) {
+      if (cx == -1 && x == nx - 1) {
+        // outflow ghost x = nx repeats this column: its post-collision value
+        // arrives at (nx - 1, y + c_y)
+        int yo = y + cy;
+        bool ok = true;
+        if (yo < 0 || yo >= ny) {
+          if (bcy == BC_PERIODIC) yo = wrap1(yo, ny);
+          else ok = false;
+        }
+        if (ok) {
+          const int jo = yo * px + x;
+          const R hold = hs.at(a, ly + cy, lx);
+          if (FLOW) Pop<T>::st(LBPF_DF(a) + jo, fp);
+          Pop<T>::st(LBPF_DG(a) + jo, gp);
+          Pop<T>::st(LBPF_DH(a) + jo, inv_a2 * hp + keep_old * hold);
+        }
+      }
+      if (cx == 1 && x == 0) {
+        // inflow ghost x = -1: equilibrium at rho = 1, u = u_in e_x, U = U_in,
+        // phi = -1 (a_s = 1; its h deviation is 0), unless behind a wall
+        const int ys = y - cy;
+        if (!((ys < 0 || ys >= ny) && bcy == BC_WALL)) {
+          const R uin = c.u_in, cui = uin;
+          if (FLOW)
+            Pop<T>::st(LBPF_DF(a) + idx,
+                       w * (R(3) * cui + R(4.5) * cui * cui - R(1.5) * uin * uin));
+          const R gu = FLOW ? cui : R(0);
+          const R Uin = c.U_in;
+          Pop<T>::st(LBPF_DG(a) + idx, w * ((Uin - c.ref_g) + Uin * R(3) * gu));
+          Pop<T>::st(LBPF_DH(a) + idx, R(0));
+        }
+      }
+    }
+  }
+#undef LBPF_DF
+#undef LBPF_DG
+#undef LBPF_DH
+}
+
+}  // namespace lbk

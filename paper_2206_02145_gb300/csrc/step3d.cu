@@ -31,6 +31,7 @@ __global__ void __launch_bounds__(TX* TY* TZ)
   const bool active = x < nx && y < ny && z < nz;
   const long long idx = z * rowz + (long long)y * px + x;
 
+  const Coef<R>& c = coef<R>(m);
   const T* sf = src;
   const T* sg = src + (long long)QF * P;
   const T* shp = src + (long long)(QF + 7) * P;
@@ -81,7 +82,7 @@ __global__ void __launch_bounds__(TX* TY* TZ)
   R dU = R(0);
 #pragma unroll
   for (int a = 0; a < 7; ++a) dU += g[a];
-  const R U = R(m.ref_g) + dU;
+  const R U = c.ref_g + dU;
   R drho = R(0), mo[3] = {R(0), R(0), R(0)};
   if (FLOW) {
 #pragma unroll
@@ -97,16 +98,16 @@ __global__ void __launch_bounds__(TX* TY* TZ)
   const R mask = R(0.5) * (R(1) - ph);
   R u[3] = {R(0), R(0), R(0)}, F[3] = {R(0), R(0), R(0)};
   if (FLOW) {
-    const R K = R(m.kdrag) * (R(1) + ph) * (R(1) + ph) * (R(1) - ph);  // Eq. 6
+    const R K = c.kdrag * (R(1) + ph) * (R(1) + ph) * (R(1) - ph);  // Eq. 6
     const R inv = R(1) / (rho + R(0.5) * K);
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
-      u[d] = (mo[d] + R(0.5) * R(m.body[d])) * inv;
-      F[d] = R(m.body[d]) - K * u[d];
+      u[d] = (mo[d] + R(0.5) * c.body[d]) * inv;
+      F[d] = c.body[d] - K * u[d];
     }
   }
   const R us[3] = {mask * u[0], mask * u[1], mask * u[2]};  // Eq. 7
-  const R omega_U = R(1) / (R(0.5) + R(m.tauU_slope) * mask);  // Eq. 18
+  const R omega_U = R(1) / (R(0.5) + c.tauU_slope * mask);  // Eq. 18
   const R dphidt = dphi - ring_prev[idx];
   ring_cur[idx] = dphi;
   if (!(finite_r(phi) && finite_r(U) && finite_r(rho))) atomicOr(err, 1u);
@@ -125,10 +126,10 @@ __global__ void __launch_bounds__(TX* TY* TZ)
   aniso<R>(m, gr[0], gr[1], gr[2], as, N[0], N[1], N[2]);
   const R a2 = as * as;
   const R inv_a2 = R(1) / a2;
-  const R omega_phi = R(1) / (a2 * R(m.tpc) + R(0.5));  // Eq. 23
+  const R omega_phi = R(1) / (a2 * c.tpc + R(0.5));  // Eq. 23
   const R phi2m = R(1) - phi * phi;
-  const R Qs = (phi - phi * phi * phi + R(m.lambda) * U * phi2m * phi2m) * R(m.inv_tau0);
-  const R tpc = R(m.tpc);
+  const R Qs = (phi - phi * phi * phi + c.lambda * U * phi2m * phi2m) * c.inv_tau0;
+  const R tpc = c.tpc;
   const R uu = us[0] * us[0] + us[1] * us[1] + us[2] * us[2];
   const R uF = us[0] * F[0] + us[1] * F[1] + us[2] * F[2];
 
@@ -147,8 +148,8 @@ __global__ void __launch_bounds__(TX* TY* TZ)
     if (FLOW) {
       const R cF = R(cx) * F[0] + R(cy) * F[1] + R(cz) * F[2];
       const R feq = wf * (drho + rho * (R(3) * cu + R(4.5) * cu * cu - R(1.5) * uu));  // Eq. 9
-      const R G = wf * R(m.guo) * (R(3) * cF + R(9) * cu * cF - R(3) * uF);           // Eq. 5
-      fp = f[a] - R(m.omega_f) * (f[a] - feq) + G;
+      const R G = wf * c.guo * (R(3) * cF + R(9) * cu * cF - R(3) * uF);           // Eq. 5
+      fp = f[a] - c.omega_f * (f[a] - feq) + G;
     }
     const bool sc = a < 7;  // direction of the D3Q7 lattices too
     const R ws = d3q7_w<R>(a);
@@ -215,14 +216,14 @@ __global__ void __launch_bounds__(TX* TY* TZ)
         const bool behind_wall = ((ys < 0 || ys >= ny) && bcy == BC_WALL) ||
                                  ((zs < 0 || zs >= nz) && bcz == BC_WALL);
         if (!behind_wall) {
-          const R uin = R(m.u_in), cui = uin;
+          const R uin = c.u_in, cui = uin;
           if (FLOW)
             Pop<T>::st(df + a * P + idx,
                        wf * (R(3) * cui + R(4.5) * cui * cui - R(1.5) * uin * uin));
           if (sc) {
             const R gu = FLOW ? cui : R(0);
-            const R Uin = R(m.U_in);
-            Pop<T>::st(dg + a * P + idx, ws * ((Uin - R(m.ref_g)) + Uin * R(4) * gu));
+            const R Uin = c.U_in;
+            Pop<T>::st(dg + a * P + idx, ws * ((Uin - c.ref_g) + Uin * R(4) * gu));
             Pop<T>::st(dh + a * P + idx, R(0));  // phi = -1: zero deviation
           }
         }
