@@ -160,10 +160,12 @@ __global__ void fields_kernel(const Model m, const T* pops, const R* phi_prev, u
     const long long j = pitched(m, x, y, z);
     R phi, U, rho, u[3];
     node_moments<T, R>(m, pops, j, phi, U, rho, u);
-    const R vals[7] = {phi, U, rho, u[0], u[1], u[2], coef<R>(m).ref_h + phi_prev[j]};
+    // phi(t-1) = -1 + ring, formed in the output precision
+    const O vals[7] = {O(phi), O(U), O(rho), O(u[0]), O(u[1]), O(u[2]),
+                       O(m.ref_h) + O(phi_prev[j])};
     int slot = 0;
     for (int b = 0; b < 7; ++b)
-      if (mask & (1u << b)) out[(long long)(slot++) * n + i] = O(vals[b]);
+      if (mask & (1u << b)) out[(long long)(slot++) * n + i] = vals[b];
   }
 }
 
