@@ -197,6 +197,38 @@ const char* lbpf_last_error(const lbpf_t* h);
 /* Release everything the handle owns; NULL is a no-op. */
 void lbpf_destroy(lbpf_t* h);
 
+/* ---- allocation-free reduction ------------------------------------------------
+ * The paper has no counterpart of this entry point; it serves callers that
+ * cannot allocate device memory where they need the conservation sums: code
+ * running inside a memory-pool or allocator callback, a host whose own arena
+ * owns all of the GPU's memory, or a real-time loop in which a cudaMalloc would
+ * stall.  It computes the three FP64 sums of lbpf_diagnostics from fields the
+ * caller already holds on the device, and allocates nothing: its only scratch
+ * (the per-block partial sums of a deterministic two-pass reduction) is a
+ * fixed file-scope device array of LBPF_NOALLOC_MAX_BLOCKS x 3 doubles
+ * (96 KiB), which every GPU that loads the library holds until the process
+ * exits.
+ *
+ * phi, phi_prev, U, rho: device arrays of n values each, float (fp64 = 0) or
+ * double (fp64 = 1), caller-owned; rho may be NULL (taken as 1).
+ * out: device pointer to 3 doubles, caller-owned, written with
+ *   out[0] = sum(U + phi_prev)   (lbpf_diag.solute_total),
+ *   out[1] = sum(rho)            (lbpf_diag.mass_total),
+ *   out[2] = sum((1 + clamp(phi, -1, 1)) / 2)   (lbpf_diag.solid_volume).
+ * n above LBPF_NOALLOC_MAX_NODES returns LBPF_EINVAL (the scratch holds one
+ * row per block, and a block covers at most 256 x 64 nodes); a NULL input or
+ * output, or n < 0, also returns LBPF_EINVAL.  Work is queued on `stream`
+ * (NULL = legacy default stream) and the call returns without waiting.
+ * The first call on a device looks up the device address of the scratch
+ * array (with that device current): make that first call before any stream
+ * capture.  Every call shares the one scratch array; calls that can overlap
+ * on the GPU (different streams without ordering) race on it and must be
+ * serialised by the caller. */
+#define LBPF_NOALLOC_MAX_BLOCKS 4096
+#define LBPF_NOALLOC_MAX_NODES ((int64_t)LBPF_NOALLOC_MAX_BLOCKS * 256 * 64)
+int lbpf_field_sums_noalloc(const void* phi, const void* phi_prev, const void* U,
+                            const void* rho, int64_t n, int fp64, double* out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

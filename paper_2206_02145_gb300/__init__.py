@@ -25,6 +25,8 @@ FP32, FP64, FP16_SHIFTED, BF16_SHIFTED = 0, 1, 2, 3
 FIELD_PHI, FIELD_U, FIELD_RHO, FIELD_UX, FIELD_UY, FIELD_UZ, FIELD_PHI_PREV = (
     1, 2, 4, 8, 16, 32, 64)
 FIELD_STATE = 256
+NOALLOC_MAX_BLOCKS = 4096
+NOALLOC_MAX_NODES = NOALLOC_MAX_BLOCKS * 256 * 64
 FIELD_NAMES = ("phi", "U", "rho", "ux", "uy", "uz", "phi_prev")
 _STATUS = {OK: "OK", EINVAL: "EINVAL", ECUDA: "ECUDA", ENOMEM: "ENOMEM", ESTATE: "ESTATE",
            ENONFINITE: "ENONFINITE", ETIMEDOUT: "ETIMEDOUT"}
@@ -66,7 +68,7 @@ class lbpf_diag(ctypes.Structure):
 EXPORTED = ("lbpf_params_default", "lbpf_create", "lbpf_init_seed", "lbpf_init_fields",
             "lbpf_step", "lbpf_read_fields", "lbpf_state_bytes", "lbpf_write_state",
             "lbpf_diagnostics", "lbpf_set_stream", "lbpf_device_bytes", "lbpf_last_error",
-            "lbpf_destroy")
+            "lbpf_destroy", "lbpf_field_sums_noalloc")
 
 
 def _load_library():
@@ -94,6 +96,7 @@ def _load_library():
     lib.lbpf_last_error.restype = ctypes.c_char_p
     lib.lbpf_destroy.argtypes = [vp]
     lib.lbpf_destroy.restype = None
+    lib.lbpf_field_sums_noalloc.argtypes = [vp, vp, vp, vp, ctypes.c_int64, ctypes.c_int, vp, vp]
     for name in EXPORTED:
         getattr(lib, name).restype = getattr(lib, name).restype if name in (
             "lbpf_state_bytes", "lbpf_device_bytes", "lbpf_last_error", "lbpf_destroy") \
@@ -191,6 +194,14 @@ def lbpf_last_error(h: int) -> str:
 
 def lbpf_destroy(h: int) -> None:
     _lib.lbpf_destroy(h)
+
+
+def lbpf_field_sums_noalloc(phi_ptr, phi_prev_ptr, U_ptr, rho_ptr, n: int, fp64: int, out_ptr,
+                            stream=None) -> int:
+    """FP64 sums of caller-owned device fields without any device allocation
+    (for callers that cannot allocate); returns the lbpf status code."""
+    return int(_lib.lbpf_field_sums_noalloc(phi_ptr, phi_prev_ptr, U_ptr, rho_ptr, int(n),
+                                            int(fp64), out_ptr, stream))
 
 
 # ---- convenience wrapper -------------------------------------------------------------
