@@ -52,7 +52,33 @@ WORKLOADS = {
                sample=dict(nx=48, ny=48, nz=48, seed=(24.0, 24.0, 24.0, 12.0, 0.3, 0.01, 1))),
     "c3_fp16": dict(base="c3", storage="fp16"),
     "c3_bf16": dict(base="c3", storage="bf16"),
+    "c4": dict(desc="batched sweep: 64 2D coupled instances in one persistent launch per step "
+                    "(sides U{256..768}, U0~U[0.1,0.6], R~U[4,24], u_in~U[0,0.02], fold 4 or 5, "
+                    "eps~U[0.02,0.06]; seed 4), FP16 shifted storage",
+               dim=2, nx=512, ny=512, nz=1, flow=1, fold=5, eps=0.04, bc=(1, 0, 0), u_in=0.01,
+               U_in=0.35, storage="fp16", kernel="step2d_batch_kernel", src="batch2d.cu",
+               batch=64, sweep_seed=4,
+               sample=dict(nx=256, ny=256, seed=(77.0, 128.0, 0.0, 12.0, 0.35, 0.01, 1))),
 }
+
+
+def sweep_members(count: int, seed: int):
+    """Seeded uneven parametric sweep (the synthetic stand-in for the paper's
+    supersaturation x seed-size x inflow studies): square sides U{256..768},
+    U0 ~ U[0.1, 0.6], seed radius ~ U[4, 24], inflow ~ U[0, 0.02], fold 4 or 5,
+    anisotropy ~ U[0.02, 0.06]; seed at (0.3 n, 0.5 n)."""
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    params, seeds = [], []
+    for i in range(count):
+        n = int(rng.integers(256, 769))
+        u0 = float(rng.uniform(0.1, 0.6))
+        r = float(rng.uniform(4, 24))
+        params.append(dict(dim=2, nx=n, ny=n, flow=1, fold=int(rng.choice([4, 5])),
+                           eps_aniso=float(rng.uniform(0.02, 0.06)), bc=(1, 0, 0),
+                           u_inlet=float(rng.uniform(0.0, 0.02)), u0_inlet=u0))
+        seeds.append((0.3 * n, 0.5 * n, 0.0, r, u0, 0.01, 1000 + i))
+    return params, seeds
 ELEM = {"fp32": 4, "fp64": 8, "fp16": 2, "bf16": 2}
 
 
@@ -67,6 +93,10 @@ def workload(name):
     ring = 8 if w["storage"] == "fp64" else 4
     w["bytes_per_lup"] = 2 * q * ELEM[w["storage"]] + 2 * ring
     w["nodes"] = w["nx"] * w["ny"] * w["nz"]
+    if w.get("batch"):
+        params, seeds = sweep_members(w["batch"], w["sweep_seed"])
+        w["members"] = (params, seeds)
+        w["nodes"] = sum(p["nx"] * p["ny"] for p in params)
     return w
 
 
@@ -252,11 +282,21 @@ def main():
 
     import paper_2206_02145_gb300 as L
     stream = torch.cuda.current_stream()
-    sim = L.Sim(stream=stream.cuda_stream, **lib_params(w, L))
-    sim.init_seed(*w["seed"])
+    batch = None
+    if w.get("batch"):
+        params, seeds = w["members"]
+        st = lib_params(w, L)["storage"]
+        batch = L.Batch([dict(p, storage=st) for p in params], seeds, stream.cuda_stream)
+        sims = [batch.instance(i) for i in range(batch.count)]
+        stepper = batch
+    else:
+        sim = L.Sim(stream=stream.cuda_stream, **lib_params(w, L))
+        sim.init_seed(*w["seed"])
+        sims = [sim]
+        stepper = sim
 
-    # warm-up (also builds the step graph)
-    sim.step(args.warmup)
+    # warm-up (also builds the step graph; a batch tunes its tile shape here)
+    stepper.step(args.warmup)
     torch.cuda.synchronize()
 
     # --- device-resident timed region: K steps, inputs already in HBM ----------
@@ -265,7 +305,7 @@ def main():
         barrier()
         torch.cuda.synchronize()
         ev0.record(stream)
-        sim.step(args.steps)
+        stepper.step(args.steps)
         ev1.record(stream)
         torch.cuda.synchronize()
         barrier()
@@ -276,33 +316,58 @@ def main():
     ms_max = float(t.item())
     per_step_ms = ms_max / args.steps
     value = w["nodes"] * world * args.steps / (ms_max * 1e-3) / 1e6
-    d = sim.diagnostics()  # also surfaces any sticky device error
+    diags = [s.diagnostics() for s in sims]  # also surfaces any sticky device error
+    d = diags[0]
+
+    batch_info = None
+    if batch is not None:
+        # the same instances stepped one after another (each its own graph),
+        # against the single batched launch per step
+        kseq = max(64, min(args.steps, 640) // 64 * 64)
+        for s_ in sims:
+            s_.step(64)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for s_ in sims:
+            s_.step(kseq)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        seq_ms = ev0.elapsed_time(ev1) / kseq
+        batch_info = {"instances": batch.count, "tuning": batch.tuning(),
+                      "sequential_ms_per_step": seq_ms,
+                      "speedup_vs_sequential": seq_ms / per_step_ms}
 
     # --- end to end through the C ABI with host buffers -------------------------
     # every step: H2D of the full state from pinned memory (lbpf_write_state),
-    # one coupled step, D2H of phi and U (lbpf_read_fields)
-    state = sim.state()
-    host_state = torch.from_numpy(state).pin_memory()
+    # one coupled step, D2H of phi and U (lbpf_read_fields); for a batch, of
+    # every instance
+    host_states = [torch.from_numpy(s_.state()).pin_memory() for s_ in sims]
     nf = 2
-    host_out = torch.empty(nf * w["nodes"], dtype=torch.float32).pin_memory()
+    host_outs = [torch.empty(nf * s_.nodes, dtype=torch.float32).pin_memory() for s_ in sims]
     mask = L.FIELD_PHI | L.FIELD_U
+
+    def e2e_step():
+        for s_, hs_ in zip(sims, host_states):
+            L.lbpf_write_state(s_.h, hs_.data_ptr(), hs_.numel())
+        stepper.step(1)
+        for s_, ho_ in zip(sims, host_outs):
+            L.lbpf_read_fields(s_.h, mask, ho_.data_ptr(), ho_.numel() * 4, 0)
+
     for _ in range(3):
-        L.lbpf_write_state(sim.h, host_state.data_ptr(), host_state.numel())
-        sim.step(1)
-        L.lbpf_read_fields(sim.h, mask, host_out.data_ptr(), host_out.numel() * 4, 0)
+        e2e_step()
     barrier()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(args.e2e_steps):
-        L.lbpf_write_state(sim.h, host_state.data_ptr(), host_state.numel())
-        sim.step(1)
-        L.lbpf_read_fields(sim.h, mask, host_out.data_ptr(), host_out.numel() * 4, 0)
+        e2e_step()
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
     te = torch.tensor([e2e_s], device="cuda")
     if dist is not None:
         dist.all_reduce(te, op=dist.ReduceOp.MAX)
     e2e_value = w["nodes"] * world * args.e2e_steps / float(te.item()) / 1e6
+    h2d = sum(int(x.numel()) for x in host_states)
+    d2h = sum(int(x.numel()) * 4 for x in host_outs)
 
     peak, peak_kind = measured_peaks()
     achieved = w["bytes_per_lup"] * w["nodes"] / (per_step_ms * 1e-3) / 1e9
@@ -336,15 +401,18 @@ def main():
                          "algorithmic_bytes_per_launch": w["bytes_per_lup"] * w["nodes"]},
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": "MLUPS",
-                    "h2d_bytes_per_step": int(host_state.numel()),
-                    "d2h_bytes_per_step": int(host_out.numel() * 4)},
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": args.steps,
             "clocks": clk.summary(),
             "diag": {"step": d["step"], "solute_drift_rel": d["solute_drift_rel"],
                      "r_eq": d["r_eq"]},
         }
+        if batch_info is not None:
+            out["config"]["batch"] = batch_info
+            out["config"]["grid"] = "64 square grids, sides 256..768"
         print(json.dumps(out), flush=True)
-    sim.close()
+    del sims
+    stepper.close()
     if dist is not None:
         dist.destroy_process_group()
 

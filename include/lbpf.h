@@ -197,6 +197,49 @@ const char* lbpf_last_error(const lbpf_t* h);
 /* Release everything the handle owns; NULL is a no-op. */
 void lbpf_destroy(lbpf_t* h);
 
+/* ---- batched sweep ------------------------------------------------------------
+ * Many independent 2D instances (the parametric sweeps of Sec. 3: supersaturation,
+ * seed size, inflow) advanced together by ONE persistent kernel launch per time
+ * step: the tiles of all instances form one work list.  Every instance is an
+ * ordinary handle with its own state (lbpf_batch_instance); a batched instance
+ * evolves bit for bit like the same instance stepped alone.  Several tile
+ * shapes are compiled; the first lbpf_batch_step that is long enough
+ * (>= 24 steps) times each of them on the live batch and keeps the fastest
+ * (lbpf_batch_tuning); every shape produces the same bits.  Steps of 64 are
+ * replayed from a CUDA graph. */
+typedef struct lbpf_batch lbpf_batch_t;
+
+/* Create `count` instances (1..65535) from p[i] and seed them with s[i]
+ * (lbpf_create + lbpf_init_seed each).  All p[i] must be 2D with the same
+ * `flow` and the same storage among LBPF_FP32, LBPF_FP16_SHIFTED,
+ * LBPF_BF16_SHIFTED; sizes and every model parameter may differ.  EINVAL
+ * otherwise.  stream: as for lbpf_create, shared by all instances. */
+int lbpf_batch_create(const lbpf_params* p, const lbpf_seed* s, int count, void* stream,
+                      lbpf_batch_t** out);
+
+/* Advance every instance by n >= 0 steps.  Asynchronous, except that the
+ * first call of >= 24 steps synchronises once to time the tile shapes.
+ * Instances re-initialised or restored since the last call are picked up;
+ * instances stepped individually to a different buffer parity give
+ * LBPF_ESTATE.  An error of any instance is reported here. */
+int lbpf_batch_step(lbpf_batch_t* b, int n);
+
+/* lbpf_diagnostics of every instance into out[0..count-1].  Synchronising;
+ * returns the first non-OK status (all entries are still filled). */
+int lbpf_batch_diagnostics(lbpf_batch_t* b, lbpf_diag* out);
+
+/* Borrowed handle of instance i (NULL if out of range); owned by the batch.
+ * Use it for lbpf_read_fields, lbpf_diagnostics, lbpf_write_state. */
+lbpf_t* lbpf_batch_instance(lbpf_batch_t* b, int i);
+int lbpf_batch_count(const lbpf_batch_t* b);
+
+/* The tile shape the tuner chose (rows of the 32-wide tile, pipeline stages)
+ * and the measured ms per step of each compiled shape (ms[0..*nvar-1]); any
+ * pointer may be NULL.  LBPF_ESTATE before tuning has run. */
+int lbpf_batch_tuning(const lbpf_batch_t* b, int* tile_rows, int* stages, float* ms, int* nvar);
+const char* lbpf_batch_last_error(const lbpf_batch_t* b);
+void lbpf_batch_destroy(lbpf_batch_t* b);
+
 /* ---- allocation-free reduction ------------------------------------------------
  * The paper has no counterpart of this entry point; it serves callers that
  * cannot allocate device memory where they need the conservation sums: code

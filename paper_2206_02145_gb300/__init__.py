@@ -68,7 +68,9 @@ class lbpf_diag(ctypes.Structure):
 EXPORTED = ("lbpf_params_default", "lbpf_create", "lbpf_init_seed", "lbpf_init_fields",
             "lbpf_step", "lbpf_read_fields", "lbpf_state_bytes", "lbpf_write_state",
             "lbpf_diagnostics", "lbpf_set_stream", "lbpf_device_bytes", "lbpf_last_error",
-            "lbpf_destroy", "lbpf_field_sums_noalloc")
+            "lbpf_destroy", "lbpf_field_sums_noalloc", "lbpf_batch_create", "lbpf_batch_step",
+            "lbpf_batch_diagnostics", "lbpf_batch_instance", "lbpf_batch_count",
+            "lbpf_batch_tuning", "lbpf_batch_last_error", "lbpf_batch_destroy")
 
 
 def _load_library():
@@ -97,10 +99,24 @@ def _load_library():
     lib.lbpf_destroy.argtypes = [vp]
     lib.lbpf_destroy.restype = None
     lib.lbpf_field_sums_noalloc.argtypes = [vp, vp, vp, vp, ctypes.c_int64, ctypes.c_int, vp, vp]
+    lib.lbpf_batch_create.argtypes = [P, ctypes.POINTER(lbpf_seed), ctypes.c_int, vp,
+                                      ctypes.POINTER(vp)]
+    lib.lbpf_batch_step.argtypes = [vp, ctypes.c_int]
+    lib.lbpf_batch_diagnostics.argtypes = [vp, ctypes.POINTER(lbpf_diag)]
+    lib.lbpf_batch_instance.argtypes = [vp, ctypes.c_int]
+    lib.lbpf_batch_instance.restype = vp
+    lib.lbpf_batch_count.argtypes = [vp]
+    ip, fp = ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_float)
+    lib.lbpf_batch_tuning.argtypes = [vp, ip, ip, fp, ip]
+    lib.lbpf_batch_last_error.argtypes = [vp]
+    lib.lbpf_batch_last_error.restype = ctypes.c_char_p
+    lib.lbpf_batch_destroy.argtypes = [vp]
+    lib.lbpf_batch_destroy.restype = None
+    keep = ("lbpf_state_bytes", "lbpf_device_bytes", "lbpf_last_error", "lbpf_destroy",
+            "lbpf_batch_instance", "lbpf_batch_last_error", "lbpf_batch_destroy")
     for name in EXPORTED:
-        getattr(lib, name).restype = getattr(lib, name).restype if name in (
-            "lbpf_state_bytes", "lbpf_device_bytes", "lbpf_last_error", "lbpf_destroy") \
-            else ctypes.c_int
+        if name not in keep:
+            getattr(lib, name).restype = ctypes.c_int
     return lib
 
 
@@ -261,3 +277,82 @@ class Sim:
 
     def diagnostics(self) -> dict:
         return lbpf_diagnostics(self.h)
+
+
+class _BorrowedSim(Sim):
+    """A batch instance: an ordinary handle owned by its batch."""
+
+    def __init__(self, h, params, batch):
+        self.params = params
+        self.h = h
+        self._batch = batch  # keeps the owner alive
+        p = params
+        self.shape = (p.nz, p.ny, p.nx) if p.dim == 3 else (p.ny, p.nx)
+        self.nodes = int(np.prod(self.shape))
+
+    def close(self):
+        self.h = None  # owned by the batch
+
+    def __del__(self):
+        pass
+
+
+def lbpf_batch_create(params: list, seeds: list, stream: int | None = None) -> int:
+    n = len(params)
+    P_arr = (lbpf_params * n)(*params)
+    S_arr = (lbpf_seed * n)(*[lbpf_seed(*s) for s in seeds])
+    b = ctypes.c_void_p()
+    rc = _lib.lbpf_batch_create(P_arr, S_arr, n, ctypes.c_void_p(stream or 0), ctypes.byref(b))
+    if rc != OK:
+        raise LbpfError(rc, "lbpf_batch_create failed (reason on stderr)")
+    return b.value
+
+
+def _bcheck(b, rc):
+    if rc != OK:
+        raise LbpfError(rc, _lib.lbpf_batch_last_error(b).decode())
+
+
+class Batch:
+    """Many 2D instances advanced by one persistent launch per step."""
+
+    def __init__(self, params: list, seeds: list, stream: int | None = None):
+        self.params = [lbpf_params_default(**p) for p in params]
+        self.b = lbpf_batch_create(self.params, seeds, stream)
+        self.count = len(self.params)
+
+    def step(self, n: int = 1):
+        _bcheck(self.b, _lib.lbpf_batch_step(self.b, int(n)))
+
+    def instance(self, i: int) -> Sim:
+        h = _lib.lbpf_batch_instance(self.b, i)
+        if not h:
+            raise IndexError(i)
+        return _BorrowedSim(h, self.params[i], self)
+
+    def diagnostics(self) -> list:
+        arr = (lbpf_diag * self.count)()
+        _bcheck(self.b, _lib.lbpf_batch_diagnostics(self.b, arr))
+        return [{"step": d.step, "solute_total": d.solute_total, "mass_total": d.mass_total,
+                 "solid_volume": d.solid_volume, "r_eq": d.r_eq,
+                 "iface_pos": np.array(d.iface_pos[:]), "max_u": d.max_u,
+                 "nonfinite": d.nonfinite} for d in arr]
+
+    def tuning(self) -> dict:
+        rows, stages, nvar = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        ms = (ctypes.c_float * 8)()
+        rc = _lib.lbpf_batch_tuning(self.b, ctypes.byref(rows), ctypes.byref(stages), ms,
+                                    ctypes.byref(nvar))
+        return {"tuned": rc == OK, "tile_rows": rows.value, "stages": stages.value,
+                "ms_per_step": list(ms[:nvar.value])}
+
+    def close(self):
+        if getattr(self, "b", None):
+            _lib.lbpf_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -7,6 +7,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <new>
+#include <vector>
 
 #include "../../include/lbpf.h"
 #include "lbpf_internal.cuh"
@@ -35,6 +36,21 @@ struct lbpf {
   lbk::StepMaps maps;
   cudaGraphExec_t graph = nullptr;
   int graph_steps = 0;
+  int status = LBPF_OK;
+  int gen = 0;  // bumped whenever the state or the model constants are replaced
+  char msg[256] = {0};
+};
+
+struct lbpf_batch {
+  std::vector<lbpf*> kids;
+  std::vector<int> gens;
+  lbk::BatchPlan plans[8];
+  int nplans = 0, chosen = -1;
+  float tune_ms[8] = {0};
+  cudaStream_t stream = nullptr;
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t graph = nullptr;
+  int cur = 0;
   int status = LBPF_OK;
   char msg[256] = {0};
 };
@@ -161,8 +177,8 @@ int launch_one(lbpf* h, cudaStream_t s) {
   cudaError_t e = h->m.dim == 2
                       ? lbk::launch_step2d(h->m, h->maps, c, h->pops[c], h->pops[c ^ 1],
                                            h->phi[c], h->phi[c ^ 1], h->d_err, s)
-                      : lbk::launch_step3d(h->m, h->pops[c], h->pops[c ^ 1], h->phi[c],
-                                            h->phi[c ^ 1], h->d_err, s);
+                      : lbk::launch_step3d(h->m, h->maps, c, h->pops[c], h->pops[c ^ 1],
+                                           h->phi[c], h->phi[c ^ 1], h->d_err, s);
   if (e != cudaSuccess) return fail(h, LBPF_ECUDA, "step launch: %s", cudaGetErrorString(e));
   h->cur ^= 1;
   return LBPF_OK;
@@ -292,8 +308,9 @@ int lbpf_create(const lbpf_params* p, void* stream, lbpf_t** out) {
     lbpf_destroy(h);
     return LBPF_ECUDA;
   }
-  if (h->m.dim == 2) {
-    e = lbk::prepare_step2d(h->m, h->pops, h->phi, &h->maps);
+  {
+    e = h->m.dim == 2 ? lbk::prepare_step2d(h->m, h->pops, h->phi, &h->maps)
+                      : lbk::prepare_step3d(h->m, h->pops, h->phi, &h->maps);
     if (e != cudaSuccess) {
       fprintf(stderr, "lbpf_create: step setup: %s\n", cudaGetErrorString(e));
       lbpf_destroy(h);
@@ -316,6 +333,7 @@ int lbpf_init_seed(lbpf_t* h, const lbpf_seed* s) {
   h->m.ref_g = s->u0;
   lbk::finalize(h->m);
   drop_graph(h);
+  ++h->gen;
   lbk::SeedArgs a{s->cx, s->cy, s->cz, s->radius, s->u0, s->noise_amp, s->seed};
   h->cur = 0;
   h->step = 0;
@@ -361,6 +379,7 @@ int lbpf_init_fields(lbpf_t* h, const double* phi, const double* U, const double
   }
   lbk::finalize(h->m);
   drop_graph(h);
+  ++h->gen;
   h->cur = 0;
   h->step = 0;
   cudaError_t e = lbk::launch_init_fields(h->m, dev[0], dev[1], dev[2], dev[3], dev[4], dev[5],
@@ -476,6 +495,7 @@ int lbpf_write_state(lbpf_t* h, const void* host_src, size_t bytes) {
   if (h->m.ref_g != hd.ref_g) drop_graph(h);
   h->m.ref_g = hd.ref_g;
   lbk::finalize(h->m);
+  ++h->gen;
   if (!h->initialized) {
     h->initialized = true;
     store_I0(h);
@@ -533,6 +553,240 @@ void lbpf_destroy(lbpf_t* h) {
   if (h->d_diag) cudaFree(h->d_diag);
   if (h->d_fields) cudaFree(h->d_fields);
   delete h;
+}
+
+}  // extern "C"
+
+// ---- batched sweep ------------------------------------------------------------------
+namespace {
+
+constexpr int kTuneWarm = 2, kTuneTimed = 4;
+
+int bfail(lbpf_batch* b, int code, const char* fmt, ...) {
+  if (!b) return code;
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(b->msg, sizeof(b->msg), fmt, ap);
+  va_end(ap);
+  if (code == LBPF_ECUDA || code == LBPF_ENONFINITE || code == LBPF_ETIMEDOUT) b->status = code;
+  return code;
+}
+
+#define BCK(b, call)                                                                       \
+  do {                                                                                     \
+    cudaError_t e_ = (call);                                                               \
+    if (e_ != cudaSuccess)                                                                 \
+      return bfail(b, LBPF_ECUDA, "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, \
+                   __LINE__);                                                              \
+  } while (0)
+
+void batch_drop_graph(lbpf_batch* b) {
+  if (b->graph) cudaGraphExecDestroy(b->graph);
+  b->graph = nullptr;
+}
+
+// (Re)build the device tables of every compiled variant from the instances.
+int batch_build(lbpf_batch* b) {
+  batch_drop_graph(b);
+  for (int v = 0; v < b->nplans; ++v) lbk::batch_plan_free(&b->plans[v]);
+  std::vector<lbk::BatchMember> mem(b->kids.size());
+  for (size_t i = 0; i < b->kids.size(); ++i) {
+    lbpf* k = b->kids[i];
+    mem[i].m = k->m;
+    for (int c = 0; c < 2; ++c) {
+      mem[i].pops[c] = k->pops[c];
+      mem[i].rings[c] = k->phi[c];
+    }
+    mem[i].err = k->d_err;
+    b->gens[i] = k->gen;
+  }
+  b->nplans = lbk::batch_variant_count();
+  const lbpf* k0 = b->kids[0];
+  for (int v = 0; v < b->nplans; ++v)
+    BCK(b, lbk::batch_plan_build(mem.data(), int(mem.size()), k0->m.storage, k0->m.flow, v,
+                                 &b->plans[v]));
+  return LBPF_OK;
+}
+
+int batch_launch(lbpf_batch* b, int v, cudaStream_t s) {
+  BCK(b, lbk::batch_plan_launch(b->plans[v], b->cur, s));
+  b->cur ^= 1;
+  return LBPF_OK;
+}
+
+int batch_build_graph(lbpf_batch* b) {
+  if (b->graph) return LBPF_OK;
+  if (!b->cap_stream) BCK(b, cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking));
+  const int saved = b->cur;
+  b->cur = 0;
+  cudaGraph_t g = nullptr;
+  BCK(b, cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal));
+  int rc = LBPF_OK;
+  for (int i = 0; i < kGraphSteps && rc == LBPF_OK; ++i) rc = batch_launch(b, b->chosen, b->cap_stream);
+  cudaError_t e = cudaStreamEndCapture(b->cap_stream, &g);
+  b->cur = saved;
+  if (rc != LBPF_OK) {
+    if (g) cudaGraphDestroy(g);
+    return rc;
+  }
+  if (e != cudaSuccess) return bfail(b, LBPF_ECUDA, "batch graph capture: %s", cudaGetErrorString(e));
+  e = cudaGraphInstantiate(&b->graph, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess)
+    return bfail(b, LBPF_ECUDA, "batch graph instantiate: %s", cudaGetErrorString(e));
+  return LBPF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int lbpf_batch_create(const lbpf_params* p, const lbpf_seed* s, int count, void* stream,
+                      lbpf_batch_t** out) {
+  if (!p || !s || !out || count < 1 || count > 65535) return LBPF_EINVAL;
+  *out = nullptr;
+  for (int i = 0; i < count; ++i) {
+    if (p[i].dim != 2 || p[i].flow != p[0].flow || p[i].storage != p[0].storage ||
+        p[i].storage == LBPF_FP64) {
+      fprintf(stderr,
+              "lbpf_batch_create: instance %d: a batch holds 2D instances with one flow flag "
+              "and one storage among FP32, FP16, BF16\n", i);
+      return LBPF_EINVAL;
+    }
+  }
+  lbpf_batch* b = new (std::nothrow) lbpf_batch();
+  if (!b) return LBPF_ENOMEM;
+  b->stream = static_cast<cudaStream_t>(stream);
+  for (int i = 0; i < count; ++i) {
+    lbpf_t* k = nullptr;
+    int rc = lbpf_create(&p[i], stream, &k);
+    if (rc == LBPF_OK) {
+      b->kids.push_back(k);
+      rc = lbpf_init_seed(k, &s[i]);
+    }
+    if (rc != LBPF_OK) {
+      fprintf(stderr, "lbpf_batch_create: instance %d: status %d %s\n", i, rc,
+              k ? k->msg : "");
+      lbpf_batch_destroy(b);
+      return rc;
+    }
+  }
+  b->gens.assign(count, 0);
+  int rc = batch_build(b);
+  if (rc != LBPF_OK) {
+    fprintf(stderr, "lbpf_batch_create: %s\n", b->msg);
+    lbpf_batch_destroy(b);
+    return rc;
+  }
+  *out = b;
+  return LBPF_OK;
+}
+
+int lbpf_batch_step(lbpf_batch_t* b, int n) {
+  if (!b) return LBPF_EINVAL;
+  if (b->status != LBPF_OK) return b->status;
+  if (n < 0) return bfail(b, LBPF_EINVAL, "n must be >= 0");
+  bool rebuild = false;
+  for (size_t i = 0; i < b->kids.size(); ++i) {
+    lbpf* k = b->kids[i];
+    if (k->status != LBPF_OK) return bfail(b, k->status, "instance %zu: %s", i, k->msg);
+    if (!k->initialized) return bfail(b, LBPF_ESTATE, "instance %zu is not initialised", i);
+    if (k->gen != b->gens[i]) rebuild = true;
+  }
+  if (rebuild) {
+    int rc = batch_build(b);
+    if (rc) return rc;
+  }
+  b->cur = b->kids[0]->cur;
+  for (size_t i = 0; i < b->kids.size(); ++i)
+    if (b->kids[i]->cur != b->cur)
+      return bfail(b, LBPF_ESTATE, "instances were stepped apart; step them to equal parity");
+  int left = n, rc;
+  if (b->chosen < 0 && left >= b->nplans * (kTuneWarm + kTuneTimed)) {
+    // time every variant on the live batch (they produce identical bits)
+    cudaEvent_t e0, e1;
+    BCK(b, cudaEventCreate(&e0));
+    BCK(b, cudaEventCreate(&e1));
+    for (int v = 0; v < b->nplans; ++v) {
+      for (int i = 0; i < kTuneWarm; ++i)
+        if ((rc = batch_launch(b, v, b->stream))) return rc;
+      BCK(b, cudaEventRecord(e0, b->stream));
+      for (int i = 0; i < kTuneTimed; ++i)
+        if ((rc = batch_launch(b, v, b->stream))) return rc;
+      BCK(b, cudaEventRecord(e1, b->stream));
+      BCK(b, cudaEventSynchronize(e1));
+      float ms = 0.f;
+      BCK(b, cudaEventElapsedTime(&ms, e0, e1));
+      b->tune_ms[v] = ms / kTuneTimed;
+      left -= kTuneWarm + kTuneTimed;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    b->chosen = 0;
+    for (int v = 1; v < b->nplans; ++v)
+      if (b->tune_ms[v] < b->tune_ms[b->chosen]) b->chosen = v;
+  }
+  const int v = b->chosen < 0 ? 0 : b->chosen;
+  if (b->chosen >= 0 && left >= kGraphSteps) {
+    if (b->cur == 1) {
+      if ((rc = batch_launch(b, v, b->stream))) return rc;
+      --left;
+    }
+    if (left >= kGraphSteps) {
+      if ((rc = batch_build_graph(b))) return rc;
+      while (left >= kGraphSteps) {
+        BCK(b, cudaGraphLaunch(b->graph, b->stream));
+        left -= kGraphSteps;
+      }
+    }
+  }
+  for (; left > 0; --left)
+    if ((rc = batch_launch(b, v, b->stream))) return rc;
+  for (lbpf* k : b->kids) {
+    k->cur = b->cur;
+    k->step += n;
+  }
+  return LBPF_OK;
+}
+
+int lbpf_batch_diagnostics(lbpf_batch_t* b, lbpf_diag* out) {
+  if (!b || !out) return LBPF_EINVAL;
+  int worst = LBPF_OK;
+  for (size_t i = 0; i < b->kids.size(); ++i) {
+    const int rc = lbpf_diagnostics(b->kids[i], &out[i]);
+    if (rc != LBPF_OK && worst == LBPF_OK) worst = rc;
+  }
+  return worst;
+}
+
+lbpf_t* lbpf_batch_instance(lbpf_batch_t* b, int i) {
+  if (!b || i < 0 || i >= int(b->kids.size())) return nullptr;
+  return b->kids[i];
+}
+
+int lbpf_batch_count(const lbpf_batch_t* b) { return b ? int(b->kids.size()) : 0; }
+
+int lbpf_batch_tuning(const lbpf_batch_t* b, int* tile_rows, int* stages, float* ms, int* nvar) {
+  if (!b) return LBPF_EINVAL;
+  if (nvar) *nvar = b->nplans;
+  if (ms)
+    for (int v = 0; v < b->nplans; ++v) ms[v] = b->tune_ms[v];
+  const int v = b->chosen;
+  if (tile_rows) *tile_rows = v < 0 ? 0 : lbk::batch_variant_rows(v);
+  if (stages) *stages = v < 0 ? 0 : lbk::batch_variant_stages(v);
+  return v < 0 ? LBPF_ESTATE : LBPF_OK;
+}
+
+const char* lbpf_batch_last_error(const lbpf_batch_t* b) { return b ? b->msg : "null handle"; }
+
+void lbpf_batch_destroy(lbpf_batch_t* b) {
+  if (!b) return;
+  cudaStreamSynchronize(b->stream);
+  batch_drop_graph(b);
+  if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+  for (int v = 0; v < b->nplans; ++v) lbk::batch_plan_free(&b->plans[v]);
+  for (lbpf* k : b->kids) lbpf_destroy(k);
+  delete b;
 }
 
 }  // extern "C"

@@ -56,6 +56,18 @@ __device__ __forceinline__ R clamp1(R v) {
   return v < R(-1) ? R(-1) : (v > R(1) ? R(1) : v);
 }
 __device__ __forceinline__ bool finite_r(float v) { return isfinite(v); }
+
+// Explicitly rounded multiply / add / fused multiply-add.  The values a node
+// pushes are written with these so that the compiler cannot fuse them
+// differently in different code paths (interior vs edge tiles, single vs
+// batched kernels): every path then rounds identically and a node's result
+// does not depend on how the grid was tiled.
+__device__ __forceinline__ float fma_r(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fma_r(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ float mul_r(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_r(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float add_r(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double add_r(double a, double b) { return __dadd_rn(a, b); }
 __device__ __forceinline__ bool finite_r(double v) { return isfinite(v); }
 
 // ---- population storage ---------------------------------------------------------

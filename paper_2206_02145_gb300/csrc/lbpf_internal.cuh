@@ -98,7 +98,7 @@ __host__ __device__ __forceinline__ const Coef<double>& coef<double>(const Model
 struct PopPtrs {
   void* p[27];
 };
-// TMA descriptors of the 2D step for both population buffers (index = the
+// TMA descriptors of the 2D or 3D step for both population buffers (index = the
 // parity of the source buffer) and the launch shape of the persistent kernel.
 struct StepMaps {
   CUtensorMap fg[2], h[2], ring[2];
@@ -117,8 +117,42 @@ inline PopPtrs pop_ptrs(const Model& m, void* buf, size_t elem_bytes) {
     r.p[a] = static_cast<char*>(buf) + size_t(a) * size_t(m.plane) * elem_bytes;
   return r;
 }
-cudaError_t launch_step3d(const Model& m, const void* src, void* dst, const void* phi_prev,
-                          void* phi_cur, unsigned* err, cudaStream_t s);
+cudaError_t prepare_step3d(const Model& m, void* const pops[2], void* const rings[2],
+                           StepMaps* out);
+cudaError_t launch_step3d(const Model& m, const StepMaps& maps, int c, const void* src, void* dst,
+                          const void* ring_prev, void* ring_cur, unsigned* err, cudaStream_t s);
+
+// ---- batched 2D step ---------------------------------------------------------------
+// One instance of a batch for one buffer parity: its TMA descriptors (64-byte
+// aligned, read by the TMA from global memory), model and buffers.
+struct alignas(128) BatchDesc {
+  CUtensorMap fg, h, ring;
+  Model m;
+  const void* src;
+  void* dst;
+  float* ring_cur;
+  unsigned* err;
+  int ntx, tile0, ntiles, pad;
+};
+struct BatchMember {  // what the batch needs of one instance
+  Model m;
+  void* pops[2];
+  void* rings[2];
+  unsigned* err;
+};
+struct BatchPlan {  // device tables of one compiled variant
+  BatchDesc* desc[2] = {nullptr, nullptr};
+  unsigned short* tile_inst = nullptr;
+  int total_tiles = 0, variant = 0, storage = 0, flow = 0, ctas = 0, smem = 0;
+  size_t bytes = 0;
+};
+int batch_variant_count();
+int batch_variant_rows(int v);
+int batch_variant_stages(int v);
+cudaError_t batch_plan_build(const BatchMember* members, int count, int storage, int flow, int v,
+                             BatchPlan* plan);
+cudaError_t batch_plan_launch(const BatchPlan& plan, int c, cudaStream_t s);
+void batch_plan_free(BatchPlan* plan);
 
 // Seeded initial state (FP64 arithmetic, stored in the population type).
 struct SeedArgs {

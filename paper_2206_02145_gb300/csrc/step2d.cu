@@ -30,10 +30,8 @@
 //
 // step2d_kernel (FP64 storage): one thread per node, one tile per CTA, the
 // same per-node code.
-#include <cudaTypedefs.h>
-
-#include "step2d_core.cuh"
-#include "tma.cuh"
+#include "step2d_tile.cuh"
+#include "tma_host.h"
 
 namespace lbk {
 namespace {
@@ -111,20 +109,6 @@ __global__ void __launch_bounds__(TX* TY)
 }
 
 // ---- TMA-pipelined persistent kernel ------------------------------------------
-template <typename T, bool FLOW, int TX, int TY>
-struct Tiles2D {
-  static constexpr int QFG = (FLOW ? 9 : 0) + 9;   // f and g arrays
-  static constexpr int HX = 16 / int(sizeof(T));   // halo box starts HX left of the tile
-  static constexpr int BXH = TX + 2 * HX;          // h box width
-  static constexpr int FG_BYTES = QFG * TY * TX * int(sizeof(T));
-  static constexpr int H_BYTES = 9 * (TY + 2) * BXH * int(sizeof(T));
-  static constexpr int RING_BYTES = TY * TX * 4;
-  static constexpr int al(int b) { return (b + 127) / 128 * 128; }
-  static constexpr int OFF_H = al(FG_BYTES);
-  static constexpr int OFF_RING = OFF_H + al(H_BYTES);
-  static constexpr int STAGE = OFF_RING + al(RING_BYTES);
-  static constexpr int TX_BYTES = FG_BYTES + H_BYTES + RING_BYTES;
-};
 
 // Pipeline depth and resident CTAs per SM of the persistent kernel.
 #ifndef LBPF_2D_STAGES
@@ -147,8 +131,7 @@ __global__ void __launch_bounds__(TX* TY, LBPF_2D_MIN_CTAS)
                       int ntiles) {
   using R = float;
   using L = Tiles2D<T, FLOW, TX, TY>;
-  constexpr int NT = TX * TY, SX = TX + 2, SY = TY + 2;
-  constexpr int QF = FLOW ? 9 : 0;
+  constexpr int SX = TX + 2, SY = TY + 2;
   extern __shared__ unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t full[S];
   __shared__ R sh_phi[SY][SX];
@@ -156,17 +139,11 @@ __global__ void __launch_bounds__(TX* TY, LBPF_2D_MIN_CTAS)
       (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
 
   const int tid = threadIdx.x;
-  const int tx = tid % TX, ty = tid / TX;
-  const int nx = m.nx, ny = m.ny, px = m.px;
   const int first = blockIdx.x, G = gridDim.x;
 
   auto issue = [&](int tile, int s) {
-    const int x0 = (tile % ntx) * TX, y0 = (tile / ntx) * TY;
-    unsigned char* st = smem + s * L::STAGE;
-    mbar_arrive_expect_tx(&full[s], L::TX_BYTES);
-    tma_load_3d(st, &tm_fg, &full[s], x0, y0, 0);
-    tma_load_3d(st + L::OFF_H, &tm_h, &full[s], x0 - L::HX, y0 - 1, L::QFG);
-    tma_load_2d(st + L::OFF_RING, &tm_ring, &full[s], x0, y0);
+    issue_tile_2d<T, FLOW, TX, TY>(&tm_fg, &tm_h, &tm_ring, &full[s], smem + s * L::STAGE,
+                                   (tile % ntx) * TX, (tile / ntx) * TY);
   };
 
   if (tid == 0) {
@@ -197,59 +174,8 @@ __global__ void __launch_bounds__(TX* TY, LBPF_2D_MIN_CTAS)
       return;
     }
     const int x0 = (tile % ntx) * TX, y0 = (tile / ntx) * TY;
-    unsigned char* st = smem + s * L::STAGE;
-    const T* fgs = reinterpret_cast<const T*>(st);
-    T* hsm = reinterpret_cast<T*>(st + L::OFF_H);
-    const float* rings = reinterpret_cast<const float*>(st + L::OFF_RING);
-    constexpr int HPLANE = SY * L::BXH;
-
-    if (x0 == 0 || y0 == 0 || x0 + TX >= nx || y0 + TY >= ny) {
-      // halo positions outside the domain: periodic wrap or nearest node
-      for (int i = tid; i < SX * SY; i += NT) {
-        const int lx = i % SX, ly = i / SX;
-        int gx = x0 + lx - 1, gy = y0 + ly - 1;
-        if (gx >= 0 && gx < nx && gy >= 0 && gy < ny) continue;
-        gx = grad_coord(gx, nx, m.bc[0]);
-        gy = grad_coord(gy, ny, m.bc[1]);
-        const int j = gy * px + gx;
-        const int P = int(m.plane);
-#pragma unroll
-        for (int a = 0; a < 9; ++a)
-          hsm[a * HPLANE + ly * L::BXH + lx + L::HX - 1] = src[(QF + 9 + a) * P + j];
-      }
-      __syncthreads();
-    }
-    // phi + 1 of the halo-extended tile
-    for (int i = tid; i < SX * SY; i += NT) {
-      const int lx = i % SX, ly = i / SX;
-      const T* hp = hsm + ly * L::BXH + lx + L::HX - 1;
-      R sum = R(0);
-#pragma unroll
-      for (int a = 0; a < 9; ++a) sum += Pop<T>::template ld<R>(hp + a * HPLANE);
-      sh_phi[ly][lx] = sum;
-    }
-    __syncthreads();
-
-    const int x = x0 + tx, y = y0 + ty;
-    if (x < nx && y < ny) {
-      R f[9], g[9], h[9];
-      const int o = ty * TX + tx;
-#pragma unroll
-      for (int a = 0; a < 9; ++a) {
-        if (FLOW) f[a] = Pop<T>::template ld<R>(fgs + a * (TY * TX) + o);
-        g[a] = Pop<T>::template ld<R>(fgs + (QF + a) * (TY * TX) + o);
-        h[a] = Pop<T>::template ld<R>(hsm + a * HPLANE + (ty + 1) * L::BXH + tx + L::HX);
-      }
-      TileView<T, R, L::BXH, HPLANE, L::HX - 1> hs{hsm};
-      if (x0 >= 1 && x0 + TX <= nx - 1 && y0 >= 1 && y0 + TY <= ny - 1)
-        collide_push_2d<T, R, FLOW, true, SX>(m, x, y, tx + 1, ty + 1, f, g, h,
-                                              sh_phi[ty + 1][tx + 1], rings[o], &sh_phi[0][0], hs,
-                                              dst, ring_cur, err);
-      else
-        collide_push_2d<T, R, FLOW, false, SX>(m, x, y, tx + 1, ty + 1, f, g, h,
-                                               sh_phi[ty + 1][tx + 1], rings[o], &sh_phi[0][0],
-                                               hs, dst, ring_cur, err);
-    }
+    tile_2d<T, FLOW, TX, TY>(m, src, dst, ring_cur, err, x0, y0, smem + s * L::STAGE,
+                             &sh_phi[0][0]);
     __syncthreads();  // stage s and sh_phi are free again
     if (tid == 0 && tile + S * G < ntiles) {
       fence_proxy_async_smem();
@@ -261,35 +187,10 @@ __global__ void __launch_bounds__(TX* TY, LBPF_2D_MIN_CTAS)
 // ---- host side: tensor maps and launches -------------------------------------------
 constexpr int kTX = 32, kTY = LBPF_2D_TY, kStages = LBPF_2D_STAGES;
 
-PFN_cuTensorMapEncodeTiled_v12000 encoder() {
-  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-  if (!fn) {
-    void* p = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
-                                         &q) == cudaSuccess &&
-        q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
-  }
-  return fn;
-}
-
-bool encode(CUtensorMap* map, CUtensorMapDataType dt, int rank, void* base, const uint64_t* dims,
-            const uint64_t* strides_bytes, const uint32_t* box) {
-  auto fn = encoder();
-  if (!fn) return false;
-  const uint32_t es[3] = {1, 1, 1};
-  return fn(map, dt, rank, base, dims, strides_bytes, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
-            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
-}
-
 template <typename T, bool FLOW>
 cudaError_t prepare_t(const Model& m, void* const pops[2], void* const rings[2], StepMaps* out) {
   using L = Tiles2D<T, FLOW, kTX, kTY>;
-  const CUtensorMapDataType dt = sizeof(T) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
-                                : (m.storage == ST_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
-                                                        : CU_TENSOR_MAP_DATA_TYPE_FLOAT16);
+  const CUtensorMapDataType dt = pop_tensor_type(m.storage);
   const uint64_t q = uint64_t(L::QFG + 9);
   for (int b = 0; b < 2; ++b) {
     const uint64_t dims3[3] = {uint64_t(m.nx), uint64_t(m.ny), q};
@@ -299,9 +200,9 @@ cudaError_t prepare_t(const Model& m, void* const pops[2], void* const rings[2],
     const uint64_t dims2[2] = {uint64_t(m.nx), uint64_t(m.ny)};
     const uint64_t str2[1] = {uint64_t(m.px) * 4};
     const uint32_t box_r[2] = {kTX, kTY};
-    if (!encode(&out->fg[b], dt, 3, pops[b], dims3, str3, box_fg) ||
-        !encode(&out->h[b], dt, 3, pops[b], dims3, str3, box_h) ||
-        !encode(&out->ring[b], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, rings[b], dims2, str2, box_r))
+    if (!encode_tiled(&out->fg[b], dt, 3, pops[b], dims3, str3, box_fg) ||
+        !encode_tiled(&out->h[b], dt, 3, pops[b], dims3, str3, box_h) ||
+        !encode_tiled(&out->ring[b], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, rings[b], dims2, str2, box_r))
       return cudaErrorInvalidValue;
   }
   auto kern = step2d_tma_kernel<T, FLOW, kTX, kTY, kStages>;

@@ -120,16 +120,18 @@ __device__ __forceinline__ void collide_push_2d(const Model& m, int x, int y, in
     R fp = R(0);
     if (FLOW) {
       const R cF = R(cx) * Fx + R(cy) * Fy;
-      fp = keep_f * f[a] + w * ((E0 + cu * (E1 + E2 * cu)) + guo * (cF * (R(3) + R(9) * cu) + G0));
+      const R feq = fma_r(cu, fma_r(E2, cu, E1), E0);
+      const R guo_t = mul_r(guo, fma_r(cF, fma_r(R(9), cu, R(3)), G0));
+      fp = fma_r(keep_f, f[a], mul_r(w, add_r(feq, guo_t)));
     }
-    const R gp = keep_U * g[a] + w * (K0 + K1 * cu);
-    const R hp = keep_phi * h[a] + w * (H0 - (R(cx) * Hx + R(cy) * Hy));
+    const R gp = fma_r(keep_U, g[a], mul_r(w, fma_r(K1, cu, K0)));
+    const R hp = fma_r(keep_phi, h[a], mul_r(w, add_r(H0, -add_r(R(cx) * Hx, R(cy) * Hy))));
     if (INTERIOR) {
       const int off = cy * px + cx;  // uniform
       const R hold = hs.at(a, ly + cy, lx + cx);  // h_a(s + c_a, t)
       if (FLOW) Pop<T>::st(pd + (a * P + off), fp);
       Pop<T>::st(pd + ((QF + a) * P + off), gp);
-      Pop<T>::st(pd + ((QF + 9 + a) * P + off), inv_a2 * hp + keep_old * hold);  // Eq. 19
+      Pop<T>::st(pd + ((QF + 9 + a) * P + off), fma_r(inv_a2, hp, mul_r(keep_old, hold)));  // Eq. 19
       continue;
     }
     // destination s + c_a
@@ -149,13 +151,13 @@ __device__ __forceinline__ void collide_push_2d(const Model& m, int x, int y, in
       const int b = D2_OPP[a];
       if (FLOW) Pop<T>::st(LBPF_DF(b) + idx, fp);
       Pop<T>::st(LBPF_DG(b) + idx, gp);
-      Pop<T>::st(LBPF_DH(b) + idx, inv_a2 * hp + keep_old * h[b]);
+      Pop<T>::st(LBPF_DH(b) + idx, fma_r(inv_a2, hp, mul_r(keep_old, h[b])));
     } else if (!drop) {
       const int jd = yd * px + xd;
       const R hold = hs.at(a, ly + cy, lx + cx);  // h_a(s + c_a, t)
       if (FLOW) Pop<T>::st(LBPF_DF(a) + jd, fp);
       Pop<T>::st(LBPF_DG(a) + jd, gp);
-      Pop<T>::st(LBPF_DH(a) + jd, inv_a2 * hp + keep_old * hold);  // Eq. 19
+      Pop<T>::st(LBPF_DH(a) + jd, fma_r(inv_a2, hp, mul_r(keep_old, hold)));  // Eq. 19
     }
     if (bcx == BC_INOUT) {
       if (cx == -1 && x == nx - 1) {
@@ -172,7 +174,7 @@ __device__ __forceinline__ void collide_push_2d(const Model& m, int x, int y, in
           const R hold = hs.at(a, ly + cy, lx);
           if (FLOW) Pop<T>::st(LBPF_DF(a) + jo, fp);
           Pop<T>::st(LBPF_DG(a) + jo, gp);
-          Pop<T>::st(LBPF_DH(a) + jo, inv_a2 * hp + keep_old * hold);
+          Pop<T>::st(LBPF_DH(a) + jo, fma_r(inv_a2, hp, mul_r(keep_old, hold)));
         }
       }
       if (cx == 1 && x == 0) {

@@ -83,3 +83,17 @@ def test_null_handle_calls_return_einval(lib):
     assert so.lbpf_diagnostics(None, None) == lib.EINVAL
     assert so.lbpf_state_bytes(None) == 0
     so.lbpf_destroy(None)
+
+
+def test_batch_validation_before_any_gpu_work(lib):
+    # a 3D instance and mixed storages are rejected before anything is allocated
+    p3 = [lib.lbpf_params_default(dim=3, nz=8, fold=0), lib.lbpf_params_default()]
+    with pytest.raises(lib.LbpfError) as e:
+        lib.lbpf_batch_create(p3, [(4, 4, 4, 2, 0.3, 0, 1)] * 2)
+    assert e.value.code == lib.EINVAL
+    pm = [lib.lbpf_params_default(), lib.lbpf_params_default(storage=lib.FP16_SHIFTED)]
+    with pytest.raises(lib.LbpfError) as e:
+        lib.lbpf_batch_create(pm, [(4, 4, 0, 2, 0.3, 0, 1)] * 2)
+    assert e.value.code == lib.EINVAL
+    assert lib._lib.lbpf_batch_step(None, 1) == lib.EINVAL
+    assert lib._lib.lbpf_batch_count(None) == 0
