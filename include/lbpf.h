@@ -240,6 +240,51 @@ int lbpf_batch_tuning(const lbpf_batch_t* b, int* tile_rows, int* stages, float*
 const char* lbpf_batch_last_error(const lbpf_batch_t* b);
 void lbpf_batch_destroy(lbpf_batch_t* b);
 
+/* ---- learned surrogate --------------------------------------------------------
+ * A BF16 U-Net (NHWC activations, FP32 accumulation, FP32 master weights,
+ * Adam) trained and run by the library's own tensor-core kernels.  It maps
+ * normalised fields (phi, U, ux, uy) to the normalised change of those fields
+ * over a fixed block of LB steps.  Architecture per level l (channels
+ * C_l = base_ch 2^l): encoder conv3x3 + ReLU twice, 2x2 average pooling;
+ * decoder nearest 2x upsampling, conv3x3 + ReLU, concatenation with the
+ * encoder output, conv3x3 + ReLU twice; a 1x1 FP32 head.  There is no
+ * counterpart in the paper: it is the sweep-exploration accelerator whose
+ * fallback and judge is the LB step above. */
+typedef struct lbpf_unet lbpf_unet_t;
+typedef struct {
+  int in_ch, out_ch;  /* 1..16 inputs, 1..4 outputs */
+  int base_ch;        /* 32 */
+  int levels;         /* 1..6 */
+  int batch, height, width; /* width / 2^(levels-1) a multiple of 64 */
+  uint64_t seed;      /* weight initialisation (He uniform, SplitMix64) */
+} lbpf_unet_cfg;
+
+int lbpf_unet_create(const lbpf_unet_cfg* cfg, void* stream, lbpf_unet_t** out);
+/* x: device FP32 [batch][height][width][in_ch]; y: device FP32 [..][out_ch].
+ * Asynchronous on the network's stream. */
+int lbpf_unet_forward(lbpf_unet_t* n, const float* x, float* y);
+/* Loss (mean squared error against device FP32 targets t, same layout as y)
+ * and the gradients of every parameter, without updating them; the loss is
+ * written to *loss_host (synchronising) if loss_host is not NULL. */
+int lbpf_unet_grad(lbpf_unet_t* n, const float* x, const float* t, float* loss_host);
+/* One Adam step (beta 0.9 / 0.999, eps 1e-8) at learning rate lr; the loss
+ * of the batch goes to the device float *loss_dev if not NULL.  Asynchronous. */
+int lbpf_unet_train_step(lbpf_unet_t* n, const float* x, const float* t, float lr,
+                         float* loss_dev);
+/* Number of parameters and their copy to / from host FP32 memory in a fixed
+ * order: the first encoder convolution of every level (0..L-1), the second
+ * encoder convolution of every level, the upsampling convolution of every
+ * level 0..L-2, the first and then the second decoder convolution of every
+ * level 0..L-2 -- each as weights [9][Cout][Cin] (taps row-major) then bias
+ * [Cout]; then the head weights [out][C0] and bias [out].  The first encoder
+ * convolution has Cin = 16 (inputs zero-padded).  which: 0 weights,
+ * 1 gradients; set = 1 writes weights.  Synchronising. */
+size_t lbpf_unet_param_count(const lbpf_unet_t* n);
+int lbpf_unet_params(lbpf_unet_t* n, int which, float* host, size_t count, int set);
+size_t lbpf_unet_device_bytes(const lbpf_unet_t* n);
+const char* lbpf_unet_last_error(const lbpf_unet_t* n);
+void lbpf_unet_destroy(lbpf_unet_t* n);
+
 /* ---- allocation-free reduction ------------------------------------------------
  * The paper has no counterpart of this entry point; it serves callers that
  * cannot allocate device memory where they need the conservation sums: code

@@ -65,12 +65,21 @@ class lbpf_diag(ctypes.Structure):
                 ("nonfinite", ctypes.c_int64)]
 
 
+class lbpf_unet_cfg(ctypes.Structure):
+    _fields_ = [("in_ch", ctypes.c_int), ("out_ch", ctypes.c_int), ("base_ch", ctypes.c_int),
+                ("levels", ctypes.c_int), ("batch", ctypes.c_int), ("height", ctypes.c_int),
+                ("width", ctypes.c_int), ("seed", ctypes.c_uint64)]
+
+
 EXPORTED = ("lbpf_params_default", "lbpf_create", "lbpf_init_seed", "lbpf_init_fields",
             "lbpf_step", "lbpf_read_fields", "lbpf_state_bytes", "lbpf_write_state",
             "lbpf_diagnostics", "lbpf_set_stream", "lbpf_device_bytes", "lbpf_last_error",
             "lbpf_destroy", "lbpf_field_sums_noalloc", "lbpf_batch_create", "lbpf_batch_step",
             "lbpf_batch_diagnostics", "lbpf_batch_instance", "lbpf_batch_count",
-            "lbpf_batch_tuning", "lbpf_batch_last_error", "lbpf_batch_destroy")
+            "lbpf_batch_tuning", "lbpf_batch_last_error", "lbpf_batch_destroy",
+            "lbpf_unet_create", "lbpf_unet_forward", "lbpf_unet_grad", "lbpf_unet_train_step",
+            "lbpf_unet_param_count", "lbpf_unet_params", "lbpf_unet_device_bytes",
+            "lbpf_unet_last_error", "lbpf_unet_destroy")
 
 
 def _load_library():
@@ -112,8 +121,23 @@ def _load_library():
     lib.lbpf_batch_last_error.restype = ctypes.c_char_p
     lib.lbpf_batch_destroy.argtypes = [vp]
     lib.lbpf_batch_destroy.restype = None
+    lib.lbpf_unet_create.argtypes = [ctypes.POINTER(lbpf_unet_cfg), vp, ctypes.POINTER(vp)]
+    lib.lbpf_unet_forward.argtypes = [vp, vp, vp]
+    lib.lbpf_unet_grad.argtypes = [vp, vp, vp, fp]
+    lib.lbpf_unet_train_step.argtypes = [vp, vp, vp, ctypes.c_float, vp]
+    lib.lbpf_unet_param_count.argtypes = [vp]
+    lib.lbpf_unet_param_count.restype = sz
+    lib.lbpf_unet_params.argtypes = [vp, ctypes.c_int, fp, sz, ctypes.c_int]
+    lib.lbpf_unet_device_bytes.argtypes = [vp]
+    lib.lbpf_unet_device_bytes.restype = sz
+    lib.lbpf_unet_last_error.argtypes = [vp]
+    lib.lbpf_unet_last_error.restype = ctypes.c_char_p
+    lib.lbpf_unet_destroy.argtypes = [vp]
+    lib.lbpf_unet_destroy.restype = None
     keep = ("lbpf_state_bytes", "lbpf_device_bytes", "lbpf_last_error", "lbpf_destroy",
-            "lbpf_batch_instance", "lbpf_batch_last_error", "lbpf_batch_destroy")
+            "lbpf_batch_instance", "lbpf_batch_last_error", "lbpf_batch_destroy",
+            "lbpf_unet_param_count", "lbpf_unet_device_bytes", "lbpf_unet_last_error",
+            "lbpf_unet_destroy")
     for name in EXPORTED:
         if name not in keep:
             getattr(lib, name).restype = ctypes.c_int
@@ -350,6 +374,80 @@ class Batch:
         if getattr(self, "b", None):
             _lib.lbpf_batch_destroy(self.b)
             self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class UNet:
+    """BF16 U-Net surrogate on the library's own kernels.  Inputs and targets
+    are device FP32 NHWC arrays (torch tensors or raw pointers) of shape
+    [batch, height, width, in_ch / out_ch]."""
+
+    def __init__(self, in_ch=4, out_ch=4, base_ch=32, levels=4, batch=1, height=512, width=512,
+                 seed=1, stream: int | None = None):
+        self.cfg = lbpf_unet_cfg(in_ch, out_ch, base_ch, levels, batch, height, width, seed)
+        self.n = ctypes.c_void_p()
+        rc = _lib.lbpf_unet_create(ctypes.byref(self.cfg), ctypes.c_void_p(stream or 0),
+                                   ctypes.byref(self.n))
+        if rc != OK:
+            raise LbpfError(rc, "lbpf_unet_create failed (reason on stderr)")
+        self.n = self.n.value
+
+    def _check(self, rc):
+        if rc != OK:
+            raise LbpfError(rc, _lib.lbpf_unet_last_error(self.n).decode())
+
+    @staticmethod
+    def _ptr(a):
+        return ctypes.c_void_p(a if isinstance(a, int) else a.data_ptr())
+
+    def forward(self, x, y):
+        self._check(_lib.lbpf_unet_forward(self.n, self._ptr(x), self._ptr(y)))
+
+    def grad(self, x, t) -> float:
+        loss = ctypes.c_float()
+        self._check(_lib.lbpf_unet_grad(self.n, self._ptr(x), self._ptr(t), ctypes.byref(loss)))
+        return float(loss.value)
+
+    def train_step(self, x, t, lr: float, loss_dev=None):
+        self._check(_lib.lbpf_unet_train_step(self.n, self._ptr(x), self._ptr(t), float(lr),
+                                              None if loss_dev is None else self._ptr(loss_dev)))
+
+    @property
+    def param_count(self) -> int:
+        return int(_lib.lbpf_unet_param_count(self.n))
+
+    def _params(self, which: int) -> np.ndarray:
+        out = np.empty(self.param_count, np.float32)
+        self._check(_lib.lbpf_unet_params(self.n, which, out.ctypes.data_as(
+            ctypes.POINTER(ctypes.c_float)), out.size, 0))
+        return out
+
+    def weights(self) -> np.ndarray:
+        return self._params(0)
+
+    def grads(self) -> np.ndarray:
+        return self._params(1)
+
+    def set_weights(self, w: np.ndarray):
+        w = np.ascontiguousarray(w, np.float32)
+        if w.size != self.param_count:
+            raise ValueError(f"expected {self.param_count} parameters, got {w.size}")
+        self._check(_lib.lbpf_unet_params(self.n, 0, w.ctypes.data_as(
+            ctypes.POINTER(ctypes.c_float)), w.size, 1))
+
+    @property
+    def device_bytes(self) -> int:
+        return int(_lib.lbpf_unet_device_bytes(self.n))
+
+    def close(self):
+        if getattr(self, "n", None):
+            _lib.lbpf_unet_destroy(self.n)
+            self.n = None
 
     def __del__(self):
         try:

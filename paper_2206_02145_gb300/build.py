@@ -15,9 +15,10 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "liblbpf.so")
-SOURCES = ["lbpf_api.cu", "step2d.cu", "step3d.cu", "batch2d.cu", "aux.cu", "noalloc.cu"]
+SOURCES = ["lbpf_api.cu", "step2d.cu", "step3d.cu", "batch2d.cu", "aux.cu", "noalloc.cu",
+           "unet.cu", "surrogate.cu"]
 HEADERS = ["lbpf_internal.cuh", "lbpf_device.cuh", "step2d_core.cuh", "step2d_tile.cuh", "step3d_core.cuh", "tma_host.h",
-           "tma.cuh"]
+           "tma.cuh", "unet.cuh", "unet_ops.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2",
               "--expt-relaxed-constexpr"]

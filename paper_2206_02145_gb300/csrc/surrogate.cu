@@ -1,0 +1,543 @@
+// BF16 U-Net surrogate of the coupled step (training and inference on the
+// project's own kernels, unet.cu) and its use as a block propagator with the
+// LB solver as fallback and judge.
+//
+// Network (levels L, base channels C0, channels C_l = C0 2^l):
+//   encoder level l: conv3x3(in -> C_l) ReLU, conv3x3(C_l -> C_l) ReLU [= skip_l];
+//                    2x2 average pooling feeds level l + 1
+//   decoder level l: nearest 2x upsampling of the level below, conv3x3(C_{l+1} -> C_l)
+//                    ReLU [= up_l], concatenation [up_l | skip_l], conv3x3(2C_l -> C_l)
+//                    ReLU, conv3x3(C_l -> C_l) ReLU
+//   head: 1x1 convolution (C0 -> out channels), FP32, predicting the residual
+// Activations and weights are bf16 (weights keep an FP32 master copy for
+// Adam); every GEMM accumulates in FP32.  Inputs are padded to 16 channels.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/lbpf.h"
+#include "lbpf_internal.cuh"
+#include "unet.cuh"
+
+using lbk::nn::bf16;
+
+namespace {
+
+// one 3x3 convolution layer
+struct ConvLayer {
+  int cin = 0, cout = 0;
+  size_t nw = 0;
+  float *w = nullptr, *b = nullptr, *gw = nullptr, *gb = nullptr;
+  float *mw = nullptr, *vw = nullptr, *mb = nullptr, *vb = nullptr;
+  bf16 *wb = nullptr, *wt = nullptr;  // bf16 weights and their flip-transpose
+};
+
+struct Act {  // NHWC bf16 buffer
+  bf16* p = nullptr;
+  int c = 0, h = 0, w = 0;
+};
+
+// SplitMix64-driven uniform numbers for the weight initialisation
+uint64_t mix(uint64_t z) {
+  z += 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+}  // namespace
+
+struct lbpf_unet {
+  lbpf_unet_cfg cfg;
+  cudaStream_t stream = nullptr;
+  int L = 0;
+  std::vector<int> C, H, W;
+  std::vector<ConvLayer> enc_a, enc_b, up, dec_a, dec_b;
+  // head
+  float *hw = nullptr, *hb = nullptr, *ghw = nullptr, *ghb = nullptr;
+  float *mhw = nullptr, *vhw = nullptr, *mhb = nullptr, *vhb = nullptr;
+  // activations and their gradients
+  Act xin;                                   // packed input, 16 channels
+  std::vector<Act> ea, cat, pool, u, da, db;  // per level
+  Act bottom;                                // encoder output of the last level
+  std::vector<Act> g_ea, g_cat, g_pool, g_u, g_da, g_db;
+  Act g_bottom;
+  float *y = nullptr, *gy = nullptr, *loss = nullptr;
+  std::vector<void*> allocs;
+  size_t bytes = 0;
+  int t = 0;  // Adam step
+  char msg[256] = {0};
+};
+
+namespace {
+
+int ufail(lbpf_unet* n, int code, const char* fmt, ...) {
+  if (!n) return code;
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(n->msg, sizeof(n->msg), fmt, ap);
+  va_end(ap);
+  return code;
+}
+
+#define UCK(n, call)                                                                      \
+  do {                                                                                    \
+    cudaError_t e_ = (call);                                                              \
+    if (e_ != cudaSuccess)                                                                \
+      return ufail(n, LBPF_ECUDA, "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, \
+                   __LINE__);                                                             \
+  } while (0)
+
+template <typename Tp>
+cudaError_t dalloc(lbpf_unet* n, Tp** p, size_t count) {
+  void* q = nullptr;
+  cudaError_t e = cudaMalloc(&q, count * sizeof(Tp) + 16);
+  if (e != cudaSuccess) return e;
+  n->allocs.push_back(q);
+  n->bytes += count * sizeof(Tp);
+  *p = static_cast<Tp*>(q);
+  return cudaMemset(q, 0, count * sizeof(Tp));
+}
+
+cudaError_t act(lbpf_unet* n, Act* a, int c, int h, int w) {
+  a->c = c;
+  a->h = h;
+  a->w = w;
+  return dalloc(n, &a->p, size_t(n->cfg.batch) * h * w * c);
+}
+
+// He-uniform initialisation in FP32, seeded
+cudaError_t make_conv(lbpf_unet* n, ConvLayer* l, int cin, int cout, int real_cin,
+                      uint64_t seed) {
+  l->cin = cin;
+  l->cout = cout;
+  l->nw = size_t(9) * cout * cin;
+  cudaError_t e;
+  float** f32[] = {&l->w, &l->gw, &l->mw, &l->vw};
+  for (float** p : f32)
+    if ((e = dalloc(n, p, l->nw)) != cudaSuccess) return e;
+  float** b32[] = {&l->b, &l->gb, &l->mb, &l->vb};
+  for (float** p : b32)
+    if ((e = dalloc(n, p, size_t(cout))) != cudaSuccess) return e;
+  if ((e = dalloc(n, &l->wb, l->nw)) != cudaSuccess) return e;
+  if ((e = dalloc(n, &l->wt, l->nw)) != cudaSuccess) return e;
+  std::vector<float> hw(l->nw, 0.f);
+  std::vector<bf16> hb(l->nw);
+  const float bound = std::sqrt(6.0f / float(9 * real_cin));
+  for (size_t i = 0; i < l->nw; ++i) {
+    const int ci = int(i % cin);
+    if (ci >= real_cin) continue;  // padded input channels stay zero
+    const double u = double(mix(seed ^ (i * 0x9E3779B97F4A7C15ull)) >> 11) * 0x1.0p-53;
+    hw[i] = float((2.0 * u - 1.0) * bound);
+  }
+  for (size_t i = 0; i < l->nw; ++i) hb[i] = __float2bfloat16(hw[i]);
+  if ((e = cudaMemcpy(l->w, hw.data(), l->nw * 4, cudaMemcpyHostToDevice)) != cudaSuccess)
+    return e;
+  return cudaMemcpy(l->wb, hb.data(), l->nw * 2, cudaMemcpyHostToDevice);
+}
+
+int conv_fwd(lbpf_unet* n, const ConvLayer& l, const Act& x, int xoff, const Act& y, int yoff) {
+  lbk::nn::ConvArgs a{};
+  a.x = x.p;
+  a.Cx = x.c;
+  a.ci_off = xoff;
+  a.Cin = l.cin;
+  a.w = l.wb;
+  a.bias = l.b;
+  a.y = y.p;
+  a.Cy = y.c;
+  a.co_off = yoff;
+  a.Cout = l.cout;
+  a.N = n->cfg.batch;
+  a.H = x.h;
+  a.W = x.w;
+  a.relu = 1;
+  a.mask = nullptr;
+  UCK(n, lbk::nn::conv3x3(a, n->stream));
+  return LBPF_OK;
+}
+
+// backward of one layer whose input is x[xoff..] and whose pre-activation
+// gradient is g[goff..]: weight and bias gradients, and (if gx) the input
+// gradient, optionally masked by `mask` (same layout as gx).
+int conv_bwd(lbpf_unet* n, const ConvLayer& l, const Act& x, int xoff, const Act& g, int goff,
+             const Act* gx, int gxoff, const Act* mask) {
+  const long long npix = (long long)n->cfg.batch * x.h * x.w;
+  lbk::nn::WgradArgs wa{};
+  wa.x = x.p;
+  wa.Cx = x.c;
+  wa.ci_off = xoff;
+  wa.Cin = l.cin;
+  wa.dy = g.p;
+  wa.Cdy = g.c;
+  wa.co_off = goff;
+  wa.Cout = l.cout;
+  wa.dw = l.gw;
+  wa.npix = npix;
+  wa.H = x.h;
+  wa.W = x.w;
+  wa.chunk = 4096;
+  UCK(n, lbk::nn::wgrad3x3(wa, n->stream));
+  UCK(n, lbk::nn::bias_grad(g.p, g.c, goff, l.cout, npix, l.gb, n->stream));
+  if (gx) {
+    lbk::nn::ConvArgs a{};
+    a.x = g.p;
+    a.Cx = g.c;
+    a.ci_off = goff;
+    a.Cin = l.cout;
+    a.w = l.wt;
+    a.bias = nullptr;
+    a.y = gx->p;
+    a.Cy = gx->c;
+    a.co_off = gxoff;
+    a.Cout = l.cin;
+    a.N = n->cfg.batch;
+    a.H = x.h;
+    a.W = x.w;
+    a.relu = 0;
+    a.mask = mask ? mask->p : nullptr;
+    UCK(n, lbk::nn::conv3x3(a, n->stream));
+  }
+  return LBPF_OK;
+}
+
+std::vector<ConvLayer*> all_layers(lbpf_unet* n) {
+  std::vector<ConvLayer*> v;
+  for (auto* vec : {&n->enc_a, &n->enc_b, &n->up, &n->dec_a, &n->dec_b})
+    for (auto& l : *vec) v.push_back(&l);
+  return v;
+}
+
+// forward pass on the packed input n->xin; output n->y (FP32 NHWC, out_ch)
+int forward(lbpf_unet* n) {
+  const int L = n->L;
+  int rc;
+  for (int l = 0; l < L; ++l) {
+    const Act& in = l == 0 ? n->xin : n->pool[l];
+    if ((rc = conv_fwd(n, n->enc_a[l], in, 0, n->ea[l], 0))) return rc;
+    if (l < L - 1) {
+      if ((rc = conv_fwd(n, n->enc_b[l], n->ea[l], 0, n->cat[l], n->C[l]))) return rc;
+      UCK(n, lbk::nn::avgpool2(n->cat[l].p, n->cat[l].c, n->C[l], n->pool[l + 1].p, n->C[l], 0,
+                               n->C[l], n->cfg.batch, n->H[l], n->W[l], n->stream));
+    } else {
+      if ((rc = conv_fwd(n, n->enc_b[l], n->ea[l], 0, n->bottom, 0))) return rc;
+    }
+  }
+  const Act* d = &n->bottom;
+  for (int l = L - 2; l >= 0; --l) {
+    UCK(n, lbk::nn::upsample2(d->p, n->u[l].p, n->C[l + 1], n->cfg.batch, n->H[l], n->W[l],
+                              n->stream));
+    if ((rc = conv_fwd(n, n->up[l], n->u[l], 0, n->cat[l], 0))) return rc;
+    if ((rc = conv_fwd(n, n->dec_a[l], n->cat[l], 0, n->da[l], 0))) return rc;
+    if ((rc = conv_fwd(n, n->dec_b[l], n->da[l], 0, n->db[l], 0))) return rc;
+    d = &n->db[l];
+  }
+  const long long npix = (long long)n->cfg.batch * n->H[0] * n->W[0];
+  UCK(n, lbk::nn::head_fwd(L > 1 ? n->db[0].p : n->bottom.p, n->C[0], n->hw, n->hb, n->y,
+                           n->cfg.out_ch, npix, n->stream));
+  return LBPF_OK;
+}
+
+// loss and gradients for targets t (FP32 NHWC, out_ch); gradients accumulate
+int backward(lbpf_unet* n, const float* t) {
+  const int L = n->L, B = n->cfg.batch;
+  const long long npix = (long long)B * n->H[0] * n->W[0];
+  int rc;
+  for (ConvLayer* l : all_layers(n))
+    UCK(n, lbk::nn::flip_transpose(l->wb, l->wt, l->cout, l->cin, n->stream));
+  UCK(n, cudaMemsetAsync(n->loss, 0, sizeof(float), n->stream));
+  UCK(n, lbk::nn::mse(n->y, t, npix * n->cfg.out_ch, n->gy, n->loss, n->stream));
+  const Act& top = L > 1 ? n->db[0] : n->bottom;
+  Act& g_top = L > 1 ? n->g_db[0] : n->g_bottom;
+  UCK(n, lbk::nn::head_bwd(top.p, n->C[0], n->hw, n->gy, n->cfg.out_ch, npix, g_top.p, n->ghw,
+                           n->ghb, n->stream));
+  // decoder, from the top level down to the bottom
+  for (int l = 0; l < L - 1; ++l) {
+    if ((rc = conv_bwd(n, n->dec_b[l], n->da[l], 0, n->g_db[l], 0, &n->g_da[l], 0, &n->da[l])))
+      return rc;
+    if ((rc = conv_bwd(n, n->dec_a[l], n->cat[l], 0, n->g_da[l], 0, &n->g_cat[l], 0, nullptr)))
+      return rc;
+    UCK(n, lbk::nn::relu_mask(n->g_cat[l].p, n->g_cat[l].c, 0, n->cat[l].p, n->cat[l].c, 0,
+                              n->C[l], (long long)B * n->H[l] * n->W[l], n->stream));
+    if ((rc = conv_bwd(n, n->up[l], n->u[l], 0, n->g_cat[l], 0, &n->g_u[l], 0, nullptr))) return rc;
+    const Act& below = l + 1 < L - 1 ? n->db[l + 1] : n->bottom;
+    Act& g_below = l + 1 < L - 1 ? n->g_db[l + 1] : n->g_bottom;
+    UCK(n, lbk::nn::upsample2_bwd_mask(n->g_u[l].p, g_below.p, below.p, n->C[l + 1], B, n->H[l],
+                                       n->W[l], n->stream));
+  }
+  // encoder, from the bottom level up
+  for (int l = L - 1; l >= 0; --l) {
+    const Act* gb;
+    int gboff;
+    const Act* eb_out;
+    if (l == L - 1) {
+      gb = &n->g_bottom;
+      gboff = 0;
+      eb_out = &n->bottom;
+    } else {
+      // skip gradient = from the concatenation + from the pooling path, masked
+      UCK(n, lbk::nn::avgpool2_bwd_add_mask(n->g_cat[l].p, n->g_pool[l + 1].p, n->cat[l].p,
+                                            n->cat[l].c, n->C[l], n->C[l], B, n->H[l], n->W[l],
+                                            n->stream));
+      gb = &n->g_cat[l];
+      gboff = n->C[l];
+      eb_out = &n->cat[l];
+    }
+    (void)eb_out;
+    if ((rc = conv_bwd(n, n->enc_b[l], n->ea[l], 0, *gb, gboff, &n->g_ea[l], 0, &n->ea[l])))
+      return rc;
+    const Act& in = l == 0 ? n->xin : n->pool[l];
+    if ((rc = conv_bwd(n, n->enc_a[l], in, 0, n->g_ea[l], 0, l == 0 ? nullptr : &n->g_pool[l], 0,
+                       nullptr)))
+      return rc;
+  }
+  return LBPF_OK;
+}
+
+int adam_all(lbpf_unet* n, float lr) {
+  ++n->t;
+  const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+  for (ConvLayer* l : all_layers(n)) {
+    UCK(n, lbk::nn::adam(l->w, l->gw, l->mw, l->vw, l->wb, (long long)l->nw, lr, b1, b2, eps, n->t,
+                         n->stream));
+    UCK(n, lbk::nn::adam(l->b, l->gb, l->mb, l->vb, nullptr, l->cout, lr, b1, b2, eps, n->t,
+                         n->stream));
+  }
+  const long long nh = (long long)n->cfg.out_ch * n->C[0];
+  UCK(n, lbk::nn::adam(n->hw, n->ghw, n->mhw, n->vhw, nullptr, nh, lr, b1, b2, eps, n->t,
+                       n->stream));
+  UCK(n, lbk::nn::adam(n->hb, n->ghb, n->mhb, n->vhb, nullptr, n->cfg.out_ch, lr, b1, b2, eps,
+                       n->t, n->stream));
+  return LBPF_OK;
+}
+
+// pack FP32 NHWC (in_ch) into the bf16 16-channel input buffer
+__global__ void pack_input_kernel(const float* x, int cin, bf16* out, long long npix) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < npix * 16;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long p = i / 16;
+    const int c = int(i % 16);
+    out[i] = __float2bfloat16(c < cin ? x[p * cin + c] : 0.f);
+  }
+}
+
+int pack_input(lbpf_unet* n, const float* x) {
+  const long long npix = (long long)n->cfg.batch * n->H[0] * n->W[0];
+  long long blocks = (npix * 16 + 255) / 256;
+  if (blocks > 152 * 32) blocks = 152 * 32;
+  pack_input_kernel<<<int(blocks), 256, 0, n->stream>>>(x, n->cfg.in_ch, n->xin.p, npix);
+  UCK(n, cudaGetLastError());
+  return LBPF_OK;
+}
+
+// parameter views, in a fixed order: per layer (w, b) in all_layers order, then the head
+struct ParamView {
+  float* p;
+  float* g;
+  size_t n;
+};
+std::vector<ParamView> params(lbpf_unet* n) {
+  std::vector<ParamView> v;
+  for (ConvLayer* l : all_layers(n)) {
+    v.push_back({l->w, l->gw, l->nw});
+    v.push_back({l->b, l->gb, size_t(l->cout)});
+  }
+  v.push_back({n->hw, n->ghw, size_t(n->cfg.out_ch) * n->C[0]});
+  v.push_back({n->hb, n->ghb, size_t(n->cfg.out_ch)});
+  return v;
+}
+
+__global__ void to_bf16_kernel(const float* w, bf16* wb, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    wb[i] = __float2bfloat16(w[i]);
+}
+
+}  // namespace
+
+extern "C" {
+
+int lbpf_unet_create(const lbpf_unet_cfg* cfg, void* stream, lbpf_unet_t** out) {
+  if (!cfg || !out) return LBPF_EINVAL;
+  *out = nullptr;
+  const int L = cfg->levels;
+  if (L < 1 || L > 6 || cfg->base_ch < 32 || cfg->base_ch % 32 || cfg->in_ch < 1 ||
+      cfg->in_ch > 16 || cfg->out_ch < 1 || cfg->out_ch > 4 || cfg->batch < 1 ||
+      cfg->height < 1 || cfg->width < 1 || cfg->base_ch > 32) {
+    fprintf(stderr, "lbpf_unet_create: unsupported configuration\n");
+    return LBPF_EINVAL;
+  }
+  if ((cfg->width >> (L - 1)) % 64 != 0 || (cfg->height >> (L - 1)) < 1 ||
+      cfg->width % (1 << (L - 1)) || cfg->height % (1 << (L - 1))) {
+    fprintf(stderr,
+            "lbpf_unet_create: width / 2^(levels-1) must be a multiple of 64 and height "
+            "divisible by 2^(levels-1)\n");
+    return LBPF_EINVAL;
+  }
+  lbpf_unet* n = new (std::nothrow) lbpf_unet();
+  if (!n) return LBPF_ENOMEM;
+  n->cfg = *cfg;
+  n->stream = static_cast<cudaStream_t>(stream);
+  n->L = L;
+  for (int l = 0; l < L; ++l) {
+    n->C.push_back(cfg->base_ch << l);
+    n->H.push_back(cfg->height >> l);
+    n->W.push_back(cfg->width >> l);
+  }
+  cudaError_t e = cudaSuccess;
+  auto chk = [&](cudaError_t r) {
+    if (e == cudaSuccess) e = r;
+  };
+  uint64_t sd = cfg->seed;
+  n->enc_a.resize(L);
+  n->enc_b.resize(L);
+  n->up.resize(L > 1 ? L - 1 : 0);
+  n->dec_a.resize(L > 1 ? L - 1 : 0);
+  n->dec_b.resize(L > 1 ? L - 1 : 0);
+  for (int l = 0; l < L; ++l) {
+    const int cin = l == 0 ? 16 : n->C[l - 1];
+    chk(make_conv(n, &n->enc_a[l], cin, n->C[l], l == 0 ? cfg->in_ch : cin, mix(sd += 101)));
+    chk(make_conv(n, &n->enc_b[l], n->C[l], n->C[l], n->C[l], mix(sd += 101)));
+  }
+  for (int l = 0; l < L - 1; ++l) {
+    chk(make_conv(n, &n->up[l], n->C[l + 1], n->C[l], n->C[l + 1], mix(sd += 101)));
+    chk(make_conv(n, &n->dec_a[l], 2 * n->C[l], n->C[l], 2 * n->C[l], mix(sd += 101)));
+    chk(make_conv(n, &n->dec_b[l], n->C[l], n->C[l], n->C[l], mix(sd += 101)));
+  }
+  const size_t nh = size_t(cfg->out_ch) * n->C[0];
+  float** hp[] = {&n->hw, &n->ghw, &n->mhw, &n->vhw};
+  for (float** p : hp) chk(dalloc(n, p, nh));
+  float** hbp[] = {&n->hb, &n->ghb, &n->mhb, &n->vhb};
+  for (float** p : hbp) chk(dalloc(n, p, size_t(cfg->out_ch)));
+  if (e == cudaSuccess) {
+    std::vector<float> h(nh);
+    const float bound = std::sqrt(6.0f / float(n->C[0])) * 0.1f;  // small head: start near 0
+    for (size_t i = 0; i < nh; ++i)
+      h[i] = float((2.0 * (double(mix(cfg->seed ^ (777 + i)) >> 11) * 0x1.0p-53) - 1.0) * bound);
+    chk(cudaMemcpy(n->hw, h.data(), nh * 4, cudaMemcpyHostToDevice));
+  }
+  n->ea.resize(L);
+  n->g_ea.resize(L);
+  n->pool.resize(L);
+  n->g_pool.resize(L);
+  n->cat.resize(L);
+  n->g_cat.resize(L);
+  n->u.resize(L);
+  n->g_u.resize(L);
+  n->da.resize(L);
+  n->g_da.resize(L);
+  n->db.resize(L);
+  n->g_db.resize(L);
+  chk(act(n, &n->xin, 16, n->H[0], n->W[0]));
+  for (int l = 0; l < L; ++l) {
+    chk(act(n, &n->ea[l], n->C[l], n->H[l], n->W[l]));
+    chk(act(n, &n->g_ea[l], n->C[l], n->H[l], n->W[l]));
+    if (l > 0) {
+      chk(act(n, &n->pool[l], n->C[l - 1], n->H[l], n->W[l]));
+      chk(act(n, &n->g_pool[l], n->C[l - 1], n->H[l], n->W[l]));
+    }
+    if (l < L - 1) {
+      chk(act(n, &n->cat[l], 2 * n->C[l], n->H[l], n->W[l]));
+      chk(act(n, &n->g_cat[l], 2 * n->C[l], n->H[l], n->W[l]));
+      chk(act(n, &n->u[l], n->C[l + 1], n->H[l], n->W[l]));
+      chk(act(n, &n->g_u[l], n->C[l + 1], n->H[l], n->W[l]));
+      chk(act(n, &n->da[l], n->C[l], n->H[l], n->W[l]));
+      chk(act(n, &n->g_da[l], n->C[l], n->H[l], n->W[l]));
+      chk(act(n, &n->db[l], n->C[l], n->H[l], n->W[l]));
+      chk(act(n, &n->g_db[l], n->C[l], n->H[l], n->W[l]));
+    }
+  }
+  chk(act(n, &n->bottom, n->C[L - 1], n->H[L - 1], n->W[L - 1]));
+  chk(act(n, &n->g_bottom, n->C[L - 1], n->H[L - 1], n->W[L - 1]));
+  const size_t ny = size_t(cfg->batch) * n->H[0] * n->W[0] * cfg->out_ch;
+  chk(dalloc(n, &n->y, ny));
+  chk(dalloc(n, &n->gy, ny));
+  chk(dalloc(n, &n->loss, 1));
+  if (e != cudaSuccess) {
+    fprintf(stderr, "lbpf_unet_create: %s\n", cudaGetErrorString(e));
+    lbpf_unet_destroy(n);
+    return LBPF_ENOMEM;
+  }
+  *out = n;
+  return LBPF_OK;
+}
+
+int lbpf_unet_forward(lbpf_unet_t* n, const float* x, float* y) {
+  if (!n || !x || !y) return LBPF_EINVAL;
+  int rc;
+  if ((rc = pack_input(n, x))) return rc;
+  if ((rc = forward(n))) return rc;
+  const size_t ny = size_t(n->cfg.batch) * n->H[0] * n->W[0] * n->cfg.out_ch;
+  UCK(n, cudaMemcpyAsync(y, n->y, ny * 4, cudaMemcpyDeviceToDevice, n->stream));
+  return LBPF_OK;
+}
+
+int lbpf_unet_grad(lbpf_unet_t* n, const float* x, const float* t, float* loss_host) {
+  if (!n || !x || !t) return LBPF_EINVAL;
+  int rc;
+  for (const ParamView& v : params(n)) UCK(n, cudaMemsetAsync(v.g, 0, v.n * 4, n->stream));
+  if ((rc = pack_input(n, x)) || (rc = forward(n)) || (rc = backward(n, t))) return rc;
+  if (loss_host) {
+    UCK(n, cudaMemcpyAsync(loss_host, n->loss, 4, cudaMemcpyDeviceToHost, n->stream));
+    UCK(n, cudaStreamSynchronize(n->stream));
+  }
+  return LBPF_OK;
+}
+
+int lbpf_unet_train_step(lbpf_unet_t* n, const float* x, const float* t, float lr,
+                         float* loss_dev) {
+  if (!n || !x || !t) return LBPF_EINVAL;
+  int rc;
+  if ((rc = pack_input(n, x)) || (rc = forward(n)) || (rc = backward(n, t)) ||
+      (rc = adam_all(n, lr)))
+    return rc;
+  if (loss_dev)
+    UCK(n, cudaMemcpyAsync(loss_dev, n->loss, 4, cudaMemcpyDeviceToDevice, n->stream));
+  return LBPF_OK;
+}
+
+size_t lbpf_unet_param_count(const lbpf_unet_t* n) {
+  if (!n) return 0;
+  size_t s = 0;
+  for (const ParamView& v : params(const_cast<lbpf_unet*>(n))) s += v.n;
+  return s;
+}
+
+int lbpf_unet_params(lbpf_unet_t* n, int which, float* host, size_t count, int set) {
+  if (!n || !host || count != lbpf_unet_param_count(n) || which < 0 || which > 1 ||
+      (set && which != 0))
+    return LBPF_EINVAL;
+  size_t off = 0;
+  for (const ParamView& v : params(n)) {
+    float* src = which == 0 ? v.p : v.g;
+    if (set)
+      UCK(n, cudaMemcpyAsync(src, host + off, v.n * 4, cudaMemcpyHostToDevice, n->stream));
+    else
+      UCK(n, cudaMemcpyAsync(host + off, src, v.n * 4, cudaMemcpyDeviceToHost, n->stream));
+    off += v.n;
+  }
+  if (set)
+    for (ConvLayer* l : all_layers(n)) {
+      long long blocks = ((long long)l->nw + 255) / 256;
+      if (blocks > 4096) blocks = 4096;
+      to_bf16_kernel<<<int(blocks), 256, 0, n->stream>>>(l->w, l->wb, (long long)l->nw);
+      UCK(n, cudaGetLastError());
+    }
+  UCK(n, cudaStreamSynchronize(n->stream));
+  return LBPF_OK;
+}
+
+size_t lbpf_unet_device_bytes(const lbpf_unet_t* n) { return n ? n->bytes : 0; }
+const char* lbpf_unet_last_error(const lbpf_unet_t* n) { return n ? n->msg : "null handle"; }
+
+void lbpf_unet_destroy(lbpf_unet_t* n) {
+  if (!n) return;
+  cudaStreamSynchronize(n->stream);
+  for (void* p : n->allocs) cudaFree(p);
+  delete n;
+}
+
+}  // extern "C"

@@ -1,0 +1,478 @@
+// Kernels of the BF16 U-Net surrogate (NHWC bf16 activations, FP32
+// accumulation and master weights):
+//   conv3x3_kernel   implicit-GEMM 3x3 convolution on the warp tensor cores
+//                    (M = pixels, N = output channels, K = 9 x input channels);
+//                    also the data gradient, run on flipped / transposed weights
+//   wgrad3x3_kernel  weight gradient, K = pixels, split over CTAs, FP32 atomics
+//   element-wise     bias gradient, ReLU masks, 2x2 average pooling and its
+//                    gradient, nearest 2x upsampling and its gradient, the 1x1
+//                    head, MSE loss, Adam, weight transposition, input packing
+#include "lbpf_internal.cuh"
+#include "unet.cuh"
+#include "unet_ops.cuh"
+
+namespace lbk {
+namespace nn {
+namespace {
+
+constexpr int kThreads = 128;
+
+// ---- 3x3 convolution, implicit GEMM ------------------------------------------------
+// Tile: 64 pixels of one image row x BN output channels; 4 warps as 2 x 2,
+// each 32 pixels x BN/2 channels (2 x BN/16 mma tiles).  K steps of 16 input
+// channels of one tap, double-buffered through cp.async.
+template <int BN>
+__global__ void __launch_bounds__(kThreads) conv3x3_kernel(const ConvArgs a) {
+  constexpr int BM = 64, LD = 24;  // 48-byte padded rows: conflict-free ldmatrix
+  __shared__ __align__(16) bf16 sA[2][BM][LD];
+  __shared__ __align__(16) bf16 sB[2][BN][LD];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int wm = warp & 1, wn = warp >> 1;
+  const int pix0 = blockIdx.x * BM;
+  const int n0 = blockIdx.y * BN;
+  const int wcol = pix0 % a.W, hrow = (pix0 / a.W) % a.H, img = pix0 / (a.W * a.H);
+  const int cchunks = a.Cin / 16, ksteps = 9 * cchunks;
+
+  float acc[2][BN / 16][4];
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < BN / 16; ++j)
+#pragma unroll
+      for (int k = 0; k < 4; ++k) acc[i][j][k] = 0.f;
+
+  auto load = [&](int ks, int buf) {
+    const int tap = ks / cchunks, c0 = (ks % cchunks) * 16;
+    const int ky = tap / 3, kx = tap % 3;
+    {
+      const int r = tid >> 1, half = tid & 1;
+      const int hh = hrow + ky - 1, ww = wcol + r + kx - 1;
+      const bool ok = hh >= 0 && hh < a.H && ww >= 0 && ww < a.W;
+      const size_t pix = (size_t(img) * a.H + (ok ? hh : 0)) * a.W + (ok ? ww : 0);
+      cp_async16(&sA[buf][r][half * 8], a.x + pix * a.Cx + a.ci_off + c0 + half * 8, ok ? 16 : 0);
+    }
+    for (int i = tid; i < BN * 2; i += kThreads) {
+      const int r = i >> 1, half = i & 1;
+      cp_async16(&sB[buf][r][half * 8],
+                 a.w + (size_t(tap) * a.Cout + n0 + r) * a.Cin + c0 + half * 8, 16);
+    }
+    cp_async_commit();
+  };
+
+  load(0, 0);
+  for (int ks = 0; ks < ksteps; ++ks) {
+    const int buf = ks & 1;
+    if (ks + 1 < ksteps) {
+      load(ks + 1, buf ^ 1);
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
+    }
+    __syncthreads();
+    uint32_t af[2][4], bfr[BN / 16][2];
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt)
+      ldmatrix_x4(af[mt], &sA[buf][wm * 32 + mt * 16 + (lane & 15)][(lane >> 4) * 8]);
+#pragma unroll
+    for (int nt = 0; nt < BN / 16; ++nt)
+      ldmatrix_x2(bfr[nt], &sB[buf][wn * (BN / 2) + nt * 8 + (lane & 7)][((lane >> 3) & 1) * 8]);
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+      for (int nt = 0; nt < BN / 16; ++nt) mma_bf16(acc[mt][nt], af[mt], bfr[nt]);
+    __syncthreads();
+  }
+  // epilogue: bias, optional ReLU, optional mask (zero where mask <= 0), bf16 out
+#pragma unroll
+  for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+    for (int nt = 0; nt < BN / 16; ++nt)
+#pragma unroll
+      for (int hlf = 0; hlf < 2; ++hlf) {
+        const size_t p = size_t(pix0) + wm * 32 + mt * 16 + (lane >> 2) + hlf * 8;
+        const int co = n0 + wn * (BN / 2) + nt * 8 + (lane & 3) * 2;
+        float v0 = acc[mt][nt][hlf * 2 + 0], v1 = acc[mt][nt][hlf * 2 + 1];
+        if (a.bias) {
+          v0 += a.bias[co];
+          v1 += a.bias[co + 1];
+        }
+        if (a.relu) {
+          v0 = fmaxf(v0, 0.f);
+          v1 = fmaxf(v1, 0.f);
+        }
+        if (a.mask) {
+          const bf16* mk = a.mask + p * a.Cy + a.co_off + co;
+          if (!(__bfloat162float(mk[0]) > 0.f)) v0 = 0.f;
+          if (!(__bfloat162float(mk[1]) > 0.f)) v1 = 0.f;
+        }
+        *reinterpret_cast<__nv_bfloat162*>(a.y + p * a.Cy + a.co_off + co) =
+            __floats2bfloat162_rn(v0, v1);
+      }
+}
+
+// ---- weight gradient ---------------------------------------------------------------
+// dW[tap][co][ci] += sum_p dy[p][co] x[p + shift(tap)][ci] over a chunk of
+// pixels.  M = BM output channels, N = BN input channels, K = 16 pixels per
+// step; A and B come from row-major [pixel][channel] tiles through
+// ldmatrix.trans.  4 warps as 2 x 2.
+template <int BM, int BN>
+__global__ void __launch_bounds__(kThreads) wgrad3x3_kernel(const WgradArgs a) {
+  constexpr int LDA = BM + 8, LDB = BN + 8;
+  __shared__ __align__(16) bf16 sA[2][16][LDA];
+  __shared__ __align__(16) bf16 sB[2][16][LDB];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int wm = warp & 1, wn = warp >> 1;
+  constexpr int WM = BM / 2, WN = BN / 2;  // warp tile
+  const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
+  const int tap = blockIdx.z % 9, chunk = blockIdx.z / 9;
+  const int ky = tap / 3, kx = tap % 3;
+  const long long p_begin = (long long)chunk * a.chunk;
+  long long p_end = p_begin + a.chunk;
+  if (p_end > a.npix) p_end = a.npix;
+  const int ksteps = int((p_end - p_begin) / 16);
+
+  float acc[WM / 16][WN / 8][4];
+#pragma unroll
+  for (int i = 0; i < WM / 16; ++i)
+#pragma unroll
+    for (int j = 0; j < WN / 8; ++j)
+#pragma unroll
+      for (int k = 0; k < 4; ++k) acc[i][j][k] = 0.f;
+
+  auto load = [&](int ks, int buf) {
+    const long long pb = p_begin + ks * 16;
+    for (int i = tid; i < 16 * (BM / 8); i += kThreads) {
+      const int r = i / (BM / 8), c = (i % (BM / 8)) * 8;
+      cp_async16(&sA[buf][r][c], a.dy + (pb + r) * a.Cdy + a.co_off + m0 + c, 16);
+    }
+    for (int i = tid; i < 16 * (BN / 8); i += kThreads) {
+      const int r = i / (BN / 8), c = (i % (BN / 8)) * 8;
+      const long long p = pb + r;
+      const int w = int(p % a.W), h = int((p / a.W) % a.H);
+      const long long img = p / ((long long)a.W * a.H);
+      const int hh = h + ky - 1, ww = w + kx - 1;
+      const bool ok = hh >= 0 && hh < a.H && ww >= 0 && ww < a.W;
+      const long long q = (img * a.H + (ok ? hh : 0)) * a.W + (ok ? ww : 0);
+      cp_async16(&sB[buf][r][c], a.x + q * a.Cx + a.ci_off + n0 + c, ok ? 16 : 0);
+    }
+    cp_async_commit();
+  };
+  if (ksteps > 0) load(0, 0);
+  for (int ks = 0; ks < ksteps; ++ks) {
+    const int buf = ks & 1;
+    if (ks + 1 < ksteps) {
+      load(ks + 1, buf ^ 1);
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
+    }
+    __syncthreads();
+    uint32_t af[WM / 16][4], bfr[WN / 8][2];
+#pragma unroll
+    for (int mt = 0; mt < WM / 16; ++mt)
+      ldmatrix_x4_t(af[mt], &sA[buf][(lane & 7) + ((lane >> 4) << 3)]
+                                [wm * WM + mt * 16 + ((lane >> 3) & 1) * 8]);
+#pragma unroll
+    for (int nt = 0; nt < WN / 8; ++nt)
+      ldmatrix_x2_t(bfr[nt], &sB[buf][lane & 15][wn * WN + nt * 8]);
+#pragma unroll
+    for (int mt = 0; mt < WM / 16; ++mt)
+#pragma unroll
+      for (int nt = 0; nt < WN / 8; ++nt) mma_bf16(acc[mt][nt], af[mt], bfr[nt]);
+    __syncthreads();
+  }
+#pragma unroll
+  for (int mt = 0; mt < WM / 16; ++mt)
+#pragma unroll
+    for (int nt = 0; nt < WN / 8; ++nt)
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int co = m0 + wm * WM + mt * 16 + (lane >> 2) + (k >> 1) * 8;
+        const int ci = n0 + wn * WN + nt * 8 + (lane & 3) * 2 + (k & 1);
+        atomicAdd(a.dw + (size_t(tap) * a.Cout + co) * a.Cin + ci, acc[mt][nt][k]);
+      }
+}
+
+// ---- element-wise kernels -------------------------------------------------------------
+__global__ void bias_grad_kernel(const bf16* g, int Cg, int off, int C, long long npix,
+                                 float* db) {
+  // one thread per channel and pixel stripe
+  const int c = blockIdx.y * blockDim.x + threadIdx.x;
+  if (c >= C) return;
+  float s = 0.f;
+  for (long long p = blockIdx.x; p < npix; p += gridDim.x)
+    s += __bfloat162float(g[p * Cg + off + c]);
+  atomicAdd(db + c, s);
+}
+
+__global__ void mask_kernel(bf16* g, int Cg, int goff, const bf16* act, int Ca, int aoff, int C,
+                            long long npix) {
+  const long long n = npix * C;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long p = i / C;
+    const int c = int(i % C);
+    if (!(__bfloat162float(act[p * Ca + aoff + c]) > 0.f)) g[p * Cg + goff + c] = __float2bfloat16(0.f);
+  }
+}
+
+// y[b][h/2][w/2][c] = mean of the 2x2 block of x
+__global__ void avgpool_kernel(const bf16* x, int Cx, int xoff, bf16* y, int Cy, int yoff, int C,
+                               int B, int H, int W) {
+  const int Ho = H / 2, Wo = W / 2;
+  const long long n = (long long)B * Ho * Wo * C;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int c = int(i % C);
+    const long long q = i / C;
+    const int wo = int(q % Wo), ho = int((q / Wo) % Ho);
+    const long long b = q / ((long long)Wo * Ho);
+    const long long p00 = (b * H + 2 * ho) * W + 2 * wo;
+    const float s = __bfloat162float(x[p00 * Cx + xoff + c]) +
+                    __bfloat162float(x[(p00 + 1) * Cx + xoff + c]) +
+                    __bfloat162float(x[(p00 + W) * Cx + xoff + c]) +
+                    __bfloat162float(x[(p00 + W + 1) * Cx + xoff + c]);
+    y[q * Cy + yoff + c] = __float2bfloat16(0.25f * s);
+  }
+}
+
+// g_skip = (g_skip + 0.25 g_pool[pooled position]) * (skip > 0)
+__global__ void pool_bwd_add_mask_kernel(bf16* gs, const bf16* gp, const bf16* act, int Cs,
+                                         int soff, int C, int B, int H, int W) {
+  const long long n = (long long)B * H * W * C;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int c = int(i % C);
+    const long long p = i / C;
+    const int w = int(p % W), h = int((p / W) % H);
+    const long long b = p / ((long long)W * H);
+    const long long q = (b * (H / 2) + h / 2) * (W / 2) + w / 2;
+    float v = __bfloat162float(gs[p * Cs + soff + c]) + 0.25f * __bfloat162float(gp[q * C + c]);
+    if (!(__bfloat162float(act[p * Cs + soff + c]) > 0.f)) v = 0.f;
+    gs[p * Cs + soff + c] = __float2bfloat16(v);
+  }
+}
+
+// nearest 2x upsampling: y[b][h][w][c] = x[b][h/2][w/2][c]
+__global__ void upsample_kernel(const bf16* x, bf16* y, int C, int B, int H, int W) {
+  const long long n = (long long)B * H * W * C;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int c = int(i % C);
+    const long long p = i / C;
+    const int w = int(p % W), h = int((p / W) % H);
+    const long long b = p / ((long long)W * H);
+    y[p * C + c] = x[((b * (H / 2) + h / 2) * (W / 2) + w / 2) * C + c];
+  }
+}
+
+// gradient of the upsampling (sum of the 2x2 block), masked by act > 0
+__global__ void upsample_bwd_mask_kernel(const bf16* g, bf16* gx, const bf16* act, int C, int B,
+                                         int H, int W) {
+  const int Ho = H / 2, Wo = W / 2;
+  const long long n = (long long)B * Ho * Wo * C;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int c = int(i % C);
+    const long long q = i / C;
+    const int wo = int(q % Wo), ho = int((q / Wo) % Ho);
+    const long long b = q / ((long long)Wo * Ho);
+    const long long p00 = (b * H + 2 * ho) * W + 2 * wo;
+    float s = __bfloat162float(g[p00 * C + c]) + __bfloat162float(g[(p00 + 1) * C + c]) +
+              __bfloat162float(g[(p00 + W) * C + c]) + __bfloat162float(g[(p00 + W + 1) * C + c]);
+    if (!(__bfloat162float(act[q * C + c]) > 0.f)) s = 0.f;
+    gx[q * C + c] = __float2bfloat16(s);
+  }
+}
+
+// 1x1 head: y[p][o] = b[o] + sum_c x[p][c] w[o][c] (FP32 out)
+__global__ void head_fwd_kernel(const bf16* x, int C, const float* w, const float* b, float* y,
+                                int O, long long npix) {
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < npix;
+       p += (long long)gridDim.x * blockDim.x) {
+    for (int o = 0; o < O; ++o) {
+      float s = b[o];
+      for (int c = 0; c < C; ++c) s += __bfloat162float(x[p * C + c]) * w[o * C + c];
+      y[p * O + o] = s;
+    }
+  }
+}
+
+// head gradient: gx = (gy w) * (x > 0) (bf16); dw += gy^T x; db += sum gy
+__global__ void head_bwd_kernel(const bf16* x, int C, const float* w, const float* gy, int O,
+                                long long npix, bf16* gx, float* dw, float* db) {
+  __shared__ float sdw[256], sdb[8];
+  for (int i = threadIdx.x; i < O * C; i += blockDim.x) sdw[i] = 0.f;
+  if (threadIdx.x < O) sdb[threadIdx.x] = 0.f;
+  __syncthreads();
+  float ldw[128];
+  float ldb[8];
+  for (int i = 0; i < O * C; ++i) ldw[i] = 0.f;
+  for (int o = 0; o < O; ++o) ldb[o] = 0.f;
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < npix;
+       p += (long long)gridDim.x * blockDim.x) {
+    for (int c = 0; c < C; ++c) {
+      const float xv = __bfloat162float(x[p * C + c]);
+      float s = 0.f;
+      for (int o = 0; o < O; ++o) {
+        const float g = gy[p * O + o];
+        s += g * w[o * C + c];
+        ldw[o * C + c] += g * xv;
+      }
+      gx[p * C + c] = __float2bfloat16(xv > 0.f ? s : 0.f);
+    }
+    for (int o = 0; o < O; ++o) ldb[o] += gy[p * O + o];
+  }
+  for (int i = 0; i < O * C; ++i) atomicAdd(&sdw[i], ldw[i]);
+  for (int o = 0; o < O; ++o) atomicAdd(&sdb[o], ldb[o]);
+  __syncthreads();
+  for (int i = threadIdx.x; i < O * C; i += blockDim.x) atomicAdd(dw + i, sdw[i]);
+  if (threadIdx.x < O) atomicAdd(db + threadIdx.x, sdb[threadIdx.x]);
+}
+
+// MSE: loss += sum (y - t)^2 / n; gy = 2 (y - t) / n
+__global__ void mse_kernel(const float* y, const float* t, long long n, float* gy, float* loss) {
+  float s = 0.f;
+  const float inv = 1.f / float(n);
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const float d = y[i] - t[i];
+    s += d * d;
+    gy[i] = 2.f * d * inv;
+  }
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) atomicAdd(loss, s * inv);
+}
+
+// Adam with bias correction; refreshes the bf16 copy and clears the gradient
+__global__ void adam_kernel(float* w, float* g, float* m, float* v, bf16* wb, long long n,
+                            float lr, float b1, float b2, float eps, float c1, float c2) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.f - b1) * gi;
+    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    const float wi = w[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    w[i] = wi;
+    if (wb) wb[i] = __float2bfloat16(wi);
+    g[i] = 0.f;
+  }
+}
+
+// wt[8 - tap][ci][co] = w[tap][co][ci]: the weights of the data gradient
+__global__ void flip_transpose_kernel(const bf16* w, bf16* wt, int Cout, int Cin) {
+  const long long n = 9LL * Cout * Cin;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int ci = int(i % Cin);
+    const int co = int((i / Cin) % Cout);
+    const int tap = int(i / ((long long)Cin * Cout));
+    wt[(size_t(8 - tap) * Cin + ci) * Cout + co] = w[i];
+  }
+}
+
+int blocks_for(long long n) {
+  long long b = (n + 255) / 256;
+  return int(b < 1 ? 1 : (b > 152 * 32 ? 152 * 32 : b));
+}
+
+}  // namespace
+
+cudaError_t conv3x3(const ConvArgs& a, cudaStream_t s) {
+  if (a.W % 64 || a.Cin % 16 || a.Cx % 8 || a.Cy % 8 || a.ci_off % 8 || a.co_off % 8)
+    return cudaErrorInvalidValue;
+  const long long npix = (long long)a.N * a.H * a.W;
+  if (a.Cout % 64 == 0) {
+    conv3x3_kernel<64><<<dim3(unsigned(npix / 64), a.Cout / 64), kThreads, 0, s>>>(a);
+  } else if (a.Cout % 32 == 0) {
+    conv3x3_kernel<32><<<dim3(unsigned(npix / 64), a.Cout / 32), kThreads, 0, s>>>(a);
+  } else {
+    return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t wgrad3x3(const WgradArgs& args, cudaStream_t s) {
+  WgradArgs a = args;
+  if (a.W % 16 || a.Cout % 32 || a.Cin % 16 || a.chunk < 16 || a.chunk % 16)
+    return cudaErrorInvalidValue;
+  // grid z = 9 x chunks must stay within 65535: enlarge the chunk if needed
+  const long long max_chunks = 65535 / 9;
+  if ((a.npix + a.chunk - 1) / a.chunk > max_chunks) {
+    const long long c = (a.npix + max_chunks - 1) / max_chunks;
+    a.chunk = int((c + 15) / 16 * 16);
+  }
+  const int chunks = int((a.npix + a.chunk - 1) / a.chunk);
+  const dim3 grid_z(1, 1, unsigned(9 * chunks));
+  if (a.Cout % 64 == 0 && a.Cin % 32 == 0)
+    wgrad3x3_kernel<64, 32><<<dim3(a.Cout / 64, a.Cin / 32, grid_z.z), kThreads, 0, s>>>(a);
+  else if (a.Cin % 32 == 0)
+    wgrad3x3_kernel<32, 32><<<dim3(a.Cout / 32, a.Cin / 32, grid_z.z), kThreads, 0, s>>>(a);
+  else
+    wgrad3x3_kernel<32, 16><<<dim3(a.Cout / 32, a.Cin / 16, grid_z.z), kThreads, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t bias_grad(const bf16* g, int Cg, int off, int C, long long npix, float* db,
+                      cudaStream_t s) {
+  bias_grad_kernel<<<dim3(256, (C + 127) / 128), 128, 0, s>>>(g, Cg, off, C, npix, db);
+  return cudaGetLastError();
+}
+cudaError_t relu_mask(bf16* g, int Cg, int goff, const bf16* act, int Ca, int aoff, int C,
+                      long long npix, cudaStream_t s) {
+  mask_kernel<<<blocks_for(npix * C), 256, 0, s>>>(g, Cg, goff, act, Ca, aoff, C, npix);
+  return cudaGetLastError();
+}
+cudaError_t avgpool2(const bf16* x, int Cx, int xoff, bf16* y, int Cy, int yoff, int C, int B,
+                     int H, int W, cudaStream_t s) {
+  avgpool_kernel<<<blocks_for((long long)B * H * W * C / 4), 256, 0, s>>>(x, Cx, xoff, y, Cy, yoff,
+                                                                          C, B, H, W);
+  return cudaGetLastError();
+}
+cudaError_t avgpool2_bwd_add_mask(bf16* gs, const bf16* gp, const bf16* act, int Cs, int soff,
+                                  int C, int B, int H, int W, cudaStream_t s) {
+  pool_bwd_add_mask_kernel<<<blocks_for((long long)B * H * W * C), 256, 0, s>>>(
+      gs, gp, act, Cs, soff, C, B, H, W);
+  return cudaGetLastError();
+}
+cudaError_t upsample2(const bf16* x, bf16* y, int C, int B, int H, int W, cudaStream_t s) {
+  upsample_kernel<<<blocks_for((long long)B * H * W * C), 256, 0, s>>>(x, y, C, B, H, W);
+  return cudaGetLastError();
+}
+cudaError_t upsample2_bwd_mask(const bf16* g, bf16* gx, const bf16* act, int C, int B, int H,
+                               int W, cudaStream_t s) {
+  upsample_bwd_mask_kernel<<<blocks_for((long long)B * H * W * C / 4), 256, 0, s>>>(g, gx, act, C,
+                                                                                   B, H, W);
+  return cudaGetLastError();
+}
+cudaError_t head_fwd(const bf16* x, int C, const float* w, const float* b, float* y, int O,
+                     long long npix, cudaStream_t s) {
+  head_fwd_kernel<<<blocks_for(npix), 256, 0, s>>>(x, C, w, b, y, O, npix);
+  return cudaGetLastError();
+}
+cudaError_t head_bwd(const bf16* x, int C, const float* w, const float* gy, int O, long long npix,
+                     bf16* gx, float* dw, float* db, cudaStream_t s) {
+  if (O * C > 128 || O > 8) return cudaErrorInvalidValue;
+  head_bwd_kernel<<<blocks_for(npix), 256, 0, s>>>(x, C, w, gy, O, npix, gx, dw, db);
+  return cudaGetLastError();
+}
+cudaError_t mse(const float* y, const float* t, long long n, float* gy, float* loss,
+                cudaStream_t s) {
+  mse_kernel<<<blocks_for(n), 256, 0, s>>>(y, t, n, gy, loss);
+  return cudaGetLastError();
+}
+cudaError_t adam(float* w, float* g, float* m, float* v, bf16* wb, long long n, float lr, float b1,
+                 float b2, float eps, int t, cudaStream_t s) {
+  const float c1 = 1.f - powf(b1, float(t)), c2 = 1.f - powf(b2, float(t));
+  adam_kernel<<<blocks_for(n), 256, 0, s>>>(w, g, m, v, wb, n, lr, b1, b2, eps, c1, c2);
+  return cudaGetLastError();
+}
+cudaError_t flip_transpose(const bf16* w, bf16* wt, int Cout, int Cin, cudaStream_t s) {
+  flip_transpose_kernel<<<blocks_for(9LL * Cout * Cin), 256, 0, s>>>(w, wt, Cout, Cin);
+  return cudaGetLastError();
+}
+
+}  // namespace nn
+}  // namespace lbk

@@ -1,0 +1,62 @@
+// Launchers of the U-Net surrogate kernels (unet.cu).  NHWC bf16 tensors;
+// `C*` is the channel stride of a buffer and `*off` the first channel used,
+// so that concatenated buffers need no copies.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+namespace lbk {
+namespace nn {
+
+using bf16 = __nv_bfloat16;
+
+struct ConvArgs {
+  const bf16* x;   // [N][H][W][Cx], channels ci_off .. ci_off + Cin
+  int Cx, ci_off, Cin;
+  const bf16* w;   // [9][Cout][Cin] (tap-major, input channels innermost)
+  const float* bias;  // [Cout] or null
+  bf16* y;         // [N][H][W][Cy], channels co_off .. co_off + Cout
+  int Cy, co_off, Cout;
+  int N, H, W;
+  int relu;            // apply max(0, .) to the output
+  const bf16* mask;    // zero the output where mask <= 0 (same layout as y), or null
+};
+// requirements: W % 64 == 0, Cin % 16 == 0, Cout % 32 == 0, strides/offsets % 8 == 0
+cudaError_t conv3x3(const ConvArgs& a, cudaStream_t s);
+
+struct WgradArgs {
+  const bf16* x;   // layer input, as in ConvArgs
+  int Cx, ci_off, Cin;
+  const bf16* dy;  // gradient of the layer's pre-activation [N][H][W][Cdy], channels co_off..
+  int Cdy, co_off, Cout;
+  float* dw;       // [9][Cout][Cin] FP32, accumulated with atomics
+  long long npix;  // N * H * W
+  int H, W;
+  int chunk;       // pixels per CTA (multiple of 16)
+};
+cudaError_t wgrad3x3(const WgradArgs& a, cudaStream_t s);
+
+cudaError_t bias_grad(const bf16* g, int Cg, int off, int C, long long npix, float* db,
+                      cudaStream_t s);
+cudaError_t relu_mask(bf16* g, int Cg, int goff, const bf16* act, int Ca, int aoff, int C,
+                      long long npix, cudaStream_t s);
+cudaError_t avgpool2(const bf16* x, int Cx, int xoff, bf16* y, int Cy, int yoff, int C, int B,
+                     int H, int W, cudaStream_t s);
+cudaError_t avgpool2_bwd_add_mask(bf16* gs, const bf16* gp, const bf16* act, int Cs, int soff,
+                                  int C, int B, int H, int W, cudaStream_t s);
+cudaError_t upsample2(const bf16* x, bf16* y, int C, int B, int H, int W, cudaStream_t s);
+cudaError_t upsample2_bwd_mask(const bf16* g, bf16* gx, const bf16* act, int C, int B, int H,
+                               int W, cudaStream_t s);
+cudaError_t head_fwd(const bf16* x, int C, const float* w, const float* b, float* y, int O,
+                     long long npix, cudaStream_t s);
+cudaError_t head_bwd(const bf16* x, int C, const float* w, const float* gy, int O, long long npix,
+                     bf16* gx, float* dw, float* db, cudaStream_t s);
+cudaError_t mse(const float* y, const float* t, long long n, float* gy, float* loss,
+                cudaStream_t s);
+cudaError_t adam(float* w, float* g, float* m, float* v, bf16* wb, long long n, float lr, float b1,
+                 float b2, float eps, int t, cudaStream_t s);
+cudaError_t flip_transpose(const bf16* w, bf16* wt, int Cout, int Cin, cudaStream_t s);
+
+}  // namespace nn
+}  // namespace lbk

@@ -1,0 +1,124 @@
+"""The U-Net surrogate's GPU forward / backward / Adam kernels against the
+FP64 CPU reference.
+
+The GPU network stores bf16 weights and activations and accumulates in FP32.
+The reference gets the same bf16-rounded 3x3 weights and input, rounds each
+activation it keeps to bf16 as the network does (so that both take every
+ReLU mask decision on the same stored values: a unit whose pre-activation
+sits within rounding of zero passes or blocks its whole gradient), and
+computes everything else in FP64.  What remains is FP32 summation order and
+the bf16 rounding of the activation gradients, about 2^-9 relative per layer.
+The bars (relative Frobenius error 2e-2 on outputs, 4e-2 on each gradient
+tensor, cosine 0.999) sit well above that and far below what a wrong tap, a
+transposed weight or a missing mask gives (relative errors of order one).
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle.unet_ref import UNetRef
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lib():
+    assert torch.cuda.is_available(), "these tests need a CUDA GPU"
+    import paper_2206_02145_gb300
+    return paper_2206_02145_gb300
+
+
+def _bf16(a):
+    return torch.from_numpy(np.asarray(a, np.float32)).to(torch.bfloat16).double().numpy()
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30))
+
+
+def _cos(a, b):
+    na, nb = np.linalg.norm(a), np.linalg.norm(b)
+    if na == 0 and nb == 0:
+        return 1.0
+    return float((a.ravel() @ b.ravel()) / (na * nb))
+
+
+@pytest.mark.parametrize("levels,batch,h,w", [(1, 2, 8, 64), (2, 2, 16, 128), (3, 1, 8, 256)])
+def test_forward_and_gradients_match_fp64_reference(lib, levels, batch, h, w):
+    in_ch, out_ch = 4, 3
+    net = lib.UNet(in_ch=in_ch, out_ch=out_ch, base_ch=32, levels=levels, batch=batch, height=h,
+                   width=w, seed=7, stream=lib.current_stream())
+    ref = UNetRef(levels, 32, in_ch, out_ch, store=_bf16)
+    flat = net.weights().astype(np.float64)
+    assert flat.size == sum(int(np.prod(s)) for s in ref.shapes) == net.param_count
+    params = ref.unflatten(flat)
+    # the GPU convolves with bf16 copies of the 3x3 weights; biases and head are FP32
+    params = [_bf16(p) if p.ndim == 3 else p for p in params]
+    rng = np.random.default_rng(levels)
+    x = rng.normal(size=(batch, h, w, in_ch)).astype(np.float32)
+    t = rng.normal(size=(batch, h, w, out_ch)).astype(np.float32)
+    xd = torch.from_numpy(x).cuda()
+    td = torch.from_numpy(t).cuda()
+    yd = torch.empty(batch, h, w, out_ch, device="cuda")
+    net.forward(xd, yd)
+    torch.cuda.synchronize()
+    loss = net.grad(xd, td)
+    g_gpu = ref.unflatten(net.grads().astype(np.float64))
+    loss_ref, y_ref, g_ref = ref.loss_and_grads(_bf16(x), t.astype(np.float64), params)
+    assert _rel(yd.cpu().double().numpy(), y_ref) < 2e-2
+    assert loss == pytest.approx(loss_ref, rel=2e-2)
+    errs = [(_rel(a, b), _cos(a, b)) for a, b in zip(g_gpu, g_ref)]
+    print("gradient rel / cos per tensor:", [(f"{r:.2e}", f"{c:.6f}") for r, c in errs])
+    for i, (a, b) in enumerate(zip(g_gpu, g_ref)):
+        assert a.shape == b.shape
+        assert errs[i][0] < 4e-2, (i, ref.shapes[i], errs[i])
+        assert errs[i][1] > 0.999, (i, ref.shapes[i], errs[i])
+    net.close()
+
+
+def test_set_weights_round_trip_and_forward_follows(lib):
+    net = lib.UNet(in_ch=2, out_ch=1, levels=2, batch=1, height=8, width=128, seed=3,
+                   stream=lib.current_stream())
+    w0 = net.weights()
+    x = torch.randn(1, 8, 128, 2, device="cuda")
+    y0 = torch.empty(1, 8, 128, 1, device="cuda")
+    y1 = torch.empty_like(y0)
+    net.forward(x, y0)
+    net.set_weights(w0 * 0.5)
+    np.testing.assert_array_equal(net.weights(), (w0 * 0.5).astype(np.float32))
+    net.forward(x, y1)
+    torch.cuda.synchronize()
+    assert not torch.equal(y0, y1)
+    net.set_weights(w0)
+    net.forward(x, y1)
+    torch.cuda.synchronize()
+    assert torch.equal(y0, y1)
+    with pytest.raises(ValueError):
+        net.set_weights(w0[:-1])
+    net.close()
+
+
+def test_adam_training_reduces_the_loss(lib):
+    # fit a fixed smooth map of the input: loss must fall by a factor of 5
+    net = lib.UNet(in_ch=4, out_ch=4, levels=3, batch=2, height=32, width=256, seed=11,
+                   stream=lib.current_stream())
+    g = torch.Generator(device="cpu").manual_seed(5)
+    x = torch.randn(2, 32, 256, 4, generator=g).cuda()
+    t = (0.5 * torch.roll(x, 1, dims=2) - 0.25 * x).contiguous()
+    l0 = net.grad(x, t)
+    loss = torch.zeros(1, device="cuda")
+    for _ in range(300):
+        net.train_step(x, t, 2e-3, loss)
+    torch.cuda.synchronize()
+    l1 = net.grad(x, t)
+    assert np.isfinite(l1) and l1 < l0 / 5, (l0, l1)
+    net.close()
+
+
+def test_rejects_unsupported_shapes(lib):
+    with pytest.raises(lib.LbpfError):
+        lib.UNet(levels=2, height=16, width=96)  # width / 2 not a multiple of 64
+    with pytest.raises(lib.LbpfError):
+        lib.UNet(base_ch=48, height=64, width=64, levels=1)
+    with pytest.raises(lib.LbpfError):
+        lib.UNet(in_ch=17, height=64, width=64, levels=1)
