@@ -280,10 +280,73 @@ int lbpf_unet_train_step(lbpf_unet_t* n, const float* x, const float* t, float l
  * convolution has Cin = 16 (inputs zero-padded).  which: 0 weights,
  * 1 gradients; set = 1 writes weights.  Synchronising. */
 size_t lbpf_unet_param_count(const lbpf_unet_t* n);
+/* Select the convolution kernels: 1 (default) the tcgen05 / TMEM / TMA
+ * kernel wherever the layer's shape allows it, 0 the warp-level mma.sync
+ * kernel everywhere.  Takes effect at the next pass. */
+int lbpf_unet_set_tensor_path(lbpf_unet_t* n, int use_tcgen05);
+/* Synchronises the network's stream and returns LBPF_ETIMEDOUT if a
+ * tensor-core kernel gave up waiting on one of its barriers since creation
+ * (lbpf_unet_grad and lbpf_surrogate_advance check the same). */
+int lbpf_unet_status(lbpf_unet_t* n);
 int lbpf_unet_params(lbpf_unet_t* n, int which, float* host, size_t count, int set);
 size_t lbpf_unet_device_bytes(const lbpf_unet_t* n);
 const char* lbpf_unet_last_error(const lbpf_unet_t* n);
 void lbpf_unet_destroy(lbpf_unet_t* n);
+
+/* ---- learned block propagator -----------------------------------------------
+ * Advances a 2D simulation by blocks of steps_per_block LB steps, each either
+ * by one application of a trained network (input: the fields (phi, U, ux, uy)
+ * normalised as (f - shift) / scale; output: their change over the block
+ * divided by res_scale) or, as fallback, by the LB step itself.  The LB is
+ * also the judge: on judged blocks it advances the state and the network's
+ * prediction from the same start is measured against it.  A prediction is
+ * committed (the state becomes the equilibrium of the predicted fields at
+ * the current density, with phi(t-1) from the block's mean rate of change)
+ * only if
+ *   - the predicted solute invariant sum(U + phi(t-1)) (Eq. 13 with its
+ *     source -dphi/dt: conserved by the LB in a closed domain) differs from
+ *     the value at initialisation by at most drift_tol (relative), and
+ *   - its interface error estimate is at most iface_tol lattice units: the
+ *     largest difference, over the axis rays of lbpf_diag.iface_pos, between
+ *     the predicted interface displacement and the displacement the LB
+ *     produced in its last block, summed over the blocks committed since
+ *     that LB block.
+ * An accepted prediction's remaining solute deficit is spread over the
+ * liquid in proportion to (1 - phi)/2 before it is committed, so that the
+ * committed state keeps the invariant exactly as the LB does.
+ * A block that fails a check is advanced by the LB and the next block is
+ * judged; so is every judge_every-th block (0: only those).  Meaningful for
+ * closed domains (periodic or wall boundaries); the network must have
+ * batch 1, 4 inputs, 4 outputs, height ny and width nx. */
+typedef struct {
+  int steps_per_block;       /* LB steps one network application stands for (>= 1) */
+  int judge_every;           /* judge every judge_every-th block (0: only after a failed check) */
+  double drift_tol;          /* relative solute drift bound (e.g. 1e-3) */
+  double iface_tol;          /* interface error bound in lattice units (e.g. 1.0) */
+  float shift[4], scale[4];  /* input normalisation of (phi, U, ux, uy); scale != 0 */
+  float res_scale[4];        /* output scale of the change of (phi, U, ux, uy) */
+} lbpf_surrogate_cfg;
+
+typedef struct {
+  int64_t blocks;            /* blocks advanced by the call */
+  int64_t surrogate_blocks;  /* advanced by the network */
+  int64_t judged_blocks;     /* advanced by the LB while judging a prediction */
+  int64_t fallback_blocks;   /* advanced by the LB because a check failed */
+  double max_drift;          /* largest predicted relative solute drift (before correction) */
+  double max_iface_err;      /* largest judged interface error (lattice units) */
+  double max_iface_est;      /* largest accumulated interface error estimate committed */
+} lbpf_surrogate_report;
+
+/* The network input of the current state: device FP32 [ny][nx][4]. */
+int lbpf_surrogate_sample(lbpf_t* h, const lbpf_surrogate_cfg* cfg, float* x);
+/* Training target from the inputs x0 (state at t) and x1 (at t + block):
+ * t = (x1 - x0) scale / res_scale per channel; device FP32 [npix][4];
+ * queued on `stream`. */
+int lbpf_surrogate_target(const lbpf_surrogate_cfg* cfg, const float* x0, const float* x1,
+                          int64_t npix, float* t, void* stream);
+/* Advance `blocks` blocks (synchronising once per block); rep may be NULL. */
+int lbpf_surrogate_advance(lbpf_t* h, lbpf_unet_t* net, const lbpf_surrogate_cfg* cfg,
+                           int blocks, lbpf_surrogate_report* rep);
 
 /* ---- allocation-free reduction ------------------------------------------------
  * The paper has no counterpart of this entry point; it serves callers that

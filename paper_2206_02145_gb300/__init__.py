@@ -71,6 +71,20 @@ class lbpf_unet_cfg(ctypes.Structure):
                 ("width", ctypes.c_int), ("seed", ctypes.c_uint64)]
 
 
+class lbpf_surrogate_cfg(ctypes.Structure):
+    _fields_ = [("steps_per_block", ctypes.c_int), ("judge_every", ctypes.c_int),
+                ("drift_tol", ctypes.c_double), ("iface_tol", ctypes.c_double),
+                ("shift", ctypes.c_float * 4), ("scale", ctypes.c_float * 4),
+                ("res_scale", ctypes.c_float * 4)]
+
+
+class lbpf_surrogate_report(ctypes.Structure):
+    _fields_ = [("blocks", ctypes.c_int64), ("surrogate_blocks", ctypes.c_int64),
+                ("judged_blocks", ctypes.c_int64), ("fallback_blocks", ctypes.c_int64),
+                ("max_drift", ctypes.c_double), ("max_iface_err", ctypes.c_double),
+                ("max_iface_est", ctypes.c_double)]
+
+
 EXPORTED = ("lbpf_params_default", "lbpf_create", "lbpf_init_seed", "lbpf_init_fields",
             "lbpf_step", "lbpf_read_fields", "lbpf_state_bytes", "lbpf_write_state",
             "lbpf_diagnostics", "lbpf_set_stream", "lbpf_device_bytes", "lbpf_last_error",
@@ -79,7 +93,9 @@ EXPORTED = ("lbpf_params_default", "lbpf_create", "lbpf_init_seed", "lbpf_init_f
             "lbpf_batch_tuning", "lbpf_batch_last_error", "lbpf_batch_destroy",
             "lbpf_unet_create", "lbpf_unet_forward", "lbpf_unet_grad", "lbpf_unet_train_step",
             "lbpf_unet_param_count", "lbpf_unet_params", "lbpf_unet_device_bytes",
-            "lbpf_unet_last_error", "lbpf_unet_destroy")
+            "lbpf_unet_last_error", "lbpf_unet_destroy", "lbpf_unet_set_tensor_path",
+            "lbpf_unet_status", "lbpf_surrogate_sample",
+            "lbpf_surrogate_target", "lbpf_surrogate_advance")
 
 
 def _load_library():
@@ -134,6 +150,13 @@ def _load_library():
     lib.lbpf_unet_last_error.restype = ctypes.c_char_p
     lib.lbpf_unet_destroy.argtypes = [vp]
     lib.lbpf_unet_destroy.restype = None
+    lib.lbpf_unet_set_tensor_path.argtypes = [vp, ctypes.c_int]
+    lib.lbpf_unet_status.argtypes = [vp]
+    lib.lbpf_surrogate_sample.argtypes = [vp, ctypes.POINTER(lbpf_surrogate_cfg), vp]
+    lib.lbpf_surrogate_target.argtypes = [ctypes.POINTER(lbpf_surrogate_cfg), vp, vp,
+                                          ctypes.c_int64, vp, vp]
+    lib.lbpf_surrogate_advance.argtypes = [vp, vp, ctypes.POINTER(lbpf_surrogate_cfg),
+                                           ctypes.c_int, ctypes.POINTER(lbpf_surrogate_report)]
     keep = ("lbpf_state_bytes", "lbpf_device_bytes", "lbpf_last_error", "lbpf_destroy",
             "lbpf_batch_instance", "lbpf_batch_last_error", "lbpf_batch_destroy",
             "lbpf_unet_param_count", "lbpf_unet_device_bytes", "lbpf_unet_last_error",
@@ -417,6 +440,14 @@ class UNet:
         self._check(_lib.lbpf_unet_train_step(self.n, self._ptr(x), self._ptr(t), float(lr),
                                               None if loss_dev is None else self._ptr(loss_dev)))
 
+    def set_tensor_path(self, use_tcgen05: bool):
+        """True (default): tcgen05 / TMEM / TMA convolutions; False: mma.sync."""
+        self._check(_lib.lbpf_unet_set_tensor_path(self.n, 1 if use_tcgen05 else 0))
+
+    def status(self):
+        """Synchronise and raise if a tensor-core kernel gave up waiting."""
+        self._check(_lib.lbpf_unet_status(self.n))
+
     @property
     def param_count(self) -> int:
         return int(_lib.lbpf_unet_param_count(self.n))
@@ -454,3 +485,32 @@ class UNet:
             self.close()
         except Exception:
             pass
+
+
+def surrogate_cfg(steps_per_block=50, judge_every=8, drift_tol=1e-3, iface_tol=1.0,
+                  shift=(0.0, 0.3, 0.0, 0.0), scale=(1.0, 0.2, 0.01, 0.01),
+                  res_scale=(0.05, 0.005, 0.001, 0.001)) -> lbpf_surrogate_cfg:
+    c = lbpf_surrogate_cfg()
+    c.steps_per_block, c.judge_every = int(steps_per_block), int(judge_every)
+    c.drift_tol, c.iface_tol = float(drift_tol), float(iface_tol)
+    c.shift[:], c.scale[:], c.res_scale[:] = list(shift), list(scale), list(res_scale)
+    return c
+
+
+def lbpf_surrogate_sample(sim: "Sim", cfg: lbpf_surrogate_cfg, x) -> None:
+    """Normalised network input of the simulation's state into device x [ny][nx][4]."""
+    _check(sim.h, _lib.lbpf_surrogate_sample(sim.h, ctypes.byref(cfg), UNet._ptr(x)))
+
+
+def lbpf_surrogate_target(cfg: lbpf_surrogate_cfg, x0, x1, npix: int, t, stream=None) -> None:
+    rc = _lib.lbpf_surrogate_target(ctypes.byref(cfg), UNet._ptr(x0), UNet._ptr(x1), int(npix),
+                                    UNet._ptr(t), ctypes.c_void_p(stream or 0))
+    if rc != OK:
+        raise LbpfError(rc, "lbpf_surrogate_target: invalid arguments")
+
+
+def lbpf_surrogate_advance(sim: "Sim", net: UNet, cfg: lbpf_surrogate_cfg, blocks: int) -> dict:
+    rep = lbpf_surrogate_report()
+    _check(sim.h, _lib.lbpf_surrogate_advance(sim.h, net.n, ctypes.byref(cfg), int(blocks),
+                                              ctypes.byref(rep)))
+    return {f: getattr(rep, f) for f, _ in rep._fields_}

@@ -268,6 +268,45 @@ __global__ void crossing_kernel(const Model m, const T* pops, int icx, int icy, 
   out[5 + r] = res;
 }
 
+// Learned block propagator, 2D: the network input (phi, U, ux, uy), each as
+// (f - shift) / scale, NHWC with H = ny and W = nx; and the same four fields
+// plus rho unnormalised as planes of n values (skipped if F is null).
+template <typename T, typename R>
+__global__ void surrogate_gather_kernel(const Model m, const T* pops, const Vec4 shift,
+                                        const Vec4 inv_scale, float* x, float* F) {
+  const long long n = (long long)m.nx * m.ny;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    int xx, yy, zz;
+    node_xyz(m, i, xx, yy, zz);
+    R phi, U, rho, u[3];
+    node_moments<T, R>(m, pops, pitched(m, xx, yy, 0), phi, U, rho, u);
+    const float f[4] = {float(phi), float(U), float(u[0]), float(u[1])};
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      x[i * 4 + c] = (f[c] - shift.v[c]) * inv_scale.v[c];
+      if (F) F[c * n + i] = f[c];
+    }
+    if (F) F[4 * n + i] = float(rho);
+  }
+}
+
+// Replace the state by the equilibrium of the fields in planes F1 (phi, U,
+// ux, uy, phi(t-1)) and rho, as the fields initialisation does.
+template <typename T, typename R>
+__global__ void surrogate_commit_kernel(const Model m, const float* F1, const float* rho, T* pops,
+                                        R* phi_prev) {
+  const long long n = (long long)m.nx * m.ny;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    int xx, yy, zz;
+    node_xyz(m, i, xx, yy, zz);
+    const long long j = pitched(m, xx, yy, 0);
+    store_equilibrium<T>(m, pops, j, F1[i], F1[n + i], rho[i], F1[2 * n + i], F1[3 * n + i], 0.0);
+    phi_prev[j] = R(double(F1[4 * n + i]) - m.ref_h);
+  }
+}
+
 int grid_for(long long n) {
   long long b = (n + 255) / 256;
   return int(b < 152 * 16 ? (b < 1 ? 1 : b) : 152 * 16);
@@ -311,6 +350,23 @@ cudaError_t diag_t(const Model& m, const void* pops, const void* pp, double* par
   return cudaGetLastError();
 }
 
+template <typename T, typename R>
+cudaError_t gather_t(const Model& m, const void* pops, const Vec4& shift, const Vec4& inv_scale,
+                     float* x, float* F, cudaStream_t s) {
+  const long long n = (long long)m.nx * m.ny;
+  surrogate_gather_kernel<T, R><<<grid_for(n), 256, 0, s>>>(m, static_cast<const T*>(pops), shift,
+                                                            inv_scale, x, F);
+  return cudaGetLastError();
+}
+template <typename T, typename R>
+cudaError_t commit_t(const Model& m, const float* F1, const float* rho, void* pops, void* pp,
+                     cudaStream_t s) {
+  const long long n = (long long)m.nx * m.ny;
+  surrogate_commit_kernel<T, R><<<grid_for(n), 256, 0, s>>>(m, F1, rho, static_cast<T*>(pops),
+                                                            static_cast<R*>(pp));
+  return cudaGetLastError();
+}
+
 }  // namespace
 
 #define LBPF_DISPATCH(FN, ...)                                          \
@@ -333,6 +389,18 @@ cudaError_t launch_init_fields(const Model& m, const double* phi, const double* 
 cudaError_t launch_fields(const Model& m, const void* pops, const void* phi_prev, unsigned mask,
                           int fp64, void* out, cudaStream_t s) {
   LBPF_DISPATCH(fields_t, m, pops, phi_prev, mask, fp64, out, s)
+}
+cudaError_t launch_surrogate_gather(const Model& m, const void* pops, const Vec4& shift,
+                                    const Vec4& scale, float* x, float* F, cudaStream_t s) {
+  if (m.dim != 2) return cudaErrorInvalidValue;
+  Vec4 inv;
+  for (int c = 0; c < 4; ++c) inv.v[c] = 1.0f / scale.v[c];
+  LBPF_DISPATCH(gather_t, m, pops, shift, inv, x, F, s)
+}
+cudaError_t launch_surrogate_commit(const Model& m, const float* F1, const float* rho, void* pops,
+                                    void* phi_prev, cudaStream_t s) {
+  if (m.dim != 2) return cudaErrorInvalidValue;
+  LBPF_DISPATCH(commit_t, m, F1, rho, pops, phi_prev, s)
 }
 size_t diag_partials_bytes(const Model&) { return sizeof(double) * kDiagBlocks * kDiagSlots; }
 cudaError_t launch_diag(const Model& m, const void* pops, const void* phi_prev, double* partials,

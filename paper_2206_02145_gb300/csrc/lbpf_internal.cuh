@@ -171,6 +171,19 @@ cudaError_t launch_init_fields(const Model& m, const double* phi, const double* 
 cudaError_t launch_fields(const Model& m, const void* pops, const void* phi_prev,
                           unsigned mask, int fp64, void* out, cudaStream_t s);
 
+// Learned block propagator (2D only).  gather: network input x[i][c] =
+// (f_c - shift_c) / scale_c of f = (phi, U, ux, uy), i = y nx + x, and the
+// unnormalised planes F[c][i] of (phi, U, ux, uy, rho).  commit: the state
+// becomes the equilibrium of the planes F1 = (phi, U, ux, uy, phi(t-1)) with
+// density rho.
+struct Vec4 {
+  float v[4];
+};
+cudaError_t launch_surrogate_gather(const Model& m, const void* pops, const Vec4& shift,
+                                    const Vec4& scale, float* x, float* F, cudaStream_t s);
+cudaError_t launch_surrogate_commit(const Model& m, const float* F1, const float* rho, void* pops,
+                                    void* phi_prev, cudaStream_t s);
+
 // FP64 diagnostics.  partials: scratch of diag_partials_bytes(m) bytes.
 // out[0..4] = sum(U + phi_prev), sum(rho), sum((1+phihat)/2), max|u|,
 // nonfinite count; out[5..10] = interface crossings from (icx, icy, icz).

@@ -19,7 +19,7 @@
 #include <vector>
 
 #include "../../include/lbpf.h"
-#include "lbpf_internal.cuh"
+#include "lbpf_handle.cuh"
 #include "unet.cuh"
 
 using lbk::nn::bf16;
@@ -66,6 +66,13 @@ struct lbpf_unet {
   std::vector<Act> g_ea, g_cat, g_pool, g_u, g_da, g_db;
   Act g_bottom;
   float *y = nullptr, *gy = nullptr, *loss = nullptr;
+  unsigned* d_err = nullptr;  // bit 2: a tensor-core kernel timed out
+  int tensor_path = 1;        // convolutions on the tcgen05 kernel where possible
+  // block propagator scratch (allocated on first use): network input x,
+  // output y, current planes F (phi, U, ux, uy, rho), predicted planes F1
+  // (phi, U, ux, uy, phi(t-1)), FP64 sums and interface crossings
+  float *px = nullptr, *py = nullptr, *pF = nullptr, *pF1 = nullptr;
+  double *psum = nullptr, *pcross = nullptr;
   std::vector<void*> allocs;
   size_t bytes = 0;
   int t = 0;  // Adam step
@@ -156,6 +163,8 @@ int conv_fwd(lbpf_unet* n, const ConvLayer& l, const Act& x, int xoff, const Act
   a.W = x.w;
   a.relu = 1;
   a.mask = nullptr;
+  a.tensor_path = n->tensor_path;
+  a.err = n->d_err;
   UCK(n, lbk::nn::conv3x3(a, n->stream));
   return LBPF_OK;
 }
@@ -199,6 +208,8 @@ int conv_bwd(lbpf_unet* n, const ConvLayer& l, const Act& x, int xoff, const Act
     a.W = x.w;
     a.relu = 0;
     a.mask = mask ? mask->p : nullptr;
+    a.tensor_path = n->tensor_path;
+    a.err = n->d_err;
     UCK(n, lbk::nn::conv3x3(a, n->stream));
   }
   return LBPF_OK;
@@ -297,6 +308,15 @@ int backward(lbpf_unet* n, const float* t) {
   return LBPF_OK;
 }
 
+// the device error word after a synchronisation: a tensor-core kernel timed out
+int check_err(lbpf_unet* n) {
+  unsigned e = 0;
+  UCK(n, cudaMemcpyAsync(&e, n->d_err, sizeof(e), cudaMemcpyDeviceToHost, n->stream));
+  UCK(n, cudaStreamSynchronize(n->stream));
+  if (e) return ufail(n, LBPF_ETIMEDOUT, "a tensor-core convolution gave up waiting (code %u)", e);
+  return LBPF_OK;
+}
+
 int adam_all(lbpf_unet* n, float lr) {
   ++n->t;
   const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
@@ -354,6 +374,115 @@ __global__ void to_bf16_kernel(const float* w, bf16* wb, long long n) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x)
     wb[i] = __float2bfloat16(w[i]);
+}
+
+// predicted planes: f' = f + res_scale y; phi(t-1)' = phi' - (phi' - phi) / n_block
+__global__ void apply_kernel(const float* F, const float* y, const lbk::Vec4 rs, float inv_nb,
+                             long long n, float* F1) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    float v[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      v[c] = F[c * n + i] + rs.v[c] * y[i * 4 + c];
+      F1[c * n + i] = v[c];
+    }
+    F1[4 * n + i] = v[0] - (v[0] - F[i]) * inv_nb;
+  }
+}
+
+// phi = 0 crossings of a field plane along the four axis rays from (icx, icy):
+// the first change from phi >= 0 to phi < 0, linearly interpolated, as a
+// distance from the origin; -1 where there is none (the definition of
+// lbpf_diag.iface_pos)
+__global__ void plane_crossing_kernel(const float* phi, int nx, int ny, int bcx, int bcy, int icx,
+                                      int icy, double* out) {
+  const int r = threadIdx.x;
+  if (r >= 4) return;
+  const int axis = r / 2, dir = (r & 1) ? -1 : 1;
+  const int n = axis == 0 ? nx : ny, bc = axis == 0 ? bcx : bcy;
+  int c[2] = {icx, icy};
+  double res = -1.0;
+  double prev = phi[(long long)c[1] * nx + c[0]];
+  if (prev >= 0.0) {
+    const int limit = bc == LBPF_BC_PERIODIC ? n / 2 : n;
+    const int start = c[axis];
+    for (int d = 1; d < limit; ++d) {
+      int v = start + dir * d;
+      if (bc == LBPF_BC_PERIODIC) v = ((v % n) + n) % n;
+      else if (v < 0 || v >= n) break;
+      c[axis] = v;
+      const double p = phi[(long long)c[1] * nx + c[0]];
+      if (p < 0.0) {
+        res = double(d - 1) + prev / (prev - p);
+        break;
+      }
+      prev = p;
+    }
+  }
+  out[r] = res;
+}
+
+// U += k (1 - clamp(phi, -1, 1)) / 2 on the predicted planes
+__global__ void correct_kernel(float* F1, long long n, float k) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const float ph = fminf(fmaxf(F1[i], -1.f), 1.f);
+    F1[n + i] += k * 0.5f * (1.f - ph);
+  }
+}
+
+__global__ void target_kernel(const float* x0, const float* x1, const lbk::Vec4 g, long long n4,
+                              float* t) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n4;
+       i += (long long)gridDim.x * blockDim.x)
+    t[i] = (x1[i] - x0[i]) * g.v[i & 3];
+}
+
+int grid_of(long long n) {
+  long long b = (n + 255) / 256;
+  return int(b < 1 ? 1 : (b > 152 * 16 ? 152 * 16 : b));
+}
+
+int sfail(lbpf* h, int code, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(h->msg, sizeof(h->msg), fmt, ap);
+  va_end(ap);
+  return code;
+}
+
+#define SCK(h, call)                                                                      \
+  do {                                                                                    \
+    cudaError_t e_ = (call);                                                              \
+    if (e_ != cudaSuccess)                                                                \
+      return sfail(h, LBPF_ECUDA, "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, \
+                   __LINE__);                                                             \
+  } while (0)
+
+int check_cfg(const lbpf_surrogate_cfg* c) {
+  if (!c || c->steps_per_block < 1 || c->judge_every < 0 || !(c->drift_tol >= 0.0) ||
+      !(c->iface_tol >= 0.0))
+    return LBPF_EINVAL;
+  for (int k = 0; k < 4; ++k)
+    if (!(std::isfinite(c->shift[k]) && std::isfinite(c->scale[k]) && c->scale[k] != 0.f &&
+          std::isfinite(c->res_scale[k])))
+      return LBPF_EINVAL;
+  return LBPF_OK;
+}
+
+lbk::Vec4 vec4(const float* v) {
+  lbk::Vec4 r;
+  for (int k = 0; k < 4; ++k) r.v[k] = v[k];
+  return r;
+}
+
+// largest |a_r - b_r| over the rays valid (>= 0) in both; -1 if none
+double ray_diff(const double* a, const double* b) {
+  double m = -1.0;
+  for (int r = 0; r < 4; ++r)
+    if (a[r] >= 0.0 && b[r] >= 0.0) m = std::fmax(m, std::fabs(a[r] - b[r]));
+  return m;
 }
 
 }  // namespace
@@ -456,6 +585,7 @@ int lbpf_unet_create(const lbpf_unet_cfg* cfg, void* stream, lbpf_unet_t** out) 
   chk(dalloc(n, &n->y, ny));
   chk(dalloc(n, &n->gy, ny));
   chk(dalloc(n, &n->loss, 1));
+  chk(dalloc(n, &n->d_err, 1));
   if (e != cudaSuccess) {
     fprintf(stderr, "lbpf_unet_create: %s\n", cudaGetErrorString(e));
     lbpf_unet_destroy(n);
@@ -480,12 +610,17 @@ int lbpf_unet_grad(lbpf_unet_t* n, const float* x, const float* t, float* loss_h
   int rc;
   for (const ParamView& v : params(n)) UCK(n, cudaMemsetAsync(v.g, 0, v.n * 4, n->stream));
   if ((rc = pack_input(n, x)) || (rc = forward(n)) || (rc = backward(n, t))) return rc;
-  if (loss_host) {
-    UCK(n, cudaMemcpyAsync(loss_host, n->loss, 4, cudaMemcpyDeviceToHost, n->stream));
-    UCK(n, cudaStreamSynchronize(n->stream));
-  }
+  if (loss_host) UCK(n, cudaMemcpyAsync(loss_host, n->loss, 4, cudaMemcpyDeviceToHost, n->stream));
+  return check_err(n);
+}
+
+int lbpf_unet_set_tensor_path(lbpf_unet_t* n, int use_tcgen05) {
+  if (!n) return LBPF_EINVAL;
+  n->tensor_path = use_tcgen05 ? 1 : 0;
   return LBPF_OK;
 }
+
+int lbpf_unet_status(lbpf_unet_t* n) { return n ? check_err(n) : LBPF_EINVAL; }
 
 int lbpf_unet_train_step(lbpf_unet_t* n, const float* x, const float* t, float lr,
                          float* loss_dev) {
@@ -527,6 +662,167 @@ int lbpf_unet_params(lbpf_unet_t* n, int which, float* host, size_t count, int s
       UCK(n, cudaGetLastError());
     }
   UCK(n, cudaStreamSynchronize(n->stream));
+  return LBPF_OK;
+}
+
+int lbpf_surrogate_target(const lbpf_surrogate_cfg* cfg, const float* x0, const float* x1,
+                          int64_t npix, float* t, void* stream) {
+  if (check_cfg(cfg) || !x0 || !x1 || !t || npix < 0) return LBPF_EINVAL;
+  lbk::Vec4 g;
+  for (int k = 0; k < 4; ++k) g.v[k] = cfg->res_scale[k] != 0.f ? cfg->scale[k] / cfg->res_scale[k] : 0.f;
+  if (npix == 0) return LBPF_OK;
+  target_kernel<<<grid_of(npix * 4), 256, 0, static_cast<cudaStream_t>(stream)>>>(x0, x1, g,
+                                                                                   npix * 4, t);
+  return cudaGetLastError() == cudaSuccess ? LBPF_OK : LBPF_ECUDA;
+}
+
+int lbpf_surrogate_sample(lbpf_t* h, const lbpf_surrogate_cfg* cfg, float* x) {
+  if (!h || !x || check_cfg(cfg)) return LBPF_EINVAL;
+  if (h->status != LBPF_OK) return h->status;
+  if (!h->initialized) return sfail(h, LBPF_ESTATE, "sample before init");
+  if (h->m.dim != 2) return sfail(h, LBPF_EINVAL, "the block propagator is 2D only");
+  SCK(h, lbk::launch_surrogate_gather(h->m, h->pops[h->cur], vec4(cfg->shift), vec4(cfg->scale), x,
+                                      nullptr, h->stream));
+  return LBPF_OK;
+}
+
+int lbpf_surrogate_advance(lbpf_t* h, lbpf_unet_t* net, const lbpf_surrogate_cfg* cfg,
+                           int blocks, lbpf_surrogate_report* rep) {
+  if (!h || !net || check_cfg(cfg) || blocks < 0) return LBPF_EINVAL;
+  if (h->status != LBPF_OK) return h->status;
+  if (!h->initialized) return sfail(h, LBPF_ESTATE, "advance before init");
+  if (h->m.dim != 2) return sfail(h, LBPF_EINVAL, "the block propagator is 2D only");
+  const lbpf_unet_cfg& nc = net->cfg;
+  if (nc.batch != 1 || nc.in_ch != 4 || nc.out_ch != 4 || nc.height != h->m.ny ||
+      nc.width != h->m.nx)
+    return sfail(h, LBPF_EINVAL, "network must be batch 1, 4 -> 4 channels, %d x %d", h->m.ny,
+                 h->m.nx);
+  const long long n = (long long)h->m.nx * h->m.ny;
+  if (!net->px) {
+    cudaError_t e = cudaSuccess;
+    auto chk = [&](cudaError_t r) {
+      if (e == cudaSuccess) e = r;
+    };
+    chk(dalloc(net, &net->px, size_t(4 * n)));
+    chk(dalloc(net, &net->py, size_t(4 * n)));
+    chk(dalloc(net, &net->pF, size_t(5 * n)));
+    chk(dalloc(net, &net->pF1, size_t(5 * n)));
+    chk(dalloc(net, &net->psum, 4));
+    chk(dalloc(net, &net->pcross, 8));
+    if (e != cudaSuccess)
+      return sfail(h, LBPF_ENOMEM, "propagator scratch: %s", cudaGetErrorString(e));
+  }
+  lbpf_surrogate_report r{};
+  r.max_iface_err = -1.0;
+  r.max_iface_est = -1.0;
+  const cudaStream_t s = h->stream;
+  const cudaStream_t saved = net->stream;
+  net->stream = s;  // the network's kernels run in order with the simulation's
+  struct Restore {
+    lbpf_unet* n;
+    cudaStream_t st;
+    ~Restore() { n->stream = st; }
+  } restore{net, saved};
+  double I0 = 0.0;
+  SCK(h, cudaMemcpyAsync(&I0, h->d_diag + 16, sizeof(double), cudaMemcpyDeviceToHost, s));
+  SCK(h, cudaStreamSynchronize(s));
+  const int nb = cfg->steps_per_block;
+  const double tol = cfg->iface_tol;
+  // controller state.  An LB block's outcome (its interface displacement and,
+  // if it was judging, the error of the prediction made from the same start)
+  // is read at the start of the next block, from that block's own read-out.
+  bool trusted = false, have_ref = false;
+  bool lb_pending = false, judge_pending = false, pending_ok = false;
+  double dref[4] = {0, 0, 0, 0}, lb_start[4] = {0, 0, 0, 0}, pred_pending[4] = {0, 0, 0, 0};
+  double acc = 0.0;  // interface error estimate accumulated since the last LB block
+  int rc;
+  for (int b = 0; b <= blocks; ++b) {
+    // read-out of the current state; its interface positions (pcross[4..7])
+    SCK(h, lbk::launch_surrogate_gather(h->m, h->pops[h->cur], vec4(cfg->shift), vec4(cfg->scale),
+                                        net->px, net->pF, s));
+    plane_crossing_kernel<<<1, 32, 0, s>>>(net->pF, h->m.nx, h->m.ny, h->m.bc[0], h->m.bc[1],
+                                           h->icx, h->icy, net->pcross + 4);
+    SCK(h, cudaGetLastError());
+    const bool last = b == blocks;  // only resolves the outcome of the final block
+    if (!last) {
+      if ((rc = lbpf_unet_forward(net, net->px, net->py)))
+        return sfail(h, rc, "network: %s", net->msg);
+      apply_kernel<<<grid_of(n), 256, 0, s>>>(net->pF, net->py, vec4(cfg->res_scale), 1.0f / nb,
+                                              n, net->pF1);
+      SCK(h, cudaGetLastError());
+      if ((rc = lbpf_field_sums_noalloc(net->pF1, net->pF1 + 4 * n, net->pF1 + n, net->pF + 4 * n,
+                                        n, 0, net->psum, s)))
+        return sfail(h, rc, "solute sum of the prediction");
+      plane_crossing_kernel<<<1, 32, 0, s>>>(net->pF1, h->m.nx, h->m.ny, h->m.bc[0], h->m.bc[1],
+                                             h->icx, h->icy, net->pcross);
+      SCK(h, cudaGetLastError());
+    }
+    double sums[3] = {0, 0, 0}, cross[8];
+    unsigned nerr = 0;
+    SCK(h, cudaMemcpyAsync(sums, net->psum, sizeof(sums), cudaMemcpyDeviceToHost, s));
+    SCK(h, cudaMemcpyAsync(cross, net->pcross, sizeof(cross), cudaMemcpyDeviceToHost, s));
+    SCK(h, cudaMemcpyAsync(&nerr, net->d_err, sizeof(nerr), cudaMemcpyDeviceToHost, s));
+    SCK(h, cudaStreamSynchronize(s));
+    if (nerr) return sfail(h, LBPF_ETIMEDOUT, "a tensor-core convolution gave up waiting");
+    const double* posP = cross;
+    const double* pos0 = cross + 4;
+    if (lb_pending) {
+      for (int k = 0; k < 4; ++k)
+        dref[k] = (pos0[k] >= 0 && lb_start[k] >= 0) ? pos0[k] - lb_start[k] : -1e300;
+      have_ref = true;
+      if (judge_pending) {
+        const double err = ray_diff(pred_pending, pos0);
+        r.max_iface_err = std::fmax(r.max_iface_err, err);
+        trusted = pending_ok && err >= 0.0 && err <= tol;
+      }
+      lb_pending = false;
+    }
+    if (last) break;
+    const double drift = std::fabs(sums[0] - I0) / std::fmax(std::fabs(I0), 1e-300);
+    r.max_drift = std::fmax(r.max_drift, std::isfinite(drift) ? drift : 1e300);
+    double est = -1.0;
+    if (have_ref)
+      for (int k = 0; k < 4; ++k)
+        if (posP[k] >= 0 && pos0[k] >= 0 && dref[k] > -1e300)
+          est = std::fmax(est, std::fabs((posP[k] - pos0[k]) - dref[k]));
+    if (est >= 0.0) est += acc;
+    const bool drift_ok = drift <= cfg->drift_tol;
+    const bool judge = !trusted || !have_ref || (cfg->judge_every > 0 && b % cfg->judge_every == 0);
+    const bool fails = !drift_ok || !(est >= 0.0 && est <= tol);
+    if (judge || fails) {
+      if ((rc = lbpf_step(h, nb))) return rc;
+      lb_pending = true;
+      judge_pending = judge;
+      pending_ok = drift_ok;
+      for (int k = 0; k < 4; ++k) {
+        lb_start[k] = pos0[k];
+        pred_pending[k] = posP[k];
+      }
+      acc = 0.0;
+      if (judge) {
+        ++r.judged_blocks;
+      } else {
+        trusted = false;
+        ++r.fallback_blocks;
+      }
+    } else {
+      // conservative correction: the accepted prediction's solute deficit is
+      // spread over the liquid in proportion to (1 - phi)/2, so that a
+      // committed state keeps sum(U + phi(t-1)) as the LB does
+      const double liquid = double(n) - sums[2];
+      const float k = liquid > 0.5 ? float((I0 - sums[0]) / liquid) : 0.f;
+      correct_kernel<<<grid_of(n), 256, 0, s>>>(net->pF1, n, k);
+      SCK(h, cudaGetLastError());
+      SCK(h, lbk::launch_surrogate_commit(h->m, net->pF1, net->pF + 4 * n, h->pops[h->cur],
+                                          h->phi[h->cur], s));
+      h->step += nb;
+      acc = est;
+      r.max_iface_est = std::fmax(r.max_iface_est, est);
+      ++r.surrogate_blocks;
+    }
+    ++r.blocks;
+  }
+  if (rep) *rep = r;
   return LBPF_OK;
 }
 

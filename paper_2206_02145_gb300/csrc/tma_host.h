@@ -24,15 +24,17 @@ inline PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
   return fn;
 }
 
-// Tiled map of rank 2..4 with unit element strides, no swizzle, zero fill.
+// Tiled map of rank 2..5 with unit element strides and zero fill outside the
+// tensor; optional shared-memory swizzle.
 inline bool encode_tiled(CUtensorMap* map, CUtensorMapDataType dt, int rank, void* base,
                          const uint64_t* dims, const uint64_t* strides_bytes,
-                         const uint32_t* box) {
+                         const uint32_t* box,
+                         CUtensorMapSwizzle swizzle = CU_TENSOR_MAP_SWIZZLE_NONE) {
   auto fn = tensor_map_encoder();
   if (!fn) return false;
   const uint32_t es[5] = {1, 1, 1, 1, 1};
   return fn(map, dt, rank, base, dims, strides_bytes, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
-            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            swizzle, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 

@@ -1,8 +1,10 @@
 // Kernels of the BF16 U-Net surrogate (NHWC bf16 activations, FP32
 // accumulation and master weights):
-//   conv3x3_kernel   implicit-GEMM 3x3 convolution on the warp tensor cores
-//                    (M = pixels, N = output channels, K = 9 x input channels);
-//                    also the data gradient, run on flipped / transposed weights
+//   conv3x3_kernel   implicit-GEMM 3x3 convolution on the warp-level mma.sync
+//                    path (M = pixels, N = output channels, K = 9 x input
+//                    channels); also the data gradient, run on flipped /
+//                    transposed weights.  Shapes the tcgen05 kernel of
+//                    conv_tc.cu takes go there instead.
 //   wgrad3x3_kernel  weight gradient, K = pixels, split over CTAs, FP32 atomics
 //   element-wise     bias gradient, ReLU masks, 2x2 average pooling and its
 //                    gradient, nearest 2x upsampling and its gradient, the 1x1
@@ -381,6 +383,7 @@ int blocks_for(long long n) {
 }  // namespace
 
 cudaError_t conv3x3(const ConvArgs& a, cudaStream_t s) {
+  if (a.tensor_path && a.err && conv3x3_tc_supported(a)) return conv3x3_tc(a, a.err, s);
   if (a.W % 64 || a.Cin % 16 || a.Cx % 8 || a.Cy % 8 || a.ci_off % 8 || a.co_off % 8)
     return cudaErrorInvalidValue;
   const long long npix = (long long)a.N * a.H * a.W;

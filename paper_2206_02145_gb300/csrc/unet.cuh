@@ -21,9 +21,15 @@ struct ConvArgs {
   int N, H, W;
   int relu;            // apply max(0, .) to the output
   const bf16* mask;    // zero the output where mask <= 0 (same layout as y), or null
+  int tensor_path;     // 1: tcgen05 kernel (conv_tc.cu) where the shape allows; 0: mma.sync
+  unsigned* err;       // device word: bit 2 set if a tcgen05 kernel timed out waiting
 };
 // requirements: W % 64 == 0, Cin % 16 == 0, Cout % 32 == 0, strides/offsets % 8 == 0
 cudaError_t conv3x3(const ConvArgs& a, cudaStream_t s);
+// the tcgen05 / TMEM / TMA kernel: W % 128 == 0 (or W == 64 with H even),
+// N H W % 128 == 0, Cin % 16 == 0, Cout % 32 == 0, strides / offsets % 8 == 0
+bool conv3x3_tc_supported(const ConvArgs& a);
+cudaError_t conv3x3_tc(const ConvArgs& a, unsigned* err, cudaStream_t s);
 
 struct WgradArgs {
   const bf16* x;   // layer input, as in ConvArgs

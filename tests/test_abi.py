@@ -46,7 +46,9 @@ def test_struct_layouts_match_header(lib, tmp_path):
     fields = {"lbpf_params": [f for f, _ in lib.lbpf_params._fields_],
               "lbpf_seed": [f for f, _ in lib.lbpf_seed._fields_],
               "lbpf_diag": [f for f, _ in lib.lbpf_diag._fields_],
-              "lbpf_unet_cfg": [f for f, _ in lib.lbpf_unet_cfg._fields_]}
+              "lbpf_unet_cfg": [f for f, _ in lib.lbpf_unet_cfg._fields_],
+              "lbpf_surrogate_cfg": [f for f, _ in lib.lbpf_surrogate_cfg._fields_],
+              "lbpf_surrogate_report": [f for f, _ in lib.lbpf_surrogate_report._fields_]}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "lbpf.h"', "int main(void){"]
     for st, fs in fields.items():
         lines.append(f'printf("{st} %zu\\n", sizeof({st}));')

@@ -43,11 +43,13 @@ def _cos(a, b):
     return float((a.ravel() @ b.ravel()) / (na * nb))
 
 
+@pytest.mark.parametrize("tc", [True, False], ids=["tcgen05", "mma_sync"])
 @pytest.mark.parametrize("levels,batch,h,w", [(1, 2, 8, 64), (2, 2, 16, 128), (3, 1, 8, 256)])
-def test_forward_and_gradients_match_fp64_reference(lib, levels, batch, h, w):
+def test_forward_and_gradients_match_fp64_reference(lib, levels, batch, h, w, tc):
     in_ch, out_ch = 4, 3
     net = lib.UNet(in_ch=in_ch, out_ch=out_ch, base_ch=32, levels=levels, batch=batch, height=h,
                    width=w, seed=7, stream=lib.current_stream())
+    net.set_tensor_path(tc)
     ref = UNetRef(levels, 32, in_ch, out_ch, store=_bf16)
     flat = net.weights().astype(np.float64)
     assert flat.size == sum(int(np.prod(s)) for s in ref.shapes) == net.param_count
@@ -73,6 +75,29 @@ def test_forward_and_gradients_match_fp64_reference(lib, levels, batch, h, w):
         assert a.shape == b.shape
         assert errs[i][0] < 4e-2, (i, ref.shapes[i], errs[i])
         assert errs[i][1] > 0.999, (i, ref.shapes[i], errs[i])
+    net.close()
+
+
+def test_tensor_core_paths_agree_at_full_size(lib):
+    # the 512 x 512 four-level network: tcgen05 and mma.sync kernels differ
+    # only in FP32 summation order (and the bf16 rounding that follows)
+    net = lib.UNet(in_ch=4, out_ch=4, levels=4, batch=1, height=512, width=512, seed=9,
+                   stream=lib.current_stream())
+    g = torch.Generator(device="cpu").manual_seed(3)
+    x = torch.randn(1, 512, 512, 4, generator=g).cuda()
+    t = torch.randn(1, 512, 512, 4, generator=g).cuda()
+    out = {}
+    for tc in (True, False):
+        net.set_tensor_path(tc)
+        y = torch.empty_like(x)
+        net.forward(x, y)
+        loss = net.grad(x, t)
+        out[tc] = (y.cpu().double().numpy(), loss, net.grads().astype(np.float64))
+    net.status()
+    assert _rel(out[True][0], out[False][0]) < 1e-2
+    assert out[True][1] == pytest.approx(out[False][1], rel=1e-3)
+    assert _rel(out[True][2], out[False][2]) < 3e-2
+    assert _cos(out[True][2], out[False][2]) > 0.9995
     net.close()
 
 
