@@ -4,23 +4,32 @@
 // ReLU, an optional mask, bf16 out.  The same kernel computes the data
 // gradient on flipped / transposed weights.
 //
-// One CTA computes a tile of 128 pixels (one or two image rows) x BN output
-// channels with the FP32 accumulator in tensor memory:
+// Persistent CTAs (one per SM) walk a strided list of output tiles of G
+// sub-tiles of 128 pixels (one or two image rows each) x BN output channels,
+// channel tiles innermost so that CTAs running side by side share their input
+// rows in L2.  The G sub-tiles share the weight box and accumulate into G
+// independent accumulators whose products are interleaved: with a narrow N
+// one accumulator's chain of dependent products would leave the tensor pipe
+// mostly idle.  Roles:
 //   warp 0     TMA producer: per K step (one tap, BK input channels) a 4D box
 //              of the NHWC input at the tap's shifted origin (zero fill
 //              outside the image gives the convolution's zero padding) and a
-//              3D box of the weights, into a stage of an S-deep ring
-//   warp 1     allocates tensor memory; one lane issues tcgen05.mma
-//              (kind::f16, bf16 x bf16 -> f32, M = 128, N = BN, K = 16) and
-//              frees each stage through tcgen05.commit
-//   warps 2-5  epilogue: tcgen05.ld of their 32-lane quarter of the
-//              accumulator, bias / ReLU / mask, bf16 stores
+//              3D box of the weights, into a stage of an S-deep ring that
+//              runs on across tiles
+//   warp 1     allocates tensor memory (two accumulators of BN FP32 columns);
+//              one lane issues tcgen05.mma (kind::f16, bf16 x bf16 -> f32,
+//              M = 128, N = BN, K = 16), frees each stage and hands each
+//              finished accumulator to the epilogue through tcgen05.commit
+//   warps 2-5  epilogue: tcgen05.ld of their 32-lane quarter of an
+//              accumulator, bias / ReLU / mask, bf16 stores; then release the
+//              accumulator, so that the next tile's products overlap them
 // Every wait on a barrier is bounded; on a timeout the kernel sets bit 2 of
 // *err, lets the copies and products already issued finish, frees its tensor
 // memory and returns (the host turns the bit into an error status).
 #include <cuda.h>
 
 #include <cstdint>
+#include <cstdlib>
 
 #include "tma.cuh"
 #include "tma_host.h"
@@ -95,141 +104,220 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
 struct TcArgs {
   int H, W, BW;          // image size; tile width in pixels (128 or 64)
   int ci_off, nchunks;   // first input channel; K steps per tap
+  int Cin;               // input channels
+  int mtiles, ntiles_n;  // pixel tiles, channel tiles
   int Cy, co_off, relu;  // output channel stride / offset
+  int Cout;              // output channels (bias entries)
   const float* bias;
   const bf16* mask;
   bf16* y;
   unsigned* err;
 };
 
-template <int BK, int BN>
+template <int BK, int BN, int G>
 struct TcShape {
-  static constexpr int A_BYTES = 128 * BK * 2;
+  static constexpr int A_BYTES = 128 * BK * 2;  // one 128-pixel sub-tile
   static constexpr int B_BYTES = BN * BK * 2;
-  static constexpr int STAGE = A_BYTES + B_BYTES;
-  // deep enough to cover latency, small enough for two CTAs per SM
-  static constexpr int S = STAGE <= 24576 ? 4 : (STAGE <= 36864 ? 3 : 2);
+  static constexpr int STAGE = G * A_BYTES + B_BYTES;
+  // one persistent CTA per SM: a ring as deep as ~200 KB of shared memory
+  // allows (small stages need many copies in flight to cover their latency)
+  static constexpr int S_FIT = 204800 / STAGE;
+  static constexpr int S = S_FIT > 32 ? 32 : (S_FIT < 2 ? 2 : S_FIT);
   static constexpr int SMEM = S * STAGE + 1024;  // + alignment slack
+  static_assert(SMEM <= 226 * 1024, "stage ring exceeds shared memory");
   static constexpr uint32_t SBO = 8 * BK * 2;
   static constexpr uint32_t MODE = BK == 64 ? 2 : (BK == 32 ? 4 : 6);  // 128 / 64 / 32 B swizzle
   // kind::f16 instruction descriptor: D f32, A and B bf16, both K-major, N, M = 128
   static constexpr uint32_t IDESC =
       (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(BN >> 3) << 17) | (uint32_t(128 >> 4) << 24);
-  static constexpr uint32_t TCOLS = BN < 32 ? 32 : BN;
+  static constexpr uint32_t ACC = G * BN;    // columns of one accumulator set
+  static constexpr uint32_t TCOLS = 2 * ACC;  // double-buffered
+  static_assert(TCOLS <= 512, "accumulators exceed tensor memory");
 };
 
-template <int BK, int BN>
+template <int BK, int BN, int G>
 __global__ void __launch_bounds__(kTcThreads, 1)
     conv3x3_tc_kernel(const __grid_constant__ CUtensorMap mx, const __grid_constant__ CUtensorMap mw,
                       const TcArgs a) {
-  using Sh = TcShape<BK, BN>;
+  using Sh = TcShape<BK, BN, G>;
   constexpr int S = Sh::S;
   extern __shared__ uint8_t smem_raw[];
-  __shared__ __align__(8) uint64_t full[S], empty[S], accum;
+  __shared__ __align__(8) uint64_t full[S], empty[S], acc_full[2], acc_empty[2], fin;
   __shared__ uint32_t tmem_base;
+  __shared__ float sbias[256];
   uint8_t* smem = smem_raw + ((1024u - (smem_addr(smem_raw) & 1023u)) & 1023u);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const long long pix0 = (long long)blockIdx.x * 128;
-  const int n0 = blockIdx.y * BN;
-  const int w0 = int(pix0 % a.W), h0 = int((pix0 / a.W) % a.H);
-  const int img = int(pix0 / ((long long)a.W * a.H));
   const int ksteps = 9 * a.nchunks;
+  const int ntiles = (a.mtiles / G) * a.ntiles_n;  // a tile: G x 128 pixels x BN channels
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < S; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
-    mbar_init(&accum, 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&acc_full[b], 1);
+      mbar_init(&acc_empty[b], 4);  // one arrival per epilogue warp
+    }
+    mbar_init(&fin, 1);
     fence_barrier_init();
   }
   if (warp == 1) tmem_alloc(&tmem_base, Sh::TCOLS);
+  for (int i = threadIdx.x; i < a.Cout; i += blockDim.x) sbias[i] = a.bias ? a.bias[i] : 0.f;
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = tmem_base;
 
   if (warp == 0 && lane == 0) {
-    int issued = 0;
-    for (int ks = 0; ks < ksteps; ++ks) {
-      const int st = ks % S, use = ks / S;
-      if (ks >= S && !mbar_wait_bounded(&empty[st], uint32_t(use - 1) & 1u, kTcSpin)) {
-        atomicOr(a.err, 2u);
-        break;
+    // producer: coordinates once per tile, counters instead of divisions
+    int st = 0, it = 0;
+    uint32_t ph = 0;  // phase of the current pass over the ring
+    bool ok = true;
+    for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+      const long long pix0 = (long long)(t / a.ntiles_n) * (128 * G);
+      const int n0 = (t % a.ntiles_n) * BN;
+      int wg[G], hg[G], ig[G];
+#pragma unroll
+      for (int g = 0; g < G; ++g) {
+        const long long pg = pix0 + g * 128;
+        wg[g] = int(pg % a.W) - 1;
+        hg[g] = int((pg / a.W) % a.H) - 1;
+        ig[g] = int(pg / ((long long)a.W * a.H));
       }
-      const int tap = ks / a.nchunks, c0 = (ks % a.nchunks) * BK;
-      const int ky = tap / 3, kx = tap % 3;
-      uint8_t* sa = smem + st * Sh::STAGE;
-      mbar_arrive_expect_tx(&full[st], Sh::STAGE);
-      tma_load_4d(sa, &mx, &full[st], a.ci_off + c0, w0 + kx - 1, h0 + ky - 1, img);
-      tma_load_3d(sa + Sh::A_BYTES, &mw, &full[st], c0, n0, tap);
-      issued = ks + 1;
+      int c0 = 0, kx = 0, ky = 0;
+      for (int ks = 0; ks < ksteps; ++ks, ++it) {
+        if (it >= S && !mbar_wait_bounded(&empty[st], ph ^ 1u, kTcSpin)) {
+          atomicOr(a.err, 2u);
+          ok = false;
+          break;
+        }
+        uint8_t* sa = smem + st * Sh::STAGE;
+        mbar_arrive_expect_tx(&full[st], Sh::STAGE);
+#pragma unroll
+        for (int g = 0; g < G; ++g)
+          tma_load_4d(sa + g * Sh::A_BYTES, &mx, &full[st], a.ci_off + c0, wg[g] + kx, hg[g] + ky,
+                      ig[g]);
+        tma_load_3d(sa + G * Sh::A_BYTES, &mw, &full[st], c0, n0, ky * 3 + kx);
+        c0 += BK;
+        if (c0 == a.Cin) {
+          c0 = 0;
+          if (++kx == 3) {
+            kx = 0;
+            ++ky;
+          }
+        }
+        if (++st == S) {
+          st = 0;
+          ph ^= 1u;
+        }
+      }
     }
     // every issued copy has landed before the CTA may finish
-    for (int ks = issued > S ? issued - S : 0; ks < issued; ++ks)
-      if (!mbar_wait_bounded(&full[ks % S], uint32_t(ks / S) & 1u, kTcSpin)) atomicOr(a.err, 2u);
+    for (int j = it > S ? it - S : 0; j < it; ++j)
+      if (!mbar_wait_bounded(&full[j % S], uint32_t(j / S) & 1u, kTcSpin)) atomicOr(a.err, 2u);
   } else if (warp == 1 && lane == 0) {
-    for (int ks = 0; ks < ksteps; ++ks) {
-      const int st = ks % S;
-      if (!mbar_wait_bounded(&full[st], uint32_t(ks / S) & 1u, kTcSpin)) {
+    // MMA issuer: descriptors as offsets from a precomputed base (the start
+    // address field holds address / 16; shared addresses stay below 256 KB)
+    const uint64_t d0 = umma_desc(smem_addr(smem), Sh::SBO, Sh::MODE);
+    int st = 0, tc = 0;
+    uint32_t ph = 0;
+    bool ok = true;
+    for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++tc) {
+      const int buf = tc & 1;
+      if (tc >= 2 && !mbar_wait_bounded(&acc_empty[buf], uint32_t((tc >> 1) - 1) & 1u, kTcSpin)) {
         atomicOr(a.err, 2u);
         break;
       }
       tc_fence_after();
-      const uint32_t sa = smem_addr(smem + st * Sh::STAGE), sb = sa + Sh::A_BYTES;
-#pragma unroll
-      for (int kk = 0; kk < BK / 16; ++kk)
-        tc_mma(tmem, umma_desc(sa + kk * 32, Sh::SBO, Sh::MODE),
-               umma_desc(sb + kk * 32, Sh::SBO, Sh::MODE), Sh::IDESC, (ks | kk) != 0);
-      tc_commit(&empty[st]);
-    }
-    tc_commit(&accum);  // also after an abort: the products issued so far complete
-  } else if (warp >= 2) {
-    bool ok = mbar_wait_bounded(&accum, 0u, kTcSpin);
-    ok = __all_sync(0xffffffffu, ok);
-    tc_fence_after();
-    if (!ok) {
-      if (lane == 0) atomicOr(a.err, 2u);
-    } else {
-      const int q = warp & 3;  // tensor-memory lanes 32q .. 32q + 31
-      const int m = q * 32 + lane;
-      const long long p =
-          ((long long)img * a.H + h0 + m / a.BW) * a.W + w0 + (m % a.BW);
-      bf16* yrow = a.y + p * a.Cy + a.co_off + n0;
-      const bf16* mrow = a.mask ? a.mask + p * a.Cy + a.co_off + n0 : nullptr;
-#pragma unroll 1
-      for (int c = 0; c < BN; c += 32) {
-        uint32_t r[32];
-        tmem_ld32(tmem + (uint32_t(q * 32) << 16) + uint32_t(c), r);
-        uint4 mk[4];
-        if (mrow)
-#pragma unroll
-          for (int v = 0; v < 4; ++v) mk[v] = reinterpret_cast<const uint4*>(mrow + c)[v];
-        uint32_t out[16];
-#pragma unroll
-        for (int j = 0; j < 32; j += 2) {
-          float v0 = __uint_as_float(r[j]), v1 = __uint_as_float(r[j + 1]);
-          if (a.bias) {
-            v0 += a.bias[n0 + c + j];
-            v1 += a.bias[n0 + c + j + 1];
-          }
-          if (a.relu) {
-            v0 = fmaxf(v0, 0.f);
-            v1 = fmaxf(v1, 0.f);
-          }
-          if (mrow) {
-            const __nv_bfloat162 mm = reinterpret_cast<const __nv_bfloat162*>(mk)[j / 2];
-            if (!(__low2float(mm) > 0.f)) v0 = 0.f;
-            if (!(__high2float(mm) > 0.f)) v1 = 0.f;
-          }
-          const __nv_bfloat162 o = __floats2bfloat162_rn(v0, v1);
-          out[j / 2] = *reinterpret_cast<const uint32_t*>(&o);
+      const uint32_t d = tmem + uint32_t(buf * Sh::ACC);
+      for (int ks = 0; ks < ksteps; ++ks) {
+        if (!mbar_wait_bounded(&full[st], ph, kTcSpin)) {
+          atomicOr(a.err, 2u);
+          ok = false;
+          break;
         }
+        tc_fence_after();
+        const uint64_t ds = d0 + uint64_t((st * Sh::STAGE) >> 4);
+        // the G sub-tiles accumulate independently: interleaving them keeps
+        // several products in flight on the tensor pipe
 #pragma unroll
-        for (int v = 0; v < 4; ++v)
-          reinterpret_cast<uint4*>(yrow + c)[v] =
-              make_uint4(out[4 * v], out[4 * v + 1], out[4 * v + 2], out[4 * v + 3]);
+        for (int kk = 0; kk < BK / 16; ++kk) {
+          const uint64_t db = ds + uint64_t((G * Sh::A_BYTES + kk * 32) >> 4);
+#pragma unroll
+          for (int g = 0; g < G; ++g)
+            tc_mma(d + uint32_t(g * BN), ds + uint64_t((g * Sh::A_BYTES + kk * 32) >> 4), db,
+                   Sh::IDESC, (ks | kk) != 0);
+        }
+        tc_commit(&empty[st]);
+        if (++st == S) {
+          st = 0;
+          ph ^= 1u;
+        }
       }
+      if (ok) tc_commit(&acc_full[buf]);
+    }
+    // all products issued by this CTA are complete before its tensor memory is freed
+    tc_commit(&fin);
+    if (!mbar_wait_bounded(&fin, 0u, kTcSpin)) atomicOr(a.err, 2u);
+  } else if (warp >= 2) {
+    const int q = warp & 3;  // tensor-memory lanes 32q .. 32q + 31
+    const int m = q * 32 + lane;
+    int tc = 0;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++tc) {
+      const int buf = tc & 1;
+      bool ok = mbar_wait_bounded(&acc_full[buf], uint32_t(tc >> 1) & 1u, kTcSpin);
+      ok = __all_sync(0xffffffffu, ok);
+      if (!ok) {
+        if (lane == 0) atomicOr(a.err, 2u);
+        break;
+      }
+      tc_fence_after();
+      const long long pix0 = (long long)(t / a.ntiles_n) * (128 * G);
+      const int n0 = (t % a.ntiles_n) * BN;
+#pragma unroll 1
+      for (int g = 0; g < G; ++g) {
+        const long long pg = pix0 + g * 128;
+        const int w0 = int(pg % a.W), h0 = int((pg / a.W) % a.H);
+        const int img = int(pg / ((long long)a.W * a.H));
+        const long long p = ((long long)img * a.H + h0 + m / a.BW) * a.W + w0 + (m % a.BW);
+        bf16* yrow = a.y + p * a.Cy + a.co_off + n0;
+        const bf16* mrow = a.mask ? a.mask + p * a.Cy + a.co_off + n0 : nullptr;
+#pragma unroll 1
+        for (int c = 0; c < BN; c += 32) {
+          uint32_t r[32];
+          tmem_ld32(tmem + (uint32_t(q * 32) << 16) + uint32_t(buf * Sh::ACC + g * BN + c), r);
+          uint4 mk[4];
+          if (mrow)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) mk[v] = reinterpret_cast<const uint4*>(mrow + c)[v];
+          uint32_t out[16];
+#pragma unroll
+          for (int j = 0; j < 32; j += 2) {
+            float v0 = __uint_as_float(r[j]) + sbias[n0 + c + j];
+            float v1 = __uint_as_float(r[j + 1]) + sbias[n0 + c + j + 1];
+            if (a.relu) {
+              v0 = fmaxf(v0, 0.f);
+              v1 = fmaxf(v1, 0.f);
+            }
+            if (mrow) {
+              const __nv_bfloat162 mm = reinterpret_cast<const __nv_bfloat162*>(mk)[j / 2];
+              if (!(__low2float(mm) > 0.f)) v0 = 0.f;
+              if (!(__high2float(mm) > 0.f)) v1 = 0.f;
+            }
+            const __nv_bfloat162 o = __floats2bfloat162_rn(v0, v1);
+            out[j / 2] = *reinterpret_cast<const uint32_t*>(&o);
+          }
+#pragma unroll
+          for (int v = 0; v < 4; ++v)
+            reinterpret_cast<uint4*>(yrow + c)[v] =
+                make_uint4(out[4 * v], out[4 * v + 1], out[4 * v + 2], out[4 * v + 3]);
+        }
+      }
+      // this warp's reads of the accumulator are done: hand it back
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&acc_empty[buf]);
     }
     tc_fence_before();
   }
@@ -246,30 +334,47 @@ CUtensorMapSwizzle swizzle_for(int bk) {
                   : (bk == 32 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_32B);
 }
 
-template <int BK, int BN>
-cudaError_t launch_tc(const ConvArgs& c, const CUtensorMap& mx, const CUtensorMap& mw,
-                      const TcArgs& t, unsigned grid_x, cudaStream_t s) {
-  using Sh = TcShape<BK, BN>;
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(conv3x3_tc_kernel<BK, BN>,
+template <int BK, int BN, int G>
+cudaError_t launch_tc(const CUtensorMap& mx, const CUtensorMap& mw, const TcArgs& t,
+                      cudaStream_t s) {
+  using Sh = TcShape<BK, BN, G>;
+  static int sms = 0;
+  if (!sms) {
+    cudaError_t e = cudaFuncSetAttribute(conv3x3_tc_kernel<BK, BN, G>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, Sh::SMEM);
     if (e != cudaSuccess) return e;
-    attr = true;
+    int dev = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+      return e;
   }
-  conv3x3_tc_kernel<BK, BN>
-      <<<dim3(grid_x, unsigned(c.Cout / BN)), kTcThreads, Sh::SMEM, s>>>(mx, mw, t);
+  // one CTA per SM: the ring fills the shared memory, the accumulators the TMEM
+  const long long tiles = (long long)(t.mtiles / G) * t.ntiles_n;
+  const unsigned grid = unsigned(tiles < sms ? tiles : sms);
+  conv3x3_tc_kernel<BK, BN, G><<<grid, kTcThreads, Sh::SMEM, s>>>(mx, mw, t);
   return cudaGetLastError();
 }
 
+// G sub-tiles per tile (independent accumulators); the widest shapes stay
+// within 227 KB of shared memory and 512 TMEM columns
+template <int BK, int BN>
+cudaError_t launch_g(int g, const CUtensorMap& mx, const CUtensorMap& mw, const TcArgs& t,
+                     cudaStream_t s) {
+  if (BN == 32 && BK < 64 && g == 8) return launch_tc<BK, BN, (BN == 32 && BK < 64) ? 8 : 1>(mx, mw, t, s);
+  if (BN <= 64 && g == 4) return launch_tc<BK, BN, (BN <= 64) ? 4 : 1>(mx, mw, t, s);
+  if (BN <= 128 && g == 2) return launch_tc<BK, BN, (BN <= 128) ? 2 : 1>(mx, mw, t, s);
+  if (g == 1) return launch_tc<BK, BN, 1>(mx, mw, t, s);
+  return cudaErrorInvalidValue;
+}
+
 template <int BK>
-cudaError_t launch_bn(int bn, const ConvArgs& c, const CUtensorMap& mx, const CUtensorMap& mw,
-                      const TcArgs& t, unsigned gx, cudaStream_t s) {
+cudaError_t launch_bn(int bn, int g, const CUtensorMap& mx, const CUtensorMap& mw,
+                      const TcArgs& t, cudaStream_t s) {
   switch (bn) {
-    case 32: return launch_tc<BK, 32>(c, mx, mw, t, gx, s);
-    case 64: return launch_tc<BK, 64>(c, mx, mw, t, gx, s);
-    case 128: return launch_tc<BK, 128>(c, mx, mw, t, gx, s);
-    case 256: return launch_tc<BK, 256>(c, mx, mw, t, gx, s);
+    case 32: return launch_g<BK, 32>(g, mx, mw, t, s);
+    case 64: return launch_g<BK, 64>(g, mx, mw, t, s);
+    case 128: return launch_g<BK, 128>(g, mx, mw, t, s);
+    case 256: return launch_g<BK, 256>(g, mx, mw, t, s);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -279,7 +384,8 @@ cudaError_t launch_bn(int bn, const ConvArgs& c, const CUtensorMap& mx, const CU
 bool conv3x3_tc_supported(const ConvArgs& a) {
   const long long npix = (long long)a.N * a.H * a.W;
   const bool rows = a.W % 128 == 0 || (a.W == 64 && a.H % 2 == 0);
-  return rows && npix % 128 == 0 && a.Cin % 16 == 0 && a.Cout % 32 == 0 && a.Cx % 8 == 0 &&
+  return rows && npix % 128 == 0 && a.Cin % 16 == 0 && a.Cout % 32 == 0 && a.Cout <= 256 &&
+         a.Cx % 8 == 0 &&
          a.Cy % 8 == 0 && a.ci_off % 8 == 0 && a.co_off % 8 == 0 && a.ci_off + a.Cin <= a.Cx &&
          a.co_off + a.Cout <= a.Cy;
 }
@@ -288,11 +394,26 @@ cudaError_t conv3x3_tc(const ConvArgs& a, unsigned* err, cudaStream_t s) {
   if (!conv3x3_tc_supported(a) || !err) return cudaErrorInvalidValue;
   const long long npix = (long long)a.N * a.H * a.W;
   const int BK = a.Cin % 64 == 0 ? 64 : (a.Cin % 32 == 0 ? 32 : 16);
+  // the widest N the channels allow: a tcgen05.mma costs about the same time
+  // whatever its N, so wide tiles beat more tiles even when some SMs idle
   int BN = 256;
   while (BN > 32 && a.Cout % BN) BN >>= 1;
-  // small grids: split the channels further so that every SM gets work
-  while (BN > 32 && (npix / 128) * (a.Cout / BN) < 2 * 152) BN >>= 1;
+  if (const char* e = getenv("LBPF_CONV_MAX_BN")) {
+    const int cap = atoi(e);
+    while (BN > 32 && BN > cap) BN >>= 1;
+  }
   const int BW = a.W % 128 == 0 ? 128 : 64;
+  // sub-tiles per tile: about 256 accumulator columns per K step, as many
+  // tiles as SMs where the image allows, G dividing the pixel tiles
+  const long long mt = npix / 128;
+  int G = 256 / BN;
+  const int gmax = BN == 32 ? (BK < 64 ? 8 : 4) : (BN == 64 ? 4 : (BN == 128 ? 2 : 1));
+  if (G > gmax) G = gmax;
+  while (G > 1 && (mt % G || (mt / G) * (a.Cout / BN) < 152)) G >>= 1;
+  if (const char* e = getenv("LBPF_CONV_G")) {
+    const int want = atoi(e);
+    while (G > 1 && G > want) G >>= 1;
+  }
   CUtensorMap mx, mw;
   {
     const uint64_t dims[4] = {uint64_t(a.Cx), uint64_t(a.W), uint64_t(a.H), uint64_t(a.N)};
@@ -324,11 +445,14 @@ cudaError_t conv3x3_tc(const ConvArgs& a, unsigned* err, cudaStream_t s) {
   t.mask = a.mask;
   t.y = a.y;
   t.err = err;
-  const unsigned gx = unsigned(npix / 128);
+  t.mtiles = int(npix / 128);
+  t.ntiles_n = a.Cout / BN;
+  t.Cout = a.Cout;
+  t.Cin = a.Cin;
   switch (BK) {
-    case 64: return launch_bn<64>(BN, a, mx, mw, t, gx, s);
-    case 32: return launch_bn<32>(BN, a, mx, mw, t, gx, s);
-    default: return launch_bn<16>(BN, a, mx, mw, t, gx, s);
+    case 64: return launch_bn<64>(BN, G, mx, mw, t, s);
+    case 32: return launch_bn<32>(BN, G, mx, mw, t, s);
+    default: return launch_bn<16>(BN, G, mx, mw, t, s);
   }
 }
 

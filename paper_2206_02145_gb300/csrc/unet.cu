@@ -196,144 +196,245 @@ __global__ void __launch_bounds__(kThreads) wgrad3x3_kernel(const WgradArgs a) {
 }
 
 // ---- element-wise kernels -------------------------------------------------------------
+// All of them move 8 channels (16 bytes) per thread and iteration; channel
+// counts, strides and offsets are multiples of 8.
+using V8 = uint4;  // 8 bf16
+
+__device__ __forceinline__ void unpack8(const V8& v, float (&f)[8]) {
+  const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&v);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    f[2 * i] = __low2float(h[i]);
+    f[2 * i + 1] = __high2float(h[i]);
+  }
+}
+__device__ __forceinline__ V8 pack8(const float (&f)[8]) {
+  V8 v;
+  __nv_bfloat162* h = reinterpret_cast<__nv_bfloat162*>(&v);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) h[i] = __floats2bfloat162_rn(f[2 * i], f[2 * i + 1]);
+  return v;
+}
+__device__ __forceinline__ const V8& ld8(const bf16* p) { return *reinterpret_cast<const V8*>(p); }
+__device__ __forceinline__ void st8(bf16* p, const V8& v) { *reinterpret_cast<V8*>(p) = v; }
+
+// bias gradient db[c] += sum over pixels of g[p][off + c]: each thread owns
+// one group of 8 channels and a stride of pixels; block reduction in shared
+// memory, one atomic per channel and block
 __global__ void bias_grad_kernel(const bf16* g, int Cg, int off, int C, long long npix,
                                  float* db) {
-  // one thread per channel and pixel stripe
-  const int c = blockIdx.y * blockDim.x + threadIdx.x;
-  if (c >= C) return;
-  float s = 0.f;
-  for (long long p = blockIdx.x; p < npix; p += gridDim.x)
-    s += __bfloat162float(g[p * Cg + off + c]);
-  atomicAdd(db + c, s);
+  __shared__ float red[256][8];
+  const int groups = C / 8;
+  const int lanes = blockDim.x / groups;  // pixel lanes per block
+  const int cg = threadIdx.x % groups, pl = threadIdx.x / groups;
+  float acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  if (pl < lanes)
+    for (long long p = (long long)blockIdx.x * lanes + pl; p < npix; p += (long long)gridDim.x * lanes) {
+      float f[8];
+      unpack8(ld8(g + p * Cg + off + cg * 8), f);
+#pragma unroll
+      for (int i = 0; i < 8; ++i) acc[i] += f[i];
+    }
+#pragma unroll
+  for (int i = 0; i < 8; ++i) red[threadIdx.x][i] = acc[i];
+  __syncthreads();
+  if (threadIdx.x < groups) {
+    float s[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (int l = 0; l < lanes; ++l)
+#pragma unroll
+      for (int i = 0; i < 8; ++i) s[i] += red[l * groups + threadIdx.x][i];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) atomicAdd(db + threadIdx.x * 8 + i, s[i]);
+  }
 }
 
+// g = 0 where act <= 0
 __global__ void mask_kernel(bf16* g, int Cg, int goff, const bf16* act, int Ca, int aoff, int C,
                             long long npix) {
-  const long long n = npix * C;
+  const int groups = C / 8;
+  const long long n = npix * groups;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x) {
-    const long long p = i / C;
-    const int c = int(i % C);
-    if (!(__bfloat162float(act[p * Ca + aoff + c]) > 0.f)) g[p * Cg + goff + c] = __float2bfloat16(0.f);
+    const long long p = i / groups;
+    const int c = int(i % groups) * 8;
+    float gv[8], av[8];
+    unpack8(ld8(g + p * Cg + goff + c), gv);
+    unpack8(ld8(act + p * Ca + aoff + c), av);
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+      if (!(av[k] > 0.f)) gv[k] = 0.f;
+    st8(g + p * Cg + goff + c, pack8(gv));
   }
 }
 
 // y[b][h/2][w/2][c] = mean of the 2x2 block of x
 __global__ void avgpool_kernel(const bf16* x, int Cx, int xoff, bf16* y, int Cy, int yoff, int C,
                                int B, int H, int W) {
-  const int Ho = H / 2, Wo = W / 2;
-  const long long n = (long long)B * Ho * Wo * C;
+  const int Ho = H / 2, Wo = W / 2, groups = C / 8;
+  const long long n = (long long)B * Ho * Wo * groups;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x) {
-    const int c = int(i % C);
-    const long long q = i / C;
+    const int c = int(i % groups) * 8;
+    const long long q = i / groups;
     const int wo = int(q % Wo), ho = int((q / Wo) % Ho);
     const long long b = q / ((long long)Wo * Ho);
     const long long p00 = (b * H + 2 * ho) * W + 2 * wo;
-    const float s = __bfloat162float(x[p00 * Cx + xoff + c]) +
-                    __bfloat162float(x[(p00 + 1) * Cx + xoff + c]) +
-                    __bfloat162float(x[(p00 + W) * Cx + xoff + c]) +
-                    __bfloat162float(x[(p00 + W + 1) * Cx + xoff + c]);
-    y[q * Cy + yoff + c] = __float2bfloat16(0.25f * s);
+    float s[8], t[8];
+    unpack8(ld8(x + p00 * Cx + xoff + c), s);
+    unpack8(ld8(x + (p00 + 1) * Cx + xoff + c), t);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) s[k] += t[k];
+    unpack8(ld8(x + (p00 + W) * Cx + xoff + c), t);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) s[k] += t[k];
+    unpack8(ld8(x + (p00 + W + 1) * Cx + xoff + c), t);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) s[k] = 0.25f * (s[k] + t[k]);
+    st8(y + q * Cy + yoff + c, pack8(s));
   }
 }
 
 // g_skip = (g_skip + 0.25 g_pool[pooled position]) * (skip > 0)
 __global__ void pool_bwd_add_mask_kernel(bf16* gs, const bf16* gp, const bf16* act, int Cs,
                                          int soff, int C, int B, int H, int W) {
-  const long long n = (long long)B * H * W * C;
+  const int groups = C / 8;
+  const long long n = (long long)B * H * W * groups;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x) {
-    const int c = int(i % C);
-    const long long p = i / C;
+    const int c = int(i % groups) * 8;
+    const long long p = i / groups;
     const int w = int(p % W), h = int((p / W) % H);
     const long long b = p / ((long long)W * H);
     const long long q = (b * (H / 2) + h / 2) * (W / 2) + w / 2;
-    float v = __bfloat162float(gs[p * Cs + soff + c]) + 0.25f * __bfloat162float(gp[q * C + c]);
-    if (!(__bfloat162float(act[p * Cs + soff + c]) > 0.f)) v = 0.f;
-    gs[p * Cs + soff + c] = __float2bfloat16(v);
+    float v[8], u[8], a[8];
+    unpack8(ld8(gs + p * Cs + soff + c), v);
+    unpack8(ld8(gp + q * C + c), u);
+    unpack8(ld8(act + p * Cs + soff + c), a);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) v[k] = a[k] > 0.f ? v[k] + 0.25f * u[k] : 0.f;
+    st8(gs + p * Cs + soff + c, pack8(v));
   }
 }
 
-// nearest 2x upsampling: y[b][h][w][c] = x[b][h/2][w/2][c]
+// nearest 2x upsampling: each source pixel's 8 channels go to its 2x2 block
 __global__ void upsample_kernel(const bf16* x, bf16* y, int C, int B, int H, int W) {
-  const long long n = (long long)B * H * W * C;
+  const int Hs = H / 2, Ws = W / 2, groups = C / 8;
+  const long long n = (long long)B * Hs * Ws * groups;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x) {
-    const int c = int(i % C);
-    const long long p = i / C;
-    const int w = int(p % W), h = int((p / W) % H);
-    const long long b = p / ((long long)W * H);
-    y[p * C + c] = x[((b * (H / 2) + h / 2) * (W / 2) + w / 2) * C + c];
+    const int c = int(i % groups) * 8;
+    const long long q = i / groups;
+    const int ws = int(q % Ws), hs = int((q / Ws) % Hs);
+    const long long b = q / ((long long)Ws * Hs);
+    const V8 v = ld8(x + q * C + c);
+    const long long p00 = (b * H + 2 * hs) * W + 2 * ws;
+    st8(y + p00 * C + c, v);
+    st8(y + (p00 + 1) * C + c, v);
+    st8(y + (p00 + W) * C + c, v);
+    st8(y + (p00 + W + 1) * C + c, v);
   }
 }
 
 // gradient of the upsampling (sum of the 2x2 block), masked by act > 0
 __global__ void upsample_bwd_mask_kernel(const bf16* g, bf16* gx, const bf16* act, int C, int B,
                                          int H, int W) {
-  const int Ho = H / 2, Wo = W / 2;
-  const long long n = (long long)B * Ho * Wo * C;
+  const int Ho = H / 2, Wo = W / 2, groups = C / 8;
+  const long long n = (long long)B * Ho * Wo * groups;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x) {
-    const int c = int(i % C);
-    const long long q = i / C;
+    const int c = int(i % groups) * 8;
+    const long long q = i / groups;
     const int wo = int(q % Wo), ho = int((q / Wo) % Ho);
     const long long b = q / ((long long)Wo * Ho);
     const long long p00 = (b * H + 2 * ho) * W + 2 * wo;
-    float s = __bfloat162float(g[p00 * C + c]) + __bfloat162float(g[(p00 + 1) * C + c]) +
-              __bfloat162float(g[(p00 + W) * C + c]) + __bfloat162float(g[(p00 + W + 1) * C + c]);
-    if (!(__bfloat162float(act[q * C + c]) > 0.f)) s = 0.f;
-    gx[q * C + c] = __float2bfloat16(s);
+    float s[8], t[8], a[8];
+    unpack8(ld8(g + p00 * C + c), s);
+    unpack8(ld8(g + (p00 + 1) * C + c), t);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) s[k] += t[k];
+    unpack8(ld8(g + (p00 + W) * C + c), t);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) s[k] += t[k];
+    unpack8(ld8(g + (p00 + W + 1) * C + c), t);
+    unpack8(ld8(act + q * C + c), a);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) s[k] = a[k] > 0.f ? s[k] + t[k] : 0.f;
+    st8(gx + q * C + c, pack8(s));
   }
 }
 
-// 1x1 head: y[p][o] = b[o] + sum_c x[p][c] w[o][c] (FP32 out)
+// 1x1 head: y[p][o] = b[o] + sum_c x[p][c] w[o][c] (FP32 out); one pixel per
+// thread, weights staged in shared memory
 __global__ void head_fwd_kernel(const bf16* x, int C, const float* w, const float* b, float* y,
                                 int O, long long npix) {
+  __shared__ float sw[8 * 256 + 8];
+  for (int i = threadIdx.x; i < O * C; i += blockDim.x) sw[i] = w[i];
+  if (threadIdx.x < O) sw[8 * 256 + threadIdx.x] = b[threadIdx.x];
+  __syncthreads();
   for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < npix;
        p += (long long)gridDim.x * blockDim.x) {
-    for (int o = 0; o < O; ++o) {
-      float s = b[o];
-      for (int c = 0; c < C; ++c) s += __bfloat162float(x[p * C + c]) * w[o * C + c];
-      y[p * O + o] = s;
+    float acc[8];
+    for (int o = 0; o < O; ++o) acc[o] = sw[8 * 256 + o];
+    for (int c = 0; c < C; c += 8) {
+      float f[8];
+      unpack8(ld8(x + p * C + c), f);
+      for (int o = 0; o < O; ++o)
+#pragma unroll
+        for (int k = 0; k < 8; ++k) acc[o] += f[k] * sw[o * C + c + k];
     }
+    for (int o = 0; o < O; ++o) y[p * O + o] = acc[o];
   }
 }
 
-// head gradient: gx = (gy w) * (x > 0) (bf16); dw += gy^T x; db += sum gy
+// head gradient for a tile of 256 pixels per block: gx = (gy w) * (x > 0)
+// (bf16, one pixel per thread); dw[o][c] += sum_p gy[p][o] x[p][c] and
+// db[o] += sum_p gy[p][o] from the tile staged in shared memory
 __global__ void head_bwd_kernel(const bf16* x, int C, const float* w, const float* gy, int O,
                                 long long npix, bf16* gx, float* dw, float* db) {
-  __shared__ float sdw[256], sdb[8];
-  for (int i = threadIdx.x; i < O * C; i += blockDim.x) sdw[i] = 0.f;
-  if (threadIdx.x < O) sdb[threadIdx.x] = 0.f;
-  __syncthreads();
-  float ldw[128];
-  float ldb[8];
-  for (int i = 0; i < O * C; ++i) ldw[i] = 0.f;
-  for (int o = 0; o < O; ++o) ldb[o] = 0.f;
-  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < npix;
-       p += (long long)gridDim.x * blockDim.x) {
-    for (int c = 0; c < C; ++c) {
-      const float xv = __bfloat162float(x[p * C + c]);
-      float s = 0.f;
-      for (int o = 0; o < O; ++o) {
-        const float g = gy[p * O + o];
-        s += g * w[o * C + c];
-        ldw[o * C + c] += g * xv;
-      }
-      gx[p * C + c] = __float2bfloat16(xv > 0.f ? s : 0.f);
+  __shared__ float sx[256][33];
+  __shared__ float sg[256][8];
+  __shared__ float sw[8 * 32];
+  for (int i = threadIdx.x; i < O * C; i += blockDim.x) sw[i] = w[i];
+  for (long long base = (long long)blockIdx.x * 256; base < npix; base += (long long)gridDim.x * 256) {
+    __syncthreads();
+    const long long p = base + threadIdx.x;
+    const bool in = p < npix;
+    for (int c = 0; c < C; c += 8) {
+      float f[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+      if (in) unpack8(ld8(x + p * C + c), f);
+#pragma unroll
+      for (int k = 0; k < 8; ++k) sx[threadIdx.x][c + k] = f[k];
     }
-    for (int o = 0; o < O; ++o) ldb[o] += gy[p * O + o];
+    for (int o = 0; o < O; ++o) sg[threadIdx.x][o] = in ? gy[p * O + o] : 0.f;
+    if (in)
+      for (int c = 0; c < C; c += 8) {
+        float f[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          float s = 0.f;
+          for (int o = 0; o < O; ++o) s += sg[threadIdx.x][o] * sw[o * C + c + k];
+          f[k] = sx[threadIdx.x][c + k] > 0.f ? s : 0.f;
+        }
+        st8(gx + p * C + c, pack8(f));
+      }
+    __syncthreads();
+    if (threadIdx.x < O * C) {
+      const int o = threadIdx.x / C, c = threadIdx.x % C;
+      float s = 0.f;
+      for (int r = 0; r < 256; ++r) s += sg[r][o] * sx[r][c];
+      atomicAdd(dw + threadIdx.x, s);
+    } else if (threadIdx.x >= 128 && threadIdx.x < 128 + O) {
+      const int o = threadIdx.x - 128;
+      float s = 0.f;
+      for (int r = 0; r < 256; ++r) s += sg[r][o];
+      atomicAdd(db + o, s);
+    }
   }
-  for (int i = 0; i < O * C; ++i) atomicAdd(&sdw[i], ldw[i]);
-  for (int o = 0; o < O; ++o) atomicAdd(&sdb[o], ldb[o]);
-  __syncthreads();
-  for (int i = threadIdx.x; i < O * C; i += blockDim.x) atomicAdd(dw + i, sdw[i]);
-  if (threadIdx.x < O) atomicAdd(db + threadIdx.x, sdb[threadIdx.x]);
 }
 
-// MSE: loss += sum (y - t)^2 / n; gy = 2 (y - t) / n
+// MSE: loss += sum (y - t)^2 / n; gy = 2 (y - t) / n (one atomic per block)
 __global__ void mse_kernel(const float* y, const float* t, long long n, float* gy, float* loss) {
+  __shared__ float ws[32];
   float s = 0.f;
   const float inv = 1.f / float(n);
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
@@ -343,7 +444,13 @@ __global__ void mse_kernel(const float* y, const float* t, long long n, float* g
     gy[i] = 2.f * d * inv;
   }
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  if ((threadIdx.x & 31) == 0) atomicAdd(loss, s * inv);
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    s = threadIdx.x < (blockDim.x >> 5) ? ws[threadIdx.x] : 0.f;
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (threadIdx.x == 0) atomicAdd(loss, s * inv);
+  }
 }
 
 // Adam with bias correction; refreshes the bf16 copy and clears the gradient
@@ -418,47 +525,62 @@ cudaError_t wgrad3x3(const WgradArgs& args, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+bool v8(int a) { return a % 8 == 0; }
+
 cudaError_t bias_grad(const bf16* g, int Cg, int off, int C, long long npix, float* db,
                       cudaStream_t s) {
-  bias_grad_kernel<<<dim3(256, (C + 127) / 128), 128, 0, s>>>(g, Cg, off, C, npix, db);
+  if (!v8(C) || !v8(Cg) || !v8(off) || C > 2048) return cudaErrorInvalidValue;
+  const int groups = C / 8, lanes = 256 / groups > 0 ? 256 / groups : 1;
+  long long blocks = (npix + lanes * 16 - 1) / (lanes * 16);
+  if (blocks > 152 * 8) blocks = 152 * 8;
+  if (blocks < 1) blocks = 1;
+  bias_grad_kernel<<<int(blocks), groups * lanes, 0, s>>>(g, Cg, off, C, npix, db);
   return cudaGetLastError();
 }
 cudaError_t relu_mask(bf16* g, int Cg, int goff, const bf16* act, int Ca, int aoff, int C,
                       long long npix, cudaStream_t s) {
-  mask_kernel<<<blocks_for(npix * C), 256, 0, s>>>(g, Cg, goff, act, Ca, aoff, C, npix);
+  if (!v8(C) || !v8(Cg) || !v8(goff) || !v8(Ca) || !v8(aoff)) return cudaErrorInvalidValue;
+  mask_kernel<<<blocks_for(npix * C / 8), 256, 0, s>>>(g, Cg, goff, act, Ca, aoff, C, npix);
   return cudaGetLastError();
 }
 cudaError_t avgpool2(const bf16* x, int Cx, int xoff, bf16* y, int Cy, int yoff, int C, int B,
                      int H, int W, cudaStream_t s) {
-  avgpool_kernel<<<blocks_for((long long)B * H * W * C / 4), 256, 0, s>>>(x, Cx, xoff, y, Cy, yoff,
-                                                                          C, B, H, W);
+  if (!v8(C) || !v8(Cx) || !v8(xoff) || !v8(Cy) || !v8(yoff)) return cudaErrorInvalidValue;
+  avgpool_kernel<<<blocks_for((long long)B * H * W * C / 32), 256, 0, s>>>(x, Cx, xoff, y, Cy,
+                                                                           yoff, C, B, H, W);
   return cudaGetLastError();
 }
 cudaError_t avgpool2_bwd_add_mask(bf16* gs, const bf16* gp, const bf16* act, int Cs, int soff,
                                   int C, int B, int H, int W, cudaStream_t s) {
-  pool_bwd_add_mask_kernel<<<blocks_for((long long)B * H * W * C), 256, 0, s>>>(
+  if (!v8(C) || !v8(Cs) || !v8(soff)) return cudaErrorInvalidValue;
+  pool_bwd_add_mask_kernel<<<blocks_for((long long)B * H * W * C / 8), 256, 0, s>>>(
       gs, gp, act, Cs, soff, C, B, H, W);
   return cudaGetLastError();
 }
 cudaError_t upsample2(const bf16* x, bf16* y, int C, int B, int H, int W, cudaStream_t s) {
-  upsample_kernel<<<blocks_for((long long)B * H * W * C), 256, 0, s>>>(x, y, C, B, H, W);
+  if (!v8(C)) return cudaErrorInvalidValue;
+  upsample_kernel<<<blocks_for((long long)B * H * W * C / 32), 256, 0, s>>>(x, y, C, B, H, W);
   return cudaGetLastError();
 }
 cudaError_t upsample2_bwd_mask(const bf16* g, bf16* gx, const bf16* act, int C, int B, int H,
                                int W, cudaStream_t s) {
-  upsample_bwd_mask_kernel<<<blocks_for((long long)B * H * W * C / 4), 256, 0, s>>>(g, gx, act, C,
-                                                                                   B, H, W);
+  if (!v8(C)) return cudaErrorInvalidValue;
+  upsample_bwd_mask_kernel<<<blocks_for((long long)B * H * W * C / 32), 256, 0, s>>>(g, gx, act,
+                                                                                    C, B, H, W);
   return cudaGetLastError();
 }
 cudaError_t head_fwd(const bf16* x, int C, const float* w, const float* b, float* y, int O,
                      long long npix, cudaStream_t s) {
+  if (!v8(C) || O > 8 || O * C > 8 * 256) return cudaErrorInvalidValue;
   head_fwd_kernel<<<blocks_for(npix), 256, 0, s>>>(x, C, w, b, y, O, npix);
   return cudaGetLastError();
 }
 cudaError_t head_bwd(const bf16* x, int C, const float* w, const float* gy, int O, long long npix,
                      bf16* gx, float* dw, float* db, cudaStream_t s) {
-  if (O * C > 128 || O > 8) return cudaErrorInvalidValue;
-  head_bwd_kernel<<<blocks_for(npix), 256, 0, s>>>(x, C, w, gy, O, npix, gx, dw, db);
+  if (O * C > 128 || O > 8 || C > 32 || !v8(C)) return cudaErrorInvalidValue;
+  long long blocks = (npix + 255) / 256;
+  if (blocks > 152 * 8) blocks = 152 * 8;
+  head_bwd_kernel<<<int(blocks), 256, 0, s>>>(x, C, w, gy, O, npix, gx, dw, db);
   return cudaGetLastError();
 }
 cudaError_t mse(const float* y, const float* t, long long n, float* gy, float* loss,

@@ -27,7 +27,7 @@ struct ConvArgs {
 // requirements: W % 64 == 0, Cin % 16 == 0, Cout % 32 == 0, strides/offsets % 8 == 0
 cudaError_t conv3x3(const ConvArgs& a, cudaStream_t s);
 // the tcgen05 / TMEM / TMA kernel: W % 128 == 0 (or W == 64 with H even),
-// N H W % 128 == 0, Cin % 16 == 0, Cout % 32 == 0, strides / offsets % 8 == 0
+// N H W % 128 == 0, Cin % 16 == 0, Cout % 32 == 0 and <= 256, strides / offsets % 8 == 0
 bool conv3x3_tc_supported(const ConvArgs& a);
 cudaError_t conv3x3_tc(const ConvArgs& a, unsigned* err, cudaStream_t s);
 
