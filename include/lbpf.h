@@ -309,8 +309,11 @@ void lbpf_unet_destroy(lbpf_unet_t* n);
  *   - its interface error estimate is at most iface_tol lattice units: the
  *     largest difference, over the axis rays of lbpf_diag.iface_pos, between
  *     the predicted interface displacement and the displacement the LB
- *     produced in its last block, summed over the blocks committed since
- *     that LB block.
+ *     produced in its most recent block; and, if iface_budget > 0, the
+ *     accumulated estimate stays within iface_budget: per ray, the signed
+ *     sum of those differences over every block the call has committed (this
+ *     one included), never reset, so that a biased network runs into the
+ *     bound and the rest of the call falls back to the LB.
  * An accepted prediction's remaining solute deficit is spread over the
  * liquid in proportion to (1 - phi)/2 before it is committed, so that the
  * committed state keeps the invariant exactly as the LB does.
@@ -322,7 +325,8 @@ typedef struct {
   int steps_per_block;       /* LB steps one network application stands for (>= 1) */
   int judge_every;           /* judge every judge_every-th block (0: only after a failed check) */
   double drift_tol;          /* relative solute drift bound (e.g. 1e-3) */
-  double iface_tol;          /* interface error bound in lattice units (e.g. 1.0) */
+  double iface_tol;          /* per-block interface error bound, lattice units (e.g. 1.0) */
+  double iface_budget;       /* bound on the accumulated estimate over a call (0: none) */
   float shift[4], scale[4];  /* input normalisation of (phi, U, ux, uy); scale != 0 */
   float res_scale[4];        /* output scale of the change of (phi, U, ux, uy) */
 } lbpf_surrogate_cfg;
@@ -334,7 +338,8 @@ typedef struct {
   int64_t fallback_blocks;   /* advanced by the LB because a check failed */
   double max_drift;          /* largest predicted relative solute drift (before correction) */
   double max_iface_err;      /* largest judged interface error (lattice units) */
-  double max_iface_est;      /* largest accumulated interface error estimate committed */
+  double max_iface_est;      /* largest per-block interface error estimate committed */
+  double iface_acc;          /* accumulated estimate at the end of the call (largest ray) */
 } lbpf_surrogate_report;
 
 /* The network input of the current state: device FP32 [ny][nx][4]. */

@@ -74,7 +74,7 @@ class lbpf_unet_cfg(ctypes.Structure):
 class lbpf_surrogate_cfg(ctypes.Structure):
     _fields_ = [("steps_per_block", ctypes.c_int), ("judge_every", ctypes.c_int),
                 ("drift_tol", ctypes.c_double), ("iface_tol", ctypes.c_double),
-                ("shift", ctypes.c_float * 4), ("scale", ctypes.c_float * 4),
+                ("iface_budget", ctypes.c_double), ("shift", ctypes.c_float * 4), ("scale", ctypes.c_float * 4),
                 ("res_scale", ctypes.c_float * 4)]
 
 
@@ -82,7 +82,7 @@ class lbpf_surrogate_report(ctypes.Structure):
     _fields_ = [("blocks", ctypes.c_int64), ("surrogate_blocks", ctypes.c_int64),
                 ("judged_blocks", ctypes.c_int64), ("fallback_blocks", ctypes.c_int64),
                 ("max_drift", ctypes.c_double), ("max_iface_err", ctypes.c_double),
-                ("max_iface_est", ctypes.c_double)]
+                ("max_iface_est", ctypes.c_double), ("iface_acc", ctypes.c_double)]
 
 
 EXPORTED = ("lbpf_params_default", "lbpf_create", "lbpf_init_seed", "lbpf_init_fields",
@@ -488,11 +488,12 @@ class UNet:
 
 
 def surrogate_cfg(steps_per_block=50, judge_every=8, drift_tol=1e-3, iface_tol=1.0,
-                  shift=(0.0, 0.3, 0.0, 0.0), scale=(1.0, 0.2, 0.01, 0.01),
+                  iface_budget=0.0, shift=(0.0, 0.3, 0.0, 0.0), scale=(1.0, 0.2, 0.01, 0.01),
                   res_scale=(0.05, 0.005, 0.001, 0.001)) -> lbpf_surrogate_cfg:
     c = lbpf_surrogate_cfg()
     c.steps_per_block, c.judge_every = int(steps_per_block), int(judge_every)
     c.drift_tol, c.iface_tol = float(drift_tol), float(iface_tol)
+    c.iface_budget = float(iface_budget)
     c.shift[:], c.scale[:], c.res_scale[:] = list(shift), list(scale), list(res_scale)
     return c
 

@@ -64,6 +64,32 @@ __device__ void store_equilibrium(const Model& m, T* pops, long long j, double p
   }
 }
 
+// The same equilibrium in the arithmetic type R (FP32 for the FP32 and 16-bit
+// storages): used where a whole state is rebuilt every few steps.
+template <typename T, typename R>
+__device__ void store_equilibrium_r(const Model& m, T* pops, long long j, R phi, R U, R rho, R ux,
+                                    R uy) {
+  const long long P = m.plane;
+  const Coef<R>& c = coef<R>(m);
+  const R ph = phi < R(-1) ? R(-1) : (phi > R(1) ? R(1) : phi);
+  const R mask = m.flow ? R(0.5) * (R(1) - ph) : R(0);
+  const R us0 = mask * ux, us1 = mask * uy;
+  const R uu = us0 * us0 + us1 * us1;
+  T* pf = pops;
+  T* pg = pops + (long long)m.qf * P;
+  T* ph_ = pops + (long long)(m.qf + m.qs) * P;
+#pragma unroll
+  for (int a = 0; a < 9; ++a) {
+    const R w = d2_w<R>(a);
+    const R cu = R(D2_CX[a]) * us0 + R(D2_CY[a]) * us1;
+    if (m.flow)
+      Pop<T>::st(pf + a * P + j,
+                 w * ((rho - c.ref_f) + rho * (R(3) * cu + R(4.5) * cu * cu - R(1.5) * uu)));
+    Pop<T>::st(pg + a * P + j, w * ((U - c.ref_g) + U * R(3) * cu));
+    Pop<T>::st(ph_ + a * P + j, w * (phi - c.ref_h));
+  }
+}
+
 template <typename T, typename R>
 __global__ void init_seed_kernel(const Model m, const SeedArgs s, T* pops, R* phi_prev) {
   const long long n = (long long)m.nx * m.ny * m.nz;
@@ -302,8 +328,9 @@ __global__ void surrogate_commit_kernel(const Model m, const float* F1, const fl
     int xx, yy, zz;
     node_xyz(m, i, xx, yy, zz);
     const long long j = pitched(m, xx, yy, 0);
-    store_equilibrium<T>(m, pops, j, F1[i], F1[n + i], rho[i], F1[2 * n + i], F1[3 * n + i], 0.0);
-    phi_prev[j] = R(double(F1[4 * n + i]) - m.ref_h);
+    store_equilibrium_r<T, R>(m, pops, j, R(F1[i]), R(F1[n + i]), R(rho[i]), R(F1[2 * n + i]),
+                              R(F1[3 * n + i]));
+    phi_prev[j] = R(F1[4 * n + i]) - coef<R>(m).ref_h;
   }
 }
 

@@ -73,6 +73,13 @@ struct lbpf_unet {
   // (phi, U, ux, uy, phi(t-1)), FP64 sums and interface crossings
   float *px = nullptr, *py = nullptr, *pF = nullptr, *pF1 = nullptr;
   double *psum = nullptr, *pcross = nullptr;
+  // the prediction phase of a block as a CUDA graph per buffer parity, with
+  // the key it was captured for; results land in pinned host memory
+  cudaGraphExec_t pgraph[2] = {nullptr, nullptr};
+  const void* pkey_pops[2] = {nullptr, nullptr};
+  lbpf_surrogate_cfg pkey_cfg[2];
+  cudaStream_t pkey_stream[2] = {nullptr, nullptr};
+  double* hres = nullptr;  // [0..2] sums, [3..10] crossings (predicted, current), [11] error word
   std::vector<void*> allocs;
   size_t bytes = 0;
   int t = 0;  // Adam step
@@ -397,30 +404,37 @@ __global__ void apply_kernel(const float* F, const float* y, const lbk::Vec4 rs,
 // lbpf_diag.iface_pos)
 __global__ void plane_crossing_kernel(const float* phi, int nx, int ny, int bcx, int bcy, int icx,
                                       int icy, double* out) {
-  const int r = threadIdx.x;
+  // one warp per ray, 32 positions per round
+  const int r = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (r >= 4) return;
   const int axis = r / 2, dir = (r & 1) ? -1 : 1;
   const int n = axis == 0 ? nx : ny, bc = axis == 0 ? bcx : bcy;
-  int c[2] = {icx, icy};
+  const int start = axis == 0 ? icx : icy;
+  auto at = [&](int d) -> float {  // phi at distance d along the ray (d in range)
+    int v = start + dir * d;
+    if (bc == LBPF_BC_PERIODIC) v = ((v % n) + n) % n;
+    return axis == 0 ? phi[(long long)icy * nx + v] : phi[(long long)v * nx + icx];
+  };
   double res = -1.0;
-  double prev = phi[(long long)c[1] * nx + c[0]];
-  if (prev >= 0.0) {
-    const int limit = bc == LBPF_BC_PERIODIC ? n / 2 : n;
-    const int start = c[axis];
-    for (int d = 1; d < limit; ++d) {
-      int v = start + dir * d;
-      if (bc == LBPF_BC_PERIODIC) v = ((v % n) + n) % n;
-      else if (v < 0 || v >= n) break;
-      c[axis] = v;
-      const double p = phi[(long long)c[1] * nx + c[0]];
-      if (p < 0.0) {
-        res = double(d - 1) + prev / (prev - p);
+  if (at(0) >= 0.f) {
+    int limit = bc == LBPF_BC_PERIODIC ? n / 2 : n;  // distances 1 .. limit - 1
+    if (bc != LBPF_BC_PERIODIC) {
+      const int room = dir > 0 ? n - 1 - start : start;  // positions inside the domain
+      if (room + 1 < limit) limit = room + 1;
+    }
+    for (int base = 1; base < limit; base += 32) {
+      const int d = base + lane;
+      const bool neg = d < limit && at(d) < 0.f;
+      const unsigned m = __ballot_sync(0xffffffffu, neg);
+      if (m) {
+        const int dd = base + __ffs(m) - 1;
+        const double p = at(dd), prev = at(dd - 1);
+        res = double(dd - 1) + prev / (prev - p);
         break;
       }
-      prev = p;
     }
   }
-  out[r] = res;
+  if (lane == 0) out[r] = res;
 }
 
 // U += k (1 - clamp(phi, -1, 1)) / 2 on the predicted planes
@@ -462,7 +476,7 @@ int sfail(lbpf* h, int code, const char* fmt, ...) {
 
 int check_cfg(const lbpf_surrogate_cfg* c) {
   if (!c || c->steps_per_block < 1 || c->judge_every < 0 || !(c->drift_tol >= 0.0) ||
-      !(c->iface_tol >= 0.0))
+      !(c->iface_tol >= 0.0) || !(c->iface_budget >= 0.0))
     return LBPF_EINVAL;
   for (int k = 0; k < 4; ++k)
     if (!(std::isfinite(c->shift[k]) && std::isfinite(c->scale[k]) && c->scale[k] != 0.f &&
@@ -686,6 +700,88 @@ int lbpf_surrogate_sample(lbpf_t* h, const lbpf_surrogate_cfg* cfg, float* x) {
   return LBPF_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+// The prediction phase of a block, queued on s: read-out of the state and its
+// interface positions, the network, the predicted planes, their FP64 sums and
+// interface positions, and the copy of those results to pinned host memory.
+int queue_prediction(lbpf* h, lbpf_unet* net, const lbpf_surrogate_cfg* cfg, cudaStream_t s) {
+  const long long n = (long long)h->m.nx * h->m.ny;
+  const int nb = cfg->steps_per_block;
+  SCK(h, lbk::launch_surrogate_gather(h->m, h->pops[h->cur], vec4(cfg->shift), vec4(cfg->scale),
+                                      net->px, net->pF, s));
+  plane_crossing_kernel<<<1, 128, 0, s>>>(net->pF, h->m.nx, h->m.ny, h->m.bc[0], h->m.bc[1], h->icx,
+                                         h->icy, net->pcross + 4);
+  SCK(h, cudaGetLastError());
+  int rc;
+  if ((rc = lbpf_unet_forward(net, net->px, net->py))) return sfail(h, rc, "network: %s", net->msg);
+  apply_kernel<<<grid_of(n), 256, 0, s>>>(net->pF, net->py, vec4(cfg->res_scale), 1.0f / nb, n,
+                                          net->pF1);
+  SCK(h, cudaGetLastError());
+  if ((rc = lbpf_field_sums_noalloc(net->pF1, net->pF1 + 4 * n, net->pF1 + n, net->pF + 4 * n, n, 0,
+                                    net->psum, s)))
+    return sfail(h, rc, "solute sum of the prediction");
+  plane_crossing_kernel<<<1, 128, 0, s>>>(net->pF1, h->m.nx, h->m.ny, h->m.bc[0], h->m.bc[1], h->icx,
+                                         h->icy, net->pcross);
+  SCK(h, cudaGetLastError());
+  SCK(h, cudaMemcpyAsync(net->hres, net->psum, 3 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  SCK(h, cudaMemcpyAsync(net->hres + 3, net->pcross, 8 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  SCK(h, cudaMemcpyAsync(net->hres + 11, net->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+  return LBPF_OK;
+}
+
+// the graph of the prediction phase for the current buffer parity, captured
+// on first use and again whenever the state buffers, stream or settings change
+int prediction_graph(lbpf* h, lbpf_unet* net, const lbpf_surrogate_cfg* cfg,
+                     cudaGraphExec_t* out) {
+  const int c = h->cur;
+  if (net->pgraph[c] && net->pkey_pops[c] == h->pops[c] && net->pkey_stream[c] == h->stream &&
+      std::memcmp(&net->pkey_cfg[c], cfg, sizeof(*cfg)) == 0) {
+    *out = net->pgraph[c];
+    return LBPF_OK;
+  }
+  if (net->pgraph[c]) {
+    cudaGraphExecDestroy(net->pgraph[c]);
+    net->pgraph[c] = nullptr;
+  }
+  // one uncaptured pass first: the first calls of some kernels set attributes
+  // and look up device symbols, which must not happen inside a capture
+  int rc = queue_prediction(h, net, cfg, h->stream);
+  if (rc) return rc;
+  SCK(h, cudaStreamSynchronize(h->stream));
+  cudaStream_t cs = nullptr;
+  SCK(h, cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  const cudaStream_t saved = net->stream;
+  net->stream = cs;
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    rc = queue_prediction(h, net, cfg, cs);
+    e = cudaStreamEndCapture(cs, &g);
+  }
+  net->stream = saved;
+  cudaStreamDestroy(cs);
+  if (rc) {
+    if (g) cudaGraphDestroy(g);
+    return rc;
+  }
+  if (e != cudaSuccess) return sfail(h, LBPF_ECUDA, "prediction capture: %s", cudaGetErrorString(e));
+  e = cudaGraphInstantiate(&net->pgraph[c], g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return sfail(h, LBPF_ECUDA, "prediction graph: %s", cudaGetErrorString(e));
+  net->pkey_pops[c] = h->pops[c];
+  net->pkey_stream[c] = h->stream;
+  net->pkey_cfg[c] = *cfg;
+  *out = net->pgraph[c];
+  return LBPF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
 int lbpf_surrogate_advance(lbpf_t* h, lbpf_unet_t* net, const lbpf_surrogate_cfg* cfg,
                            int blocks, lbpf_surrogate_report* rep) {
   if (!h || !net || check_cfg(cfg) || blocks < 0) return LBPF_EINVAL;
@@ -709,6 +805,7 @@ int lbpf_surrogate_advance(lbpf_t* h, lbpf_unet_t* net, const lbpf_surrogate_cfg
     chk(dalloc(net, &net->pF1, size_t(5 * n)));
     chk(dalloc(net, &net->psum, 4));
     chk(dalloc(net, &net->pcross, 8));
+    chk(cudaMallocHost(&net->hres, 16 * sizeof(double)));
     if (e != cudaSuccess)
       return sfail(h, LBPF_ENOMEM, "propagator scratch: %s", cudaGetErrorString(e));
   }
@@ -728,44 +825,30 @@ int lbpf_surrogate_advance(lbpf_t* h, lbpf_unet_t* net, const lbpf_surrogate_cfg
   SCK(h, cudaStreamSynchronize(s));
   const int nb = cfg->steps_per_block;
   const double tol = cfg->iface_tol;
-  // controller state.  An LB block's outcome (its interface displacement and,
+  // Controller state.  An LB block's outcome (its interface displacement and,
   // if it was judging, the error of the prediction made from the same start)
   // is read at the start of the next block, from that block's own read-out.
+  // acc: per ray, the signed sum over every committed block of the predicted
+  // displacement minus the displacement the LB showed in its last block: an
+  // estimate of how far the committed trajectory has drifted from the LB's
+  // (bounded by iface_budget when that is set).
   bool trusted = false, have_ref = false;
   bool lb_pending = false, judge_pending = false, pending_ok = false;
   double dref[4] = {0, 0, 0, 0}, lb_start[4] = {0, 0, 0, 0}, pred_pending[4] = {0, 0, 0, 0};
-  double acc = 0.0;  // interface error estimate accumulated since the last LB block
+  double acc[4] = {0, 0, 0, 0};
   int rc;
   for (int b = 0; b <= blocks; ++b) {
-    // read-out of the current state; its interface positions (pcross[4..7])
-    SCK(h, lbk::launch_surrogate_gather(h->m, h->pops[h->cur], vec4(cfg->shift), vec4(cfg->scale),
-                                        net->px, net->pF, s));
-    plane_crossing_kernel<<<1, 32, 0, s>>>(net->pF, h->m.nx, h->m.ny, h->m.bc[0], h->m.bc[1],
-                                           h->icx, h->icy, net->pcross + 4);
-    SCK(h, cudaGetLastError());
     const bool last = b == blocks;  // only resolves the outcome of the final block
-    if (!last) {
-      if ((rc = lbpf_unet_forward(net, net->px, net->py)))
-        return sfail(h, rc, "network: %s", net->msg);
-      apply_kernel<<<grid_of(n), 256, 0, s>>>(net->pF, net->py, vec4(cfg->res_scale), 1.0f / nb,
-                                              n, net->pF1);
-      SCK(h, cudaGetLastError());
-      if ((rc = lbpf_field_sums_noalloc(net->pF1, net->pF1 + 4 * n, net->pF1 + n, net->pF + 4 * n,
-                                        n, 0, net->psum, s)))
-        return sfail(h, rc, "solute sum of the prediction");
-      plane_crossing_kernel<<<1, 32, 0, s>>>(net->pF1, h->m.nx, h->m.ny, h->m.bc[0], h->m.bc[1],
-                                             h->icx, h->icy, net->pcross);
-      SCK(h, cudaGetLastError());
-    }
-    double sums[3] = {0, 0, 0}, cross[8];
-    unsigned nerr = 0;
-    SCK(h, cudaMemcpyAsync(sums, net->psum, sizeof(sums), cudaMemcpyDeviceToHost, s));
-    SCK(h, cudaMemcpyAsync(cross, net->pcross, sizeof(cross), cudaMemcpyDeviceToHost, s));
-    SCK(h, cudaMemcpyAsync(&nerr, net->d_err, sizeof(nerr), cudaMemcpyDeviceToHost, s));
+    cudaGraphExec_t g = nullptr;
+    if ((rc = prediction_graph(h, net, cfg, &g))) return rc;
+    SCK(h, cudaGraphLaunch(g, s));
     SCK(h, cudaStreamSynchronize(s));
+    const double* res = net->hres;
+    unsigned nerr = 0;
+    std::memcpy(&nerr, res + 11, sizeof(nerr));
     if (nerr) return sfail(h, LBPF_ETIMEDOUT, "a tensor-core convolution gave up waiting");
-    const double* posP = cross;
-    const double* pos0 = cross + 4;
+    const double* posP = res + 3;
+    const double* pos0 = res + 7;
     if (lb_pending) {
       for (int k = 0; k < 4; ++k)
         dref[k] = (pos0[k] >= 0 && lb_start[k] >= 0) ? pos0[k] - lb_start[k] : -1e300;
@@ -778,17 +861,22 @@ int lbpf_surrogate_advance(lbpf_t* h, lbpf_unet_t* net, const lbpf_surrogate_cfg
       lb_pending = false;
     }
     if (last) break;
-    const double drift = std::fabs(sums[0] - I0) / std::fmax(std::fabs(I0), 1e-300);
+    const double drift = std::fabs(res[0] - I0) / std::fmax(std::fabs(I0), 1e-300);
     r.max_drift = std::fmax(r.max_drift, std::isfinite(drift) ? drift : 1e300);
-    double est = -1.0;
+    double cand[4] = {acc[0], acc[1], acc[2], acc[3]};
+    double est = -1.0, est_acc = 0.0;
     if (have_ref)
       for (int k = 0; k < 4; ++k)
-        if (posP[k] >= 0 && pos0[k] >= 0 && dref[k] > -1e300)
-          est = std::fmax(est, std::fabs((posP[k] - pos0[k]) - dref[k]));
-    if (est >= 0.0) est += acc;
+        if (posP[k] >= 0 && pos0[k] >= 0 && dref[k] > -1e300) {
+          const double e = (posP[k] - pos0[k]) - dref[k];
+          est = std::fmax(est, std::fabs(e));
+          cand[k] = acc[k] + e;
+          est_acc = std::fmax(est_acc, std::fabs(cand[k]));
+        }
     const bool drift_ok = drift <= cfg->drift_tol;
     const bool judge = !trusted || !have_ref || (cfg->judge_every > 0 && b % cfg->judge_every == 0);
-    const bool fails = !drift_ok || !(est >= 0.0 && est <= tol);
+    const bool fails = !drift_ok || !(est >= 0.0 && est <= tol) ||
+                       (cfg->iface_budget > 0.0 && !(est_acc <= cfg->iface_budget));
     if (judge || fails) {
       if ((rc = lbpf_step(h, nb))) return rc;
       lb_pending = true;
@@ -798,7 +886,6 @@ int lbpf_surrogate_advance(lbpf_t* h, lbpf_unet_t* net, const lbpf_surrogate_cfg
         lb_start[k] = pos0[k];
         pred_pending[k] = posP[k];
       }
-      acc = 0.0;
       if (judge) {
         ++r.judged_blocks;
       } else {
@@ -809,15 +896,16 @@ int lbpf_surrogate_advance(lbpf_t* h, lbpf_unet_t* net, const lbpf_surrogate_cfg
       // conservative correction: the accepted prediction's solute deficit is
       // spread over the liquid in proportion to (1 - phi)/2, so that a
       // committed state keeps sum(U + phi(t-1)) as the LB does
-      const double liquid = double(n) - sums[2];
-      const float k = liquid > 0.5 ? float((I0 - sums[0]) / liquid) : 0.f;
+      const double liquid = double(n) - res[2];
+      const float k = liquid > 0.5 ? float((I0 - res[0]) / liquid) : 0.f;
       correct_kernel<<<grid_of(n), 256, 0, s>>>(net->pF1, n, k);
       SCK(h, cudaGetLastError());
       SCK(h, lbk::launch_surrogate_commit(h->m, net->pF1, net->pF + 4 * n, h->pops[h->cur],
                                           h->phi[h->cur], s));
       h->step += nb;
-      acc = est;
+      for (int k = 0; k < 4; ++k) acc[k] = cand[k];
       r.max_iface_est = std::fmax(r.max_iface_est, est);
+      r.iface_acc = est_acc;
       ++r.surrogate_blocks;
     }
     ++r.blocks;
@@ -832,6 +920,9 @@ const char* lbpf_unet_last_error(const lbpf_unet_t* n) { return n ? n->msg : "nu
 void lbpf_unet_destroy(lbpf_unet_t* n) {
   if (!n) return;
   cudaStreamSynchronize(n->stream);
+  for (auto& g : n->pgraph)
+    if (g) cudaGraphExecDestroy(g);
+  if (n->hres) cudaFreeHost(n->hres);
   for (void* p : n->allocs) cudaFree(p);
   delete n;
 }

@@ -25,8 +25,8 @@ import torch
 from . import (Sim, UNet, current_stream, lbpf_surrogate_advance, lbpf_surrogate_sample,
                lbpf_surrogate_target, surrogate_cfg)
 
-__all__ = ["channel_problem", "make_sim", "generate_pairs", "train", "inference_net",
-           "surrogate_cfg", "lbpf_surrogate_advance"]
+__all__ = ["channel_problem", "make_sim", "default_cfg", "generate_pairs", "train",
+           "inference_net", "prediction_error", "surrogate_cfg", "lbpf_surrogate_advance"]
 
 
 def channel_problem(rng: np.random.Generator, nx: int, ny: int, tau_f: float = 0.6,
@@ -59,29 +59,52 @@ def make_sim(params: dict, fields: dict, stream: int | None = None) -> Sim:
     return sim
 
 
+def default_cfg(steps_per_block: int = 50, **kw):
+    """Propagator settings for the channel problems: inputs (phi, U, ux, uy)
+    shifted and scaled to O(1), outputs scaled by about four standard
+    deviations of the change near the crystal over a 50-step block (measured
+    on the sampler's trajectories), growing with the square root of the block
+    length as diffusive changes do."""
+    g = math.sqrt(steps_per_block / 50.0)
+    kw.setdefault("res_scale", (0.02 * g, 0.012 * g, 0.0015 * g, 0.001 * g))
+    return surrogate_cfg(steps_per_block=steps_per_block, shift=(0.0, 0.3, 0.0, 0.0),
+                         scale=(1.0, 0.2, 0.01, 0.01), **kw)
+
+
 def generate_pairs(n_traj: int, t_end: int, every: int, nx: int, ny: int, cfg, seed: int,
-                   device="cuda"):
-    """Pairs (x(t), target) from n_traj sampled problems, at t = 0, every,
-    2 every, ... < t_end: x(t) the normalised fields, target the normalised
-    change over cfg.steps_per_block LB steps.  Returns device tensors
-    X, T of shape [N, ny, nx, 4]."""
+                   crop: int | None = None, t_start: int = 0, device="cuda"):
+    """Pairs (x(t), target) from n_traj sampled problems, at t = t_start,
+    t_start + every, ... < t_end: x(t) the normalised fields, target the
+    normalised change over cfg.steps_per_block LB steps.  crop: keep only a
+    band of `crop` rows centred on the seed, where the fields change, at full
+    width (the network's deepest level needs the width); a convolutional
+    network trained on bands applies to the whole domain.
+    Returns device tensors X, T of shape [N, h, nx, 4]."""
     nb = cfg.steps_per_block
-    assert every >= nb and t_end % every == 0
-    per = t_end // every
+    assert every >= nb and (t_end - t_start) % every == 0
+    per = (t_end - t_start) // every
     N = n_traj * per
-    X = torch.empty(N, ny, nx, 4, device=device)
+    h, w = (crop, nx) if crop else (ny, nx)
+    y0, x0 = (ny // 2 - h // 2, 0) if crop else (0, 0)
+    X = torch.empty(N, h, w, 4, device=device)
     T = torch.empty_like(X)
-    x1 = torch.empty(ny, nx, 4, device=device)
+    x0f = torch.empty(ny, nx, 4, device=device)
+    x1f = torch.empty_like(x0f)
+    tf = torch.empty_like(x0f)
     rng = np.random.default_rng(seed)
     k = 0
     for _ in range(n_traj):
         params, fields, _ = channel_problem(rng, nx, ny)
         sim = make_sim(params, fields)
+        if t_start:
+            sim.step(t_start)
         for _ in range(per):
-            lbpf_surrogate_sample(sim, cfg, X[k])
+            lbpf_surrogate_sample(sim, cfg, x0f)
             sim.step(nb)
-            lbpf_surrogate_sample(sim, cfg, x1)
-            lbpf_surrogate_target(cfg, X[k], x1, ny * nx, T[k], current_stream())
+            lbpf_surrogate_sample(sim, cfg, x1f)
+            lbpf_surrogate_target(cfg, x0f, x1f, ny * nx, tf, current_stream())
+            X[k].copy_(x0f[y0:y0 + h, x0:x0 + w])
+            T[k].copy_(tf[y0:y0 + h, x0:x0 + w])
             sim.step(every - nb)
             k += 1
         sim.close()
