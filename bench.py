@@ -8,7 +8,12 @@ step over the whole grid; the metric is MLUPS (million node updates per
 second) with the HBM roofline of the step kernel beside it.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload c2|c1|c3|c3_fp16|c3_bf16|c2_fp16]
+                  [--workload c2|c1|c3|c3_fp16|c3_bf16|c2_fp16|c4|c5]
+
+Workload c5 times the learned block propagator (a U-Net trained on the GPU
+on trajectories of this solver, judged by and falling back to the LB)
+against the plain LB on a held-out problem; --steps is then the number of
+LB-equivalent steps timed.
 
 Multi-GPU: the path does not shard in this build (one grid per GPU), so N
 GPUs run N independent replicas ("replicas only", weak scaling).
@@ -28,6 +33,13 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+# the files each timed kernel is compiled from (a committed profile's counters
+# stand only while their digest is unchanged)
+SRC_2D = ["step2d.cu", "step2d_tile.cuh", "step2d_core.cuh", "lbpf_device.cuh", "tma.cuh"]
+SRC_3D = ["step3d.cu", "step3d_core.cuh", "lbpf_device.cuh"]
+SRC_BATCH = ["batch2d.cu", "step2d_tile.cuh", "step2d_core.cuh", "lbpf_device.cuh", "tma.cuh"]
+SRC_CONV = ["conv_tc.cu", "tma.cuh"]
+
 # bytes each node moves through HBM per step (populations read + written,
 # phi(t-1) read, phi(t) written)
 WORKLOADS = {
@@ -35,20 +47,20 @@ WORKLOADS = {
                     "seed R=16 at x=300, U0=0.4, 5-fold eps 0.03",
                dim=2, nx=1024, ny=1024, nz=1, flow=1, fold=5, eps=0.03, bc=(1, 0, 0),
                u_in=0.01, U_in=0.4, seed=(300.0, 512.0, 0.0, 16.0, 0.4, 0.01, 1),
-               storage="fp32", kernel="step2d_tma_kernel", src="step2d.cu",
+               storage="fp32", kernel="step2d_tma_kernel", src=SRC_2D,
                sample=dict(nx=256, ny=256, seed=(75.0, 128.0, 0.0, 16.0, 0.4, 0.01, 1))),
     "c2_fp16": dict(base="c2", storage="fp16"),
     "c1": dict(desc="2D 128x128 periodic, no flow (phase field + solute D2Q9), U0=0.3, R=8, "
                     "4-fold eps 0.05",
                dim=2, nx=128, ny=128, nz=1, flow=0, fold=4, eps=0.05, bc=(0, 0, 0), u_in=0.0,
                U_in=0.0, seed=(64.0, 64.0, 0.0, 8.0, 0.3, 0.01, 1), storage="fp32",
-               kernel="step2d_tma_kernel", src="step2d.cu",
+               kernel="step2d_tma_kernel", src=SRC_2D,
                sample=dict(nx=128, ny=128, seed=(64.0, 64.0, 0.0, 8.0, 0.3, 0.01, 1))),
     "c3": dict(desc="3D 256^3 coupled LB (D3Q19 flow, D3Q7 solute and phase field), cubic eps "
                     "0.04, sphere R=12, U0=0.3, inflow 0.005",
                dim=3, nx=256, ny=256, nz=256, flow=1, fold=0, eps=0.04, bc=(1, 0, 0),
                u_in=0.005, U_in=0.3, seed=(128.0, 128.0, 128.0, 12.0, 0.3, 0.01, 1),
-               storage="fp32", kernel="step3d_kernel", src="step3d.cu",
+               storage="fp32", kernel="step3d_kernel", src=SRC_3D,
                sample=dict(nx=48, ny=48, nz=48, seed=(24.0, 24.0, 24.0, 12.0, 0.3, 0.01, 1))),
     "c3_fp16": dict(base="c3", storage="fp16"),
     "c3_bf16": dict(base="c3", storage="bf16"),
@@ -56,9 +68,27 @@ WORKLOADS = {
                     "(sides U{256..768}, U0~U[0.1,0.6], R~U[4,24], u_in~U[0,0.02], fold 4 or 5, "
                     "eps~U[0.02,0.06]; seed 4), FP16 shifted storage",
                dim=2, nx=512, ny=512, nz=1, flow=1, fold=5, eps=0.04, bc=(1, 0, 0), u_in=0.01,
-               U_in=0.35, storage="fp16", kernel="step2d_batch_kernel", src="batch2d.cu",
+               U_in=0.35, storage="fp16", kernel="step2d_batch_kernel", src=SRC_BATCH,
                batch=64, sweep_seed=4,
                sample=dict(nx=256, ny=256, seed=(77.0, 128.0, 0.0, 12.0, 0.35, 0.01, 1))),
+    "c5": dict(desc="learned block propagator on 2D 512x512 closed channels (periodic x, walls y, "
+                    "body-force Poiseuille flow u_max~U[0,0.01], U0~U[0.25,0.45], R~U[6,16], "
+                    "fold 4 or 5, eps~U[0.02,0.05]): BF16 U-Net 32/64/128/256 channels trained "
+                    "on the GPU on 2000 LB pairs from 50 sampled problems, 200-step blocks, LB "
+                    "judge every 8th block, fallback at drift > 1e-3 or interface error > 1 lu; "
+                    "held-out problem; FP32 LB",
+               dim=2, nx=512, ny=512, nz=1, flow=1, fold=5, eps=0.03, bc=(0, 2, 0), u_in=0.0,
+               U_in=0.0, storage="fp32", kernel="conv3x3_tc_kernel", src=SRC_CONV,
+               surrogate=dict(block=200, judge_every=8, traj=50, t_end=20000, every=500,
+                              crop=256, train_steps=2000, batch=8, lr=1e-3, start=1000),
+               sample=dict(nx=256, ny=256, channel=True)),
+    "c5net": dict(desc="the c5 network alone: BF16 U-Net 32/64/128/256 channels on a 512x512 "
+                       "sample (4 -> 4 channels, random weights): forward passes, then "
+                       "training steps (forward, backward, Adam)",
+                  dim=2, nx=512, ny=512, nz=1, flow=1, fold=5, eps=0.03, bc=(0, 2, 0),
+                  u_in=0.0, U_in=0.0, storage="fp32", kernel="conv3x3_tc_kernel",
+                  src=SRC_CONV, network=dict(batch=1),
+                  sample=dict(nx=256, ny=256, channel=True)),
 }
 
 
@@ -129,11 +159,18 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
+def source_digest(files):
+    """sha256 over the concatenated sources a kernel is compiled from."""
+    h = hashlib.sha256()
+    for f in files:
+        h.update(open(os.path.join(ROOT, "paper_2206_02145_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()
+
+
 def profiled_traffic(w):
     """Per-launch DRAM bytes from the committed ncu summary of this kernel, or
-    None when the kernel source changed since the counters were taken."""
+    None when the kernel's sources changed since the counters were taken."""
     prof = os.path.join(ROOT, "profiles", f"{w['kernel']}_{w['nx']}_{w['storage']}.md")
-    src = os.path.join(ROOT, "paper_2206_02145_gb300", "csrc", w["src"])
     if not os.path.exists(prof):
         return None
     text = open(prof).read()
@@ -141,7 +178,7 @@ def profiled_traffic(w):
     mt = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", text)
     if not (mh and mt):
         return None
-    if hashlib.sha256(open(src, "rb").read()).hexdigest() != mh.group(1):
+    if source_digest(w["src"]) != mh.group(1):
         return None
     return float(mt.group(1))
 
@@ -196,15 +233,39 @@ class ClockSampler:
                 "samples": len(self.rows)}
 
 
-def oracle_sample(w, seconds: float, threads: int):
-    """The FP64 CPU oracle, as it stands, on a bounded sample of the workload."""
+def channel_sample(nx, ny, tau_f=0.6, w0=2.0, u0=0.35, radius=11.0, umax=0.005):
+    """Inputs of one closed-channel problem (the centre of the c5 sweep):
+    tanh seed at the centre, uniform U0, Poiseuille profile of a body force."""
+    import numpy as np
+    nu = (tau_f - 0.5) / 3.0
+    g = 8.0 * nu * umax / (ny * ny)
+    y, x = np.mgrid[0:ny, 0:nx].astype(np.float64)
+    phi = np.tanh((radius - np.hypot(x - nx // 2, y - ny // 2)) / (np.sqrt(2.0) * w0))
+    ux = g / (2.0 * nu) * (y + 0.5) * (ny - 0.5 - y)
+    return g, dict(phi=phi, U=np.full_like(phi, u0), ux=ux, uy=np.zeros_like(phi))
+
+
+def oracle_problem(w):
     import oracle
     s = w["sample"]
+    body = (0.0, 0.0, 0.0)
+    if s.get("channel"):
+        g, f = channel_sample(s["nx"], s["ny"])
+        body = (g, 0.0, 0.0)
     p = oracle.Params(dim=w["dim"], nx=s["nx"], ny=s["ny"], nz=s.get("nz", 1), bc=w["bc"],
                       flow=w["flow"], fold=w["fold"], eps=w["eps"], u_inlet=w["u_in"],
-                      u0_inlet=w["U_in"])
+                      u0_inlet=w["U_in"], body=body)
     o = oracle.Oracle(p)
-    o.init_seed(*s["seed"])
+    if s.get("channel"):
+        o.init_fields(f["phi"], f["U"], None, f["ux"], f["uy"])
+    else:
+        o.init_seed(*s["seed"])
+    return p, o
+
+
+def oracle_sample(w, seconds: float, threads: int):
+    """The FP64 CPU oracle, as it stands, on a bounded sample of the workload."""
+    p, o = oracle_problem(w)
     o.step(1, threads)
     steps, t0 = 0, time.perf_counter()
     while time.perf_counter() - t0 < seconds:
@@ -219,14 +280,11 @@ def run_reference(args, w):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    import oracle
     threads = os.cpu_count() or 1
     s = w["sample"]
-    p = oracle.Params(dim=w["dim"], nx=s["nx"], ny=s["ny"], nz=s.get("nz", 1), bc=w["bc"],
-                      flow=w["flow"], fold=w["fold"], eps=w["eps"], u_inlet=w["u_in"],
-                      u0_inlet=w["U_in"])
-    o = oracle.Oracle(p)
-    o.init_seed(*s["seed"])
+    p, o = oracle_problem(w)
+    if w.get("surrogate"):  # LB-equivalent steps: the oracle runs the LB
+        args.steps = min(args.steps, 200)
     for _ in range(args.warmup):
         o.step(1, threads)
     t0 = time.perf_counter()
@@ -236,8 +294,10 @@ def run_reference(args, w):
     v = p.nodes * args.steps / dt / 1e6
     sample = (f"{s['nx']}x{s['ny']}" + (f"x{s['nz']}" if w['dim'] == 3 else "") +
               " nodes of the same workload per step (FP64 oracle, OpenMP)")
+    metric = ("LB-equivalent MLUPS (learned block propagator)" if w.get("surrogate")
+              else "coupled-LB MLUPS")
     print(json.dumps({
-        "impl": "reference", "metric": "coupled-LB MLUPS", "value": v, "unit": "MLUPS",
+        "impl": "reference", "metric": metric, "value": v, "unit": "MLUPS",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -263,6 +323,10 @@ def main():
     w = workload(args.workload)
     if args.impl == "reference":
         return run_reference(args, w)
+    if w.get("surrogate"):
+        return run_surrogate(args, w)
+    if w.get("network"):
+        return run_network(args, w)
 
     import numpy as np
     import torch
@@ -413,6 +477,255 @@ def main():
         print(json.dumps(out), flush=True)
     del sims
     stepper.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def unet_forward_flops(nx, ny, batch=1):
+    """Algorithmic FLOPs of one forward pass of the 4-level 32/64/128/256 U-Net
+    (3x3 convolutions only; 2 flops per multiply-add)."""
+    Cs = [32, 64, 128, 256]
+    flop = 0
+    for lev in range(4):
+        px = batch * (ny >> lev) * (nx >> lev)
+        flop += 2 * 9 * px * ((16 if lev == 0 else Cs[lev - 1]) * Cs[lev] + Cs[lev] * Cs[lev])
+        if lev < 3:
+            flop += 2 * 9 * px * (Cs[lev + 1] * Cs[lev] + 3 * Cs[lev] * Cs[lev])
+    return flop
+
+
+def run_network(args, w):
+    """c5net: the network's kernels alone, K forward passes then K training steps."""
+    import torch
+    import paper_2206_02145_gb300 as L
+    B = w["network"]["batch"]
+    nx, ny = w["nx"], w["ny"]
+    stream = torch.cuda.current_stream()
+    net = L.UNet(in_ch=4, out_ch=4, levels=4, batch=B, height=ny, width=nx, seed=1,
+                 stream=stream.cuda_stream)
+    g = torch.Generator(device="cpu").manual_seed(0)
+    x = torch.randn(B, ny, nx, 4, generator=g).cuda()
+    t = torch.randn(B, ny, nx, 4, generator=g).cuda()
+    y = torch.empty_like(x)
+    for _ in range(args.warmup):
+        net.forward(x, y)
+        net.train_step(x, t, 1e-5)
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    with ClockSampler(int(os.environ.get("LOCAL_RANK", "0"))) as clk:
+        ev[0].record(stream)
+        for _ in range(args.steps):
+            net.forward(x, y)
+        ev[1].record(stream)
+        for _ in range(args.steps):
+            net.train_step(x, t, 1e-5)
+        ev[2].record(stream)
+        torch.cuda.synchronize()
+    net.status()
+    fwd = ev[0].elapsed_time(ev[1]) / args.steps
+    trn = ev[1].elapsed_time(ev[2]) / args.steps
+    flop = unet_forward_flops(nx, ny, B)
+    tf = flop / (fwd * 1e-3) / 1e12
+    print(json.dumps({
+        "metric": "U-Net forward TFLOP/s", "value": tf, "unit": "TFLOP/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": fwd,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
+        "data": "synthetic (random weights and inputs)",
+        "config": {"workload": w["desc"], "batch": B, "params": net.param_count},
+        "train_step_ms": trn, "train_tflops": 3 * flop / (trn * 1e-3) / 1e12,
+        "roofline": {"bound": "tensor", "achieved": tf, "peak": 1900.0, "unit": "TFLOP/s",
+                     "frac": tf / 1900.0, "peak_source": "fallback", "traffic": None},
+        "clocks": clk.summary()}), flush=True)
+    net.close()
+
+
+def run_surrogate(args, w):
+    """c5: train the U-Net on LB trajectories, then time the block propagator
+    against the plain LB on a held-out problem (one GPU; replicas beyond)."""
+    import numpy as np
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import paper_2206_02145_gb300 as L
+    from paper_2206_02145_gb300 import surrogate as S
+    c = w["surrogate"]
+    nx, ny, nb = w["nx"], w["ny"], c["block"]
+    stream = torch.cuda.current_stream()
+    cfg = S.default_cfg(nb)
+
+    # --- setup (untimed): training pairs from the LB, training on the GPU -------
+    t0 = time.perf_counter()
+    X, T = S.generate_pairs(c["traj"], c["t_end"], c["every"], nx, ny, cfg, seed=100,
+                            crop=c["crop"])
+    t_data = time.perf_counter() - t0
+    tr = L.UNet(in_ch=4, out_ch=4, levels=4, batch=c["batch"], height=c["crop"], width=nx,
+                seed=1, stream=stream.cuda_stream)
+    t0 = time.perf_counter()
+    hist = S.train(tr, X, T, c["train_steps"], lr=c["lr"], log_every=500)
+    tr.status()
+    t_train = time.perf_counter() - t0
+    npairs = int(X.shape[0])
+    del X, T
+    net = S.inference_net(tr, nx, ny, stream.cuda_stream)
+    tr.close()
+
+    # held-out problem: propagator (a) and plain LB (b) from the same state
+    rng = np.random.default_rng(4242 + rank)
+    params, fields, info = S.channel_problem(rng, nx, ny)
+    a = S.make_sim(params, fields, stream.cuda_stream)
+    b = S.make_sim(params, fields, stream.cuda_stream)
+    a.step(c["start"])
+    b.step(c["start"])
+    pcfg = S.default_cfg(nb, judge_every=c["judge_every"], drift_tol=1e-3, iface_tol=1.0)
+    L.lbpf_surrogate_advance(a, net, pcfg, 1)  # warm-up: captures the prediction graph
+    b.step(nb)
+    torch.cuda.synchronize()
+    d0 = b.diagnostics()
+    K = max(1, args.steps // nb)
+    steps = K * nb
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        rep = L.lbpf_surrogate_advance(a, net, pcfg, K)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        ms_s = ev0.elapsed_time(ev1)
+        ev0.record(stream)
+        b.step(steps)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        ms_lb = ev0.elapsed_time(ev1)
+    t = torch.tensor([ms_s, ms_lb], device="cuda")
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_s, ms_lb = float(t[0]), float(t[1])
+    da, db = a.diagnostics(), b.diagnostics()
+    grow_lb = db["iface_pos"][:4] - d0["iface_pos"][:4]
+    grow_s = da["iface_pos"][:4] - d0["iface_pos"][:4]
+    nodes = nx * ny
+    value = nodes * world * steps / (ms_s * 1e-3) / 1e6
+    lb_value = nodes * world * steps / (ms_lb * 1e-3) / 1e6
+
+    # the same held-out run with the accumulated interface estimate bounded at
+    # 1 lattice unit (the controller then hands the rest of the run to the LB)
+    cb = S.make_sim(params, fields, stream.cuda_stream)
+    cb.step(c["start"] + nb)
+    bcfg = S.default_cfg(nb, judge_every=c["judge_every"], drift_tol=1e-3, iface_tol=1.0,
+                         iface_budget=1.0)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    rep_b = L.lbpf_surrogate_advance(cb, net, bcfg, K)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms_b = ev0.elapsed_time(ev1)
+    dcb = cb.diagnostics()
+    grow_b = dcb["iface_pos"][:4] - d0["iface_pos"][:4]
+    budgeted = {"iface_budget_lu": 1.0, "speedup_vs_plain_lb": ms_lb / ms_b, "report": rep_b,
+                "growth_lu": grow_b.tolist(),
+                "iface_pos_error_lu": float(np.max(np.abs(dcb["iface_pos"][:4] -
+                                                          db["iface_pos"][:4])))}
+    cb.close()
+
+    # the network forward alone: the tensor-core part of the path
+    xs = torch.zeros(ny, nx, 4, device="cuda")
+    ys = torch.empty_like(xs)
+    for _ in range(3):
+        net.forward(xs, ys)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for _ in range(20):
+        net.forward(xs, ys)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    fwd_ms = ev0.elapsed_time(ev1) / 20
+    flop = unet_forward_flops(nx, ny)
+    tflops = flop / (fwd_ms * 1e-3) / 1e12
+    peak_tf, peak_kind = 1900.0, "fallback"
+    try:
+        d = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        for k, v in d.items():
+            if "bf16" in k and "sustained" not in k and isinstance(v, (int, float)):
+                peak_tf, peak_kind = float(v), "measured"
+    except Exception:
+        pass
+
+    # --- end to end through the C ABI with host buffers ---------------------------
+    # per call: the state from pinned host memory (lbpf_write_state), Ke blocks
+    # of the propagator, phi and U back to pinned host memory
+    hs = torch.from_numpy(a.state()).pin_memory()
+    ho = torch.empty(2 * nodes, dtype=torch.float32).pin_memory()
+    Ke = min(K, 10)
+    L.lbpf_write_state(a.h, hs.data_ptr(), hs.numel())
+    L.lbpf_surrogate_advance(a, net, pcfg, 1)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    L.lbpf_write_state(a.h, hs.data_ptr(), hs.numel())
+    L.lbpf_surrogate_advance(a, net, pcfg, Ke)
+    L.lbpf_read_fields(a.h, L.FIELD_PHI | L.FIELD_U, ho.data_ptr(), ho.numel() * 4, 0)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    e2e_value = nodes * world * Ke * nb / e2e_s / 1e6
+
+    if rank == 0:
+        cpu = None
+        if not args.no_cpu_baseline:
+            threads = os.cpu_count() or 1
+            v, osteps, n, dt = oracle_sample(w, args.cpu_seconds, threads)
+            cpu = {"value": v, "unit": "MLUPS", "cores": threads, "kind": "oracle",
+                   "sample": f"{osteps} LB steps of a 256x256 closed channel of the same family "
+                             f"({n} nodes), {dt:.1f} s, FP64"}
+        launches = (K + 1) * 31 + rep["surrogate_blocks"] * 2 + (
+            rep["judged_blocks"] + rep["fallback_blocks"]) * nb
+        rel = (grow_s - grow_lb) / np.where(np.abs(grow_lb) > 1e-9, np.abs(grow_lb), np.nan)
+        out = {
+            "metric": "LB-equivalent MLUPS (learned block propagator)", "value": value,
+            "unit": "MLUPS", "n_gpus": world, "steps": steps, "warmup": nb,
+            "ms_per_step": ms_s / steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "bf16 network, f32 LB", "data": "synthetic "
+            "(seeded channel problems; the network's training pairs come from this LB)",
+            "config": {"workload": w["desc"], "grid": [nx, ny, 1], "block_steps": nb,
+                       "judge_every": c["judge_every"], "pairs": npairs,
+                       "training": {"steps": c["train_steps"], "batch": c["batch"],
+                                    "band_rows": c["crop"], "data_s": round(t_data, 1),
+                                    "train_s": round(t_train, 1),
+                                    "loss": [round(x[1], 5) for x in hist]},
+                       "held_out_problem": info,
+                       "l2": "network activations of a 512x512 sample exceed L2 at level 0 "
+                             "only partly; the LB state (59 MB) fits in L2: both arms time the "
+                             "same K blocks back to back",
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "plain_lb": {"value": lb_value, "unit": "MLUPS", "ms": ms_lb},
+            "speedup_vs_plain_lb": ms_lb / ms_s,
+            "report": rep,
+            "growth_lu": {"plain_lb": grow_lb.tolist(), "propagator": grow_s.tolist(),
+                          "rel_error": [None if not np.isfinite(x) else float(x) for x in rel]},
+            "iface_pos_error_lu": float(np.max(np.abs(da["iface_pos"][:4] -
+                                                      db["iface_pos"][:4]))),
+            "solute_drift_rel": da["solute_drift_rel"],
+            "with_accumulated_bound": budgeted,
+            "roofline": {"bound": "tensor", "achieved": tflops, "peak": peak_tf,
+                         "unit": "TFLOP/s", "frac": tflops / peak_tf, "peak_source": peak_kind,
+                         "traffic": None, "kernel": "network forward (17 conv3x3_tc + 8 "
+                         "element-wise launches), 512x512, batch 1",
+                         "algorithmic_flops_per_forward": flop, "forward_ms": fwd_ms},
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": "MLUPS",
+                    "h2d_bytes_per_step": int(hs.numel()) / (Ke * nb),
+                    "d2h_bytes_per_step": int(ho.numel()) * 4 / (Ke * nb)},
+            "gpu_launches": launches,
+            "clocks": clk.summary(),
+        }
+        print(json.dumps(out), flush=True)
+    for x in (a, b, net):
+        x.close()
     if dist is not None:
         dist.destroy_process_group()
 
