@@ -174,7 +174,7 @@ def profiled_traffic(w):
     if not os.path.exists(prof):
         return None
     text = open(prof).read()
-    mh = re.search(r"source_sha256:\s*([0-9a-f]+)", text)
+    mh = re.search(r"source_sha256[^:\n]*:\s*([0-9a-f]+)", text)
     mt = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", text)
     if not (mh and mt):
         return None
