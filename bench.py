@@ -60,9 +60,13 @@ WORKLOADS = {
                     "0.04, sphere R=12, U0=0.3, inflow 0.005",
                dim=3, nx=256, ny=256, nz=256, flow=1, fold=0, eps=0.04, bc=(1, 0, 0),
                u_in=0.005, U_in=0.3, seed=(128.0, 128.0, 128.0, 12.0, 0.3, 0.01, 1),
-               storage="fp32", kernel="step3d_kernel", src=SRC_3D,
+               storage="fp32", kernel="step3d_march_kernel", src=SRC_3D,
                sample=dict(nx=48, ny=48, nz=48, seed=(24.0, 24.0, 24.0, 12.0, 0.3, 0.01, 1))),
     "c3_fp16": dict(base="c3", storage="fp16"),
+    "c3s": dict(base="c3", nx=128, ny=128, nz=128, seed=(64.0, 64.0, 64.0, 12.0, 0.3, 0.01, 1),
+                desc="3D 128^3 case of c3 for profiler captures (D3Q19 flow, D3Q7 solute and "
+                     "phase field), cubic eps 0.04, sphere R=12, U0=0.3, inflow 0.005",
+                desc_note="FP32"),
     "c3_bf16": dict(base="c3", storage="bf16"),
     "c4": dict(desc="batched sweep: 64 2D coupled instances in one persistent launch per step "
                     "(sides U{256..768}, U0~U[0.1,0.6], R~U[4,24], u_in~U[0,0.02], fold 4 or 5, "
@@ -116,8 +120,10 @@ def workload(name):
     w = dict(WORKLOADS[name])
     if "base" in w:
         b = dict(WORKLOADS[w.pop("base")])
+        note = w.pop("desc_note", None)
         b.update(w)
-        b["desc"] = b["desc"] + f", {b['storage'].upper()} shifted storage"
+        if not note:
+            b["desc"] = b["desc"] + f", {b['storage'].upper()} shifted storage"
         w = b
     q = (9 if w["dim"] == 2 else 19) * w["flow"] + 2 * (9 if w["dim"] == 2 else 7)
     ring = 8 if w["storage"] == "fp64" else 4

@@ -7,9 +7,11 @@
 // halo in shared memory.  Populations are deviations d_a = p_a - w_a M_ref
 // as in 2D; the ring holds phi + 1.
 //
-// step3d_kernel: one thread per node, one 32 x 4 x 2 tile per CTA (16 x 4 x 2
-// in FP64); the tile's own populations and the halo's h are loaded by the CTA,
-// then every node collides and pushes (step3d_core.cuh).  A TMA-fed
+// step3d_march_kernel (FP32 arithmetic: FP32, FP16 and BF16 storage): a CTA
+// walks a column of nodes along z with a ring of h / phi planes in shared
+// memory (below).  step3d_kernel (FP64): one thread per node, one 16 x 4 x 2
+// tile per CTA; the tile's own populations and the halo's h are loaded by the
+// CTA, then every node collides and pushes (step3d_core.cuh).  A TMA-fed
 // persistent variant of the 2D design measured slower in 3D (8.2 vs 13.4
 // GLUPS at 256^3): its halo box carries 3.75x the tile's h data, a quarter of
 // the tiles touch an x face, and the stage size allows 2 CTAs per SM only.
@@ -81,17 +83,130 @@ __global__ void __launch_bounds__(TX* TY* TZ)
   }
   __syncthreads();
   if (!active) return;
-  TileView3<R, R, SX, SX * SY, SX * SY * SZ, 0> hs{&sh_h[0][0][0][0]};
+  HSlab3<R, SX, SX * SY, SX * SY * SZ> hs{&sh_h[0][tz + 1][0][0]};
+  PhiSlab3<R, SX, SX * SY> pv{&sh_phi[tz + 1][0][0]};
   const bool interior = x0 >= 1 && x0 + TX <= nx - 1 && y0 >= 1 && y0 + TY <= ny - 1 &&
                         z0 >= 1 && z0 + TZ <= nz - 1;
   if (interior)
-    collide_push_3d<T, R, FLOW, true, SX, SX * SY>(m, x, y, z, tx + 1, ty + 1, tz + 1, f, g, h,
-                                                   sh_phi[tz + 1][ty + 1][tx + 1], dphi_prev,
-                                                   &sh_phi[0][0][0], hs, dst, ring_cur, err);
+    collide_push_3d<T, R, FLOW, true>(m, x, y, z, tx + 1, ty + 1, f, g, h,
+                                      sh_phi[tz + 1][ty + 1][tx + 1], dphi_prev, pv, hs, dst,
+                                      ring_cur, err);
   else
-    collide_push_3d<T, R, FLOW, false, SX, SX * SY>(m, x, y, z, tx + 1, ty + 1, tz + 1, f, g, h,
-                                                    sh_phi[tz + 1][ty + 1][tx + 1], dphi_prev,
-                                                    &sh_phi[0][0][0], hs, dst, ring_cur, err);
+    collide_push_3d<T, R, FLOW, false>(m, x, y, z, tx + 1, ty + 1, f, g, h,
+                                       sh_phi[tz + 1][ty + 1][tx + 1], dphi_prev, pv, hs, dst,
+                                       ring_cur, err);
+}
+
+// ---- the z-marching kernel (FP32 arithmetic) --------------------------------------
+// One CTA per column of TX x TY nodes and chunk of zc planes.  The CTA walks
+// its column along z; a ring of four halo-extended planes of h and phi + 1
+// lives in shared memory, so every h plane of the column is read once (the
+// x/y halo is (TX + 2)(TY + 2) / (TX TY) of the plane) instead of the
+// three-plane-deep halo box of the tile kernel.  Each iteration first issues
+// the loads of the node's own f, g and phi(t-1), then loads plane z + 1 into
+// the ring, synchronises once and collides / pushes plane z.  With four
+// slots, the slot filled at z + 1 is never one another thread may still read.
+template <typename T, bool FLOW, int TX, int TY, int MINB>
+__global__ void __launch_bounds__(TX* TY, MINB)
+    step3d_march_kernel(const Model m, const T* __restrict__ src, T* __restrict__ dst,
+                        const float* __restrict__ ring_prev, float* __restrict__ ring_cur,
+                        unsigned* __restrict__ err, int zc) {
+  using R = float;
+  constexpr int SX = TX + 2, SY = TY + 2, PL = SX * SY;
+  constexpr int QF = FLOW ? 19 : 0;
+  constexpr int NT = TX * TY;
+  __shared__ R sh_phi[4][PL];
+  __shared__ R sh_h[4][7 * PL];
+  const int tid = threadIdx.x;
+  const int tx = tid % TX, ty = tid / TX;
+  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+  const int nx = m.nx, ny = m.ny, nz = m.nz, px = m.px;
+  const int P = int(m.plane);
+  const int slab = ny * px;
+  const int zs = blockIdx.z * zc;
+  const int ze = zs + zc < nz ? zs + zc : nz;
+  const int x = x0 + tx, y = y0 + ty;
+  const bool active = x < nx && y < ny;
+  const bool xy_inner = x0 >= 1 && x0 + TX <= nx - 1 && y0 >= 1 && y0 + TY <= ny - 1;
+
+  // h and phi + 1 of plane zz (ghost planes by the gradient rule) into slot
+  auto load_plane = [&](int zz, int slot) {
+    const int gz = grad_coord(zz, nz, m.bc[2]);
+    for (int i = tid; i < PL; i += NT) {
+      const int lx = i % SX, ly = i / SX;
+      const int gx = grad_coord(x0 + lx - 1, nx, m.bc[0]);
+      const int gy = grad_coord(y0 + ly - 1, ny, m.bc[1]);
+      const int j = gz * slab + gy * px + gx;
+      R s = R(0);
+#pragma unroll
+      for (int a = 0; a < 7; ++a) {
+        const R v = Pop<T>::template ld<R>(src + ((QF + 7 + a) * P + j));
+        sh_h[slot][a * PL + i] = v;
+        s += v;
+      }
+      sh_phi[slot][i] = s;
+    }
+  };
+
+  load_plane(zs - 1, 0);
+  load_plane(zs, 1);
+  for (int z = zs; z < ze; ++z) {
+    const int k = z - zs;
+    const int sm = k & 3, s0 = (k + 1) & 3, sp = (k + 2) & 3;  // planes z - 1, z, z + 1
+    const int idx = z * slab + y * px + x;
+    R f[19], g[7], h[7];
+    R dphi_prev = R(0);
+    if (active) {
+#pragma unroll
+      for (int a = 0; a < 19; ++a)
+        if (FLOW) f[a] = Pop<T>::template ld<R>(src + (a * P + idx));
+#pragma unroll
+      for (int a = 0; a < 7; ++a) g[a] = Pop<T>::template ld<R>(src + ((QF + a) * P + idx));
+      dphi_prev = ring_prev[idx];
+    }
+    load_plane(z + 1, sp);
+    __syncthreads();
+    if (active) {
+      const int o = (ty + 1) * SX + tx + 1;
+#pragma unroll
+      for (int a = 0; a < 7; ++a) h[a] = sh_h[s0][a * PL + o];
+      PhiRing3<R, SX> pv{{sh_phi[sm], sh_phi[s0], sh_phi[sp]}};
+      HRing3<R, SX, PL> hv{{sh_h[sm], sh_h[s0], sh_h[sp]}};
+      if (xy_inner && z >= 1 && z <= nz - 2)
+        collide_push_3d<T, R, FLOW, true>(m, x, y, z, tx + 1, ty + 1, f, g, h, sh_phi[s0][o],
+                                          dphi_prev, pv, hv, dst, ring_cur, err);
+      else
+        collide_push_3d<T, R, FLOW, false>(m, x, y, z, tx + 1, ty + 1, f, g, h, sh_phi[s0][o],
+                                           dphi_prev, pv, hv, dst, ring_cur, err);
+    }
+  }
+}
+
+// Column 32 x 4, chunks of 8 planes, 4 CTAs per SM: measured at 256^3 FP32
+// against 32 x 8 / 32 x 2 columns, chunks of 4 to 64 planes and 1 to 8 CTAs
+// per SM (16.7 GLUPS here; 32-plane chunks of 32 x 8 columns 14.6, the tile
+// kernel 13.3): short chunks keep enough CTAs in flight, the two extra planes
+// per chunk cost less than that gains.
+#ifndef LBPF_3D_TY
+#define LBPF_3D_TY 4
+#endif
+#ifndef LBPF_3D_ZC
+#define LBPF_3D_ZC 8
+#endif
+#ifndef LBPF_3D_MINB
+#define LBPF_3D_MINB 4
+#endif
+
+template <typename T, bool FLOW>
+cudaError_t launch3_march_t(const Model& m, const void* src, void* dst, const void* ring_prev,
+                            void* ring_cur, unsigned* err, cudaStream_t s) {
+  constexpr int TX = 32, TY = LBPF_3D_TY;
+  const int zc = LBPF_3D_ZC;
+  dim3 grid((m.nx + TX - 1) / TX, (m.ny + TY - 1) / TY, (m.nz + zc - 1) / zc);
+  step3d_march_kernel<T, FLOW, TX, TY, LBPF_3D_MINB><<<grid, TX * TY, 0, s>>>(
+      m, static_cast<const T*>(src), static_cast<T*>(dst), static_cast<const float*>(ring_prev),
+      static_cast<float*>(ring_cur), err, zc);
+  return cudaGetLastError();
 }
 
 // ---- host side -------------------------------------------------------------------
@@ -121,15 +236,14 @@ cudaError_t launch_step3d(const Model& m, const StepMaps&, int, const void* src,
       return m.flow ? launch3_plain_t<double, double, true>(m, src, dst, ring_prev, ring_cur, err, s)
                     : launch3_plain_t<double, double, false>(m, src, dst, ring_prev, ring_cur, err, s);
     case ST_FP16:
-      return m.flow ? launch3_plain_t<__half, float, true>(m, src, dst, ring_prev, ring_cur, err, s)
-                    : launch3_plain_t<__half, float, false>(m, src, dst, ring_prev, ring_cur, err, s);
+      return m.flow ? launch3_march_t<__half, true>(m, src, dst, ring_prev, ring_cur, err, s)
+                    : launch3_march_t<__half, false>(m, src, dst, ring_prev, ring_cur, err, s);
     case ST_BF16:
-      return m.flow
-                 ? launch3_plain_t<__nv_bfloat16, float, true>(m, src, dst, ring_prev, ring_cur, err, s)
-                 : launch3_plain_t<__nv_bfloat16, float, false>(m, src, dst, ring_prev, ring_cur, err, s);
+      return m.flow ? launch3_march_t<__nv_bfloat16, true>(m, src, dst, ring_prev, ring_cur, err, s)
+                    : launch3_march_t<__nv_bfloat16, false>(m, src, dst, ring_prev, ring_cur, err, s);
     default:
-      return m.flow ? launch3_plain_t<float, float, true>(m, src, dst, ring_prev, ring_cur, err, s)
-                    : launch3_plain_t<float, float, false>(m, src, dst, ring_prev, ring_cur, err, s);
+      return m.flow ? launch3_march_t<float, true>(m, src, dst, ring_prev, ring_cur, err, s)
+                    : launch3_march_t<float, false>(m, src, dst, ring_prev, ring_cur, err, s);
   }
 }
 

@@ -1,31 +1,53 @@
 // Per-node part of the 3D coupled step, shared by the 3D step kernels:
 // D3Q19 flow f (Eqs. 4-12), D3Q7 solute g (Eqs. 13-18) and D3Q7 phase field
 // h (Eqs. 19-23, cubic anisotropy of Eq. 3), push streaming.  The caller has
-// the node's own population deviations in registers and the tile's phi + 1
-// and h deviations (with a one-node halo in x, y and z) in shared memory.
+// the node's own population deviations in registers and phi + 1 and the h
+// deviations around the node (one node in x, y and z) in shared memory.
 #pragma once
 
 #include "lbpf_device.cuh"
 
 namespace lbk {
 
-// Shared-memory view of a halo-extended 3D tile with compile-time shape.
-template <typename T, typename R, int ROW, int SLAB, int PLANE, int XOFF>
-struct TileView3 {
-  const T* base;
-  __device__ __forceinline__ R at(int a, int lz, int ly, int lx) const {
-    return Pop<T>::template ld<R>(base + a * PLANE + lz * SLAB + ly * ROW + lx + XOFF);
+// Shared-memory views of the node's neighbourhood, indexed by the plane
+// offset dz in {-1, 0, 1} from the node's plane and the local (ly, lx) of a
+// halo-extended tile.  PhiSlab3 / HSlab3: a contiguous [z][y][x] tile (plane
+// of the node at lz); PhiRing3 / HRing3: three separately stored planes.
+template <typename R, int ROW, int SLAB>
+struct PhiSlab3 {
+  const R* base;  // plane of the node
+  __device__ __forceinline__ R at(int dz, int ly, int lx) const {
+    return base[dz * SLAB + ly * ROW + lx];
+  }
+};
+template <typename R, int ROW, int SLAB, int PLANE>
+struct HSlab3 {
+  const R* base;  // direction 0, plane of the node
+  __device__ __forceinline__ R at(int a, int dz, int ly, int lx) const {
+    return base[a * PLANE + dz * SLAB + ly * ROW + lx];
+  }
+};
+template <typename R, int ROW>
+struct PhiRing3 {
+  const R* p[3];  // planes dz = -1, 0, 1
+  __device__ __forceinline__ R at(int dz, int ly, int lx) const { return p[dz + 1][ly * ROW + lx]; }
+};
+template <typename R, int ROW, int PLANE>
+struct HRing3 {
+  const R* p[3];  // planes dz = -1, 0, 1 (direction 0; direction a at + a * PLANE)
+  __device__ __forceinline__ R at(int a, int dz, int ly, int lx) const {
+    return p[dz + 1][a * PLANE + ly * ROW + lx];
   }
 };
 
-// phi_s: phi + 1 of the halo-extended tile, [lz][ly][lx] with row PROW and
-// slab PSLAB.  INTERIOR: every node of the tile is at least one node away from
-// every domain face, so every destination is an ordinary node.
-template <typename T, typename R, bool FLOW, bool INTERIOR, int PROW, int PSLAB, typename HV>
+// pv: phi + 1 around the node, hv: the h deviations around it (views above).
+// INTERIOR: every node of the tile is at least one node away from every
+// domain face, so every destination is an ordinary node.
+template <typename T, typename R, bool FLOW, bool INTERIOR, typename PV, typename HV>
 __device__ __forceinline__ void collide_push_3d(const Model& m, int x, int y, int z, int lx,
-                                                int ly, int lz, const R (&f)[19],
-                                                const R (&g)[7], const R (&h)[7], R dphi,
-                                                R dphi_prev, const R* phi_s, const HV& hs,
+                                                int ly, const R (&f)[19], const R (&g)[7],
+                                                const R (&h)[7], R dphi, R dphi_prev,
+                                                const PV& pv, const HV& hs,
                                                 T* __restrict__ dst, R* __restrict__ ring_cur,
                                                 unsigned* __restrict__ err) {
   constexpr int QF = FLOW ? 19 : 0;
@@ -72,11 +94,10 @@ __device__ __forceinline__ void collide_push_3d(const Model& m, int x, int y, in
   if (!(finite_r(phi) && finite_r(U) && finite_r(rho))) atomicOr(err, 1u);
 
   // ---- grad = 3 sum_a w_a c_a phi(x + c_a) over D3Q19 ---------------------------
-  const R* pc = phi_s + lz * PSLAB + ly * PROW + lx;
   R gr[3] = {R(0), R(0), R(0)};
 #pragma unroll
   for (int a = 1; a < 19; ++a) {
-    const R v = pc[D3_CZ[a] * PSLAB + D3_CY[a] * PROW + D3_CX[a]] * (a < 7 ? R(1.0 / 6.0) : R(1.0 / 12.0));
+    const R v = pv.at(D3_CZ[a], ly + D3_CY[a], lx + D3_CX[a]) * (a < 7 ? R(1.0 / 6.0) : R(1.0 / 12.0));
     if (D3_CX[a]) gr[0] += R(D3_CX[a]) * v;
     if (D3_CY[a]) gr[1] += R(D3_CY[a]) * v;
     if (D3_CZ[a]) gr[2] += R(D3_CZ[a]) * v;
@@ -129,7 +150,7 @@ __device__ __forceinline__ void collide_push_3d(const Model& m, int x, int y, in
       const int off = cz * slab + cy * px + cx;
       if (FLOW) Pop<T>::st(pd + (a * P + off), fp);
       if (sc) {
-        const R hold = hs.at(a, lz + cz, ly + cy, lx + cx);
+        const R hold = hs.at(a, cz, ly + cy, lx + cx);
         Pop<T>::st(pd + ((QF + a) * P + off), gp);
         Pop<T>::st(pd + ((QF + 7 + a) * P + off), fma_r(inv_a2, hp, mul_r(keep_old, hold)));  // Eq. 19
       }
@@ -162,7 +183,7 @@ __device__ __forceinline__ void collide_push_3d(const Model& m, int x, int y, in
       const int jd = zd * slab + yd * px + xd;
       if (FLOW) Pop<T>::st(dst + (a * P + jd), fp);
       if (sc) {
-        const R hold = hs.at(a, lz + cz, ly + cy, lx + cx);
+        const R hold = hs.at(a, cz, ly + cy, lx + cx);
         Pop<T>::st(dst + ((QF + a) * P + jd), gp);
         Pop<T>::st(dst + ((QF + 7 + a) * P + jd), fma_r(inv_a2, hp, mul_r(keep_old, hold)));  // Eq. 19
       }
@@ -184,7 +205,7 @@ __device__ __forceinline__ void collide_push_3d(const Model& m, int x, int y, in
           const int jo = zo * slab + yo * px + x;
           if (FLOW) Pop<T>::st(dst + (a * P + jo), fp);
           if (sc) {
-            const R hold = hs.at(a, lz + cz, ly + cy, lx);
+            const R hold = hs.at(a, cz, ly + cy, lx);
             Pop<T>::st(dst + ((QF + a) * P + jo), gp);
             Pop<T>::st(dst + ((QF + 7 + a) * P + jo), fma_r(inv_a2, hp, mul_r(keep_old, hold)));
           }

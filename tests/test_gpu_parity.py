@@ -133,6 +133,28 @@ def test_3d_fp64_walls(P):
     check(P, a, b, TOL64, ("phi", "U", "rho", "ux", "uy", "uz"))
 
 
+def test_3d_fp32_ragged_walls_inlet(P):
+    # sizes that are not multiples of the 32 x 8 column or of the z chunk of
+    # the z-marching kernel (two chunks, a partial one), walls in y and z
+    p = P.params(dim=3, nx=37, ny=19, nz=45, flow=1, fold=0, eps=0.04, bc=(1, 2, 2),
+                 u_in=0.004, U_in=0.45)
+    f = P.seeded_fields(p, seed=11, radius=5.0, u0=0.45, amp_u=0.004)
+    a, b = P.pair(p, "fp32", fields=f)
+    a.step(80)
+    b.step(80, P.THREADS)
+    check(P, a, b, TOL32, ("phi", "U", "rho", "ux", "uy", "uz"))
+
+
+def test_3d_fp32_walls_periodic_body(P):
+    p = P.params(dim=3, nx=21, ny=18, nz=14, flow=1, fold=0, eps=0.04, bc=(0, 2, 2),
+                 body=(1e-6, 0, 0))
+    f = P.seeded_fields(p, seed=7, radius=4.0, u0=0.5, amp_u=0.01)
+    a, b = P.pair(p, "fp32", fields=f)
+    a.step(60)
+    b.step(60, P.THREADS)
+    check(P, a, b, TOL32, ("phi", "U", "rho", "ux", "uy", "uz"))
+
+
 def test_3d_no_flow_periodic(P):
     p = P.params(dim=3, nx=32, ny=32, nz=32, flow=0, fold=0, eps=0.04)
     a, b = P.pair(p, "fp32", seed_args=(16.0, 16.0, 16.0, 7.0, 0.5, 0.01, 8))
