@@ -23,6 +23,9 @@
 //   warps 2-5  epilogue: tcgen05.ld of their 32-lane quarter of an
 //              accumulator, bias / ReLU / mask, bf16 stores; then release the
 //              accumulator, so that the next tile's products overlap them
+// conv3x3_tc_halo_kernel (below) is the variant taken wherever the image
+// width is a multiple of 128 and N <= 128: one input box per (channel chunk,
+// ky) serves the three kx taps.
 // Every wait on a barrier is bounded; on a timeout the kernel sets bit 2 of
 // *err, lets the copies and products already issued finish, frees its tensor
 // memory and returns (the host turns the bit into an error status).
@@ -52,6 +55,17 @@ __device__ __forceinline__ uint64_t umma_desc(uint32_t saddr, uint32_t sbo, uint
   d |= uint64_t(1) << 46;                           // descriptor version
   d |= uint64_t(mode) << 61;                        // swizzle mode
   return d;
+}
+
+// The same with the matrix starting `row` rows (of one swizzle span, rb
+// bytes) into a 1024-byte aligned swizzled buffer.  The swizzle phase follows
+// the absolute shared-memory address (as the TMA wrote it), so the start may
+// sit at any row with the base-offset field left at 0 (measured: setting it
+// to the row's phase, or starting at the aligned group with that phase,
+// gives wrong products).
+__device__ __forceinline__ uint64_t umma_desc_row(uint32_t saddr_aligned, int row, uint32_t rb,
+                                                  uint32_t sbo, uint32_t mode) {
+  return umma_desc(saddr_aligned + uint32_t(row) * rb, sbo, mode);
 }
 
 __device__ __forceinline__ void tc_fence_before() {
@@ -329,6 +343,247 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   }
 }
 
+// ---- halo variant: one input box per (channel chunk, ky) serves the three kx taps
+// Tiles of G image rows x 128 pixels (images of width a multiple of 128), BK
+// input channels per K step.  A K step loads the G rows h0 + ky - 1 + g of the
+// tile's columns w0 - 1 .. w0 + 128 (130 pixels, zero fill outside the
+// image) and the weights of the taps (ky, kx = 0, 1, 2); sub-tile g's operand
+// for tap kx is the 128 rows starting kx rows into row g of the box, so each
+// input row is fetched once per ky instead of once per tap.
+template <int BK, int BN, int G>
+struct HaloShape {
+  static constexpr int ROWS = 130;                 // pixels per box row
+  static constexpr int RB = BK * 2;                // bytes per pixel row (one swizzle span)
+  static constexpr int A_ROW = ROWS * RB;          // bytes of one image row of the box
+  static constexpr int A_BYTES = G * A_ROW;
+  static constexpr int B_TAP = BN * RB;            // bytes of one tap's weights
+  static constexpr int B_OFF = (A_BYTES + 1023) / 1024 * 1024;
+  static constexpr int STAGE = (B_OFF + 3 * B_TAP + 1023) / 1024 * 1024;
+  static constexpr int TX_BYTES = A_BYTES + 3 * B_TAP;
+  static constexpr int S_FIT = 204800 / STAGE;
+  static constexpr int S = S_FIT > 16 ? 16 : (S_FIT < 2 ? 2 : S_FIT);
+  static constexpr int SMEM = S * STAGE + 1024;
+  static_assert(SMEM <= 226 * 1024, "stage ring exceeds shared memory");
+  static constexpr uint32_t SBO = 8 * RB;
+  static constexpr uint32_t MODE = BK == 64 ? 2 : (BK == 32 ? 4 : 6);  // 128 / 64 / 32 B swizzle
+  static constexpr uint32_t IDESC =
+      (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(BN >> 3) << 17) | (uint32_t(128 >> 4) << 24);
+  static constexpr uint32_t ACC = G * BN;
+  static constexpr uint32_t TCOLS = 2 * ACC;
+  static_assert(TCOLS <= 512, "accumulators exceed tensor memory");
+};
+
+struct HaloArgs {
+  int H, W, rows_t, cols_t;  // image size; tiles per image column / row
+  int ci_off, nchunks;       // first input channel; 64-channel chunks
+  int ntiles, ntiles_n;      // tiles; channel tiles
+  int Cy, co_off, relu, Cout;
+  const float* bias;
+  const bf16* mask;
+  bf16* y;
+  unsigned* err;
+};
+
+template <int BK, int BN, int G>
+__global__ void __launch_bounds__(kTcThreads, 1)
+    conv3x3_tc_halo_kernel(const __grid_constant__ CUtensorMap mx,
+                           const __grid_constant__ CUtensorMap mw, const HaloArgs a) {
+  using Sh = HaloShape<BK, BN, G>;
+  constexpr int S = Sh::S;
+  extern __shared__ uint8_t smem_raw[];
+  __shared__ __align__(8) uint64_t full[S], empty[S], acc_full[2], acc_empty[2], fin;
+  __shared__ uint32_t tmem_base;
+  __shared__ float sbias[256];
+  uint8_t* smem = smem_raw + ((1024u - (smem_addr(smem_raw) & 1023u)) & 1023u);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int ksteps = 3 * a.nchunks;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < S; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&acc_full[b], 1);
+      mbar_init(&acc_empty[b], 4);
+    }
+    mbar_init(&fin, 1);
+    fence_barrier_init();
+  }
+  if (warp == 1) tmem_alloc(&tmem_base, Sh::TCOLS);
+  for (int i = threadIdx.x; i < a.Cout; i += blockDim.x) sbias[i] = a.bias ? a.bias[i] : 0.f;
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_base;
+  // tile t -> (image, first row, first column, first output channel)
+  auto tile_at = [&](int t, int& img, int& h0, int& w0, int& n0) {
+    const int gm = t / a.ntiles_n;
+    n0 = (t % a.ntiles_n) * BN;
+    const int per_img = a.rows_t * a.cols_t;
+    img = gm / per_img;
+    const int r = gm % per_img;
+    h0 = (r / a.cols_t) * G;
+    w0 = (r % a.cols_t) * 128;
+  };
+
+  if (warp == 0 && lane == 0) {
+    int st = 0, it = 0;
+    uint32_t ph = 0;
+    bool ok = true;
+    for (int t = blockIdx.x; t < a.ntiles && ok; t += gridDim.x) {
+      int img, h0, w0, n0;
+      tile_at(t, img, h0, w0, n0);
+      int c0 = 0, ky = 0;
+      for (int ks = 0; ks < ksteps; ++ks, ++it) {
+        if (it >= S && !mbar_wait_bounded(&empty[st], ph ^ 1u, kTcSpin)) {
+          atomicOr(a.err, 2u);
+          ok = false;
+          break;
+        }
+        uint8_t* sa = smem + st * Sh::STAGE;
+        mbar_arrive_expect_tx(&full[st], Sh::TX_BYTES);
+        tma_load_4d(sa, &mx, &full[st], a.ci_off + c0, w0 - 1, h0 + ky - 1, img);
+        tma_load_4d(sa + Sh::B_OFF, &mw, &full[st], c0, n0, 0, ky);
+        if (++ky == 3) {
+          ky = 0;
+          c0 += BK;
+        }
+        if (++st == S) {
+          st = 0;
+          ph ^= 1u;
+        }
+      }
+    }
+    for (int j = it > S ? it - S : 0; j < it; ++j)
+      if (!mbar_wait_bounded(&full[j % S], uint32_t(j / S) & 1u, kTcSpin)) atomicOr(a.err, 2u);
+  } else if (warp == 1 && lane == 0) {
+    const uint32_t s0 = smem_addr(smem);
+    int st = 0, tc = 0;
+    uint32_t ph = 0;
+    bool ok = true;
+    for (int t = blockIdx.x; t < a.ntiles && ok; t += gridDim.x, ++tc) {
+      const int buf = tc & 1;
+      if (tc >= 2 && !mbar_wait_bounded(&acc_empty[buf], uint32_t((tc >> 1) - 1) & 1u, kTcSpin)) {
+        atomicOr(a.err, 2u);
+        break;
+      }
+      tc_fence_after();
+      const uint32_t d = tmem + uint32_t(buf * Sh::ACC);
+      for (int ks = 0; ks < ksteps; ++ks) {
+        if (!mbar_wait_bounded(&full[st], ph, kTcSpin)) {
+          atomicOr(a.err, 2u);
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t sa = s0 + uint32_t(st * Sh::STAGE), sb = sa + Sh::B_OFF;
+#pragma unroll
+        for (int kk = 0; kk < BK / 16; ++kk)
+#pragma unroll
+          for (int kx = 0; kx < 3; ++kx) {
+            const uint64_t db =
+                umma_desc(sb + uint32_t(kx * Sh::B_TAP + kk * 32), Sh::SBO, Sh::MODE);
+#pragma unroll
+            for (int g = 0; g < G; ++g)
+              tc_mma(d + uint32_t(g * BN),
+                     umma_desc_row(sa, g * Sh::ROWS + kx, Sh::RB, Sh::SBO, Sh::MODE) +
+                         uint64_t((kk * 32) >> 4),
+                     db, Sh::IDESC, (ks | kk | kx) != 0);
+          }
+        tc_commit(&empty[st]);
+        if (++st == S) {
+          st = 0;
+          ph ^= 1u;
+        }
+      }
+      if (ok) tc_commit(&acc_full[buf]);
+    }
+    tc_commit(&fin);
+    if (!mbar_wait_bounded(&fin, 0u, kTcSpin)) atomicOr(a.err, 2u);
+  } else if (warp >= 2) {
+    const int q = warp & 3;
+    const int m = q * 32 + lane;
+    int tc = 0;
+    for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x, ++tc) {
+      const int buf = tc & 1;
+      bool ok = mbar_wait_bounded(&acc_full[buf], uint32_t(tc >> 1) & 1u, kTcSpin);
+      ok = __all_sync(0xffffffffu, ok);
+      if (!ok) {
+        if (lane == 0) atomicOr(a.err, 2u);
+        break;
+      }
+      tc_fence_after();
+      int img, h0, w0, n0;
+      tile_at(t, img, h0, w0, n0);
+#pragma unroll 1
+      for (int g = 0; g < G; ++g) {
+        const long long p = ((long long)img * a.H + h0 + g) * a.W + w0 + m;
+        bf16* yrow = a.y + p * a.Cy + a.co_off + n0;
+        const bf16* mrow = a.mask ? a.mask + p * a.Cy + a.co_off + n0 : nullptr;
+#pragma unroll 1
+        for (int c = 0; c < BN; c += 32) {
+          uint32_t r[32];
+          tmem_ld32(tmem + (uint32_t(q * 32) << 16) + uint32_t(buf * Sh::ACC + g * BN + c), r);
+          uint4 mk[4];
+          if (mrow)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) mk[v] = reinterpret_cast<const uint4*>(mrow + c)[v];
+          uint32_t out[16];
+#pragma unroll
+          for (int j = 0; j < 32; j += 2) {
+            float v0 = __uint_as_float(r[j]) + sbias[n0 + c + j];
+            float v1 = __uint_as_float(r[j + 1]) + sbias[n0 + c + j + 1];
+            if (a.relu) {
+              v0 = fmaxf(v0, 0.f);
+              v1 = fmaxf(v1, 0.f);
+            }
+            if (mrow) {
+              const __nv_bfloat162 mm = reinterpret_cast<const __nv_bfloat162*>(mk)[j / 2];
+              if (!(__low2float(mm) > 0.f)) v0 = 0.f;
+              if (!(__high2float(mm) > 0.f)) v1 = 0.f;
+            }
+            const __nv_bfloat162 o = __floats2bfloat162_rn(v0, v1);
+            out[j / 2] = *reinterpret_cast<const uint32_t*>(&o);
+          }
+#pragma unroll
+          for (int v = 0; v < 4; ++v)
+            reinterpret_cast<uint4*>(yrow + c)[v] =
+                make_uint4(out[4 * v], out[4 * v + 1], out[4 * v + 2], out[4 * v + 3]);
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&acc_empty[buf]);
+    }
+    tc_fence_before();
+  }
+  __syncthreads();
+  if (warp == 1) {
+    __syncwarp();
+    tc_fence_after();
+    tmem_dealloc(tmem, Sh::TCOLS);
+  }
+}
+
+template <int BK, int BN, int G>
+cudaError_t launch_halo(const CUtensorMap& mx, const CUtensorMap& mw, const HaloArgs& t,
+                        cudaStream_t s) {
+  using Sh = HaloShape<BK, BN, G>;
+  static int sms = 0;
+  if (!sms) {
+    cudaError_t e = cudaFuncSetAttribute(conv3x3_tc_halo_kernel<BK, BN, G>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, Sh::SMEM);
+    if (e != cudaSuccess) return e;
+    int dev = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+      return e;
+  }
+  const unsigned grid = unsigned(t.ntiles < sms ? t.ntiles : sms);
+  conv3x3_tc_halo_kernel<BK, BN, G><<<grid, kTcThreads, Sh::SMEM, s>>>(mx, mw, t);
+  return cudaGetLastError();
+}
+
 CUtensorMapSwizzle swizzle_for(int bk) {
   return bk == 64 ? CU_TENSOR_MAP_SWIZZLE_128B
                   : (bk == 32 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_32B);
@@ -390,8 +645,98 @@ bool conv3x3_tc_supported(const ConvArgs& a) {
          a.co_off + a.Cout <= a.Cy;
 }
 
+// the halo variant: images of width a multiple of 128, output tiles of at
+// most 128 channels (its three-tap weight box bounds N)
+template <int BK>
+cudaError_t launch_halo_bk(int BN, int G, const CUtensorMap& mx, const CUtensorMap& mw,
+                           const HaloArgs& t, cudaStream_t s) {
+  switch (BN * 16 + G) {
+    case 32 * 16 + 8: return launch_halo<BK, 32, (BK < 64 ? 8 : 4)>(mx, mw, t, s);
+    case 32 * 16 + 4: return launch_halo<BK, 32, 4>(mx, mw, t, s);
+    case 32 * 16 + 2: return launch_halo<BK, 32, 2>(mx, mw, t, s);
+    case 32 * 16 + 1: return launch_halo<BK, 32, 1>(mx, mw, t, s);
+    case 64 * 16 + 4: return launch_halo<BK, 64, (BK < 64 ? 4 : 2)>(mx, mw, t, s);
+    case 64 * 16 + 2: return launch_halo<BK, 64, 2>(mx, mw, t, s);
+    case 64 * 16 + 1: return launch_halo<BK, 64, 1>(mx, mw, t, s);
+    case 128 * 16 + 2: return launch_halo<BK, 128, (BK < 64 ? 2 : 1)>(mx, mw, t, s);
+    case 128 * 16 + 1: return launch_halo<BK, 128, 1>(mx, mw, t, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+static cudaError_t conv3x3_tc_halo(const ConvArgs& a, unsigned* err, cudaStream_t s, bool* used) {
+  *used = false;
+  if (const char* e = getenv("LBPF_CONV_HALO"))
+    if (atoi(e) == 0) return cudaSuccess;
+  if (a.W % 128 || a.Cin % 16) return cudaSuccess;
+  // the widest channel chunk: splitting 64 channels into 32-wide chunks (to
+  // fit 8 rows per tile instead of 4) measured slower
+  const int BK = a.Cin % 64 == 0 ? 64 : (a.Cin % 32 == 0 ? 32 : 16);
+  int BN = 128;
+  while (BN > 32 && a.Cout % BN) BN >>= 1;
+  if (a.Cout % BN) return cudaSuccess;
+  // rows per tile: about 256 accumulator columns (within shared memory), as
+  // many tiles as SMs where the image allows, G dividing the image height
+  int G = 256 / BN;
+  if (BK == 64 && G > 4) G = 4;
+  if (BK == 64 && BN == 64) G = 2;
+  if (BK == 64 && BN == 128) G = 1;
+  const long long row_tiles = (long long)a.N * a.H * (a.W / 128);
+  while (G > 1 && (a.H % G || (row_tiles / G) * (a.Cout / BN) < 152)) G >>= 1;
+  if (a.H % G) return cudaSuccess;
+  const CUtensorMapSwizzle sw = swizzle_for(BK);
+  CUtensorMap mx, mw;
+  {
+    const uint64_t dims[4] = {uint64_t(a.Cx), uint64_t(a.W), uint64_t(a.H), uint64_t(a.N)};
+    const uint64_t strides[3] = {uint64_t(a.Cx) * 2, uint64_t(a.W) * a.Cx * 2,
+                                 uint64_t(a.H) * a.W * a.Cx * 2};
+    const uint32_t box[4] = {uint32_t(BK), 130, uint32_t(G), 1};
+    if (!encode_tiled(&mx, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<bf16*>(a.x), dims,
+                      strides, box, sw))
+      return cudaErrorInvalidValue;
+  }
+  {
+    // weights [ky][kx][Cout][Cin] viewed as (Cin, Cout, kx, ky)
+    const uint64_t dims[4] = {uint64_t(a.Cin), uint64_t(a.Cout), 3, 3};
+    const uint64_t strides[3] = {uint64_t(a.Cin) * 2, uint64_t(a.Cout) * a.Cin * 2,
+                                 3ull * a.Cout * a.Cin * 2};
+    const uint32_t box[4] = {uint32_t(BK), uint32_t(BN), 3, 1};
+    if (!encode_tiled(&mw, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<bf16*>(a.w), dims,
+                      strides, box, sw))
+      return cudaErrorInvalidValue;
+  }
+  HaloArgs t;
+  t.H = a.H;
+  t.W = a.W;
+  t.rows_t = a.H / G;
+  t.cols_t = a.W / 128;
+  t.ci_off = a.ci_off;
+  t.nchunks = a.Cin / BK;
+  t.ntiles_n = a.Cout / BN;
+  t.ntiles = a.N * t.rows_t * t.cols_t * t.ntiles_n;
+  t.Cy = a.Cy;
+  t.co_off = a.co_off;
+  t.relu = a.relu;
+  t.Cout = a.Cout;
+  t.bias = a.bias;
+  t.mask = a.mask;
+  t.y = a.y;
+  t.err = err;
+  *used = true;
+  switch (BK) {
+    case 64: return launch_halo_bk<64>(BN, G, mx, mw, t, s);
+    case 32: return launch_halo_bk<32>(BN, G, mx, mw, t, s);
+    default: return launch_halo_bk<16>(BN, G, mx, mw, t, s);
+  }
+}
+
 cudaError_t conv3x3_tc(const ConvArgs& a, unsigned* err, cudaStream_t s) {
   if (!conv3x3_tc_supported(a) || !err) return cudaErrorInvalidValue;
+  {
+    bool used = false;
+    const cudaError_t e = conv3x3_tc_halo(a, err, s, &used);
+    if (used || e != cudaSuccess) return e;
+  }
   const long long npix = (long long)a.N * a.H * a.W;
   const int BK = a.Cin % 64 == 0 ? 64 : (a.Cin % 32 == 0 ? 32 : 16);
   // the widest N the channels allow: a tcgen05.mma costs about the same time
