@@ -165,6 +165,25 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
+def max_over_ranks(values, dist=None, device="cuda"):
+    """The element-wise maximum of per-rank timings over all ranks (the job
+    is as slow as its slowest replica); the values themselves without a
+    process group.  device: where the reduction runs (cuda for NCCL, cpu for
+    gloo)."""
+    if dist is None:
+        return [float(v) for v in values]
+    import torch
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.tolist()]
+
+
+def whole_job_rate(units_per_rank, world, seconds):
+    """Whole-job throughput: the units all ranks processed over the slowest
+    rank's time (weak scaling: every replica processes the same units)."""
+    return units_per_rank * world / seconds
+
+
 def source_digest(files):
     """sha256 over the concatenated sources a kernel is compiled from."""
     h = hashlib.sha256()
@@ -380,12 +399,9 @@ def main():
         torch.cuda.synchronize()
         barrier()
     ms = ev0.elapsed_time(ev1)
-    t = torch.tensor([ms], device="cuda")
-    if dist is not None:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
+    ms_max = max_over_ranks([ms], dist)[0]
     per_step_ms = ms_max / args.steps
-    value = w["nodes"] * world * args.steps / (ms_max * 1e-3) / 1e6
+    value = whole_job_rate(w["nodes"] * args.steps, world, ms_max * 1e-3) / 1e6
     diags = [s.diagnostics() for s in sims]  # also surfaces any sticky device error
     d = diags[0]
 
@@ -432,10 +448,8 @@ def main():
         e2e_step()
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
-    te = torch.tensor([e2e_s], device="cuda")
-    if dist is not None:
-        dist.all_reduce(te, op=dist.ReduceOp.MAX)
-    e2e_value = w["nodes"] * world * args.e2e_steps / float(te.item()) / 1e6
+    e2e_max = max_over_ranks([e2e_s], dist)[0]
+    e2e_value = whole_job_rate(w["nodes"] * args.e2e_steps, world, e2e_max) / 1e6
     h2d = sum(int(x.numel()) for x in host_states)
     d2h = sum(int(x.numel()) * 4 for x in host_outs)
 
@@ -609,10 +623,7 @@ def run_surrogate(args, w):
         ev1.record(stream)
         torch.cuda.synchronize()
         ms_lb = ev0.elapsed_time(ev1)
-    t = torch.tensor([ms_s, ms_lb], device="cuda")
-    if dist is not None:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_s, ms_lb = float(t[0]), float(t[1])
+    ms_s, ms_lb = max_over_ranks([ms_s, ms_lb], dist)
     da, db = a.diagnostics(), b.diagnostics()
     grow_lb = db["iface_pos"][:4] - d0["iface_pos"][:4]
     grow_s = da["iface_pos"][:4] - d0["iface_pos"][:4]
