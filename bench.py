@@ -78,13 +78,14 @@ WORKLOADS = {
     "c5": dict(desc="learned block propagator on 2D 512x512 closed channels (periodic x, walls y, "
                     "body-force Poiseuille flow u_max~U[0,0.01], U0~U[0.25,0.45], R~U[6,16], "
                     "fold 4 or 5, eps~U[0.02,0.05]): BF16 U-Net 32/64/128/256 channels trained "
-                    "on the GPU on 2000 LB pairs from 50 sampled problems, 200-step blocks, LB "
+                    "on the GPU on 2000 LB pairs from 50 sampled problems (mirror "
+                    "augmentation, 4000 Adam steps), 200-step blocks, LB "
                     "judge every 8th block, fallback at drift > 1e-3 or interface error > 1 lu; "
                     "held-out problem; FP32 LB",
                dim=2, nx=512, ny=512, nz=1, flow=1, fold=5, eps=0.03, bc=(0, 2, 0), u_in=0.0,
                U_in=0.0, storage="fp32", kernel="conv3x3_tc_kernel", src=SRC_CONV,
                surrogate=dict(block=200, judge_every=8, traj=50, t_end=20000, every=500,
-                              crop=256, train_steps=2000, batch=8, lr=1e-3, start=1000),
+                              crop=256, train_steps=4000, batch=8, lr=5e-4, start=1000),
                sample=dict(nx=256, ny=256, channel=True)),
     "c5net": dict(desc="the c5 network alone: BF16 U-Net 32/64/128/256 channels on a 512x512 "
                        "sample (4 -> 4 channels, random weights): forward passes, then "
@@ -588,11 +589,18 @@ def run_surrogate(args, w):
     tr = L.UNet(in_ch=4, out_ch=4, levels=4, batch=c["batch"], height=c["crop"], width=nx,
                 seed=1, stream=stream.cuda_stream)
     t0 = time.perf_counter()
-    hist = S.train(tr, X, T, c["train_steps"], lr=c["lr"], log_every=500)
+    hist = S.train(tr, X, T, c["train_steps"], lr=c["lr"], log_every=1000)
     tr.status()
     t_train = time.perf_counter() - t0
     npairs = int(X.shape[0])
     del X, T
+    # held-out pairs (other problems): the network's error against predicting no change
+    Xv, Tv = S.generate_pairs(3, c["t_end"], 2 * c["every"], nx, ny, cfg, seed=999,
+                              crop=c["crop"])
+    ev = S.inference_net(tr, nx, c["crop"], stream.cuda_stream)
+    mse_net, mse_none = S.prediction_error(ev, Xv, Tv)
+    ev.close()
+    del Xv, Tv
     net = S.inference_net(tr, nx, ny, stream.cuda_stream)
     tr.close()
 
@@ -713,7 +721,9 @@ def run_surrogate(args, w):
                        "training": {"steps": c["train_steps"], "batch": c["batch"],
                                     "band_rows": c["crop"], "data_s": round(t_data, 1),
                                     "train_s": round(t_train, 1),
-                                    "loss": [round(x[1], 5) for x in hist]},
+                                    "loss": [round(x[1], 5) for x in hist],
+                                    "held_out_mse": mse_net, "held_out_mse_no_network": mse_none,
+                                    "held_out_ratio": mse_net / mse_none},
                        "held_out_problem": info,
                        "l2": "network activations of a 512x512 sample exceed L2 at level 0 "
                              "only partly; the LB state (59 MB) fits in L2: both arms time the "

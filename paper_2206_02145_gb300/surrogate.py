@@ -112,17 +112,30 @@ def generate_pairs(n_traj: int, t_end: int, every: int, nx: int, ny: int, cfg, s
     return X, T
 
 
-def train(net: UNet, X, T, steps: int, lr: float = 1e-3, seed: int = 0, log_every: int = 50):
+# the channel problems' mirror symmetries: x -> -x with ux -> -ux, y -> -y
+# with uy -> -uy (channels phi, U, ux, uy of the inputs and the targets)
+_FLIP_SIGN = {2: (1.0, 1.0, -1.0, 1.0), 1: (1.0, 1.0, 1.0, -1.0)}
+
+
+def train(net: UNet, X, T, steps: int, lr: float = 5e-4, seed: int = 0, log_every: int = 50,
+          augment: bool = True):
     """Adam on random minibatches of net's batch size, cosine-decayed learning
-    rate; returns [(step, loss)] read every log_every steps."""
+    rate; with augment, each minibatch is mirrored in x or y (or left as is)
+    at random.  Returns [(step, loss)] read every log_every steps."""
     B = net.cfg.batch
     g = torch.Generator(device="cpu").manual_seed(seed)
     loss = torch.zeros(1, device=X.device)
+    signs = {d: torch.tensor(v, device=X.device, dtype=X.dtype) for d, v in _FLIP_SIGN.items()}
     hist = []
     for s in range(steps):
         idx = torch.randint(0, X.shape[0], (B,), generator=g).to(X.device)
         xb = X.index_select(0, idx)
         tb = T.index_select(0, idx)
+        if augment:
+            d = int(torch.randint(0, 3, (1,), generator=g))
+            if d in signs:  # dims of [B, H, W, C]: 2 mirrors x, 1 mirrors y
+                xb = (xb.flip(d) * signs[d]).contiguous()
+                tb = (tb.flip(d) * signs[d]).contiguous()
         a = lr * 0.5 * (1.0 + math.cos(math.pi * s / max(steps, 1)))
         net.train_step(xb, tb, max(a, lr * 0.02), loss)
         if (s + 1) % log_every == 0 or s == steps - 1:

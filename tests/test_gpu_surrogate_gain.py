@@ -30,7 +30,7 @@ def trained():
     Xv, Tv = S.generate_pairs(2, 4000, 400, NX, NY, cfg, seed=999, crop=128)
     net = L.UNet(in_ch=4, out_ch=4, levels=3, batch=8, height=128, width=NX, seed=1,
                  stream=L.current_stream())
-    hist = S.train(net, X, T, 800, lr=1e-3, log_every=200)
+    hist = S.train(net, X, T, 800, lr=1e-3, log_every=200, augment=False)
     net.status()
     return L, S, cfg, net, (Xv, Tv), hist
 
