@@ -75,6 +75,11 @@ WORKLOADS = {
                U_in=0.35, storage="fp16", kernel="step2d_batch_kernel", src=SRC_BATCH,
                batch=64, sweep_seed=4,
                sample=dict(nx=256, ny=256, seed=(77.0, 128.0, 0.0, 12.0, 0.35, 0.01, 1))),
+    "c4s": dict(base="c4", batch=256, sides=(32, 128),
+                desc="batched sweep of small instances: 256 2D coupled instances in one "
+                     "persistent launch per step (sides U{32..128}, U0~U[0.1,0.6], "
+                     "R~U[4,min(24,n/5)], u_in~U[0,0.02], fold 4 or 5, eps~U[0.02,0.06]; "
+                     "seed 4), FP16 shifted storage", desc_note="small instances"),
     "c5": dict(desc="learned block propagator on 2D 512x512 closed channels (periodic x, walls y, "
                     "body-force Poiseuille flow u_max~U[0,0.01], U0~U[0.25,0.45], R~U[6,16], "
                     "fold 4 or 5, eps~U[0.02,0.05]): BF16 U-Net 32/64/128/256 channels trained "
@@ -97,18 +102,18 @@ WORKLOADS = {
 }
 
 
-def sweep_members(count: int, seed: int):
+def sweep_members(count: int, seed: int, lo: int = 256, hi: int = 768):
     """Seeded uneven parametric sweep (the synthetic stand-in for the paper's
-    supersaturation x seed-size x inflow studies): square sides U{256..768},
-    U0 ~ U[0.1, 0.6], seed radius ~ U[4, 24], inflow ~ U[0, 0.02], fold 4 or 5,
-    anisotropy ~ U[0.02, 0.06]; seed at (0.3 n, 0.5 n)."""
+    supersaturation x seed-size x inflow studies): square sides U{lo..hi},
+    U0 ~ U[0.1, 0.6], seed radius ~ U[4, min(24, n/5)], inflow ~ U[0, 0.02],
+    fold 4 or 5, anisotropy ~ U[0.02, 0.06]; seed at (0.3 n, 0.5 n)."""
     import numpy as np
     rng = np.random.default_rng(seed)
     params, seeds = [], []
     for i in range(count):
-        n = int(rng.integers(256, 769))
+        n = int(rng.integers(lo, hi + 1))
         u0 = float(rng.uniform(0.1, 0.6))
-        r = float(rng.uniform(4, 24))
+        r = float(rng.uniform(4, min(24, n / 5)))
         params.append(dict(dim=2, nx=n, ny=n, flow=1, fold=int(rng.choice([4, 5])),
                            eps_aniso=float(rng.uniform(0.02, 0.06)), bc=(1, 0, 0),
                            u_inlet=float(rng.uniform(0.0, 0.02)), u0_inlet=u0))
@@ -131,7 +136,7 @@ def workload(name):
     w["bytes_per_lup"] = 2 * q * ELEM[w["storage"]] + 2 * ring
     w["nodes"] = w["nx"] * w["ny"] * w["nz"]
     if w.get("batch"):
-        params, seeds = sweep_members(w["batch"], w["sweep_seed"])
+        params, seeds = sweep_members(w["batch"], w["sweep_seed"], *w.get("sides", (256, 768)))
         w["members"] = (params, seeds)
         w["nodes"] = sum(p["nx"] * p["ny"] for p in params)
     return w
@@ -420,9 +425,29 @@ def main():
         ev1.record(stream)
         torch.cuda.synchronize()
         seq_ms = ev0.elapsed_time(ev1) / kseq
+        # the plain form: the same instances in FP32 storage, one after another
+        params32, seeds32 = w["members"]
+        plain = []
+        for p_, s_ in zip(params32, seeds32):
+            q = L.Sim(stream=stream.cuda_stream, **dict(p_, storage=L.FP32))
+            q.init_seed(*s_)
+            plain.append(q)
+        for q in plain:
+            q.step(64)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for q in plain:
+            q.step(kseq)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        fp32_ms = ev0.elapsed_time(ev1) / kseq
+        for q in plain:
+            q.close()
         batch_info = {"instances": batch.count, "tuning": batch.tuning(),
                       "sequential_ms_per_step": seq_ms,
-                      "speedup_vs_sequential": seq_ms / per_step_ms}
+                      "speedup_vs_sequential": seq_ms / per_step_ms,
+                      "plain_fp32_sequential_ms_per_step": fp32_ms,
+                      "speedup_vs_plain_fp32": fp32_ms / per_step_ms}
 
     # --- end to end through the C ABI with host buffers -------------------------
     # every step: H2D of the full state from pinned memory (lbpf_write_state),
