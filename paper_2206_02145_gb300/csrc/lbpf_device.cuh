@@ -50,6 +50,11 @@ __device__ __forceinline__ R d3q7_w(int a) {
 
 // ---- arithmetic helpers -------------------------------------------------------
 __device__ __forceinline__ float rsqrt_r(float v) { return rsqrtf(v); }
+// Reciprocal of the per-node relaxation and velocity denominators (all in
+// [0.5, ~10]): in FP32 the hardware approximation (2 ulp) instead of the
+// IEEE-exact division sequence; in FP64 the exact division.
+__device__ __forceinline__ float rcp_r(float v) { return __fdividef(1.0f, v); }
+__device__ __forceinline__ double rcp_r(double v) { return 1.0 / v; }
 __device__ __forceinline__ double rsqrt_r(double v) { return rsqrt(v); }
 template <typename R>
 __device__ __forceinline__ R clamp1(R v) {

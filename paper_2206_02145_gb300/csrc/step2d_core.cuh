@@ -62,14 +62,14 @@ __device__ __forceinline__ void collide_push_2d(const Model& m, int x, int y, in
     // Eq. 6: F = b - K u, K = h tau_f (1+phi)^2 (1-phi) / (4 W0^2); the Guo
     // half-force velocity u = (m + F/2)/rho solved in closed form.
     const R K = c.kdrag * (R(1) + ph) * (R(1) + ph) * (R(1) - ph);
-    const R inv = R(1) / (rho + R(0.5) * K);
+    const R inv = rcp_r(rho + R(0.5) * K);
     ux = (mx + R(0.5) * c.body[0]) * inv;
     uy = (my + R(0.5) * c.body[1]) * inv;
     Fx = c.body[0] - K * ux;
     Fy = c.body[1] - K * uy;
   }
   const R usx = mask * ux, usy = mask * uy;  // u* (Eq. 7)
-  const R omega_U = R(1) / (R(0.5) + c.tauU_slope * mask);  // Eq. 18
+  const R omega_U = rcp_r(R(0.5) + c.tauU_slope * mask);  // Eq. 18
   const R dphidt = dphi - dphi_prev;
   ring_cur[idx] = dphi;
   if (!(finite_r(phi) && finite_r(U) && finite_r(rho))) atomicOr(err, 1u);
@@ -84,8 +84,8 @@ __device__ __forceinline__ void collide_push_2d(const Model& m, int x, int y, in
   R as, Nx, Ny, Nz;
   aniso<R>(m, gxv, gyv, R(0), as, Nx, Ny, Nz);
   const R a2 = as * as;
-  const R inv_a2 = R(1) / a2;
-  const R omega_phi = R(1) / (a2 * c.tpc + R(0.5));  // Eq. 23
+  const R inv_a2 = rcp_r(a2);
+  const R omega_phi = rcp_r(a2 * c.tpc + R(0.5));  // Eq. 23
   const R phi2m = R(1) - phi * phi;
   const R Qs = (phi - phi * phi * phi + c.lambda * U * phi2m * phi2m) * c.inv_tau0;  // Eq. 20
   // Node constants of the collisions, so that each direction costs a few FMAs:

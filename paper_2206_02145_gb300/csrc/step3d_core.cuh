@@ -80,7 +80,7 @@ __device__ __forceinline__ void collide_push_3d(const Model& m, int x, int y, in
   R u[3] = {R(0), R(0), R(0)}, F[3] = {R(0), R(0), R(0)};
   if (FLOW) {
     const R K = c.kdrag * (R(1) + ph) * (R(1) + ph) * (R(1) - ph);  // Eq. 6
-    const R inv = R(1) / (rho + R(0.5) * K);
+    const R inv = rcp_r(rho + R(0.5) * K);
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
       u[d] = (mo[d] + R(0.5) * c.body[d]) * inv;
@@ -88,7 +88,7 @@ __device__ __forceinline__ void collide_push_3d(const Model& m, int x, int y, in
     }
   }
   const R us[3] = {mask * u[0], mask * u[1], mask * u[2]};  // Eq. 7
-  const R omega_U = R(1) / (R(0.5) + c.tauU_slope * mask);  // Eq. 18
+  const R omega_U = rcp_r(R(0.5) + c.tauU_slope * mask);  // Eq. 18
   const R dphidt = dphi - dphi_prev;
   ring_cur[idx] = dphi;
   if (!(finite_r(phi) && finite_r(U) && finite_r(rho))) atomicOr(err, 1u);
@@ -105,8 +105,8 @@ __device__ __forceinline__ void collide_push_3d(const Model& m, int x, int y, in
   R as, N[3];
   aniso<R>(m, gr[0], gr[1], gr[2], as, N[0], N[1], N[2]);
   const R a2 = as * as;
-  const R inv_a2 = R(1) / a2;
-  const R omega_phi = R(1) / (a2 * c.tpc + R(0.5));  // Eq. 23
+  const R inv_a2 = rcp_r(a2);
+  const R omega_phi = rcp_r(a2 * c.tpc + R(0.5));  // Eq. 23
   const R phi2m = R(1) - phi * phi;
   const R Qs = (phi - phi * phi * phi + c.lambda * U * phi2m * phi2m) * c.inv_tau0;  // Eq. 20
 
