@@ -30,7 +30,10 @@ def trained():
     Xv, Tv = S.generate_pairs(2, 4000, 400, NX, NY, cfg, seed=999, crop=128)
     net = L.UNet(in_ch=4, out_ch=4, levels=3, batch=8, height=128, width=NX, seed=1,
                  stream=L.current_stream())
-    hist = S.train(net, X, T, 800, lr=1e-3, log_every=200, augment=False)
+    # measured across seeds: 2000 Adam steps at 3e-4 with mirror augmentation
+    # learn reliably (shorter schedules at 1e-3 sometimes do not: the weight
+    # gradient accumulates with FP32 atomics, so training is not bit-reproducible)
+    hist = S.train(net, X, T, 2000, lr=3e-4, log_every=500, augment=True)
     net.status()
     return L, S, cfg, net, (Xv, Tv), hist
 
