@@ -190,6 +190,23 @@ def whole_job_rate(units_per_rank, world, seconds):
     return units_per_rank * world / seconds
 
 
+def iface_compare(d0, fast, plain, dim, min_growth=0.5):
+    """The fast form's interface against the plain FP32 run from the same
+    start: largest position difference over the axis rays (lattice units) and
+    the relative growth-rate error per ray (rays that grew by > min_growth)."""
+    n = 4 if dim == 2 else 6
+    err, rel = [], []
+    for r in range(n):
+        a, b, c = fast[r], plain[r], d0[r]
+        if a < 0 or b < 0 or c < 0:
+            continue
+        err.append(abs(a - b))
+        g = b - c
+        if abs(g) > min_growth:
+            rel.append((a - c - g) / g)
+    return (max(err) if err else None), rel
+
+
 def source_digest(files):
     """sha256 over the concatenated sources a kernel is compiled from."""
     h = hashlib.sha256()
@@ -403,6 +420,9 @@ def main():
         sims = [sim]
         stepper = sim
 
+    # interface rays of the initial state (for the growth comparison below)
+    d_init = [s_.diagnostics()["iface_pos"] for s_ in sims]
+
     # warm-up (also builds the step graph; a batch tunes its tile shape here)
     stepper.step(args.warmup)
     torch.cuda.synchronize()
@@ -423,6 +443,25 @@ def main():
     value = whole_job_rate(w["nodes"] * args.steps, world, ms_max * 1e-3) / 1e6
     diags = [s.diagnostics() for s in sims]  # also surfaces any sticky device error
     d = diags[0]
+    total_steps = args.warmup + args.steps
+
+    vs_fp32 = None
+    if batch is None and w["storage"] != "fp32":
+        # the plain form: the same problem in FP32 storage, the same steps
+        q = L.Sim(stream=stream.cuda_stream, **lib_params(w, L, storage="fp32"))
+        q.init_seed(*w["seed"])
+        q.step(args.warmup)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        q.step(args.steps)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        ms32 = max_over_ranks([ev0.elapsed_time(ev1)], dist)[0]
+        e, rel = iface_compare(d_init[0], d["iface_pos"], q.diagnostics()["iface_pos"], w["dim"])
+        vs_fp32 = {"plain_fp32_ms_per_step": ms32 / args.steps,
+                   "speedup": ms32 / ms_max, "steps": total_steps,
+                   "iface_pos_err_lu": e, "growth_rel_err": rel}
+        q.close()
 
     batch_info = None
     if batch is not None:
@@ -454,13 +493,29 @@ def main():
         ev1.record(stream)
         torch.cuda.synchronize()
         fp32_ms = ev0.elapsed_time(ev1) / kseq
+        # accuracy: every plain FP32 instance brought to the batch's step count
+        left = total_steps - 64 - kseq
         for q in plain:
+            if left > 0:
+                q.step(left)
+        errs, rels = [], []
+        for i, q in enumerate(plain):
+            e, rel = iface_compare(d_init[i], diags[i]["iface_pos"],
+                                   q.diagnostics()["iface_pos"], 2)
+            if e is not None:
+                errs.append(e)
+            rels.extend(rel)
             q.close()
         batch_info = {"instances": batch.count, "tuning": batch.tuning(),
                       "sequential_ms_per_step": seq_ms,
                       "speedup_vs_sequential": seq_ms / per_step_ms,
                       "plain_fp32_sequential_ms_per_step": fp32_ms,
-                      "speedup_vs_plain_fp32": fp32_ms / per_step_ms}
+                      "speedup_vs_plain_fp32": fp32_ms / per_step_ms,
+                      "vs_plain_fp32_after_steps": total_steps,
+                      "iface_pos_err_lu_max": max(errs) if errs else None,
+                      "growth_rel_err_max": max((abs(r) for r in rels), default=None),
+                      "growth_rel_err_median": (sorted(abs(r) for r in rels)[len(rels) // 2]
+                                                if rels else None)}
 
     # --- end to end through the C ABI with host buffers -------------------------
     # every step: H2D of the full state from pinned memory (lbpf_write_state),
@@ -530,6 +585,8 @@ def main():
             "diag": {"step": d["step"], "solute_drift_rel": d["solute_drift_rel"],
                      "r_eq": d["r_eq"]},
         }
+        if vs_fp32 is not None:
+            out["vs_plain_fp32"] = vs_fp32
         if batch_info is not None:
             out["config"]["batch"] = batch_info
             out["config"]["grid"] = "64 square grids, sides 256..768"
