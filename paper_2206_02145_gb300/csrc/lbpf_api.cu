@@ -50,6 +50,16 @@ int fail(lbpf* h, int code, const char* fmt, ...) {
                   __LINE__);                                                            \
   } while (0)
 
+// Rows of `width` bytes between pitched buffers; one contiguous copy when
+// both pitches equal the width (grids whose x size fills the padded row), so
+// that the transfer runs as a single large DMA rather than row by row.
+cudaError_t copy_rows(void* dst, size_t dpitch, const void* src, size_t spitch, size_t width,
+                      size_t rows, cudaMemcpyKind kind, cudaStream_t s) {
+  if (dpitch == width && spitch == width)
+    return cudaMemcpyAsync(dst, src, width * rows, kind, s);
+  return cudaMemcpy2DAsync(dst, dpitch, src, spitch, width, rows, kind, s);
+}
+
 long long nodes(const lbpf_params& p) {
   return (long long)p.nx * p.ny * (p.dim == 3 ? p.nz : 1);
 }
@@ -424,12 +434,11 @@ int lbpf_read_fields(lbpf_t* h, unsigned mask, void* host_dst, size_t bytes, int
     char* dst = static_cast<char*>(host_dst);
     std::memcpy(dst, &hd, sizeof(hd));
     const size_t rows = size_t(hd.q) * h->m.ny * h->m.nz;
-    CK(h, cudaMemcpy2DAsync(dst + sizeof(hd), h->m.nx * h->es, h->pops[h->cur],
-                            h->m.px * h->es, h->m.nx * h->es, rows, cudaMemcpyDeviceToHost,
-                            h->stream));
-    CK(h, cudaMemcpy2DAsync(dst + sizeof(hd) + size_t(hd.q) * n * h->es, h->m.nx * h->rs,
-                            h->phi[h->cur], h->m.px * h->rs, h->m.nx * h->rs,
-                            size_t(h->m.ny) * h->m.nz, cudaMemcpyDeviceToHost, h->stream));
+    CK(h, copy_rows(dst + sizeof(hd), h->m.nx * h->es, h->pops[h->cur], h->m.px * h->es,
+                    h->m.nx * h->es, rows, cudaMemcpyDeviceToHost, h->stream));
+    CK(h, copy_rows(dst + sizeof(hd) + size_t(hd.q) * n * h->es, h->m.nx * h->rs,
+                    h->phi[h->cur], h->m.px * h->rs, h->m.nx * h->rs, size_t(h->m.ny) * h->m.nz,
+                    cudaMemcpyDeviceToHost, h->stream));
     return check_device_error(h);
   }
   const unsigned fm = mask & 0x7Fu;
@@ -459,11 +468,11 @@ int lbpf_write_state(lbpf_t* h, const void* host_src, size_t bytes) {
   const char* src = static_cast<const char*>(host_src);
   h->cur = 0;
   const size_t rows = size_t(hd.q) * h->m.ny * h->m.nz;
-  CK(h, cudaMemcpy2DAsync(h->pops[0], h->m.px * h->es, src + sizeof(hd), h->m.nx * h->es,
-                          h->m.nx * h->es, rows, cudaMemcpyHostToDevice, h->stream));
-  CK(h, cudaMemcpy2DAsync(h->phi[0], h->m.px * h->rs, src + sizeof(hd) + size_t(hd.q) * n * h->es,
-                          h->m.nx * h->rs, h->m.nx * h->rs, size_t(h->m.ny) * h->m.nz,
-                          cudaMemcpyHostToDevice, h->stream));
+  CK(h, copy_rows(h->pops[0], h->m.px * h->es, src + sizeof(hd), h->m.nx * h->es,
+                  h->m.nx * h->es, rows, cudaMemcpyHostToDevice, h->stream));
+  CK(h, copy_rows(h->phi[0], h->m.px * h->rs, src + sizeof(hd) + size_t(hd.q) * n * h->es,
+                  h->m.nx * h->rs, h->m.nx * h->rs, size_t(h->m.ny) * h->m.nz,
+                  cudaMemcpyHostToDevice, h->stream));
   h->step = hd.step;
   if (h->m.ref_g != hd.ref_g) drop_graph(h);
   h->m.ref_g = hd.ref_g;
