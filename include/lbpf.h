@@ -259,9 +259,14 @@ typedef struct {
   uint64_t seed;      /* weight initialisation (He uniform, SplitMix64) */
 } lbpf_unet_cfg;
 
+/* Allocates the network's weights, optimiser state and activations on the
+ * current device (owned by the handle until lbpf_unet_destroy) and
+ * initialises the weights from cfg->seed.  stream: the CUDA stream its work
+ * is queued on (NULL = legacy default).  LBPF_EINVAL for an unsupported
+ * configuration (reason on stderr), LBPF_ENOMEM if an allocation fails. */
 int lbpf_unet_create(const lbpf_unet_cfg* cfg, void* stream, lbpf_unet_t** out);
-/* x: device FP32 [batch][height][width][in_ch]; y: device FP32 [..][out_ch].
- * Asynchronous on the network's stream. */
+/* x: device FP32 [batch][height][width][in_ch]; y: device FP32 [..][out_ch];
+ * both caller-owned, not overlapping.  Asynchronous on the network's stream. */
 int lbpf_unet_forward(lbpf_unet_t* n, const float* x, float* y);
 /* Loss (mean squared error against device FP32 targets t, same layout as y)
  * and the gradients of every parameter, without updating them; the loss is
@@ -280,6 +285,7 @@ int lbpf_unet_train_step(lbpf_unet_t* n, const float* x, const float* t, float l
  * convolution has Cin = 16 (inputs zero-padded).  which: 0 weights,
  * 1 gradients; set = 1 writes weights.  Synchronising. */
 size_t lbpf_unet_param_count(const lbpf_unet_t* n);
+int lbpf_unet_params(lbpf_unet_t* n, int which, float* host, size_t count, int set);
 /* Select the convolution kernels: 1 (default) the tcgen05 / TMEM / TMA
  * kernel wherever the layer's shape allows it, 0 the warp-level mma.sync
  * kernel everywhere.  Takes effect at the next pass. */
@@ -288,7 +294,6 @@ int lbpf_unet_set_tensor_path(lbpf_unet_t* n, int use_tcgen05);
  * tensor-core kernel gave up waiting on one of its barriers since creation
  * (lbpf_unet_grad and lbpf_surrogate_advance check the same). */
 int lbpf_unet_status(lbpf_unet_t* n);
-int lbpf_unet_params(lbpf_unet_t* n, int which, float* host, size_t count, int set);
 size_t lbpf_unet_device_bytes(const lbpf_unet_t* n);
 const char* lbpf_unet_last_error(const lbpf_unet_t* n);
 void lbpf_unet_destroy(lbpf_unet_t* n);
@@ -349,7 +354,14 @@ int lbpf_surrogate_sample(lbpf_t* h, const lbpf_surrogate_cfg* cfg, float* x);
  * queued on `stream`. */
 int lbpf_surrogate_target(const lbpf_surrogate_cfg* cfg, const float* x0, const float* x1,
                           int64_t npix, float* t, void* stream);
-/* Advance `blocks` blocks (synchronising once per block); rep may be NULL. */
+/* Advance `blocks` blocks (synchronising once per block); rep may be NULL.
+ * The network's kernels run on the simulation's stream during the call.  The
+ * first call for a network allocates its propagator scratch (device memory
+ * and a small pinned host buffer, owned by the network) and captures the
+ * prediction phase as a CUDA graph per state buffer, recaptured when the
+ * simulation, its stream or cfg change: do not call it inside a stream
+ * capture of your own.  LBPF_ETIMEDOUT if a tensor-core kernel gave up
+ * waiting; LBPF_EINVAL for a mismatched network or cfg. */
 int lbpf_surrogate_advance(lbpf_t* h, lbpf_unet_t* net, const lbpf_surrogate_cfg* cfg,
                            int blocks, lbpf_surrogate_report* rep);
 
