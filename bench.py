@@ -134,6 +134,10 @@ def workload(name):
     q = (9 if w["dim"] == 2 else 19) * w["flow"] + 2 * (9 if w["dim"] == 2 else 7)
     ring = 8 if w["storage"] == "fp64" else 4
     w["bytes_per_lup"] = 2 * q * ELEM[w["storage"]] + 2 * ring
+    if w["dim"] == 2 and ELEM[w["storage"]] == 2:
+        # the per-node g reference of 16-bit 2D storage (FP16): the node's own
+        # read, its neighbours' encoding reference read, the new one written
+        w["bytes_per_lup"] += 3 * 2
     w["nodes"] = w["nx"] * w["ny"] * w["nz"]
     if w.get("batch"):
         params, seeds = sweep_members(w["batch"], w["sweep_seed"], *w.get("sides", (256, 768)))

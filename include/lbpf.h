@@ -69,6 +69,12 @@ enum {
   LBPF_FP16_SHIFTED = 2, /* binary16 deviation from the lattice weight times a reference moment */
   LBPF_BF16_SHIFTED = 3  /* bfloat16, same shift */
 };
+/* With 16-bit storage in 2D the reference moment of g is per node: each node
+ * keeps its U of an earlier step (FP16, two planes that alternate with the
+ * population buffers), and the g pushed to a node is stored as its deviation
+ * from w_a times that node's reference.  The rounding of the stored
+ * deviations then no longer accumulates into a drift of the growth rate over
+ * long runs.  f, h and the 3D g keep one global reference. */
 
 /* Field selection bits of lbpf_read_fields. */
 enum {
@@ -174,7 +180,10 @@ int lbpf_read_fields(lbpf_t* h, unsigned field_mask, void* host_dst, size_t byte
  * (1,0,1) (-1,0,-1) (1,0,-1) (-1,0,1) (0,1,1) (0,-1,-1) (0,1,-1) (0,-1,1);
  * D3Q7 the first seven of those), each stored as its deviation
  * d_a = p_a - w_a M_ref with M_ref = 1 for f, U_ref for g and -1 for h; then
- * phi(t-1) + 1 in FP64 for LBPF_FP64 storage and FP32 otherwise. */
+ * phi(t-1) + 1 in FP64 for LBPF_FP64 storage and FP32 otherwise; then, for
+ * 2D with 16-bit storage only, two FP16 planes of nx*ny values: the per-node
+ * g reference of the stored populations (their M_ref of g instead of U_ref),
+ * and the one the next step encodes against. */
 size_t lbpf_state_bytes(const lbpf_t* h);
 
 /* Restore a state written by lbpf_read_fields(LBPF_FIELD_STATE) of a handle

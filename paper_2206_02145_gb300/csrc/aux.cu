@@ -25,7 +25,9 @@ __device__ __forceinline__ unsigned long long splitmix64(unsigned long long z) {
 
 // Equilibrium populations of (rho, u*, U, phi) in FP64 (Eq. 9 at second
 // order, Eq. 16, Eq. 21 with N = 0), stored as deviations from w_a M_ref
-// (M_ref = 1, U_ref, -1) in the population type.
+// (M_ref = 1, U_ref, -1) in the population type; with a per-node g reference
+// (2D, 16-bit storage) g relative to w_a U_n, U_n the node's U rounded to the
+// FP16 of the reference planes, and both planes of the node set to U_n.
 template <typename T>
 __device__ void store_equilibrium(const Model& m, T* pops, long long j, double phi, double U,
                                   double rho, double ux, double uy, double uz) {
@@ -34,6 +36,8 @@ __device__ void store_equilibrium(const Model& m, T* pops, long long j, double p
   const double mask = m.flow ? 0.5 * (1.0 - ph) : 0.0;
   const double us[3] = {mask * ux, mask * uy, mask * uz};
   const double uu = us[0] * us[0] + us[1] * us[1] + us[2] * us[2];
+  const __half Rh = __float2half_rn(float(U));
+  const double Rg = m.rel_g ? double(__half2float(Rh)) : m.ref_g;
   T* pf = pops;
   T* pg = pops + (long long)m.qf * P;
   T* ph_ = pops + (long long)(m.qf + m.qs) * P;
@@ -44,9 +48,10 @@ __device__ void store_equilibrium(const Model& m, T* pops, long long j, double p
       if (m.flow)
         Pop<T>::st(pf + a * P + j,
                    w * ((rho - m.ref_f) + rho * (3.0 * cu + 4.5 * cu * cu - 1.5 * uu)));
-      Pop<T>::st(pg + a * P + j, w * ((U - m.ref_g) + U * 3.0 * cu));
+      Pop<T>::st(pg + a * P + j, w * ((U - Rg) + U * 3.0 * cu));
       Pop<T>::st(ph_ + a * P + j, w * (phi - m.ref_h));
     }
+    if (m.rel_g) m.uring[j] = m.uring[P + j] = Rh;
   } else {
     if (m.flow)
       for (int a = 0; a < 19; ++a) {
@@ -75,6 +80,8 @@ __device__ void store_equilibrium_r(const Model& m, T* pops, long long j, R phi,
   const R mask = m.flow ? R(0.5) * (R(1) - ph) : R(0);
   const R us0 = mask * ux, us1 = mask * uy;
   const R uu = us0 * us0 + us1 * us1;
+  const __half Rh = __float2half_rn(float(U));
+  const R Rg = m.rel_g ? R(__half2float(Rh)) : c.ref_g;
   T* pf = pops;
   T* pg = pops + (long long)m.qf * P;
   T* ph_ = pops + (long long)(m.qf + m.qs) * P;
@@ -85,9 +92,10 @@ __device__ void store_equilibrium_r(const Model& m, T* pops, long long j, R phi,
     if (m.flow)
       Pop<T>::st(pf + a * P + j,
                  w * ((rho - c.ref_f) + rho * (R(3) * cu + R(4.5) * cu * cu - R(1.5) * uu)));
-    Pop<T>::st(pg + a * P + j, w * ((U - c.ref_g) + U * R(3) * cu));
+    Pop<T>::st(pg + a * P + j, w * ((U - Rg) + U * R(3) * cu));
     Pop<T>::st(ph_ + a * P + j, w * (phi - c.ref_h));
   }
+  if (m.rel_g) m.uring[j] = m.uring[P + j] = Rh;
 }
 
 template <typename T, typename R>
@@ -130,7 +138,7 @@ __global__ void init_fields_kernel(const Model m, const double* phi, const doubl
 // of the step (FP32, or FP64 for FP64 storage).
 template <typename T, typename R>
 __device__ void node_moments(const Model& m, const T* pops, long long j, R& phi, R& U, R& rho,
-                             R u[3]) {
+                             R u[3], const __half* uref = nullptr) {
   const long long P = m.plane;
   const T* pf = pops;
   const T* pg = pops + (long long)m.qf * P;
@@ -167,7 +175,7 @@ __device__ void node_moments(const Model& m, const T* pops, long long j, R& phi,
   }
   const Coef<R>& c = coef<R>(m);
   phi = c.ref_h + dphi;
-  U = c.ref_g + dU;
+  U = (uref ? R(__half2float(uref[j])) : c.ref_g) + dU;  // per-node g reference where it is stored so
   rho = c.ref_f + drho;
   const R ph = phi < R(-1) ? R(-1) : (phi > R(1) ? R(1) : phi);
   const R K = m.flow ? c.kdrag * (R(1) + ph) * (R(1) + ph) * (R(1) - ph) : R(0);
@@ -176,8 +184,8 @@ __device__ void node_moments(const Model& m, const T* pops, long long j, R& phi,
 }
 
 template <typename T, typename R, typename O>
-__global__ void fields_kernel(const Model m, const T* pops, const R* phi_prev, unsigned mask,
-                              O* out) {
+__global__ void fields_kernel(const Model m, const T* pops, const R* phi_prev,
+                              const __half* uref, unsigned mask, O* out) {
   const long long n = (long long)m.nx * m.ny * m.nz;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x) {
@@ -185,7 +193,7 @@ __global__ void fields_kernel(const Model m, const T* pops, const R* phi_prev, u
     node_xyz(m, i, x, y, z);
     const long long j = pitched(m, x, y, z);
     R phi, U, rho, u[3];
-    node_moments<T, R>(m, pops, j, phi, U, rho, u);
+    node_moments<T, R>(m, pops, j, phi, U, rho, u, uref);
     // phi(t-1) = -1 + ring, formed in the output precision
     const O vals[7] = {O(phi), O(U), O(rho), O(u[0]), O(u[1]), O(u[2]),
                        O(m.ref_h) + O(phi_prev[j])};
@@ -201,7 +209,8 @@ constexpr int kDiagSlots = 5;  // sum(U + phi_prev), sum(rho), solid, max|u|, no
 
 template <typename T, typename R>
 __global__ void __launch_bounds__(kDiagThreads)
-    diag_partial_kernel(const Model m, const T* pops, const R* phi_prev, double* partials) {
+    diag_partial_kernel(const Model m, const T* pops, const R* phi_prev, const __half* uref,
+                        double* partials) {
   const long long n = (long long)m.nx * m.ny * m.nz;
   double acc[kDiagSlots] = {0.0, 0.0, 0.0, 0.0, 0.0};
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
@@ -210,7 +219,7 @@ __global__ void __launch_bounds__(kDiagThreads)
     node_xyz(m, i, x, y, z);
     const long long j = pitched(m, x, y, z);
     R phi, U, rho, u[3];
-    node_moments<T, R>(m, pops, j, phi, U, rho, u);
+    node_moments<T, R>(m, pops, j, phi, U, rho, u, uref);
     // FP64 accumulation of per-node values formed in the step's arithmetic
     const double pp = m.ref_h + double(phi_prev[j]);
     const R ph = phi < R(-1) ? R(-1) : (phi > R(1) ? R(1) : phi);
@@ -298,7 +307,8 @@ __global__ void crossing_kernel(const Model m, const T* pops, int icx, int icy, 
 // (f - shift) / scale, NHWC with H = ny and W = nx; and the same four fields
 // plus rho unnormalised as planes of n values (skipped if F is null).
 template <typename T, typename R>
-__global__ void surrogate_gather_kernel(const Model m, const T* pops, const Vec4 shift,
+__global__ void surrogate_gather_kernel(const Model m, const T* pops, const __half* uref,
+                                        const Vec4 shift,
                                         const Vec4 inv_scale, float* x, float* F) {
   const long long n = (long long)m.nx * m.ny;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
@@ -306,7 +316,7 @@ __global__ void surrogate_gather_kernel(const Model m, const T* pops, const Vec4
     int xx, yy, zz;
     node_xyz(m, i, xx, yy, zz);
     R phi, U, rho, u[3];
-    node_moments<T, R>(m, pops, pitched(m, xx, yy, 0), phi, U, rho, u);
+    node_moments<T, R>(m, pops, pitched(m, xx, yy, 0), phi, U, rho, u, uref);
     const float f[4] = {float(phi), float(U), float(u[0]), float(u[1])};
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
@@ -356,33 +366,35 @@ cudaError_t init_fields_t(const Model& m, const double* phi, const double* U, co
   return cudaGetLastError();
 }
 template <typename T, typename R>
-cudaError_t fields_t(const Model& m, const void* pops, const void* pp, unsigned mask, int fp64,
-                     void* out, cudaStream_t s) {
+cudaError_t fields_t(const Model& m, const void* pops, const void* pp, const __half* uref,
+                     unsigned mask, int fp64, void* out, cudaStream_t s) {
   const long long n = (long long)m.nx * m.ny * m.nz;
   if (fp64)
     fields_kernel<T, R, double><<<grid_for(n), 256, 0, s>>>(
-        m, static_cast<const T*>(pops), static_cast<const R*>(pp), mask, static_cast<double*>(out));
+        m, static_cast<const T*>(pops), static_cast<const R*>(pp), uref, mask,
+        static_cast<double*>(out));
   else
     fields_kernel<T, R, float><<<grid_for(n), 256, 0, s>>>(
-        m, static_cast<const T*>(pops), static_cast<const R*>(pp), mask, static_cast<float*>(out));
+        m, static_cast<const T*>(pops), static_cast<const R*>(pp), uref, mask,
+        static_cast<float*>(out));
   return cudaGetLastError();
 }
 template <typename T, typename R>
-cudaError_t diag_t(const Model& m, const void* pops, const void* pp, double* partials,
-                   double* out, int icx, int icy, int icz, cudaStream_t s) {
+cudaError_t diag_t(const Model& m, const void* pops, const void* pp, const __half* uref,
+                   double* partials, double* out, int icx, int icy, int icz, cudaStream_t s) {
   diag_partial_kernel<T, R><<<kDiagBlocks, kDiagThreads, 0, s>>>(
-      m, static_cast<const T*>(pops), static_cast<const R*>(pp), partials);
+      m, static_cast<const T*>(pops), static_cast<const R*>(pp), uref, partials);
   diag_final_kernel<<<1, kDiagThreads, 0, s>>>(partials, kDiagBlocks, out);
   crossing_kernel<T, R><<<1, 32, 0, s>>>(m, static_cast<const T*>(pops), icx, icy, icz, out);
   return cudaGetLastError();
 }
 
 template <typename T, typename R>
-cudaError_t gather_t(const Model& m, const void* pops, const Vec4& shift, const Vec4& inv_scale,
-                     float* x, float* F, cudaStream_t s) {
+cudaError_t gather_t(const Model& m, const void* pops, const __half* uref, const Vec4& shift,
+                     const Vec4& inv_scale, float* x, float* F, cudaStream_t s) {
   const long long n = (long long)m.nx * m.ny;
-  surrogate_gather_kernel<T, R><<<grid_for(n), 256, 0, s>>>(m, static_cast<const T*>(pops), shift,
-                                                            inv_scale, x, F);
+  surrogate_gather_kernel<T, R><<<grid_for(n), 256, 0, s>>>(m, static_cast<const T*>(pops), uref,
+                                                            shift, inv_scale, x, F);
   return cudaGetLastError();
 }
 template <typename T, typename R>
@@ -413,16 +425,18 @@ cudaError_t launch_init_fields(const Model& m, const double* phi, const double* 
                                const double* uz, void* pops, void* phi_prev, cudaStream_t s) {
   LBPF_DISPATCH(init_fields_t, m, phi, U, rho, ux, uy, uz, pops, phi_prev, s)
 }
-cudaError_t launch_fields(const Model& m, const void* pops, const void* phi_prev, unsigned mask,
-                          int fp64, void* out, cudaStream_t s) {
-  LBPF_DISPATCH(fields_t, m, pops, phi_prev, mask, fp64, out, s)
+cudaError_t launch_fields(const Model& m, const void* pops, const void* phi_prev, int c,
+                          unsigned mask, int fp64, void* out, cudaStream_t s) {
+  const __half* uref = uref_plane(m, c);
+  LBPF_DISPATCH(fields_t, m, pops, phi_prev, uref, mask, fp64, out, s)
 }
-cudaError_t launch_surrogate_gather(const Model& m, const void* pops, const Vec4& shift,
+cudaError_t launch_surrogate_gather(const Model& m, const void* pops, int c, const Vec4& shift,
                                     const Vec4& scale, float* x, float* F, cudaStream_t s) {
   if (m.dim != 2) return cudaErrorInvalidValue;
   Vec4 inv;
-  for (int c = 0; c < 4; ++c) inv.v[c] = 1.0f / scale.v[c];
-  LBPF_DISPATCH(gather_t, m, pops, shift, inv, x, F, s)
+  for (int k = 0; k < 4; ++k) inv.v[k] = 1.0f / scale.v[k];
+  const __half* uref = uref_plane(m, c);
+  LBPF_DISPATCH(gather_t, m, pops, uref, shift, inv, x, F, s)
 }
 cudaError_t launch_surrogate_commit(const Model& m, const float* F1, const float* rho, void* pops,
                                     void* phi_prev, cudaStream_t s) {
@@ -430,9 +444,10 @@ cudaError_t launch_surrogate_commit(const Model& m, const float* F1, const float
   LBPF_DISPATCH(commit_t, m, F1, rho, pops, phi_prev, s)
 }
 size_t diag_partials_bytes(const Model&) { return sizeof(double) * kDiagBlocks * kDiagSlots; }
-cudaError_t launch_diag(const Model& m, const void* pops, const void* phi_prev, double* partials,
-                        double* out, int icx, int icy, int icz, cudaStream_t s) {
-  LBPF_DISPATCH(diag_t, m, pops, phi_prev, partials, out, icx, icy, icz, s)
+cudaError_t launch_diag(const Model& m, const void* pops, const void* phi_prev, int c,
+                        double* partials, double* out, int icx, int icy, int icz, cudaStream_t s) {
+  const __half* uref = uref_plane(m, c);
+  LBPF_DISPATCH(diag_t, m, pops, phi_prev, uref, partials, out, icx, icy, icz, s)
 }
 
 }  // namespace lbk

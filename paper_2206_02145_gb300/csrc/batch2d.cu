@@ -37,8 +37,8 @@ __global__ void __launch_bounds__(TX* TY, 3)
   auto issue = [&](int tile, int s) {
     const BatchDesc& d = descs[tile_inst[tile]];
     const int lt = tile - d.tile0;
-    issue_tile_2d<T, FLOW, TX, TY>(&d.fg, &d.h, &d.ring, &full[s], smem + s * L::STAGE,
-                                   (lt % d.ntx) * TX, (lt / d.ntx) * TY);
+    issue_tile_2d<T, FLOW, TX, TY>(&d.fg, &d.h, &d.ring, &d.uown, &d.uhal, d.c, &full[s],
+                                   smem + s * L::STAGE, (lt % d.ntx) * TX, (lt / d.ntx) * TY);
   };
 
   if (tid == 0) {
@@ -80,7 +80,7 @@ __global__ void __launch_bounds__(TX* TY, 3)
     }
     const int lt = tile - d.tile0;
     tile_2d<T, FLOW, TX, TY>(sm, static_cast<const T*>(d.src), static_cast<T*>(d.dst),
-                             d.ring_cur, d.err, (lt % d.ntx) * TX, (lt / d.ntx) * TY,
+                             d.ring_cur, d.err, (lt % d.ntx) * TX, (lt / d.ntx) * TY, d.c,
                              smem + s * L::STAGE, &sh_phi[0][0]);
     __syncthreads();  // stage s, sh_phi and sm are free again
     if (tid == 0 && tile + S * G < total_tiles) {
@@ -190,7 +190,20 @@ cudaError_t batch_plan_build(const BatchMember* members, int count, int storage,
           !encode_tiled(&d.ring, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, members[i].rings[c], dims2,
                         str2, box_r))
         return cudaErrorInvalidValue;
+      if (es == 2) {  // the two per-node U planes of 16-bit storage (g reference)
+        const uint64_t dimsu[3] = {uint64_t(m.nx), uint64_t(m.ny), 2};
+        const uint64_t stru[2] = {uint64_t(m.px) * 2, uint64_t(m.plane) * 2};
+        const uint32_t box_uo[3] = {uint32_t(tx), uint32_t(ty), 1};
+        const uint32_t box_uh[3] = {uint32_t(tx + 16), uint32_t(ty + 2), 1};
+        if (!m.rel_g || !m.uring ||
+            !encode_tiled(&d.uown, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 3, m.uring, dimsu, stru,
+                          box_uo) ||
+            !encode_tiled(&d.uhal, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 3, m.uring, dimsu, stru,
+                          box_uh))
+          return cudaErrorInvalidValue;
+      }
       d.m = m;
+      d.c = c;
       d.src = members[i].pops[c];
       d.dst = members[i].pops[c ^ 1];
       d.ring_cur = static_cast<float*>(members[i].rings[c ^ 1]);

@@ -134,6 +134,10 @@ Model derive(const lbpf_params& p) {
   m.ref_f = 1.0;
   m.ref_g = 0.0;
   m.ref_h = -1.0;
+  // 16-bit 2D storage keeps g relative to a per-node U (two FP32 planes,
+  // allocated by lbpf_create)
+  m.rel_g = (p.dim == 2 && (p.storage == LBPF_FP16_SHIFTED || p.storage == LBPF_BF16_SHIFTED)) ? 1 : 0;
+  m.uring = nullptr;
   lbk::finalize(m);
   return m;
 }
@@ -213,10 +217,13 @@ int ensure_fields_buffer(lbpf* h, size_t bytes) {
   return LBPF_OK;
 }
 
+// plane c of the per-node g reference (16-bit 2D storage)
+__half* uref_dev(lbpf* h, int c) { return h->m.uring + size_t(c) * size_t(h->m.plane); }
+
 void store_I0(lbpf* h) {
   // solute total at init, kept on the device for the drift of lbpf_diagnostics
-  lbk::launch_diag(h->m, h->pops[h->cur], h->phi[h->cur], h->d_partials, h->d_diag, h->icx,
-                    h->icy, h->icz, h->stream);
+  lbk::launch_diag(h->m, h->pops[h->cur], h->phi[h->cur], h->cur, h->d_partials, h->d_diag,
+                    h->icx, h->icy, h->icz, h->stream);
   cudaMemcpyAsync(h->d_diag + 16, h->d_diag, sizeof(double), cudaMemcpyDeviceToDevice, h->stream);
 }
 
@@ -277,13 +284,15 @@ int lbpf_create(const lbpf_params* p, void* stream, lbpf_t** out) {
   if (e == cudaSuccess) e = cudaMalloc(&h->d_err, 256);
   if (e == cudaSuccess) e = cudaMalloc(&h->d_partials, lbk::diag_partials_bytes(h->m));
   if (e == cudaSuccess) e = cudaMalloc(&h->d_diag, 32 * sizeof(double));
+  const size_t uring_bytes = h->m.rel_g ? 2 * size_t(h->m.plane) * sizeof(__half) : 0;
+  if (e == cudaSuccess && uring_bytes) e = cudaMalloc(&h->m.uring, uring_bytes);
   if (e != cudaSuccess) {
     fprintf(stderr, "lbpf_create: %s\n", cudaGetErrorString(e));
     lbpf_destroy(h);
     return LBPF_ENOMEM;
   }
-  h->dev_bytes = 2 * pop_bytes + 2 * ring_bytes + 256 + lbk::diag_partials_bytes(h->m) +
-                 32 * sizeof(double);
+  h->dev_bytes = 2 * pop_bytes + 2 * ring_bytes + uring_bytes + 256 +
+                 lbk::diag_partials_bytes(h->m) + 32 * sizeof(double);
   e = cudaMemsetAsync(h->d_err, 0, 256, h->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(h->d_diag, 0, 32 * sizeof(double), h->stream);
   if (e != cudaSuccess) {
@@ -407,7 +416,7 @@ size_t lbpf_state_bytes(const lbpf_t* h) {
   if (!h) return 0;
   const size_t n = size_t(nodes(h->p));
   const size_t q = size_t(h->m.qf + 2 * h->m.qs);
-  return sizeof(StateHeader) + q * n * h->es + n * h->rs;
+  return sizeof(StateHeader) + q * n * h->es + n * h->rs + (h->m.rel_g ? 2 * n * 2 : 0);
 }
 
 int lbpf_read_fields(lbpf_t* h, unsigned mask, void* host_dst, size_t bytes, int as_fp64) {
@@ -439,6 +448,12 @@ int lbpf_read_fields(lbpf_t* h, unsigned mask, void* host_dst, size_t bytes, int
     CK(h, copy_rows(dst + sizeof(hd) + size_t(hd.q) * n * h->es, h->m.nx * h->rs,
                     h->phi[h->cur], h->m.px * h->rs, h->m.nx * h->rs, size_t(h->m.ny) * h->m.nz,
                     cudaMemcpyDeviceToHost, h->stream));
+    if (h->m.rel_g) {  // g references: the current buffer's, then the other one
+      char* ud = dst + sizeof(hd) + size_t(hd.q) * n * h->es + n * h->rs;
+      for (int k = 0; k < 2; ++k)
+        CK(h, copy_rows(ud + k * n * 2, h->m.nx * 2, uref_dev(h, h->cur ^ k), h->m.px * 2,
+                        h->m.nx * 2, h->m.ny, cudaMemcpyDeviceToHost, h->stream));
+    }
     return check_device_error(h);
   }
   const unsigned fm = mask & 0x7Fu;
@@ -447,8 +462,8 @@ int lbpf_read_fields(lbpf_t* h, unsigned mask, void* host_dst, size_t bytes, int
   const size_t es = as_fp64 ? 8 : 4;
   if (bytes != size_t(nf) * n * es) return fail(h, LBPF_EINVAL, "field buffer size mismatch");
   if ((rc = ensure_fields_buffer(h, bytes))) return rc;
-  CK(h, lbk::launch_fields(h->m, h->pops[h->cur], h->phi[h->cur], fm, as_fp64, h->d_fields,
-                            h->stream));
+  CK(h, lbk::launch_fields(h->m, h->pops[h->cur], h->phi[h->cur], h->cur, fm, as_fp64,
+                            h->d_fields, h->stream));
   CK(h, cudaMemcpyAsync(host_dst, h->d_fields, bytes, cudaMemcpyDeviceToHost, h->stream));
   return check_device_error(h);
 }
@@ -473,6 +488,12 @@ int lbpf_write_state(lbpf_t* h, const void* host_src, size_t bytes) {
   CK(h, copy_rows(h->phi[0], h->m.px * h->rs, src + sizeof(hd) + size_t(hd.q) * n * h->es,
                   h->m.nx * h->rs, h->m.nx * h->rs, size_t(h->m.ny) * h->m.nz,
                   cudaMemcpyHostToDevice, h->stream));
+  if (h->m.rel_g) {
+    const char* us = src + sizeof(hd) + size_t(hd.q) * n * h->es + n * h->rs;
+    for (int k = 0; k < 2; ++k)
+      CK(h, copy_rows(uref_dev(h, k), h->m.px * 2, us + k * n * 2, h->m.nx * 2, h->m.nx * 2,
+                      h->m.ny, cudaMemcpyHostToDevice, h->stream));
+  }
   h->step = hd.step;
   if (h->m.ref_g != hd.ref_g) drop_graph(h);
   h->m.ref_g = hd.ref_g;
@@ -491,8 +512,8 @@ int lbpf_diagnostics(lbpf_t* h, lbpf_diag* out) {
   if (rc) return rc;
   if (!out) return fail(h, LBPF_EINVAL, "null output");
   if (!h->initialized) return fail(h, LBPF_ESTATE, "diagnostics before init");
-  CK(h, lbk::launch_diag(h->m, h->pops[h->cur], h->phi[h->cur], h->d_partials, h->d_diag, h->icx,
-                          h->icy, h->icz, h->stream));
+  CK(h, lbk::launch_diag(h->m, h->pops[h->cur], h->phi[h->cur], h->cur, h->d_partials,
+                          h->d_diag, h->icx, h->icy, h->icz, h->stream));
   double v[17];
   CK(h, cudaMemcpyAsync(v, h->d_diag, sizeof(v), cudaMemcpyDeviceToHost, h->stream));
   if ((rc = check_device_error(h))) return rc;
@@ -530,6 +551,7 @@ void lbpf_destroy(lbpf_t* h) {
     if (h->pops[i]) cudaFree(h->pops[i]);
     if (h->phi[i]) cudaFree(h->phi[i]);
   }
+  if (h->m.uring) cudaFree(h->m.uring);
   if (h->d_err) cudaFree(h->d_err);
   if (h->d_partials) cudaFree(h->d_partials);
   if (h->d_diag) cudaFree(h->d_diag);

@@ -53,7 +53,22 @@ struct Model {
   double ref_f, ref_g, ref_h;  // reference moments of the stored deviations (1, U_ref, -1)
   Coef<float> cf;   // the constants above in FP32 ...
   Coef<double> cd;  // ... and in FP64 (filled by finalize())
+  // 2D with 16-bit storage: g is stored relative to a per-node U instead of
+  // the global U_ref.  uring: two FP16 planes of `plane` values; for the
+  // populations of buffer c, plane c holds each node's reference, while the
+  // step that reads them writes the node's new U into plane c and encodes the
+  // populations it pushes against the destination's value in plane c ^ 1.
+  // The reference only has to be the same number at encoding and decoding,
+  // so FP16 loses nothing.
+  int rel_g;
+  __half* uring;
 };
+
+// The stored-g reference of the populations in buffer c (null when g is
+// stored relative to the global U_ref).
+inline const __half* uref_plane(const Model& m, int c) {
+  return m.rel_g ? m.uring + size_t(c) * size_t(m.plane) : nullptr;
+}
 
 // Fill m.cf and m.cd from the FP64 fields; call after every change of those.
 inline void finalize(Model& m) {
@@ -102,6 +117,7 @@ struct PopPtrs {
 // parity of the source buffer) and the launch shape of the persistent kernel.
 struct StepMaps {
   CUtensorMap fg[2], h[2], ring[2];
+  CUtensorMap uown, uhal;  // 2D 16-bit: the U planes (tile box, halo box; plane = coordinate)
   int ctas = 0, smem = 0, ready = 0;
 };
 
@@ -126,13 +142,13 @@ cudaError_t launch_step3d(const Model& m, const StepMaps& maps, int c, const voi
 // One instance of a batch for one buffer parity: its TMA descriptors (64-byte
 // aligned, read by the TMA from global memory), model and buffers.
 struct alignas(128) BatchDesc {
-  CUtensorMap fg, h, ring;
+  CUtensorMap fg, h, ring, uown, uhal;
   Model m;
   const void* src;
   void* dst;
   float* ring_cur;
   unsigned* err;
-  int ntx, tile0, ntiles, pad;
+  int ntx, tile0, ntiles, c;
 };
 struct BatchMember {  // what the batch needs of one instance
   Model m;
@@ -168,7 +184,7 @@ cudaError_t launch_init_fields(const Model& m, const double* phi, const double* 
 // Moments of the state into a packed device buffer: the fields selected by
 // `mask` (LBPF_FIELD_* bits 0..6) one after another, N values each, as
 // double (fp64) or float.
-cudaError_t launch_fields(const Model& m, const void* pops, const void* phi_prev,
+cudaError_t launch_fields(const Model& m, const void* pops, const void* phi_prev, int c,
                           unsigned mask, int fp64, void* out, cudaStream_t s);
 
 // Learned block propagator (2D only).  gather: network input x[i][c] =
@@ -179,7 +195,7 @@ cudaError_t launch_fields(const Model& m, const void* pops, const void* phi_prev
 struct Vec4 {
   float v[4];
 };
-cudaError_t launch_surrogate_gather(const Model& m, const void* pops, const Vec4& shift,
+cudaError_t launch_surrogate_gather(const Model& m, const void* pops, int c, const Vec4& shift,
                                     const Vec4& scale, float* x, float* F, cudaStream_t s);
 cudaError_t launch_surrogate_commit(const Model& m, const float* F1, const float* rho, void* pops,
                                     void* phi_prev, cudaStream_t s);
@@ -188,7 +204,7 @@ cudaError_t launch_surrogate_commit(const Model& m, const float* F1, const float
 // out[0..4] = sum(U + phi_prev), sum(rho), sum((1+phihat)/2), max|u|,
 // nonfinite count; out[5..10] = interface crossings from (icx, icy, icz).
 size_t diag_partials_bytes(const Model& m);
-cudaError_t launch_diag(const Model& m, const void* pops, const void* phi_prev, double* partials,
-                        double* out, int icx, int icy, int icz, cudaStream_t s);
+cudaError_t launch_diag(const Model& m, const void* pops, const void* phi_prev, int c,
+                        double* partials, double* out, int icx, int icy, int icz, cudaStream_t s);
 
 }  // namespace lbk

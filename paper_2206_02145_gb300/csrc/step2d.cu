@@ -101,11 +101,11 @@ __global__ void __launch_bounds__(TX* TY)
   if (x0 >= 1 && x0 + TX <= nx - 1 && y0 >= 1 && y0 + TY <= ny - 1)
     collide_push_2d<T, R, FLOW, true, SX>(m, x, y, tx + 1, ty + 1, f, g, h,
                                           sh_phi[ty + 1][tx + 1], dphi_prev, &sh_phi[0][0], hs,
-                                          static_cast<T*>(dp.p[0]), ring_cur, err);
+                                          NoUView{}, static_cast<T*>(dp.p[0]), ring_cur, err);
   else
     collide_push_2d<T, R, FLOW, false, SX>(m, x, y, tx + 1, ty + 1, f, g, h,
                                            sh_phi[ty + 1][tx + 1], dphi_prev, &sh_phi[0][0], hs,
-                                           static_cast<T*>(dp.p[0]), ring_cur, err);
+                                           NoUView{}, static_cast<T*>(dp.p[0]), ring_cur, err);
 }
 
 // ---- TMA-pipelined persistent kernel ------------------------------------------
@@ -125,10 +125,12 @@ template <typename T, bool FLOW, int TX, int TY, int S>
 __global__ void __launch_bounds__(TX* TY, LBPF_2D_MIN_CTAS)
     step2d_tma_kernel(const __grid_constant__ CUtensorMap tm_fg,
                       const __grid_constant__ CUtensorMap tm_h,
-                      const __grid_constant__ CUtensorMap tm_ring, const Model m,
+                      const __grid_constant__ CUtensorMap tm_ring,
+                      const __grid_constant__ CUtensorMap tm_uown,
+                      const __grid_constant__ CUtensorMap tm_uhal, const Model m,
                       const T* __restrict__ src, T* __restrict__ dst,
                       float* __restrict__ ring_cur, unsigned* __restrict__ err, int ntx,
-                      int ntiles) {
+                      int ntiles, int c) {
   using R = float;
   using L = Tiles2D<T, FLOW, TX, TY>;
   constexpr int SX = TX + 2, SY = TY + 2;
@@ -142,8 +144,8 @@ __global__ void __launch_bounds__(TX* TY, LBPF_2D_MIN_CTAS)
   const int first = blockIdx.x, G = gridDim.x;
 
   auto issue = [&](int tile, int s) {
-    issue_tile_2d<T, FLOW, TX, TY>(&tm_fg, &tm_h, &tm_ring, &full[s], smem + s * L::STAGE,
-                                   (tile % ntx) * TX, (tile / ntx) * TY);
+    issue_tile_2d<T, FLOW, TX, TY>(&tm_fg, &tm_h, &tm_ring, &tm_uown, &tm_uhal, c, &full[s],
+                                   smem + s * L::STAGE, (tile % ntx) * TX, (tile / ntx) * TY);
   };
 
   if (tid == 0) {
@@ -174,7 +176,7 @@ __global__ void __launch_bounds__(TX* TY, LBPF_2D_MIN_CTAS)
       return;
     }
     const int x0 = (tile % ntx) * TX, y0 = (tile / ntx) * TY;
-    tile_2d<T, FLOW, TX, TY>(m, src, dst, ring_cur, err, x0, y0, smem + s * L::STAGE,
+    tile_2d<T, FLOW, TX, TY>(m, src, dst, ring_cur, err, x0, y0, c, smem + s * L::STAGE,
                              &sh_phi[0][0]);
     __syncthreads();  // stage s and sh_phi are free again
     if (tid == 0 && tile + S * G < ntiles) {
@@ -205,6 +207,20 @@ cudaError_t prepare_t(const Model& m, void* const pops[2], void* const rings[2],
         !encode_tiled(&out->ring[b], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, rings[b], dims2, str2, box_r))
       return cudaErrorInvalidValue;
   }
+  if (L::REL) {
+    // the two U planes as one 3D tensor; the plane is the third coordinate
+    if (!m.uring) return cudaErrorInvalidValue;
+    const uint64_t dimsu[3] = {uint64_t(m.nx), uint64_t(m.ny), 2};
+    const uint64_t stru[2] = {uint64_t(m.px) * 2, uint64_t(m.plane) * 2};
+    const uint32_t box_uo[3] = {kTX, kTY, 1};
+    const uint32_t box_uh[3] = {uint32_t(L::BXU), kTY + 2, 1};
+    if (!encode_tiled(&out->uown, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 3, m.uring, dimsu, stru, box_uo) ||
+        !encode_tiled(&out->uhal, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 3, m.uring, dimsu, stru, box_uh))
+      return cudaErrorInvalidValue;
+  } else {
+    out->uown = out->ring[0];  // unused
+    out->uhal = out->ring[0];
+  }
   auto kern = step2d_tma_kernel<T, FLOW, kTX, kTY, kStages>;
   const int smem = kStages * L::STAGE + 128;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
@@ -229,8 +245,8 @@ cudaError_t launch_tma_t(const Model& m, const StepMaps& maps, int c, const void
   const int ntiles = ntx * nty;
   const int grid = ntiles < maps.ctas ? ntiles : maps.ctas;
   step2d_tma_kernel<T, FLOW, kTX, kTY, kStages><<<grid, kTX * kTY, maps.smem, s>>>(
-      maps.fg[c], maps.h[c], maps.ring[c], m, static_cast<const T*>(src), static_cast<T*>(dst),
-      static_cast<float*>(ring_cur), err, ntx, ntiles);
+      maps.fg[c], maps.h[c], maps.ring[c], maps.uown, maps.uhal, m, static_cast<const T*>(src),
+      static_cast<T*>(dst), static_cast<float*>(ring_cur), err, ntx, ntiles, c);
   return cudaGetLastError();
 }
 

@@ -21,17 +21,36 @@ struct TileView {
   }
 };
 
+// The per-node g reference around a node (2D, 16-bit storage): `own` the
+// reference of the node's own populations, at(ly, lx) the encoding reference
+// of the node at local (ly, lx) (halo box of row pitch ROW, the pointer
+// offset so that lx = 0 is the tile's left halo column), `out` the plane that
+// receives each node's new U.  With REL = false (FP32 and FP64 storage) g is
+// relative to the global U_ref and every member is unused.
+template <bool REL, int ROW>
+struct UView {
+  static constexpr bool kRel = REL;
+  const __half* hal;
+  __half* out;
+  float own;
+  __device__ __forceinline__ float at(int ly, int lx) const {
+    return REL ? __half2float(hal[ly * ROW + lx]) : 0.f;
+  }
+};
+using NoUView = UView<false, 1>;
+
 // dphi_prev: phi(t-1) + 1 of this node; ring_cur: where phi(t) + 1 goes.
 // phi_s: the tile's phi + 1 with halo ([ly][lx], row pitch PROW).
 // dst: the destination population buffer (array a at dst + a * plane).
 // INTERIOR: the caller guarantees 1 <= x <= nx - 2 and 1 <= y <= ny - 2 for
 // every node of the tile, so every destination is an ordinary node (no wrap,
 // wall or ghost) and the push needs no boundary logic.
-template <typename T, typename R, bool FLOW, bool INTERIOR, int PROW, typename HV>
+template <typename T, typename R, bool FLOW, bool INTERIOR, int PROW, typename HV,
+          typename UV>
 __device__ __forceinline__ void collide_push_2d(const Model& m, int x, int y, int lx, int ly,
                                                 const R (&f)[9], const R (&g)[9],
                                                 const R (&h)[9], R dphi, R dphi_prev,
-                                                const R* phi_s, const HV& hs,
+                                                const R* phi_s, const HV& hs, const UV& uh,
                                                 T* __restrict__ dst, R* __restrict__ ring_cur,
                                                 unsigned* __restrict__ err) {
   constexpr int QF = FLOW ? 9 : 0;
@@ -46,7 +65,10 @@ __device__ __forceinline__ void collide_push_2d(const Model& m, int x, int y, in
   R dU = R(0);
 #pragma unroll
   for (int a = 0; a < 9; ++a) dU += g[a];
-  const R U = c.ref_g + dU;
+  // g deviations are taken from w_a Rg; the collision (Eqs. 13-16) is linear
+  // in them, so any per-node Rg gives the same populations
+  const R Rg = UV::kRel ? R(uh.own) : c.ref_g;
+  const R U = Rg + dU;
   R drho = R(0), mx = R(0), my = R(0);
   if (FLOW) {
 #pragma unroll
@@ -72,7 +94,13 @@ __device__ __forceinline__ void collide_push_2d(const Model& m, int x, int y, in
   const R omega_U = rcp_r(R(0.5) + c.tauU_slope * mask);  // Eq. 18
   const R dphidt = dphi - dphi_prev;
   ring_cur[idx] = dphi;
+  if (UV::kRel) uh.out[idx] = __float2half_rn(float(U));
   if (!(finite_r(phi) && finite_r(U) && finite_r(rho))) atomicOr(err, 1u);
+  // a g deviation pushed to the node at local (dly, dlx), taken from its
+  // reference there instead of this node's
+  auto genc = [&](R v, R w, int dly, int dlx) -> R {
+    return UV::kRel ? fma_r(-w, R(uh.at(dly, dlx)) - Rg, v) : v;
+  };
 
   // ---- gradient, anisotropy, phase-field coefficients (Eqs. 3, 20, 21, 23) --
   const R* pc = phi_s + ly * PROW + lx;
@@ -130,7 +158,7 @@ __device__ __forceinline__ void collide_push_2d(const Model& m, int x, int y, in
       const int off = cy * px + cx;  // uniform
       const R hold = hs.at(a, ly + cy, lx + cx);  // h_a(s + c_a, t)
       if (FLOW) Pop<T>::st(pd + (a * P + off), fp);
-      Pop<T>::st(pd + ((QF + a) * P + off), gp);
+      Pop<T>::st(pd + ((QF + a) * P + off), genc(gp, w, ly + cy, lx + cx));
       Pop<T>::st(pd + ((QF + 9 + a) * P + off), fma_r(inv_a2, hp, mul_r(keep_old, hold)));  // Eq. 19
       continue;
     }
@@ -150,13 +178,13 @@ __device__ __forceinline__ void collide_push_2d(const Model& m, int x, int y, in
       // half-way bounce-back: comes back to this node reversed
       const int b = D2_OPP[a];
       if (FLOW) Pop<T>::st(LBPF_DF(b) + idx, fp);
-      Pop<T>::st(LBPF_DG(b) + idx, gp);
+      Pop<T>::st(LBPF_DG(b) + idx, genc(gp, w, ly, lx));
       Pop<T>::st(LBPF_DH(b) + idx, fma_r(inv_a2, hp, mul_r(keep_old, h[b])));
     } else if (!drop) {
       const int jd = yd * px + xd;
       const R hold = hs.at(a, ly + cy, lx + cx);  // h_a(s + c_a, t)
       if (FLOW) Pop<T>::st(LBPF_DF(a) + jd, fp);
-      Pop<T>::st(LBPF_DG(a) + jd, gp);
+      Pop<T>::st(LBPF_DG(a) + jd, genc(gp, w, ly + cy, lx + cx));
       Pop<T>::st(LBPF_DH(a) + jd, fma_r(inv_a2, hp, mul_r(keep_old, hold)));  // Eq. 19
     }
     if (bcx == BC_INOUT) {
@@ -173,7 +201,7 @@ __device__ __forceinline__ void collide_push_2d(const Model& m, int x, int y, in
           const int jo = yo * px + x;
           const R hold = hs.at(a, ly + cy, lx);
           if (FLOW) Pop<T>::st(LBPF_DF(a) + jo, fp);
-          Pop<T>::st(LBPF_DG(a) + jo, gp);
+          Pop<T>::st(LBPF_DG(a) + jo, genc(gp, w, ly + cy, lx));
           Pop<T>::st(LBPF_DH(a) + jo, fma_r(inv_a2, hp, mul_r(keep_old, hold)));
         }
       }
@@ -188,7 +216,7 @@ __device__ __forceinline__ void collide_push_2d(const Model& m, int x, int y, in
                        w * (R(3) * cui + R(4.5) * cui * cui - R(1.5) * uin * uin));
           const R gu = FLOW ? cui : R(0);
           const R Uin = c.U_in;
-          Pop<T>::st(LBPF_DG(a) + idx, w * ((Uin - c.ref_g) + Uin * R(3) * gu));
+          Pop<T>::st(LBPF_DG(a) + idx, genc(w * ((Uin - Rg) + Uin * R(3) * gu), w, ly, lx));
           Pop<T>::st(LBPF_DH(a) + idx, R(0));
         }
       }

@@ -17,23 +17,40 @@ struct Tiles2D {
   static constexpr int FG_BYTES = QFG * TY * TX * int(sizeof(T));
   static constexpr int H_BYTES = 9 * (TY + 2) * BXH * int(sizeof(T));
   static constexpr int RING_BYTES = TY * TX * 4;
+  // 16-bit storage: g relative to a per-node U (the own reference of the tile
+  // and a halo box of the encoding reference, FP16, starting 8 left of the
+  // tile so that the box starts on a 16-byte boundary)
+  static constexpr bool REL = sizeof(T) == 2;
+  static constexpr int HXU = 8, BXU = TX + 2 * HXU;
+  static constexpr int UOWN_BYTES = REL ? TY * TX * 2 : 0;
+  static constexpr int UHAL_BYTES = REL ? (TY + 2) * BXU * 2 : 0;
   static constexpr int al(int b) { return (b + 127) / 128 * 128; }
   static constexpr int OFF_H = al(FG_BYTES);
   static constexpr int OFF_RING = OFF_H + al(H_BYTES);
-  static constexpr int STAGE = OFF_RING + al(RING_BYTES);
-  static constexpr int TX_BYTES = FG_BYTES + H_BYTES + RING_BYTES;
+  static constexpr int OFF_UOWN = OFF_RING + al(RING_BYTES);
+  static constexpr int OFF_UHAL = OFF_UOWN + al(UOWN_BYTES);
+  static constexpr int STAGE = OFF_UHAL + al(UHAL_BYTES);
+  static constexpr int TX_BYTES = FG_BYTES + H_BYTES + RING_BYTES + UOWN_BYTES + UHAL_BYTES;
 };
 
-// Fill one stage: f and g of the tile, h with its halo, the phi ring.
+// Fill one stage: f and g of the tile, h with its halo, the phi ring; with
+// 16-bit storage also the tile's U reference (plane c) and the halo of the
+// encoding reference (plane c ^ 1).
 template <typename T, bool FLOW, int TX, int TY>
 __device__ __forceinline__ void issue_tile_2d(const CUtensorMap* tm_fg, const CUtensorMap* tm_h,
-                                              const CUtensorMap* tm_ring, uint64_t* bar,
+                                              const CUtensorMap* tm_ring,
+                                              const CUtensorMap* tm_uown,
+                                              const CUtensorMap* tm_uhal, int c, uint64_t* bar,
                                               unsigned char* st, int x0, int y0) {
   using L = Tiles2D<T, FLOW, TX, TY>;
   mbar_arrive_expect_tx(bar, L::TX_BYTES);
   tma_load_3d(st, tm_fg, bar, x0, y0, 0);
   tma_load_3d(st + L::OFF_H, tm_h, bar, x0 - L::HX, y0 - 1, L::QFG);
   tma_load_2d(st + L::OFF_RING, tm_ring, bar, x0, y0);
+  if (L::REL) {
+    tma_load_3d(st + L::OFF_UOWN, tm_uown, bar, x0, y0, c);
+    tma_load_3d(st + L::OFF_UHAL, tm_uhal, bar, x0 - L::HXU, y0 - 1, c ^ 1);
+  }
 }
 
 // Work on a filled stage `st` for the tile at (x0, y0).  Called by all
@@ -41,7 +58,7 @@ __device__ __forceinline__ void issue_tile_2d(const CUtensorMap* tm_fg, const CU
 template <typename T, bool FLOW, int TX, int TY>
 __device__ __forceinline__ void tile_2d(const Model& m, const T* __restrict__ src,
                                         T* __restrict__ dst, float* __restrict__ ring_cur,
-                                        unsigned* __restrict__ err, int x0, int y0,
+                                        unsigned* __restrict__ err, int x0, int y0, int c,
                                         unsigned char* st, float* sh_phi_flat) {
   using R = float;
   using L = Tiles2D<T, FLOW, TX, TY>;
@@ -54,6 +71,8 @@ __device__ __forceinline__ void tile_2d(const Model& m, const T* __restrict__ sr
     const T* fgs = reinterpret_cast<const T*>(st);
     T* hsm = reinterpret_cast<T*>(st + L::OFF_H);
     const float* rings = reinterpret_cast<const float*>(st + L::OFF_RING);
+    const __half* uown = reinterpret_cast<const __half*>(st + L::OFF_UOWN);
+    __half* uhal = reinterpret_cast<__half*>(st + L::OFF_UHAL);
     constexpr int HPLANE = SY * L::BXH;
 
     if (x0 == 0 || y0 == 0 || x0 + TX >= nx || y0 + TY >= ny) {
@@ -69,6 +88,7 @@ __device__ __forceinline__ void tile_2d(const Model& m, const T* __restrict__ sr
 #pragma unroll
         for (int a = 0; a < 9; ++a)
           hsm[a * HPLANE + ly * L::BXH + lx + L::HX - 1] = src[(QF + 9 + a) * P + j];
+        if (L::REL) uhal[ly * L::BXU + lx + L::HXU - 1] = m.uring[size_t(c ^ 1) * m.plane + j];
       }
       __syncthreads();
     }
@@ -93,15 +113,20 @@ __device__ __forceinline__ void tile_2d(const Model& m, const T* __restrict__ sr
         g[a] = Pop<T>::template ld<R>(fgs + (QF + a) * (TY * TX) + o);
         h[a] = Pop<T>::template ld<R>(hsm + a * HPLANE + (ty + 1) * L::BXH + tx + L::HX);
       }
+      // g stored relative to the node's own U reference, the collision
+      // takes the deviations from it as they are
+      UView<L::REL, L::BXU> uh{uhal + L::HXU - 1,
+                               L::REL ? m.uring + size_t(c) * m.plane : nullptr,
+                               L::REL ? __half2float(uown[o]) : 0.f};
       TileView<T, R, L::BXH, HPLANE, L::HX - 1> hs{hsm};
       if (x0 >= 1 && x0 + TX <= nx - 1 && y0 >= 1 && y0 + TY <= ny - 1)
         collide_push_2d<T, R, FLOW, true, SX>(m, x, y, tx + 1, ty + 1, f, g, h,
                                               sh_phi[ty + 1][tx + 1], rings[o], &sh_phi[0][0], hs,
-                                              dst, ring_cur, err);
+                                              uh, dst, ring_cur, err);
       else
         collide_push_2d<T, R, FLOW, false, SX>(m, x, y, tx + 1, ty + 1, f, g, h,
                                                sh_phi[ty + 1][tx + 1], rings[o], &sh_phi[0][0],
-                                               hs, dst, ring_cur, err);
+                                               hs, uh, dst, ring_cur, err);
     }
 }
 

@@ -695,7 +695,7 @@ int lbpf_surrogate_sample(lbpf_t* h, const lbpf_surrogate_cfg* cfg, float* x) {
   if (h->status != LBPF_OK) return h->status;
   if (!h->initialized) return sfail(h, LBPF_ESTATE, "sample before init");
   if (h->m.dim != 2) return sfail(h, LBPF_EINVAL, "the block propagator is 2D only");
-  SCK(h, lbk::launch_surrogate_gather(h->m, h->pops[h->cur], vec4(cfg->shift), vec4(cfg->scale), x,
+  SCK(h, lbk::launch_surrogate_gather(h->m, h->pops[h->cur], h->cur, vec4(cfg->shift), vec4(cfg->scale), x,
                                       nullptr, h->stream));
   return LBPF_OK;
 }
@@ -710,7 +710,7 @@ namespace {
 int queue_prediction(lbpf* h, lbpf_unet* net, const lbpf_surrogate_cfg* cfg, cudaStream_t s) {
   const long long n = (long long)h->m.nx * h->m.ny;
   const int nb = cfg->steps_per_block;
-  SCK(h, lbk::launch_surrogate_gather(h->m, h->pops[h->cur], vec4(cfg->shift), vec4(cfg->scale),
+  SCK(h, lbk::launch_surrogate_gather(h->m, h->pops[h->cur], h->cur, vec4(cfg->shift), vec4(cfg->scale),
                                       net->px, net->pF, s));
   plane_crossing_kernel<<<1, 128, 0, s>>>(net->pF, h->m.nx, h->m.ny, h->m.bc[0], h->m.bc[1], h->icx,
                                          h->icy, net->pcross + 4);

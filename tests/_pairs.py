@@ -101,8 +101,14 @@ def decode_pops(sim, buf=None):
     raw = raw.astype(np.float64)
     qf = (9 if dim == 2 else 19) if flow else 0
     qs = 9 if dim == 2 else 7
+    g_ref = u_ref
+    if dim == 2 and elem == 2:
+        # per-node g reference: the first FP16 plane after the FP32 phi ring
+        off = 64 + q * n * elem + n * 4
+        g_ref = np.frombuffer(buf[off:off + 2 * n].tobytes(), dtype=np.float16)
+        g_ref = g_ref.astype(np.float64)[None, :]
     out = {}
-    for name, lo, qq, ref in (("f", 0, qf, 1.0), ("g", qf, qs, u_ref), ("h", qf + qs, qs, -1.0)):
+    for name, lo, qq, ref in (("f", 0, qf, 1.0), ("g", qf, qs, g_ref), ("h", qf + qs, qs, -1.0)):
         w = np.array(_W[qq]) if qq else np.zeros(0)
         out[name] = (raw[lo:lo + qq] + w[:, None] * ref).reshape((qq,) + sim.shape)
     return out

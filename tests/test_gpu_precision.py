@@ -70,3 +70,47 @@ def test_16bit_restart_and_graph_are_bitwise(P, storage):
     for _ in range(70):
         b.step(1)
     assert np.array_equal(a.state(), b.state())
+
+
+# Long runs: the interface of a coupled 2D problem (inflow, 5-fold seed)
+# along the four axis rays against the FP64-storage path of the library
+# (itself held to the oracle by the parity tests).  16-bit storage keeps g
+# relative to a per-node U, so the rounding of the stored g deviations does
+# not accumulate into a drift of the growth rate.
+LONG = dict(nx=512, ny=512, flow=1, fold=5, eps=0.03, bc=(1, 0, 0), u_in=0.01, U_in=0.4)
+LONG_SEED = (150.0, 256.0, 0.0, 16.0, 0.4, 0.01, 1)
+
+
+@pytest.mark.parametrize("storage,steps,iface,growth", [("fp16", 10000, 0.1, 0.01),
+                                                        ("bf16", 5000, 1.0, 0.1)])
+def test_16bit_long_run_interface(P, storage, steps, iface, growth):
+    p = P.params(**LONG)
+    ref = P.lib_sim(p, "fp64")
+    ref.init_seed(*LONG_SEED)
+    d0 = ref.diagnostics()["iface_pos"][:4].copy()
+    ref.step(steps)
+    want = ref.diagnostics()["iface_pos"][:4]
+    a = P.lib_sim(p, storage)
+    a.init_seed(*LONG_SEED)
+    a.step(steps)
+    got = a.diagnostics()["iface_pos"][:4]
+    assert np.abs(got - want).max() < iface, (got, want)
+    grown = want - d0
+    assert np.all(np.abs(grown) > 2.0), grown  # every ray has grown
+    assert np.abs((got - d0) / grown - 1.0).max() < growth, (got - d0, grown)
+
+
+def test_16bit_2d_state_carries_the_per_node_reference(P):
+    """The exported 2D FP16 state decodes with its per-node g reference: the
+    decoded g sums to the library's U, and f, g, h match the oracle's
+    populations to the storage's field errors."""
+    p = P.params(**CPL)
+    a, b = P.pair(p, "fp16", seed_args=CPL_SEED)
+    a.step(300)
+    b.step(300, P.THREADS)
+    pa = P.decode_pops(a)
+    U = a.fields(("U",))["U"]
+    assert np.abs(pa["g"].sum(axis=0) - U).max() < 1e-5
+    pb = {k: b.pops(k) for k in "fgh"}
+    for k, tol in (("f", 1e-4), ("g", 5e-3), ("h", 1e-2)):
+        assert np.abs(pa[k] - pb[k]).max() < tol, (k, np.abs(pa[k] - pb[k]).max())
