@@ -69,6 +69,8 @@ def _load():
         lib.orc_destroy.argtypes = [vp]
         lib.orc_init_seed.argtypes = [vp] + [ctypes.c_double] * 6 + [ctypes.c_uint64]
         lib.orc_init_fields.argtypes = [vp] + [dp] * 6
+        lib.orc_init_polygon.argtypes = ([vp, ctypes.c_double, ctypes.c_double, ctypes.c_int]
+                                         + [dp] * 3 + [ctypes.c_double] * 2 + [ctypes.c_uint64])
         lib.orc_step.argtypes = [vp, ctypes.c_int, ctypes.c_int]
         lib.orc_step_count.argtypes = [vp]
         lib.orc_step_count.restype = ctypes.c_longlong
@@ -172,6 +174,15 @@ class Oracle:
 
     def init_seed(self, cx, cy, cz, radius, u0, noise_amp, seed):
         self._lib.orc_init_seed(self._h, cx, cy, cz, radius, u0, noise_amp, seed)
+
+    def init_polygon(self, cx, cy, normals, dist, u0, noise_amp, seed):
+        """Convex polygon seed: normals [k, 2] outward unit normals, dist [k]."""
+        nrm = np.ascontiguousarray(np.asarray(normals, dtype=np.float64).reshape(-1, 2))
+        nx, ny = np.ascontiguousarray(nrm[:, 0]), np.ascontiguousarray(nrm[:, 1])
+        d = np.ascontiguousarray(np.asarray(dist, dtype=np.float64).reshape(-1))
+        assert d.size == nx.size
+        self._lib.orc_init_polygon(self._h, cx, cy, int(d.size), _ptr(nx), _ptr(ny), _ptr(d),
+                                   u0, noise_amp, seed)
 
     def init_fields(self, phi, U, rho=None, ux=None, uy=None, uz=None):
         arrs = []

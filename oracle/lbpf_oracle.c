@@ -514,6 +514,33 @@ void orc_init_seed(orc_sim* s, double cx, double cy, double cz, double radius,
   s->step = 0;
 }
 
+/* Convex polygon seed, 2D (the rhombic and hexagonal seeds of Sec. 3.1):
+ * the polygon is {x : (x - c).n_i <= d_i for every facet i}; the signed
+ * distance to it is taken as s(x) = max_i [(x - c).n_i - d_i] (exact inside
+ * and beside the sides, an underestimate only outside the corners) and
+ * phi0 = tanh(-s / (sqrt(2) W0)), plus the noise of the round seed; U = u0,
+ * rho = 1 and the inlet velocity as there. */
+void orc_init_polygon(orc_sim* s, double cx, double cy, int k, const double* nx,
+                      const double* ny, const double* d, double u0, double noise_amp,
+                      uint64_t seed) {
+  const orc_params* p = &s->p;
+  for (int i = 0; i < s->n; ++i) {
+    int x = i % p->nx, y = (i / p->nx) % p->ny;
+    double sd = -1e300;
+    for (int f = 0; f < k; ++f) {
+      double v = (x - cx) * nx[f] + (y - cy) * ny[f] - d[f];
+      if (v > sd) sd = v;
+    }
+    double phi = tanh(-sd / (sqrt(2.0) * p->w0));
+    uint64_t bits = splitmix64(seed ^ ((uint64_t)i * 0x9E3779B97F4A7C15ull));
+    double xi = (double)(bits >> 11) * (1.0 / 4503599627370496.0) - 1.0; /* [-1, 1) */
+    phi += noise_amp * xi;
+    double u[3] = {p->flow ? p->u_inlet : 0.0, 0.0, 0.0};
+    set_equilibrium(s, i, phi, u0, 1.0, u);
+  }
+  s->step = 0;
+}
+
 void orc_init_fields(orc_sim* s, const double* phi, const double* U, const double* rho,
                      const double* ux, const double* uy, const double* uz) {
   for (int i = 0; i < s->n; ++i) {

@@ -69,6 +69,11 @@ void orc_init_seed(orc_sim* s, double cx, double cy, double cz, double radius,
                    double u0, double noise_amp, uint64_t seed);
 /* Equilibrium populations from given macroscopic fields (length nx*ny*nz,
  * x fastest).  uz may be NULL in 2D. */
+/* convex polygon seed (2D): facets with outward unit normals (nx, ny) at
+ * distances d from the centre (cx, cy) */
+void orc_init_polygon(orc_sim* s, double cx, double cy, int k, const double* nx,
+                      const double* ny, const double* d, double u0, double noise_amp,
+                      uint64_t seed);
 void orc_init_fields(orc_sim* s, const double* phi, const double* U, const double* rho,
                      const double* ux, const double* uy, const double* uz);
 
