@@ -39,6 +39,7 @@ SRC_2D = ["step2d.cu", "step2d_tile.cuh", "step2d_core.cuh", "lbpf_device.cuh", 
 SRC_3D = ["step3d.cu", "step3d_core.cuh", "lbpf_device.cuh"]
 SRC_BATCH = ["batch2d.cu", "step2d_tile.cuh", "step2d_core.cuh", "lbpf_device.cuh", "tma.cuh"]
 SRC_CONV = ["conv_tc.cu", "tma.cuh"]
+SRC_FACETS = ["facets.cu"]
 
 # bytes each node moves through HBM per step (populations read + written,
 # phi(t-1) read, phi(t) written)
@@ -50,6 +51,17 @@ WORKLOADS = {
                storage="fp32", kernel="step2d_tma_kernel", src=SRC_2D,
                sample=dict(nx=256, ny=256, seed=(75.0, 128.0, 0.0, 16.0, 0.4, 0.01, 1))),
     "c2_fp16": dict(base="c2", storage="fp16"),
+    "f1": dict(desc="2D 1024x1024 coupled LB, inflow 0.01, hexagonal seed (perimeter 120 lu, "
+                    "side normals at 0.1 + pi/6 + k pi/3) at x=300, U0=0.4, 6-fold eps 0.03 at "
+                    "theta0 0.1; crystal shape (side lengths, centre, Q, aspect ratio) measured "
+                    "every 1000 steps, growth rates and R^2 fitted",
+               dim=2, nx=1024, ny=1024, nz=1, flow=1, fold=6, eps=0.03, theta0=0.1,
+               bc=(1, 0, 0), u_in=0.01, U_in=0.4, every=1000,
+               polygon=dict(cx=300.0, cy=512.0, perimeter=120.0, u0=0.4, noise=0.01, seed=1),
+               storage="fp32", kernel="step2d_tma_kernel", src=SRC_2D,
+               sample=dict(nx=256, ny=256,
+                           polygon=dict(cx=75.0, cy=128.0, perimeter=120.0, u0=0.4,
+                                        noise=0.01, seed=1))),
     "c1": dict(desc="2D 128x128 periodic, no flow (phase field + solute D2Q9), U0=0.3, R=8, "
                     "4-fold eps 0.05",
                dim=2, nx=128, ny=128, nz=1, flow=0, fold=4, eps=0.05, bc=(0, 0, 0), u_in=0.0,
@@ -150,7 +162,8 @@ def lib_params(w, L, storage=None):
     return dict(dim=w["dim"], nx=w["nx"], ny=w["ny"], nz=w["nz"], bc=w["bc"], flow=w["flow"],
                 storage={"fp32": L.FP32, "fp64": L.FP64, "fp16": L.FP16_SHIFTED,
                          "bf16": L.BF16_SHIFTED}[storage or w["storage"]],
-                fold=w["fold"], eps_aniso=w["eps"], u_inlet=w["u_in"], u0_inlet=w["U_in"])
+                fold=w["fold"], eps_aniso=w["eps"], u_inlet=w["u_in"], u0_inlet=w["U_in"],
+                theta0=w.get("theta0", 0.0))
 
 
 def measured_peaks():
@@ -319,13 +332,25 @@ def oracle_problem(w):
         body = (g, 0.0, 0.0)
     p = oracle.Params(dim=w["dim"], nx=s["nx"], ny=s["ny"], nz=s.get("nz", 1), bc=w["bc"],
                       flow=w["flow"], fold=w["fold"], eps=w["eps"], u_inlet=w["u_in"],
-                      u0_inlet=w["U_in"], body=body)
+                      u0_inlet=w["U_in"], body=body, theta0=w.get("theta0", 0.0))
     o = oracle.Oracle(p)
     if s.get("channel"):
         o.init_fields(f["phi"], f["U"], None, f["ux"], f["uy"])
+    elif s.get("polygon"):
+        g = s["polygon"]
+        nrm, d = hexagon(g["perimeter"], w["theta0"] + 3.141592653589793 / 6)
+        o.init_polygon(g["cx"], g["cy"], nrm, d, g["u0"], g["noise"], g["seed"])
     else:
         o.init_seed(*s["seed"])
     return p, o
+
+
+def hexagon(perimeter, theta):
+    """Side normals (counter-clockwise from theta) and apothems of a regular
+    hexagon of the given perimeter."""
+    import numpy as np
+    a = theta + np.pi / 3.0 * np.arange(6)
+    return np.stack([np.cos(a), np.sin(a)], axis=1), np.full(6, perimeter / 6.0 * 3 ** 0.5 / 2)
 
 
 def oracle_sample(w, seconds: float, threads: int):
@@ -392,6 +417,8 @@ def main():
         return run_surrogate(args, w)
     if w.get("network"):
         return run_network(args, w)
+    if w.get("polygon"):
+        return run_facets(args, w)
 
     import numpy as np
     import torch
@@ -597,6 +624,108 @@ def main():
         print(json.dumps(out), flush=True)
     del sims
     stepper.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def run_facets(args, w):
+    """f1: the coupled step with the crystal-shape measurement every `every`
+    steps (one GPU; replicas beyond).  value = MLUPS of the whole run,
+    measurements included; beside it the measurement's own time and HBM
+    roofline, and the growth-rate fits of the side lengths."""
+    import numpy as np
+    import torch
+    import paper_2206_02145_gb300 as L
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    stream = torch.cuda.current_stream()
+    g = w["polygon"]
+    nrm, dist0 = hexagon(g["perimeter"], w["theta0"] + np.pi / 6)
+    sim = L.Sim(stream=stream.cuda_stream, **lib_params(w, L))
+    sim.init_polygon(g["cx"], g["cy"], nrm, dist0, g["u0"], g["noise"], g["seed"])
+    every = w["every"]
+    steps = max(every, args.steps // every * every)
+    sim.step(args.warmup)
+    first = sim.facets(nrm)
+    torch.cuda.synchronize()
+    hist_t, hist_L = [args.warmup], [first["L"]]
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for k in range(steps // every):
+            sim.step(every)
+            r = sim.facets(nrm)
+            hist_t.append(args.warmup + (k + 1) * every)
+            hist_L.append(r["L"])
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+    ms = max_over_ranks([ev0.elapsed_time(ev1)], dist)[0]
+    value = whole_job_rate(w["nodes"] * steps, world, ms * 1e-3) / 1e6
+    # the measurement alone: fields (phi in FP64) and the two support passes
+    nrep = 20
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for _ in range(nrep):
+        sim.facets(nrm)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    meas_us = ev0.elapsed_time(ev1) / nrep * 1e3
+    # algorithmic bytes of one measurement: h read (9 x 4 B) and phi written
+    # (8 B) by the read-out, phi read (8 B) by the support pass
+    meas_bytes = (9 * 4 + 8 + 8) * w["nodes"]
+    peak, peak_kind = measured_peaks()
+    ach = meas_bytes / (meas_us * 1e-6) / 1e9
+    Lh = np.array(hist_L)
+    t = np.array(hist_t, dtype=np.float64)
+    fits = [L.lbpf_growth_fit(t, Lh[:, i]) for i in range(Lh.shape[1])]
+    favg = L.lbpf_growth_fit(t, Lh.mean(axis=1))
+    d = sim.diagnostics()
+    if rank == 0:
+        cpu = None
+        if not args.no_cpu_baseline:
+            threads = os.cpu_count() or 1
+            v, st, n, dt = oracle_sample(w, args.cpu_seconds, threads)
+            cpu = {"value": v, "unit": "MLUPS", "cores": threads, "kind": "oracle",
+                   "sample": f"{st} LB steps of a 256x256 grid of the same workload ({n} "
+                             f"nodes), {dt:.1f} s, FP64"}
+        print(json.dumps({
+            "metric": "coupled-LB MLUPS (with crystal-shape measurement)", "value": value,
+            "unit": "MLUPS", "n_gpus": world, "steps": steps, "warmup": args.warmup,
+            "ms_per_step": ms / steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded hexagonal seed + "
+            "SplitMix64 noise)",
+            "config": {"workload": w["desc"], "grid": [w["nx"], w["ny"], 1], "every": every,
+                       "l2": "inputs larger than L2: 235 MB moved per step vs 129 MB L2",
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "shape": {"L_initial": first["L"].tolist(), "L_final": hist_L[-1].tolist(),
+                      "growth_rate_lu_per_step": [f[0] for f in fits],
+                      "r2": [f[2] for f in fits],
+                      "L_avg_growth_rate": favg[0], "L_avg_r2": favg[2],
+                      "Q": float(Lh[-1].max() / Lh[-1].min()), "aspect": r["aspect"],
+                      "centre": r["centre"].tolist(), "samples": len(hist_t)},
+            "measurement": {"us_per_call": meas_us, "share_of_run":
+                            (steps // every) * meas_us * 1e-3 / ms},
+            "roofline": {"bound": "hbm", "kernel": "facet measurement (read-out + support)",
+                         "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                         "peak_source": peak_kind, "traffic": None,
+                         "algorithmic_bytes_per_launch": meas_bytes},
+            "cpu_baseline": cpu,
+            "gpu_launches": steps + 3 * (steps // every),
+            "clocks": clk.summary(),
+            "diag": {"step": d["step"], "solute_drift_rel": d["solute_drift_rel"]},
+        }), flush=True)
+    sim.close()
     if dist is not None:
         dist.destroy_process_group()
 

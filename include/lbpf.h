@@ -124,6 +124,38 @@ typedef struct {
   uint64_t seed;
 } lbpf_seed;
 
+/* Convex polygon seed, 2D (the rhombic and hexagonal seeds of Sec. 3.1):
+ * the polygon {x : (x - c) . n_i <= dist_i for every facet i}. */
+#define LBPF_MAX_FACETS 12
+typedef struct {
+  double cx, cy;                /* centre in node units */
+  int nfacets;                  /* 3 .. LBPF_MAX_FACETS */
+  double nx[LBPF_MAX_FACETS];   /* outward unit normal of facet i */
+  double ny[LBPF_MAX_FACETS];
+  double dist[LBPF_MAX_FACETS]; /* distance of facet i's line from the centre */
+  double u0;                    /* initial supersaturation */
+  double noise_amp;
+  uint64_t seed;
+} lbpf_polygon_seed;
+
+/* Shape of a faceted 2D crystal (Sec. 3.1.2, Sec. 3.2), from the phi = 0
+ * contour: the crossings of phi = 0 on the grid's x- and y-edges (phi > 0 at
+ * one end only; linear interpolation; no edge across a periodic wrap). */
+typedef struct {
+  int64_t points;                  /* contour points found; 0: every value NaN */
+  int nfacets;
+  double support[LBPF_MAX_FACETS]; /* h_i = max over the contour of p . n_i (node units) */
+  double side_cx[LBPF_MAX_FACETS]; /* centre of side i: midpoint of the segment of */
+  double side_cy[LBPF_MAX_FACETS]; /* p . n_i = h_i between sides i - 1 and i + 1 */
+  double cx, cy;                   /* crystal centre: least-squares meet of the lines
+                                      joining the centres of opposite sides */
+  double L[LBPF_MAX_FACETS];       /* normal distance of side i from the centre */
+  double L_avg;                    /* mean of L */
+  double Q;                        /* quality parameter max L / min L (Sec. 3.2) */
+  double width, height;            /* extent of the contour along x and along y */
+  double aspect;                   /* width / height (Sec. 3.2) */
+} lbpf_facets;
+
 /* FP64 diagnostics of the current state. */
 typedef struct {
   int64_t step;
@@ -152,6 +184,14 @@ int lbpf_create(const lbpf_params* p, void* stream, lbpf_t** out);
 /* Initial state from a seed (computed on the device in FP64, stored in the
  * population type); resets the step counter to 0.  Asynchronous. */
 int lbpf_init_seed(lbpf_t* h, const lbpf_seed* s);
+
+/* Initial state from a convex polygon seed (2D only): phi0 = tanh(-s /
+ * (sqrt(2) W0)) with s = max_i [(x - c) . n_i - dist_i], plus the noise of
+ * lbpf_init_seed (same generator and amplitude meaning); U = u0, rho = 1, the
+ * inlet velocity as there.  Resets the step counter.  EINVAL for 3D, a
+ * facet count outside 3..LBPF_MAX_FACETS, a normal whose length differs from
+ * 1 by more than 1e-9, or a non-finite value.  Asynchronous. */
+int lbpf_init_polygon(lbpf_t* h, const lbpf_polygon_seed* s);
 
 /* Initial state from host FP64 fields of nx*ny*nz values each: every
  * population at the equilibrium of (rho, u* = (1 - clamp(phi))/2 u, U, phi);
@@ -193,6 +233,25 @@ int lbpf_write_state(lbpf_t* h, const void* host_src, size_t bytes);
 /* FP64 reductions of the current state (deterministic two-pass sums).
  * Synchronising; reports a non-finite state as LBPF_ENONFINITE. */
 int lbpf_diagnostics(lbpf_t* h, lbpf_diag* out);
+
+/* Crystal shape of the current state along k facet normals (nx[k], ny[k],
+ * host arrays read during the call): k even in 4..LBPF_MAX_FACETS, unit
+ * normals in counter-clockwise order, normal i + k/2 opposite to normal i.
+ * The support values are FP64 maxima over the contour, reduced on the device
+ * in a fixed order (reproducible bit for bit); the side centres, the centre
+ * and the lengths follow on the host in FP64.  The first call allocates a
+ * small device scratch.  2D only (EINVAL otherwise); ESTATE before init.
+ * Synchronising. */
+int lbpf_measure_facets(lbpf_t* h, int k, const double* nx, const double* ny,
+                        lbpf_facets* out);
+
+/* Straight-line fit L'(t) = intercept + slope t of a size history of n >= 2
+ * points (host arrays), and its coefficient of determination R^2 =
+ * 1 - A_res / A_tot (Eqs. 26-28); R^2 is NaN when every L is the same.
+ * EINVAL for a null pointer, n < 2, non-finite data or all t equal.  A host
+ * computation; needs no handle. */
+int lbpf_growth_fit(const double* t, const double* L, int n, double* slope, double* intercept,
+                    double* r2);
 
 /* Rebind the handle to another stream (e.g. the caller's current stream). */
 int lbpf_set_stream(lbpf_t* h, void* stream);

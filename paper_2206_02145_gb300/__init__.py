@@ -57,6 +57,26 @@ class lbpf_seed(ctypes.Structure):
                 ("noise_amp", ctypes.c_double), ("seed", ctypes.c_uint64)]
 
 
+MAX_FACETS = 12
+
+
+class lbpf_polygon_seed(ctypes.Structure):
+    _fields_ = [("cx", ctypes.c_double), ("cy", ctypes.c_double), ("nfacets", ctypes.c_int),
+                ("nx", ctypes.c_double * MAX_FACETS), ("ny", ctypes.c_double * MAX_FACETS),
+                ("dist", ctypes.c_double * MAX_FACETS), ("u0", ctypes.c_double),
+                ("noise_amp", ctypes.c_double), ("seed", ctypes.c_uint64)]
+
+
+class lbpf_facets(ctypes.Structure):
+    _fields_ = [("points", ctypes.c_int64), ("nfacets", ctypes.c_int),
+                ("support", ctypes.c_double * MAX_FACETS),
+                ("side_cx", ctypes.c_double * MAX_FACETS),
+                ("side_cy", ctypes.c_double * MAX_FACETS), ("cx", ctypes.c_double),
+                ("cy", ctypes.c_double), ("L", ctypes.c_double * MAX_FACETS),
+                ("L_avg", ctypes.c_double), ("Q", ctypes.c_double), ("width", ctypes.c_double),
+                ("height", ctypes.c_double), ("aspect", ctypes.c_double)]
+
+
 class lbpf_diag(ctypes.Structure):
     _fields_ = [("step", ctypes.c_int64), ("solute_total", ctypes.c_double),
                 ("solute_drift_rel", ctypes.c_double), ("mass_total", ctypes.c_double),
@@ -95,7 +115,8 @@ EXPORTED = ("lbpf_params_default", "lbpf_create", "lbpf_init_seed", "lbpf_init_f
             "lbpf_unet_param_count", "lbpf_unet_params", "lbpf_unet_device_bytes",
             "lbpf_unet_last_error", "lbpf_unet_destroy", "lbpf_unet_set_tensor_path",
             "lbpf_unet_status", "lbpf_surrogate_sample",
-            "lbpf_surrogate_target", "lbpf_surrogate_advance")
+            "lbpf_surrogate_target", "lbpf_surrogate_advance", "lbpf_init_polygon",
+            "lbpf_measure_facets", "lbpf_growth_fit")
 
 
 def _load_library():
@@ -157,6 +178,9 @@ def _load_library():
                                           ctypes.c_int64, vp, vp]
     lib.lbpf_surrogate_advance.argtypes = [vp, vp, ctypes.POINTER(lbpf_surrogate_cfg),
                                            ctypes.c_int, ctypes.POINTER(lbpf_surrogate_report)]
+    lib.lbpf_init_polygon.argtypes = [vp, ctypes.POINTER(lbpf_polygon_seed)]
+    lib.lbpf_measure_facets.argtypes = [vp, ctypes.c_int, dp, dp, ctypes.POINTER(lbpf_facets)]
+    lib.lbpf_growth_fit.argtypes = [dp, dp, ctypes.c_int, dp, dp, dp]
     keep = ("lbpf_state_bytes", "lbpf_device_bytes", "lbpf_last_error", "lbpf_destroy",
             "lbpf_batch_instance", "lbpf_batch_last_error", "lbpf_batch_destroy",
             "lbpf_unet_param_count", "lbpf_unet_device_bytes", "lbpf_unet_last_error",
@@ -209,6 +233,73 @@ def lbpf_create(params: lbpf_params, stream: int | None = None) -> int:
 def lbpf_init_seed(h: int, cx, cy, cz, radius, u0, noise_amp, seed) -> None:
     s = lbpf_seed(cx, cy, cz, radius, u0, noise_amp, seed)
     _check(h, _lib.lbpf_init_seed(h, ctypes.byref(s)))
+
+
+def lbpf_init_polygon(h: int, cx, cy, normals, dist, u0, noise_amp, seed) -> None:
+    """normals: [k, 2] outward unit normals; dist: [k] distances from (cx, cy)."""
+    n = np.asarray(normals, np.float64).reshape(-1, 2)
+    d = np.asarray(dist, np.float64).reshape(-1)
+    if n.shape[0] != d.size or not 0 < d.size <= MAX_FACETS:
+        raise LbpfError(EINVAL, "normals and dist must have the same length, at most 12")
+    s = lbpf_polygon_seed(cx=cx, cy=cy, nfacets=d.size, u0=u0, noise_amp=noise_amp, seed=seed)
+    for i in range(d.size):
+        s.nx[i], s.ny[i], s.dist[i] = n[i, 0], n[i, 1], d[i]
+    _check(h, _lib.lbpf_init_polygon(h, ctypes.byref(s)))
+
+
+def lbpf_measure_facets(h: int, normals) -> dict:
+    """Crystal shape along the facet normals [k, 2] (k even, counter-clockwise,
+    normal i + k/2 opposite to normal i)."""
+    n = np.ascontiguousarray(np.asarray(normals, np.float64).reshape(-1, 2))
+    nx, ny = np.ascontiguousarray(n[:, 0]), np.ascontiguousarray(n[:, 1])
+    f = lbpf_facets()
+    _check(h, _lib.lbpf_measure_facets(h, int(nx.size), _dptr(nx), _dptr(ny), ctypes.byref(f)))
+    k = f.nfacets
+    return {"points": int(f.points), "support": np.array(f.support[:k]),
+            "side_centre": np.stack([np.array(f.side_cx[:k]), np.array(f.side_cy[:k])], axis=1),
+            "centre": np.array([f.cx, f.cy]), "L": np.array(f.L[:k]), "L_avg": f.L_avg,
+            "Q": f.Q, "width": f.width, "height": f.height, "aspect": f.aspect}
+
+
+def lbpf_growth_fit(t, L) -> tuple:
+    """(slope, intercept, R^2) of the straight-line fit of L(t) (Eqs. 26-28)."""
+    t = np.ascontiguousarray(np.asarray(t, np.float64).reshape(-1))
+    L = np.ascontiguousarray(np.asarray(L, np.float64).reshape(-1))
+    if t.size != L.size:
+        raise LbpfError(EINVAL, "t and L differ in length")
+    out = np.zeros(3)
+    rc = _lib.lbpf_growth_fit(_dptr(t), _dptr(L), int(t.size), _dptr(out[0:]), _dptr(out[1:]),
+                              _dptr(out[2:]))
+    if rc != OK:
+        raise LbpfError(rc, "lbpf_growth_fit: need >= 2 finite points, t not all equal")
+    return float(out[0]), float(out[1]), float(out[2])
+
+
+def hexagon_normals(theta: float = 0.0) -> np.ndarray:
+    """Outward normals of a hexagon's sides, counter-clockwise from theta."""
+    a = theta + np.pi / 3.0 * np.arange(6)
+    return np.stack([np.cos(a), np.sin(a)], axis=1)
+
+
+def rhombus_normals(theta: float = 0.0, acute: float = np.pi / 3.0) -> np.ndarray:
+    """Outward normals of a rhombus whose long diagonal lies along theta and
+    whose acute angle is `acute`, counter-clockwise.  With acute = 60 deg they
+    are normals 1, 2, 4, 5 of hexagon_normals(theta)."""
+    b = np.pi / 2.0 - acute / 2.0
+    a = theta + np.array([b, np.pi - b, np.pi + b, 2.0 * np.pi - b])
+    return np.stack([np.cos(a), np.sin(a)], axis=1)
+
+
+def hexagonal_seed(perimeter: float, theta: float = 0.0):
+    """(normals, dist) of a regular hexagon of the given perimeter."""
+    side = perimeter / 6.0
+    return hexagon_normals(theta), np.full(6, side * np.sqrt(3.0) / 2.0)
+
+
+def rhombic_seed(perimeter: float, theta: float = 0.0, acute: float = np.pi / 3.0):
+    """(normals, dist) of a rhombus of the given perimeter and acute angle."""
+    side = perimeter / 4.0
+    return rhombus_normals(theta, acute), np.full(4, side * np.sin(acute) / 2.0)
 
 
 def lbpf_init_fields(h: int, phi, U, rho=None, ux=None, uy=None, uz=None) -> None:
@@ -300,6 +391,12 @@ class Sim:
 
     def init_fields(self, phi, U, rho=None, ux=None, uy=None, uz=None):
         lbpf_init_fields(self.h, phi, U, rho, ux, uy, uz)
+
+    def init_polygon(self, cx, cy, normals, dist, u0=0.3, noise_amp=0.0, seed=1):
+        lbpf_init_polygon(self.h, cx, cy, normals, dist, u0, noise_amp, seed)
+
+    def facets(self, normals) -> dict:
+        return lbpf_measure_facets(self.h, normals)
 
     def step(self, n: int = 1):
         lbpf_step(self.h, n)

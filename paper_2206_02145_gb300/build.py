@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "liblbpf.so")
 SOURCES = ["lbpf_api.cu", "step2d.cu", "step3d.cu", "batch2d.cu", "aux.cu", "noalloc.cu",
-           "unet.cu", "conv_tc.cu", "surrogate.cu"]
+           "unet.cu", "conv_tc.cu", "surrogate.cu", "facets.cu"]
 HEADERS = ["lbpf_internal.cuh", "lbpf_device.cuh", "step2d_core.cuh", "step2d_tile.cuh", "step3d_core.cuh", "tma_host.h",
            "tma.cuh", "unet.cuh", "unet_ops.cuh", "lbpf_handle.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

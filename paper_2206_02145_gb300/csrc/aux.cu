@@ -118,6 +118,33 @@ __global__ void init_seed_kernel(const Model m, const SeedArgs s, T* pops, R* ph
   }
 }
 
+// Convex polygon seed (2D; the rhombic and hexagonal seeds of Sec. 3.1): the
+// signed distance to {x : (x - c).n_i <= d_i} taken as s = max_i [(x - c).n_i
+// - d_i] (exact inside and beside the sides), phi0 = tanh(-s / (sqrt(2) W0));
+// noise, U, rho and u as for the round seed.
+template <typename T, typename R>
+__global__ void init_polygon_kernel(const Model m, const PolygonArgs a, T* pops, R* phi_prev) {
+  const long long n = (long long)m.nx * m.ny;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    int x, y, z;
+    node_xyz(m, i, x, y, z);
+    double sd = -1e300;
+    for (int f = 0; f < a.k; ++f) {
+      const double v = (x - a.cx) * a.nx[f] + (y - a.cy) * a.ny[f] - a.d[f];
+      sd = v > sd ? v : sd;
+    }
+    double phi = tanh(-sd / (sqrt(2.0) * m.w0));
+    const unsigned long long bits =
+        splitmix64(a.seed ^ ((unsigned long long)i * 0x9E3779B97F4A7C15ull));
+    const double xi = double(bits >> 11) * 0x1.0p-52 - 1.0;  // [-1, 1)
+    phi += a.noise_amp * xi;
+    const long long j = pitched(m, x, y, z);
+    store_equilibrium<T>(m, pops, j, phi, a.u0, 1.0, m.flow ? m.u_in : 0.0, 0.0, 0.0);
+    phi_prev[j] = R(phi - m.ref_h);  // the ring holds phi + 1
+  }
+}
+
 template <typename T, typename R>
 __global__ void init_fields_kernel(const Model m, const double* phi, const double* U,
                                    const double* rho, const double* ux, const double* uy,
@@ -357,6 +384,14 @@ cudaError_t init_seed_t(const Model& m, const SeedArgs& a, void* pops, void* pp,
   return cudaGetLastError();
 }
 template <typename T, typename R>
+cudaError_t init_polygon_t(const Model& m, const PolygonArgs& a, void* pops, void* pp,
+                           cudaStream_t s) {
+  const long long n = (long long)m.nx * m.ny;
+  init_polygon_kernel<T, R><<<grid_for(n), 256, 0, s>>>(m, a, static_cast<T*>(pops),
+                                                        static_cast<R*>(pp));
+  return cudaGetLastError();
+}
+template <typename T, typename R>
 cudaError_t init_fields_t(const Model& m, const double* phi, const double* U, const double* rho,
                           const double* ux, const double* uy, const double* uz, void* pops,
                           void* pp, cudaStream_t s) {
@@ -419,6 +454,11 @@ cudaError_t commit_t(const Model& m, const float* F1, const float* rho, void* po
 cudaError_t launch_init_seed(const Model& m, const SeedArgs& a, void* pops, void* phi_prev,
                              cudaStream_t s) {
   LBPF_DISPATCH(init_seed_t, m, a, pops, phi_prev, s)
+}
+cudaError_t launch_init_polygon(const Model& m, const PolygonArgs& a, void* pops,
+                                void* phi_prev, cudaStream_t s) {
+  if (m.dim != 2 || a.k < 1 || a.k > kMaxFacets) return cudaErrorInvalidValue;
+  LBPF_DISPATCH(init_polygon_t, m, a, pops, phi_prev, s)
 }
 cudaError_t launch_init_fields(const Model& m, const double* phi, const double* U,
                                const double* rho, const double* ux, const double* uy,

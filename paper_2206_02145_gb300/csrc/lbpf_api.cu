@@ -343,6 +343,48 @@ int lbpf_init_seed(lbpf_t* h, const lbpf_seed* s) {
   return LBPF_OK;
 }
 
+int lbpf_init_polygon(lbpf_t* h, const lbpf_polygon_seed* s) {
+  int rc = check_handle(h);
+  if (rc) return rc;
+  if (h->m.dim != 2) return fail(h, LBPF_EINVAL, "polygon seeds are 2D");
+  if (!s || s->nfacets < 3 || s->nfacets > LBPF_MAX_FACETS || !std::isfinite(s->cx) ||
+      !std::isfinite(s->cy) || !std::isfinite(s->u0) || !std::isfinite(s->noise_amp))
+    return fail(h, LBPF_EINVAL, "invalid polygon seed");
+  lbk::PolygonArgs a{};
+  a.cx = s->cx;
+  a.cy = s->cy;
+  a.k = s->nfacets;
+  for (int i = 0; i < s->nfacets; ++i) {
+    const double len = std::hypot(s->nx[i], s->ny[i]);
+    if (!(std::fabs(len - 1.0) <= 1e-9) || !std::isfinite(s->dist[i]))
+      return fail(h, LBPF_EINVAL, "facet %d: normal not of unit length or distance not finite", i);
+    a.nx[i] = s->nx[i];
+    a.ny[i] = s->ny[i];
+    a.d[i] = s->dist[i];
+  }
+  a.u0 = s->u0;
+  a.noise_amp = s->noise_amp;
+  a.seed = s->seed;
+  h->m.ref_g = s->u0;
+  lbk::finalize(h->m);
+  drop_graph(h);
+  ++h->gen;
+  h->cur = 0;
+  h->step = 0;
+  CK(h, lbk::launch_init_polygon(h->m, a, h->pops[0], h->phi[0], h->stream));
+  auto clampi = [](double v, int n) {
+    long long i = std::llround(v);
+    return int(i < 0 ? 0 : (i >= n ? n - 1 : i));
+  };
+  h->icx = clampi(s->cx, h->m.nx);
+  h->icy = clampi(s->cy, h->m.ny);
+  h->icz = 0;
+  h->initialized = true;
+  store_I0(h);
+  CK(h, cudaGetLastError());
+  return LBPF_OK;
+}
+
 int lbpf_init_fields(lbpf_t* h, const double* phi, const double* U, const double* rho,
                      const double* ux, const double* uy, const double* uz) {
   int rc = check_handle(h);
@@ -532,6 +574,155 @@ int lbpf_diagnostics(lbpf_t* h, lbpf_diag* out) {
   return LBPF_OK;
 }
 
+int lbpf_measure_facets(lbpf_t* h, int k, const double* nx, const double* ny,
+                        lbpf_facets* out) {
+  int rc = check_handle(h);
+  if (rc) return rc;
+  if (!out || !nx || !ny) return fail(h, LBPF_EINVAL, "null argument");
+  if (!h->initialized) return fail(h, LBPF_ESTATE, "facets before init");
+  if (h->m.dim != 2) return fail(h, LBPF_EINVAL, "facet measurement is 2D");
+  if (k < 4 || k > LBPF_MAX_FACETS || k % 2)
+    return fail(h, LBPF_EINVAL, "facet count must be even, 4..%d", LBPF_MAX_FACETS);
+  for (int i = 0; i < k; ++i) {
+    const int o = (i + k / 2) % k, nb = (i + 1) % k;
+    if (!(std::fabs(std::hypot(nx[i], ny[i]) - 1.0) <= 1e-9))
+      return fail(h, LBPF_EINVAL, "facet %d: normal not of unit length", i);
+    if (!(std::fabs(nx[i] + nx[o]) <= 1e-9 && std::fabs(ny[i] + ny[o]) <= 1e-9))
+      return fail(h, LBPF_EINVAL, "facet %d: normal %d is not its opposite", i, o);
+    if (!(nx[i] * ny[nb] - ny[i] * nx[nb] > 1e-6))
+      return fail(h, LBPF_EINVAL, "facets %d, %d: normals not in counter-clockwise order", i, nb);
+  }
+  const size_t n = size_t(h->m.nx) * h->m.ny;
+  if ((rc = ensure_fields_buffer(h, n * sizeof(double)))) return rc;
+  if (!h->d_facets) {
+    const size_t b = lbk::facet_scratch_bytes() + 32 * sizeof(double);
+    cudaError_t e = cudaMalloc(&h->d_facets, b);
+    if (e != cudaSuccess) return fail(h, LBPF_ENOMEM, "facet scratch: %s", cudaGetErrorString(e));
+    h->dev_bytes += b;
+  }
+  // directions: the k normals, then +x, -x, +y, -y for the extents
+  lbk::FacetDirs d{};
+  d.n = k + 4;
+  for (int i = 0; i < k; ++i) {
+    d.dx[i] = nx[i];
+    d.dy[i] = ny[i];
+  }
+  const double ax[4] = {1.0, -1.0, 0.0, 0.0}, ay[4] = {0.0, 0.0, 1.0, -1.0};
+  for (int j = 0; j < 4; ++j) {
+    d.dx[k + j] = ax[j];
+    d.dy[k + j] = ay[j];
+  }
+  double* res = h->d_facets + lbk::facet_scratch_bytes() / sizeof(double);
+  CK(h, lbk::launch_fields(h->m, h->pops[h->cur], h->phi[h->cur], h->cur, LBPF_FIELD_PHI, 1,
+                            h->d_fields, h->stream));
+  CK(h, lbk::launch_facet_support(static_cast<const double*>(h->d_fields), h->m.nx, h->m.ny, d,
+                                   h->d_facets, res, h->stream));
+  double v[lbk::kMaxDirs + 1];
+  CK(h, cudaMemcpyAsync(v, res, sizeof(double) * (k + 5), cudaMemcpyDeviceToHost, h->stream));
+  if ((rc = check_device_error(h))) return rc;
+
+  const double nan = std::nan("");
+  std::memset(out, 0, sizeof(*out));
+  out->nfacets = k;
+  out->points = (long long)v[k + 4];
+  if (out->points == 0) {
+    for (int i = 0; i < LBPF_MAX_FACETS; ++i)
+      out->support[i] = out->side_cx[i] = out->side_cy[i] = out->L[i] = nan;
+    out->cx = out->cy = out->L_avg = out->Q = out->width = out->height = out->aspect = nan;
+    return LBPF_OK;
+  }
+  // side i runs between its meets with the supporting lines of sides i - 1
+  // and i + 1; its centre is the midpoint
+  double ex[LBPF_MAX_FACETS], ey[LBPF_MAX_FACETS];  // end shared by sides i and i + 1
+  for (int i = 0; i < k; ++i) {
+    const int j = (i + 1) % k;
+    const double det = nx[i] * ny[j] - ny[i] * nx[j];
+    ex[i] = (v[i] * ny[j] - ny[i] * v[j]) / det;
+    ey[i] = (nx[i] * v[j] - v[i] * nx[j]) / det;
+    out->support[i] = v[i];
+  }
+  for (int i = 0; i < k; ++i) {
+    const int p = (i + k - 1) % k;
+    out->side_cx[i] = 0.5 * (ex[p] + ex[i]);
+    out->side_cy[i] = 0.5 * (ey[p] + ey[i]);
+  }
+  // centre: the point nearest (least squares) to the lines joining the
+  // centres of opposite sides; their mean if those lines cannot fix a point
+  double a11 = 0.0, a12 = 0.0, a22 = 0.0, r1 = 0.0, r2 = 0.0;
+  int lines = 0;
+  for (int i = 0; i < k / 2; ++i) {
+    const int o = i + k / 2;
+    double ux = out->side_cx[o] - out->side_cx[i], uy = out->side_cy[o] - out->side_cy[i];
+    const double len = std::hypot(ux, uy);
+    if (!(len > 0.0)) continue;
+    ux /= len;
+    uy /= len;
+    const double m11 = 1.0 - ux * ux, m12 = -ux * uy, m22 = 1.0 - uy * uy;
+    a11 += m11;
+    a12 += m12;
+    a22 += m22;
+    r1 += m11 * out->side_cx[i] + m12 * out->side_cy[i];
+    r2 += m12 * out->side_cx[i] + m22 * out->side_cy[i];
+    ++lines;
+  }
+  const double det = a11 * a22 - a12 * a12;
+  if (lines >= 2 && std::fabs(det) > 1e-12) {
+    out->cx = (r1 * a22 - a12 * r2) / det;
+    out->cy = (a11 * r2 - a12 * r1) / det;
+  } else {
+    out->cx = out->cy = 0.0;
+    for (int i = 0; i < k; ++i) {
+      out->cx += out->side_cx[i] / k;
+      out->cy += out->side_cy[i] / k;
+    }
+  }
+  double sum = 0.0, lo = INFINITY, hi = -INFINITY;
+  for (int i = 0; i < k; ++i) {
+    out->L[i] = v[i] - (nx[i] * out->cx + ny[i] * out->cy);
+    sum += out->L[i];
+    lo = std::fmin(lo, out->L[i]);
+    hi = std::fmax(hi, out->L[i]);
+  }
+  for (int i = k; i < LBPF_MAX_FACETS; ++i)
+    out->support[i] = out->side_cx[i] = out->side_cy[i] = out->L[i] = nan;
+  out->L_avg = sum / k;
+  out->Q = hi / lo;
+  out->width = v[k] + v[k + 1];    // max x - min x
+  out->height = v[k + 2] + v[k + 3];
+  out->aspect = out->height > 0.0 ? out->width / out->height : nan;
+  return LBPF_OK;
+}
+
+int lbpf_growth_fit(const double* t, const double* L, int n, double* slope, double* intercept,
+                    double* r2) {
+  if (!t || !L || !slope || !intercept || !r2 || n < 2) return LBPF_EINVAL;
+  double tm = 0.0, Lm = 0.0;
+  for (int i = 0; i < n; ++i) {
+    if (!std::isfinite(t[i]) || !std::isfinite(L[i])) return LBPF_EINVAL;
+    tm += t[i];
+    Lm += L[i];
+  }
+  tm /= n;
+  Lm /= n;
+  double stt = 0.0, stl = 0.0;
+  for (int i = 0; i < n; ++i) {
+    stt += (t[i] - tm) * (t[i] - tm);
+    stl += (t[i] - tm) * (L[i] - Lm);
+  }
+  if (!(stt > 0.0)) return LBPF_EINVAL;
+  const double b = stl / stt, a = Lm - b * tm;
+  double res = 0.0, tot = 0.0;  // Eqs. 27, 28
+  for (int i = 0; i < n; ++i) {
+    const double e = L[i] - (a + b * t[i]);
+    res += e * e;
+    tot += (L[i] - Lm) * (L[i] - Lm);
+  }
+  *slope = b;
+  *intercept = a;
+  *r2 = tot > 0.0 ? 1.0 - res / tot : std::nan("");  // Eq. 26
+  return LBPF_OK;
+}
+
 int lbpf_set_stream(lbpf_t* h, void* stream) {
   if (!h) return LBPF_EINVAL;
   h->stream = static_cast<cudaStream_t>(stream);
@@ -556,6 +747,7 @@ void lbpf_destroy(lbpf_t* h) {
   if (h->d_partials) cudaFree(h->d_partials);
   if (h->d_diag) cudaFree(h->d_diag);
   if (h->d_fields) cudaFree(h->d_fields);
+  if (h->d_facets) cudaFree(h->d_facets);
   delete h;
 }
 

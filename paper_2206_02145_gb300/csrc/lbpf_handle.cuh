@@ -21,6 +21,7 @@ struct lbpf {
   double* d_diag = nullptr;  // [0..10] diag outputs, [16] solute total at init
   void* d_fields = nullptr;
   size_t fields_cap = 0;
+  double* d_facets = nullptr;  // facet-support scratch, then the results (first use)
   int icx = 0, icy = 0, icz = 0;
   size_t dev_bytes = 0;
   size_t es = 4;  // population element bytes

@@ -177,6 +177,29 @@ struct SeedArgs {
 };
 cudaError_t launch_init_seed(const Model& m, const SeedArgs& a, void* pops, void* phi_prev,
                              cudaStream_t s);
+// Convex polygon seed (2D): facets of outward unit normals (nx, ny) at
+// distances d from (cx, cy).
+constexpr int kMaxFacets = 12;
+struct PolygonArgs {
+  double cx, cy;
+  int k;
+  double nx[kMaxFacets], ny[kMaxFacets], d[kMaxFacets];
+  double u0, noise_amp;
+  unsigned long long seed;
+};
+cudaError_t launch_init_polygon(const Model& m, const PolygonArgs& a, void* pops, void* phi_prev,
+                                cudaStream_t s);
+// Support values of the phi = 0 contour of a 2D FP64 field phi[ny][nx] (no
+// padding) along up to kMaxFacets + 4 unit directions: out[j] = max over the
+// contour points p of p . dir_j, out[ndir] = the number of contour points.
+constexpr int kMaxDirs = kMaxFacets + 4;
+struct FacetDirs {
+  int n;
+  double dx[kMaxDirs], dy[kMaxDirs];
+};
+size_t facet_scratch_bytes();
+cudaError_t launch_facet_support(const double* phi, int nx, int ny, const FacetDirs& dirs,
+                                 double* scratch, double* out, cudaStream_t s);
 // Equilibrium state from device FP64 fields (rho/ux/uy/uz may be null).
 cudaError_t launch_init_fields(const Model& m, const double* phi, const double* U,
                                const double* rho, const double* ux, const double* uy,

@@ -48,7 +48,9 @@ def test_struct_layouts_match_header(lib, tmp_path):
               "lbpf_diag": [f for f, _ in lib.lbpf_diag._fields_],
               "lbpf_unet_cfg": [f for f, _ in lib.lbpf_unet_cfg._fields_],
               "lbpf_surrogate_cfg": [f for f, _ in lib.lbpf_surrogate_cfg._fields_],
-              "lbpf_surrogate_report": [f for f, _ in lib.lbpf_surrogate_report._fields_]}
+              "lbpf_surrogate_report": [f for f, _ in lib.lbpf_surrogate_report._fields_],
+              "lbpf_polygon_seed": [f for f, _ in lib.lbpf_polygon_seed._fields_],
+              "lbpf_facets": [f for f, _ in lib.lbpf_facets._fields_]}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "lbpf.h"', "int main(void){"]
     for st, fs in fields.items():
         lines.append(f'printf("{st} %zu\\n", sizeof({st}));')
@@ -100,3 +102,22 @@ def test_batch_validation_before_any_gpu_work(lib):
     assert e.value.code == lib.EINVAL
     assert lib._lib.lbpf_batch_step(None, 1) == lib.EINVAL
     assert lib._lib.lbpf_batch_count(None) == 0
+
+
+def test_growth_fit_host_logic_matches_the_oracle(lib):
+    # lbpf_growth_fit is host code: checked here without a GPU
+    from oracle import facets as F
+    import numpy as np
+    rng = np.random.default_rng(11)
+    for n in (2, 5, 40):
+        t = np.sort(rng.uniform(0, 20, n)) + np.arange(n)
+        L = 3.0 + 0.06 * t + rng.normal(0, 0.1, n)
+        got = lib.lbpf_growth_fit(t, L)
+        want = F.growth_fit(t, L)
+        assert np.allclose(got[:2], want[:2], rtol=0, atol=1e-12)
+        if n > 2:
+            assert abs(got[2] - want[2]) < 1e-12
+    assert np.isnan(lib.lbpf_growth_fit([0.0, 1.0, 2.0], [1.0, 1.0, 1.0])[2])
+    for t, L in (([1.0], [2.0]), ([1.0, 1.0], [2.0, 3.0]), ([0.0, np.nan], [1.0, 2.0])):
+        with pytest.raises(lib.LbpfError):
+            lib.lbpf_growth_fit(t, L)
