@@ -672,18 +672,27 @@ def run_facets(args, w):
             dist.barrier()
     ms = max_over_ranks([ev0.elapsed_time(ev1)], dist)[0]
     value = whole_job_rate(w["nodes"] * steps, world, ms * 1e-3) / 1e6
-    # the measurement alone: fields (phi in FP64) and the two support passes
-    nrep = 20
+    # the measurement alone: blocking calls (host round trip included), and
+    # the device part queued back to back (support pass, final reduction, the
+    # copy of 21 numbers; an upper bound of the device time where the host's
+    # launches are the slower side)
+    nrep = 50
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(nrep):
+        sim.facets(nrm)
+    call_us = (time.perf_counter() - t0) / nrep * 1e6
     torch.cuda.synchronize()
     ev0.record(stream)
     for _ in range(nrep):
-        sim.facets(nrm)
+        L.lbpf_facets_enqueue(sim.h, nrm)
     ev1.record(stream)
     torch.cuda.synchronize()
     meas_us = ev0.elapsed_time(ev1) / nrep * 1e3
-    # algorithmic bytes of one measurement: h read (9 x 4 B) and phi written
-    # (8 B) by the read-out, phi read (8 B) by the support pass
-    meas_bytes = (9 * 4 + 8 + 8) * w["nodes"]
+    L.lbpf_facets_collect(sim.h)
+    # algorithmic bytes of one measurement: the 9 h populations of every node
+    # read once (FP32)
+    meas_bytes = 9 * 4 * w["nodes"]
     peak, peak_kind = measured_peaks()
     ach = meas_bytes / (meas_us * 1e-6) / 1e9
     Lh = np.array(hist_L)
@@ -714,14 +723,18 @@ def run_facets(args, w):
                       "L_avg_growth_rate": favg[0], "L_avg_r2": favg[2],
                       "Q": float(Lh[-1].max() / Lh[-1].min()), "aspect": r["aspect"],
                       "centre": r["centre"].tolist(), "samples": len(hist_t)},
-            "measurement": {"us_per_call": meas_us, "share_of_run":
-                            (steps // every) * meas_us * 1e-3 / ms},
-            "roofline": {"bound": "hbm", "kernel": "facet measurement (read-out + support)",
+            "measurement": {"us_per_call": call_us, "device_us": meas_us, "share_of_run":
+                            (steps // every) * call_us * 1e-3 / ms},
+            "roofline": {"bound": "hbm",
+                         "kernel": "facet_support_kernel (+ result reset and copy)",
                          "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
-                         "peak_source": peak_kind, "traffic": None,
+                         "peak_source": peak_kind,
+                         "traffic": profiled_traffic(dict(kernel="facet_support_kernel",
+                                                          nx=w["nx"], storage="fp32",
+                                                          src=SRC_FACETS)),
                          "algorithmic_bytes_per_launch": meas_bytes},
             "cpu_baseline": cpu,
-            "gpu_launches": steps + 3 * (steps // every),
+            "gpu_launches": steps + 2 * (steps // every),
             "clocks": clk.summary(),
             "diag": {"step": d["step"], "solute_drift_rel": d["solute_drift_rel"]},
         }), flush=True)

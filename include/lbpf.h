@@ -245,6 +245,15 @@ int lbpf_diagnostics(lbpf_t* h, lbpf_diag* out);
 int lbpf_measure_facets(lbpf_t* h, int k, const double* nx, const double* ny,
                         lbpf_facets* out);
 
+/* The same in two halves.  lbpf_facets_enqueue validates as above and queues
+ * the device part on the handle's stream (the state at that point of the
+ * stream is measured; the normals are copied); asynchronous.
+ * lbpf_facets_collect waits for it and fills *out (synchronising); ESTATE if
+ * nothing is queued.  A second enqueue before the collect replaces the
+ * first. */
+int lbpf_facets_enqueue(lbpf_t* h, int k, const double* nx, const double* ny);
+int lbpf_facets_collect(lbpf_t* h, lbpf_facets* out);
+
 /* Straight-line fit L'(t) = intercept + slope t of a size history of n >= 2
  * points (host arrays), and its coefficient of determination R^2 =
  * 1 - A_res / A_tot (Eqs. 26-28); R^2 is NaN when every L is the same.

@@ -116,7 +116,8 @@ EXPORTED = ("lbpf_params_default", "lbpf_create", "lbpf_init_seed", "lbpf_init_f
             "lbpf_unet_last_error", "lbpf_unet_destroy", "lbpf_unet_set_tensor_path",
             "lbpf_unet_status", "lbpf_surrogate_sample",
             "lbpf_surrogate_target", "lbpf_surrogate_advance", "lbpf_init_polygon",
-            "lbpf_measure_facets", "lbpf_growth_fit")
+            "lbpf_measure_facets", "lbpf_growth_fit", "lbpf_facets_enqueue",
+            "lbpf_facets_collect")
 
 
 def _load_library():
@@ -181,6 +182,8 @@ def _load_library():
     lib.lbpf_init_polygon.argtypes = [vp, ctypes.POINTER(lbpf_polygon_seed)]
     lib.lbpf_measure_facets.argtypes = [vp, ctypes.c_int, dp, dp, ctypes.POINTER(lbpf_facets)]
     lib.lbpf_growth_fit.argtypes = [dp, dp, ctypes.c_int, dp, dp, dp]
+    lib.lbpf_facets_enqueue.argtypes = [vp, ctypes.c_int, dp, dp]
+    lib.lbpf_facets_collect.argtypes = [vp, ctypes.POINTER(lbpf_facets)]
     keep = ("lbpf_state_bytes", "lbpf_device_bytes", "lbpf_last_error", "lbpf_destroy",
             "lbpf_batch_instance", "lbpf_batch_last_error", "lbpf_batch_destroy",
             "lbpf_unet_param_count", "lbpf_unet_device_bytes", "lbpf_unet_last_error",
@@ -247,13 +250,32 @@ def lbpf_init_polygon(h: int, cx, cy, normals, dist, u0, noise_amp, seed) -> Non
     _check(h, _lib.lbpf_init_polygon(h, ctypes.byref(s)))
 
 
+def _normals_xy(normals):
+    n = np.ascontiguousarray(np.asarray(normals, np.float64).reshape(-1, 2))
+    return np.ascontiguousarray(n[:, 0]), np.ascontiguousarray(n[:, 1])
+
+
 def lbpf_measure_facets(h: int, normals) -> dict:
     """Crystal shape along the facet normals [k, 2] (k even, counter-clockwise,
     normal i + k/2 opposite to normal i)."""
-    n = np.ascontiguousarray(np.asarray(normals, np.float64).reshape(-1, 2))
-    nx, ny = np.ascontiguousarray(n[:, 0]), np.ascontiguousarray(n[:, 1])
+    nx, ny = _normals_xy(normals)
     f = lbpf_facets()
     _check(h, _lib.lbpf_measure_facets(h, int(nx.size), _dptr(nx), _dptr(ny), ctypes.byref(f)))
+    return _facets_dict(f)
+
+
+def lbpf_facets_enqueue(h: int, normals) -> None:
+    nx, ny = _normals_xy(normals)
+    _check(h, _lib.lbpf_facets_enqueue(h, int(nx.size), _dptr(nx), _dptr(ny)))
+
+
+def lbpf_facets_collect(h: int) -> dict:
+    f = lbpf_facets()
+    _check(h, _lib.lbpf_facets_collect(h, ctypes.byref(f)))
+    return _facets_dict(f)
+
+
+def _facets_dict(f) -> dict:
     k = f.nfacets
     return {"points": int(f.points), "support": np.array(f.support[:k]),
             "side_centre": np.stack([np.array(f.side_cx[:k]), np.array(f.side_cy[:k])], axis=1),

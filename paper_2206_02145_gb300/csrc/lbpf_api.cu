@@ -574,11 +574,10 @@ int lbpf_diagnostics(lbpf_t* h, lbpf_diag* out) {
   return LBPF_OK;
 }
 
-int lbpf_measure_facets(lbpf_t* h, int k, const double* nx, const double* ny,
-                        lbpf_facets* out) {
+int lbpf_facets_enqueue(lbpf_t* h, int k, const double* nx, const double* ny) {
   int rc = check_handle(h);
   if (rc) return rc;
-  if (!out || !nx || !ny) return fail(h, LBPF_EINVAL, "null argument");
+  if (!nx || !ny) return fail(h, LBPF_EINVAL, "null argument");
   if (!h->initialized) return fail(h, LBPF_ESTATE, "facets before init");
   if (h->m.dim != 2) return fail(h, LBPF_EINVAL, "facet measurement is 2D");
   if (k < 4 || k > LBPF_MAX_FACETS || k % 2)
@@ -592,39 +591,48 @@ int lbpf_measure_facets(lbpf_t* h, int k, const double* nx, const double* ny,
     if (!(nx[i] * ny[nb] - ny[i] * nx[nb] > 1e-6))
       return fail(h, LBPF_EINVAL, "facets %d, %d: normals not in counter-clockwise order", i, nb);
   }
-  const size_t n = size_t(h->m.nx) * h->m.ny;
-  if ((rc = ensure_fields_buffer(h, n * sizeof(double)))) return rc;
+  const size_t nres = sizeof(unsigned long long) * (lbk::kMaxDirs + 1);
   if (!h->d_facets) {
-    const size_t b = lbk::facet_scratch_bytes() + 32 * sizeof(double);
-    cudaError_t e = cudaMalloc(&h->d_facets, b);
-    if (e != cudaSuccess) return fail(h, LBPF_ENOMEM, "facet scratch: %s", cudaGetErrorString(e));
-    h->dev_bytes += b;
+    cudaError_t e = cudaMalloc(&h->d_facets, nres);
+    if (e == cudaSuccess) e = cudaMallocHost(&h->h_facets, nres);
+    if (e != cudaSuccess) return fail(h, LBPF_ENOMEM, "facet results: %s", cudaGetErrorString(e));
+    h->dev_bytes += nres;
   }
   // directions: the k normals, then +x, -x, +y, -y for the extents
   lbk::FacetDirs d{};
   d.n = k + 4;
   for (int i = 0; i < k; ++i) {
-    d.dx[i] = nx[i];
-    d.dy[i] = ny[i];
+    d.dx[i] = h->facet_nx[i] = nx[i];
+    d.dy[i] = h->facet_ny[i] = ny[i];
   }
   const double ax[4] = {1.0, -1.0, 0.0, 0.0}, ay[4] = {0.0, 0.0, 1.0, -1.0};
   for (int j = 0; j < 4; ++j) {
     d.dx[k + j] = ax[j];
     d.dy[k + j] = ay[j];
   }
-  double* res = h->d_facets + lbk::facet_scratch_bytes() / sizeof(double);
-  CK(h, lbk::launch_fields(h->m, h->pops[h->cur], h->phi[h->cur], h->cur, LBPF_FIELD_PHI, 1,
-                            h->d_fields, h->stream));
-  CK(h, lbk::launch_facet_support(static_cast<const double*>(h->d_fields), h->m.nx, h->m.ny, d,
-                                   h->d_facets, res, h->stream));
-  double v[lbk::kMaxDirs + 1];
-  CK(h, cudaMemcpyAsync(v, res, sizeof(double) * (k + 5), cudaMemcpyDeviceToHost, h->stream));
-  if ((rc = check_device_error(h))) return rc;
+  h->facet_k = 0;
+  CK(h, lbk::launch_facet_support(h->m, h->pops[h->cur], d, h->d_facets, h->stream));
+  CK(h, cudaMemcpyAsync(h->h_facets, h->d_facets, nres, cudaMemcpyDeviceToHost, h->stream));
+  h->facet_k = k;
+  return LBPF_OK;
+}
 
+int lbpf_facets_collect(lbpf_t* h, lbpf_facets* out) {
+  int rc = check_handle(h);
+  if (rc) return rc;
+  if (!out) return fail(h, LBPF_EINVAL, "null argument");
+  if (!h->facet_k) return fail(h, LBPF_ESTATE, "no facet measurement enqueued");
+  if ((rc = check_device_error(h))) return rc;
+  const int k = h->facet_k;
+  const double* nx = h->facet_nx;
+  const double* ny = h->facet_ny;
+  double v[lbk::kMaxDirs];  // the k supports, then max x, -min x, max y, -min y
+  for (int j = 0; j < k + 4; ++j) v[j] = lbk::facet_key_value(h->h_facets[j]);
+  h->facet_k = 0;
   const double nan = std::nan("");
   std::memset(out, 0, sizeof(*out));
   out->nfacets = k;
-  out->points = (long long)v[k + 4];
+  out->points = (long long)h->h_facets[lbk::kMaxDirs];
   if (out->points == 0) {
     for (int i = 0; i < LBPF_MAX_FACETS; ++i)
       out->support[i] = out->side_cx[i] = out->side_cy[i] = out->L[i] = nan;
@@ -693,6 +701,12 @@ int lbpf_measure_facets(lbpf_t* h, int k, const double* nx, const double* ny,
   return LBPF_OK;
 }
 
+int lbpf_measure_facets(lbpf_t* h, int k, const double* nx, const double* ny,
+                        lbpf_facets* out) {
+  int rc = lbpf_facets_enqueue(h, k, nx, ny);
+  return rc ? rc : lbpf_facets_collect(h, out);
+}
+
 int lbpf_growth_fit(const double* t, const double* L, int n, double* slope, double* intercept,
                     double* r2) {
   if (!t || !L || !slope || !intercept || !r2 || n < 2) return LBPF_EINVAL;
@@ -748,6 +762,7 @@ void lbpf_destroy(lbpf_t* h) {
   if (h->d_diag) cudaFree(h->d_diag);
   if (h->d_fields) cudaFree(h->d_fields);
   if (h->d_facets) cudaFree(h->d_facets);
+  if (h->h_facets) cudaFreeHost(h->h_facets);
   delete h;
 }
 

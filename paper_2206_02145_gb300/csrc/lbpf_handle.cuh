@@ -21,7 +21,10 @@ struct lbpf {
   double* d_diag = nullptr;  // [0..10] diag outputs, [16] solute total at init
   void* d_fields = nullptr;
   size_t fields_cap = 0;
-  double* d_facets = nullptr;  // facet-support scratch, then the results (first use)
+  unsigned long long* d_facets = nullptr;  // facet-support results (first use)
+  unsigned long long* h_facets = nullptr;  // their pinned host copy
+  int facet_k = 0;             // normals of the enqueued measurement (0: none pending)
+  double facet_nx[LBPF_MAX_FACETS], facet_ny[LBPF_MAX_FACETS];
   int icx = 0, icy = 0, icz = 0;
   size_t dev_bytes = 0;
   size_t es = 4;  // population element bytes

@@ -189,17 +189,19 @@ struct PolygonArgs {
 };
 cudaError_t launch_init_polygon(const Model& m, const PolygonArgs& a, void* pops, void* phi_prev,
                                 cudaStream_t s);
-// Support values of the phi = 0 contour of a 2D FP64 field phi[ny][nx] (no
-// padding) along up to kMaxFacets + 4 unit directions: out[j] = max over the
-// contour points p of p . dir_j, out[ndir] = the number of contour points.
+// Support values of the phi = 0 contour of a 2D state (phi from the h
+// populations) along up to kMaxFacets + 4 unit directions, into out[0 ..
+// kMaxDirs] on the device: out[j] the order-preserving integer key of max over
+// the contour points p of p . dir_j (facet_key_value turns it back into the
+// double; key 0: no point), out[kMaxDirs] the number of contour points.
 constexpr int kMaxDirs = kMaxFacets + 4;
 struct FacetDirs {
   int n;
   double dx[kMaxDirs], dy[kMaxDirs];
 };
-size_t facet_scratch_bytes();
-cudaError_t launch_facet_support(const double* phi, int nx, int ny, const FacetDirs& dirs,
-                                 double* scratch, double* out, cudaStream_t s);
+cudaError_t launch_facet_support(const Model& m, const void* pops, const FacetDirs& dirs,
+                                 unsigned long long* out, cudaStream_t s);
+double facet_key_value(unsigned long long key);
 // Equilibrium state from device FP64 fields (rho/ux/uy/uz may be null).
 cudaError_t launch_init_fields(const Model& m, const double* phi, const double* U,
                                const double* rho, const double* ux, const double* uy,

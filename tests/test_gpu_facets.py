@@ -156,3 +156,23 @@ def test_no_crystal_and_invalid_arguments(P, L):
     with pytest.raises(L.LbpfError) as e:
         q.init_polygon(8.0, 8.0, L.hexagon_normals(), np.full(6, 4.0))
     assert e.value.code == L.EINVAL
+
+
+def test_enqueue_measures_the_state_at_its_point_of_the_stream(P, L):
+    p = hex_case(P, 128)
+    nrm, d = L.hexagonal_seed(80.0, 0.1 + math.pi / 6)
+    a = P.lib_sim(p, "fp32")
+    a.init_polygon(64.0, 64.0, nrm, d, 0.35, 0.01, 4)
+    a.step(100)
+    want = a.facets(nrm)
+    L.lbpf_facets_enqueue(a.h, nrm)
+    a.step(300)  # queued behind the measurement
+    got = L.lbpf_facets_collect(a.h)
+    assert got["points"] == want["points"]
+    for k in ("support", "centre", "L"):  # the same state: bit for bit
+        assert np.array_equal(got[k], want[k]), k
+    later = a.facets(nrm)
+    assert later["L_avg"] > got["L_avg"]
+    with pytest.raises(L.LbpfError) as e:
+        L.lbpf_facets_collect(a.h)
+    assert e.value.code == L.ESTATE
