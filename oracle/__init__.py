@@ -69,6 +69,8 @@ def _load():
         lib.orc_destroy.argtypes = [vp]
         lib.orc_init_seed.argtypes = [vp] + [ctypes.c_double] * 6 + [ctypes.c_uint64]
         lib.orc_init_fields.argtypes = [vp] + [dp] * 6
+        lib.orc_set_solid.argtypes = [vp, ctypes.c_void_p]
+        lib.orc_set_solid.restype = ctypes.c_int
         lib.orc_init_polygon.argtypes = ([vp, ctypes.c_double, ctypes.c_double, ctypes.c_int]
                                          + [dp] * 3 + [ctypes.c_double] * 2 + [ctypes.c_uint64])
         lib.orc_step.argtypes = [vp, ctypes.c_int, ctypes.c_int]
@@ -183,6 +185,17 @@ class Oracle:
         assert d.size == nx.size
         self._lib.orc_init_polygon(self._h, cx, cy, int(d.size), _ptr(nx), _ptr(ny), _ptr(d),
                                    u0, noise_amp, seed)
+
+    def set_solid(self, mask):
+        """Solid nodes (2D): mask [ny, nx], nonzero = solid; None removes it."""
+        if mask is None:
+            rc = self._lib.orc_set_solid(self._h, None)
+        else:
+            m = np.ascontiguousarray(np.asarray(mask).reshape(-1) != 0, dtype=np.uint8)
+            assert m.size == self.p.nodes
+            rc = self._lib.orc_set_solid(self._h, m.ctypes.data)
+        if rc != 0:
+            raise ValueError("solid mask rejected (3D, or a solid inlet/outlet column)")
 
     def init_fields(self, phi, U, rho=None, ux=None, uy=None, uz=None):
         arrs = []

@@ -118,6 +118,7 @@ struct orc_sim {
   /* per-node quantities of the current time level */
   double *phi, *U, *rho, *u[3], *us[3], *F[3], *phihat, *K, *tauU, *dphidt;
   double *grad[3], *as, *a2, *tauphi, *N[3], *Q;
+  unsigned char* solid; /* 2D solid mask (1 = solid node), NULL = none */
 };
 
 static double* zalloc(size_t n) { return (double*)calloc(n ? n : 1, sizeof(double)); }
@@ -190,10 +191,26 @@ void orc_destroy(orc_sim* s) {
   }
   free(s->phihat); free(s->K); free(s->tauU); free(s->dphidt);
   free(s->as); free(s->a2); free(s->tauphi); free(s->Q);
+  free(s->solid);
   free(s);
 }
 
 long long orc_step_count(const orc_sim* s) { return s->step; }
+
+int orc_set_solid(orc_sim* s, const unsigned char* mask) {
+  if (!mask) {
+    free(s->solid);
+    s->solid = NULL;
+    return 0;
+  }
+  if (s->p.dim != 2) return -1;
+  if (s->p.bc[0] == ORC_INLET_OUTLET) /* the inlet and outlet columns stay fluid */
+    for (int y = 0; y < s->p.ny; ++y)
+      if (mask[y * s->p.nx] || mask[y * s->p.nx + s->p.nx - 1]) return -1;
+  if (!s->solid) s->solid = (unsigned char*)malloc((size_t)s->n);
+  for (int i = 0; i < s->n; ++i) s->solid[i] = mask[i] ? 1 : 0;
+  return 0;
+}
 
 static double clamp1(double v) { return v < -1.0 ? -1.0 : (v > 1.0 ? 1.0 : v); }
 
@@ -252,6 +269,22 @@ static int grad_neighbor(const orc_sim* s, const int x[3], const int c[3]) {
   return (y[2] * s->p.ny + y[1]) * s->p.nx + y[0];
 }
 
+/* Gradient neighbour with solid nodes (walls and obstacles of Sec. 3.1.2):
+ * a solid node in the stencil is replaced by the first fluid node among
+ * x + (c_x, 0), x + (0, c_y) and x itself (each mapped like any stencil
+ * neighbour) -- for a straight wall this is the nearest-node copy of the
+ * domain walls, a zero normal derivative. */
+static int grad_neighbor_masked(const orc_sim* s, const int x[3], const int c[3]) {
+  int j = grad_neighbor(s, x, c);
+  if (!s->solid || !s->solid[j]) return j;
+  const int cx[3] = {c[0], 0, 0}, cy[3] = {0, c[1], 0}, c0[3] = {0, 0, 0};
+  j = grad_neighbor(s, x, cx);
+  if (!s->solid[j]) return j;
+  j = grad_neighbor(s, x, cy);
+  if (!s->solid[j]) return j;
+  return grad_neighbor(s, x, c0);
+}
+
 enum { SRC_NODE = 0, SRC_INLET = 1, SRC_BOUNCE = 2 };
 
 /* Source of the population arriving at x along c (pull form s = x - c). */
@@ -284,6 +317,10 @@ static int stream_source(const orc_sim* s, const int x[3], const int c[3], int* 
     return SRC_INLET;
   }
   *sidx = (y[2] * s->p.ny + y[1]) * s->p.nx + y[0];
+  if (s->solid && s->solid[*sidx]) { /* half-way bounce-back at a solid node */
+    *sidx = (x[2] * s->p.ny + x[1]) * s->p.nx + x[0];
+    return SRC_BOUNCE;
+  }
   return SRC_NODE;
 }
 
@@ -327,7 +364,7 @@ static void node_gradient_terms(orc_sim* s, int i) {
   int x[3] = {i % p->nx, (i / p->nx) % p->ny, i / (p->nx * p->ny)};
   double gr[3] = {0.0, 0.0, 0.0};
   for (int a = 1; a < s->LG.q; ++a) {
-    int j = grad_neighbor(s, x, s->LG.c[a]);
+    int j = grad_neighbor_masked(s, x, s->LG.c[a]);
     for (int d = 0; d < 3; ++d) gr[d] += s->LG.w[a] * s->LG.c[a][d] * s->phi[j];
   }
   for (int d = 0; d < 3; ++d) gr[d] /= s->LG.cs2;
@@ -401,6 +438,14 @@ static double h_inlet(const orc_sim* s, int a) { return -s->LS.w[a]; }
 static void update_node(orc_sim* s, int i) {
   const orc_params* p = &s->p;
   int n = s->n;
+  if (s->solid && s->solid[i]) { /* solid nodes keep their state */
+    for (int a = 0; a < s->LF.q && p->flow; ++a) s->fn[(size_t)a * n + i] = s->f[(size_t)a * n + i];
+    for (int a = 0; a < s->LS.q; ++a) {
+      s->gn[(size_t)a * n + i] = s->g[(size_t)a * n + i];
+      s->hn[(size_t)a * n + i] = s->h[(size_t)a * n + i];
+    }
+    return;
+  }
   int x[3] = {i % p->nx, (i / p->nx) % p->ny, i / (p->nx * p->ny)};
   int src;
   if (p->flow) {

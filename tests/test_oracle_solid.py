@@ -1,0 +1,156 @@
+"""Pins of the oracle's solid nodes (walls and obstacles; the paper's reactor
+walls and baffles, Sec. 3.1.2 and Sec. 3.2): half-way bounce-back for f, g
+and h, frozen solid nodes, zero normal phi-derivative in the gradient.
+
+Pinned against: the closed-form Poiseuille profile in a channel cut out of a
+periodic domain by solid rows; the domain walls (rows of solid nodes inside
+the grid reproduce the wall boundary condition, whose own pin is the
+Poiseuille profile of test_oracle_pins); conservation of mass and of the
+solute invariant around obstacles; mirror symmetry; fixed points.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from oracle import Params, PERIODIC, WALL, INLET_OUTLET
+
+
+@pytest.fixture(scope="module")
+def orc(oracle_mod):
+    return oracle_mod
+
+
+def test_poiseuille_in_a_masked_channel(orc):
+    # walls at rows 3 and 20 of a periodic 24-row domain: the fluid rows 4..19
+    # see half-way walls at y = 3.5 and 19.5, exactly as the domain walls
+    tau, H, b = 0.5 + math.sqrt(3.0 / 16.0), 16, 1e-6
+    ny = 24
+    p = Params(nx=4, ny=ny, flow=1, tau_f=tau, eps=0.0, lambda_=0.0,
+               bc=(PERIODIC, PERIODIC, PERIODIC), body=(b, 0.0, 0.0))
+    o = O.Oracle(p)
+    mask = np.zeros((ny, 4), np.uint8)
+    mask[3, :] = mask[20, :] = 1
+    o.set_solid(mask)
+    n = p.nodes
+    o.init_fields(-np.ones(n), np.zeros(n), np.ones(n), np.zeros(n), np.zeros(n))
+    f0 = o.pops("f")
+    o.step(25000)
+    nu = (tau - 0.5) / 3.0
+    y = np.arange(H) + 0.5
+    exact = b / (2 * nu) * y * (H - y)
+    got = o.fields()["ux"][4:20, 0]
+    assert np.abs(got / exact - 1).max() < 1e-6, np.abs(got / exact - 1).max()
+    # the solid rows kept their initial state
+    assert np.array_equal(o.pops("f")[:, [3, 20]], f0[:, [3, 20]])
+
+
+@pytest.mark.parametrize("flow", [0, 1])
+def test_solid_rows_reproduce_the_domain_walls(orc, flow):
+    # A: periodic x, walls in y, ny = 30.  B: periodic x and y, ny = 32, rows
+    # 0 and 31 solid.  Same fields on the fluid rows (a seed touching the
+    # lower wall, so that the gradient next to the wall is exercised).
+    nx, ny = 40, 30
+    kw = dict(nx=nx, flow=flow, eps=0.04, fold=4, theta0=0.3,
+              body=(2e-6, 0.0, 0.0) if flow else (0.0, 0.0, 0.0))
+    pa = Params(ny=ny, bc=(PERIODIC, WALL, PERIODIC), **kw)
+    pb = Params(ny=ny + 2, bc=(PERIODIC, PERIODIC, PERIODIC), **kw)
+    rng = np.random.default_rng(3)
+    y, x = np.mgrid[0:ny, 0:nx].astype(float)
+    phi = np.tanh((7.0 - np.hypot(x - 17.3, y - 3.2)) / (math.sqrt(2) * 2.0))
+    phi += 0.01 * rng.uniform(-1, 1, phi.shape)
+    U = 0.35 + 0.01 * rng.uniform(-1, 1, phi.shape)
+    ux = 0.01 * np.sin(2 * np.pi * y / ny) if flow else np.zeros_like(phi)
+    a = O.Oracle(pa)
+    a.init_fields(phi, U, None, ux, None)
+    pad = lambda f, v: np.concatenate([np.full((1, nx), v), f, np.full((1, nx), v)])
+    b = O.Oracle(pb)
+    b.init_fields(pad(phi, -1.0), pad(U, 0.35), None, pad(ux, 0.0), None)
+    mask = np.zeros((ny + 2, nx), np.uint8)
+    mask[0, :] = mask[-1, :] = 1
+    b.set_solid(mask)
+    a.step(200)
+    b.step(200)
+    fa, fb = a.fields(), b.fields()
+    for k in ("phi", "U", "rho", "ux", "uy"):
+        assert np.abs(fa[k] - fb[k][1:-1]).max() < 1e-13, k
+    for k in "fgh":
+        if k == "f" and not flow:
+            continue
+        assert np.abs(a.pops(k) - b.pops(k)[:, 1:-1]).max() < 1e-13, k
+    a.close()
+    b.close()
+
+
+def baffle_mask(nx, ny, x0, y0, y1, w=2):
+    m = np.zeros((ny, nx), np.uint8)
+    m[y0:y1, x0:x0 + w] = 1
+    return m
+
+
+def test_conservation_around_obstacles(orc):
+    nx, ny = 56, 44
+    p = Params(nx=nx, ny=ny, flow=1, eps=0.05, fold=6, body=(3e-6, 1e-6, 0.0))
+    o = O.Oracle(p)
+    mask = baffle_mask(nx, ny, 8, 10, 30) | baffle_mask(nx, ny, 40, 25, 41, 3)
+    mask[2:5, 20:24] = 1
+    o.init_seed(25.0, 20.0, 0.0, 6.0, 0.4, 0.01, 7)
+    o.set_solid(mask)
+    d0 = o.diag(25, 20)
+    o.step(200)
+    d1 = o.diag(25, 20)
+    assert d1["solid_volume"] > d0["solid_volume"] * 1.02  # the crystal grew
+    assert abs(d1["solute_total"] / d0["solute_total"] - 1) < 1e-12
+    assert abs(d1["mass_total"] / d0["mass_total"] - 1) < 1e-12
+    f = o.fields()
+    assert np.abs(f["ux"]).max() > 1e-5  # the flow went round the obstacles
+
+
+def test_mirror_symmetry_with_an_obstacle(orc):
+    # obstacle and seed symmetric about y = (ny - 1)/2, flow along x
+    nx, ny = 48, 40
+    p = Params(nx=nx, ny=ny, flow=1, eps=0.03, fold=4, bc=(INLET_OUTLET, PERIODIC, PERIODIC),
+               u_inlet=0.01, u0_inlet=0.3)
+    o = O.Oracle(p)
+    mask = np.zeros((ny, nx), np.uint8)
+    mask[12:28, 10:12] = 1
+    y, x = np.mgrid[0:ny, 0:nx].astype(float)
+    phi = np.tanh((6.0 - np.hypot(x - 30.0, y - (ny - 1) / 2)) / (math.sqrt(2) * 2.0))
+    o.init_fields(phi, np.full_like(phi, 0.3), None, np.full_like(phi, 0.01), None)
+    o.set_solid(mask)
+    o.step(150)
+    f = o.fields()
+    for k in ("phi", "U", "rho", "ux"):
+        assert np.abs(f[k] - f[k][::-1]).max() < 1e-12, k
+    assert np.abs(f["uy"] + f["uy"][::-1]).max() < 1e-12
+    assert np.abs(f["uy"]).max() > 1e-5  # the flow was deflected
+
+
+def test_liquid_at_rest_is_a_fixed_point_with_obstacles(orc):
+    p = Params(nx=32, ny=24, flow=1, eps=0.05, fold=4)
+    o = O.Oracle(p)
+    n = p.nodes
+    o.init_fields(-np.ones(n), np.full(n, 0.2))
+    o.set_solid(baffle_mask(32, 24, 12, 5, 19))
+    s0 = o.fields()
+    o.step(50)
+    s1 = o.fields()
+    for k in ("phi", "U", "rho", "ux", "uy"):
+        assert np.abs(s1[k] - s0[k]).max() < 1e-14, k
+
+
+def test_mask_rejections(orc):
+    p = Params(nx=16, ny=12, flow=1, bc=(INLET_OUTLET, PERIODIC, PERIODIC), u_inlet=0.01)
+    o = O.Oracle(p)
+    m = np.zeros((12, 16), np.uint8)
+    m[3, 0] = 1
+    with pytest.raises(ValueError):
+        o.set_solid(m)
+    m[3, 0] = 0
+    m[3, 15] = 1
+    with pytest.raises(ValueError):
+        o.set_solid(m)
+    m[3, 15] = 0
+    m[3, 7] = 1
+    o.set_solid(m)
