@@ -51,6 +51,14 @@ WORKLOADS = {
                storage="fp32", kernel="step2d_tma_kernel", src=SRC_2D,
                sample=dict(nx=256, ny=256, seed=(75.0, 128.0, 0.0, 16.0, 0.4, 0.01, 1))),
     "c2_fp16": dict(base="c2", storage="fp16"),
+    "f2": dict(base="c2", desc_note=True,
+               desc="2D 1024x1024 coupled LB, inflow 0.01, seed R=16 at x=300, U0=0.4, 5-fold "
+                    "eps 0.03, with a baffle of solid nodes 4 lu thick and 320 lu long at x=150 "
+                    "in front of the inlet (dimensions invented: the paper shows its baffles "
+                    "only in a figure)",
+               baffle=dict(x0=150, y0=352, y1=672, w=4), kernel="step2d_tma_kernel_mask",
+               sample=dict(nx=256, ny=256, seed=(75.0, 128.0, 0.0, 16.0, 0.4, 0.01, 1),
+                           baffle=dict(x0=37, y0=88, y1=168, w=1))),
     "f1": dict(desc="2D 1024x1024 coupled LB, inflow 0.01, hexagonal seed (perimeter 120 lu, "
                     "side normals at 0.1 + pi/6 + k pi/3) at x=300, U0=0.4, 6-fold eps 0.03 at "
                     "theta0 0.1; crystal shape (side lengths, centre, Q, aspect ratio) measured "
@@ -146,6 +154,8 @@ def workload(name):
     q = (9 if w["dim"] == 2 else 19) * w["flow"] + 2 * (9 if w["dim"] == 2 else 7)
     ring = 8 if w["storage"] == "fp64" else 4
     w["bytes_per_lup"] = 2 * q * ELEM[w["storage"]] + 2 * ring
+    if w.get("baffle"):
+        w["bytes_per_lup"] += 1  # the solid mask
     if w["dim"] == 2 and ELEM[w["storage"]] == 2:
         # the per-node g reference of 16-bit 2D storage (FP16): the node's own
         # read, its neighbours' encoding reference read, the new one written
@@ -342,6 +352,8 @@ def oracle_problem(w):
         o.init_polygon(g["cx"], g["cy"], nrm, d, g["u0"], g["noise"], g["seed"])
     else:
         o.init_seed(*s["seed"])
+    if s.get("baffle"):
+        o.set_solid(baffle_mask(s["nx"], s["ny"], s["baffle"]))
     return p, o
 
 
@@ -351,6 +363,15 @@ def hexagon(perimeter, theta):
     import numpy as np
     a = theta + np.pi / 3.0 * np.arange(6)
     return np.stack([np.cos(a), np.sin(a)], axis=1), np.full(6, perimeter / 6.0 * 3 ** 0.5 / 2)
+
+
+def baffle_mask(nx, ny, b):
+    """Solid mask [ny, nx] with a baffle of b["w"] columns at b["x0"], rows
+    b["y0"] .. b["y1"] - 1."""
+    import numpy as np
+    m = np.zeros((ny, nx), np.uint8)
+    m[b["y0"]:b["y1"], b["x0"]:b["x0"] + b["w"]] = 1
+    return m
 
 
 def oracle_sample(w, seconds: float, threads: int):
@@ -447,6 +468,8 @@ def main():
         stepper = batch
     else:
         sim = L.Sim(stream=stream.cuda_stream, **lib_params(w, L))
+        if w.get("baffle"):
+            sim.set_solid(baffle_mask(w["nx"], w["ny"], w["baffle"]))
         sim.init_seed(*w["seed"])
         sims = [sim]
         stepper = sim

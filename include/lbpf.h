@@ -262,6 +262,22 @@ int lbpf_facets_collect(lbpf_t* h, lbpf_facets* out);
 int lbpf_growth_fit(const double* t, const double* L, int n, double* slope, double* intercept,
                     double* r2);
 
+/* Solid nodes, 2D (the reactor walls and baffles of Sec. 3.1.2 and 3.2):
+ * mask is a host array of nx*ny bytes (x fastest), nonzero = solid, read
+ * during the call; NULL removes the mask.  A fluid node sends what it would
+ * stream into a solid node back into itself reversed (half-way bounce-back,
+ * for f, g and h: no flow through, zero flux of U and phi); in the phi
+ * gradient a solid neighbour counts as the first fluid node among
+ * (x + c_x, y), (x, y + c_y) and (x, y) (zero normal derivative; for a
+ * straight row of solid nodes this is exactly the LBPF_BC_WALL boundary).
+ * Solid nodes keep their state (both buffers hold it; the field read-out and
+ * the diagnostics include their constant values).  Tiles that touch no solid
+ * node run at full speed.  With LBPF_BC_INLET_OUTLET the first and last
+ * columns must be fluid.  EINVAL for 3D.  The mask is configuration, not
+ * state: lbpf_write_state keeps it.  The block propagator refuses a handle
+ * with solid nodes.  Synchronising. */
+int lbpf_set_solid(lbpf_t* h, const uint8_t* mask);
+
 /* Rebind the handle to another stream (e.g. the caller's current stream). */
 int lbpf_set_stream(lbpf_t* h, void* stream);
 

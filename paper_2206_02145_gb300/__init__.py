@@ -117,7 +117,7 @@ EXPORTED = ("lbpf_params_default", "lbpf_create", "lbpf_init_seed", "lbpf_init_f
             "lbpf_unet_status", "lbpf_surrogate_sample",
             "lbpf_surrogate_target", "lbpf_surrogate_advance", "lbpf_init_polygon",
             "lbpf_measure_facets", "lbpf_growth_fit", "lbpf_facets_enqueue",
-            "lbpf_facets_collect")
+            "lbpf_facets_collect", "lbpf_set_solid")
 
 
 def _load_library():
@@ -184,6 +184,7 @@ def _load_library():
     lib.lbpf_growth_fit.argtypes = [dp, dp, ctypes.c_int, dp, dp, dp]
     lib.lbpf_facets_enqueue.argtypes = [vp, ctypes.c_int, dp, dp]
     lib.lbpf_facets_collect.argtypes = [vp, ctypes.POINTER(lbpf_facets)]
+    lib.lbpf_set_solid.argtypes = [vp, vp]
     keep = ("lbpf_state_bytes", "lbpf_device_bytes", "lbpf_last_error", "lbpf_destroy",
             "lbpf_batch_instance", "lbpf_batch_last_error", "lbpf_batch_destroy",
             "lbpf_unet_param_count", "lbpf_unet_device_bytes", "lbpf_unet_last_error",
@@ -324,6 +325,15 @@ def rhombic_seed(perimeter: float, theta: float = 0.0, acute: float = np.pi / 3.
     return rhombus_normals(theta, acute), np.full(4, side * np.sin(acute) / 2.0)
 
 
+def lbpf_set_solid(h: int, mask) -> None:
+    """Solid nodes (2D): mask [ny, nx] (nonzero = solid), or None to remove."""
+    if mask is None:
+        _check(h, _lib.lbpf_set_solid(h, None))
+        return
+    m = np.ascontiguousarray(np.asarray(mask).reshape(-1) != 0, dtype=np.uint8)
+    _check(h, _lib.lbpf_set_solid(h, ctypes.c_void_p(m.ctypes.data)))
+
+
 def lbpf_init_fields(h: int, phi, U, rho=None, ux=None, uy=None, uz=None) -> None:
     arrs = [None if a is None else np.ascontiguousarray(np.asarray(a, np.float64).reshape(-1))
             for a in (phi, U, rho, ux, uy, uz)]
@@ -419,6 +429,12 @@ class Sim:
 
     def facets(self, normals) -> dict:
         return lbpf_measure_facets(self.h, normals)
+
+    def set_solid(self, mask):
+        m = None if mask is None else np.asarray(mask)
+        if m is not None and m.size != self.nodes:
+            raise LbpfError(EINVAL, f"mask must have {self.nodes} values")
+        lbpf_set_solid(self.h, m)
 
     def step(self, n: int = 1):
         lbpf_step(self.h, n)

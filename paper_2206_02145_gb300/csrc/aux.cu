@@ -145,6 +145,24 @@ __global__ void init_polygon_kernel(const Model m, const PolygonArgs a, T* pops,
   }
 }
 
+// Solid nodes: buffer c's state copied to buffer c ^ 1.
+template <typename T, typename R>
+__global__ void solid_sync_kernel(const Model m, const T* src, T* dst, const R* ring_src,
+                                  R* ring_dst, const __half* uref_src, __half* uref_dst) {
+  const long long n = (long long)m.nx * m.ny;
+  const int q = m.qf + 2 * m.qs;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    int x, y, z;
+    node_xyz(m, i, x, y, z);
+    const long long j = pitched(m, x, y, z);
+    if (!m.solid[j]) continue;
+    for (int a = 0; a < q; ++a) dst[a * m.plane + j] = src[a * m.plane + j];
+    ring_dst[j] = ring_src[j];
+    if (uref_src) uref_dst[j] = uref_src[j];
+  }
+}
+
 template <typename T, typename R>
 __global__ void init_fields_kernel(const Model m, const double* phi, const double* U,
                                    const double* rho, const double* ux, const double* uy,
@@ -392,6 +410,18 @@ cudaError_t init_polygon_t(const Model& m, const PolygonArgs& a, void* pops, voi
   return cudaGetLastError();
 }
 template <typename T, typename R>
+cudaError_t solid_sync_t(const Model& m, void* const pops[2], void* const rings[2], int c,
+                         cudaStream_t s) {
+  const long long n = (long long)m.nx * m.ny;
+  __half* u = m.rel_g ? m.uring : nullptr;
+  solid_sync_kernel<T, R><<<grid_for(n), 256, 0, s>>>(
+      m, static_cast<const T*>(pops[c]), static_cast<T*>(pops[c ^ 1]),
+      static_cast<const R*>(rings[c]), static_cast<R*>(rings[c ^ 1]),
+      u ? u + size_t(c) * size_t(m.plane) : nullptr,
+      u ? u + size_t(c ^ 1) * size_t(m.plane) : nullptr);
+  return cudaGetLastError();
+}
+template <typename T, typename R>
 cudaError_t init_fields_t(const Model& m, const double* phi, const double* U, const double* rho,
                           const double* ux, const double* uy, const double* uz, void* pops,
                           void* pp, cudaStream_t s) {
@@ -459,6 +489,11 @@ cudaError_t launch_init_polygon(const Model& m, const PolygonArgs& a, void* pops
                                 void* phi_prev, cudaStream_t s) {
   if (m.dim != 2 || a.k < 1 || a.k > kMaxFacets) return cudaErrorInvalidValue;
   LBPF_DISPATCH(init_polygon_t, m, a, pops, phi_prev, s)
+}
+cudaError_t launch_solid_sync(const Model& m, void* const pops[2], void* const rings[2], int c,
+                              cudaStream_t s) {
+  if (m.dim != 2 || !m.solid) return cudaErrorInvalidValue;
+  LBPF_DISPATCH(solid_sync_t, m, pops, rings, c, s)
 }
 cudaError_t launch_init_fields(const Model& m, const double* phi, const double* U,
                                const double* rho, const double* ux, const double* uy,

@@ -138,6 +138,8 @@ Model derive(const lbpf_params& p) {
   // allocated by lbpf_create)
   m.rel_g = (p.dim == 2 && (p.storage == LBPF_FP16_SHIFTED || p.storage == LBPF_BF16_SHIFTED)) ? 1 : 0;
   m.uring = nullptr;
+  m.solid = nullptr;
+  m.solid_tiles = nullptr;
   lbk::finalize(m);
   return m;
 }
@@ -219,6 +221,14 @@ int ensure_fields_buffer(lbpf* h, size_t bytes) {
 
 // plane c of the per-node g reference (16-bit 2D storage)
 __half* uref_dev(lbpf* h, int c) { return h->m.uring + size_t(c) * size_t(h->m.plane); }
+
+// After the state of buffer cur was replaced: the solid nodes' frozen state
+// into the other buffer as well.
+int sync_solids(lbpf* h) {
+  if (!h->m.solid) return LBPF_OK;
+  CK(h, lbk::launch_solid_sync(h->m, h->pops, h->phi, h->cur, h->stream));
+  return LBPF_OK;
+}
 
 void store_I0(lbpf* h) {
   // solute total at init, kept on the device for the drift of lbpf_diagnostics
@@ -330,6 +340,7 @@ int lbpf_init_seed(lbpf_t* h, const lbpf_seed* s) {
   h->cur = 0;
   h->step = 0;
   CK(h, lbk::launch_init_seed(h->m, a, h->pops[0], h->phi[0], h->stream));
+  if ((rc = sync_solids(h))) return rc;
   auto clampi = [](double v, int n) {
     long long i = std::llround(v);
     return int(i < 0 ? 0 : (i >= n ? n - 1 : i));
@@ -372,6 +383,7 @@ int lbpf_init_polygon(lbpf_t* h, const lbpf_polygon_seed* s) {
   h->cur = 0;
   h->step = 0;
   CK(h, lbk::launch_init_polygon(h->m, a, h->pops[0], h->phi[0], h->stream));
+  if ((rc = sync_solids(h))) return rc;
   auto clampi = [](double v, int n) {
     long long i = std::llround(v);
     return int(i < 0 ? 0 : (i >= n ? n - 1 : i));
@@ -418,6 +430,7 @@ int lbpf_init_fields(lbpf_t* h, const double* phi, const double* U, const double
   h->step = 0;
   cudaError_t e = lbk::launch_init_fields(h->m, dev[0], dev[1], dev[2], dev[3], dev[4], dev[5],
                                            h->pops[0], h->phi[0], h->stream);
+  if (e == cudaSuccess && h->m.solid) e = lbk::launch_solid_sync(h->m, h->pops, h->phi, 0, h->stream);
   cudaError_t e2 = cudaStreamSynchronize(h->stream);
   cudaFree(block);
   if (e != cudaSuccess || e2 != cudaSuccess)
@@ -536,6 +549,7 @@ int lbpf_write_state(lbpf_t* h, const void* host_src, size_t bytes) {
       CK(h, copy_rows(uref_dev(h, k), h->m.px * 2, us + k * n * 2, h->m.nx * 2, h->m.nx * 2,
                       h->m.ny, cudaMemcpyHostToDevice, h->stream));
   }
+  if ((rc = sync_solids(h))) return rc;
   h->step = hd.step;
   if (h->m.ref_g != hd.ref_g) drop_graph(h);
   h->m.ref_g = hd.ref_g;
@@ -737,6 +751,43 @@ int lbpf_growth_fit(const double* t, const double* L, int n, double* slope, doub
   return LBPF_OK;
 }
 
+int lbpf_set_solid(lbpf_t* h, const uint8_t* mask) {
+  int rc = check_handle(h);
+  if (rc) return rc;
+  if (h->m.dim != 2) return fail(h, LBPF_EINVAL, "solid nodes are 2D");
+  if (!mask) {
+    h->m.solid = nullptr;
+    h->m.solid_tiles = nullptr;
+    drop_graph(h);
+    ++h->gen;
+    return LBPF_OK;
+  }
+  const int nx = h->m.nx, ny = h->m.ny, px = h->m.px;
+  if (h->m.bc[0] == LBPF_BC_INLET_OUTLET)
+    for (int y = 0; y < ny; ++y)
+      if (mask[size_t(y) * nx] || mask[size_t(y) * nx + nx - 1])
+        return fail(h, LBPF_EINVAL, "the inlet and outlet columns must be fluid (row %d)", y);
+  std::vector<unsigned char> host(size_t(px) * ny, 0);
+  for (int y = 0; y < ny; ++y)
+    for (int x = 0; x < nx; ++x) host[size_t(y) * px + x] = mask[size_t(y) * nx + x] ? 1 : 0;
+  const size_t nt = lbk::solid_tile_count(h->m);
+  if (!h->d_solid) {
+    cudaError_t e = cudaMalloc(&h->d_solid, host.size());
+    if (e == cudaSuccess) e = cudaMalloc(&h->d_solid_tiles, nt);
+    if (e != cudaSuccess) return fail(h, LBPF_ENOMEM, "solid mask: %s", cudaGetErrorString(e));
+    h->dev_bytes += host.size() + nt;
+  }
+  CK(h, cudaMemcpyAsync(h->d_solid, host.data(), host.size(), cudaMemcpyHostToDevice, h->stream));
+  h->m.solid = h->d_solid;
+  h->m.solid_tiles = h->d_solid_tiles;
+  CK(h, lbk::launch_solid_tiles(h->m, h->d_solid_tiles, h->stream));
+  CK(h, cudaStreamSynchronize(h->stream));  // the host copy goes out of scope
+  drop_graph(h);
+  ++h->gen;
+  if (h->initialized && (rc = sync_solids(h))) return rc;
+  return LBPF_OK;
+}
+
 int lbpf_set_stream(lbpf_t* h, void* stream) {
   if (!h) return LBPF_EINVAL;
   h->stream = static_cast<cudaStream_t>(stream);
@@ -762,6 +813,8 @@ void lbpf_destroy(lbpf_t* h) {
   if (h->d_diag) cudaFree(h->d_diag);
   if (h->d_fields) cudaFree(h->d_fields);
   if (h->d_facets) cudaFree(h->d_facets);
+  if (h->d_solid) cudaFree(h->d_solid);
+  if (h->d_solid_tiles) cudaFree(h->d_solid_tiles);
   if (h->h_facets) cudaFreeHost(h->h_facets);
   delete h;
 }
@@ -801,6 +854,10 @@ int batch_build(lbpf_batch* b) {
   batch_drop_graph(b);
   for (int v = 0; v < b->nplans; ++v) lbk::batch_plan_free(&b->plans[v]);
   std::vector<lbk::BatchMember> mem(b->kids.size());
+  for (size_t i = 0; i < b->kids.size(); ++i)
+    if (b->kids[i]->m.solid)
+      return bfail(b, LBPF_EINVAL, "instance %d has solid nodes: the batched step has no "
+                   "solid-node path; step it on its own", int(i));
   for (size_t i = 0; i < b->kids.size(); ++i) {
     lbpf* k = b->kids[i];
     mem[i].m = k->m;

@@ -25,6 +25,8 @@ struct lbpf {
   unsigned long long* h_facets = nullptr;  // their pinned host copy
   int facet_k = 0;             // normals of the enqueued measurement (0: none pending)
   double facet_nx[LBPF_MAX_FACETS], facet_ny[LBPF_MAX_FACETS];
+  unsigned char* d_solid = nullptr;  // solid mask, px x ny bytes (first lbpf_set_solid)
+  unsigned char* d_solid_tiles = nullptr;  // its per-tile flags
   int icx = 0, icy = 0, icz = 0;
   size_t dev_bytes = 0;
   size_t es = 4;  // population element bytes

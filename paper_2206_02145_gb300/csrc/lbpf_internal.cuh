@@ -62,6 +62,12 @@ struct Model {
   // so FP16 loses nothing.
   int rel_g;
   __half* uring;
+  // 2D solid nodes (walls, obstacles): one byte per node at y * px + x, 1 =
+  // solid; null when there are none.  solid_tiles: one byte per 32 x 4 tile
+  // of the step (row-major over the tiles), 1 = the tile or its one-node halo
+  // holds a solid node
+  const unsigned char* solid;
+  const unsigned char* solid_tiles;
 };
 
 // The stored-g reference of the populations in buffer c (null when g is
@@ -119,6 +125,7 @@ struct StepMaps {
   CUtensorMap fg[2], h[2], ring[2];
   CUtensorMap uown, uhal;  // 2D 16-bit: the U planes (tile box, halo box; plane = coordinate)
   int ctas = 0, smem = 0, ready = 0;
+  int ctas_mask = 0;  // 2D: CTAs of the kernel with the solid-node path
 };
 
 // Launchers (each returns the launch error).
@@ -189,6 +196,15 @@ struct PolygonArgs {
 };
 cudaError_t launch_init_polygon(const Model& m, const PolygonArgs& a, void* pops, void* phi_prev,
                                 cudaStream_t s);
+// Copy the state of the solid nodes from buffer c to buffer c ^ 1 (both
+// population buffers, phi rings and, for 16-bit 2D storage, g-reference
+// planes hold the same frozen state).
+cudaError_t launch_solid_sync(const Model& m, void* const pops[2], void* const rings[2], int c,
+                              cudaStream_t s);
+// The per-tile flags of m.solid for the 2D step's tiles, into `flags`
+// (solid_tile_count(m) bytes).
+size_t solid_tile_count(const Model& m);
+cudaError_t launch_solid_tiles(const Model& m, unsigned char* flags, cudaStream_t s);
 // Support values of the phi = 0 contour of a 2D state (phi from the h
 // populations) along up to kMaxFacets + 4 unit directions, into out[0 ..
 // kMaxDirs] on the device: out[j] the order-preserving integer key of max over

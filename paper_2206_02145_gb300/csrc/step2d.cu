@@ -96,16 +96,23 @@ __global__ void __launch_bounds__(TX* TY)
     sh_phi[ly][lx] = s;
   }
   __syncthreads();
+  const bool solids = m.solid && m.solid_tiles[blockIdx.y * gridDim.x + blockIdx.x];
   if (!active) return;
+  if (solids && m.solid[idx]) {
+    ring_cur[idx] = sh_phi[ty + 1][tx + 1];  // a solid node keeps its state
+    return;
+  }
   TileView<R, R, SX, SX * SY, 0> hs{&sh_h[0][0][0]};
-  if (x0 >= 1 && x0 + TX <= nx - 1 && y0 >= 1 && y0 + TY <= ny - 1)
-    collide_push_2d<T, R, FLOW, true, SX>(m, x, y, tx + 1, ty + 1, f, g, h,
-                                          sh_phi[ty + 1][tx + 1], dphi_prev, &sh_phi[0][0], hs,
-                                          NoUView{}, static_cast<T*>(dp.p[0]), ring_cur, err);
+  if (!solids && x0 >= 1 && x0 + TX <= nx - 1 && y0 >= 1 && y0 + TY <= ny - 1)
+    collide_push_2d<T, R, FLOW, true, SX, true>(m, x, y, tx + 1, ty + 1, f, g, h,
+                                                sh_phi[ty + 1][tx + 1], dphi_prev,
+                                                &sh_phi[0][0], hs, NoUView{},
+                                                static_cast<T*>(dp.p[0]), ring_cur, err);
   else
-    collide_push_2d<T, R, FLOW, false, SX>(m, x, y, tx + 1, ty + 1, f, g, h,
-                                           sh_phi[ty + 1][tx + 1], dphi_prev, &sh_phi[0][0], hs,
-                                           NoUView{}, static_cast<T*>(dp.p[0]), ring_cur, err);
+    collide_push_2d<T, R, FLOW, false, SX, true>(m, x, y, tx + 1, ty + 1, f, g, h,
+                                                 sh_phi[ty + 1][tx + 1], dphi_prev,
+                                                 &sh_phi[0][0], hs, NoUView{},
+                                                 static_cast<T*>(dp.p[0]), ring_cur, err, solids);
 }
 
 // ---- TMA-pipelined persistent kernel ------------------------------------------
@@ -121,8 +128,10 @@ __global__ void __launch_bounds__(TX* TY)
 #define LBPF_2D_TY 4
 #endif
 
-template <typename T, bool FLOW, int TX, int TY, int S>
-__global__ void __launch_bounds__(TX* TY, LBPF_2D_MIN_CTAS)
+// MASK: the variant with the solid-node path (its extra registers held to
+// five CTAs per SM, which measured faster than four at more registers)
+template <typename T, bool FLOW, int TX, int TY, int S, bool MASK>
+__global__ void __launch_bounds__(TX* TY, MASK ? 5 : LBPF_2D_MIN_CTAS)
     step2d_tma_kernel(const __grid_constant__ CUtensorMap tm_fg,
                       const __grid_constant__ CUtensorMap tm_h,
                       const __grid_constant__ CUtensorMap tm_ring,
@@ -176,8 +185,8 @@ __global__ void __launch_bounds__(TX* TY, LBPF_2D_MIN_CTAS)
       return;
     }
     const int x0 = (tile % ntx) * TX, y0 = (tile / ntx) * TY;
-    tile_2d<T, FLOW, TX, TY>(m, src, dst, ring_cur, err, x0, y0, c, smem + s * L::STAGE,
-                             &sh_phi[0][0]);
+    tile_2d<T, FLOW, TX, TY, MASK>(m, src, dst, ring_cur, err, x0, y0, c, smem + s * L::STAGE,
+                                   &sh_phi[0][0]);
     __syncthreads();  // stage s and sh_phi are free again
     if (tid == 0 && tile + S * G < ntiles) {
       fence_proxy_async_smem();
@@ -188,6 +197,18 @@ __global__ void __launch_bounds__(TX* TY, LBPF_2D_MIN_CTAS)
 
 // ---- host side: tensor maps and launches -------------------------------------------
 constexpr int kTX = 32, kTY = LBPF_2D_TY, kStages = LBPF_2D_STAGES;
+
+// one thread per kTX x kTY tile: does the tile or its one-node halo (mapped
+// like the gradient stencil) hold a solid node?
+__global__ void solid_tiles_kernel(const Model m, unsigned char* flags, int ntx, int nty) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= ntx * nty) return;
+  const int x0 = (t % ntx) * kTX, y0 = (t / ntx) * kTY;
+  bool any = false;
+  for (int ly = -1; ly <= kTY; ++ly)
+    for (int lx = -1; lx <= kTX; ++lx) any |= solid_mapped(m, x0 + lx, y0 + ly);
+  flags[t] = any ? 1 : 0;
+}
 
 template <typename T, bool FLOW>
 cudaError_t prepare_t(const Model& m, void* const pops[2], void* const rings[2], StepMaps* out) {
@@ -221,18 +242,26 @@ cudaError_t prepare_t(const Model& m, void* const pops[2], void* const rings[2],
     out->uown = out->ring[0];  // unused
     out->uhal = out->ring[0];
   }
-  auto kern = step2d_tma_kernel<T, FLOW, kTX, kTY, kStages>;
   const int smem = kStages * L::STAGE + 128;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  if (e != cudaSuccess) return e;
-  int dev = 0, sms = 0, per_sm = 0;
+  int dev = 0, sms = 0;
+  cudaError_t e;
   if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
   if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
     return e;
-  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kTX * kTY, smem)) !=
+  auto setup = [&](auto kern, int* ctas) {
+    int per_sm = 0;
+    cudaError_t r = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (r == cudaSuccess)
+      r = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kTX * kTY, smem);
+    *ctas = sms * (per_sm > 0 ? per_sm : 1);
+    return r;
+  };
+  if ((e = setup(step2d_tma_kernel<T, FLOW, kTX, kTY, kStages, false>, &out->ctas)) !=
       cudaSuccess)
     return e;
-  out->ctas = sms * (per_sm > 0 ? per_sm : 1);
+  if ((e = setup(step2d_tma_kernel<T, FLOW, kTX, kTY, kStages, true>, &out->ctas_mask)) !=
+      cudaSuccess)
+    return e;
   out->smem = smem;
   out->ready = 1;
   return cudaSuccess;
@@ -243,10 +272,17 @@ cudaError_t launch_tma_t(const Model& m, const StepMaps& maps, int c, const void
                          void* ring_cur, unsigned* err, cudaStream_t s) {
   const int ntx = (m.nx + kTX - 1) / kTX, nty = (m.ny + kTY - 1) / kTY;
   const int ntiles = ntx * nty;
-  const int grid = ntiles < maps.ctas ? ntiles : maps.ctas;
-  step2d_tma_kernel<T, FLOW, kTX, kTY, kStages><<<grid, kTX * kTY, maps.smem, s>>>(
-      maps.fg[c], maps.h[c], maps.ring[c], maps.uown, maps.uhal, m, static_cast<const T*>(src),
-      static_cast<T*>(dst), static_cast<float*>(ring_cur), err, ntx, ntiles, c);
+  if (m.solid) {
+    const int grid = ntiles < maps.ctas_mask ? ntiles : maps.ctas_mask;
+    step2d_tma_kernel<T, FLOW, kTX, kTY, kStages, true><<<grid, kTX * kTY, maps.smem, s>>>(
+        maps.fg[c], maps.h[c], maps.ring[c], maps.uown, maps.uhal, m, static_cast<const T*>(src),
+        static_cast<T*>(dst), static_cast<float*>(ring_cur), err, ntx, ntiles, c);
+  } else {
+    const int grid = ntiles < maps.ctas ? ntiles : maps.ctas;
+    step2d_tma_kernel<T, FLOW, kTX, kTY, kStages, false><<<grid, kTX * kTY, maps.smem, s>>>(
+        maps.fg[c], maps.h[c], maps.ring[c], maps.uown, maps.uhal, m, static_cast<const T*>(src),
+        static_cast<T*>(dst), static_cast<float*>(ring_cur), err, ntx, ntiles, c);
+  }
   return cudaGetLastError();
 }
 
@@ -278,6 +314,17 @@ cudaError_t prepare_step2d(const Model& m, void* const pops[2], void* const ring
       return m.flow ? prepare_t<float, true>(m, pops, rings, out)
                     : prepare_t<float, false>(m, pops, rings, out);
   }
+}
+
+size_t solid_tile_count(const Model& m) {
+  return size_t((m.nx + kTX - 1) / kTX) * size_t((m.ny + kTY - 1) / kTY);
+}
+
+cudaError_t launch_solid_tiles(const Model& m, unsigned char* flags, cudaStream_t s) {
+  if (m.dim != 2 || !m.solid) return cudaErrorInvalidValue;
+  const int ntx = (m.nx + kTX - 1) / kTX, nty = (m.ny + kTY - 1) / kTY;
+  solid_tiles_kernel<<<(ntx * nty + 127) / 128, 128, 0, s>>>(m, flags, ntx, nty);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_step2d(const Model& m, const StepMaps& maps, int c, const void* src, void* dst,

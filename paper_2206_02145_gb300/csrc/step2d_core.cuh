@@ -39,20 +39,31 @@ struct UView {
 };
 using NoUView = UView<false, 1>;
 
+// Solid nodes (2D mask): is the node at (x, y), mapped like a gradient
+// neighbour (periodic wrap, else nearest node), solid?
+__device__ __forceinline__ bool solid_mapped(const Model& m, int x, int y) {
+  x = grad_coord(x, m.nx, m.bc[0]);
+  y = grad_coord(y, m.ny, m.bc[1]);
+  return m.solid[y * m.px + x] != 0;
+}
+
 // dphi_prev: phi(t-1) + 1 of this node; ring_cur: where phi(t) + 1 goes.
 // phi_s: the tile's phi + 1 with halo ([ly][lx], row pitch PROW).
 // dst: the destination population buffer (array a at dst + a * plane).
 // INTERIOR: the caller guarantees 1 <= x <= nx - 2 and 1 <= y <= ny - 2 for
 // every node of the tile, so every destination is an ordinary node (no wrap,
-// wall or ghost) and the push needs no boundary logic.
-template <typename T, typename R, bool FLOW, bool INTERIOR, int PROW, typename HV,
+// wall or ghost) and the push needs no boundary logic.  MASK: the code for
+// solid nodes is compiled in; `solids` (the tile holds or borders a solid
+// node) switches it on.
+template <typename T, typename R, bool FLOW, bool INTERIOR, int PROW, bool MASK, typename HV,
           typename UV>
 __device__ __forceinline__ void collide_push_2d(const Model& m, int x, int y, int lx, int ly,
                                                 const R (&f)[9], const R (&g)[9],
                                                 const R (&h)[9], R dphi, R dphi_prev,
                                                 const R* phi_s, const HV& hs, const UV& uh,
                                                 T* __restrict__ dst, R* __restrict__ ring_cur,
-                                                unsigned* __restrict__ err) {
+                                                unsigned* __restrict__ err,
+                                                bool solids = false) {
   constexpr int QF = FLOW ? 9 : 0;
   const int nx = m.nx, ny = m.ny, px = m.px;
   const int P = int(m.plane);  // fits: checked at creation
@@ -104,8 +115,26 @@ __device__ __forceinline__ void collide_push_2d(const Model& m, int x, int y, in
 
   // ---- gradient, anisotropy, phase-field coefficients (Eqs. 3, 20, 21, 23) --
   const R* pc = phi_s + ly * PROW + lx;
-  const R pE = pc[1], pW = pc[-1], pN = pc[PROW], pS = pc[-PROW];
-  const R pNE = pc[PROW + 1], pNW = pc[PROW - 1], pSE = pc[-PROW + 1], pSW = pc[-PROW - 1];
+  R pE = pc[1], pW = pc[-1], pN = pc[PROW], pS = pc[-PROW];
+  R pNE = pc[PROW + 1], pNW = pc[PROW - 1], pSE = pc[-PROW + 1], pSW = pc[-PROW - 1];
+  if (MASK && !INTERIOR && solids) {
+    // a solid neighbour counts as the first fluid node among (x + c_x, y),
+    // (x, y + c_y) and (x, y): zero normal derivative at walls and obstacles
+    auto sv = [&](int cx, int cy, R v) -> R {
+      if (!solid_mapped(m, x + cx, y + cy)) return v;
+      if (cx != 0 && !solid_mapped(m, x + cx, y)) return pc[cx];
+      if (cy != 0 && !solid_mapped(m, x, y + cy)) return pc[cy * PROW];
+      return pc[0];
+    };
+    pE = sv(1, 0, pE);
+    pW = sv(-1, 0, pW);
+    pN = sv(0, 1, pN);
+    pS = sv(0, -1, pS);
+    pNE = sv(1, 1, pNE);
+    pNW = sv(-1, 1, pNW);
+    pSE = sv(1, -1, pSE);
+    pSW = sv(-1, -1, pSW);
+  }
   // grad = 3 sum_a w_a c_a phi(x + c_a) over D2Q9
   const R gxv = R(1.0 / 3.0) * (pE - pW) + R(1.0 / 12.0) * ((pNE + pSE) - (pNW + pSW));
   const R gyv = R(1.0 / 3.0) * (pN - pS) + R(1.0 / 12.0) * ((pNE + pNW) - (pSE + pSW));
@@ -174,6 +203,7 @@ __device__ __forceinline__ void collide_push_2d(const Model& m, int x, int y, in
       else if (bcx == BC_WALL) bounce = true;
       else drop = true;
     }
+    if (MASK && solids && !bounce && !drop && m.solid[yd * px + xd]) bounce = true;  // obstacle
     if (bounce) {
       // half-way bounce-back: comes back to this node reversed
       const int b = D2_OPP[a];

@@ -55,7 +55,8 @@ __device__ __forceinline__ void issue_tile_2d(const CUtensorMap* tm_fg, const CU
 
 // Work on a filled stage `st` for the tile at (x0, y0).  Called by all
 // threads of the CTA; contains CTA barriers.  sh_phi: (TY + 2) x (TX + 2).
-template <typename T, bool FLOW, int TX, int TY>
+// MASK: solid nodes are handled (flag of the tile from m.solid_tiles).
+template <typename T, bool FLOW, int TX, int TY, bool MASK>
 __device__ __forceinline__ void tile_2d(const Model& m, const T* __restrict__ src,
                                         T* __restrict__ dst, float* __restrict__ ring_cur,
                                         unsigned* __restrict__ err, int x0, int y0, int c,
@@ -74,6 +75,10 @@ __device__ __forceinline__ void tile_2d(const Model& m, const T* __restrict__ sr
     const __half* uown = reinterpret_cast<const __half*>(st + L::OFF_UOWN);
     __half* uhal = reinterpret_cast<__half*>(st + L::OFF_UHAL);
     constexpr int HPLANE = SY * L::BXH;
+    // tiles next to solid nodes take the general path with the mask (the
+    // flag is loaded first, so that its latency overlaps the phi sums)
+    const bool solids =
+        MASK && m.solid && m.solid_tiles[(y0 / TY) * ((nx + TX - 1) / TX) + x0 / TX];
 
     if (x0 == 0 || y0 == 0 || x0 + TX >= nx || y0 + TY >= ny) {
       // halo positions outside the domain: periodic wrap or nearest node
@@ -104,7 +109,9 @@ __device__ __forceinline__ void tile_2d(const Model& m, const T* __restrict__ sr
     __syncthreads();
 
     const int x = x0 + tx, y = y0 + ty;
-    if (x < nx && y < ny) {
+    if (x < nx && y < ny && solids && m.solid[y * px + x]) {
+      ring_cur[y * px + x] = sh_phi[ty + 1][tx + 1];  // a solid node keeps its state
+    } else if (x < nx && y < ny) {
       R f[9], g[9], h[9];
       const int o = ty * TX + tx;
 #pragma unroll
@@ -119,14 +126,15 @@ __device__ __forceinline__ void tile_2d(const Model& m, const T* __restrict__ sr
                                L::REL ? m.uring + size_t(c) * m.plane : nullptr,
                                L::REL ? __half2float(uown[o]) : 0.f};
       TileView<T, R, L::BXH, HPLANE, L::HX - 1> hs{hsm};
-      if (x0 >= 1 && x0 + TX <= nx - 1 && y0 >= 1 && y0 + TY <= ny - 1)
-        collide_push_2d<T, R, FLOW, true, SX>(m, x, y, tx + 1, ty + 1, f, g, h,
-                                              sh_phi[ty + 1][tx + 1], rings[o], &sh_phi[0][0], hs,
-                                              uh, dst, ring_cur, err);
+      if (!solids && x0 >= 1 && x0 + TX <= nx - 1 && y0 >= 1 && y0 + TY <= ny - 1)
+        collide_push_2d<T, R, FLOW, true, SX, MASK>(m, x, y, tx + 1, ty + 1, f, g, h,
+                                                    sh_phi[ty + 1][tx + 1], rings[o],
+                                                    &sh_phi[0][0], hs, uh, dst, ring_cur, err);
       else
-        collide_push_2d<T, R, FLOW, false, SX>(m, x, y, tx + 1, ty + 1, f, g, h,
-                                               sh_phi[ty + 1][tx + 1], rings[o], &sh_phi[0][0],
-                                               hs, uh, dst, ring_cur, err);
+        collide_push_2d<T, R, FLOW, false, SX, MASK>(m, x, y, tx + 1, ty + 1, f, g, h,
+                                                     sh_phi[ty + 1][tx + 1], rings[o],
+                                                     &sh_phi[0][0], hs, uh, dst, ring_cur, err,
+                                                     solids);
     }
 }
 

@@ -788,6 +788,8 @@ int lbpf_surrogate_advance(lbpf_t* h, lbpf_unet_t* net, const lbpf_surrogate_cfg
   if (h->status != LBPF_OK) return h->status;
   if (!h->initialized) return sfail(h, LBPF_ESTATE, "advance before init");
   if (h->m.dim != 2) return sfail(h, LBPF_EINVAL, "the block propagator is 2D only");
+  if (h->m.solid)
+    return sfail(h, LBPF_EINVAL, "the block propagator was not trained with solid nodes");
   const lbpf_unet_cfg& nc = net->cfg;
   if (nc.batch != 1 || nc.in_ch != 4 || nc.out_ch != 4 || nc.height != h->m.ny ||
       nc.width != h->m.nx)
