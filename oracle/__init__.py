@@ -47,6 +47,8 @@ class _Params(ctypes.Structure):
         ("eps", ctypes.c_double), ("theta0", ctypes.c_double), ("h_drag", ctypes.c_double),
         ("u_inlet", ctypes.c_double), ("u0_inlet", ctypes.c_double),
         ("body", ctypes.c_double * 3),
+        ("collision", ctypes.c_int), ("omega_bulk", ctypes.c_double),
+        ("omega_high", ctypes.c_double),
     ]
 
 
@@ -109,6 +111,9 @@ class Params:
     u_inlet: float = 0.0
     u0_inlet: float = 0.0
     body: tuple = (0.0, 0.0, 0.0)
+    collision: int = 0
+    omega_bulk: float = 0.0
+    omega_high: float = 0.0
 
     def _c(self) -> _Params:
         p = _Params()

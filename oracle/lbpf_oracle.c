@@ -119,6 +119,7 @@ struct orc_sim {
   double *phi, *U, *rho, *u[3], *us[3], *F[3], *phihat, *K, *tauU, *dphidt;
   double *grad[3], *as, *a2, *tauphi, *N[3], *Q;
   unsigned char* solid; /* 2D solid mask (1 = solid node), NULL = none */
+  double* fpost;        /* central Hermite MRT: post-collision f of every node [q][n] */
 };
 
 static double* zalloc(size_t n) { return (double*)calloc(n ? n : 1, sizeof(double)); }
@@ -179,6 +180,7 @@ orc_sim* orc_create(const orc_params* p) {
   s->a2 = zalloc(n);
   s->tauphi = zalloc(n);
   s->Q = zalloc(n);
+  if (p->collision == 1 && p->dim == 2) s->fpost = zalloc(n * s->LF.q);
   return s;
 }
 
@@ -192,6 +194,7 @@ void orc_destroy(orc_sim* s) {
   free(s->phihat); free(s->K); free(s->tauU); free(s->dphidt);
   free(s->as); free(s->a2); free(s->tauphi); free(s->Q);
   free(s->solid);
+  free(s->fpost);
   free(s);
 }
 
@@ -382,8 +385,100 @@ static void node_gradient_terms(orc_sim* s, int i) {
             s->lambda * s->U[i] * (1.0 - phi * phi) * (1.0 - phi * phi); /* Eq. 20 */
 }
 
+/* ---- central Hermite multiple-relaxation-time collision of f (2D) ---------
+ * The collision the paper uses for the flow (Sec. 2.2, after Eq. 9: a central
+ * Hermite MRT, defined in the work it cites), in this reading:
+ *   1. central Hermite moments of f about the velocity u* of the equilibrium,
+ *      k_j = sum_a f_a P_j(c_a - u*), with the nine D2Q9 polynomials
+ *      1, X, Y, X^2 - cs2, Y^2 - cs2, XY, X^2 Y - cs2 Y, X Y^2 - cs2 X,
+ *      X^2 Y^2 - cs2 (X^2 + Y^2) + cs2^2;
+ *   2. their equilibrium values: rho, then zeros (the moments of the
+ *      product-form equilibrium about its own velocity);
+ *   3. relaxation by order: the first-order moments at 1/tau_f (as BGK:
+ *      momentum relaxes towards rho u*) with the force, (1 - w/2) F; the
+ *      deviatoric second-order moments and XY at 1/tau_f (the viscosity,
+ *      Eq. 10); their trace at omega_bulk (default 1); third and fourth
+ *      order at omega_high (default 1);
+ *   4. back to populations: the solution of the 9 x 9 system
+ *      sum_a P_j(c_a - u*) f*_a = k*_j. */
+static void chm_poly(double X, double Y, double cs2, double P[9]) {
+  P[0] = 1.0;
+  P[1] = X;
+  P[2] = Y;
+  P[3] = X * X - cs2;
+  P[4] = Y * Y - cs2;
+  P[5] = X * Y;
+  P[6] = X * X * Y - cs2 * Y;
+  P[7] = X * Y * Y - cs2 * X;
+  P[8] = X * X * Y * Y - cs2 * (X * X + Y * Y) + cs2 * cs2;
+}
+
+/* solve A x = b (n x n, row-major) by Gauss-Jordan elimination with partial
+ * pivoting; A and b are overwritten, x = b on return */
+static void solve_dense(double* A, double* b, int n) {
+  for (int c = 0; c < n; ++c) {
+    int piv = c;
+    for (int r = c + 1; r < n; ++r)
+      if (fabs(A[r * n + c]) > fabs(A[piv * n + c])) piv = r;
+    if (piv != c) {
+      for (int k = 0; k < n; ++k) {
+        double t = A[c * n + k];
+        A[c * n + k] = A[piv * n + k];
+        A[piv * n + k] = t;
+      }
+      double t = b[c];
+      b[c] = b[piv];
+      b[piv] = t;
+    }
+    double d = A[c * n + c];
+    for (int k = 0; k < n; ++k) A[c * n + k] /= d;
+    b[c] /= d;
+    for (int r = 0; r < n; ++r) {
+      if (r == c) continue;
+      double m = A[r * n + c];
+      if (m == 0.0) continue;
+      for (int k = 0; k < n; ++k) A[r * n + k] -= m * A[c * n + k];
+      b[r] -= m * b[c];
+    }
+  }
+}
+
+static void chm_collide(orc_sim* s, int i) {
+  const lattice* L = &s->LF;
+  const int n = s->n;
+  const double cs2 = L->cs2;
+  const double wf = 1.0 / s->p.tau_f;
+  const double wb = s->p.omega_bulk > 0.0 ? s->p.omega_bulk : 1.0;
+  const double wh = s->p.omega_high > 0.0 ? s->p.omega_high : 1.0;
+  const double vx = s->us[0][i], vy = s->us[1][i];
+  double M[81], k[9];
+  for (int j = 0; j < 9; ++j) k[j] = 0.0;
+  for (int a = 0; a < 9; ++a) {
+    double P[9];
+    chm_poly(L->c[a][0] - vx, L->c[a][1] - vy, cs2, P);
+    double fa = s->f[(size_t)a * n + i];
+    for (int j = 0; j < 9; ++j) {
+      M[j * 9 + a] = P[j];
+      k[j] += P[j] * fa;
+    }
+  }
+  /* relaxation; equilibrium values: rho (k[0], conserved), zeros */
+  double ks[9];
+  ks[0] = k[0];
+  ks[1] = (1.0 - wf) * k[1] + (1.0 - 0.5 * wf) * s->F[0][i];
+  ks[2] = (1.0 - wf) * k[2] + (1.0 - 0.5 * wf) * s->F[1][i];
+  double tr = (1.0 - wb) * (k[3] + k[4]), dv = (1.0 - wf) * (k[3] - k[4]);
+  ks[3] = 0.5 * (tr + dv);
+  ks[4] = 0.5 * (tr - dv);
+  ks[5] = (1.0 - wf) * k[5];
+  for (int j = 6; j < 9; ++j) ks[j] = (1.0 - wh) * k[j];
+  solve_dense(M, ks, 9);
+  for (int a = 0; a < 9; ++a) s->fpost[(size_t)a * n + i] = ks[a];
+}
+
 /* ---- post-collision values at a node (Eqs. 4-9, 13-16, 19-21) ------------- */
 static double f_post(const orc_sim* s, int i, int a) {
+  if (s->fpost) return s->fpost[(size_t)a * s->n + i];
   const lattice* L = &s->LF;
   double cs2 = L->cs2, tf = s->p.tau_f;
   double cu = 0.0, cF = 0.0, uF = 0.0, uu = 0.0;
@@ -488,6 +583,10 @@ static void compute_node_fields(orc_sim* s, int nthreads) {
   for (int i = 0; i < n; ++i) node_moments(s, i);
 #pragma omp parallel for num_threads(nthreads) schedule(static)
   for (int i = 0; i < n; ++i) node_gradient_terms(s, i);
+  if (s->fpost && s->p.flow) {
+#pragma omp parallel for num_threads(nthreads) schedule(static)
+    for (int i = 0; i < n; ++i) chm_collide(s, i);
+  }
 }
 
 void orc_step(orc_sim* s, int nsteps, int nthreads) {

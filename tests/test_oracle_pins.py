@@ -184,8 +184,12 @@ def test_uniform_phase_solute_recurrence(oracle_mod):
 # The flow lattice at uniform phi = 0 with a uniform velocity: the moments of
 # Eq. 4 with Eq. 5-9 give m(t+1) = m - (m - rho u*)/tau + (1 - 1/(2 tau)) F,
 # u = m / (rho + K/2), F = -K u, u* = u/2, K = h tau (1+0)^2 (1-0)/(4 W0^2).
-def test_uniform_drag_recurrence(oracle_mod):
-    p = Params(nx=4, ny=4, flow=1, eps=0.0, lambda_=0.0, tau_f=0.7, w0=2.0)
+# The central Hermite MRT (collision = 1) relaxes the first-order moments
+# about u* at the same rate with the same force term: the same recurrence.
+@pytest.mark.parametrize("collision", [0, 1])
+def test_uniform_drag_recurrence(oracle_mod, collision):
+    p = Params(nx=4, ny=4, flow=1, eps=0.0, lambda_=0.0, tau_f=0.7, w0=2.0,
+               collision=collision)
     o = O.Oracle(p)
     n = p.nodes
     u0 = np.array([0.03, -0.02])
