@@ -59,6 +59,11 @@ WORKLOADS = {
                baffle=dict(x0=150, y0=352, y1=672, w=4), kernel="step2d_tma_kernel_mask",
                sample=dict(nx=256, ny=256, seed=(75.0, 128.0, 0.0, 16.0, 0.4, 0.01, 1),
                            baffle=dict(x0=37, y0=88, y1=168, w=1))),
+    "f3": dict(base="c2", desc_note=True,
+               desc="2D 1024x1024 coupled LB, inflow 0.01, seed R=16 at x=300, U0=0.4, 5-fold "
+                    "eps 0.03, the flow colliding by the central Hermite MRT (trace of the "
+                    "second-order and the third/fourth-order central moments relaxed at 1)",
+               collision=1, kernel="step2d_tma_kernel_chm"),
     "f1": dict(desc="2D 1024x1024 coupled LB, inflow 0.01, hexagonal seed (perimeter 120 lu, "
                     "side normals at 0.1 + pi/6 + k pi/3) at x=300, U0=0.4, 6-fold eps 0.03 at "
                     "theta0 0.1; crystal shape (side lengths, centre, Q, aspect ratio) measured "
@@ -173,7 +178,7 @@ def lib_params(w, L, storage=None):
                 storage={"fp32": L.FP32, "fp64": L.FP64, "fp16": L.FP16_SHIFTED,
                          "bf16": L.BF16_SHIFTED}[storage or w["storage"]],
                 fold=w["fold"], eps_aniso=w["eps"], u_inlet=w["u_in"], u0_inlet=w["U_in"],
-                theta0=w.get("theta0", 0.0))
+                theta0=w.get("theta0", 0.0), collision=w.get("collision", 0))
 
 
 def measured_peaks():
@@ -342,7 +347,8 @@ def oracle_problem(w):
         body = (g, 0.0, 0.0)
     p = oracle.Params(dim=w["dim"], nx=s["nx"], ny=s["ny"], nz=s.get("nz", 1), bc=w["bc"],
                       flow=w["flow"], fold=w["fold"], eps=w["eps"], u_inlet=w["u_in"],
-                      u0_inlet=w["U_in"], body=body, theta0=w.get("theta0", 0.0))
+                      u0_inlet=w["U_in"], body=body, theta0=w.get("theta0", 0.0),
+                      collision=w.get("collision", 0))
     o = oracle.Oracle(p)
     if s.get("channel"):
         o.init_fields(f["phi"], f["U"], None, f["ux"], f["uy"])
@@ -517,6 +523,23 @@ def main():
                    "iface_pos_err_lu": e, "growth_rel_err": rel}
         q.close()
 
+    vs_bgk = None
+    if batch is None and w.get("collision"):
+        # the same problem with the BGK collision (Eq. 8), the same steps
+        q = L.Sim(stream=stream.cuda_stream, **dict(lib_params(w, L), collision=0))
+        q.init_seed(*w["seed"])
+        q.step(args.warmup)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        q.step(args.steps)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        msb = max_over_ranks([ev0.elapsed_time(ev1)], dist)[0]
+        e, rel = iface_compare(d_init[0], d["iface_pos"], q.diagnostics()["iface_pos"], w["dim"])
+        vs_bgk = {"bgk_ms_per_step": msb / args.steps, "time_ratio_chm_over_bgk": ms_max / msb,
+                  "steps": total_steps, "iface_pos_diff_lu": e, "growth_rel_diff": rel}
+        q.close()
+
     batch_info = None
     if batch is not None:
         # the same instances stepped one after another (each its own graph),
@@ -641,6 +664,8 @@ def main():
         }
         if vs_fp32 is not None:
             out["vs_plain_fp32"] = vs_fp32
+        if vs_bgk is not None:
+            out["vs_bgk"] = vs_bgk
         if batch_info is not None:
             out["config"]["batch"] = batch_info
             out["config"]["grid"] = "64 square grids, sides 256..768"

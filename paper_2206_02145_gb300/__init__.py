@@ -22,6 +22,7 @@ LIB_PATH = os.environ.get("LBPF_LIB") or os.path.join(_HERE, "_build", "liblbpf.
 OK, EINVAL, ECUDA, ENOMEM, ESTATE, ENONFINITE, ETIMEDOUT = 0, -1, -2, -3, -4, -5, -6
 BC_PERIODIC, BC_INLET_OUTLET, BC_WALL = 0, 1, 2
 FP32, FP64, FP16_SHIFTED, BF16_SHIFTED = 0, 1, 2, 3
+COLL_BGK, COLL_CHM = 0, 1
 FIELD_PHI, FIELD_U, FIELD_RHO, FIELD_UX, FIELD_UY, FIELD_UZ, FIELD_PHI_PREV = (
     1, 2, 4, 8, 16, 32, 64)
 FIELD_STATE = 256
@@ -48,6 +49,8 @@ class lbpf_params(ctypes.Structure):
         ("eps_aniso", ctypes.c_double), ("theta0", ctypes.c_double),
         ("h_drag", ctypes.c_double), ("u_inlet", ctypes.c_double),
         ("u0_inlet", ctypes.c_double), ("body_force", ctypes.c_double * 3),
+        ("collision", ctypes.c_int), ("chm_omega_bulk", ctypes.c_double),
+        ("chm_omega_high", ctypes.c_double),
     ]
 
 

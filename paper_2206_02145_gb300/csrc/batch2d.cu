@@ -79,7 +79,7 @@ __global__ void __launch_bounds__(TX* TY, 3)
       if (tid == 0) cur_inst = inst;
     }
     const int lt = tile - d.tile0;
-    tile_2d<T, FLOW, TX, TY, false>(sm, static_cast<const T*>(d.src), static_cast<T*>(d.dst),
+    tile_2d<T, FLOW, TX, TY, false, false>(sm, static_cast<const T*>(d.src), static_cast<T*>(d.dst),
                              d.ring_cur, d.err, (lt % d.ntx) * TX, (lt / d.ntx) * TY, d.c,
                              smem + s * L::STAGE, &sh_phi[0][0]);
     __syncthreads();  // stage s, sh_phi and sm are free again

@@ -91,6 +91,13 @@ int validate(const lbpf_params* p, char* why, size_t n) {
     return bad("non-finite parameter");
   for (int d = 0; d < 3; ++d)
     if (!std::isfinite(p->body_force[d])) return bad("non-finite body force");
+  if (p->collision != LBPF_COLL_BGK && p->collision != LBPF_COLL_CHM)
+    return bad("unknown collision");
+  if (p->collision == LBPF_COLL_CHM) {
+    if (p->dim != 2 || !p->flow) return bad("the central Hermite MRT is 2D with flow");
+    for (double w : {p->chm_omega_bulk, p->chm_omega_high})
+      if (!(w == 0.0 || (w > 0.0 && w < 2.0))) return bad("CHM rates must be in (0, 2) or 0");
+  }
   return LBPF_OK;
 }
 
@@ -140,6 +147,9 @@ Model derive(const lbpf_params& p) {
   m.uring = nullptr;
   m.solid = nullptr;
   m.solid_tiles = nullptr;
+  m.chm = p.collision == LBPF_COLL_CHM ? 1 : 0;
+  m.chm_wb = p.chm_omega_bulk > 0.0 ? p.chm_omega_bulk : 1.0;
+  m.chm_wh = p.chm_omega_high > 0.0 ? p.chm_omega_high : 1.0;
   lbk::finalize(m);
   return m;
 }
@@ -854,10 +864,14 @@ int batch_build(lbpf_batch* b) {
   batch_drop_graph(b);
   for (int v = 0; v < b->nplans; ++v) lbk::batch_plan_free(&b->plans[v]);
   std::vector<lbk::BatchMember> mem(b->kids.size());
-  for (size_t i = 0; i < b->kids.size(); ++i)
+  for (size_t i = 0; i < b->kids.size(); ++i) {
     if (b->kids[i]->m.solid)
       return bfail(b, LBPF_EINVAL, "instance %d has solid nodes: the batched step has no "
                    "solid-node path; step it on its own", int(i));
+    if (b->kids[i]->m.chm)
+      return bfail(b, LBPF_EINVAL, "instance %d uses the central Hermite MRT: the batched "
+                   "step is BGK only", int(i));
+  }
   for (size_t i = 0; i < b->kids.size(); ++i) {
     lbpf* k = b->kids[i];
     mem[i].m = k->m;
@@ -915,7 +929,7 @@ int lbpf_batch_create(const lbpf_params* p, const lbpf_seed* s, int count, void*
   *out = nullptr;
   for (int i = 0; i < count; ++i) {
     if (p[i].dim != 2 || p[i].flow != p[0].flow || p[i].storage != p[0].storage ||
-        p[i].storage == LBPF_FP64) {
+        p[i].storage == LBPF_FP64 || p[i].collision != LBPF_COLL_BGK) {
       fprintf(stderr,
               "lbpf_batch_create: instance %d: a batch holds 2D instances with one flow flag "
               "and one storage among FP32, FP16, BF16\n", i);

@@ -23,6 +23,7 @@ struct Coef {
   R omega_f, guo, tauU_slope, inv_tau0, tpc, lambda, eps, ck0, sk0, aniso_fac, kdrag;
   R body[3];
   R u_in, U_in, ref_f, ref_g, ref_h;
+  R chm_wb, chm_wh;  // central Hermite MRT: trace and higher-order rates
 };
 
 // Derived model constants (FP64 on the host; the kernels use cf / cd).  Device layout: every population is its own array of
@@ -60,6 +61,8 @@ struct Model {
   // populations it pushes against the destination's value in plane c ^ 1.
   // The reference only has to be the same number at encoding and decoding,
   // so FP16 loses nothing.
+  int chm;              // flow collision: 0 BGK, 1 central Hermite MRT (2D)
+  double chm_wb, chm_wh;
   int rel_g;
   __half* uring;
   // 2D solid nodes (walls, obstacles): one byte per node at y * px + x, 1 =
@@ -97,6 +100,8 @@ inline void finalize(Model& m) {
     c.ref_f = R(m.ref_f);
     c.ref_g = R(m.ref_g);
     c.ref_h = R(m.ref_h);
+    c.chm_wb = R(m.chm_wb);
+    c.chm_wh = R(m.chm_wh);
   };
   fill(m.cf);
   fill(m.cd);
@@ -125,7 +130,7 @@ struct StepMaps {
   CUtensorMap fg[2], h[2], ring[2];
   CUtensorMap uown, uhal;  // 2D 16-bit: the U planes (tile box, halo box; plane = coordinate)
   int ctas = 0, smem = 0, ready = 0;
-  int ctas_mask = 0;  // 2D: CTAs of the kernel with the solid-node path
+  int ctas_v[4] = {0, 0, 0, 0};  // 2D: CTAs of the variant MASK + 2 CHM
 };
 
 // Launchers (each returns the launch error).

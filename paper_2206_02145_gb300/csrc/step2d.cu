@@ -39,7 +39,7 @@ namespace {
 constexpr int kSpin = 1 << 22;  // bound on mbarrier polls before giving up
 
 // ---- FP64 (and reference) kernel: one tile per CTA ------------------------------
-template <typename T, typename R, bool FLOW, int TX, int TY>
+template <typename T, typename R, bool FLOW, int TX, int TY, bool CHM>
 __global__ void __launch_bounds__(TX* TY)
     step2d_kernel(const Model m, const PopPtrs sp, const PopPtrs dp,
                   const R* __restrict__ ring_prev, R* __restrict__ ring_cur,
@@ -104,12 +104,12 @@ __global__ void __launch_bounds__(TX* TY)
   }
   TileView<R, R, SX, SX * SY, 0> hs{&sh_h[0][0][0]};
   if (!solids && x0 >= 1 && x0 + TX <= nx - 1 && y0 >= 1 && y0 + TY <= ny - 1)
-    collide_push_2d<T, R, FLOW, true, SX, true>(m, x, y, tx + 1, ty + 1, f, g, h,
+    collide_push_2d<T, R, FLOW, true, SX, true, CHM>(m, x, y, tx + 1, ty + 1, f, g, h,
                                                 sh_phi[ty + 1][tx + 1], dphi_prev,
                                                 &sh_phi[0][0], hs, NoUView{},
                                                 static_cast<T*>(dp.p[0]), ring_cur, err);
   else
-    collide_push_2d<T, R, FLOW, false, SX, true>(m, x, y, tx + 1, ty + 1, f, g, h,
+    collide_push_2d<T, R, FLOW, false, SX, true, CHM>(m, x, y, tx + 1, ty + 1, f, g, h,
                                                  sh_phi[ty + 1][tx + 1], dphi_prev,
                                                  &sh_phi[0][0], hs, NoUView{},
                                                  static_cast<T*>(dp.p[0]), ring_cur, err, solids);
@@ -129,9 +129,10 @@ __global__ void __launch_bounds__(TX* TY)
 #endif
 
 // MASK: the variant with the solid-node path (its extra registers held to
-// five CTAs per SM, which measured faster than four at more registers)
-template <typename T, bool FLOW, int TX, int TY, int S, bool MASK>
-__global__ void __launch_bounds__(TX* TY, MASK ? 5 : LBPF_2D_MIN_CTAS)
+// five CTAs per SM, which measured faster than four at more registers); CHM:
+// the central Hermite MRT flow collision (likewise)
+template <typename T, bool FLOW, int TX, int TY, int S, bool MASK, bool CHM>
+__global__ void __launch_bounds__(TX* TY, (MASK || CHM) ? 5 : LBPF_2D_MIN_CTAS)
     step2d_tma_kernel(const __grid_constant__ CUtensorMap tm_fg,
                       const __grid_constant__ CUtensorMap tm_h,
                       const __grid_constant__ CUtensorMap tm_ring,
@@ -185,8 +186,8 @@ __global__ void __launch_bounds__(TX* TY, MASK ? 5 : LBPF_2D_MIN_CTAS)
       return;
     }
     const int x0 = (tile % ntx) * TX, y0 = (tile / ntx) * TY;
-    tile_2d<T, FLOW, TX, TY, MASK>(m, src, dst, ring_cur, err, x0, y0, c, smem + s * L::STAGE,
-                                   &sh_phi[0][0]);
+    tile_2d<T, FLOW, TX, TY, MASK, CHM>(m, src, dst, ring_cur, err, x0, y0, c,
+                                        smem + s * L::STAGE, &sh_phi[0][0]);
     __syncthreads();  // stage s and sh_phi are free again
     if (tid == 0 && tile + S * G < ntiles) {
       fence_proxy_async_smem();
@@ -256,12 +257,19 @@ cudaError_t prepare_t(const Model& m, void* const pops[2], void* const rings[2],
     *ctas = sms * (per_sm > 0 ? per_sm : 1);
     return r;
   };
-  if ((e = setup(step2d_tma_kernel<T, FLOW, kTX, kTY, kStages, false>, &out->ctas)) !=
-      cudaSuccess)
+  if ((e = setup(step2d_tma_kernel<T, FLOW, kTX, kTY, kStages, false, false>,
+                 &out->ctas_v[0])) != cudaSuccess ||
+      (e = setup(step2d_tma_kernel<T, FLOW, kTX, kTY, kStages, true, false>,
+                 &out->ctas_v[1])) != cudaSuccess)
     return e;
-  if ((e = setup(step2d_tma_kernel<T, FLOW, kTX, kTY, kStages, true>, &out->ctas_mask)) !=
-      cudaSuccess)
-    return e;
+  if constexpr (FLOW) {  // the central Hermite MRT exists with flow only
+    if ((e = setup(step2d_tma_kernel<T, FLOW, kTX, kTY, kStages, false, true>,
+                   &out->ctas_v[2])) != cudaSuccess ||
+        (e = setup(step2d_tma_kernel<T, FLOW, kTX, kTY, kStages, true, true>,
+                   &out->ctas_v[3])) != cudaSuccess)
+      return e;
+  }
+  out->ctas = out->ctas_v[0];
   out->smem = smem;
   out->ready = 1;
   return cudaSuccess;
@@ -272,16 +280,19 @@ cudaError_t launch_tma_t(const Model& m, const StepMaps& maps, int c, const void
                          void* ring_cur, unsigned* err, cudaStream_t s) {
   const int ntx = (m.nx + kTX - 1) / kTX, nty = (m.ny + kTY - 1) / kTY;
   const int ntiles = ntx * nty;
-  if (m.solid) {
-    const int grid = ntiles < maps.ctas_mask ? ntiles : maps.ctas_mask;
-    step2d_tma_kernel<T, FLOW, kTX, kTY, kStages, true><<<grid, kTX * kTY, maps.smem, s>>>(
-        maps.fg[c], maps.h[c], maps.ring[c], maps.uown, maps.uhal, m, static_cast<const T*>(src),
-        static_cast<T*>(dst), static_cast<float*>(ring_cur), err, ntx, ntiles, c);
-  } else {
-    const int grid = ntiles < maps.ctas ? ntiles : maps.ctas;
-    step2d_tma_kernel<T, FLOW, kTX, kTY, kStages, false><<<grid, kTX * kTY, maps.smem, s>>>(
-        maps.fg[c], maps.h[c], maps.ring[c], maps.uown, maps.uhal, m, static_cast<const T*>(src),
-        static_cast<T*>(dst), static_cast<float*>(ring_cur), err, ntx, ntiles, c);
+  const int v = (m.solid ? 1 : 0) + (FLOW && m.chm ? 2 : 0);
+  const int grid = ntiles < maps.ctas_v[v] ? ntiles : maps.ctas_v[v];
+  auto go = [&](auto kern) {
+    kern<<<grid, kTX * kTY, maps.smem, s>>>(maps.fg[c], maps.h[c], maps.ring[c], maps.uown,
+                                            maps.uhal, m, static_cast<const T*>(src),
+                                            static_cast<T*>(dst), static_cast<float*>(ring_cur),
+                                            err, ntx, ntiles, c);
+  };
+  if (v == 0) go(step2d_tma_kernel<T, FLOW, kTX, kTY, kStages, false, false>);
+  else if (v == 1) go(step2d_tma_kernel<T, FLOW, kTX, kTY, kStages, true, false>);
+  if constexpr (FLOW) {
+    if (v == 2) go(step2d_tma_kernel<T, FLOW, kTX, kTY, kStages, false, true>);
+    else if (v == 3) go(step2d_tma_kernel<T, FLOW, kTX, kTY, kStages, true, true>);
   }
   return cudaGetLastError();
 }
@@ -291,9 +302,14 @@ cudaError_t launch_plain_t(const Model& m, const void* src, void* dst, const voi
                            void* ring_cur, unsigned* err, cudaStream_t s) {
   dim3 block(kTX, kTY);
   dim3 grid((m.nx + kTX - 1) / kTX, (m.ny + kTY - 1) / kTY);
-  step2d_kernel<T, R, FLOW, kTX, kTY><<<grid, block, 0, s>>>(
-      m, pop_ptrs(m, const_cast<void*>(src), sizeof(T)), pop_ptrs(m, dst, sizeof(T)),
-      static_cast<const R*>(ring_prev), static_cast<R*>(ring_cur), err);
+  const PopPtrs sp = pop_ptrs(m, const_cast<void*>(src), sizeof(T));
+  const PopPtrs dp = pop_ptrs(m, dst, sizeof(T));
+  if (FLOW && m.chm)
+    step2d_kernel<T, R, FLOW, kTX, kTY, FLOW><<<grid, block, 0, s>>>(
+        m, sp, dp, static_cast<const R*>(ring_prev), static_cast<R*>(ring_cur), err);
+  else
+    step2d_kernel<T, R, FLOW, kTX, kTY, false><<<grid, block, 0, s>>>(
+        m, sp, dp, static_cast<const R*>(ring_prev), static_cast<R*>(ring_cur), err);
   return cudaGetLastError();
 }
 

@@ -47,6 +47,72 @@ __device__ __forceinline__ bool solid_mapped(const Model& m, int x, int y) {
   return m.solid[y * m.px + x] != 0;
 }
 
+// Central Hermite MRT of the flow populations (2D; the collision of the
+// paper's flow solver, read as the C ABI documents for LBPF_COLL_CHM).
+// d: pre-collision deviations f - w; drho, rho, (mx, my): their zeroth and
+// first moments; (vx, vy) = u*; F the force; wf, wb, wh the rates.  The
+// moments are formed from the deviations with the weights' own moments
+// (1, 0, 0, 1/3, 1/3, 0, 0, 0, 1/9) taken out analytically, so that FP32
+// keeps the small quantities: raw moments e_pq -> central Hermite moments
+// about u* -> relaxation by order -> raw moments -> populations through the
+// inverse of the D2Q9 raw-moment matrix.  out: post-collision deviations.
+template <typename R>
+__device__ __forceinline__ void chm_post_2d(const R (&d)[9], R drho, R rho, R mx, R my, R vx,
+                                            R vy, R Fx, R Fy, R wf, R wb, R wh, R (&out)[9]) {
+  const R t3 = R(1.0 / 3.0), t9 = R(1.0 / 9.0);
+  // raw moments of the deviations
+  const R e00 = drho, e10 = mx, e01 = my;
+  const R dd = (d[5] + d[6]) + (d[7] + d[8]);
+  const R e20 = (d[1] + d[3]) + dd, e02 = (d[2] + d[4]) + dd;
+  const R e11 = (d[5] - d[6]) + (d[7] - d[8]);
+  const R e21 = (d[5] + d[6]) - (d[7] + d[8]);
+  const R e12 = (d[5] - d[6]) - (d[7] - d[8]);
+  const R e22 = dd;
+  const R vxx = vx * vx, vyy = vy * vy, vxy = vx * vy;
+  // central Hermite moments about (vx, vy)
+  const R h1 = e10 - vx * rho, h2 = e01 - vy * rho;
+  const R hxx = e20 - t3 * e00 - R(2) * vx * e10 + vxx * rho;
+  const R hyy = e02 - t3 * e00 - R(2) * vy * e01 + vyy * rho;
+  const R hxy = e11 - vx * e01 - vy * e10 + vxy * rho;
+  const R hxxy = e21 - R(2) * vx * e11 + vxx * e01 - vy * e20 + R(2) * vxy * e10 -
+                 vxx * vy * rho - t3 * e01 + t3 * vy * e00;
+  const R hxyy = e12 - R(2) * vy * e11 + vyy * e10 - vx * e02 + R(2) * vxy * e01 -
+                 vx * vyy * rho - t3 * e10 + t3 * vx * e00;
+  const R hxxyy = e22 - R(2) * vx * e12 - R(2) * vy * e21 + vxx * e02 + vyy * e20 +
+                  R(4) * vxy * e11 - R(2) * vxy * vy * e10 - R(2) * vxy * vx * e01 +
+                  vxx * vyy * rho - t3 * (e20 + e02) + R(2) * t3 * (vx * e10 + vy * e01) -
+                  t3 * (vxx + vyy) * e00 + t9 * e00;
+  // relaxation towards rho and zeros; the force in the first order
+  const R kf = R(1) - wf, gf = R(1) - R(0.5) * wf, kh = R(1) - wh;
+  const R h1s = kf * h1 + gf * Fx, h2s = kf * h2 + gf * Fy;
+  const R tr = (R(1) - wb) * (hxx + hyy), dv = kf * (hxx - hyy);
+  const R hxxs = R(0.5) * (tr + dv), hyys = R(0.5) * (tr - dv);
+  const R hxys = kf * hxy;
+  const R hxxys = kh * hxxy, hxyys = kh * hxyy, hxxyys = kh * hxxyy;
+  // central (raw) moments after collision, then raw moments of the deviations
+  const R k20 = hxxs + t3 * rho, k02 = hyys + t3 * rho;
+  const R k21 = hxxys + t3 * h2s, k12 = hxyys + t3 * h1s;
+  const R f10 = h1s + vx * rho, f01 = h2s + vy * rho;
+  const R f20 = hxxs + t3 * e00 + R(2) * vx * h1s + vxx * rho;
+  const R f02 = hyys + t3 * e00 + R(2) * vy * h2s + vyy * rho;
+  const R f11 = hxys + vx * h2s + vy * h1s + vxy * rho;
+  const R f21 = k21 + R(2) * vx * hxys + vxx * h2s + vy * k20 + R(2) * vxy * h1s + vxx * vy * rho;
+  const R f12 = k12 + R(2) * vy * hxys + vyy * h1s + vx * k02 + R(2) * vxy * h2s + vx * vyy * rho;
+  const R f22 = hxxyys + t3 * (hxxs + hyys) + t9 * e00 + R(2) * vx * k12 + R(2) * vy * k21 +
+                vxx * k02 + vyy * k20 + R(4) * vxy * hxys + R(2) * vxy * vy * h1s +
+                R(2) * vxy * vx * h2s + vxx * vyy * rho;
+  // populations (D2Q9 order: rest, +x, +y, -x, -y, ++, -+, --, +-)
+  out[0] = e00 - f20 - f02 + f22;
+  out[1] = R(0.5) * (f10 + f20 - f12 - f22);
+  out[3] = R(0.5) * (-f10 + f20 + f12 - f22);
+  out[2] = R(0.5) * (f01 + f02 - f21 - f22);
+  out[4] = R(0.5) * (-f01 + f02 + f21 - f22);
+  out[5] = R(0.25) * (f11 + f21 + f12 + f22);
+  out[6] = R(0.25) * (-f11 + f21 - f12 + f22);
+  out[7] = R(0.25) * (f11 - f21 - f12 + f22);
+  out[8] = R(0.25) * (-f11 - f21 + f12 + f22);
+}
+
 // dphi_prev: phi(t-1) + 1 of this node; ring_cur: where phi(t) + 1 goes.
 // phi_s: the tile's phi + 1 with halo ([ly][lx], row pitch PROW).
 // dst: the destination population buffer (array a at dst + a * plane).
@@ -54,9 +120,9 @@ __device__ __forceinline__ bool solid_mapped(const Model& m, int x, int y) {
 // every node of the tile, so every destination is an ordinary node (no wrap,
 // wall or ghost) and the push needs no boundary logic.  MASK: the code for
 // solid nodes is compiled in; `solids` (the tile holds or borders a solid
-// node) switches it on.
-template <typename T, typename R, bool FLOW, bool INTERIOR, int PROW, bool MASK, typename HV,
-          typename UV>
+// node) switches it on.  CHM: the flow collides by the central Hermite MRT.
+template <typename T, typename R, bool FLOW, bool INTERIOR, int PROW, bool MASK, bool CHM,
+          typename HV, typename UV>
 __device__ __forceinline__ void collide_push_2d(const Model& m, int x, int y, int lx, int ly,
                                                 const R (&f)[9], const R (&g)[9],
                                                 const R (&h)[9], R dphi, R dphi_prev,
@@ -102,6 +168,9 @@ __device__ __forceinline__ void collide_push_2d(const Model& m, int x, int y, in
     Fy = c.body[1] - K * uy;
   }
   const R usx = mask * ux, usy = mask * uy;  // u* (Eq. 7)
+  R fchm[9];
+  if (FLOW && CHM)
+    chm_post_2d<R>(f, drho, rho, mx, my, usx, usy, Fx, Fy, c.omega_f, c.chm_wb, c.chm_wh, fchm);
   const R omega_U = rcp_r(R(0.5) + c.tauU_slope * mask);  // Eq. 18
   const R dphidt = dphi - dphi_prev;
   ring_cur[idx] = dphi;
@@ -175,7 +244,9 @@ __device__ __forceinline__ void collide_push_2d(const Model& m, int x, int y, in
     const R cu = R(cx) * usx + R(cy) * usy;
     // post-collision deviations at this node
     R fp = R(0);
-    if (FLOW) {
+    if (FLOW && CHM) {
+      fp = fchm[a];
+    } else if (FLOW) {
       const R cF = R(cx) * Fx + R(cy) * Fy;
       const R feq = fma_r(cu, fma_r(E2, cu, E1), E0);
       const R guo_t = mul_r(guo, fma_r(cF, fma_r(R(9), cu, R(3)), G0));

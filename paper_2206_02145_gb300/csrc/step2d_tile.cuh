@@ -55,8 +55,9 @@ __device__ __forceinline__ void issue_tile_2d(const CUtensorMap* tm_fg, const CU
 
 // Work on a filled stage `st` for the tile at (x0, y0).  Called by all
 // threads of the CTA; contains CTA barriers.  sh_phi: (TY + 2) x (TX + 2).
-// MASK: solid nodes are handled (flag of the tile from m.solid_tiles).
-template <typename T, bool FLOW, int TX, int TY, bool MASK>
+// MASK: solid nodes are handled (flag of the tile from m.solid_tiles).  CHM:
+// the flow collides by the central Hermite MRT.
+template <typename T, bool FLOW, int TX, int TY, bool MASK, bool CHM>
 __device__ __forceinline__ void tile_2d(const Model& m, const T* __restrict__ src,
                                         T* __restrict__ dst, float* __restrict__ ring_cur,
                                         unsigned* __restrict__ err, int x0, int y0, int c,
@@ -127,11 +128,11 @@ __device__ __forceinline__ void tile_2d(const Model& m, const T* __restrict__ sr
                                L::REL ? __half2float(uown[o]) : 0.f};
       TileView<T, R, L::BXH, HPLANE, L::HX - 1> hs{hsm};
       if (!solids && x0 >= 1 && x0 + TX <= nx - 1 && y0 >= 1 && y0 + TY <= ny - 1)
-        collide_push_2d<T, R, FLOW, true, SX, MASK>(m, x, y, tx + 1, ty + 1, f, g, h,
+        collide_push_2d<T, R, FLOW, true, SX, MASK, CHM>(m, x, y, tx + 1, ty + 1, f, g, h,
                                                     sh_phi[ty + 1][tx + 1], rings[o],
                                                     &sh_phi[0][0], hs, uh, dst, ring_cur, err);
       else
-        collide_push_2d<T, R, FLOW, false, SX, MASK>(m, x, y, tx + 1, ty + 1, f, g, h,
+        collide_push_2d<T, R, FLOW, false, SX, MASK, CHM>(m, x, y, tx + 1, ty + 1, f, g, h,
                                                      sh_phi[ty + 1][tx + 1], rings[o],
                                                      &sh_phi[0][0], hs, uh, dst, ring_cur, err,
                                                      solids);
