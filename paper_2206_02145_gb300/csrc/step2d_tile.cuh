@@ -98,9 +98,28 @@ __device__ __forceinline__ void tile_2d(const Model& m, const T* __restrict__ sr
       }
       __syncthreads();
     }
-    // phi + 1 of the halo-extended tile
-    for (int i = tid; i < SX * SY; i += NT) {
-      const int lx = i % SX, ly = i / SX;
+    // phi + 1 of the halo-extended tile: each thread's own position from the
+    // h it keeps for the collision, the ring around the tile by a pass
+    R h[9];
+    {
+      R sum = R(0);
+#pragma unroll
+      for (int a = 0; a < 9; ++a) {
+        h[a] = Pop<T>::template ld<R>(hsm + a * HPLANE + (ty + 1) * L::BXH + tx + L::HX);
+        sum += h[a];
+      }
+      sh_phi[ty + 1][tx + 1] = sum;
+    }
+    constexpr int NRING = 2 * SX + 2 * TY;
+    for (int i = tid; i < NRING; i += NT) {
+      int lx, ly;
+      if (i < 2 * SX) {
+        lx = i % SX;
+        ly = i < SX ? 0 : SY - 1;
+      } else {
+        lx = (i - 2 * SX) & 1 ? SX - 1 : 0;
+        ly = 1 + (i - 2 * SX) / 2;
+      }
       const T* hp = hsm + ly * L::BXH + lx + L::HX - 1;
       R sum = R(0);
 #pragma unroll
@@ -113,13 +132,12 @@ __device__ __forceinline__ void tile_2d(const Model& m, const T* __restrict__ sr
     if (x < nx && y < ny && solids && m.solid[y * px + x]) {
       ring_cur[y * px + x] = sh_phi[ty + 1][tx + 1];  // a solid node keeps its state
     } else if (x < nx && y < ny) {
-      R f[9], g[9], h[9];
+      R f[9], g[9];
       const int o = ty * TX + tx;
 #pragma unroll
       for (int a = 0; a < 9; ++a) {
         if (FLOW) f[a] = Pop<T>::template ld<R>(fgs + a * (TY * TX) + o);
         g[a] = Pop<T>::template ld<R>(fgs + (QF + a) * (TY * TX) + o);
-        h[a] = Pop<T>::template ld<R>(hsm + a * HPLANE + (ty + 1) * L::BXH + tx + L::HX);
       }
       // g stored relative to the node's own U reference, the collision
       // takes the deviations from it as they are
