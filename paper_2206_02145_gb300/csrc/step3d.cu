@@ -129,14 +129,26 @@ __global__ void __launch_bounds__(TX* TY, MINB)
   const bool active = x < nx && y < ny;
   const bool xy_inner = x0 >= 1 && x0 + TX <= nx - 1 && y0 >= 1 && y0 + TY <= ny - 1;
 
+  // the in-plane offsets of this thread's positions of the halo-extended
+  // plane (the same on every plane of the column)
+  constexpr int NPOS = (PL + NT - 1) / NT;
+  int jxy[NPOS];
+#pragma unroll
+  for (int r = 0; r < NPOS; ++r) {
+    const int i = tid + r * NT;
+    const int lx = i % SX, ly = i / SX;
+    const int gx = grad_coord(x0 + lx - 1, nx, m.bc[0]);
+    const int gy = grad_coord(y0 + ly - 1, ny, m.bc[1]);
+    jxy[r] = i < PL ? gy * px + gx : 0;
+  }
   // h and phi + 1 of plane zz (ghost planes by the gradient rule) into slot
   auto load_plane = [&](int zz, int slot) {
     const int gz = grad_coord(zz, nz, m.bc[2]);
-    for (int i = tid; i < PL; i += NT) {
-      const int lx = i % SX, ly = i / SX;
-      const int gx = grad_coord(x0 + lx - 1, nx, m.bc[0]);
-      const int gy = grad_coord(y0 + ly - 1, ny, m.bc[1]);
-      const int j = gz * slab + gy * px + gx;
+#pragma unroll
+    for (int r = 0; r < NPOS; ++r) {
+      const int i = tid + r * NT;
+      if (i >= PL) break;
+      const int j = gz * slab + jxy[r];
       R s = R(0);
 #pragma unroll
       for (int a = 0; a < 7; ++a) {
