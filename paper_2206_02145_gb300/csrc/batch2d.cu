@@ -18,8 +18,10 @@ namespace {
 
 constexpr int kBatchSpin = 1 << 22;
 
+// registers held to 20 resident warps per SM (five CTAs of 32 x 4), the
+// occupancy of the single-instance step
 template <typename T, bool FLOW, int TX, int TY, int S>
-__global__ void __launch_bounds__(TX* TY, 3)
+__global__ void __launch_bounds__(TX* TY, (640 / (TX * TY)) > 2 ? 640 / (TX * TY) : 2)
     step2d_batch_kernel(const BatchDesc* __restrict__ descs,
                         const unsigned short* __restrict__ tile_inst, int total_tiles) {
   using L = Tiles2D<T, FLOW, TX, TY>;
