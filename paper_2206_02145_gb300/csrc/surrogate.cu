@@ -341,19 +341,23 @@ int adam_all(lbpf_unet* n, float lr) {
   return LBPF_OK;
 }
 
-// pack FP32 NHWC (in_ch) into the bf16 16-channel input buffer
+// pack FP32 NHWC (in_ch <= 16) into the bf16 16-channel input buffer: one
+// pixel per thread, its 16 outputs written as two 16-byte stores
 __global__ void pack_input_kernel(const float* x, int cin, bf16* out, long long npix) {
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < npix * 16;
-       i += (long long)gridDim.x * blockDim.x) {
-    const long long p = i / 16;
-    const int c = int(i % 16);
-    out[i] = __float2bfloat16(c < cin ? x[p * cin + c] : 0.f);
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < npix;
+       p += (long long)gridDim.x * blockDim.x) {
+    __align__(16) bf16 v[16];
+#pragma unroll
+    for (int c = 0; c < 16; ++c) v[c] = __float2bfloat16(c < cin ? x[p * cin + c] : 0.f);
+    uint4* o = reinterpret_cast<uint4*>(out + p * 16);
+    o[0] = reinterpret_cast<const uint4*>(v)[0];
+    o[1] = reinterpret_cast<const uint4*>(v)[1];
   }
 }
 
 int pack_input(lbpf_unet* n, const float* x) {
   const long long npix = (long long)n->cfg.batch * n->H[0] * n->W[0];
-  long long blocks = (npix * 16 + 255) / 256;
+  long long blocks = (npix + 255) / 256;
   if (blocks > 152 * 32) blocks = 152 * 32;
   pack_input_kernel<<<int(blocks), 256, 0, n->stream>>>(x, n->cfg.in_ch, n->xin.p, npix);
   UCK(n, cudaGetLastError());

@@ -364,24 +364,29 @@ __global__ void upsample_bwd_mask_kernel(const bf16* g, bf16* gx, const bf16* ac
 }
 
 // 1x1 head: y[p][o] = b[o] + sum_c x[p][c] w[o][c] (FP32 out); one pixel per
-// thread, weights staged in shared memory
+// thread, weights staged in shared memory; the output count O is a template
+// parameter so that the accumulators stay in registers
+template <int O>
 __global__ void head_fwd_kernel(const bf16* x, int C, const float* w, const float* b, float* y,
-                                int O, long long npix) {
-  __shared__ float sw[8 * 256 + 8];
+                                long long npix) {
+  __shared__ float sw[O * 256 + O];
   for (int i = threadIdx.x; i < O * C; i += blockDim.x) sw[i] = w[i];
-  if (threadIdx.x < O) sw[8 * 256 + threadIdx.x] = b[threadIdx.x];
+  if (threadIdx.x < O) sw[O * 256 + threadIdx.x] = b[threadIdx.x];
   __syncthreads();
   for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < npix;
        p += (long long)gridDim.x * blockDim.x) {
-    float acc[8];
-    for (int o = 0; o < O; ++o) acc[o] = sw[8 * 256 + o];
+    float acc[O];
+#pragma unroll
+    for (int o = 0; o < O; ++o) acc[o] = sw[O * 256 + o];
     for (int c = 0; c < C; c += 8) {
       float f[8];
       unpack8(ld8(x + p * C + c), f);
+#pragma unroll
       for (int o = 0; o < O; ++o)
 #pragma unroll
-        for (int k = 0; k < 8; ++k) acc[o] += f[k] * sw[o * C + c + k];
+        for (int k = 0; k < 8; ++k) acc[o] = fmaf(f[k], sw[o * C + c + k], acc[o]);
     }
+#pragma unroll
     for (int o = 0; o < O; ++o) y[p * O + o] = acc[o];
   }
 }
@@ -571,8 +576,18 @@ cudaError_t upsample2_bwd_mask(const bf16* g, bf16* gx, const bf16* act, int C, 
 }
 cudaError_t head_fwd(const bf16* x, int C, const float* w, const float* b, float* y, int O,
                      long long npix, cudaStream_t s) {
-  if (!v8(C) || O > 8 || O * C > 8 * 256) return cudaErrorInvalidValue;
-  head_fwd_kernel<<<blocks_for(npix), 256, 0, s>>>(x, C, w, b, y, O, npix);
+  if (!v8(C) || O < 1 || O > 8 || C > 256) return cudaErrorInvalidValue;
+  const int g = blocks_for(npix);
+  switch (O) {
+    case 1: head_fwd_kernel<1><<<g, 256, 0, s>>>(x, C, w, b, y, npix); break;
+    case 2: head_fwd_kernel<2><<<g, 256, 0, s>>>(x, C, w, b, y, npix); break;
+    case 3: head_fwd_kernel<3><<<g, 256, 0, s>>>(x, C, w, b, y, npix); break;
+    case 4: head_fwd_kernel<4><<<g, 256, 0, s>>>(x, C, w, b, y, npix); break;
+    case 5: head_fwd_kernel<5><<<g, 256, 0, s>>>(x, C, w, b, y, npix); break;
+    case 6: head_fwd_kernel<6><<<g, 256, 0, s>>>(x, C, w, b, y, npix); break;
+    case 7: head_fwd_kernel<7><<<g, 256, 0, s>>>(x, C, w, b, y, npix); break;
+    default: head_fwd_kernel<8><<<g, 256, 0, s>>>(x, C, w, b, y, npix); break;
+  }
   return cudaGetLastError();
 }
 cudaError_t head_bwd(const bf16* x, int C, const float* w, const float* gy, int O, long long npix,
