@@ -104,7 +104,8 @@ WORKLOADS = {
                 desc="batched sweep of small instances: 256 2D coupled instances in one "
                      "persistent launch per step (sides U{32..128}, U0~U[0.1,0.6], "
                      "R~U[4,min(24,n/5)], u_in~U[0,0.02], fold 4 or 5, eps~U[0.02,0.06]; "
-                     "seed 4), FP16 shifted storage", desc_note="small instances"),
+                     "seed 4), FP16 shifted storage", desc_note="small instances",
+                kernel="step2d_batch_kernel_small"),
     "c5": dict(desc="learned block propagator on 2D 512x512 closed channels (periodic x, walls y, "
                     "body-force Poiseuille flow u_max~U[0,0.01], U0~U[0.25,0.45], R~U[6,16], "
                     "fold 4 or 5, eps~U[0.02,0.05]): BF16 U-Net 32/64/128/256 channels trained "
