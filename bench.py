@@ -783,7 +783,7 @@ def run_facets(args, w):
                                                           src=SRC_FACETS)),
                          "algorithmic_bytes_per_launch": meas_bytes},
             "cpu_baseline": cpu,
-            "gpu_launches": steps + 2 * (steps // every),
+            "gpu_launches": steps + (steps // every),  # the step, one shape kernel each
             "clocks": clk.summary(),
             "diag": {"step": d["step"], "solute_drift_rel": d["solute_drift_rel"]},
         }), flush=True)
