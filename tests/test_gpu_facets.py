@@ -78,7 +78,7 @@ def test_polygon_seed_shape_at_start(P, L):
     assert abs(r["Q"] - 1.0) < 2e-3
 
 
-@pytest.mark.parametrize("storage", ["fp64", "fp32"])
+@pytest.mark.parametrize("storage", ["fp64", "fp32", "fp16", "bf16"])
 def test_facets_of_the_same_field_match_oracle(P, L, storage):
     p = hex_case(P, 128, flow=1, u_in=0.01)
     nrm, d = L.rhombic_seed(100.0, 0.1)
