@@ -8,15 +8,19 @@ step over the whole grid; the metric is MLUPS (million node updates per
 second) with the HBM roofline of the step kernel beside it.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload c2|c1|c3|c3_fp16|c3_bf16|c2_fp16|c4|c5]
+                  [--workload c1|c2|c2_fp16|c3|c3s|c3_fp16|c3_bf16|c4|c4s|c5|c5net|f1|f2|f3]
+
+Workloads f1 (the crystal-shape measurement with a hexagonal seed), f2 (a
+baffle of solid nodes in front of the inlet) and f3 (the central Hermite MRT
+flow collision) run the C2 problem with those parts.
 
 Workload c5 times the learned block propagator (a U-Net trained on the GPU
 on trajectories of this solver, judged by and falling back to the LB)
 against the plain LB on a held-out problem; --steps is then the number of
 LB-equivalent steps timed.
 
-Multi-GPU: the path does not shard in this build (one grid per GPU), so N
-GPUs run N independent replicas ("replicas only", weak scaling).
+Multi-GPU: the step is not sharded (one grid per GPU), so N GPUs run N
+independent replicas ("replicas only", weak scaling).
 """
 from __future__ import annotations
 
