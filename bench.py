@@ -657,6 +657,7 @@ def main():
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "peak_source": peak_kind,
+                         "frac_of_nominal_7900": achieved / 7900.0,
                          "traffic": traffic,
                          "algorithmic_bytes_per_launch": w["bytes_per_lup"] * w["nodes"]},
             "cpu_baseline": cpu,
