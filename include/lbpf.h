@@ -127,7 +127,7 @@ typedef struct {
  * order with (1 - 1/(2 tau_f)) F, as Eq. 4-5 do), the trace of the second
  * order at chm_omega_bulk, third and fourth order at chm_omega_high.  With
  * every rate 1/tau_f and no force it is BGK with the product-form
- * equilibrium.  The batched step refuses CHM instances. */
+ * equilibrium.  A batch holds one collision for all its instances. */
 enum { LBPF_COLL_BGK = 0, LBPF_COLL_CHM = 1 };
 
 /* Circular (2D) / spherical (3D) seed: phi0 = tanh((radius - r)/(sqrt(2) W0))
@@ -322,9 +322,10 @@ typedef struct lbpf_batch lbpf_batch_t;
 
 /* Create `count` instances (1..65535) from p[i] and seed them with s[i]
  * (lbpf_create + lbpf_init_seed each).  All p[i] must be 2D with the same
- * `flow` and the same storage among LBPF_FP32, LBPF_FP16_SHIFTED,
- * LBPF_BF16_SHIFTED; sizes and every model parameter may differ.  EINVAL
- * otherwise.  stream: as for lbpf_create, shared by all instances. */
+ * `flow`, the same `collision` and the same storage among LBPF_FP32,
+ * LBPF_FP16_SHIFTED, LBPF_BF16_SHIFTED; sizes and every other model
+ * parameter may differ.  EINVAL otherwise.  Instances may carry solid nodes
+ * (lbpf_set_solid on lbpf_batch_instance; picked up by the next step).  stream: as for lbpf_create, shared by all instances. */
 int lbpf_batch_create(const lbpf_params* p, const lbpf_seed* s, int count, void* stream,
                       lbpf_batch_t** out);
 

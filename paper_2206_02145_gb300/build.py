@@ -15,10 +15,12 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "liblbpf.so")
-SOURCES = ["lbpf_api.cu", "step2d.cu", "step3d.cu", "batch2d.cu", "aux.cu", "noalloc.cu",
-           "unet.cu", "conv_tc.cu", "surrogate.cu", "facets.cu"]
-HEADERS = ["lbpf_internal.cuh", "lbpf_device.cuh", "step2d_core.cuh", "step2d_tile.cuh", "step3d_core.cuh", "tma_host.h",
-           "tma.cuh", "unet.cuh", "unet_ops.cuh", "lbpf_handle.cuh"]
+SOURCES = ["lbpf_api.cu", "step2d.cu", "step3d.cu", "batch2d.cu", "batch2d_fp32.cu",
+           "batch2d_fp16.cu", "batch2d_bf16.cu", "aux.cu", "noalloc.cu", "unet.cu", "conv_tc.cu",
+           "surrogate.cu", "facets.cu"]
+HEADERS = ["lbpf_internal.cuh", "lbpf_device.cuh", "step2d_core.cuh", "step2d_tile.cuh",
+           "step3d_core.cuh", "batch2d_kernels.cuh", "tma_host.h", "tma.cuh", "unet.cuh",
+           "unet_ops.cuh", "lbpf_handle.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2",
               "--expt-relaxed-constexpr"]

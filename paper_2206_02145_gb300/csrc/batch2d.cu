@@ -10,169 +10,64 @@
 // the live batch (all produce the same bits) and keeps the fastest.
 #include <vector>
 
-#include "step2d_tile.cuh"
+#include "batch2d_kernels.cuh"
 #include "tma_host.h"
 
 namespace lbk {
 namespace {
 
-constexpr int kBatchSpin = 1 << 22;
-
-// registers held to 20 resident warps per SM (five CTAs of 32 x 4), the
-// occupancy of the single-instance step
-template <typename T, bool FLOW, int TX, int TY, int S>
-__global__ void __launch_bounds__(TX* TY, (640 / (TX * TY)) > 2 ? 640 / (TX * TY) : 2)
-    step2d_batch_kernel(const BatchDesc* __restrict__ descs,
-                        const unsigned short* __restrict__ tile_inst, int total_tiles) {
-  using L = Tiles2D<T, FLOW, TX, TY>;
-  constexpr int NT = TX * TY, SX = TX + 2, SY = TY + 2;
-  extern __shared__ unsigned char smem_raw[];
-  __shared__ __align__(8) uint64_t full[S];
-  __shared__ float sh_phi[SY][SX];
-  __shared__ __align__(16) Model sm;  // model of the instance being computed
-  __shared__ int cur_inst;
-  unsigned char* smem = reinterpret_cast<unsigned char*>(
-      (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
-  const int tid = threadIdx.x;
-  const int first = blockIdx.x, G = gridDim.x;
-
-  auto issue = [&](int tile, int s) {
-    const BatchDesc& d = descs[tile_inst[tile]];
-    const int lt = tile - d.tile0;
-    issue_tile_2d<T, FLOW, TX, TY>(&d.fg, &d.h, &d.ring, &d.uown, &d.uhal, d.c, &full[s],
-                                   smem + s * L::STAGE, (lt % d.ntx) * TX, (lt / d.ntx) * TY);
-  };
-
-  if (tid == 0) {
-    for (int s = 0; s < S; ++s) mbar_init(&full[s], 1);
-    fence_barrier_init();
-    cur_inst = -1;
-  }
-  __syncthreads();
-  if (tid == 0)
-    for (int k = 0; k < S; ++k)
-      if (first + k * G < total_tiles) issue(first + k * G, k);
-
-  for (int k = 0;; ++k) {
-    const int tile = first + k * G;
-    if (tile >= total_tiles) break;
-    const int s = k % S;
-    const bool ok = mbar_wait_bounded(&full[s], uint32_t((k / S) & 1), kBatchSpin);
-    if (__syncthreads_or(!ok)) {
-      // a tile never arrived: report on its instance, let copies land, stop
-      if (tid == 0) {
-        atomicOr(descs[tile_inst[tile]].err, 2u);
-        for (int j = 1; j < S; ++j) {
-          const int kk = k + j;
-          if (first + kk * G < total_tiles)
-            mbar_wait_bounded(&full[kk % S], uint32_t((kk / S) & 1), kBatchSpin);
-        }
-      }
-      __syncthreads();
-      return;
-    }
-    const int inst = tile_inst[tile];
-    const BatchDesc& d = descs[inst];
-    if (inst != cur_inst) {  // uniform: every thread read cur_inst after the last barrier
-      const uint32_t* from = reinterpret_cast<const uint32_t*>(&d.m);
-      uint32_t* to = reinterpret_cast<uint32_t*>(&sm);
-      for (int w = tid; w < int(sizeof(Model) / 4); w += NT) to[w] = from[w];
-      __syncthreads();
-      if (tid == 0) cur_inst = inst;
-    }
-    const int lt = tile - d.tile0;
-    tile_2d<T, FLOW, TX, TY, false, false>(sm, static_cast<const T*>(d.src), static_cast<T*>(d.dst),
-                             d.ring_cur, d.err, (lt % d.ntx) * TX, (lt / d.ntx) * TY, d.c,
-                             smem + s * L::STAGE, &sh_phi[0][0]);
-    __syncthreads();  // stage s, sh_phi and sm are free again
-    if (tid == 0 && tile + S * G < total_tiles) {
-      fence_proxy_async_smem();
-      issue(tile + S * G, s);
-    }
-  }
-}
-
-// Compiled variants: (tile rows, pipeline stages).
-struct Variant {
-  int ty, stages;
-};
-constexpr Variant kVariants[] = {{4, 2}, {8, 2}, {2, 3}, {4, 3}};
-constexpr int kNumVariants = int(sizeof(kVariants) / sizeof(kVariants[0]));
-
-template <typename T, bool FLOW, int TY, int S>
-struct VariantImpl {
-  static constexpr int TX = 32;
-  using L = Tiles2D<T, FLOW, TX, TY>;
-  static cudaError_t setup(int* ctas, int* smem) {
-    auto kern = step2d_batch_kernel<T, FLOW, TX, TY, S>;
-    *smem = S * L::STAGE + 128;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, *smem);
-    if (e != cudaSuccess) return e;
-    int dev = 0, sms = 0, per_sm = 0;
-    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
-    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
-      return e;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, TX * TY, *smem)) !=
-        cudaSuccess)
-      return e;
-    *ctas = sms * (per_sm > 0 ? per_sm : 1);
-    return cudaSuccess;
-  }
-  static cudaError_t launch(const BatchDesc* d, const unsigned short* ti, int total, int ctas,
-                            int smem, cudaStream_t s) {
-    const int grid = total < ctas ? total : ctas;
-    step2d_batch_kernel<T, FLOW, TX, TY, S><<<grid, TX * TY, smem, s>>>(d, ti, total);
-    return cudaGetLastError();
-  }
-};
-
-template <typename T, bool FLOW>
-cudaError_t dispatch(int v, bool setup, int* ctas, int* smem, const BatchDesc* d,
-                     const unsigned short* ti, int total, cudaStream_t s) {
-#define LBPF_VARIANT(I, TY, S)                                               \
-  case I:                                                                    \
-    return setup ? VariantImpl<T, FLOW, TY, S>::setup(ctas, smem)            \
-                 : VariantImpl<T, FLOW, TY, S>::launch(d, ti, total, *ctas, *smem, s);
-  switch (v) {
-    LBPF_VARIANT(0, 4, 2)
-    LBPF_VARIANT(1, 8, 2)
-    LBPF_VARIANT(2, 2, 3)
-    LBPF_VARIANT(3, 4, 3)
-    default: return cudaErrorInvalidValue;
-  }
-#undef LBPF_VARIANT
-}
-
-cudaError_t dispatch_any(int storage, int flow, int v, bool setup, int* ctas, int* smem,
-                         const BatchDesc* d, const unsigned short* ti, int total, cudaStream_t s) {
+cudaError_t dispatch_any(int storage, int flow, int v, bool mask, bool chm, bool setup, int* ctas,
+                         int* smem, const BatchDesc* d, const unsigned short* ti, int total,
+                         cudaStream_t s) {
   switch (storage) {
     case ST_FP16:
-      return flow ? dispatch<__half, true>(v, setup, ctas, smem, d, ti, total, s)
-                  : dispatch<__half, false>(v, setup, ctas, smem, d, ti, total, s);
+      return batch_dispatch_fp16(flow, v, mask, chm, setup, ctas, smem, d, ti, total, s);
     case ST_BF16:
-      return flow ? dispatch<__nv_bfloat16, true>(v, setup, ctas, smem, d, ti, total, s)
-                  : dispatch<__nv_bfloat16, false>(v, setup, ctas, smem, d, ti, total, s);
+      return batch_dispatch_bf16(flow, v, mask, chm, setup, ctas, smem, d, ti, total, s);
     default:
-      return flow ? dispatch<float, true>(v, setup, ctas, smem, d, ti, total, s)
-                  : dispatch<float, false>(v, setup, ctas, smem, d, ti, total, s);
+      return batch_dispatch_fp32(flow, v, mask, chm, setup, ctas, smem, d, ti, total, s);
   }
+}
+
+// the solid flags of one instance's TX x TY tiles (tile or one-node halo holds
+// a solid node), into flags[0 .. ntx * nty)
+__global__ void batch_solid_tiles_kernel(const Model m, unsigned char* flags, int ntx, int nty,
+                                         int tx, int ty) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= ntx * nty) return;
+  const int x0 = (t % ntx) * tx, y0 = (t / ntx) * ty;
+  bool any = false;
+  for (int ly = -1; ly <= ty; ++ly)
+    for (int lx = -1; lx <= tx; ++lx) any |= solid_mapped(m, x0 + lx, y0 + ly);
+  flags[t] = any ? 1 : 0;
 }
 
 }  // namespace
 
-int batch_variant_count() { return kNumVariants; }
-int batch_variant_rows(int v) { return kVariants[v].ty; }
-int batch_variant_stages(int v) { return kVariants[v].stages; }
+int batch_variant_count() { return batch::kNumVariants; }
+int batch_variant_rows(int v) { return batch::kVariants[v].ty; }
+int batch_variant_stages(int v) { return batch::kVariants[v].stages; }
 
 cudaError_t batch_plan_build(const BatchMember* members, int count, int storage, int flow, int v,
                              BatchPlan* plan) {
-  const int ty = kVariants[v].ty, tx = 32;
+  const int ty = batch::kVariants[v].ty, tx = 32;
   const size_t es = storage == ST_FP32 ? 4 : 2;
   const int qfg = (flow ? 9 : 0) + 9;
   const int hx = int(16 / es);
   std::vector<BatchDesc> host[2];
   std::vector<unsigned short> inst;
   int tile0 = 0;
+  bool mask = false;
+  for (int i = 0; i < count; ++i) mask = mask || members[i].m.solid != nullptr;
+  int all_tiles = 0;
+  for (int i = 0; i < count; ++i)
+    all_tiles += ((members[i].m.nx + tx - 1) / tx) * ((members[i].m.ny + ty - 1) / ty);
+  cudaError_t e;
+  if (mask) {  // (the masks were written on the instances' streams)
+    if ((e = cudaDeviceSynchronize()) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&plan->solid_tiles, size_t(all_tiles))) != cudaSuccess) return e;
+    if ((e = cudaMemset(plan->solid_tiles, 0, size_t(all_tiles))) != cudaSuccess) return e;
+  }
   for (int i = 0; i < count; ++i) {
     const Model& m = members[i].m;
     const int ntx = (m.nx + tx - 1) / tx, nty = (m.ny + ty - 1) / ty;
@@ -205,6 +100,7 @@ cudaError_t batch_plan_build(const BatchMember* members, int count, int storage,
           return cudaErrorInvalidValue;
       }
       d.m = m;
+      if (m.solid) d.m.solid_tiles = plan->solid_tiles + tile0;
       d.c = c;
       d.src = members[i].pops[c];
       d.dst = members[i].pops[c ^ 1];
@@ -216,13 +112,19 @@ cudaError_t batch_plan_build(const BatchMember* members, int count, int storage,
       host[c].push_back(d);
     }
     for (int t = 0; t < ntx * nty; ++t) inst.push_back((unsigned short)i);
+    if (m.solid) {
+      batch_solid_tiles_kernel<<<(ntx * nty + 127) / 128, 128>>>(m, plan->solid_tiles + tile0, ntx,
+                                                                  nty, tx, ty);
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
     tile0 += ntx * nty;
   }
   plan->total_tiles = tile0;
   plan->variant = v;
   plan->storage = storage;
   plan->flow = flow;
-  cudaError_t e;
+  plan->mask = mask;
+  plan->chm = members[0].m.chm;
   for (int c = 0; c < 2; ++c) {
     if ((e = cudaMalloc(&plan->desc[c], sizeof(BatchDesc) * count)) != cudaSuccess) return e;
     if ((e = cudaMemcpy(plan->desc[c], host[c].data(), sizeof(BatchDesc) * count,
@@ -234,21 +136,24 @@ cudaError_t batch_plan_build(const BatchMember* members, int count, int storage,
   if ((e = cudaMemcpy(plan->tile_inst, inst.data(), sizeof(unsigned short) * inst.size(),
                       cudaMemcpyHostToDevice)) != cudaSuccess)
     return e;
-  plan->bytes = 2 * sizeof(BatchDesc) * count + sizeof(unsigned short) * inst.size();
-  return dispatch_any(storage, flow, v, true, &plan->ctas, &plan->smem, nullptr, nullptr, 0,
+  if (mask && (e = cudaDeviceSynchronize()) != cudaSuccess) return e;
+  plan->bytes = 2 * sizeof(BatchDesc) * count + sizeof(unsigned short) * inst.size() +
+                (mask ? size_t(all_tiles) : 0);
+  return dispatch_any(storage, flow, v, plan->mask, plan->chm, true, &plan->ctas, &plan->smem, nullptr, nullptr, 0,
                       nullptr);
 }
 
 cudaError_t batch_plan_launch(const BatchPlan& plan, int c, cudaStream_t s) {
   int ctas = plan.ctas, smem = plan.smem;
-  return dispatch_any(plan.storage, plan.flow, plan.variant, false, &ctas, &smem, plan.desc[c],
-                      plan.tile_inst, plan.total_tiles, s);
+  return dispatch_any(plan.storage, plan.flow, plan.variant, plan.mask, plan.chm, false, &ctas,
+                      &smem, plan.desc[c], plan.tile_inst, plan.total_tiles, s);
 }
 
 void batch_plan_free(BatchPlan* plan) {
   for (int c = 0; c < 2; ++c)
     if (plan->desc[c]) cudaFree(plan->desc[c]);
   if (plan->tile_inst) cudaFree(plan->tile_inst);
+  if (plan->solid_tiles) cudaFree(plan->solid_tiles);
   *plan = BatchPlan{};
 }
 

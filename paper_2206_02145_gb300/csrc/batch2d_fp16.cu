@@ -1,0 +1,12 @@
+// Batched 2D step: the kernel variants of FP16 population storage.
+#include "batch2d_kernels.cuh"
+
+namespace lbk {
+
+cudaError_t batch_dispatch_fp16(int flow, int v, bool mask, bool chm, bool setup, int* ctas,
+                              int* smem, const BatchDesc* d, const unsigned short* ti,
+                              int total, cudaStream_t s) {
+  return batch::dispatch_storage<__half>(flow, v, mask, chm, setup, ctas, smem, d, ti, total, s);
+}
+
+}  // namespace lbk

@@ -864,14 +864,9 @@ int batch_build(lbpf_batch* b) {
   batch_drop_graph(b);
   for (int v = 0; v < b->nplans; ++v) lbk::batch_plan_free(&b->plans[v]);
   std::vector<lbk::BatchMember> mem(b->kids.size());
-  for (size_t i = 0; i < b->kids.size(); ++i) {
-    if (b->kids[i]->m.solid)
-      return bfail(b, LBPF_EINVAL, "instance %d has solid nodes: the batched step has no "
-                   "solid-node path; step it on its own", int(i));
-    if (b->kids[i]->m.chm)
-      return bfail(b, LBPF_EINVAL, "instance %d uses the central Hermite MRT: the batched "
-                   "step is BGK only", int(i));
-  }
+  for (size_t i = 0; i < b->kids.size(); ++i)
+    if (b->kids[i]->m.chm != b->kids[0]->m.chm)
+      return bfail(b, LBPF_EINVAL, "instance %d: a batch holds one flow collision", int(i));
   for (size_t i = 0; i < b->kids.size(); ++i) {
     lbpf* k = b->kids[i];
     mem[i].m = k->m;
@@ -929,10 +924,10 @@ int lbpf_batch_create(const lbpf_params* p, const lbpf_seed* s, int count, void*
   *out = nullptr;
   for (int i = 0; i < count; ++i) {
     if (p[i].dim != 2 || p[i].flow != p[0].flow || p[i].storage != p[0].storage ||
-        p[i].storage == LBPF_FP64 || p[i].collision != LBPF_COLL_BGK) {
+        p[i].storage == LBPF_FP64 || p[i].collision != p[0].collision) {
       fprintf(stderr,
-              "lbpf_batch_create: instance %d: a batch holds 2D instances with one flow flag "
-              "and one storage among FP32, FP16, BF16\n", i);
+              "lbpf_batch_create: instance %d: a batch holds 2D instances with one flow flag, "
+              "one flow collision and one storage among FP32, FP16, BF16\n", i);
       return LBPF_EINVAL;
     }
   }

@@ -171,7 +171,9 @@ struct BatchMember {  // what the batch needs of one instance
 struct BatchPlan {  // device tables of one compiled variant
   BatchDesc* desc[2] = {nullptr, nullptr};
   unsigned short* tile_inst = nullptr;
+  unsigned char* solid_tiles = nullptr;  // per-tile solid flags of this variant's tiles
   int total_tiles = 0, variant = 0, storage = 0, flow = 0, ctas = 0, smem = 0;
+  int mask = 0, chm = 0;  // some instance has solid nodes; the flow collides by CHM
   size_t bytes = 0;
 };
 int batch_variant_count();
@@ -180,6 +182,15 @@ int batch_variant_stages(int v);
 cudaError_t batch_plan_build(const BatchMember* members, int count, int storage, int flow, int v,
                              BatchPlan* plan);
 cudaError_t batch_plan_launch(const BatchPlan& plan, int c, cudaStream_t s);
+// the kernel variants of one storage type (setup: occupancy and shared memory
+// into *ctas, *smem; else one launch of the step over the tile list)
+#define LBPF_BATCH_DISPATCH(NAME)                                                            \
+  cudaError_t NAME(int flow, int v, bool mask, bool chm, bool setup, int* ctas, int* smem,   \
+                   const BatchDesc* d, const unsigned short* ti, int total, cudaStream_t s);
+LBPF_BATCH_DISPATCH(batch_dispatch_fp32)
+LBPF_BATCH_DISPATCH(batch_dispatch_fp16)
+LBPF_BATCH_DISPATCH(batch_dispatch_bf16)
+#undef LBPF_BATCH_DISPATCH
 void batch_plan_free(BatchPlan* plan);
 
 // Seeded initial state (FP64 arithmetic, stored in the population type).

@@ -103,6 +103,12 @@ def test_batch_validation_before_any_gpu_work(lib):
     with pytest.raises(lib.LbpfError) as e:
         lib.lbpf_batch_create(pm, [(4, 4, 0, 2, 0.3, 0, 1)] * 2)
     assert e.value.code == lib.EINVAL
+    # one flow collision per batch
+    pc = [lib.lbpf_params_default(flow=1),
+          lib.lbpf_params_default(flow=1, collision=lib.COLL_CHM)]
+    with pytest.raises(lib.LbpfError) as e:
+        lib.lbpf_batch_create(pc, [(4, 4, 0, 2, 0.3, 0, 1)] * 2)
+    assert e.value.code == lib.EINVAL
     assert lib._lib.lbpf_batch_step(None, 1) == lib.EINVAL
     assert lib._lib.lbpf_batch_count(None) == 0
 

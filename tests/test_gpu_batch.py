@@ -82,6 +82,33 @@ def test_batch_picks_up_reinitialised_instance(L):
     assert np.array_equal(b.instance(1).state(), sim.state())
 
 
+@pytest.mark.parametrize("storage_name", ["FP32", "BF16_SHIFTED"])
+def test_batch_with_obstacles_equals_single_instances_bitwise(L, storage_name):
+    # obstacles in some instances (edge tiles, across the periodic wrap, a
+    # single node): each variant's per-tile solid flags are its own
+    storage = getattr(L, storage_name)
+    params, seeds = sweep(storage)
+    masks = {}
+    for i in (0, 3, 4):
+        nx, ny = params[i]["nx"], params[i]["ny"]
+        m = np.zeros((ny, nx), np.uint8)
+        m[ny // 4:3 * ny // 4, nx // 5:nx // 5 + 2] = 1
+        m[0, nx // 2] = 1          # wraps to the top row
+        m[ny - 1, 3 * nx // 4] = 1
+        masks[i] = m
+    b = L.Batch(params, seeds)
+    for i, m in masks.items():
+        b.instance(i).set_solid(m)
+    b.step(131)
+    for i, (p, s) in enumerate(zip(params, seeds)):
+        sim = L.Sim(**p)
+        if i in masks:
+            sim.set_solid(masks[i])
+        sim.init_seed(*s)
+        sim.step(131)
+        assert np.array_equal(b.instance(i).state(), sim.state()), i
+
+
 def test_batch_rejects_mixed_instances(L):
     params, seeds = sweep(L.FP32, n=2)
     params[1]["storage"] = L.FP16_SHIFTED

@@ -140,22 +140,29 @@ def test_graph_batch_and_restart_with_a_mask(P, L):
     g.step(30)
     r.step(30)
     assert np.array_equal(g.state(), r.state())
-    # the batched step has no solid-node path: it refuses a masked instance,
-    # and steps the batch again once the mask is gone
+    # the batched step: a masked and a free instance side by side evolve bit
+    # for bit like each stepped alone; removing the mask is picked up too
     kw = dict(dim=2, nx=100, ny=72, bc=(1, 0, 0), flow=1, fold=5, eps_aniso=0.03,
               u_inlet=0.01, u0_inlet=0.4, storage=L.FP32)
     bt = L.Batch([kw, kw], [seed, seed], None)
     bt.instance(0).set_solid(mask)
-    with pytest.raises(L.LbpfError) as e:
-        bt.step(1)
-    assert e.value.code == L.EINVAL
-    bt.instance(0).set_solid(None)
     bt.step(100)
     free = P.lib_sim(p, "fp32")
     free.init_seed(*seed)
     free.step(100)
-    for i in range(2):
-        assert np.array_equal(bt.instance(i).state(), free.state())
+    masked = P.lib_sim(p, "fp32")
+    masked.set_solid(mask)
+    masked.init_seed(*seed)
+    masked.step(100)
+    assert np.array_equal(bt.instance(0).state(), masked.state())
+    assert np.array_equal(bt.instance(1).state(), free.state())
+    bt.instance(0).set_solid(None)
+    masked.set_solid(None)
+    bt.step(30)
+    free.step(30)
+    masked.step(30)
+    assert np.array_equal(bt.instance(0).state(), masked.state())
+    assert np.array_equal(bt.instance(1).state(), free.state())
     bt.close()
 
 
