@@ -180,7 +180,7 @@ orc_sim* orc_create(const orc_params* p) {
   s->a2 = zalloc(n);
   s->tauphi = zalloc(n);
   s->Q = zalloc(n);
-  if (p->collision == 1 && p->dim == 2) s->fpost = zalloc(n * s->LF.q);
+  if (p->collision == 1) s->fpost = zalloc(n * s->LF.q);
   return s;
 }
 
@@ -385,21 +385,26 @@ static void node_gradient_terms(orc_sim* s, int i) {
             s->lambda * s->U[i] * (1.0 - phi * phi) * (1.0 - phi * phi); /* Eq. 20 */
 }
 
-/* ---- central Hermite multiple-relaxation-time collision of f (2D) ---------
+/* ---- central Hermite multiple-relaxation-time collision of f -------------
  * The collision the paper uses for the flow (Sec. 2.2, after Eq. 9: a central
  * Hermite MRT, defined in the work it cites), in this reading:
  *   1. central Hermite moments of f about the velocity u* of the equilibrium,
  *      k_j = sum_a f_a P_j(c_a - u*), with the nine D2Q9 polynomials
  *      1, X, Y, X^2 - cs2, Y^2 - cs2, XY, X^2 Y - cs2 Y, X Y^2 - cs2 X,
- *      X^2 Y^2 - cs2 (X^2 + Y^2) + cs2^2;
+ *      X^2 Y^2 - cs2 (X^2 + Y^2) + cs2^2, or the nineteen D3Q19 ones: the
+ *      products H_i(X) H_j(Y) H_k(Z) of the Hermite polynomials H_0 = 1,
+ *      H_1 = X, H_2 = X^2 - cs2 with i, j, k <= 2 and at most two of them
+ *      non-zero (1; X, Y, Z; three H_2; XY, XZ, YZ; six H_2 H_1; three
+ *      H_2 H_2);
  *   2. their equilibrium values: rho, then zeros (the moments of the
- *      product-form equilibrium about its own velocity);
+ *      Maxwellian about its own velocity; in 2D those of the product-form
+ *      equilibrium);
  *   3. relaxation by order: the first-order moments at 1/tau_f (as BGK:
  *      momentum relaxes towards rho u*) with the force, (1 - w/2) F; the
- *      deviatoric second-order moments and XY at 1/tau_f (the viscosity,
- *      Eq. 10); their trace at omega_bulk (default 1); third and fourth
- *      order at omega_high (default 1);
- *   4. back to populations: the solution of the 9 x 9 system
+ *      deviatoric second-order moments and the mixed ones (XY, ...) at
+ *      1/tau_f (the viscosity, Eq. 10); their trace at omega_bulk (default
+ *      1); third and fourth order at omega_high (default 1);
+ *   4. back to populations: the solution of the q x q system
  *      sum_a P_j(c_a - u*) f*_a = k*_j. */
 static void chm_poly(double X, double Y, double cs2, double P[9]) {
   P[0] = 1.0;
@@ -411,6 +416,22 @@ static void chm_poly(double X, double Y, double cs2, double P[9]) {
   P[6] = X * X * Y - cs2 * Y;
   P[7] = X * Y * Y - cs2 * X;
   P[8] = X * X * Y * Y - cs2 * (X * X + Y * Y) + cs2 * cs2;
+}
+
+static double hermite(int k, double X, double cs2) {
+  return k == 0 ? 1.0 : k == 1 ? X : X * X - cs2;
+}
+
+/* the D3Q19 polynomials, in the order: 1; X, Y, Z; H2(X), H2(Y), H2(Z); XY,
+ * XZ, YZ; H2(X) Y, H2(X) Z, X H2(Y), H2(Y) Z, X H2(Z), Y H2(Z); H2(X) H2(Y),
+ * H2(X) H2(Z), H2(Y) H2(Z) */
+static void chm_poly3(double X, double Y, double Z, double cs2, double P[19]) {
+  static const int e[19][3] = {{0, 0, 0}, {1, 0, 0}, {0, 1, 0}, {0, 0, 1}, {2, 0, 0},
+                               {0, 2, 0}, {0, 0, 2}, {1, 1, 0}, {1, 0, 1}, {0, 1, 1},
+                               {2, 1, 0}, {2, 0, 1}, {1, 2, 0}, {0, 2, 1}, {1, 0, 2},
+                               {0, 1, 2}, {2, 2, 0}, {2, 0, 2}, {0, 2, 2}};
+  for (int j = 0; j < 19; ++j)
+    P[j] = hermite(e[j][0], X, cs2) * hermite(e[j][1], Y, cs2) * hermite(e[j][2], Z, cs2);
 }
 
 /* solve A x = b (n x n, row-major) by Gauss-Jordan elimination with partial
@@ -445,35 +466,42 @@ static void solve_dense(double* A, double* b, int n) {
 
 static void chm_collide(orc_sim* s, int i) {
   const lattice* L = &s->LF;
-  const int n = s->n;
+  const int n = s->n, q = L->q, D = s->p.dim;
   const double cs2 = L->cs2;
   const double wf = 1.0 / s->p.tau_f;
   const double wb = s->p.omega_bulk > 0.0 ? s->p.omega_bulk : 1.0;
   const double wh = s->p.omega_high > 0.0 ? s->p.omega_high : 1.0;
-  const double vx = s->us[0][i], vy = s->us[1][i];
-  double M[81], k[9];
-  for (int j = 0; j < 9; ++j) k[j] = 0.0;
-  for (int a = 0; a < 9; ++a) {
-    double P[9];
-    chm_poly(L->c[a][0] - vx, L->c[a][1] - vy, cs2, P);
+  const double v[3] = {s->us[0][i], s->us[1][i], s->us[2][i]};
+  double M[19 * 19], k[19];
+  for (int j = 0; j < q; ++j) k[j] = 0.0;
+  for (int a = 0; a < q; ++a) {
+    double P[19];
+    if (D == 2)
+      chm_poly(L->c[a][0] - v[0], L->c[a][1] - v[1], cs2, P);
+    else
+      chm_poly3(L->c[a][0] - v[0], L->c[a][1] - v[1], L->c[a][2] - v[2], cs2, P);
     double fa = s->f[(size_t)a * n + i];
-    for (int j = 0; j < 9; ++j) {
-      M[j * 9 + a] = P[j];
+    for (int j = 0; j < q; ++j) {
+      M[j * q + a] = P[j];
       k[j] += P[j] * fa;
     }
   }
-  /* relaxation; equilibrium values: rho (k[0], conserved), zeros */
-  double ks[9];
+  /* relaxation; equilibrium values: rho (k[0], conserved), zeros.  Moments
+   * 1..D: first order; D+1..2D: the diagonal second order; then the mixed
+   * second order (1 in 2D, 3 in 3D); the rest third and fourth order. */
+  double ks[19];
   ks[0] = k[0];
-  ks[1] = (1.0 - wf) * k[1] + (1.0 - 0.5 * wf) * s->F[0][i];
-  ks[2] = (1.0 - wf) * k[2] + (1.0 - 0.5 * wf) * s->F[1][i];
-  double tr = (1.0 - wb) * (k[3] + k[4]), dv = (1.0 - wf) * (k[3] - k[4]);
-  ks[3] = 0.5 * (tr + dv);
-  ks[4] = 0.5 * (tr - dv);
-  ks[5] = (1.0 - wf) * k[5];
-  for (int j = 6; j < 9; ++j) ks[j] = (1.0 - wh) * k[j];
-  solve_dense(M, ks, 9);
-  for (int a = 0; a < 9; ++a) s->fpost[(size_t)a * n + i] = ks[a];
+  for (int d = 0; d < D; ++d) ks[1 + d] = (1.0 - wf) * k[1 + d] + (1.0 - 0.5 * wf) * s->F[d][i];
+  double mean = 0.0;
+  for (int d = 0; d < D; ++d) mean += k[1 + D + d];
+  mean /= D;
+  for (int d = 0; d < D; ++d)
+    ks[1 + D + d] = (1.0 - wb) * mean + (1.0 - wf) * (k[1 + D + d] - mean);
+  const int nmix = D == 2 ? 1 : 3;
+  for (int j = 1 + 2 * D; j < 1 + 2 * D + nmix; ++j) ks[j] = (1.0 - wf) * k[j];
+  for (int j = 1 + 2 * D + nmix; j < q; ++j) ks[j] = (1.0 - wh) * k[j];
+  solve_dense(M, ks, q);
+  for (int a = 0; a < q; ++a) s->fpost[(size_t)a * n + i] = ks[a];
 }
 
 /* ---- post-collision values at a node (Eqs. 4-9, 13-16, 19-21) ------------- */

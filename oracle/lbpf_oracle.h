@@ -49,7 +49,7 @@ typedef struct {
   double u_inlet;     /* inlet velocity along +x */
   double u0_inlet;    /* supersaturation of the inflow */
   double body[3];     /* constant body force (test cases only) */
-  int collision;      /* flow collision: 0 BGK (Eq. 8), 1 central Hermite MRT (2D) */
+  int collision;      /* flow collision: 0 BGK (Eq. 8), 1 central Hermite MRT */
   double omega_bulk;  /* CHM: rate of the trace of the second-order moments (0: 1) */
   double omega_high;  /* CHM: rate of the third- and fourth-order moments (0: 1) */
 } orc_params;
