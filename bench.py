@@ -8,11 +8,13 @@ step over the whole grid; the metric is MLUPS (million node updates per
 second) with the HBM roofline of the step kernel beside it.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload c1|c2|c2_fp16|c3|c3s|c3_fp16|c3_bf16|c4|c4s|c5|c5net|f1|f2|f3]
+                  [--workload c1|c2|c2_fp16|c3|c3s|c3_fp16|c3_bf16|c4|c4s|c5|c5net|f1|f2|f3|
+                              f3_3d|f3_3ds]
 
 Workloads f1 (the crystal-shape measurement with a hexagonal seed), f2 (a
 baffle of solid nodes in front of the inlet) and f3 (the central Hermite MRT
-flow collision) run the C2 problem with those parts.
+flow collision) run the C2 problem with those parts; f3_3d runs the C3 problem
+with the central Hermite MRT (f3_3ds: its 128^3 case for profiler captures).
 
 Workload c5 times the learned block propagator (a U-Net trained on the GPU
 on trajectories of this solver, judged by and falling back to the LB)
@@ -41,7 +43,8 @@ sys.path.insert(0, ROOT)
 # stand only while their digest is unchanged)
 SRC_2D = ["step2d.cu", "step2d_tile.cuh", "step2d_core.cuh", "lbpf_device.cuh", "tma.cuh"]
 SRC_3D = ["step3d.cu", "step3d_core.cuh", "lbpf_device.cuh"]
-SRC_BATCH = ["batch2d.cu", "step2d_tile.cuh", "step2d_core.cuh", "lbpf_device.cuh", "tma.cuh"]
+SRC_BATCH = ["batch2d.cu", "batch2d_kernels.cuh", "batch2d_fp32.cu", "batch2d_fp16.cu",
+             "batch2d_bf16.cu", "step2d_tile.cuh", "step2d_core.cuh", "lbpf_device.cuh", "tma.cuh"]
 SRC_CONV = ["conv_tc.cu", "tma.cuh"]
 SRC_FACETS = ["facets.cu"]
 
@@ -97,6 +100,18 @@ WORKLOADS = {
                      "phase field), cubic eps 0.04, sphere R=12, U0=0.3, inflow 0.005",
                 desc_note="FP32"),
     "c3_bf16": dict(base="c3", storage="bf16"),
+    "f3_3d": dict(base="c3", desc_note=True,
+                  desc="3D 256^3 coupled LB (D3Q19 flow, D3Q7 solute and phase field), cubic "
+                       "eps 0.04, sphere R=12, U0=0.3, inflow 0.005, the flow colliding by the "
+                       "central Hermite MRT (trace of the second-order and the third/fourth-"
+                       "order central moments relaxed at 1)",
+                  collision=1, kernel="step3d_march_kernel_chm"),
+    "f3_3ds": dict(base="c3", nx=128, ny=128, nz=128, collision=1,
+                   kernel="step3d_march_kernel_chm",
+                   seed=(64.0, 64.0, 64.0, 12.0, 0.3, 0.01, 1), desc_note=True,
+                   desc="3D 128^3 case of f3_3d for profiler captures (D3Q19 flow colliding by "
+                        "the central Hermite MRT, D3Q7 solute and phase field), cubic eps 0.04, "
+                        "sphere R=12, U0=0.3, inflow 0.005"),
     "c4": dict(desc="batched sweep: 64 2D coupled instances in one persistent launch per step "
                     "(sides U{256..768}, U0~U[0.1,0.6], R~U[4,24], u_in~U[0,0.02], fold 4 or 5, "
                     "eps~U[0.02,0.06]; seed 4), FP16 shifted storage",

@@ -110,7 +110,7 @@ typedef struct {
   double u_inlet;     /* inflow velocity along +x (|u| <= 0.1) */
   double u0_inlet;    /* supersaturation of the inflow */
   double body_force[3]; /* constant body force density (test flows); usually 0 */
-  int collision;      /* flow collision: LBPF_COLL_BGK (Eq. 8) or LBPF_COLL_CHM (2D) */
+  int collision;      /* flow collision: LBPF_COLL_BGK (Eq. 8) or LBPF_COLL_CHM */
   double chm_omega_bulk; /* CHM: rate of the trace of the second-order central
                             moments, in (0, 2); 0 selects 1 */
   double chm_omega_high; /* CHM: rate of the third- and fourth-order central
@@ -119,15 +119,18 @@ typedef struct {
 
 /* Flow collision.  LBPF_COLL_CHM: the central Hermite multiple-relaxation-
  * time collision the paper uses for the flow (after Eq. 9; defined in the
- * work it cites), 2D with flow only.  Central Hermite moments of f about the
- * equilibrium velocity u* (the nine D2Q9 polynomials of X = c_x - u*_x,
+ * work it cites), with flow only.  Central Hermite moments of f about the
+ * equilibrium velocity u* (in 2D the nine D2Q9 polynomials of X = c_x - u*_x,
  * Y = c_y - u*_y: 1, X, Y, X^2 - cs^2, Y^2 - cs^2, XY, X^2 Y - cs^2 Y,
- * X Y^2 - cs^2 X, X^2 Y^2 - cs^2 (X^2 + Y^2) + cs^4) relax towards rho and
- * zeros: first order and the deviatoric second order at 1/tau_f (the first
+ * X Y^2 - cs^2 X, X^2 Y^2 - cs^2 (X^2 + Y^2) + cs^4; in 3D the nineteen
+ * D3Q19 products H_i(X) H_j(Y) H_k(Z), H_0 = 1, H_1 = X, H_2 = X^2 - cs^2,
+ * i, j, k <= 2 with at most two non-zero) relax towards rho and zeros: first
+ * order, the mixed and the deviatoric second order at 1/tau_f (the first
  * order with (1 - 1/(2 tau_f)) F, as Eq. 4-5 do), the trace of the second
  * order at chm_omega_bulk, third and fourth order at chm_omega_high.  With
- * every rate 1/tau_f and no force it is BGK with the product-form
- * equilibrium.  A batch holds one collision for all its instances. */
+ * every rate 1/tau_f and no force it is BGK with the equilibrium that has
+ * the Maxwellian's moments (in 2D the product form).  A batch holds one
+ * collision for all its instances. */
 enum { LBPF_COLL_BGK = 0, LBPF_COLL_CHM = 1 };
 
 /* Circular (2D) / spherical (3D) seed: phi0 = tanh((radius - r)/(sqrt(2) W0))

@@ -94,7 +94,7 @@ int validate(const lbpf_params* p, char* why, size_t n) {
   if (p->collision != LBPF_COLL_BGK && p->collision != LBPF_COLL_CHM)
     return bad("unknown collision");
   if (p->collision == LBPF_COLL_CHM) {
-    if (p->dim != 2 || !p->flow) return bad("the central Hermite MRT is 2D with flow");
+    if (!p->flow) return bad("the central Hermite MRT is a collision of the flow lattice");
     for (double w : {p->chm_omega_bulk, p->chm_omega_high})
       if (!(w == 0.0 || (w > 0.0 && w < 2.0))) return bad("CHM rates must be in (0, 2) or 0");
   }

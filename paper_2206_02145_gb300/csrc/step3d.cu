@@ -21,7 +21,7 @@ namespace lbk {
 namespace {
 
 // ---- the 3D step kernel: one tile per CTA -------------------------------------
-template <typename T, typename R, bool FLOW, int TX, int TY, int TZ>
+template <typename T, typename R, bool FLOW, bool CHM, int TX, int TY, int TZ>
 __global__ void __launch_bounds__(TX* TY* TZ)
     step3d_kernel(const Model m, const T* __restrict__ src, T* __restrict__ dst,
                   const R* __restrict__ ring_prev, R* __restrict__ ring_cur,
@@ -88,13 +88,13 @@ __global__ void __launch_bounds__(TX* TY* TZ)
   const bool interior = x0 >= 1 && x0 + TX <= nx - 1 && y0 >= 1 && y0 + TY <= ny - 1 &&
                         z0 >= 1 && z0 + TZ <= nz - 1;
   if (interior)
-    collide_push_3d<T, R, FLOW, true>(m, x, y, z, tx + 1, ty + 1, f, g, h,
-                                      sh_phi[tz + 1][ty + 1][tx + 1], dphi_prev, pv, hs, dst,
-                                      ring_cur, err);
+    collide_push_3d<T, R, FLOW, true, CHM>(m, x, y, z, tx + 1, ty + 1, f, g, h,
+                                           sh_phi[tz + 1][ty + 1][tx + 1], dphi_prev, pv, hs,
+                                           dst, ring_cur, err);
   else
-    collide_push_3d<T, R, FLOW, false>(m, x, y, z, tx + 1, ty + 1, f, g, h,
-                                       sh_phi[tz + 1][ty + 1][tx + 1], dphi_prev, pv, hs, dst,
-                                       ring_cur, err);
+    collide_push_3d<T, R, FLOW, false, CHM>(m, x, y, z, tx + 1, ty + 1, f, g, h,
+                                            sh_phi[tz + 1][ty + 1][tx + 1], dphi_prev, pv, hs,
+                                            dst, ring_cur, err);
 }
 
 // ---- the z-marching kernel (FP32 arithmetic) --------------------------------------
@@ -106,7 +106,7 @@ __global__ void __launch_bounds__(TX* TY* TZ)
 // the loads of the node's own f, g and phi(t-1), then loads plane z + 1 into
 // the ring, synchronises once and collides / pushes plane z.  With four
 // slots, the slot filled at z + 1 is never one another thread may still read.
-template <typename T, bool FLOW, int TX, int TY, int MINB>
+template <typename T, bool FLOW, bool CHM, int TX, int TY, int MINB>
 __global__ void __launch_bounds__(TX* TY, MINB)
     step3d_march_kernel(const Model m, const T* __restrict__ src, T* __restrict__ dst,
                         const float* __restrict__ ring_prev, float* __restrict__ ring_cur,
@@ -185,11 +185,13 @@ __global__ void __launch_bounds__(TX* TY, MINB)
       PhiRing3<R, SX> pv{{sh_phi[sm], sh_phi[s0], sh_phi[sp]}};
       HRing3<R, SX, PL> hv{{sh_h[sm], sh_h[s0], sh_h[sp]}};
       if (xy_inner && z >= 1 && z <= nz - 2)
-        collide_push_3d<T, R, FLOW, true>(m, x, y, z, tx + 1, ty + 1, f, g, h, sh_phi[s0][o],
-                                          dphi_prev, pv, hv, dst, ring_cur, err);
+        collide_push_3d<T, R, FLOW, true, CHM>(m, x, y, z, tx + 1, ty + 1, f, g, h,
+                                               sh_phi[s0][o], dphi_prev, pv, hv, dst, ring_cur,
+                                               err);
       else
-        collide_push_3d<T, R, FLOW, false>(m, x, y, z, tx + 1, ty + 1, f, g, h, sh_phi[s0][o],
-                                           dphi_prev, pv, hv, dst, ring_cur, err);
+        collide_push_3d<T, R, FLOW, false, CHM>(m, x, y, z, tx + 1, ty + 1, f, g, h,
+                                                sh_phi[s0][o], dphi_prev, pv, hv, dst, ring_cur,
+                                                err);
     }
   }
 }
@@ -215,9 +217,11 @@ cudaError_t launch3_march_t(const Model& m, const void* src, void* dst, const vo
   constexpr int TX = 32, TY = LBPF_3D_TY;
   const int zc = LBPF_3D_ZC;
   dim3 grid((m.nx + TX - 1) / TX, (m.ny + TY - 1) / TY, (m.nz + zc - 1) / zc);
-  step3d_march_kernel<T, FLOW, TX, TY, LBPF_3D_MINB><<<grid, TX * TY, 0, s>>>(
-      m, static_cast<const T*>(src), static_cast<T*>(dst), static_cast<const float*>(ring_prev),
-      static_cast<float*>(ring_cur), err, zc);
+  auto kern = FLOW && m.chm ? step3d_march_kernel<T, FLOW, FLOW, TX, TY, LBPF_3D_MINB>
+                            : step3d_march_kernel<T, FLOW, false, TX, TY, LBPF_3D_MINB>;
+  kern<<<grid, TX * TY, 0, s>>>(m, static_cast<const T*>(src), static_cast<T*>(dst),
+                                static_cast<const float*>(ring_prev),
+                                static_cast<float*>(ring_cur), err, zc);
   return cudaGetLastError();
 }
 
@@ -228,9 +232,10 @@ cudaError_t launch3_plain_t(const Model& m, const void* src, void* dst, const vo
   constexpr int TX = sizeof(R) == 8 ? 16 : 32, TY = 4, TZ = 2;
   dim3 block(TX, TY, TZ);
   dim3 grid((m.nx + TX - 1) / TX, (m.ny + TY - 1) / TY, (m.nz + TZ - 1) / TZ);
-  step3d_kernel<T, R, FLOW, TX, TY, TZ><<<grid, block, 0, s>>>(
-      m, static_cast<const T*>(src), static_cast<T*>(dst), static_cast<const R*>(ring_prev),
-      static_cast<R*>(ring_cur), err);
+  auto kern = FLOW && m.chm ? step3d_kernel<T, R, FLOW, FLOW, TX, TY, TZ>
+                            : step3d_kernel<T, R, FLOW, false, TX, TY, TZ>;
+  kern<<<grid, block, 0, s>>>(m, static_cast<const T*>(src), static_cast<T*>(dst),
+                              static_cast<const R*>(ring_prev), static_cast<R*>(ring_cur), err);
   return cudaGetLastError();
 }
 

@@ -40,10 +40,160 @@ struct HRing3 {
   }
 };
 
+// ---- central Hermite MRT of the D3Q19 flow lattice (Sec. 2.2 after Eq. 9) ----
+// The nineteen moments are the products H_i(X) H_j(Y) H_k(Z) (H_0 = 1,
+// H_1 = X, H_2 = X^2 - 1/3; i, j, k <= 2, at most two non-zero) about u*.
+// Every one involves at most two axes, and the weights' moments over an axis
+// pair are those of D2Q9 (1, 1/3, 1/3, 1/9), so each pair (p, q) takes the
+// 2D transform of its nine raw moments; the pairs share the moments of one
+// axis.  Raw moments of the stored deviations -> central Hermite moments ->
+// relaxation by order -> raw moments -> populations through the inverse of
+// the D3Q19 raw-moment matrix (rest, faces and each pair's four edges in
+// closed form).
+
+// central Hermite moments XY, X^2 Y, X Y^2, X^2 Y^2 of the pair (p, q) from
+// the raw deviation moments e_ij of p^i q^j
+template <typename R>
+struct ChmPair {
+  R hpq, hppq, hpqq, hppqq;
+};
+
+template <typename R>
+__device__ __forceinline__ ChmPair<R> chm_pair_central(R e00, R e10, R e01, R e20, R e02, R e11,
+                                                      R e21, R e12, R e22, R vp, R vq, R rho) {
+  const R t3 = R(1.0 / 3.0), t9 = R(1.0 / 9.0);
+  const R vpp = vp * vp, vqq = vq * vq, vpq = vp * vq;
+  ChmPair<R> h;
+  h.hpq = e11 - vp * e01 - vq * e10 + vpq * rho;
+  h.hppq = e21 - R(2) * vp * e11 + vpp * e01 - vq * e20 + R(2) * vpq * e10 - vpp * vq * rho -
+           t3 * e01 + t3 * vq * e00;
+  h.hpqq = e12 - R(2) * vq * e11 + vqq * e10 - vp * e02 + R(2) * vpq * e01 - vp * vqq * rho -
+           t3 * e10 + t3 * vp * e00;
+  h.hppqq = e22 - R(2) * vp * e12 - R(2) * vq * e21 + vpp * e02 + vqq * e20 + R(4) * vpq * e11 -
+            R(2) * vpq * vq * e10 - R(2) * vpq * vp * e01 + vpp * vqq * rho -
+            t3 * (e20 + e02) + R(2) * t3 * (vp * e10 + vq * e01) - t3 * (vpp + vqq) * e00 +
+            t9 * e00;
+  return h;
+}
+
+// raw deviation moments f11, f21 (p^2 q), f12 (p q^2), f22 of the pair after
+// collision, from its relaxed central Hermite moments (s: first and
+// diagonal second order of p and q, m: the pair's own)
+template <typename R>
+__device__ __forceinline__ void chm_pair_raw(const ChmPair<R>& m, R hp, R hq, R hpp, R hqq, R vp,
+                                             R vq, R rho, R e00, R& f11, R& f21, R& f12,
+                                             R& f22) {
+  const R t3 = R(1.0 / 3.0), t9 = R(1.0 / 9.0);
+  const R vpp = vp * vp, vqq = vq * vq, vpq = vp * vq;
+  const R kpp = hpp + t3 * rho, kqq = hqq + t3 * rho;
+  const R k21 = m.hppq + t3 * hq, k12 = m.hpqq + t3 * hp;
+  f11 = m.hpq + vp * hq + vq * hp + vpq * rho;
+  f21 = k21 + R(2) * vp * m.hpq + vpp * hq + vq * kpp + R(2) * vpq * hp + vpp * vq * rho;
+  f12 = k12 + R(2) * vq * m.hpq + vqq * hp + vp * kqq + R(2) * vpq * hq + vp * vqq * rho;
+  f22 = m.hppqq + t3 * (hpp + hqq) + t9 * e00 + R(2) * vp * k12 + R(2) * vq * k21 + vpp * kqq +
+        vqq * kpp + R(4) * vpq * m.hpq + R(2) * vpq * vq * hp + R(2) * vpq * vp * hq +
+        vpp * vqq * rho;
+}
+
+// d: the node's f deviations (D3Q19 order: rest, +x, -x, +y, -y, +z, -z, then
+// the pairs xy, xz, yz with four edges each, (+,+), (-,-), (+,-), (-,+));
+// mo: their first moments; v: u*; F: the force.  out: post-collision
+// deviations.
+template <typename R>
+__device__ __forceinline__ void chm_post_3d(const R (&d)[19], R drho, R rho, const R (&mo)[3],
+                                            const R (&v)[3], const R (&F)[3], R wf, R wb, R wh,
+                                            R (&out)[19]) {
+  const R t3 = R(1.0 / 3.0);
+  const R e00 = drho;
+  // raw moments of each pair: p^2 q^2, p q, p^2 q, p q^2
+  R e22[3], e11[3], e21[3], e12[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const int b = 7 + 4 * k;
+    e22[k] = (d[b] + d[b + 1]) + (d[b + 2] + d[b + 3]);
+    e11[k] = (d[b] + d[b + 1]) - (d[b + 2] + d[b + 3]);
+    e21[k] = (d[b] - d[b + 1]) - (d[b + 2] - d[b + 3]);
+    e12[k] = (d[b] - d[b + 1]) + (d[b + 2] - d[b + 3]);
+  }
+  // pairs: 0 = (x, y), 1 = (x, z), 2 = (y, z)
+  const R e2[3] = {(d[1] + d[2]) + (e22[0] + e22[1]), (d[3] + d[4]) + (e22[0] + e22[2]),
+                   (d[5] + d[6]) + (e22[1] + e22[2])};
+  // central Hermite moments, first and diagonal second order
+  R h1[3], h2[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    h1[a] = mo[a] - v[a] * rho;
+    h2[a] = e2[a] - t3 * e00 - R(2) * v[a] * mo[a] + v[a] * v[a] * rho;
+  }
+  constexpr int PP[3] = {0, 0, 1}, QQ[3] = {1, 2, 2};
+  ChmPair<R> hp[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const int p = PP[k], q = QQ[k];
+    hp[k] = chm_pair_central<R>(e00, mo[p], mo[q], e2[p], e2[q], e11[k], e21[k], e12[k], e22[k],
+                                v[p], v[q], rho);
+  }
+  // relaxation towards rho and zeros; the force in the first order; the
+  // trace of the second order at wb, its deviatoric part and the mixed
+  // moments at wf, third and fourth order at wh
+  const R kf = R(1) - wf, gf = R(1) - R(0.5) * wf, kh = R(1) - wh;
+  const R mean = (h2[0] + h2[1] + h2[2]) * t3;
+  const R kb = (R(1) - wb) * mean;
+  R s1[3], s2[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    s1[a] = kf * h1[a] + gf * F[a];
+    s2[a] = kb + kf * (h2[a] - mean);
+  }
+  R f11[3], f21[3], f12[3], f22[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const int p = PP[k], q = QQ[k];
+    ChmPair<R> m;
+    m.hpq = kf * hp[k].hpq;
+    m.hppq = kh * hp[k].hppq;
+    m.hpqq = kh * hp[k].hpqq;
+    m.hppqq = kh * hp[k].hppqq;
+    chm_pair_raw<R>(m, s1[p], s1[q], s2[p], s2[q], v[p], v[q], rho, e00, f11[k], f21[k], f12[k],
+                    f22[k]);
+  }
+  // raw moments of one axis after collision
+  R f1[3], f2[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    f1[a] = s1[a] + v[a] * rho;
+    f2[a] = s2[a] + t3 * e00 + R(2) * v[a] * s1[a] + v[a] * v[a] * rho;
+  }
+  // populations: rest, faces, edges
+  out[0] = e00 - (f2[0] + f2[1] + f2[2]) + (f22[0] + f22[1] + f22[2]);
+  {
+    // faces of x: x y^2 and x z^2 are the p q^2 of pairs xy and xz; of y:
+    // x^2 y (pair xy, p^2 q) and y z^2 (pair yz, p q^2); of z: x^2 z and y^2 z
+    const R sx = f2[0] - f22[0] - f22[1], ax = f1[0] - f12[0] - f12[1];
+    const R sy = f2[1] - f22[0] - f22[2], ay = f1[1] - f21[0] - f12[2];
+    const R sz = f2[2] - f22[1] - f22[2], az = f1[2] - f21[1] - f21[2];
+    out[1] = R(0.5) * (sx + ax);
+    out[2] = R(0.5) * (sx - ax);
+    out[3] = R(0.5) * (sy + ay);
+    out[4] = R(0.5) * (sy - ay);
+    out[5] = R(0.5) * (sz + az);
+    out[6] = R(0.5) * (sz - az);
+  }
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const int b = 7 + 4 * k;
+    out[b] = R(0.25) * (f22[k] + f12[k] + f21[k] + f11[k]);
+    out[b + 1] = R(0.25) * (f22[k] - f12[k] - f21[k] + f11[k]);
+    out[b + 2] = R(0.25) * (f22[k] + f12[k] - f21[k] - f11[k]);
+    out[b + 3] = R(0.25) * (f22[k] - f12[k] + f21[k] - f11[k]);
+  }
+}
+
 // pv: phi + 1 around the node, hv: the h deviations around it (views above).
 // INTERIOR: every node of the tile is at least one node away from every
-// domain face, so every destination is an ordinary node.
-template <typename T, typename R, bool FLOW, bool INTERIOR, typename PV, typename HV>
+// domain face, so every destination is an ordinary node.  CHM: the flow
+// collides by the central Hermite MRT.
+template <typename T, typename R, bool FLOW, bool INTERIOR, bool CHM, typename PV, typename HV>
 __device__ __forceinline__ void collide_push_3d(const Model& m, int x, int y, int z, int lx,
                                                 int ly, const R (&f)[19], const R (&g)[7],
                                                 const R (&h)[7], R dphi, R dphi_prev,
@@ -88,6 +238,8 @@ __device__ __forceinline__ void collide_push_3d(const Model& m, int x, int y, in
     }
   }
   const R us[3] = {mask * u[0], mask * u[1], mask * u[2]};  // Eq. 7
+  R fchm[19];
+  if (FLOW && CHM) chm_post_3d<R>(f, drho, rho, mo, us, F, c.omega_f, c.chm_wb, c.chm_wh, fchm);
   const R omega_U = rcp_r(R(0.5) + c.tauU_slope * mask);  // Eq. 18
   const R dphidt = dphi - dphi_prev;
   ring_cur[idx] = dphi;
@@ -138,7 +290,7 @@ __device__ __forceinline__ void collide_push_3d(const Model& m, int x, int y, in
       const R cF = R(cx) * F[0] + R(cy) * F[1] + R(cz) * F[2];
       const R feq = fma_r(cu, fma_r(E2, cu, E1), E0);
       const R guo_t = mul_r(guo, fma_r(cF, fma_r(R(9), cu, R(3)), G0));
-      fp = fma_r(keep_f, f[a], mul_r(wf, add_r(feq, guo_t)));
+      fp = CHM ? fchm[a] : fma_r(keep_f, f[a], mul_r(wf, add_r(feq, guo_t)));
     }
     if (sc) {
       const R ws = d3q7_w<R>(a);

@@ -74,8 +74,8 @@ def test_struct_layouts_match_header(lib, tmp_path):
     dict(eps_aniso=1.0), dict(eps_aniso=-0.1), dict(fold=13), dict(dim=3, nz=8, fold=4),
     dict(nx=3), dict(dim=4), dict(bc=(0, 1, 0)), dict(u_inlet=0.2), dict(storage=7),
     dict(lambda_=float("nan")),
-    # the central Hermite MRT: 2D with flow, rates in (0, 2) or 0 for the default
-    dict(collision=1), dict(collision=1, flow=1, dim=3, nz=8, fold=0), dict(collision=2, flow=1),
+    # the central Hermite MRT: with flow, rates in (0, 2) or 0 for the default
+    dict(collision=1), dict(collision=1, flow=0, dim=3, nz=8, fold=0), dict(collision=2, flow=1),
     dict(collision=1, flow=1, chm_omega_bulk=2.0), dict(collision=1, flow=1, chm_omega_high=-1.0),
 ])
 def test_invalid_parameters_are_rejected_without_a_gpu(lib, bad):
