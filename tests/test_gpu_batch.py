@@ -109,6 +109,31 @@ def test_batch_with_obstacles_equals_single_instances_bitwise(L, storage_name):
         assert np.array_equal(b.instance(i).state(), sim.state()), i
 
 
+def test_full_size_sweep_sampled_instances_match_oracle(L):
+    # the benchmark's sweep (64 instances of 256^2..768^2, FP16 storage) over
+    # the tuner's 24 steps and one graph replay; its smallest and largest
+    # instance against the oracle within the 2D FP16 storage bounds
+    import bench
+    import _pairs as P
+    params, seeds = bench.sweep_members(64, 4)
+    params = [dict(p, storage=L.FP16_SHIFTED) for p in params]
+    b = L.Batch(params, seeds)
+    b.step(88)
+    sizes = [p["nx"] for p in params]
+    for k in (int(np.argmin(sizes)), int(np.argmax(sizes))):
+        p = params[k]
+        o = P.oracle_sim(P.params(nx=p["nx"], ny=p["ny"], flow=1, fold=p["fold"],
+                                  eps=p["eps_aniso"], bc=(1, 0, 0), u_in=p["u_inlet"],
+                                  U_in=p["u0_inlet"]))
+        o.init_seed(*seeds[k])
+        o.step(88, P.THREADS)
+        errs = P.max_errors(b.instance(k), o)
+        for f, bound in dict(phi=8e-3, U=9e-3, rho=4e-5, ux=4e-5, uy=3e-5).items():
+            assert errs[f] < bound, (k, f, errs)
+    assert b.tuning()["tuned"]
+    b.close()
+
+
 def test_batch_rejects_mixed_instances(L):
     params, seeds = sweep(L.FP32, n=2)
     params[1]["storage"] = L.FP16_SHIFTED

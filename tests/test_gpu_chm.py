@@ -275,3 +275,17 @@ def test_3d_stable_where_bgk_fails(P, L):
             return float("inf")
     assert run(L.COLL_BGK) > 1.0
     assert run(L.COLL_CHM) < 0.2
+
+
+def test_3d_full_size_sample(P, L):
+    # the 256^3 problem of the benchmark with CHM, two steps, FP32
+    p = P.params(dim=3, nx=256, ny=256, nz=256, flow=1, fold=0, eps=0.04, bc=(1, 0, 0),
+                 u_in=0.005, U_in=0.3)
+    seed = (128.0, 128.0, 128.0, 12.0, 0.3, 0.01, 1)
+    a, b = chm_pair(P, L, p, "fp32")
+    a.init_seed(*seed)
+    b.init_seed(*seed)
+    a.step(2)
+    b.step(2, P.THREADS)
+    errs = P.max_errors(a, b, F3)
+    assert max(errs.values()) < TOL32, errs

@@ -173,6 +173,31 @@ def test_full_size_1024_coupled(P):
     check(P, a, b, TOL32)
 
 
+# --- the 3D workload at full size: 256^3 coupled with inflow, FP32 and 16-bit ------
+def test_full_size_256_cubed_3d(P):
+    # the 256^3 problem in the benchmark's launch configuration (one replay of
+    # the step graph), FP32 to 1e-5; the 16-bit storages within the bounds of
+    # their 3D storage error (the 48^3 case over 200 steps)
+    p = P.params(dim=3, nx=256, ny=256, nz=256, flow=1, fold=0, eps=0.04, bc=(1, 0, 0),
+                 u_in=0.005, U_in=0.3)
+    seed = (128.0, 128.0, 128.0, 12.0, 0.3, 0.01, 1)
+    b = P.oracle_sim(p)
+    b.init_seed(*seed)
+    b.step(64, P.THREADS)
+    fields = ("phi", "U", "rho", "ux", "uy", "uz")
+    bounds = {"fp32": dict.fromkeys(fields, TOL32),
+              "fp16": dict(phi=2e-3, U=3e-3, rho=1.3e-5, ux=1e-5, uy=6e-6, uz=6e-6),
+              "bf16": dict(phi=0.04, U=0.025, rho=1e-4, ux=8e-5, uy=5e-5, uz=5e-5)}
+    for storage, bound in bounds.items():
+        a = P.lib_sim(p, storage)
+        a.init_seed(*seed)
+        a.step(64)
+        errs = P.max_errors(a, b, fields)
+        for k in fields:
+            assert errs[k] < bound[k], (storage, k, errs)
+        a.close()
+
+
 # --- properties of the library path -------------------------------------------------
 def test_graph_replay_equals_single_launches(P):
     p = coupled_inlet(P, 128)
