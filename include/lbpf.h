@@ -391,6 +391,33 @@ int lbpf_unet_grad(lbpf_unet_t* n, const float* x, const float* t, float* loss_h
  * of the batch goes to the device float *loss_dev if not NULL.  Asynchronous. */
 int lbpf_unet_train_step(lbpf_unet_t* n, const float* x, const float* t, float lr,
                          float* loss_dev);
+/* The training loop of the block propagator's network, on pairs held on the
+ * device: per step, a minibatch of pairs gathered (and mirrored) into the
+ * network's own buffers, then one lbpf_unet_train_step at the step's learning
+ * rate; every step is queued on the network's stream, with one
+ * synchronisation at the end.
+ *   X, T: device FP32 [n_pairs][height][width][4], the normalised fields
+ *         (phi, U, ux, uy) and their targets (lbpf_surrogate_sample /
+ *         lbpf_surrogate_target); height and width those of the network,
+ *         which maps 4 inputs to 4 outputs.  Caller-owned, read only.
+ *   idx:  host int32 [steps][batch], the pairs of each minibatch, in
+ *         [0, n_pairs);
+ *   flip: host int32 [steps] or NULL: 0 as stored, 1 mirrored in y (row
+ *         height-1-i, uy negated), 2 mirrored in x (column width-1-j, ux
+ *         negated) -- the mirror symmetries of a channel with walls in y;
+ *   lr:   host float [steps], the learning rate of each step (>= 0, finite);
+ *   loss_log: host float [ceil(steps / log_every)] or NULL: the minibatch
+ *         loss at steps log_every, 2 log_every, ... and at the last step.
+ * The caller draws the minibatches and the schedule: the same draws give the
+ * same minibatches and rates as a loop of lbpf_unet_train_step calls (the
+ * gradients are reduced with atomic additions, so two runs agree to rounding,
+ * not bit for bit).  The first call allocates two minibatch buffers
+ * owned by the network.  LBPF_EINVAL for an index, flip or rate out of range
+ * or a network that is not 4 -> 4 (nothing queued). */
+int lbpf_surrogate_train(lbpf_unet_t* net, const float* X, const float* T, int64_t n_pairs,
+                         int steps, const int32_t* idx, const int32_t* flip, const float* lr,
+                         int log_every, float* loss_log);
+
 /* Number of parameters and their copy to / from host FP32 memory in a fixed
  * order: the first encoder convolution of every level (0..L-1), the second
  * encoder convolution of every level, the upsampling convolution of every

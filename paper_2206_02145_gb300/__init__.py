@@ -117,7 +117,7 @@ EXPORTED = ("lbpf_params_default", "lbpf_create", "lbpf_init_seed", "lbpf_init_f
             "lbpf_unet_create", "lbpf_unet_forward", "lbpf_unet_grad", "lbpf_unet_train_step",
             "lbpf_unet_param_count", "lbpf_unet_params", "lbpf_unet_device_bytes",
             "lbpf_unet_last_error", "lbpf_unet_destroy", "lbpf_unet_set_tensor_path",
-            "lbpf_unet_status", "lbpf_surrogate_sample",
+            "lbpf_unet_status", "lbpf_surrogate_sample", "lbpf_surrogate_train",
             "lbpf_surrogate_target", "lbpf_surrogate_advance", "lbpf_init_polygon",
             "lbpf_measure_facets", "lbpf_growth_fit", "lbpf_facets_enqueue",
             "lbpf_facets_collect", "lbpf_set_solid")
@@ -178,6 +178,8 @@ def _load_library():
     lib.lbpf_unet_set_tensor_path.argtypes = [vp, ctypes.c_int]
     lib.lbpf_unet_status.argtypes = [vp]
     lib.lbpf_surrogate_sample.argtypes = [vp, ctypes.POINTER(lbpf_surrogate_cfg), vp]
+    lib.lbpf_surrogate_train.argtypes = [vp, vp, vp, ctypes.c_int64, ctypes.c_int, vp, vp, vp,
+                                         ctypes.c_int, vp]
     lib.lbpf_surrogate_target.argtypes = [ctypes.POINTER(lbpf_surrogate_cfg), vp, vp,
                                           ctypes.c_int64, vp, vp]
     lib.lbpf_surrogate_advance.argtypes = [vp, vp, ctypes.POINTER(lbpf_surrogate_cfg),
@@ -639,6 +641,24 @@ def surrogate_cfg(steps_per_block=50, judge_every=8, drift_tol=1e-3, iface_tol=1
 def lbpf_surrogate_sample(sim: "Sim", cfg: lbpf_surrogate_cfg, x) -> None:
     """Normalised network input of the simulation's state into device x [ny][nx][4]."""
     _check(sim.h, _lib.lbpf_surrogate_sample(sim.h, ctypes.byref(cfg), UNet._ptr(x)))
+
+
+def lbpf_surrogate_train(net: "UNet", X, T, idx, flip, lr, log_every: int = 50) -> np.ndarray:
+    """The library's training loop on device pairs X, T [n, h, w, 4]: idx
+    [steps, batch] pair indices, flip [steps] (0, 1 rows, 2 columns) or None,
+    lr [steps].  Returns the logged minibatch losses."""
+    idx = np.ascontiguousarray(idx, np.int32)
+    lr = np.ascontiguousarray(lr, np.float32)
+    steps = int(lr.shape[0])
+    flip = None if flip is None else np.ascontiguousarray(flip, np.int32)
+    nlog = -(-steps // log_every)
+    out = np.zeros(nlog, np.float32)
+    rc = _lib.lbpf_surrogate_train(net.n, UNet._ptr(X), UNet._ptr(T), int(X.shape[0]), steps,
+                                   idx.ctypes.data, None if flip is None else flip.ctypes.data,
+                                   lr.ctypes.data, int(log_every), out.ctypes.data)
+    if rc != OK:
+        raise LbpfError(rc, _lib.lbpf_unet_last_error(net.n).decode())
+    return out
 
 
 def lbpf_surrogate_target(cfg: lbpf_surrogate_cfg, x0, x1, npix: int, t, stream=None) -> None:

@@ -72,6 +72,7 @@ struct lbpf_unet {
   // output y, current planes F (phi, U, ux, uy, rho), predicted planes F1
   // (phi, U, ux, uy, phi(t-1)), FP64 sums and interface crossings
   float *px = nullptr, *py = nullptr, *pF = nullptr, *pF1 = nullptr;
+  float *tx = nullptr, *tt = nullptr;  // training minibatch (lbpf_surrogate_train)
   double *psum = nullptr, *pcross = nullptr;
   // the prediction phase of a block as a CUDA graph per buffer parity, with
   // the key it was captured for; results land in pinned host memory
@@ -457,6 +458,28 @@ __global__ void target_kernel(const float* x0, const float* x1, const lbk::Vec4 
     t[i] = (x1[i] - x0[i]) * g.v[i & 3];
 }
 
+// One minibatch of the training loop: pairs idx[0..B) of X / T ([n][H][W][4],
+// channels phi, U, ux, uy), mirrored as `flip` says (1: rows, uy negated;
+// 2: columns, ux negated), into xb / tb ([B][H][W][4]).  A copy up to the
+// sign: the values are those of the stored pairs exactly.
+__global__ void gather_pairs_kernel(const float* __restrict__ X, const float* __restrict__ T,
+                                    const int* __restrict__ idx, int flip, int H, int W,
+                                    long long n, float* __restrict__ xb, float* __restrict__ tb) {
+  const long long hw4 = (long long)H * W * 4;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long b = e / hw4, r = e % hw4;
+    int i = int(r / (W * 4)), j = int((r / 4) % W);
+    const int c = int(r & 3);
+    if (flip == 1) i = H - 1 - i;
+    if (flip == 2) j = W - 1 - j;
+    const float sg = (flip == 1 && c == 3) || (flip == 2 && c == 2) ? -1.f : 1.f;
+    const long long src = (long long)idx[b] * hw4 + ((long long)i * W + j) * 4 + c;
+    xb[e] = sg * X[src];
+    tb[e] = sg * T[src];
+  }
+}
+
 int grid_of(long long n) {
   long long b = (n + 255) / 256;
   return int(b < 1 ? 1 : (b > 152 * 16 ? 152 * 16 : b));
@@ -650,6 +673,74 @@ int lbpf_unet_train_step(lbpf_unet_t* n, const float* x, const float* t, float l
   if (loss_dev)
     UCK(n, cudaMemcpyAsync(loss_dev, n->loss, 4, cudaMemcpyDeviceToDevice, n->stream));
   return LBPF_OK;
+}
+
+int lbpf_surrogate_train(lbpf_unet_t* n, const float* X, const float* T, int64_t n_pairs,
+                         int steps, const int32_t* idx, const int32_t* flip, const float* lr,
+                         int log_every, float* loss_log) {
+  if (!n || !X || !T || n_pairs < 1 || steps < 0 || (steps > 0 && (!idx || !lr)) ||
+      log_every < 1)
+    return LBPF_EINVAL;
+  const lbpf_unet_cfg& c = n->cfg;
+  if (c.in_ch != 4 || c.out_ch != 4)
+    return ufail(n, LBPF_EINVAL, "lbpf_surrogate_train: the network must map 4 fields to 4");
+  const int B = c.batch, H = n->H[0], W = n->W[0];
+  for (long long k = 0; k < (long long)steps * B; ++k)
+    if (idx[k] < 0 || idx[k] >= n_pairs)
+      return ufail(n, LBPF_EINVAL, "lbpf_surrogate_train: pair index %d outside [0, %lld)",
+                   int(idx[k]), (long long)n_pairs);
+  for (int k = 0; flip && k < steps; ++k)
+    if (flip[k] < 0 || flip[k] > 2)
+      return ufail(n, LBPF_EINVAL, "lbpf_surrogate_train: flip %d of step %d not 0, 1 or 2",
+                   int(flip[k]), k);
+  for (int k = 0; k < steps; ++k)
+    if (!(lr[k] >= 0.f && std::isfinite(lr[k])))
+      return ufail(n, LBPF_EINVAL, "lbpf_surrogate_train: learning rate of step %d", k);
+  if (steps == 0) return LBPF_OK;
+  const int nlog = steps / log_every + (steps % log_every ? 1 : 0);
+  const long long nb = (long long)B * H * W * 4;
+  if (!n->tx) {  // minibatch buffers, kept with the network
+    UCK(n, dalloc(n, &n->tx, size_t(nb)));
+    UCK(n, dalloc(n, &n->tt, size_t(nb)));
+  }
+  int* d_idx = nullptr;
+  float* d_log = nullptr;
+  auto release = [&]() {
+    if (d_idx) cudaFree(d_idx);
+    if (d_log) cudaFree(d_log);
+  };
+  cudaError_t e = cudaMalloc(&d_idx, sizeof(int) * size_t(steps) * B);
+  if (e == cudaSuccess) e = cudaMalloc(&d_log, sizeof(float) * size_t(nlog));
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(d_idx, idx, sizeof(int) * size_t(steps) * B, cudaMemcpyHostToDevice,
+                        n->stream);
+  if (e != cudaSuccess) {
+    release();
+    return ufail(n, LBPF_ECUDA, "lbpf_surrogate_train: %s", cudaGetErrorString(e));
+  }
+  int rc = LBPF_OK, k = 0;
+  for (int st = 0; st < steps && rc == LBPF_OK; ++st) {
+    gather_pairs_kernel<<<grid_of(nb), 256, 0, n->stream>>>(X, T, d_idx + size_t(st) * B,
+                                                           flip ? flip[st] : 0, H, W, nb, n->tx,
+                                                           n->tt);
+    if ((e = cudaGetLastError()) != cudaSuccess) {
+      rc = ufail(n, LBPF_ECUDA, "gather_pairs_kernel: %s", cudaGetErrorString(e));
+      break;
+    }
+    rc = lbpf_unet_train_step(n, n->tx, n->tt, lr[st], nullptr);
+    if (rc == LBPF_OK && ((st + 1) % log_every == 0 || st == steps - 1) &&
+        (e = cudaMemcpyAsync(d_log + k++, n->loss, 4, cudaMemcpyDeviceToDevice, n->stream)) !=
+            cudaSuccess)
+      rc = ufail(n, LBPF_ECUDA, "loss log: %s", cudaGetErrorString(e));
+  }
+  if (rc == LBPF_OK && loss_log &&
+      (e = cudaMemcpyAsync(loss_log, d_log, sizeof(float) * size_t(nlog), cudaMemcpyDeviceToHost,
+                           n->stream)) != cudaSuccess)
+    rc = ufail(n, LBPF_ECUDA, "loss log: %s", cudaGetErrorString(e));
+  if ((e = cudaStreamSynchronize(n->stream)) != cudaSuccess && rc == LBPF_OK)
+    rc = ufail(n, LBPF_ECUDA, "lbpf_surrogate_train: %s", cudaGetErrorString(e));
+  release();
+  return rc == LBPF_OK ? check_err(n) : rc;
 }
 
 size_t lbpf_unet_param_count(const lbpf_unet_t* n) {

@@ -23,10 +23,11 @@ import numpy as np
 import torch
 
 from . import (Sim, UNet, current_stream, lbpf_surrogate_advance, lbpf_surrogate_sample,
-               lbpf_surrogate_target, surrogate_cfg)
+               lbpf_surrogate_target, lbpf_surrogate_train, surrogate_cfg)
 
-__all__ = ["channel_problem", "make_sim", "default_cfg", "generate_pairs", "train",
-           "inference_net", "prediction_error", "surrogate_cfg", "lbpf_surrogate_advance"]
+__all__ = ["channel_problem", "make_sim", "default_cfg", "generate_pairs", "train_schedule",
+           "train", "inference_net", "prediction_error", "surrogate_cfg",
+           "lbpf_surrogate_advance"]
 
 
 def channel_problem(rng: np.random.Generator, nx: int, ny: int, tau_f: float = 0.6,
@@ -112,35 +113,35 @@ def generate_pairs(n_traj: int, t_end: int, every: int, nx: int, ny: int, cfg, s
     return X, T
 
 
-# the channel problems' mirror symmetries: x -> -x with ux -> -ux, y -> -y
-# with uy -> -uy (channels phi, U, ux, uy of the inputs and the targets)
-_FLIP_SIGN = {2: (1.0, 1.0, -1.0, 1.0), 1: (1.0, 1.0, 1.0, -1.0)}
+def train_schedule(n_pairs: int, batch: int, steps: int, lr: float = 5e-4, seed: int = 0,
+                   augment: bool = True):
+    """The draws of the training loop: minibatch pair indices [steps, batch],
+    mirror choices [steps] (0 none, 1 in y, 2 in x: the channel problems'
+    mirror symmetries, y -> -y with uy -> -uy and x -> -x with ux -> -ux) and
+    the cosine-decayed learning rate [steps], floored at 2 % of lr."""
+    g = torch.Generator(device="cpu").manual_seed(seed)
+    idx = np.empty((steps, batch), np.int32)
+    flip = np.zeros(steps, np.int32)
+    rates = np.empty(steps, np.float32)
+    for s in range(steps):
+        idx[s] = torch.randint(0, n_pairs, (batch,), generator=g).numpy()
+        if augment:
+            flip[s] = int(torch.randint(0, 3, (1,), generator=g))
+        a = lr * 0.5 * (1.0 + math.cos(math.pi * s / max(steps, 1)))
+        rates[s] = max(a, lr * 0.02)
+    return idx, flip, rates
 
 
 def train(net: UNet, X, T, steps: int, lr: float = 5e-4, seed: int = 0, log_every: int = 50,
           augment: bool = True):
     """Adam on random minibatches of net's batch size, cosine-decayed learning
     rate; with augment, each minibatch is mirrored in x or y (or left as is)
-    at random.  Returns [(step, loss)] read every log_every steps."""
-    B = net.cfg.batch
-    g = torch.Generator(device="cpu").manual_seed(seed)
-    loss = torch.zeros(1, device=X.device)
-    signs = {d: torch.tensor(v, device=X.device, dtype=X.dtype) for d, v in _FLIP_SIGN.items()}
-    hist = []
-    for s in range(steps):
-        idx = torch.randint(0, X.shape[0], (B,), generator=g).to(X.device)
-        xb = X.index_select(0, idx)
-        tb = T.index_select(0, idx)
-        if augment:
-            d = int(torch.randint(0, 3, (1,), generator=g))
-            if d in signs:  # dims of [B, H, W, C]: 2 mirrors x, 1 mirrors y
-                xb = (xb.flip(d) * signs[d]).contiguous()
-                tb = (tb.flip(d) * signs[d]).contiguous()
-        a = lr * 0.5 * (1.0 + math.cos(math.pi * s / max(steps, 1)))
-        net.train_step(xb, tb, max(a, lr * 0.02), loss)
-        if (s + 1) % log_every == 0 or s == steps - 1:
-            hist.append((s + 1, float(loss.item())))
-    return hist
+    at random.  The loop runs in the library (lbpf_surrogate_train).  Returns
+    [(step, loss)] at every log_every-th step and the last."""
+    idx, flip, rates = train_schedule(int(X.shape[0]), net.cfg.batch, steps, lr, seed, augment)
+    losses = lbpf_surrogate_train(net, X, T, idx, flip, rates, log_every)
+    at = [s + 1 for s in range(steps) if (s + 1) % log_every == 0 or s == steps - 1]
+    return [(a, float(v)) for a, v in zip(at, losses)]
 
 
 def inference_net(trained: UNet, nx: int, ny: int, stream: int | None = None) -> UNet:

@@ -90,6 +90,7 @@ def test_null_handle_calls_return_einval(lib):
     assert so.lbpf_step(None, 1) == lib.EINVAL
     assert so.lbpf_diagnostics(None, None) == lib.EINVAL
     assert so.lbpf_state_bytes(None) == 0
+    assert so.lbpf_surrogate_train(None, None, None, 1, 1, None, None, None, 1, None) == lib.EINVAL
     so.lbpf_destroy(None)
 
 

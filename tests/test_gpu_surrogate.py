@@ -140,6 +140,79 @@ def test_adam_training_reduces_the_loss(lib):
     net.close()
 
 
+def test_library_training_loop_follows_the_explicit_loop(lib):
+    # lbpf_surrogate_train against the same minibatches gathered, mirrored and
+    # stepped one call at a time.  The gradients and the loss are reduced with
+    # atomic additions, so two runs agree to rounding, not bit for bit.  At
+    # learning rate 0 every step's loss is that of the fixed network on its
+    # minibatch: equal losses step by step pin the gather and the mirrors, and
+    # the weights stay as they were; with the schedule, the weights agree far
+    # inside the size of the update
+    from paper_2206_02145_gb300 import surrogate as S
+    kw = dict(in_ch=4, out_ch=4, levels=2, batch=2, height=16, width=128, seed=3,
+              stream=lib.current_stream())
+    g = torch.Generator(device="cpu").manual_seed(8)
+    X = torch.randn(7, 16, 128, 4, generator=g).cuda()
+    T = (0.3 * torch.roll(X, 1, dims=2) - 0.2 * X).contiguous()
+    steps = 23
+    idx, flip, rates = S.train_schedule(7, 2, steps, lr=1e-3, seed=4)
+    assert set(flip.tolist()) == {0, 1, 2}
+    sign = {1: torch.tensor([1.0, 1.0, 1.0, -1.0], device="cuda"),
+            2: torch.tensor([1.0, 1.0, -1.0, 1.0], device="cuda")}
+
+    def explicit(net, lrs, every):
+        loss = torch.zeros(1, device="cuda")
+        out = []
+        for s in range(steps):
+            k = torch.from_numpy(idx[s].astype(np.int64)).cuda()
+            xb, tb = X.index_select(0, k), T.index_select(0, k)
+            if flip[s]:
+                d = int(flip[s])  # 1 mirrors rows (dim 1), 2 columns (dim 2)
+                xb = (xb.flip(d) * sign[d]).contiguous()
+                tb = (tb.flip(d) * sign[d]).contiguous()
+            net.train_step(xb, tb, float(lrs[s]), loss)
+            if (s + 1) % every == 0 or s == steps - 1:
+                out.append(float(loss.item()))
+        return np.array(out)
+
+    zero = np.zeros(steps, np.float32)
+    a, b = lib.UNet(**kw), lib.UNet(**kw)
+    w0 = a.weights()
+    got = lib.lbpf_surrogate_train(a, X, T, idx, flip, zero, 1)
+    want = explicit(b, zero, 1)
+    assert got.shape == (steps,) and np.all(got > 0)
+    np.testing.assert_allclose(got, want, rtol=1e-5)
+    assert np.array_equal(a.weights(), w0)
+    # the mirrors matter: the same steps unmirrored give other losses (by
+    # 6e-4 to 1e-2 relative for a network of this size at He scale)
+    plain = lib.lbpf_surrogate_train(a, X, T, idx, np.zeros(steps, np.int32), zero, 1)
+    assert np.median(np.abs(plain / got - 1)[flip != 0]) > 1e-3
+    assert np.array_equal(plain[flip == 0], got[flip == 0]) or \
+        np.allclose(plain[flip == 0], got[flip == 0], rtol=1e-5)
+    a.close()
+    b.close()
+
+    a, b = lib.UNet(**kw), lib.UNet(**kw)
+    hist = S.train(a, X, T, steps, lr=1e-3, seed=4, log_every=5)
+    want = explicit(b, rates, 5)
+    wa, wb = a.weights(), b.weights()
+    assert [h[0] for h in hist] == [5, 10, 15, 20, 23]
+    # (norms: Adam scales a weight's step by its gradient's sign, so where a
+    # gradient nearly cancels the rounding of the sums moves single weights)
+    assert np.linalg.norm(wa - wb) < 0.05 * np.linalg.norm(wb - w0)
+    np.testing.assert_allclose([h[1] for h in hist], want, rtol=2e-2)
+    # rejections: a pair index out of range, a flip code, a rate; nothing queued
+    bad_idx = idx.copy()
+    bad_idx[3, 1] = 7
+    for args in ((bad_idx, flip, rates), (idx, np.full(steps, 3), rates),
+                 (idx, flip, np.full(steps, np.nan, np.float32))):
+        with pytest.raises(lib.LbpfError) as e:
+            lib.lbpf_surrogate_train(a, X, T, *args)
+        assert e.value.code == lib.EINVAL
+    a.close()
+    b.close()
+
+
 def test_rejects_unsupported_shapes(lib):
     with pytest.raises(lib.LbpfError):
         lib.UNet(levels=2, height=16, width=96)  # width / 2 not a multiple of 64
