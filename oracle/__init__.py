@@ -192,7 +192,8 @@ class Oracle:
                                    u0, noise_amp, seed)
 
     def set_solid(self, mask):
-        """Solid nodes (2D): mask [ny, nx], nonzero = solid; None removes it."""
+        """Solid nodes: mask of the grid's shape ([ny, nx] or [nz, ny, nx]),
+        nonzero = solid; None removes it."""
         if mask is None:
             rc = self._lib.orc_set_solid(self._h, None)
         else:
@@ -200,7 +201,7 @@ class Oracle:
             assert m.size == self.p.nodes
             rc = self._lib.orc_set_solid(self._h, m.ctypes.data)
         if rc != 0:
-            raise ValueError("solid mask rejected (3D, or a solid inlet/outlet column)")
+            raise ValueError("solid mask rejected (a solid inlet or outlet column)")
 
     def init_fields(self, phi, U, rho=None, ux=None, uy=None, uz=None):
         arrs = []

@@ -118,7 +118,7 @@ struct orc_sim {
   /* per-node quantities of the current time level */
   double *phi, *U, *rho, *u[3], *us[3], *F[3], *phihat, *K, *tauU, *dphidt;
   double *grad[3], *as, *a2, *tauphi, *N[3], *Q;
-  unsigned char* solid; /* 2D solid mask (1 = solid node), NULL = none */
+  unsigned char* solid; /* solid mask (1 = solid node), NULL = none */
   double* fpost;        /* central Hermite MRT: post-collision f of every node [q][n] */
 };
 
@@ -206,10 +206,11 @@ int orc_set_solid(orc_sim* s, const unsigned char* mask) {
     s->solid = NULL;
     return 0;
   }
-  if (s->p.dim != 2) return -1;
-  if (s->p.bc[0] == ORC_INLET_OUTLET) /* the inlet and outlet columns stay fluid */
-    for (int y = 0; y < s->p.ny; ++y)
-      if (mask[y * s->p.nx] || mask[y * s->p.nx + s->p.nx - 1]) return -1;
+  if (s->p.bc[0] == ORC_INLET_OUTLET) { /* the inlet and outlet columns stay fluid */
+    const int nz = s->p.dim == 3 ? s->p.nz : 1;
+    for (int r = 0; r < s->p.ny * nz; ++r)
+      if (mask[(size_t)r * s->p.nx] || mask[(size_t)r * s->p.nx + s->p.nx - 1]) return -1;
+  }
   if (!s->solid) s->solid = (unsigned char*)malloc((size_t)s->n);
   for (int i = 0; i < s->n; ++i) s->solid[i] = mask[i] ? 1 : 0;
   return 0;
@@ -273,18 +274,22 @@ static int grad_neighbor(const orc_sim* s, const int x[3], const int c[3]) {
 }
 
 /* Gradient neighbour with solid nodes (walls and obstacles of Sec. 3.1.2):
- * a solid node in the stencil is replaced by the first fluid node among
- * x + (c_x, 0), x + (0, c_y) and x itself (each mapped like any stencil
- * neighbour) -- for a straight wall this is the nearest-node copy of the
- * domain walls, a zero normal derivative. */
+ * a solid node in the stencil is replaced by the first fluid node among the
+ * single-axis steps of c -- x + c_x e_x, x + c_y e_y, x + c_z e_z, those with
+ * a non-zero component, in that order -- and x itself (each mapped like any
+ * stencil neighbour).  For a straight wall this is the nearest-node copy of
+ * the domain walls, a zero normal derivative. */
 static int grad_neighbor_masked(const orc_sim* s, const int x[3], const int c[3]) {
   int j = grad_neighbor(s, x, c);
   if (!s->solid || !s->solid[j]) return j;
-  const int cx[3] = {c[0], 0, 0}, cy[3] = {0, c[1], 0}, c0[3] = {0, 0, 0};
-  j = grad_neighbor(s, x, cx);
-  if (!s->solid[j]) return j;
-  j = grad_neighbor(s, x, cy);
-  if (!s->solid[j]) return j;
+  for (int d = 0; d < 3; ++d) {
+    if (c[d] == 0) continue;
+    int cd[3] = {0, 0, 0};
+    cd[d] = c[d];
+    j = grad_neighbor(s, x, cd);
+    if (!s->solid[j]) return j;
+  }
+  const int c0[3] = {0, 0, 0};
   return grad_neighbor(s, x, c0);
 }
 

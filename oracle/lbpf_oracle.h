@@ -77,12 +77,13 @@ void orc_init_seed(orc_sim* s, double cx, double cy, double cz, double radius,
 void orc_init_polygon(orc_sim* s, double cx, double cy, int k, const double* nx,
                       const double* ny, const double* d, double u0, double noise_amp,
                       uint64_t seed);
-/* Solid nodes (2D): mask[nx*ny], nonzero = solid; NULL removes the mask.
- * Fluid nodes bounce back (half-way) what they send into a solid node, for
- * f, g and h; solid nodes keep their state; in the phi gradient a solid node
- * counts as the first fluid node among x + (c_x, 0), x + (0, c_y), x.  With
- * an inlet/outlet along x the first and last columns must be fluid.
- * Returns 0, or -1 (3D, or a solid inlet/outlet column). */
+/* Solid nodes (2D and 3D): mask[nodes] (x fastest), nonzero = solid; NULL
+ * removes the mask.  Fluid nodes bounce back (half-way) what they send into a
+ * solid node, for f, g and h; solid nodes keep their state; in the phi
+ * gradient a solid node counts as the first fluid node among the single-axis
+ * steps x + c_d e_d of its non-zero components (in the order x, y, z) and x
+ * itself.  With an inlet/outlet along x the first and last columns must be
+ * fluid.  Returns 0, or -1 (a solid inlet/outlet column). */
 int orc_set_solid(orc_sim* s, const unsigned char* mask);
 void orc_init_fields(orc_sim* s, const double* phi, const double* U, const double* rho,
                      const double* ux, const double* uy, const double* uz);
