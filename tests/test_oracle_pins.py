@@ -207,6 +207,28 @@ def test_uniform_drag_recurrence(oracle_mod, collision):
         assert abs(f["phi"][1, 1]) < 1e-15 and abs(f["rho"][1, 1] - 1) < 1e-14
 
 
+# The same recurrence on the D3Q19 lattice with a three-component velocity.
+@pytest.mark.parametrize("collision", [0, 1])
+def test_uniform_drag_recurrence_3d(oracle_mod, collision):
+    p = Params(dim=3, nx=4, ny=4, nz=4, fold=0, flow=1, eps=0.0, lambda_=0.0, tau_f=0.7,
+               w0=2.0, collision=collision)
+    o = O.Oracle(p)
+    n = p.nodes
+    u0 = np.array([0.03, -0.02, 0.015])
+    o.init_fields(np.zeros(n), np.zeros(n), np.ones(n), *(np.full(n, v) for v in u0))
+    K = 2.757 * 0.7 / (4 * 4.0)
+    m = 0.5 * u0
+    for _ in range(40):
+        u = m / (1.0 + K / 2)
+        F = -K * u
+        m = m - (m - 0.5 * u) / 0.7 + (1 - 1 / 1.4) * F
+        o.step(1)
+        f = o.fields()
+        np.testing.assert_allclose([f["ux"][1, 2, 3], f["uy"][1, 2, 3], f["uz"][1, 2, 3]],
+                                   m / (1 + K / 2), rtol=0, atol=1e-15)
+        assert abs(f["phi"][1, 2, 3]) < 1e-15 and abs(f["rho"][1, 2, 3] - 1) < 1e-14
+
+
 # ---------------------------------------------------------------------------
 # P5: periodic domain: sum_x [U(t) + phi(t-1)] and sum rho are invariants.
 @pytest.mark.parametrize("flow", [0, 1])
