@@ -21,8 +21,11 @@ on trajectories of this solver, judged by and falling back to the LB)
 against the plain LB on a held-out problem; --steps is then the number of
 LB-equivalent steps timed.
 
-Multi-GPU: the step is not sharded (one grid per GPU), so N GPUs run N
-independent replicas ("replicas only", weak scaling).
+Multi-GPU: a single grid is not sharded (one grid per GPU), so N GPUs run N
+independent replicas ("replicas only", weak scaling).  The batched sweeps (c4,
+c4s) are sharded: rank r of N advances every N-th instance of a sweep of
+N x batch instances, with no exchange between ranks (weak scaling); the
+whole-job rate counts the nodes of all shards.
 """
 from __future__ import annotations
 
@@ -167,7 +170,17 @@ def sweep_members(count: int, seed: int, lo: int = 256, hi: int = 768):
 ELEM = {"fp32": 4, "fp64": 8, "fp16": 2, "bf16": 2}
 
 
-def workload(name):
+def shard(members, rank: int, world: int):
+    """The members of a sweep that rank `rank` of `world` advances: every
+    world-th one from its rank on (instances are independent: no exchange)."""
+    params, seeds = members
+    return params[rank::world], seeds[rank::world]
+
+
+def workload(name, rank: int = 0, world: int = 1):
+    """The workload's settings for rank `rank` of `world`.  nodes: the nodes
+    this rank steps; nodes_all: those of all ranks (replicas of one grid, or
+    the shards of a sweep of world x batch instances)."""
     w = dict(WORKLOADS[name])
     if "base" in w:
         b = dict(WORKLOADS[w.pop("base")])
@@ -186,10 +199,12 @@ def workload(name):
         # read, its neighbours' encoding reference read, the new one written
         w["bytes_per_lup"] += 3 * 2
     w["nodes"] = w["nx"] * w["ny"] * w["nz"]
+    w["nodes_all"] = w["nodes"] * world
     if w.get("batch"):
-        params, seeds = sweep_members(w["batch"], w["sweep_seed"], *w.get("sides", (256, 768)))
-        w["members"] = (params, seeds)
-        w["nodes"] = sum(p["nx"] * p["ny"] for p in params)
+        full = sweep_members(w["batch"] * world, w["sweep_seed"], *w.get("sides", (256, 768)))
+        w["members"] = shard(full, rank, world)
+        w["nodes"] = sum(p["nx"] * p["ny"] for p in w["members"][0])
+        w["nodes_all"] = sum(p["nx"] * p["ny"] for p in full[0])
     return w
 
 
@@ -457,7 +472,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
-    w = workload(args.workload)
+    w = workload(args.workload, int(os.environ.get("RANK", "0")),
+                 int(os.environ.get("WORLD_SIZE", "1")))
     if args.impl == "reference":
         return run_reference(args, w)
     if w.get("surrogate"):
@@ -520,7 +536,7 @@ def main():
     ms = ev0.elapsed_time(ev1)
     ms_max = max_over_ranks([ms], dist)[0]
     per_step_ms = ms_max / args.steps
-    value = whole_job_rate(w["nodes"] * args.steps, world, ms_max * 1e-3) / 1e6
+    value = w["nodes_all"] * args.steps / (ms_max * 1e-3) / 1e6
     diags = [s.diagnostics() for s in sims]  # also surfaces any sticky device error
     d = diags[0]
     total_steps = args.warmup + args.steps
@@ -640,7 +656,7 @@ def main():
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
     e2e_max = max_over_ranks([e2e_s], dist)[0]
-    e2e_value = whole_job_rate(w["nodes"] * args.e2e_steps, world, e2e_max) / 1e6
+    e2e_value = w["nodes_all"] * args.e2e_steps / e2e_max / 1e6
     h2d = sum(int(x.numel()) for x in host_states)
     d2h = sum(int(x.numel()) * 4 for x in host_outs)
 
@@ -669,7 +685,9 @@ def main():
                        "storage": w["storage"], "bytes_per_lup": w["bytes_per_lup"],
                        "l2": f"inputs larger than L2: {w['bytes_per_lup'] * w['nodes'] / 1e6:.0f}"
                              " MB moved per step vs 129 MB L2",
-                       "parallelism": "replicas" if world > 1 else "single GPU"},
+                       "parallelism": "single GPU" if world == 1 else (
+                           f"sweep of {w['batch'] * world} instances sharded over {world} GPUs"
+                           if w.get("batch") else "replicas")},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "peak_source": peak_kind,
                          "frac_of_nominal_7900": achieved / 7900.0,

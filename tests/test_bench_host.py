@@ -57,6 +57,26 @@ def test_sweep_is_seeded_and_within_its_ranges(bench):
     assert w["nodes"] == sum(p["nx"] * p["ny"] for p in params)
 
 
+def test_sweep_shards_over_ranks(bench):
+    # N ranks advance disjoint shards of one sweep of N x 64 instances; the
+    # whole-job node count is the same on every rank; N = 1 is the plain sweep
+    one = bench.workload("c4")
+    assert one["nodes_all"] == one["nodes"]
+    assert one["members"] == bench.sweep_members(64, 4)
+    world = 3
+    full = bench.sweep_members(64 * world, 4)
+    shards = [bench.workload("c4", r, world) for r in range(world)]
+    seen = sorted(s for w in shards for s in w["members"][1])
+    assert seen == sorted(full[1])  # every instance exactly once
+    for w in shards:
+        assert len(w["members"][0]) == 64
+        assert w["nodes_all"] == sum(p["nx"] * p["ny"] for p in full[0])
+    assert sum(w["nodes"] for w in shards) == shards[0]["nodes_all"]
+    # a single grid runs as replicas
+    c2 = bench.workload("c2", 1, world)
+    assert c2["nodes_all"] == world * c2["nodes"]
+
+
 def test_profiled_traffic_follows_the_source_digest(bench, tmp_path, monkeypatch):
     w = dict(bench.workload("f3_3d"))
     got = bench.profiled_traffic(w)
