@@ -49,13 +49,13 @@ def test_poiseuille_in_a_masked_channel(orc):
     assert np.array_equal(o.pops("f")[:, [3, 20]], f0[:, [3, 20]])
 
 
-@pytest.mark.parametrize("flow", [0, 1])
-def test_solid_rows_reproduce_the_domain_walls(orc, flow):
+@pytest.mark.parametrize("flow,collision", [(0, 0), (1, 0), (1, 1)])
+def test_solid_rows_reproduce_the_domain_walls(orc, flow, collision):
     # A: periodic x, walls in y, ny = 30.  B: periodic x and y, ny = 32, rows
     # 0 and 31 solid.  Same fields on the fluid rows (a seed touching the
     # lower wall, so that the gradient next to the wall is exercised).
     nx, ny = 40, 30
-    kw = dict(nx=nx, flow=flow, eps=0.04, fold=4, theta0=0.3,
+    kw = dict(nx=nx, flow=flow, eps=0.04, fold=4, theta0=0.3, collision=collision,
               body=(2e-6, 0.0, 0.0) if flow else (0.0, 0.0, 0.0))
     pa = Params(ny=ny, bc=(PERIODIC, WALL, PERIODIC), **kw)
     pb = Params(ny=ny + 2, bc=(PERIODIC, PERIODIC, PERIODIC), **kw)
@@ -181,14 +181,15 @@ def test_3d_poiseuille_between_solid_planes(orc):
     assert np.array_equal(o.pops("f")[:, [3, 20]], f0[:, [3, 20]])
 
 
-@pytest.mark.parametrize("flow", [0, 1])
+@pytest.mark.parametrize("flow,collision", [(0, 0), (1, 0), (1, 1)])
 @pytest.mark.parametrize("axis", [1, 2])
-def test_3d_solid_planes_reproduce_the_domain_walls(orc, flow, axis):
+def test_3d_solid_planes_reproduce_the_domain_walls(orc, flow, collision, axis):
     # A: walls normal to `axis` (1: y, 2: z), periodic otherwise.  B: periodic,
     # two more nodes along `axis`, the first and last planes solid.  A seed
     # touching the lower wall, so that the gradient next to it is exercised.
     dims = [14, 12, 10]
-    kw = dict(dim=3, fold=0, flow=flow, eps=0.04, body=(2e-6, 0.0, 0.0) if flow else (0, 0, 0))
+    kw = dict(dim=3, fold=0, flow=flow, eps=0.04, collision=collision,
+              body=(2e-6, 0.0, 0.0) if flow else (0, 0, 0))
     bc_a = [PERIODIC, PERIODIC, PERIODIC]
     bc_a[axis] = WALL
     pa = Params(nx=dims[0], ny=dims[1], nz=dims[2], bc=tuple(bc_a), **kw)
