@@ -92,9 +92,11 @@ def baffle_mask(nx, ny, x0, y0, y1, w=2):
     return m
 
 
-def test_conservation_around_obstacles(orc):
+@pytest.mark.parametrize("collision", [0, 1])
+def test_conservation_around_obstacles(orc, collision):
     nx, ny = 56, 44
-    p = Params(nx=nx, ny=ny, flow=1, eps=0.05, fold=6, body=(3e-6, 1e-6, 0.0))
+    p = Params(nx=nx, ny=ny, flow=1, eps=0.05, fold=6, body=(3e-6, 1e-6, 0.0),
+               collision=collision)
     o = O.Oracle(p)
     mask = baffle_mask(nx, ny, 8, 10, 30) | baffle_mask(nx, ny, 40, 25, 41, 3)
     mask[2:5, 20:24] = 1
@@ -234,8 +236,10 @@ def test_3d_solid_planes_reproduce_the_domain_walls(orc, flow, collision, axis):
         assert np.abs(a.pops(k) - b.pops(k)[(slice(None),) + tuple(inner)]).max() < 1e-13, k
 
 
-def test_3d_conservation_around_obstacles(orc):
-    p = Params(dim=3, nx=24, ny=20, nz=16, fold=0, flow=1, eps=0.05, body=(3e-6, 1e-6, -1e-6))
+@pytest.mark.parametrize("collision", [0, 1])
+def test_3d_conservation_around_obstacles(orc, collision):
+    p = Params(dim=3, nx=24, ny=20, nz=16, fold=0, flow=1, eps=0.05, body=(3e-6, 1e-6, -1e-6),
+               collision=collision)
     o = O.Oracle(p)
     mask = np.zeros(p.shape, np.uint8)
     mask[2:14, 4:16, 3:5] = 1     # a baffle
