@@ -58,9 +58,9 @@ WORKLOADS = {
                     "seed R=16 at x=300, U0=0.4, 5-fold eps 0.03",
                dim=2, nx=1024, ny=1024, nz=1, flow=1, fold=5, eps=0.03, bc=(1, 0, 0),
                u_in=0.01, U_in=0.4, seed=(300.0, 512.0, 0.0, 16.0, 0.4, 0.01, 1),
-               storage="fp32", kernel="step2d_tma_kernel", src=SRC_2D,
+               storage="fp32", kernel="step2d_tma_kernel", src=SRC_2D, fp16_compare=True,
                sample=dict(nx=256, ny=256, seed=(75.0, 128.0, 0.0, 16.0, 0.4, 0.01, 1))),
-    "c2_fp16": dict(base="c2", storage="fp16"),
+    "c2_fp16": dict(base="c2", storage="fp16", fp16_compare=False),
     "f2": dict(base="c2", desc_note=True,
                desc="2D 1024x1024 coupled LB, inflow 0.01, seed R=16 at x=300, U0=0.4, 5-fold "
                     "eps 0.03, with a baffle of solid nodes 4 lu thick and 320 lu long at x=150 "
@@ -312,15 +312,19 @@ def profiled_traffic(w):
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    """nvidia-smi clocks and throttle reasons, sampled every 50 ms from before
+    the warm-up to the end of the timed region; summary() keeps the samples
+    taken inside the timed window (mark_start / mark_end)."""
     Q = ("clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,"
          "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
          "clocks_event_reasons.sw_power_cap")
 
     def __init__(self, index: int):
         self.index = index
-        self.rows = []
+        self.rows = []  # (host time, fields)
         self.proc = None
+        self.t0 = self.t1 = None
+        self.first = threading.Event()
 
     def __enter__(self):
         try:
@@ -334,11 +338,23 @@ class ClockSampler:
             self.proc = None
         return self
 
+    def wait_first(self, timeout: float = 5.0) -> bool:
+        """Block until the first sample has arrived (nvidia-smi takes a few
+        hundred ms to start), so that a short timed region is still sampled."""
+        return self.proc is not None and self.first.wait(timeout)
+
+    def mark_start(self):
+        self.t0 = time.monotonic()
+
+    def mark_end(self):
+        self.t1 = time.monotonic()
+
     def _read(self):
         for line in self.proc.stdout:
             parts = [p.strip() for p in line.split(",")]
             if len(parts) == 6:
-                self.rows.append(parts)
+                self.rows.append((time.monotonic(), parts))
+                self.first.set()
 
     def __exit__(self, *a):
         if self.proc:
@@ -348,17 +364,71 @@ class ClockSampler:
             except Exception:
                 self.proc.kill()
 
-    def summary(self):
+    def window(self):
+        """The samples of the timed window; if it was shorter than the sampling
+        period, the sample nearest to its middle."""
         if not self.rows:
+            return []
+        t0 = self.t0 if self.t0 is not None else -1e300
+        t1 = self.t1 if self.t1 is not None else 1e300
+        inside = [r for t, r in self.rows if t0 <= t <= t1]
+        if inside:
+            return inside
+        mid = 0.5 * (t0 + t1) if self.t0 is not None and self.t1 is not None else t1
+        return [min(self.rows, key=lambda tr: abs(tr[0] - mid))[1]]
+
+    def summary(self):
+        rows = self.window()
+        if not rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
-        sm = sorted(float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit())
-        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        sm = sorted(float(r[0]) for r in rows if r[0].replace(".", "").isdigit())
+        mx = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for r in self.rows for i in range(4)
+        reasons = sorted({names[i] for r in rows for i in range(4)
                           if r[2 + i].lower() == "active"})
         return {"sm_mhz": sm[len(sm) // 2] if sm else None,
                 "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
-                "samples": len(self.rows)}
+                "samples": len(rows), "samples_total": len(self.rows)}
+
+
+# the timed region is repeated until it has lasted at least this long
+MIN_TIMED_SECONDS = 1.0
+# warm-up steps beyond the requested ones: enough to capture the step graph
+# (64 steps), let a batch time its tile shapes and bring the clocks up
+MIN_WARMUP_STEPS = 192
+
+
+def timed_blocks(step, k: int, stream, min_seconds: float = MIN_TIMED_SECONDS,
+                 max_blocks: int = 100000):
+    """Run step(k) R times back to back, each bracketed by CUDA events on the
+    launching stream, until the blocks have taken at least min_seconds of
+    device time; returns the per-block device times in ms.  The first block is
+    timed alone to size R, so that the whole region is queued without host
+    synchronisation between blocks."""
+    import torch
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    step(k)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    times = [e0.elapsed_time(e1)]
+    need = int(min(max_blocks, max(0, min_seconds * 1e3 / max(times[0], 1e-3) - 1)))
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(need)]
+    for a, b in evs:
+        a.record(stream)
+        step(k)
+        b.record(stream)
+    torch.cuda.synchronize()
+    times += [a.elapsed_time(b) for a, b in evs]
+    return times
+
+
+def median(v):
+    s = sorted(v)
+    n = len(s)
+    return s[n // 2] if n % 2 else 0.5 * (s[n // 2 - 1] + s[n // 2])
 
 
 def channel_sample(nx, ny, tau_f=0.6, w0=2.0, u0=0.35, radius=11.0, umax=0.005):
@@ -519,62 +589,76 @@ def main():
     # interface rays of the initial state (for the growth comparison below)
     d_init = [s_.diagnostics()["iface_pos"] for s_ in sims]
 
-    # warm-up (also builds the step graph; a batch tunes its tile shape here)
-    stepper.step(args.warmup)
-    torch.cuda.synchronize()
-
-    # --- device-resident timed region: K steps, inputs already in HBM ----------
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(local) as clk:
+        clk.wait_first()
+        # warm-up: at least MIN_WARMUP_STEPS, so that the step graph is built
+        # (and a batch has timed its tile shapes) before the timed region
+        warm = max(args.warmup, MIN_WARMUP_STEPS)
+        stepper.step(warm)
+        torch.cuda.synchronize()
+
+        # --- device-resident timed region: R blocks of K steps, inputs in HBM ---
         barrier()
         torch.cuda.synchronize()
-        ev0.record(stream)
-        stepper.step(args.steps)
-        ev1.record(stream)
-        torch.cuda.synchronize()
+        clk.mark_start()
+        blocks = timed_blocks(stepper.step, args.steps, stream)
+        clk.mark_end()
         barrier()
-    ms = ev0.elapsed_time(ev1)
+    reps = len(blocks)
+    ms = median(blocks)  # median device time of one block of K steps
     ms_max = max_over_ranks([ms], dist)[0]
     per_step_ms = ms_max / args.steps
     value = w["nodes_all"] * args.steps / (ms_max * 1e-3) / 1e6
     diags = [s.diagnostics() for s in sims]  # also surfaces any sticky device error
     d = diags[0]
-    total_steps = args.warmup + args.steps
+    total_steps = warm + args.steps * reps
+
+    def same_steps_plain(storage=None, collision=None):
+        """The same problem in another storage or collision, brought through the
+        same warm-up and timed blocks; returns its median block time (ms) and
+        its final interface rays."""
+        kw = lib_params(w, L, storage=storage)
+        if collision is not None:
+            kw["collision"] = collision
+        q = L.Sim(stream=stream.cuda_stream, **kw)
+        if w.get("baffle"):
+            q.set_solid(baffle_mask(w["nx"], w["ny"], w["baffle"]))
+        q.init_seed(*w["seed"])
+        q.step(warm)
+        torch.cuda.synchronize()
+        t = timed_blocks(q.step, args.steps, stream, max_blocks=reps - 1)
+        left = total_steps - warm - args.steps * len(t)
+        if left > 0:
+            q.step(left)
+        iface = q.diagnostics()["iface_pos"]
+        q.close()
+        return max_over_ranks([median(t)], dist)[0], iface
 
     vs_fp32 = None
     if batch is None and w["storage"] != "fp32":
         # the plain form: the same problem in FP32 storage, the same steps
-        q = L.Sim(stream=stream.cuda_stream, **lib_params(w, L, storage="fp32"))
-        q.init_seed(*w["seed"])
-        q.step(args.warmup)
-        torch.cuda.synchronize()
-        ev0.record(stream)
-        q.step(args.steps)
-        ev1.record(stream)
-        torch.cuda.synchronize()
-        ms32 = max_over_ranks([ev0.elapsed_time(ev1)], dist)[0]
-        e, rel = iface_compare(d_init[0], d["iface_pos"], q.diagnostics()["iface_pos"], w["dim"])
+        ms32, iface32 = same_steps_plain(storage="fp32")
+        e, rel = iface_compare(d_init[0], d["iface_pos"], iface32, w["dim"])
         vs_fp32 = {"plain_fp32_ms_per_step": ms32 / args.steps,
                    "speedup": ms32 / ms_max, "steps": total_steps,
                    "iface_pos_err_lu": e, "growth_rel_err": rel}
-        q.close()
+
+    fp16_form = None
+    if batch is None and w["storage"] == "fp32" and w.get("fp16_compare"):
+        # the FP16-storage form of the same problem over the same steps: its
+        # speed-up over this FP32 run and its interface against it
+        ms16, iface16 = same_steps_plain(storage="fp16")
+        e, rel = iface_compare(d_init[0], iface16, d["iface_pos"], w["dim"])
+        fp16_form = {"fp16_ms_per_step": ms16 / args.steps, "speedup_over_fp32": ms_max / ms16,
+                     "steps": total_steps, "iface_pos_err_lu": e, "growth_rel_err": rel}
 
     vs_bgk = None
     if batch is None and w.get("collision"):
         # the same problem with the BGK collision (Eq. 8), the same steps
-        q = L.Sim(stream=stream.cuda_stream, **dict(lib_params(w, L), collision=0))
-        q.init_seed(*w["seed"])
-        q.step(args.warmup)
-        torch.cuda.synchronize()
-        ev0.record(stream)
-        q.step(args.steps)
-        ev1.record(stream)
-        torch.cuda.synchronize()
-        msb = max_over_ranks([ev0.elapsed_time(ev1)], dist)[0]
-        e, rel = iface_compare(d_init[0], d["iface_pos"], q.diagnostics()["iface_pos"], w["dim"])
+        msb, ifaceb = same_steps_plain(collision=0)
+        e, rel = iface_compare(d_init[0], d["iface_pos"], ifaceb, w["dim"])
         vs_bgk = {"bgk_ms_per_step": msb / args.steps, "time_ratio_chm_over_bgk": ms_max / msb,
                   "steps": total_steps, "iface_pos_diff_lu": e, "growth_rel_diff": rel}
-        q.close()
 
     batch_info = None
     if batch is not None:
@@ -663,6 +747,11 @@ def main():
     peak, peak_kind = measured_peaks()
     achieved = w["bytes_per_lup"] * w["nodes"] / (per_step_ms * 1e-3) / 1e9
     traffic = profiled_traffic(w)
+    clocks = clk.summary()
+    if clocks.get("sm_mhz"):
+        # the step time scaled to the median SM clock seen (ms x MHz): compares
+        # runs taken at different clocks
+        clocks["ms_per_step_x_mhz"] = per_step_ms * clocks["sm_mhz"]
 
     if rank == 0:
         cpu = None
@@ -677,6 +766,11 @@ def main():
         out = {
             "metric": "coupled-LB MLUPS", "value": value, "unit": "MLUPS", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_step_ms,
+            "timing": {"blocks": reps, "steps_per_block": args.steps,
+                       "statistic": "median over blocks (CUDA events on the step stream)",
+                       "ms_per_block_median": ms, "ms_per_block_mean": sum(blocks) / reps,
+                       "ms_per_block_min": min(blocks), "ms_per_block_max": max(blocks),
+                       "timed_s": sum(blocks) * 1e-3, "warmup_steps_run": warm},
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32" if w["storage"] == "fp32" else (
                 "f64" if w["storage"] == "fp64" else f"f32 ({w['storage']} storage)"),
@@ -696,13 +790,15 @@ def main():
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": "MLUPS",
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-            "gpu_launches": args.steps,
-            "clocks": clk.summary(),
+            "gpu_launches": args.steps * reps,
+            "clocks": clocks,
             "diag": {"step": d["step"], "solute_drift_rel": d["solute_drift_rel"],
                      "r_eq": d["r_eq"]},
         }
         if vs_fp32 is not None:
             out["vs_plain_fp32"] = vs_fp32
+        if fp16_form is not None:
+            out["fp16_storage"] = fp16_form
         if vs_bgk is not None:
             out["vs_bgk"] = vs_bgk
         if batch_info is not None:
@@ -744,9 +840,11 @@ def run_facets(args, w):
     hist_t, hist_L = [args.warmup], [first["L"]]
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(local) as clk:
+        clk.wait_first()
         if dist is not None:
             dist.barrier()
         torch.cuda.synchronize()
+        clk.mark_start()
         ev0.record(stream)
         for k in range(steps // every):
             sim.step(every)
@@ -755,6 +853,7 @@ def run_facets(args, w):
             hist_L.append(r["L"])
         ev1.record(stream)
         torch.cuda.synchronize()
+        clk.mark_end()
         if dist is not None:
             dist.barrier()
     ms = max_over_ranks([ev0.elapsed_time(ev1)], dist)[0]
@@ -862,6 +961,8 @@ def run_network(args, w):
     torch.cuda.synchronize()
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
     with ClockSampler(int(os.environ.get("LOCAL_RANK", "0"))) as clk:
+        clk.wait_first()
+        clk.mark_start()
         ev[0].record(stream)
         for _ in range(args.steps):
             net.forward(x, y)
@@ -870,6 +971,7 @@ def run_network(args, w):
             net.train_step(x, t, 1e-5)
         ev[2].record(stream)
         torch.cuda.synchronize()
+        clk.mark_end()
     net.status()
     fwd = ev[0].elapsed_time(ev[1]) / args.steps
     trn = ev[1].elapsed_time(ev[2]) / args.steps
@@ -949,7 +1051,9 @@ def run_surrogate(args, w):
     steps = K * nb
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(local) as clk:
+        clk.wait_first()
         torch.cuda.synchronize()
+        clk.mark_start()
         ev0.record(stream)
         rep = L.lbpf_surrogate_advance(a, net, pcfg, K)
         ev1.record(stream)
@@ -959,6 +1063,7 @@ def run_surrogate(args, w):
         b.step(steps)
         ev1.record(stream)
         torch.cuda.synchronize()
+        clk.mark_end()
         ms_lb = ev0.elapsed_time(ev1)
     ms_s, ms_lb = max_over_ranks([ms_s, ms_lb], dist)
     da, db = a.diagnostics(), b.diagnostics()

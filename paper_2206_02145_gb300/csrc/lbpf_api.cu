@@ -31,6 +31,7 @@ struct lbpf_batch {
 namespace {
 
 constexpr int kGraphSteps = 64;  // even, so a replay keeps the buffer parity
+constexpr int kTailMin = 4;      // shorter remainders are launched one by one
 
 int fail(lbpf* h, int code, const char* fmt, ...) {
   if (!h) return code;
@@ -183,16 +184,15 @@ int launch_one(lbpf* h, cudaStream_t s) {
   return LBPF_OK;
 }
 
-// Capture kGraphSteps launches starting from buffer parity 0.
-int build_graph(lbpf* h) {
-  if (h->graph) return LBPF_OK;
+// Capture n launches starting from buffer parity `parity` into *out.
+int capture_steps(lbpf* h, int n, int parity, cudaGraphExec_t* out) {
   if (!h->cap_stream) CK(h, cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
   const int saved = h->cur;
-  h->cur = 0;
+  h->cur = parity;
   cudaGraph_t g = nullptr;
   CK(h, cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
   int rc = LBPF_OK;
-  for (int i = 0; i < kGraphSteps && rc == LBPF_OK; ++i) rc = launch_one(h, h->cap_stream);
+  for (int i = 0; i < n && rc == LBPF_OK; ++i) rc = launch_one(h, h->cap_stream);
   cudaError_t e = cudaStreamEndCapture(h->cap_stream, &g);
   h->cur = saved;
   if (rc != LBPF_OK) {
@@ -200,18 +200,51 @@ int build_graph(lbpf* h) {
     return rc;
   }
   if (e != cudaSuccess) return fail(h, LBPF_ECUDA, "graph capture: %s", cudaGetErrorString(e));
-  e = cudaGraphInstantiate(&h->graph, g, 0);
+  e = cudaGraphInstantiate(out, g, 0);
   cudaGraphDestroy(g);
   if (e != cudaSuccess) return fail(h, LBPF_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
+  return LBPF_OK;
+}
+
+// Capture kGraphSteps launches starting from buffer parity 0.
+int build_graph(lbpf* h) {
+  if (h->graph) return LBPF_OK;
+  int rc = capture_steps(h, kGraphSteps, 0, &h->graph);
+  if (rc) return rc;
   h->graph_steps = kGraphSteps;
   return LBPF_OK;
 }
 
-// The graph bakes the model constants in; drop it when they change.
+// The graph of n (< kGraphSteps) steps from the current parity: found among
+// the cached ones or captured (replacing the oldest).
+int tail_graph(lbpf* h, int n, cudaGraphExec_t* out) {
+  for (int i = 0; i < lbpf::kTailGraphs; ++i)
+    if (h->tail_graph[i] && h->tail_n[i] == n && h->tail_parity[i] == h->cur) {
+      *out = h->tail_graph[i];
+      return LBPF_OK;
+    }
+  const int i = h->tail_next;
+  h->tail_next = (i + 1) % lbpf::kTailGraphs;
+  if (h->tail_graph[i]) cudaGraphExecDestroy(h->tail_graph[i]);
+  h->tail_graph[i] = nullptr;
+  int rc = capture_steps(h, n, h->cur, &h->tail_graph[i]);
+  if (rc) return rc;
+  h->tail_n[i] = n;
+  h->tail_parity[i] = h->cur;
+  *out = h->tail_graph[i];
+  return LBPF_OK;
+}
+
+// The graphs bake the model constants in; drop them when they change.
 void drop_graph(lbpf* h) {
   if (h->graph) cudaGraphExecDestroy(h->graph);
   h->graph = nullptr;
   h->graph_steps = 0;
+  for (int i = 0; i < lbpf::kTailGraphs; ++i) {
+    if (h->tail_graph[i]) cudaGraphExecDestroy(h->tail_graph[i]);
+    h->tail_graph[i] = nullptr;
+    h->tail_n[i] = 0;
+  }
 }
 
 int ensure_fields_buffer(lbpf* h, size_t bytes) {
@@ -247,16 +280,22 @@ void store_I0(lbpf* h) {
   cudaMemcpyAsync(h->d_diag + 16, h->d_diag, sizeof(double), cudaMemcpyDeviceToDevice, h->stream);
 }
 
-constexpr char kMagic[8] = {'L', 'B', 'P', 'F', 'S', 'T', '0', '1'};
+constexpr char kMagic[8] = {'L', 'B', 'P', 'F', 'S', 'T', '0', '2'};
 
 struct StateHeader {
   char magic[8];
   int64_t step;
   int32_t dim, nx, ny, nz, storage, flow, q, elem;
   double ref_g;  // reference U of the stored g deviations
-  char pad[8];
+  // where the diagnostics measure from: the node the interface rays start at
+  // (the seed centre) and the solute total Sum(U + phi_lag) at initialisation
+  // (the base of solute_drift_rel), so that a restored run reports what the
+  // uninterrupted one does
+  int32_t icx, icy, icz, pad0;
+  double solute0;
+  char pad[48];
 };
-static_assert(sizeof(StateHeader) == 64, "state header must be 64 bytes");
+static_assert(sizeof(StateHeader) == 128, "state header must be 128 bytes");
 
 }  // namespace
 
@@ -471,6 +510,14 @@ int lbpf_step(lbpf_t* h, int n) {
       }
     }
   }
+  if (left >= kTailMin) {
+    // the rest as one graph of its own (cached per count and parity)
+    cudaGraphExec_t g = nullptr;
+    if ((rc = tail_graph(h, left, &g))) return rc;
+    CK(h, cudaGraphLaunch(g, h->stream));
+    h->cur ^= left & 1;
+    left = 0;
+  }
   for (; left > 0; --left)
     if ((rc = launch_one(h, h->stream))) return rc;
   h->step += n;
@@ -505,8 +552,12 @@ int lbpf_read_fields(lbpf_t* h, unsigned mask, void* host_dst, size_t bytes, int
     hd.q = h->m.qf + 2 * h->m.qs;
     hd.elem = int32_t(h->es);
     hd.ref_g = h->m.ref_g;
+    hd.icx = h->icx;
+    hd.icy = h->icy;
+    hd.icz = h->icz;
+    CK(h, cudaMemcpyAsync(&hd.solute0, h->d_diag + 16, sizeof(double), cudaMemcpyDeviceToHost,
+                          h->stream));
     char* dst = static_cast<char*>(host_dst);
-    std::memcpy(dst, &hd, sizeof(hd));
     const size_t rows = size_t(hd.q) * h->m.ny * h->m.nz;
     CK(h, copy_rows(dst + sizeof(hd), h->m.nx * h->es, h->pops[h->cur], h->m.px * h->es,
                     h->m.nx * h->es, rows, cudaMemcpyDeviceToHost, h->stream));
@@ -519,7 +570,9 @@ int lbpf_read_fields(lbpf_t* h, unsigned mask, void* host_dst, size_t bytes, int
         CK(h, copy_rows(ud + k * n * 2, h->m.nx * 2, uref_dev(h, h->cur ^ k), h->m.px * 2,
                         h->m.nx * 2, h->m.ny, cudaMemcpyDeviceToHost, h->stream));
     }
-    return check_device_error(h);
+    rc = check_device_error(h);  // synchronises: hd.solute0 has arrived
+    std::memcpy(dst, &hd, sizeof(hd));
+    return rc;
   }
   const unsigned fm = mask & 0x7Fu;
   if (fm == 0 || mask != fm) return fail(h, LBPF_EINVAL, "unknown field bits");
@@ -542,7 +595,9 @@ int lbpf_write_state(lbpf_t* h, const void* host_src, size_t bytes) {
   std::memcpy(&hd, host_src, sizeof(hd));
   if (std::memcmp(hd.magic, kMagic, 8) != 0 || hd.dim != h->m.dim || hd.nx != h->m.nx ||
       hd.ny != h->m.ny || hd.nz != h->m.nz || hd.storage != h->m.storage || hd.flow != h->m.flow ||
-      hd.q != h->m.qf + 2 * h->m.qs || hd.elem != int32_t(h->es) || hd.step < 0)
+      hd.q != h->m.qf + 2 * h->m.qs || hd.elem != int32_t(h->es) || hd.step < 0 ||
+      hd.icx < 0 || hd.icx >= h->m.nx || hd.icy < 0 || hd.icy >= h->m.ny || hd.icz < 0 ||
+      hd.icz >= h->m.nz || !std::isfinite(hd.solute0))
     return fail(h, LBPF_EINVAL, "state does not match this handle");
   const size_t n = size_t(nodes(h->p));
   const char* src = static_cast<const char*>(host_src);
@@ -565,10 +620,12 @@ int lbpf_write_state(lbpf_t* h, const void* host_src, size_t bytes) {
   h->m.ref_g = hd.ref_g;
   lbk::finalize(h->m);
   ++h->gen;
-  if (!h->initialized) {
-    h->initialized = true;
-    store_I0(h);
-  }
+  h->icx = hd.icx;
+  h->icy = hd.icy;
+  h->icz = hd.icz;
+  CK(h, cudaMemcpyAsync(h->d_diag + 16, &hd.solute0, sizeof(double), cudaMemcpyHostToDevice,
+                        h->stream));
+  h->initialized = true;
   CK(h, cudaStreamSynchronize(h->stream));
   return LBPF_OK;
 }
@@ -811,7 +868,7 @@ const char* lbpf_last_error(const lbpf_t* h) { return h ? h->msg : "null handle"
 void lbpf_destroy(lbpf_t* h) {
   if (!h) return;
   cudaStreamSynchronize(h->stream);
-  if (h->graph) cudaGraphExecDestroy(h->graph);
+  drop_graph(h);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   for (int i = 0; i < 2; ++i) {
     if (h->pops[i]) cudaFree(h->pops[i]);

@@ -34,6 +34,13 @@ struct lbpf {
   lbk::StepMaps maps;
   cudaGraphExec_t graph = nullptr;
   int graph_steps = 0;
+  // graphs of shorter step counts (the remainder of an lbpf_step call below
+  // the main graph's length), keyed by count and starting buffer parity
+  static constexpr int kTailGraphs = 4;
+  cudaGraphExec_t tail_graph[kTailGraphs] = {nullptr, nullptr, nullptr, nullptr};
+  int tail_n[kTailGraphs] = {0, 0, 0, 0};
+  int tail_parity[kTailGraphs] = {0, 0, 0, 0};
+  int tail_next = 0;
   int status = LBPF_OK;
   int gen = 0;  // bumped whenever the state or the model constants are replaced
   char msg[256] = {0};
