@@ -81,6 +81,9 @@ _W = {9: [4 / 9] + [1 / 9] * 4 + [1 / 36] * 4,
       7: [1 / 4] + [1 / 8] * 6}
 
 
+HDR = 128  # bytes of the exported state's header
+
+
 def decode_pops(sim, buf=None):
     """Populations {'f','g','h'} [q, ...] of a library handle's exported state."""
     if buf is None:
@@ -91,7 +94,7 @@ def decode_pops(sim, buf=None):
     storage = int(hdr[4])
     dt = {8: np.float64, 4: np.float32}.get(elem)
     n = sim.nodes
-    raw = np.frombuffer(buf[64:64 + q * n * elem].tobytes(),
+    raw = np.frombuffer(buf[HDR:HDR + q * n * elem].tobytes(),
                         dtype=dt if dt else np.uint16).reshape((q, n))
     if elem == 2:
         if storage == L.FP16_SHIFTED:
@@ -104,7 +107,7 @@ def decode_pops(sim, buf=None):
     g_ref = u_ref
     if dim == 2 and elem == 2:
         # per-node g reference: the first FP16 plane after the FP32 phi ring
-        off = 64 + q * n * elem + n * 4
+        off = HDR + q * n * elem + n * 4
         g_ref = np.frombuffer(buf[off:off + 2 * n].tobytes(), dtype=np.float16)
         g_ref = g_ref.astype(np.float64)[None, :]
     out = {}
