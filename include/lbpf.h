@@ -232,9 +232,12 @@ int lbpf_step(lbpf_t* h, int n);
 int lbpf_read_fields(lbpf_t* h, unsigned field_mask, void* host_dst, size_t bytes,
                      int as_fp64);
 
-/* Size of the restartable state: a 64-byte header (magic "LBPFST01", int64
+/* Size of the restartable state: a 128-byte header (magic "LBPFST02", int64
  * step, int32 dim, nx, ny, nz, storage, flow, populations per node, element
- * bytes, then at byte 48 the double U_ref), then the populations
+ * bytes, then at byte 48 the double U_ref, at byte 56 int32 cx, cy, cz: the
+ * node the interface rays of lbpf_diagnostics start from, at byte 72 the
+ * double solute total at initialisation that solute_drift_rel is relative
+ * to; the rest zero), then the populations
  * direction-major in the storage type (f, then g, then h; directions in the
  * order: D2Q9 (0,0) (1,0) (0,1) (-1,0) (0,-1) (1,1) (-1,1) (-1,-1) (1,-1);
  * D3Q19 rest, +x, -x, +y, -y, +z, -z, (1,1,0) (-1,-1,0) (1,-1,0) (-1,1,0)
@@ -248,7 +251,10 @@ int lbpf_read_fields(lbpf_t* h, unsigned field_mask, void* host_dst, size_t byte
 size_t lbpf_state_bytes(const lbpf_t* h);
 
 /* Restore a state written by lbpf_read_fields(LBPF_FIELD_STATE) of a handle
- * with the same grid, flow and storage.  Synchronising. */
+ * with the same grid, flow and storage: the populations, the phi ring, the
+ * step count and the diagnostics' references (ray origin, initial solute
+ * total), so that a restored run continues and reports exactly as the
+ * uninterrupted one.  Synchronising. */
 int lbpf_write_state(lbpf_t* h, const void* host_src, size_t bytes);
 
 /* FP64 reductions of the current state (deterministic two-pass sums).
@@ -502,8 +508,11 @@ int lbpf_surrogate_target(const lbpf_surrogate_cfg* cfg, const float* x0, const 
  * and a small pinned host buffer, owned by the network) and captures the
  * prediction phase as a CUDA graph per state buffer, recaptured when the
  * simulation, its stream or cfg change: do not call it inside a stream
- * capture of your own.  LBPF_ETIMEDOUT if a tensor-core kernel gave up
- * waiting; LBPF_EINVAL for a mismatched network or cfg. */
+ * capture of your own.  The scratch (its FP64 reduction included) belongs to
+ * the network, so propagators with networks of their own run independently,
+ * on unordered streams too; calls that share one network must not overlap
+ * (from several host threads).  LBPF_ETIMEDOUT if a tensor-core kernel gave
+ * up waiting; LBPF_EINVAL for a mismatched network or cfg. */
 int lbpf_surrogate_advance(lbpf_t* h, lbpf_unet_t* net, const lbpf_surrogate_cfg* cfg,
                            int blocks, lbpf_surrogate_report* rep);
 
@@ -531,9 +540,12 @@ int lbpf_surrogate_advance(lbpf_t* h, lbpf_unet_t* net, const lbpf_surrogate_cfg
  * (NULL = legacy default stream) and the call returns without waiting.
  * The first call on a device looks up the device address of the scratch
  * array (with that device current): make that first call before any stream
- * capture.  Every call shares the one scratch array; calls that can overlap
- * on the GPU (different streams without ordering) race on it and must be
- * serialised by the caller. */
+ * capture.  The address is kept per device together with the ID of the
+ * context it belongs to, and looked up again when that context changes (after
+ * a cudaDeviceReset, for instance).  Every call shares the one scratch array;
+ * calls that can overlap on the GPU (different streams without ordering) race
+ * on it and must be serialised by the caller.  The library's own block
+ * propagator does not use it (it reduces into its network's scratch). */
 #define LBPF_NOALLOC_MAX_BLOCKS 4096
 #define LBPF_NOALLOC_MAX_NODES ((int64_t)LBPF_NOALLOC_MAX_BLOCKS * 256 * 64)
 int lbpf_field_sums_noalloc(const void* phi, const void* phi_prev, const void* U,

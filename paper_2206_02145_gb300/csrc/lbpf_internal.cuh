@@ -264,4 +264,14 @@ size_t diag_partials_bytes(const Model& m);
 cudaError_t launch_diag(const Model& m, const void* pops, const void* phi_prev, int c,
                         double* partials, double* out, int icx, int icy, int icz, cudaStream_t s);
 
+// FP64 sums of caller-held fields (n values each, float or double; rho may be
+// null for 1): out[0] = sum(U + phi_prev), out[1] = sum(rho), out[2] =
+// sum((1 + clamp(phi))/2), by the deterministic two-pass reduction.
+// partials: scratch of field_sums_blocks(n) x 3 doubles, owned by the caller
+// (the allocation-free entry point passes its file-scope array).
+int field_sums_blocks(int64_t n);
+cudaError_t launch_field_sums(const void* phi, const void* phi_prev, const void* U,
+                              const void* rho, int64_t n, int fp64, double* partials,
+                              int blocks, double* out, cudaStream_t s);
+
 }  // namespace lbk

@@ -74,6 +74,7 @@ struct lbpf_unet {
   float *px = nullptr, *py = nullptr, *pF = nullptr, *pF1 = nullptr;
   float *tx = nullptr, *tt = nullptr;  // training minibatch (lbpf_surrogate_train)
   double *psum = nullptr, *pcross = nullptr;
+  double* ppart = nullptr;  // partial sums of the prediction's FP64 reduction
   // the prediction phase of a block as a CUDA graph per buffer parity, with
   // the key it was captured for; results land in pinned host memory
   cudaGraphExec_t pgraph[2] = {nullptr, nullptr};
@@ -815,9 +816,10 @@ int queue_prediction(lbpf* h, lbpf_unet* net, const lbpf_surrogate_cfg* cfg, cud
   apply_kernel<<<grid_of(n), 256, 0, s>>>(net->pF, net->py, vec4(cfg->res_scale), 1.0f / nb, n,
                                           net->pF1);
   SCK(h, cudaGetLastError());
-  if ((rc = lbpf_field_sums_noalloc(net->pF1, net->pF1 + 4 * n, net->pF1 + n, net->pF + 4 * n, n, 0,
-                                    net->psum, s)))
-    return sfail(h, rc, "solute sum of the prediction");
+  // the prediction's FP64 sums, into this network's own scratch: two
+  // propagators on unordered streams do not share it
+  SCK(h, lbk::launch_field_sums(net->pF1, net->pF1 + 4 * n, net->pF1 + n, net->pF + 4 * n, n, 0,
+                                net->ppart, lbk::field_sums_blocks(n), net->psum, s));
   plane_crossing_kernel<<<1, 128, 0, s>>>(net->pF1, h->m.nx, h->m.ny, h->m.bc[0], h->m.bc[1], h->icx,
                                          h->icy, net->pcross);
   SCK(h, cudaGetLastError());
@@ -901,6 +903,7 @@ int lbpf_surrogate_advance(lbpf_t* h, lbpf_unet_t* net, const lbpf_surrogate_cfg
     chk(dalloc(net, &net->pF, size_t(5 * n)));
     chk(dalloc(net, &net->pF1, size_t(5 * n)));
     chk(dalloc(net, &net->psum, 4));
+    chk(dalloc(net, &net->ppart, size_t(3 * lbk::field_sums_blocks(n))));
     chk(dalloc(net, &net->pcross, 8));
     chk(cudaMallocHost(&net->hres, 16 * sizeof(double)));
     if (e != cudaSuccess)

@@ -107,6 +107,9 @@ def test_frozen_network_is_caught_by_the_interface_estimate(L, S):
     rep = L.lbpf_surrogate_advance(a, net, cfg, 16)
     assert rep["blocks"] == 16
     assert rep["judged_blocks"] + rep["fallback_blocks"] >= 2, rep
+    # once trusted after a judged block, the frozen network is accepted until
+    # its accumulated estimate passes the budget: that block falls back
+    assert rep["fallback_blocks"] >= 1, rep
     assert rep["iface_acc"] <= tol
     assert a.diagnostics()["step"] == 200 + 16 * 50
     for s in (a, net):
@@ -124,3 +127,38 @@ def test_rejects_mismatched_network(L, S):
         L.lbpf_surrogate_advance(a, _net(L), L.surrogate_cfg(steps_per_block=0), 1)
     a.close()
     net.close()
+
+
+def test_two_propagators_on_unordered_streams(L, S):
+    # each network holds its own propagator scratch (the FP64 reduction of the
+    # prediction included): two propagators advanced at the same time from two
+    # host threads on two unordered streams give what each gives alone
+    import threading
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    probs = [_problem(S, 11), _problem(S, 12)]
+
+    def run(i, stream, out):
+        params, fields, _ = probs[i]
+        sim = S.make_sim(params, fields, stream.cuda_stream)
+        sim.step(100)
+        net = L.UNet(in_ch=4, out_ch=4, levels=3, batch=1, height=NY, width=NX, seed=5,
+                     stream=stream.cuda_stream)
+        net.set_weights(np.zeros(net.param_count, np.float32))  # predicts no change
+        cfg = L.surrogate_cfg(judge_every=3, iface_tol=1.0)
+        out[i] = (L.lbpf_surrogate_advance(sim, net, cfg, 9), sim.state())
+        sim.close()
+        net.close()
+
+    alone = [None, None]
+    for i in range(2):
+        run(i, streams[i], alone)
+    both = [None, None]
+    threads = [threading.Thread(target=run, args=(i, streams[i], both)) for i in range(2)]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join()
+    for i in range(2):
+        assert both[i][0] == alone[i][0], (both[i][0], alone[i][0])
+        assert alone[i][0]["surrogate_blocks"] > 0, alone[i][0]
+        np.testing.assert_array_equal(both[i][1], alone[i][1])
