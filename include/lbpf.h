@@ -69,12 +69,12 @@ enum {
   LBPF_FP16_SHIFTED = 2, /* binary16 deviation from the lattice weight times a reference moment */
   LBPF_BF16_SHIFTED = 3  /* bfloat16, same shift */
 };
-/* With 16-bit storage in 2D the reference moment of g is per node: each node
- * keeps its U of an earlier step (FP16, two planes that alternate with the
- * population buffers), and the g pushed to a node is stored as its deviation
- * from w_a times that node's reference.  The rounding of the stored
+/* With 16-bit storage the reference moment of g is per node (2D and 3D):
+ * each node keeps its U of an earlier step (FP16, two planes that alternate
+ * with the population buffers), and the g pushed to a node is stored as its
+ * deviation from w_a times that node's reference.  The rounding of the stored
  * deviations then no longer accumulates into a drift of the growth rate over
- * long runs.  f, h and the 3D g keep one global reference. */
+ * long runs.  f and h keep one global reference. */
 
 /* Field selection bits of lbpf_read_fields. */
 enum {
@@ -245,8 +245,8 @@ int lbpf_read_fields(lbpf_t* h, unsigned field_mask, void* host_dst, size_t byte
  * D3Q7 the first seven of those), each stored as its deviation
  * d_a = p_a - w_a M_ref with M_ref = 1 for f, U_ref for g and -1 for h; then
  * phi(t-1) + 1 in FP64 for LBPF_FP64 storage and FP32 otherwise; then, for
- * 2D with 16-bit storage only, two FP16 planes of nx*ny values: the per-node
- * g reference of the stored populations (their M_ref of g instead of U_ref),
+ * 16-bit storage only, two FP16 planes of nx*ny*nz values: the per-node g
+ * reference of the stored populations (their M_ref of g instead of U_ref),
  * and the one the next step encodes against. */
 size_t lbpf_state_bytes(const lbpf_t* h);
 
@@ -289,20 +289,22 @@ int lbpf_facets_collect(lbpf_t* h, lbpf_facets* out);
 int lbpf_growth_fit(const double* t, const double* L, int n, double* slope, double* intercept,
                     double* r2);
 
-/* Solid nodes, 2D (the reactor walls and baffles of Sec. 3.1.2 and 3.2):
- * mask is a host array of nx*ny bytes (x fastest), nonzero = solid, read
- * during the call; NULL removes the mask.  A fluid node sends what it would
- * stream into a solid node back into itself reversed (half-way bounce-back,
- * for f, g and h: no flow through, zero flux of U and phi); in the phi
- * gradient a solid neighbour counts as the first fluid node among
- * (x + c_x, y), (x, y + c_y) and (x, y) (zero normal derivative; for a
- * straight row of solid nodes this is exactly the LBPF_BC_WALL boundary).
- * Solid nodes keep their state (both buffers hold it; the field read-out and
- * the diagnostics include their constant values).  Tiles that touch no solid
- * node run at full speed.  With LBPF_BC_INLET_OUTLET the first and last
- * columns must be fluid.  EINVAL for 3D.  The mask is configuration, not
- * state: lbpf_write_state keeps it.  The block propagator refuses a handle
- * with solid nodes.  Synchronising. */
+/* Solid nodes (the reactor walls and baffles of Sec. 3.1.2 and 3.2): mask is
+ * a host array of nx*ny*nz bytes (x fastest, then y, then z; nz = 1 in 2D),
+ * nonzero = solid, read during the call; NULL removes the mask.  A fluid node
+ * sends what it would stream into a solid node back into itself reversed
+ * (half-way bounce-back, for f, g and h: no flow through, zero flux of U and
+ * phi); in the phi gradient a solid neighbour x + c counts as the first fluid
+ * node among the single-axis steps x + c_x e_x, x + c_y e_y, x + c_z e_z (those
+ * with a non-zero component, in that order) and x itself (zero normal
+ * derivative; for a straight row or plane of solid nodes this is exactly the
+ * LBPF_BC_WALL boundary).  Solid nodes keep their state (both buffers hold it;
+ * the field read-out and the diagnostics include their constant values).
+ * Tiles (3D: column chunks) that touch no solid node run at full speed.  With
+ * LBPF_BC_INLET_OUTLET the first and last columns (x = 0 and x = nx - 1 of
+ * every row) must be fluid.  The mask is configuration, not state:
+ * lbpf_write_state keeps it.  The block propagator refuses a handle with solid
+ * nodes.  Synchronising. */
 int lbpf_set_solid(lbpf_t* h, const uint8_t* mask);
 
 /* Rebind the handle to another stream (e.g. the caller's current stream). */

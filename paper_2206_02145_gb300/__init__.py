@@ -331,7 +331,8 @@ def rhombic_seed(perimeter: float, theta: float = 0.0, acute: float = np.pi / 3.
 
 
 def lbpf_set_solid(h: int, mask) -> None:
-    """Solid nodes (2D): mask [ny, nx] (nonzero = solid), or None to remove."""
+    """Solid nodes: mask [ny, nx] or [nz, ny, nx] (nonzero = solid), or None
+    to remove."""
     if mask is None:
         _check(h, _lib.lbpf_set_solid(h, None))
         return

@@ -63,9 +63,10 @@ __device__ void store_equilibrium(const Model& m, T* pops, long long j, double p
     for (int a = 0; a < 7; ++a) {
       const double w = d3q7_w<double>(a);
       const double cu = D3_CX[a] * us[0] + D3_CY[a] * us[1] + D3_CZ[a] * us[2];
-      Pop<T>::st(pg + a * P + j, w * ((U - m.ref_g) + U * 4.0 * cu));  // cs^2 = 1/4
+      Pop<T>::st(pg + a * P + j, w * ((U - Rg) + U * 4.0 * cu));  // cs^2 = 1/4
       Pop<T>::st(ph_ + a * P + j, w * (phi - m.ref_h));
     }
+    if (m.rel_g) m.uring[j] = m.uring[P + j] = Rh;
   }
 }
 
@@ -149,7 +150,7 @@ __global__ void init_polygon_kernel(const Model m, const PolygonArgs a, T* pops,
 template <typename T, typename R>
 __global__ void solid_sync_kernel(const Model m, const T* src, T* dst, const R* ring_src,
                                   R* ring_dst, const __half* uref_src, __half* uref_dst) {
-  const long long n = (long long)m.nx * m.ny;
+  const long long n = (long long)m.nx * m.ny * m.nz;
   const int q = m.qf + 2 * m.qs;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x) {
@@ -412,7 +413,7 @@ cudaError_t init_polygon_t(const Model& m, const PolygonArgs& a, void* pops, voi
 template <typename T, typename R>
 cudaError_t solid_sync_t(const Model& m, void* const pops[2], void* const rings[2], int c,
                          cudaStream_t s) {
-  const long long n = (long long)m.nx * m.ny;
+  const long long n = (long long)m.nx * m.ny * m.nz;
   __half* u = m.rel_g ? m.uring : nullptr;
   solid_sync_kernel<T, R><<<grid_for(n), 256, 0, s>>>(
       m, static_cast<const T*>(pops[c]), static_cast<T*>(pops[c ^ 1]),
@@ -492,7 +493,7 @@ cudaError_t launch_init_polygon(const Model& m, const PolygonArgs& a, void* pops
 }
 cudaError_t launch_solid_sync(const Model& m, void* const pops[2], void* const rings[2], int c,
                               cudaStream_t s) {
-  if (m.dim != 2 || !m.solid) return cudaErrorInvalidValue;
+  if (!m.solid) return cudaErrorInvalidValue;
   LBPF_DISPATCH(solid_sync_t, m, pops, rings, c, s)
 }
 cudaError_t launch_init_fields(const Model& m, const double* phi, const double* U,

@@ -142,9 +142,9 @@ Model derive(const lbpf_params& p) {
   m.ref_f = 1.0;
   m.ref_g = 0.0;
   m.ref_h = -1.0;
-  // 16-bit 2D storage keeps g relative to a per-node U (two FP32 planes,
+  // 16-bit storage keeps g relative to a per-node U (two FP16 planes,
   // allocated by lbpf_create)
-  m.rel_g = (p.dim == 2 && (p.storage == LBPF_FP16_SHIFTED || p.storage == LBPF_BF16_SHIFTED)) ? 1 : 0;
+  m.rel_g = (p.storage == LBPF_FP16_SHIFTED || p.storage == LBPF_BF16_SHIFTED) ? 1 : 0;
   m.uring = nullptr;
   m.solid = nullptr;
   m.solid_tiles = nullptr;
@@ -568,7 +568,8 @@ int lbpf_read_fields(lbpf_t* h, unsigned mask, void* host_dst, size_t bytes, int
       char* ud = dst + sizeof(hd) + size_t(hd.q) * n * h->es + n * h->rs;
       for (int k = 0; k < 2; ++k)
         CK(h, copy_rows(ud + k * n * 2, h->m.nx * 2, uref_dev(h, h->cur ^ k), h->m.px * 2,
-                        h->m.nx * 2, h->m.ny, cudaMemcpyDeviceToHost, h->stream));
+                        h->m.nx * 2, size_t(h->m.ny) * h->m.nz, cudaMemcpyDeviceToHost,
+                        h->stream));
     }
     rc = check_device_error(h);  // synchronises: hd.solute0 has arrived
     std::memcpy(dst, &hd, sizeof(hd));
@@ -612,7 +613,7 @@ int lbpf_write_state(lbpf_t* h, const void* host_src, size_t bytes) {
     const char* us = src + sizeof(hd) + size_t(hd.q) * n * h->es + n * h->rs;
     for (int k = 0; k < 2; ++k)
       CK(h, copy_rows(uref_dev(h, k), h->m.px * 2, us + k * n * 2, h->m.nx * 2, h->m.nx * 2,
-                      h->m.ny, cudaMemcpyHostToDevice, h->stream));
+                      size_t(h->m.ny) * h->m.nz, cudaMemcpyHostToDevice, h->stream));
   }
   if ((rc = sync_solids(h))) return rc;
   h->step = hd.step;
@@ -821,7 +822,6 @@ int lbpf_growth_fit(const double* t, const double* L, int n, double* slope, doub
 int lbpf_set_solid(lbpf_t* h, const uint8_t* mask) {
   int rc = check_handle(h);
   if (rc) return rc;
-  if (h->m.dim != 2) return fail(h, LBPF_EINVAL, "solid nodes are 2D");
   if (!mask) {
     h->m.solid = nullptr;
     h->m.solid_tiles = nullptr;
@@ -829,15 +829,17 @@ int lbpf_set_solid(lbpf_t* h, const uint8_t* mask) {
     ++h->gen;
     return LBPF_OK;
   }
-  const int nx = h->m.nx, ny = h->m.ny, px = h->m.px;
+  const int nx = h->m.nx, ny = h->m.ny, nz = h->m.nz, px = h->m.px;
+  const size_t rows = size_t(ny) * nz;  // rows of nx nodes (y fastest, then z)
   if (h->m.bc[0] == LBPF_BC_INLET_OUTLET)
-    for (int y = 0; y < ny; ++y)
-      if (mask[size_t(y) * nx] || mask[size_t(y) * nx + nx - 1])
-        return fail(h, LBPF_EINVAL, "the inlet and outlet columns must be fluid (row %d)", y);
-  std::vector<unsigned char> host(size_t(px) * ny, 0);
-  for (int y = 0; y < ny; ++y)
-    for (int x = 0; x < nx; ++x) host[size_t(y) * px + x] = mask[size_t(y) * nx + x] ? 1 : 0;
-  const size_t nt = lbk::solid_tile_count(h->m);
+    for (size_t r = 0; r < rows; ++r)
+      if (mask[r * nx] || mask[r * nx + nx - 1])
+        return fail(h, LBPF_EINVAL, "the inlet and outlet columns must be fluid (row %zu)", r);
+  std::vector<unsigned char> host(size_t(px) * rows, 0);
+  for (size_t r = 0; r < rows; ++r)
+    for (int x = 0; x < nx; ++x) host[r * px + x] = mask[r * nx + x] ? 1 : 0;
+  const size_t nt =
+      h->m.dim == 3 ? lbk::solid_chunk_count(h->m) : lbk::solid_tile_count(h->m);
   if (!h->d_solid) {
     cudaError_t e = cudaMalloc(&h->d_solid, host.size());
     if (e == cudaSuccess) e = cudaMalloc(&h->d_solid_tiles, nt);
@@ -847,7 +849,8 @@ int lbpf_set_solid(lbpf_t* h, const uint8_t* mask) {
   CK(h, cudaMemcpyAsync(h->d_solid, host.data(), host.size(), cudaMemcpyHostToDevice, h->stream));
   h->m.solid = h->d_solid;
   h->m.solid_tiles = h->d_solid_tiles;
-  CK(h, lbk::launch_solid_tiles(h->m, h->d_solid_tiles, h->stream));
+  CK(h, h->m.dim == 3 ? lbk::launch_solid_chunks(h->m, h->d_solid_tiles, h->stream)
+                      : lbk::launch_solid_tiles(h->m, h->d_solid_tiles, h->stream));
   CK(h, cudaStreamSynchronize(h->stream));  // the host copy goes out of scope
   drop_graph(h);
   ++h->gen;

@@ -54,20 +54,21 @@ struct Model {
   double ref_f, ref_g, ref_h;  // reference moments of the stored deviations (1, U_ref, -1)
   Coef<float> cf;   // the constants above in FP32 ...
   Coef<double> cd;  // ... and in FP64 (filled by finalize())
-  // 2D with 16-bit storage: g is stored relative to a per-node U instead of
-  // the global U_ref.  uring: two FP16 planes of `plane` values; for the
+  // 16-bit storage (2D and 3D): g is stored relative to a per-node U instead
+  // of the global U_ref.  uring: two FP16 planes of `plane` values; for the
   // populations of buffer c, plane c holds each node's reference, while the
   // step that reads them writes the node's new U into plane c and encodes the
   // populations it pushes against the destination's value in plane c ^ 1.
   // The reference only has to be the same number at encoding and decoding,
   // so FP16 loses nothing.
-  int chm;              // flow collision: 0 BGK, 1 central Hermite MRT (2D)
+  int chm;              // flow collision: 0 BGK, 1 central Hermite MRT
   double chm_wb, chm_wh;
   int rel_g;
   __half* uring;
-  // 2D solid nodes (walls, obstacles): one byte per node at y * px + x, 1 =
-  // solid; null when there are none.  solid_tiles: one byte per 32 x 4 tile
-  // of the step (row-major over the tiles), 1 = the tile or its one-node halo
+  // Solid nodes (walls, obstacles): one byte per node at (z * ny + y) * px +
+  // x, 1 = solid; null when there are none.  solid_tiles: in 2D one byte per
+  // 32 x 4 tile of the step (row-major over the tiles), in 3D one per column
+  // chunk of the z-marching step; 1 = the tile or chunk or its one-node halo
   // holds a solid node
   const unsigned char* solid;
   const unsigned char* solid_tiles;
@@ -221,6 +222,9 @@ cudaError_t launch_solid_sync(const Model& m, void* const pops[2], void* const r
 // (solid_tile_count(m) bytes).
 size_t solid_tile_count(const Model& m);
 cudaError_t launch_solid_tiles(const Model& m, unsigned char* flags, cudaStream_t s);
+// 3D: one flag per column chunk of the z-marching step
+size_t solid_chunk_count(const Model& m);
+cudaError_t launch_solid_chunks(const Model& m, unsigned char* flags, cudaStream_t s);
 // Support values of the phi = 0 contour of a 2D state (phi from the h
 // populations) along up to kMaxFacets + 4 unit directions, into out[0 ..
 // kMaxDirs] on the device: out[j] the order-preserving integer key of max over

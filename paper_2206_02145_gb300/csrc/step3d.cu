@@ -83,18 +83,25 @@ __global__ void __launch_bounds__(TX* TY* TZ)
   }
   __syncthreads();
   if (!active) return;
+  // with solid nodes every tile takes the general path with the mask (this
+  // kernel is the FP64 parity path; the FP32 one keeps per-chunk flags)
+  const bool solids = m.solid != nullptr;
+  if (solids && m.solid[idx]) {
+    ring_cur[idx] = sh_phi[tz + 1][ty + 1][tx + 1];  // a solid node keeps its state
+    return;
+  }
   HSlab3<R, SX, SX * SY, SX * SY * SZ> hs{&sh_h[0][tz + 1][0][0]};
   PhiSlab3<R, SX, SX * SY> pv{&sh_phi[tz + 1][0][0]};
   const bool interior = x0 >= 1 && x0 + TX <= nx - 1 && y0 >= 1 && y0 + TY <= ny - 1 &&
                         z0 >= 1 && z0 + TZ <= nz - 1;
-  if (interior)
+  if (interior && !solids)
     collide_push_3d<T, R, FLOW, true, CHM>(m, x, y, z, tx + 1, ty + 1, f, g, h,
                                            sh_phi[tz + 1][ty + 1][tx + 1], dphi_prev, pv, hs,
                                            dst, ring_cur, err);
   else
-    collide_push_3d<T, R, FLOW, false, CHM>(m, x, y, z, tx + 1, ty + 1, f, g, h,
-                                            sh_phi[tz + 1][ty + 1][tx + 1], dphi_prev, pv, hs,
-                                            dst, ring_cur, err);
+    collide_push_3d<T, R, FLOW, false, CHM, true>(m, x, y, z, tx + 1, ty + 1, f, g, h,
+                                                  sh_phi[tz + 1][ty + 1][tx + 1], dphi_prev, pv,
+                                                  hs, dst, ring_cur, err, solids);
 }
 
 // ---- the z-marching kernel (FP32 arithmetic) --------------------------------------
@@ -106,17 +113,29 @@ __global__ void __launch_bounds__(TX* TY* TZ)
 // the loads of the node's own f, g and phi(t-1), then loads plane z + 1 into
 // the ring, synchronises once and collides / pushes plane z.  With four
 // slots, the slot filled at z + 1 is never one another thread may still read.
-template <typename T, bool FLOW, bool CHM, int TX, int TY, int MINB>
+// MASK: the variant with solid nodes; a chunk whose flag (m.solid_tiles, one
+// per column and chunk) says that it or its one-node halo holds a solid node
+// takes the general path with the mask.
+//
+// 16-bit storage keeps g relative to a per-node U (two FP16 planes, as in
+// the 2D step): the node's own reference is read from plane c, its new U
+// written there, and every pushed g is encoded against the destination's
+// reference in plane c ^ 1, carried in a third ring of halo-extended planes.
+template <typename T, bool FLOW, bool CHM, int TX, int TY, int MINB, bool MASK>
 __global__ void __launch_bounds__(TX* TY, MINB)
     step3d_march_kernel(const Model m, const T* __restrict__ src, T* __restrict__ dst,
                         const float* __restrict__ ring_prev, float* __restrict__ ring_cur,
-                        unsigned* __restrict__ err, int zc) {
+                        unsigned* __restrict__ err, int zc, int c) {
   using R = float;
   constexpr int SX = TX + 2, SY = TY + 2, PL = SX * SY;
   constexpr int QF = FLOW ? 19 : 0;
   constexpr int NT = TX * TY;
+  constexpr bool REL = sizeof(T) == 2;
   __shared__ R sh_phi[4][PL];
   __shared__ R sh_h[4][7 * PL];
+  __shared__ __half sh_u[REL ? 4 : 1][REL ? PL : 1];
+  const __half* uref_own = REL ? m.uring + size_t(c) * size_t(m.plane) : nullptr;
+  const __half* uref_enc = REL ? m.uring + size_t(c ^ 1) * size_t(m.plane) : nullptr;
   const int tid = threadIdx.x;
   const int tx = tid % TX, ty = tid / TX;
   const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
@@ -128,6 +147,9 @@ __global__ void __launch_bounds__(TX* TY, MINB)
   const int x = x0 + tx, y = y0 + ty;
   const bool active = x < nx && y < ny;
   const bool xy_inner = x0 >= 1 && x0 + TX <= nx - 1 && y0 >= 1 && y0 + TY <= ny - 1;
+  const bool solids =
+      MASK && m.solid &&
+      m.solid_tiles[(size_t(blockIdx.z) * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x];
 
   // the in-plane offsets of this thread's positions of the halo-extended
   // plane (the same on every plane of the column)
@@ -157,6 +179,7 @@ __global__ void __launch_bounds__(TX* TY, MINB)
         s += v;
       }
       sh_phi[slot][i] = s;
+      if (REL) sh_u[slot][i] = uref_enc[j];
     }
   };
 
@@ -168,6 +191,7 @@ __global__ void __launch_bounds__(TX* TY, MINB)
     const int idx = z * slab + y * px + x;
     R f[19], g[7], h[7];
     R dphi_prev = R(0);
+    float uown = 0.f;
     if (active) {
 #pragma unroll
       for (int a = 0; a < 19; ++a)
@@ -175,23 +199,32 @@ __global__ void __launch_bounds__(TX* TY, MINB)
 #pragma unroll
       for (int a = 0; a < 7; ++a) g[a] = Pop<T>::template ld<R>(src + ((QF + a) * P + idx));
       dphi_prev = ring_prev[idx];
+      if (REL) uown = __half2float(uref_own[idx]);
     }
     load_plane(z + 1, sp);
     __syncthreads();
     if (active) {
       const int o = (ty + 1) * SX + tx + 1;
+      if (MASK && solids && m.solid[idx]) {
+        ring_cur[idx] = sh_phi[s0][o];  // a solid node keeps its state
+        continue;
+      }
 #pragma unroll
       for (int a = 0; a < 7; ++a) h[a] = sh_h[s0][a * PL + o];
       PhiRing3<R, SX> pv{{sh_phi[sm], sh_phi[s0], sh_phi[sp]}};
       HRing3<R, SX, PL> hv{{sh_h[sm], sh_h[s0], sh_h[sp]}};
-      if (xy_inner && z >= 1 && z <= nz - 2)
-        collide_push_3d<T, R, FLOW, true, CHM>(m, x, y, z, tx + 1, ty + 1, f, g, h,
-                                               sh_phi[s0][o], dphi_prev, pv, hv, dst, ring_cur,
-                                               err);
+      // the encoding references of the three planes; uref_own's plane c
+      // receives the node's new U (its own value was read above)
+      UView3<REL, SX> uh{{sh_u[REL ? sm : 0], sh_u[REL ? s0 : 0], sh_u[REL ? sp : 0]},
+                         const_cast<__half*>(uref_own), uown};
+      if (!solids && xy_inner && z >= 1 && z <= nz - 2)
+        collide_push_3d<T, R, FLOW, true, CHM, false>(m, x, y, z, tx + 1, ty + 1, f, g, h,
+                                                      sh_phi[s0][o], dphi_prev, pv, hv, dst,
+                                                      ring_cur, err, false, uh);
       else
-        collide_push_3d<T, R, FLOW, false, CHM>(m, x, y, z, tx + 1, ty + 1, f, g, h,
-                                                sh_phi[s0][o], dphi_prev, pv, hv, dst, ring_cur,
-                                                err);
+        collide_push_3d<T, R, FLOW, false, CHM, MASK>(m, x, y, z, tx + 1, ty + 1, f, g, h,
+                                                      sh_phi[s0][o], dphi_prev, pv, hv, dst,
+                                                      ring_cur, err, solids, uh);
     }
   }
 }
@@ -211,18 +244,40 @@ __global__ void __launch_bounds__(TX* TY, MINB)
 #define LBPF_3D_MINB 4
 #endif
 
+constexpr int k3TX = 32, k3TY = LBPF_3D_TY, k3ZC = LBPF_3D_ZC;
+
 template <typename T, bool FLOW>
-cudaError_t launch3_march_t(const Model& m, const void* src, void* dst, const void* ring_prev,
-                            void* ring_cur, unsigned* err, cudaStream_t s) {
-  constexpr int TX = 32, TY = LBPF_3D_TY;
-  const int zc = LBPF_3D_ZC;
+cudaError_t launch3_march_t(const Model& m, int c, const void* src, void* dst,
+                            const void* ring_prev, void* ring_cur, unsigned* err,
+                            cudaStream_t s) {
+  if (sizeof(T) == 2 && !m.uring) return cudaErrorInvalidValue;
+  constexpr int TX = k3TX, TY = k3TY;
+  const int zc = k3ZC;
   dim3 grid((m.nx + TX - 1) / TX, (m.ny + TY - 1) / TY, (m.nz + zc - 1) / zc);
-  auto kern = FLOW && m.chm ? step3d_march_kernel<T, FLOW, FLOW, TX, TY, LBPF_3D_MINB>
-                            : step3d_march_kernel<T, FLOW, false, TX, TY, LBPF_3D_MINB>;
+  auto kern =
+      m.solid ? (FLOW && m.chm ? step3d_march_kernel<T, FLOW, FLOW, TX, TY, LBPF_3D_MINB, true>
+                               : step3d_march_kernel<T, FLOW, false, TX, TY, LBPF_3D_MINB, true>)
+              : (FLOW && m.chm ? step3d_march_kernel<T, FLOW, FLOW, TX, TY, LBPF_3D_MINB, false>
+                               : step3d_march_kernel<T, FLOW, false, TX, TY, LBPF_3D_MINB, false>);
   kern<<<grid, TX * TY, 0, s>>>(m, static_cast<const T*>(src), static_cast<T*>(dst),
                                 static_cast<const float*>(ring_prev),
-                                static_cast<float*>(ring_cur), err, zc);
+                                static_cast<float*>(ring_cur), err, zc, c);
   return cudaGetLastError();
+}
+
+// one thread per column chunk of the z-marching kernel: does the chunk or its
+// one-node halo (mapped like the gradient stencil) hold a solid node?
+__global__ void solid_chunks_kernel(const Model m, unsigned char* flags, int ntx, int nty,
+                                    int nzc) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= ntx * nty * nzc) return;
+  const int x0 = (t % ntx) * k3TX, y0 = ((t / ntx) % nty) * k3TY, z0 = (t / (ntx * nty)) * k3ZC;
+  bool any = false;
+  for (int lz = -1; lz <= k3ZC && !any; ++lz)
+    for (int ly = -1; ly <= k3TY && !any; ++ly)
+      for (int lx = -1; lx <= k3TX && !any; ++lx)
+        any = solid_mapped3(m, x0 + lx, y0 + ly, z0 + lz);
+  flags[t] = any ? 1 : 0;
 }
 
 // ---- host side -------------------------------------------------------------------
@@ -241,26 +296,40 @@ cudaError_t launch3_plain_t(const Model& m, const void* src, void* dst, const vo
 
 }  // namespace
 
+size_t solid_chunk_count(const Model& m) {
+  return size_t((m.nx + k3TX - 1) / k3TX) * size_t((m.ny + k3TY - 1) / k3TY) *
+         size_t((m.nz + k3ZC - 1) / k3ZC);
+}
+
+cudaError_t launch_solid_chunks(const Model& m, unsigned char* flags, cudaStream_t s) {
+  if (m.dim != 3 || !m.solid) return cudaErrorInvalidValue;
+  const int ntx = (m.nx + k3TX - 1) / k3TX, nty = (m.ny + k3TY - 1) / k3TY,
+            nzc = (m.nz + k3ZC - 1) / k3ZC;
+  const int n = ntx * nty * nzc;
+  solid_chunks_kernel<<<(n + 127) / 128, 128, 0, s>>>(m, flags, ntx, nty, nzc);
+  return cudaGetLastError();
+}
+
 cudaError_t prepare_step3d(const Model&, void* const[2], void* const[2], StepMaps* out) {
   out->ready = 0;  // the 3D kernel needs no tensor maps
   return cudaSuccess;
 }
 
-cudaError_t launch_step3d(const Model& m, const StepMaps&, int, const void* src, void* dst,
+cudaError_t launch_step3d(const Model& m, const StepMaps&, int c, const void* src, void* dst,
                           const void* ring_prev, void* ring_cur, unsigned* err, cudaStream_t s) {
   switch (m.storage) {
     case ST_FP64:
       return m.flow ? launch3_plain_t<double, double, true>(m, src, dst, ring_prev, ring_cur, err, s)
                     : launch3_plain_t<double, double, false>(m, src, dst, ring_prev, ring_cur, err, s);
     case ST_FP16:
-      return m.flow ? launch3_march_t<__half, true>(m, src, dst, ring_prev, ring_cur, err, s)
-                    : launch3_march_t<__half, false>(m, src, dst, ring_prev, ring_cur, err, s);
+      return m.flow ? launch3_march_t<__half, true>(m, c, src, dst, ring_prev, ring_cur, err, s)
+                    : launch3_march_t<__half, false>(m, c, src, dst, ring_prev, ring_cur, err, s);
     case ST_BF16:
-      return m.flow ? launch3_march_t<__nv_bfloat16, true>(m, src, dst, ring_prev, ring_cur, err, s)
-                    : launch3_march_t<__nv_bfloat16, false>(m, src, dst, ring_prev, ring_cur, err, s);
+      return m.flow ? launch3_march_t<__nv_bfloat16, true>(m, c, src, dst, ring_prev, ring_cur, err, s)
+                    : launch3_march_t<__nv_bfloat16, false>(m, c, src, dst, ring_prev, ring_cur, err, s);
     default:
-      return m.flow ? launch3_march_t<float, true>(m, src, dst, ring_prev, ring_cur, err, s)
-                    : launch3_march_t<float, false>(m, src, dst, ring_prev, ring_cur, err, s);
+      return m.flow ? launch3_march_t<float, true>(m, c, src, dst, ring_prev, ring_cur, err, s)
+                    : launch3_march_t<float, false>(m, c, src, dst, ring_prev, ring_cur, err, s);
   }
 }
 

@@ -189,17 +189,49 @@ __device__ __forceinline__ void chm_post_3d(const R (&d)[19], R drho, R rho, con
   }
 }
 
+// The per-node g reference around a node (3D, 16-bit storage), as UView of
+// the 2D step: `own` the reference of the node's own populations, at(dz, ly,
+// lx) the encoding reference of the node at plane offset dz and local (ly,
+// lx) (three halo-extended planes of row pitch ROW), `out` the plane that
+// receives each node's new U.  REL = false: every member unused.
+template <bool REL, int ROW>
+struct UView3 {
+  static constexpr bool kRel = REL;
+  const __half* p[3];
+  __half* out;
+  float own;
+  __device__ __forceinline__ float at(int dz, int ly, int lx) const {
+    return REL ? __half2float(p[dz + 1][ly * ROW + lx]) : 0.f;
+  }
+};
+using NoUView3 = UView3<false, 1>;
+
+// Solid nodes (3D mask): is the node at (x, y, z), mapped like a gradient
+// neighbour (periodic wrap, else nearest node), solid?
+__device__ __forceinline__ bool solid_mapped3(const Model& m, int x, int y, int z) {
+  x = grad_coord(x, m.nx, m.bc[0]);
+  y = grad_coord(y, m.ny, m.bc[1]);
+  z = grad_coord(z, m.nz, m.bc[2]);
+  return m.solid[(size_t(z) * m.ny + y) * m.px + x] != 0;
+}
+
 // pv: phi + 1 around the node, hv: the h deviations around it (views above).
 // INTERIOR: every node of the tile is at least one node away from every
 // domain face, so every destination is an ordinary node.  CHM: the flow
-// collides by the central Hermite MRT.
-template <typename T, typename R, bool FLOW, bool INTERIOR, bool CHM, typename PV, typename HV>
+// collides by the central Hermite MRT.  MASK: the code for solid nodes is
+// compiled in; `solids` (the tile or column chunk holds or borders a solid
+// node) switches it on: a solid gradient neighbour counts as the first fluid
+// node among the single-axis steps of its direction (x, y, z order) and the
+// node itself, and a push towards a solid node comes back reversed.
+template <typename T, typename R, bool FLOW, bool INTERIOR, bool CHM, bool MASK = false,
+          typename PV, typename HV, typename UV = NoUView3>
 __device__ __forceinline__ void collide_push_3d(const Model& m, int x, int y, int z, int lx,
                                                 int ly, const R (&f)[19], const R (&g)[7],
                                                 const R (&h)[7], R dphi, R dphi_prev,
                                                 const PV& pv, const HV& hs,
                                                 T* __restrict__ dst, R* __restrict__ ring_cur,
-                                                unsigned* __restrict__ err) {
+                                                unsigned* __restrict__ err,
+                                                bool solids = false, const UV& uh = UV()) {
   constexpr int QF = FLOW ? 19 : 0;
   const int nx = m.nx, ny = m.ny, nz = m.nz, px = m.px;
   const int P = int(m.plane);  // fits: checked at creation
@@ -213,7 +245,10 @@ __device__ __forceinline__ void collide_push_3d(const Model& m, int x, int y, in
   R dU = R(0);
 #pragma unroll
   for (int a = 0; a < 7; ++a) dU += g[a];
-  const R U = c.ref_g + dU;
+  // g deviations are taken from w_a Rg; the collision (Eqs. 13-16) is linear
+  // in them, so any per-node Rg gives the same populations
+  const R Rg = UV::kRel ? R(uh.own) : c.ref_g;
+  const R U = Rg + dU;
   R drho = R(0), mo[3] = {R(0), R(0), R(0)};
   if (FLOW) {
 #pragma unroll
@@ -243,13 +278,27 @@ __device__ __forceinline__ void collide_push_3d(const Model& m, int x, int y, in
   const R omega_U = rcp_r(R(0.5) + c.tauU_slope * mask);  // Eq. 18
   const R dphidt = dphi - dphi_prev;
   ring_cur[idx] = dphi;
+  if (UV::kRel) uh.out[idx] = __float2half_rn(float(U));
   if (!(finite_r(phi) && finite_r(U) && finite_r(rho))) atomicOr(err, 1u);
+  // a g deviation pushed to the node at (dz, dly, dlx), taken from its
+  // reference there instead of this node's
+  auto genc = [&](R v, R w, int dz, int dly, int dlx) -> R {
+    return UV::kRel ? fma_r(-w, R(uh.at(dz, dly, dlx)) - Rg, v) : v;
+  };
 
   // ---- grad = 3 sum_a w_a c_a phi(x + c_a) over D3Q19 ---------------------------
   R gr[3] = {R(0), R(0), R(0)};
 #pragma unroll
   for (int a = 1; a < 19; ++a) {
-    const R v = pv.at(D3_CZ[a], ly + D3_CY[a], lx + D3_CX[a]) * (a < 7 ? R(1.0 / 6.0) : R(1.0 / 12.0));
+    const int gcx = D3_CX[a], gcy = D3_CY[a], gcz = D3_CZ[a];
+    R pn = pv.at(gcz, ly + gcy, lx + gcx);
+    if (MASK && !INTERIOR && solids && solid_mapped3(m, x + gcx, y + gcy, z + gcz)) {
+      if (gcx != 0 && !solid_mapped3(m, x + gcx, y, z)) pn = pv.at(0, ly, lx + gcx);
+      else if (gcy != 0 && !solid_mapped3(m, x, y + gcy, z)) pn = pv.at(0, ly + gcy, lx);
+      else if (gcz != 0 && !solid_mapped3(m, x, y, z + gcz)) pn = pv.at(gcz, ly, lx);
+      else pn = pv.at(0, ly, lx);
+    }
+    const R v = pn * (a < 7 ? R(1.0 / 6.0) : R(1.0 / 12.0));
     if (D3_CX[a]) gr[0] += R(D3_CX[a]) * v;
     if (D3_CY[a]) gr[1] += R(D3_CY[a]) * v;
     if (D3_CZ[a]) gr[2] += R(D3_CZ[a]) * v;
@@ -303,7 +352,7 @@ __device__ __forceinline__ void collide_push_3d(const Model& m, int x, int y, in
       if (FLOW) Pop<T>::st(pd + (a * P + off), fp);
       if (sc) {
         const R hold = hs.at(a, cz, ly + cy, lx + cx);
-        Pop<T>::st(pd + ((QF + a) * P + off), gp);
+        Pop<T>::st(pd + ((QF + a) * P + off), genc(gp, d3q7_w<R>(a), cz, ly + cy, lx + cx));
         Pop<T>::st(pd + ((QF + 7 + a) * P + off), fma_r(inv_a2, hp, mul_r(keep_old, hold)));  // Eq. 19
       }
       continue;
@@ -323,12 +372,14 @@ __device__ __forceinline__ void collide_push_3d(const Model& m, int x, int y, in
       else if (bcx == BC_WALL) bounce = true;
       else drop = true;
     }
+    if (MASK && solids && !bounce && !drop && m.solid[zd * slab + yd * px + xd])
+      bounce = true;  // obstacle
     if (bounce) {
       // half-way bounce-back: comes back to this node reversed
       const int b = D3_OPP[a];
       if (FLOW) Pop<T>::st(dst + (b * P + idx), fp);
       if (sc) {
-        Pop<T>::st(dst + ((QF + b) * P + idx), gp);
+        Pop<T>::st(dst + ((QF + b) * P + idx), genc(gp, d3q7_w<R>(a), 0, ly, lx));
         Pop<T>::st(dst + ((QF + 7 + b) * P + idx), fma_r(inv_a2, hp, mul_r(keep_old, h[b])));
       }
     } else if (!drop) {
@@ -336,7 +387,7 @@ __device__ __forceinline__ void collide_push_3d(const Model& m, int x, int y, in
       if (FLOW) Pop<T>::st(dst + (a * P + jd), fp);
       if (sc) {
         const R hold = hs.at(a, cz, ly + cy, lx + cx);
-        Pop<T>::st(dst + ((QF + a) * P + jd), gp);
+        Pop<T>::st(dst + ((QF + a) * P + jd), genc(gp, d3q7_w<R>(a), cz, ly + cy, lx + cx));
         Pop<T>::st(dst + ((QF + 7 + a) * P + jd), fma_r(inv_a2, hp, mul_r(keep_old, hold)));  // Eq. 19
       }
     }
@@ -358,7 +409,7 @@ __device__ __forceinline__ void collide_push_3d(const Model& m, int x, int y, in
           if (FLOW) Pop<T>::st(dst + (a * P + jo), fp);
           if (sc) {
             const R hold = hs.at(a, cz, ly + cy, lx);
-            Pop<T>::st(dst + ((QF + a) * P + jo), gp);
+            Pop<T>::st(dst + ((QF + a) * P + jo), genc(gp, d3q7_w<R>(a), cz, ly + cy, lx));
             Pop<T>::st(dst + ((QF + 7 + a) * P + jo), fma_r(inv_a2, hp, mul_r(keep_old, hold)));
           }
         }
@@ -376,7 +427,8 @@ __device__ __forceinline__ void collide_push_3d(const Model& m, int x, int y, in
           if (sc) {
             const R ws = d3q7_w<R>(a);
             const R gu = FLOW ? cui : R(0);
-            Pop<T>::st(dst + ((QF + a) * P + idx), ws * ((c.U_in - c.ref_g) + c.U_in * R(4) * gu));
+            Pop<T>::st(dst + ((QF + a) * P + idx),
+                       genc(ws * ((c.U_in - Rg) + c.U_in * R(4) * gu), ws, 0, ly, lx));
             Pop<T>::st(dst + ((QF + 7 + a) * P + idx), R(0));  // phi = -1: zero deviation
           }
         }

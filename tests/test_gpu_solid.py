@@ -191,8 +191,176 @@ def test_rejections(P, L):
     with pytest.raises(L.LbpfError) as e:
         a.set_solid(m)
     assert e.value.code == L.EINVAL
-    q = P.lib_sim(P.params(dim=3, nx=16, ny=16, nz=16, fold=0, eps=0.04), "fp32")
+    # 3D: the inlet and outlet columns (x = 0 and nx - 1 of every row) too
+    q = P.lib_sim(P.params(dim=3, nx=16, ny=16, nz=16, fold=0, eps=0.04, flow=1,
+                           bc=(1, 0, 0), u_in=0.005, U_in=0.3), "fp32")
+    m3 = np.zeros((16, 16, 16), np.uint8)
+    m3[9, 3, 15] = 1
     with pytest.raises(L.LbpfError) as e:
-        q.set_solid(np.zeros(16 ** 3, np.uint8))
+        q.set_solid(m3)
+    assert e.value.code == L.EINVAL
+    with pytest.raises(L.LbpfError) as e:  # a mask of the wrong size
+        q.set_solid(np.zeros(16 ** 2, np.uint8))
     assert e.value.code == L.EINVAL
     a.set_solid(None)  # removing a mask that is not there is fine
+
+
+# ---- 3D: D3Q19 flow, D3Q7 solute and phase field, the z-marching kernel ------
+F3 = ("phi", "U", "rho", "ux", "uy", "uz")
+
+
+def obstacles3(nx, ny, nz):
+    """A baffle plate across the inflow, a block, and a bar across the
+    periodic wrap in y and z (the solid nodes of Sec. 3.1.2 / 3.2 in 3D)."""
+    m = np.zeros((nz, ny, nx), np.uint8)
+    m[4:nz - 6, 6:ny - 10, 9:11] = 1       # plate normal to x
+    m[nz // 2:nz // 2 + 3, 2:5, 30:33] = 1  # block
+    m[0:2, ny - 2:ny, 20:24] = 1            # bar in the corner of the wrap
+    m[nz - 1, 0, 25] = 1                    # ... and its other side
+    return m
+
+
+@pytest.mark.parametrize("storage,tol", [("fp64", TOL64), ("fp32", TOL32)])
+@pytest.mark.parametrize("collision", ["bgk", "chm"])
+def test_3d_obstacles_in_the_inflow_match_oracle(P, L, storage, tol, collision):
+    # sizes off the 32 x 4 column and the 8-plane chunk, obstacles in edge
+    # columns and chunks and across the wrap
+    nx, ny, nz = 44, 26, 21
+    p = P.params(dim=3, nx=nx, ny=ny, nz=nz, flow=1, fold=0, eps=0.04, bc=(1, 0, 0),
+                 u_in=0.005, U_in=0.45)
+    mask = obstacles3(nx, ny, nz)
+    seed = (24.0, 13.0, 10.0, 5.0, 0.45, 0.01, 3)
+    if collision == "chm":
+        import oracle
+        a = L.Sim(dim=3, nx=nx, ny=ny, nz=nz, bc=(1, 0, 0), flow=1, storage=P.STORAGE[storage],
+                  fold=0, eps_aniso=0.04, u_inlet=0.005, u0_inlet=0.45, collision=L.COLL_CHM)
+        b = oracle.Oracle(oracle.Params(dim=3, nx=nx, ny=ny, nz=nz, bc=(1, 0, 0), flow=1,
+                                        fold=0, eps=0.04, u_inlet=0.005, u0_inlet=0.45,
+                                        collision=1))
+    else:
+        a, b = P.lib_sim(p, storage), P.oracle_sim(p)
+    a.set_solid(mask)
+    b.set_solid(mask)
+    a.init_seed(*seed)
+    b.init_seed(*seed)
+    a.step(80)
+    b.step(80, P.THREADS)
+    errs = P.max_errors(a, b, F3)
+    assert max(errs.values()) < tol, errs
+    pa, pb = P.decode_pops(a), {k: b.pops(k) for k in "fgh"}
+    for k in "fgh":
+        assert np.abs(pa[k] - pb[k]).max() < tol, k
+    f = a.fields(("uy", "uz"))
+    assert np.abs(f["uy"]).max() > 1e-5  # deflected by the obstacles
+
+
+def test_3d_walls_with_flow_and_a_crystal_on_a_ragged_grid(P, L):
+    # walls in y and z, a periodic x, a body force, a crystal touching an
+    # obstacle; FP64 to the oracle
+    nx, ny, nz = 37, 19, 27
+    p = P.params(dim=3, nx=nx, ny=ny, nz=nz, flow=1, fold=0, eps=0.04, bc=(0, 2, 2),
+                 body=(3e-6, 0.0, 1e-6))
+    m = np.zeros((nz, ny, nx), np.uint8)
+    m[10:14, 0:4, 15:19] = 1
+    m[20:27, 12:15, 2:4] = 1
+    m[5, 9, 0] = m[5, 9, nx - 1] = 1  # across the periodic wrap in x
+    f = P.seeded_fields(p, seed=21, radius=5.0, u0=0.4, amp_u=0.003)
+    a, b = P.lib_sim(p, "fp64"), P.oracle_sim(p)
+    a.set_solid(m)
+    b.set_solid(m)
+    a.init_fields(f[0], f[1], f[2], *f[3])
+    b.init_fields(f[0], f[1], f[2], *f[3])
+    a.step(60)
+    b.step(60, P.THREADS)
+    errs = P.max_errors(a, b, F3)
+    assert max(errs.values()) < TOL64, errs
+
+
+def test_3d_solid_planes_reproduce_the_domain_walls(P, L):
+    # planes of solid nodes at y = 0 and y = ny + 1 of a periodic domain act
+    # as the walls of LBPF_BC_WALL in y (bounce-back of f, g, h and the
+    # gradient's nearest-node copy), with a crystal touching the wall
+    nx, ny, nz = 36, 22, 18
+    kw = dict(dim=3, nx=nx, nz=nz, flow=1, fold=0, eps=0.04, body=(2e-6, 0.0, 0.0))
+    pw = P.params(ny=ny, bc=(0, 2, 0), **kw)
+    pm = P.params(ny=ny + 2, bc=(0, 0, 0), **kw)
+    rng = np.random.default_rng(4)
+    z, y, x = np.mgrid[0:nz, 0:ny, 0:nx].astype(float)
+    phi = np.tanh((6.0 - np.sqrt((x - 17.2) ** 2 + (y - 2.4) ** 2 + (z - 9.1) ** 2))
+                  / (math.sqrt(2) * 2.0))
+    phi += 0.01 * rng.uniform(-1, 1, phi.shape)
+    U = 0.35 + 0.01 * rng.uniform(-1, 1, phi.shape)
+    pad = lambda f, v: np.concatenate([np.full((nz, 1, nx), v), f, np.full((nz, 1, nx), v)],
+                                      axis=1)
+    for storage, tol in (("fp64", 1e-12), ("fp32", 1e-6)):
+        a = P.lib_sim(pw, storage)
+        a.init_fields(phi, U)
+        b = P.lib_sim(pm, storage)
+        m = np.zeros((nz, ny + 2, nx), np.uint8)
+        m[:, 0] = m[:, -1] = 1
+        b.set_solid(m)
+        b.init_fields(pad(phi, -1.0), pad(U, 0.35))
+        a.step(120)
+        b.step(120)
+        fa, fb = a.fields(F3), b.fields(F3)
+        for k in F3:
+            assert np.abs(fa[k] - fb[k][:, 1:-1]).max() < tol, (storage, k)
+
+
+@pytest.mark.parametrize("storage", ["fp16", "bf16"])
+def test_3d_16bit_storage_with_obstacles(P, L, storage):
+    nx, ny, nz = 48, 40, 32
+    p = P.params(dim=3, nx=nx, ny=ny, nz=nz, flow=1, fold=0, eps=0.04, bc=(1, 0, 0),
+                 u_in=0.005, U_in=0.3)
+    mask = obstacles3(nx, ny, nz)
+    a, b = P.lib_sim(p, storage), P.oracle_sim(p)
+    a.set_solid(mask)
+    b.set_solid(mask)
+    seed = (26.0, 20.0, 16.0, 7.0, 0.3, 0.01, 1)
+    a.init_seed(*seed)
+    b.init_seed(*seed)
+    s0 = a.fields(F3)
+    a.step(100)
+    b.step(100, P.THREADS)
+    errs = P.max_errors(a, b, F3)
+    # the 3D storage bounds of the plain problem (test_gpu_chm, test_gpu_precision)
+    bounds = dict(phi=2e-3, U=3e-3, rho=1.3e-5, ux=1e-5, uy=6e-6, uz=6e-6) if storage == "fp16" \
+        else dict(phi=0.04, U=0.025, rho=1e-4, ux=8e-5, uy=5e-5, uz=5e-5)
+    for k, bound in bounds.items():
+        assert errs[k] < bound, (k, errs)
+    s1 = a.fields(F3)
+    sel = mask.astype(bool)
+    for k in ("phi", "U", "rho"):  # the solid nodes kept their state
+        assert np.array_equal(s1[k][sel], s0[k][sel]), k
+
+
+def test_3d_graph_restart_and_mask_removal(P, L):
+    nx, ny, nz = 40, 24, 20
+    p = P.params(dim=3, nx=nx, ny=ny, nz=nz, flow=1, fold=0, eps=0.04, bc=(1, 0, 0),
+                 u_in=0.005, U_in=0.4)
+    mask = obstacles3(nx, ny, nz)
+    seed = (22.0, 12.0, 10.0, 5.0, 0.4, 0.01, 6)
+    one = P.lib_sim(p, "fp32")
+    one.set_solid(mask)
+    one.init_seed(*seed)
+    for _ in range(70):
+        one.step(1)  # launch by launch
+    g = P.lib_sim(p, "fp32")
+    g.set_solid(mask)
+    g.init_seed(*seed)
+    g.step(70)  # graphs
+    assert np.array_equal(one.state(), g.state())
+    r = P.lib_sim(p, "fp32")
+    r.set_solid(mask)
+    r.load_state(g.state())
+    g.step(30)
+    r.step(30)
+    assert np.array_equal(g.state(), r.state())
+    # removing the mask: the plain kernel continues from the same state
+    free = P.lib_sim(p, "fp32")
+    free.load_state(g.state())
+    g.set_solid(None)
+    g.step(20)
+    free.step(20)
+    assert np.array_equal(g.state(), free.state())
+
