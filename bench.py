@@ -132,13 +132,14 @@ WORKLOADS = {
                     "body-force Poiseuille flow u_max~U[0,0.01], U0~U[0.25,0.45], R~U[6,16], "
                     "fold 4 or 5, eps~U[0.02,0.05]): BF16 U-Net 32/64/128/256 channels trained "
                     "on the GPU on 2000 LB pairs from 50 sampled problems (mirror "
-                    "augmentation, 4000 Adam steps), 200-step blocks, LB "
-                    "judge every 8th block, fallback at drift > 1e-3 or interface error > 1 lu; "
-                    "held-out problem; FP32 LB",
+                    "augmentation, 4000 Adam steps), blocks of 50 LB steps (and 200 beside "
+                    "them), LB judge every 8th block, fallback at drift > 1e-3 or interface "
+                    "error > 1 lu; held-out problem; FP32 LB",
                dim=2, nx=512, ny=512, nz=1, flow=1, fold=5, eps=0.03, bc=(0, 2, 0), u_in=0.0,
                U_in=0.0, storage="fp32", kernel="conv3x3_tc_kernel", src=SRC_CONV,
-               surrogate=dict(block=200, judge_every=8, traj=50, t_end=20000, every=500,
-                              crop=256, train_steps=4000, batch=8, lr=5e-4, start=1000),
+               surrogate=dict(blocks=(50, 200), judge_every=8, traj=50, t_end=20000,
+                              every=500, crop=256, train_steps=4000, batch=8, lr=5e-4,
+                              start=1000),
                sample=dict(nx=256, ny=256, channel=True)),
     "c5net": dict(desc="the c5 network alone: BF16 U-Net 32/64/128/256 channels on a 512x512 "
                        "sample (4 -> 4 channels, random weights): forward passes, then "
@@ -194,8 +195,8 @@ def workload(name, rank: int = 0, world: int = 1):
     w["bytes_per_lup"] = 2 * q * ELEM[w["storage"]] + 2 * ring
     if w.get("baffle"):
         w["bytes_per_lup"] += 1  # the solid mask
-    if w["dim"] == 2 and ELEM[w["storage"]] == 2:
-        # the per-node g reference of 16-bit 2D storage (FP16): the node's own
+    if ELEM[w["storage"]] == 2:
+        # the per-node g reference of 16-bit storage (FP16): the node's own
         # read, its neighbours' encoding reference read, the new one written
         w["bytes_per_lup"] += 3 * 2
     w["nodes"] = w["nx"] * w["ny"] * w["nz"]
@@ -991,29 +992,20 @@ def run_network(args, w):
     net.close()
 
 
-def run_surrogate(args, w):
-    """c5: train the U-Net on LB trajectories, then time the block propagator
-    against the plain LB on a held-out problem (one GPU; replicas beyond)."""
+def surrogate_arm(args, w, nb, stream, dist, clk, rank):
+    """Train the network for blocks of nb LB steps (pairs from the LB, training
+    on the GPU) and time the block propagator against the plain LB over the
+    same LB-equivalent steps of a held-out problem.  Returns the arm's figures
+    and its inference network (closed by the caller)."""
     import numpy as np
     import torch
-
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    torch.cuda.set_device(local)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     import paper_2206_02145_gb300 as L
     from paper_2206_02145_gb300 import surrogate as S
     c = w["surrogate"]
-    nx, ny, nb = w["nx"], w["ny"], c["block"]
-    stream = torch.cuda.current_stream()
+    nx, ny = w["nx"], w["ny"]
     cfg = S.default_cfg(nb)
-
-    # --- setup (untimed): training pairs from the LB, training on the GPU -------
     t0 = time.perf_counter()
+    # pairs every `every` steps along each trajectory, the block nb apart
     X, T = S.generate_pairs(c["traj"], c["t_end"], c["every"], nx, ny, cfg, seed=100,
                             crop=c["crop"])
     t_data = time.perf_counter() - t0
@@ -1050,28 +1042,24 @@ def run_surrogate(args, w):
     K = max(1, args.steps // nb)
     steps = K * nb
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    with ClockSampler(local) as clk:
-        clk.wait_first()
-        torch.cuda.synchronize()
-        clk.mark_start()
-        ev0.record(stream)
-        rep = L.lbpf_surrogate_advance(a, net, pcfg, K)
-        ev1.record(stream)
-        torch.cuda.synchronize()
-        ms_s = ev0.elapsed_time(ev1)
-        ev0.record(stream)
-        b.step(steps)
-        ev1.record(stream)
-        torch.cuda.synchronize()
-        clk.mark_end()
-        ms_lb = ev0.elapsed_time(ev1)
+    torch.cuda.synchronize()
+    clk.mark_start()
+    ev0.record(stream)
+    rep = L.lbpf_surrogate_advance(a, net, pcfg, K)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms_s = ev0.elapsed_time(ev1)
+    ev0.record(stream)
+    b.step(steps)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clk.mark_end()
+    ms_lb = ev0.elapsed_time(ev1)
     ms_s, ms_lb = max_over_ranks([ms_s, ms_lb], dist)
     da, db = a.diagnostics(), b.diagnostics()
     grow_lb = db["iface_pos"][:4] - d0["iface_pos"][:4]
     grow_s = da["iface_pos"][:4] - d0["iface_pos"][:4]
-    nodes = nx * ny
-    value = nodes * world * steps / (ms_s * 1e-3) / 1e6
-    lb_value = nodes * world * steps / (ms_lb * 1e-3) / 1e6
+    rel = (grow_s - grow_lb) / np.where(np.abs(grow_lb) > 1e-9, np.abs(grow_lb), np.nan)
 
     # the same held-out run with the accumulated interface estimate bounded at
     # 1 lattice unit (the controller then hands the rest of the run to the LB)
@@ -1092,8 +1080,65 @@ def run_surrogate(args, w):
                 "iface_pos_error_lu": float(np.max(np.abs(dcb["iface_pos"][:4] -
                                                           db["iface_pos"][:4])))}
     cb.close()
+    b.close()
+    nodes = nx * ny * w.get("world", 1)
+    return {
+        "block_steps": nb, "steps": steps, "blocks": K, "ms": ms_s, "plain_lb_ms": ms_lb,
+        "value": nodes * steps / (ms_s * 1e-3) / 1e6,
+        "plain_lb_value": nodes * steps / (ms_lb * 1e-3) / 1e6,
+        "speedup_vs_plain_lb": ms_lb / ms_s, "report": rep,
+        "growth_lu": {"plain_lb": grow_lb.tolist(), "propagator": grow_s.tolist(),
+                      "rel_error": [None if not np.isfinite(x) else float(x) for x in rel]},
+        "growth_rel_err_max": float(np.nanmax(np.abs(rel))) if np.isfinite(rel).any() else None,
+        "iface_pos_error_lu": float(np.max(np.abs(da["iface_pos"][:4] - db["iface_pos"][:4]))),
+        "solute_drift_rel": da["solute_drift_rel"],
+        "with_accumulated_bound": budgeted,
+        "training": {"pairs": npairs, "steps": c["train_steps"], "batch": c["batch"],
+                     "band_rows": c["crop"], "data_s": round(t_data, 1),
+                     "train_s": round(t_train, 1), "loss": [round(x[1], 5) for x in hist],
+                     "held_out_mse": mse_net, "held_out_mse_no_network": mse_none,
+                     "held_out_ratio": mse_net / mse_none},
+        "held_out_problem": info,
+    }, net, a, pcfg, K
+
+
+def run_surrogate(args, w):
+    """c5: for each block length (the configured 50 LB steps first, then 200),
+    train the U-Net on LB trajectories and time the block propagator against
+    the plain LB on a held-out problem (one GPU; replicas beyond).  The line's
+    value is the configured block's; the other is reported beside it."""
+    import numpy as np
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import paper_2206_02145_gb300 as L
+    c = w["surrogate"]
+    nx, ny = w["nx"], w["ny"]
+    w = dict(w, world=world)
+    stream = torch.cuda.current_stream()
+    arms, keep = {}, None
+    with ClockSampler(local) as clk:
+        clk.wait_first()
+        for nb in c["blocks"]:
+            res, net, a, pcfg, K = surrogate_arm(args, w, nb, stream, dist, clk, rank)
+            arms[nb] = res
+            if keep is None:
+                keep = (net, a, pcfg, K, nb)
+            else:
+                net.close()
+                a.close()
+    net, a, pcfg, K, nb = keep
+    head = arms[nb]
 
     # the network forward alone: the tensor-core part of the path
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     xs = torch.zeros(ny, nx, 4, device="cuda")
     ys = torch.empty_like(xs)
     for _ in range(3):
@@ -1112,6 +1157,7 @@ def run_surrogate(args, w):
     # --- end to end through the C ABI with host buffers ---------------------------
     # per call: the state from pinned host memory (lbpf_write_state), Ke blocks
     # of the propagator, phi and U back to pinned host memory
+    nodes = nx * ny
     hs = torch.from_numpy(a.state()).pin_memory()
     ho = torch.empty(2 * nodes, dtype=torch.float32).pin_memory()
     Ke = min(K, 10)
@@ -1134,37 +1180,36 @@ def run_surrogate(args, w):
             cpu = {"value": v, "unit": "MLUPS", "cores": threads, "kind": "oracle",
                    "sample": f"{osteps} LB steps of a 256x256 closed channel of the same family "
                              f"({n} nodes), {dt:.1f} s, FP64"}
+        rep = head["report"]
         launches = (K + 1) * 31 + rep["surrogate_blocks"] * 2 + (
             rep["judged_blocks"] + rep["fallback_blocks"]) * nb
-        rel = (grow_s - grow_lb) / np.where(np.abs(grow_lb) > 1e-9, np.abs(grow_lb), np.nan)
         out = {
-            "metric": "LB-equivalent MLUPS (learned block propagator)", "value": value,
-            "unit": "MLUPS", "n_gpus": world, "steps": steps, "warmup": nb,
-            "ms_per_step": ms_s / steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "bf16 network, f32 LB", "data": "synthetic "
-            "(seeded channel problems; the network's training pairs come from this LB)",
+            "metric": "LB-equivalent MLUPS (learned block propagator)", "value": head["value"],
+            "unit": "MLUPS", "n_gpus": world, "steps": head["steps"], "warmup": nb,
+            "ms_per_step": head["ms"] / head["steps"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "bf16 network, f32 LB",
+            "data": "synthetic (seeded channel problems; the network's training pairs come "
+                    "from this LB)",
             "config": {"workload": w["desc"], "grid": [nx, ny, 1], "block_steps": nb,
-                       "judge_every": c["judge_every"], "pairs": npairs,
-                       "training": {"steps": c["train_steps"], "batch": c["batch"],
-                                    "band_rows": c["crop"], "data_s": round(t_data, 1),
-                                    "train_s": round(t_train, 1),
-                                    "loss": [round(x[1], 5) for x in hist],
-                                    "held_out_mse": mse_net, "held_out_mse_no_network": mse_none,
-                                    "held_out_ratio": mse_net / mse_none},
-                       "held_out_problem": info,
+                       "judge_every": c["judge_every"], "training": head["training"],
+                       "held_out_problem": head["held_out_problem"],
                        "l2": "network activations of a 512x512 sample exceed L2 at level 0 "
                              "only partly; the LB state (59 MB) fits in L2: both arms time the "
                              "same K blocks back to back",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
-            "plain_lb": {"value": lb_value, "unit": "MLUPS", "ms": ms_lb},
-            "speedup_vs_plain_lb": ms_lb / ms_s,
+            "plain_lb": {"value": head["plain_lb_value"], "unit": "MLUPS",
+                         "ms": head["plain_lb_ms"]},
+            "speedup_vs_plain_lb": head["speedup_vs_plain_lb"],
             "report": rep,
-            "growth_lu": {"plain_lb": grow_lb.tolist(), "propagator": grow_s.tolist(),
-                          "rel_error": [None if not np.isfinite(x) else float(x) for x in rel]},
-            "iface_pos_error_lu": float(np.max(np.abs(da["iface_pos"][:4] -
-                                                      db["iface_pos"][:4]))),
-            "solute_drift_rel": da["solute_drift_rel"],
-            "with_accumulated_bound": budgeted,
+            "growth_lu": head["growth_lu"],
+            "growth_rel_err_max": head["growth_rel_err_max"],
+            "iface_pos_error_lu": head["iface_pos_error_lu"],
+            "solute_drift_rel": head["solute_drift_rel"],
+            "with_accumulated_bound": head["with_accumulated_bound"],
+            "block_lengths": {str(k): {kk: v for kk, v in r.items()
+                                       if kk not in ("training", "held_out_problem")}
+                              | {"held_out_ratio": r["training"]["held_out_ratio"]}
+                              for k, r in arms.items()},
             "roofline": {"bound": "tensor", "achieved": tflops, "peak": peak_tf,
                          "unit": "TFLOP/s", "frac": tflops / peak_tf, "peak_source": peak_kind,
                          "traffic": None, "kernel": "network forward (17 conv3x3_tc + 8 "
@@ -1178,11 +1223,10 @@ def run_surrogate(args, w):
             "clocks": clk.summary(),
         }
         print(json.dumps(out), flush=True)
-    for x in (a, b, net):
+    for x in (a, net):
         x.close()
     if dist is not None:
         dist.destroy_process_group()
-
 
 if __name__ == "__main__":
     main()

@@ -105,7 +105,7 @@ def decode_pops(sim, buf=None):
     qf = (9 if dim == 2 else 19) if flow else 0
     qs = 9 if dim == 2 else 7
     g_ref = u_ref
-    if dim == 2 and elem == 2:
+    if elem == 2:
         # per-node g reference: the first FP16 plane after the FP32 phi ring
         off = HDR + q * n * elem + n * 4
         g_ref = np.frombuffer(buf[off:off + 2 * n].tobytes(), dtype=np.float16)

@@ -114,3 +114,52 @@ def test_16bit_2d_state_carries_the_per_node_reference(P):
     pb = {k: b.pops(k) for k in "fgh"}
     for k, tol in (("f", 1e-4), ("g", 5e-3), ("h", 1e-2)):
         assert np.abs(pa[k] - pb[k]).max() < tol, (k, np.abs(pa[k] - pb[k]).max())
+
+
+# The same in 3D (C3-like problem at 96^3, cubic anisotropy, inflow): with
+# the per-node g reference the 16-bit interface stays with the FP64-storage
+# run along the six axis rays.
+LONG3 = dict(dim=3, nx=96, ny=96, nz=96, flow=1, fold=0, eps=0.04, bc=(1, 0, 0), u_in=0.005,
+             U_in=0.3)
+LONG3_SEED = (40.0, 48.0, 48.0, 10.0, 0.3, 0.01, 1)
+
+
+def test_16bit_3d_long_run_interface(P):
+    p = P.params(**LONG3)
+    steps = 4000
+    ref = P.lib_sim(p, "fp64")
+    ref.init_seed(*LONG3_SEED)
+    d0 = ref.diagnostics()["iface_pos"].copy()
+    ref.step(steps)
+    want = ref.diagnostics()["iface_pos"]
+    a = P.lib_sim(p, "fp16")
+    a.init_seed(*LONG3_SEED)
+    a.step(steps)
+    got = a.diagnostics()["iface_pos"]
+    assert np.abs(got - want).max() < 0.1, (got, want)
+    grown = want - d0
+    assert np.all(np.abs(grown) > 1.0), grown
+    assert np.abs((got - d0) / grown - 1.0).max() < 0.02, (got - d0, grown)
+
+
+def test_16bit_3d_state_carries_the_per_node_reference(P):
+    p = P.params(dim=3, nx=40, ny=36, nz=20, flow=1, fold=0, eps=0.04, bc=(1, 0, 0), u_in=0.005,
+                 U_in=0.45)
+    seed = (20.0, 18.0, 10.0, 6.0, 0.45, 0.01, 4)
+    a, b = P.pair(p, "fp16", seed_args=seed)
+    a.step(100)
+    b.step(100, P.THREADS)
+    pa = P.decode_pops(a)
+    U = a.fields(("U",))["U"]
+    assert np.abs(pa["g"].sum(axis=0) - U).max() < 1e-5
+    pb = {k: b.pops(k) for k in "fgh"}
+    for k, tol in (("f", 1e-4), ("g", 5e-3), ("h", 1e-2)):
+        assert np.abs(pa[k] - pb[k]).max() < tol, (k, np.abs(pa[k] - pb[k]).max())
+    # restart and launch by launch are bitwise
+    st = a.state()
+    a.step(70)
+    r = P.lib_sim(p, "fp16")
+    r.load_state(st)
+    for _ in range(70):
+        r.step(1)
+    assert np.array_equal(a.state(), r.state())
