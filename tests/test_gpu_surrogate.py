@@ -220,3 +220,51 @@ def test_rejects_unsupported_shapes(lib):
         lib.UNet(base_ch=48, height=64, width=64, levels=1)
     with pytest.raises(lib.LbpfError):
         lib.UNet(in_ch=17, height=64, width=64, levels=1)
+
+
+def _maxrel(a, b):
+    """Largest element-wise difference, relative to the tensor's largest
+    reference magnitude."""
+    return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-30))
+
+
+def test_configured_network_elementwise_at_full_size(lib):
+    # the propagator's network as configured (4 levels, 32/64/128/256
+    # channels, 4 -> 4, 512 x 512, batch 1) on the tcgen05 path: the same
+    # layer shapes, hence the same kernel variants (halo and row tiles, every
+    # channel chunk and tile width), as the propagator and the benchmark run
+    levels, h, w = 4, 512, 512
+    net = lib.UNet(in_ch=4, out_ch=4, base_ch=32, levels=levels, batch=1, height=h, width=w,
+                   seed=11, stream=lib.current_stream())
+    net.set_tensor_path(True)
+    ref = UNetRef(levels, 32, 4, 4, store=_bf16)
+    params = ref.unflatten(net.weights().astype(np.float64))
+    params = [_bf16(p) if p.ndim == 3 else p for p in params]
+    rng = np.random.default_rng(21)
+    x = rng.normal(size=(1, h, w, 4)).astype(np.float32)
+    t = rng.normal(size=(1, h, w, 4)).astype(np.float32)
+    xd, td = torch.from_numpy(x).cuda(), torch.from_numpy(t).cuda()
+    yd = torch.empty(1, h, w, 4, device="cuda")
+    net.forward(xd, yd)
+    torch.cuda.synchronize()
+    loss = net.grad(xd, td)
+    g_gpu = ref.unflatten(net.grads().astype(np.float64))
+    net.status()
+    net.close()
+    loss_ref, y_ref, g_ref = ref.loss_and_grads(_bf16(x), t.astype(np.float64), params)
+    y = yd.cpu().double().numpy()
+    # Both sides round every stored activation to bf16 (unit roundoff
+    # u = 2^-9); they differ by FP32 summation order, which flips the
+    # rounding of a few elements by one bf16 ulp per layer, and by the GPU's
+    # bf16 activation gradients.  The output passes 17 stored layers: bound
+    # 17 u on its largest element; a gradient passes at most 2 x 17 roundings
+    # on the way back: bound 34 u.  A wrong tap, channel or mask gives O(1).
+    u = 2.0 ** -9
+    e_y = _maxrel(y, y_ref)
+    e_g = [_maxrel(a, b) for a, b in zip(g_gpu, g_ref)]
+    print(f"output max-rel {e_y:.3e}; gradients max-rel "
+          + " ".join(f"{e:.2e}" for e in e_g))
+    assert e_y < 17 * u, e_y
+    assert loss == pytest.approx(loss_ref, rel=17 * u)
+    for i, e in enumerate(e_g):
+        assert e < 34 * u, (i, ref.shapes[i], e)
