@@ -163,6 +163,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int ksteps = 9 * a.nchunks;
   const int ntiles = (a.mtiles / G) * a.ntiles_n;  // a tile: G x 128 pixels x BN channels
+  pdl_trigger();
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < S; ++s) {
@@ -177,6 +178,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     fence_barrier_init();
   }
   if (warp == 1) tmem_alloc(&tmem_base, Sh::TCOLS);
+  pdl_wait();  // the previous kernel's outputs (and any weight update) are visible
   for (int i = threadIdx.x; i < a.Cout; i += blockDim.x) sbias[i] = a.bias ? a.bias[i] : 0.f;
   tc_fence_before();
   __syncthreads();
@@ -382,6 +384,14 @@ struct HaloArgs {
   const bf16* mask;
   bf16* y;
   unsigned* err;
+  // fused 1x1 head (null head_y: none): with one channel tile holding all
+  // Cout channels of a pixel, head_y[p][o] = head_b[o] + sum_c head_w[o][c]
+  // y[p][c] over the bf16 values stored, in channel order (the arithmetic of
+  // the separate head kernel, so the result is the same)
+  const float* head_w;
+  const float* head_b;
+  float* head_y;
+  int head_out;
 };
 
 template <int BK, int BN, int G>
@@ -394,9 +404,12 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   __shared__ __align__(8) uint64_t full[S], empty[S], acc_full[2], acc_empty[2], fin;
   __shared__ uint32_t tmem_base;
   __shared__ float sbias[256];
+  __shared__ float shead[8 * BN + 8];
   uint8_t* smem = smem_raw + ((1024u - (smem_addr(smem_raw) & 1023u)) & 1023u);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int ksteps = 3 * a.nchunks;
+  const bool head = a.head_y != nullptr;
+  pdl_trigger();
   if (threadIdx.x == 0) {
     for (int s = 0; s < S; ++s) {
       mbar_init(&full[s], 1);
@@ -410,7 +423,11 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     fence_barrier_init();
   }
   if (warp == 1) tmem_alloc(&tmem_base, Sh::TCOLS);
+  pdl_wait();  // the previous kernel's outputs (and any weight update) are visible
   for (int i = threadIdx.x; i < a.Cout; i += blockDim.x) sbias[i] = a.bias ? a.bias[i] : 0.f;
+  if (head)
+    for (int i = threadIdx.x; i < a.head_out * (BN + 1); i += blockDim.x)
+      shead[i] = i < a.head_out * BN ? a.head_w[i] : a.head_b[i - a.head_out * BN];
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -520,6 +537,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         const long long p = ((long long)img * a.H + h0 + g) * a.W + w0 + m;
         bf16* yrow = a.y + p * a.Cy + a.co_off + n0;
         const bf16* mrow = a.mask ? a.mask + p * a.Cy + a.co_off + n0 : nullptr;
+        float hacc[8];
+        if (head)
+#pragma unroll
+          for (int o = 0; o < 8; ++o) hacc[o] = o < a.head_out ? shead[a.head_out * BN + o] : 0.f;
 #pragma unroll 1
         for (int c = 0; c < BN; c += 32) {
           uint32_t r[32];
@@ -549,7 +570,24 @@ __global__ void __launch_bounds__(kTcThreads, 1)
           for (int v = 0; v < 4; ++v)
             reinterpret_cast<uint4*>(yrow + c)[v] =
                 make_uint4(out[4 * v], out[4 * v + 1], out[4 * v + 2], out[4 * v + 3]);
+          if (head) {
+#pragma unroll
+            for (int j = 0; j < 32; j += 2) {
+              const __nv_bfloat162 hv = *reinterpret_cast<const __nv_bfloat162*>(&out[j / 2]);
+              const float f0 = __low2float(hv), f1 = __high2float(hv);
+#pragma unroll
+              for (int o = 0; o < 8; ++o)
+                if (o < a.head_out) {
+                  hacc[o] = fmaf(f0, shead[o * BN + c + j], hacc[o]);
+                  hacc[o] = fmaf(f1, shead[o * BN + c + j + 1], hacc[o]);
+                }
+            }
+          }
         }
+        if (head)
+#pragma unroll
+          for (int o = 0; o < 8; ++o)
+            if (o < a.head_out) a.head_y[p * a.head_out + o] = hacc[o];
       }
       tc_fence_before();
       __syncwarp();
@@ -580,8 +618,8 @@ cudaError_t launch_halo(const CUtensorMap& mx, const CUtensorMap& mw, const Halo
       return e;
   }
   const unsigned grid = unsigned(t.ntiles < sms ? t.ntiles : sms);
-  conv3x3_tc_halo_kernel<BK, BN, G><<<grid, kTcThreads, Sh::SMEM, s>>>(mx, mw, t);
-  return cudaGetLastError();
+  return launch_pdl(conv3x3_tc_halo_kernel<BK, BN, G>, dim3(grid), dim3(kTcThreads), Sh::SMEM, s,
+                    mx, mw, t);
 }
 
 CUtensorMapSwizzle swizzle_for(int bk) {
@@ -606,8 +644,8 @@ cudaError_t launch_tc(const CUtensorMap& mx, const CUtensorMap& mw, const TcArgs
   // one CTA per SM: the ring fills the shared memory, the accumulators the TMEM
   const long long tiles = (long long)(t.mtiles / G) * t.ntiles_n;
   const unsigned grid = unsigned(tiles < sms ? tiles : sms);
-  conv3x3_tc_kernel<BK, BN, G><<<grid, kTcThreads, Sh::SMEM, s>>>(mx, mw, t);
-  return cudaGetLastError();
+  return launch_pdl(conv3x3_tc_kernel<BK, BN, G>, dim3(grid), dim3(kTcThreads), Sh::SMEM, s, mx,
+                    mw, t);
 }
 
 // G sub-tiles per tile (independent accumulators); the widest shapes stay
@@ -722,6 +760,14 @@ static cudaError_t conv3x3_tc_halo(const ConvArgs& a, unsigned* err, cudaStream_
   t.mask = a.mask;
   t.y = a.y;
   t.err = err;
+  // the head rides along when one tile holds every channel of a pixel
+  const bool fuse = a.head_y && BN == a.Cout && a.co_off == 0 && a.head_out >= 1 &&
+                    a.head_out <= 8 && !a.mask;
+  t.head_w = fuse ? a.head_w : nullptr;
+  t.head_b = fuse ? a.head_b : nullptr;
+  t.head_y = fuse ? a.head_y : nullptr;
+  t.head_out = fuse ? a.head_out : 0;
+  if (a.head_done) *a.head_done = fuse ? 1 : 0;
   *used = true;
   switch (BK) {
     case 64: return launch_halo_bk<64>(BN, G, mx, mw, t, s);

@@ -155,7 +155,10 @@ cudaError_t make_conv(lbpf_unet* n, ConvLayer* l, int cin, int cout, int real_ci
   return cudaMemcpy(l->wb, hb.data(), l->nw * 2, cudaMemcpyHostToDevice);
 }
 
-int conv_fwd(lbpf_unet* n, const ConvLayer& l, const Act& x, int xoff, const Act& y, int yoff) {
+// head: the 1x1 head to fuse into this layer's epilogue where the kernel can
+// (*head_done says whether it did)
+int conv_fwd(lbpf_unet* n, const ConvLayer& l, const Act& x, int xoff, const Act& y, int yoff,
+             int* head_done = nullptr) {
   lbk::nn::ConvArgs a{};
   a.x = x.p;
   a.Cx = x.c;
@@ -174,6 +177,13 @@ int conv_fwd(lbpf_unet* n, const ConvLayer& l, const Act& x, int xoff, const Act
   a.mask = nullptr;
   a.tensor_path = n->tensor_path;
   a.err = n->d_err;
+  if (head_done) {
+    a.head_w = n->hw;
+    a.head_b = n->hb;
+    a.head_y = n->y;
+    a.head_out = n->cfg.out_ch;
+    a.head_done = head_done;
+  }
   UCK(n, lbk::nn::conv3x3(a, n->stream));
   return LBPF_OK;
 }
@@ -247,17 +257,22 @@ int forward(lbpf_unet* n) {
     }
   }
   const Act* d = &n->bottom;
+  int head_done = 0;
   for (int l = L - 2; l >= 0; --l) {
     UCK(n, lbk::nn::upsample2(d->p, n->u[l].p, n->C[l + 1], n->cfg.batch, n->H[l], n->W[l],
                               n->stream));
     if ((rc = conv_fwd(n, n->up[l], n->u[l], 0, n->cat[l], 0))) return rc;
     if ((rc = conv_fwd(n, n->dec_a[l], n->cat[l], 0, n->da[l], 0))) return rc;
-    if ((rc = conv_fwd(n, n->dec_b[l], n->da[l], 0, n->db[l], 0))) return rc;
+    // the last convolution carries the 1x1 head in its epilogue where it can
+    if ((rc = conv_fwd(n, n->dec_b[l], n->da[l], 0, n->db[l], 0, l == 0 ? &head_done : nullptr)))
+      return rc;
     d = &n->db[l];
   }
-  const long long npix = (long long)n->cfg.batch * n->H[0] * n->W[0];
-  UCK(n, lbk::nn::head_fwd(L > 1 ? n->db[0].p : n->bottom.p, n->C[0], n->hw, n->hb, n->y,
-                           n->cfg.out_ch, npix, n->stream));
+  if (!head_done) {
+    const long long npix = (long long)n->cfg.batch * n->H[0] * n->W[0];
+    UCK(n, lbk::nn::head_fwd(L > 1 ? n->db[0].p : n->bottom.p, n->C[0], n->hw, n->hb, n->y,
+                             n->cfg.out_ch, npix, n->stream));
+  }
   return LBPF_OK;
 }
 
@@ -345,12 +360,24 @@ int adam_all(lbpf_unet* n, float lr) {
 
 // pack FP32 NHWC (in_ch <= 16) into the bf16 16-channel input buffer: one
 // pixel per thread, its 16 outputs written as two 16-byte stores
-__global__ void pack_input_kernel(const float* x, int cin, bf16* out, long long npix) {
+__global__ void pack_input_kernel(const float* x, int cin, int vec4, bf16* out, long long npix) {
+  lbk::nn::pdl_trigger();
+  lbk::nn::pdl_wait();
   for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < npix;
        p += (long long)gridDim.x * blockDim.x) {
     __align__(16) bf16 v[16];
+    if (vec4) {  // four 16-byte aligned channels (the propagator's phi, U, ux, uy)
+      const float4 f = reinterpret_cast<const float4*>(x)[p];
+      v[0] = __float2bfloat16(f.x);
+      v[1] = __float2bfloat16(f.y);
+      v[2] = __float2bfloat16(f.z);
+      v[3] = __float2bfloat16(f.w);
 #pragma unroll
-    for (int c = 0; c < 16; ++c) v[c] = __float2bfloat16(c < cin ? x[p * cin + c] : 0.f);
+      for (int c = 4; c < 16; ++c) v[c] = __float2bfloat16(0.f);
+    } else {
+#pragma unroll
+      for (int c = 0; c < 16; ++c) v[c] = __float2bfloat16(c < cin ? x[p * cin + c] : 0.f);
+    }
     uint4* o = reinterpret_cast<uint4*>(out + p * 16);
     o[0] = reinterpret_cast<const uint4*>(v)[0];
     o[1] = reinterpret_cast<const uint4*>(v)[1];
@@ -361,8 +388,10 @@ int pack_input(lbpf_unet* n, const float* x) {
   const long long npix = (long long)n->cfg.batch * n->H[0] * n->W[0];
   long long blocks = (npix + 255) / 256;
   if (blocks > 152 * 32) blocks = 152 * 32;
-  pack_input_kernel<<<int(blocks), 256, 0, n->stream>>>(x, n->cfg.in_ch, n->xin.p, npix);
-  UCK(n, cudaGetLastError());
+  // four channels are read as one float4 where x is 16-byte aligned
+  const int vec4 = n->cfg.in_ch == 4 && (reinterpret_cast<uintptr_t>(x) & 15u) == 0;
+  UCK(n, lbk::nn::launch_pdl(pack_input_kernel, dim3(unsigned(blocks)), dim3(256), 0, n->stream,
+                             x, n->cfg.in_ch, vec4, n->xin.p, npix));
   return LBPF_OK;
 }
 

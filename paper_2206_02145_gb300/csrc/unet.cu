@@ -270,6 +270,8 @@ __global__ void mask_kernel(bf16* g, int Cg, int goff, const bf16* act, int Ca, 
 // y[b][h/2][w/2][c] = mean of the 2x2 block of x
 __global__ void avgpool_kernel(const bf16* x, int Cx, int xoff, bf16* y, int Cy, int yoff, int C,
                                int B, int H, int W) {
+  pdl_trigger();
+  pdl_wait();
   const int Ho = H / 2, Wo = W / 2, groups = C / 8;
   const long long n = (long long)B * Ho * Wo * groups;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
@@ -318,6 +320,8 @@ __global__ void pool_bwd_add_mask_kernel(bf16* gs, const bf16* gp, const bf16* a
 
 // nearest 2x upsampling: each source pixel's 8 channels go to its 2x2 block
 __global__ void upsample_kernel(const bf16* x, bf16* y, int C, int B, int H, int W) {
+  pdl_trigger();
+  pdl_wait();
   const int Hs = H / 2, Ws = W / 2, groups = C / 8;
   const long long n = (long long)B * Hs * Ws * groups;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
@@ -370,6 +374,8 @@ template <int O>
 __global__ void head_fwd_kernel(const bf16* x, int C, const float* w, const float* b, float* y,
                                 long long npix) {
   __shared__ float sw[O * 256 + O];
+  pdl_trigger();
+  pdl_wait();
   for (int i = threadIdx.x; i < O * C; i += blockDim.x) sw[i] = w[i];
   if (threadIdx.x < O) sw[O * 256 + threadIdx.x] = b[threadIdx.x];
   __syncthreads();
@@ -495,6 +501,7 @@ int blocks_for(long long n) {
 }  // namespace
 
 cudaError_t conv3x3(const ConvArgs& a, cudaStream_t s) {
+  if (a.head_done) *a.head_done = 0;
   if (a.tensor_path && a.err && conv3x3_tc_supported(a)) return conv3x3_tc(a, a.err, s);
   if (a.W % 64 || a.Cin % 16 || a.Cx % 8 || a.Cy % 8 || a.ci_off % 8 || a.co_off % 8)
     return cudaErrorInvalidValue;
@@ -551,9 +558,8 @@ cudaError_t relu_mask(bf16* g, int Cg, int goff, const bf16* act, int Ca, int ao
 cudaError_t avgpool2(const bf16* x, int Cx, int xoff, bf16* y, int Cy, int yoff, int C, int B,
                      int H, int W, cudaStream_t s) {
   if (!v8(C) || !v8(Cx) || !v8(xoff) || !v8(Cy) || !v8(yoff)) return cudaErrorInvalidValue;
-  avgpool_kernel<<<blocks_for((long long)B * H * W * C / 32), 256, 0, s>>>(x, Cx, xoff, y, Cy,
-                                                                           yoff, C, B, H, W);
-  return cudaGetLastError();
+  return launch_pdl(avgpool_kernel, dim3(blocks_for((long long)B * H * W * C / 32)), dim3(256), 0,
+                    s, x, Cx, xoff, y, Cy, yoff, C, B, H, W);
 }
 cudaError_t avgpool2_bwd_add_mask(bf16* gs, const bf16* gp, const bf16* act, int Cs, int soff,
                                   int C, int B, int H, int W, cudaStream_t s) {
@@ -564,8 +570,8 @@ cudaError_t avgpool2_bwd_add_mask(bf16* gs, const bf16* gp, const bf16* act, int
 }
 cudaError_t upsample2(const bf16* x, bf16* y, int C, int B, int H, int W, cudaStream_t s) {
   if (!v8(C)) return cudaErrorInvalidValue;
-  upsample_kernel<<<blocks_for((long long)B * H * W * C / 32), 256, 0, s>>>(x, y, C, B, H, W);
-  return cudaGetLastError();
+  return launch_pdl(upsample_kernel, dim3(blocks_for((long long)B * H * W * C / 32)), dim3(256), 0,
+                    s, x, y, C, B, H, W);
 }
 cudaError_t upsample2_bwd_mask(const bf16* g, bf16* gx, const bf16* act, int C, int B, int H,
                                int W, cudaStream_t s) {
@@ -577,18 +583,17 @@ cudaError_t upsample2_bwd_mask(const bf16* g, bf16* gx, const bf16* act, int C, 
 cudaError_t head_fwd(const bf16* x, int C, const float* w, const float* b, float* y, int O,
                      long long npix, cudaStream_t s) {
   if (!v8(C) || O < 1 || O > 8 || C > 256) return cudaErrorInvalidValue;
-  const int g = blocks_for(npix);
+  const dim3 g(blocks_for(npix)), bl(256);
   switch (O) {
-    case 1: head_fwd_kernel<1><<<g, 256, 0, s>>>(x, C, w, b, y, npix); break;
-    case 2: head_fwd_kernel<2><<<g, 256, 0, s>>>(x, C, w, b, y, npix); break;
-    case 3: head_fwd_kernel<3><<<g, 256, 0, s>>>(x, C, w, b, y, npix); break;
-    case 4: head_fwd_kernel<4><<<g, 256, 0, s>>>(x, C, w, b, y, npix); break;
-    case 5: head_fwd_kernel<5><<<g, 256, 0, s>>>(x, C, w, b, y, npix); break;
-    case 6: head_fwd_kernel<6><<<g, 256, 0, s>>>(x, C, w, b, y, npix); break;
-    case 7: head_fwd_kernel<7><<<g, 256, 0, s>>>(x, C, w, b, y, npix); break;
-    default: head_fwd_kernel<8><<<g, 256, 0, s>>>(x, C, w, b, y, npix); break;
+    case 1: return launch_pdl(head_fwd_kernel<1>, g, bl, 0, s, x, C, w, b, y, npix);
+    case 2: return launch_pdl(head_fwd_kernel<2>, g, bl, 0, s, x, C, w, b, y, npix);
+    case 3: return launch_pdl(head_fwd_kernel<3>, g, bl, 0, s, x, C, w, b, y, npix);
+    case 4: return launch_pdl(head_fwd_kernel<4>, g, bl, 0, s, x, C, w, b, y, npix);
+    case 5: return launch_pdl(head_fwd_kernel<5>, g, bl, 0, s, x, C, w, b, y, npix);
+    case 6: return launch_pdl(head_fwd_kernel<6>, g, bl, 0, s, x, C, w, b, y, npix);
+    case 7: return launch_pdl(head_fwd_kernel<7>, g, bl, 0, s, x, C, w, b, y, npix);
+    default: return launch_pdl(head_fwd_kernel<8>, g, bl, 0, s, x, C, w, b, y, npix);
   }
-  return cudaGetLastError();
 }
 cudaError_t head_bwd(const bf16* x, int C, const float* w, const float* gy, int O, long long npix,
                      bf16* gx, float* dw, float* db, cudaStream_t s) {

@@ -11,6 +11,34 @@ namespace nn {
 
 using bf16 = __nv_bfloat16;
 
+// Programmatic dependent launch between the network's kernels: a kernel
+// launched by launch_pdl may be scheduled (and run its prologue: barrier
+// set-up, tensor-memory allocation) while the kernel before it on the stream
+// finishes.  Each such kernel signals pdl_trigger() at its start and calls
+// pdl_wait() before its first access to global memory; pdl_wait returns once
+// the kernel before it has completed and its writes are visible.  Without the
+// launch attribute both are no-ops.
+__device__ __forceinline__ void pdl_trigger() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                              cudaStream_t s, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
 struct ConvArgs {
   const bf16* x;   // [N][H][W][Cx], channels ci_off .. ci_off + Cin
   int Cx, ci_off, Cin;
@@ -23,6 +51,15 @@ struct ConvArgs {
   const bf16* mask;    // zero the output where mask <= 0 (same layout as y), or null
   int tensor_path;     // 1: tcgen05 kernel (conv_tc.cu) where the shape allows; 0: mma.sync
   unsigned* err;       // device word: bit 2 set if a tcgen05 kernel timed out waiting
+  // optional 1x1 head on the output (head_y null: none), computed in the
+  // convolution's epilogue where its tiling allows (*head_done = 1), else
+  // left to the caller (*head_done = 0): head_y [N][H][W][head_out] FP32,
+  // head_w [head_out][Cout], head_b [head_out]
+  const float* head_w;
+  const float* head_b;
+  float* head_y;
+  int head_out;
+  int* head_done;
 };
 // requirements: W % 64 == 0, Cin % 16 == 0, Cout % 32 == 0, strides/offsets % 8 == 0
 cudaError_t conv3x3(const ConvArgs& a, cudaStream_t s);
