@@ -49,7 +49,11 @@ typedef enum {
   LBPF_ESTATE = -4,      /* call out of order (e.g. step before init) */
   LBPF_ENONFINITE = -5,  /* a NaN/Inf appeared in the fields */
   LBPF_ETIMEDOUT = -6    /* a bounded device wait gave up */
-} lbpf_status;
+} lbpf_status_code;
+/* What every status-returning call returns: one of the lbpf_status_code
+ * values above (an int, so that the ABI is the same from C, C++ and any
+ * foreign-function interface). */
+typedef int lbpf_status;
 
 /* Boundary condition per axis. */
 enum {
@@ -194,17 +198,17 @@ typedef struct {
 /* Fill *p with the defaults: 2D 128 x 128 periodic, no flow, FP32, fold 4,
  * eps 0.05, tau_phi0 = tau_u_liquid = 0.8, tau_f = 0.6, W0 = 2, default
  * lambda, h_drag = 2.757. */
-int lbpf_params_default(lbpf_params* p);
+lbpf_status lbpf_params_default(lbpf_params* p);
 
 /* Validate *p, allocate the device state and return a handle in *out.
  * stream: a cudaStream_t (NULL = legacy default stream).  EINVAL cases:
  * tau <= 1/2, W0 <= 0, eps outside [0, 1), fold outside 0..12 (or != 0 in
  * 3D), grid dimension < 4, INLET_OUTLET on y or z, |u_inlet| > 0.1. */
-int lbpf_create(const lbpf_params* p, void* stream, lbpf_t** out);
+lbpf_status lbpf_create(const lbpf_params* p, void* stream, lbpf_t** out);
 
 /* Initial state from a seed (computed on the device in FP64, stored in the
  * population type); resets the step counter to 0.  Asynchronous. */
-int lbpf_init_seed(lbpf_t* h, const lbpf_seed* s);
+lbpf_status lbpf_init_seed(lbpf_t* h, const lbpf_seed* s);
 
 /* Initial state from a convex polygon seed (2D only): phi0 = tanh(-s /
  * (sqrt(2) W0)) with s = max_i [(x - c) . n_i - dist_i], plus the noise of
@@ -212,24 +216,24 @@ int lbpf_init_seed(lbpf_t* h, const lbpf_seed* s);
  * inlet velocity as there.  Resets the step counter.  EINVAL for 3D, a
  * facet count outside 3..LBPF_MAX_FACETS, a normal whose length differs from
  * 1 by more than 1e-9, or a non-finite value.  Asynchronous. */
-int lbpf_init_polygon(lbpf_t* h, const lbpf_polygon_seed* s);
+lbpf_status lbpf_init_polygon(lbpf_t* h, const lbpf_polygon_seed* s);
 
 /* Initial state from host FP64 fields of nx*ny*nz values each: every
  * population at the equilibrium of (rho, u* = (1 - clamp(phi))/2 u, U, phi);
  * phi(t-1) = phi.  rho, ux, uy, uz may be NULL (1, 0).  Synchronising. */
-int lbpf_init_fields(lbpf_t* h, const double* phi, const double* U, const double* rho,
+lbpf_status lbpf_init_fields(lbpf_t* h, const double* phi, const double* U, const double* rho,
                      const double* ux, const double* uy, const double* uz);
 
 /* Advance n >= 0 coupled steps (Eqs. 4-23, pull-equivalent push streaming).
  * Asynchronous; n = 0 is a no-op. */
-int lbpf_step(lbpf_t* h, int n);
+lbpf_status lbpf_step(lbpf_t* h, int n);
 
 /* Copy fields to host_dst (caller-owned).  Without LBPF_FIELD_STATE: the
  * selected fields one after another in bit order, nx*ny*nz values each, as
  * double if as_fp64 else float; bytes must equal that total.  With
  * LBPF_FIELD_STATE alone: the restartable state of lbpf_state_bytes() bytes.
  * Synchronising. */
-int lbpf_read_fields(lbpf_t* h, unsigned field_mask, void* host_dst, size_t bytes,
+lbpf_status lbpf_read_fields(lbpf_t* h, unsigned field_mask, void* host_dst, size_t bytes,
                      int as_fp64);
 
 /* Size of the restartable state: a 128-byte header (magic "LBPFST02", int64
@@ -255,11 +259,11 @@ size_t lbpf_state_bytes(const lbpf_t* h);
  * step count and the diagnostics' references (ray origin, initial solute
  * total), so that a restored run continues and reports exactly as the
  * uninterrupted one.  Synchronising. */
-int lbpf_write_state(lbpf_t* h, const void* host_src, size_t bytes);
+lbpf_status lbpf_write_state(lbpf_t* h, const void* host_src, size_t bytes);
 
 /* FP64 reductions of the current state (deterministic two-pass sums).
  * Synchronising; reports a non-finite state as LBPF_ENONFINITE. */
-int lbpf_diagnostics(lbpf_t* h, lbpf_diag* out);
+lbpf_status lbpf_diagnostics(lbpf_t* h, lbpf_diag* out);
 
 /* Crystal shape of the current state along k facet normals (nx[k], ny[k],
  * host arrays read during the call): k even in 4..LBPF_MAX_FACETS, unit
@@ -269,7 +273,7 @@ int lbpf_diagnostics(lbpf_t* h, lbpf_diag* out);
  * and the lengths follow on the host in FP64.  The first call allocates a
  * small device scratch.  2D only (EINVAL otherwise); ESTATE before init.
  * Synchronising. */
-int lbpf_measure_facets(lbpf_t* h, int k, const double* nx, const double* ny,
+lbpf_status lbpf_measure_facets(lbpf_t* h, int k, const double* nx, const double* ny,
                         lbpf_facets* out);
 
 /* The same in two halves.  lbpf_facets_enqueue validates as above and queues
@@ -278,15 +282,15 @@ int lbpf_measure_facets(lbpf_t* h, int k, const double* nx, const double* ny,
  * lbpf_facets_collect waits for it and fills *out (synchronising); ESTATE if
  * nothing is queued.  A second enqueue before the collect replaces the
  * first. */
-int lbpf_facets_enqueue(lbpf_t* h, int k, const double* nx, const double* ny);
-int lbpf_facets_collect(lbpf_t* h, lbpf_facets* out);
+lbpf_status lbpf_facets_enqueue(lbpf_t* h, int k, const double* nx, const double* ny);
+lbpf_status lbpf_facets_collect(lbpf_t* h, lbpf_facets* out);
 
 /* Straight-line fit L'(t) = intercept + slope t of a size history of n >= 2
  * points (host arrays), and its coefficient of determination R^2 =
  * 1 - A_res / A_tot (Eqs. 26-28); R^2 is NaN when every L is the same.
  * EINVAL for a null pointer, n < 2, non-finite data or all t equal.  A host
  * computation; needs no handle. */
-int lbpf_growth_fit(const double* t, const double* L, int n, double* slope, double* intercept,
+lbpf_status lbpf_growth_fit(const double* t, const double* L, int n, double* slope, double* intercept,
                     double* r2);
 
 /* Solid nodes (the reactor walls and baffles of Sec. 3.1.2 and 3.2): mask is
@@ -305,10 +309,10 @@ int lbpf_growth_fit(const double* t, const double* L, int n, double* slope, doub
  * every row) must be fluid.  The mask is configuration, not state:
  * lbpf_write_state keeps it.  The block propagator refuses a handle with solid
  * nodes.  Synchronising. */
-int lbpf_set_solid(lbpf_t* h, const uint8_t* mask);
+lbpf_status lbpf_set_solid(lbpf_t* h, const uint8_t* mask);
 
 /* Rebind the handle to another stream (e.g. the caller's current stream). */
-int lbpf_set_stream(lbpf_t* h, void* stream);
+lbpf_status lbpf_set_stream(lbpf_t* h, void* stream);
 
 /* Bytes of device memory the handle owns. */
 size_t lbpf_device_bytes(const lbpf_t* h);
@@ -337,7 +341,7 @@ typedef struct lbpf_batch lbpf_batch_t;
  * LBPF_FP16_SHIFTED, LBPF_BF16_SHIFTED; sizes and every other model
  * parameter may differ.  EINVAL otherwise.  Instances may carry solid nodes
  * (lbpf_set_solid on lbpf_batch_instance; picked up by the next step).  stream: as for lbpf_create, shared by all instances. */
-int lbpf_batch_create(const lbpf_params* p, const lbpf_seed* s, int count, void* stream,
+lbpf_status lbpf_batch_create(const lbpf_params* p, const lbpf_seed* s, int count, void* stream,
                       lbpf_batch_t** out);
 
 /* Advance every instance by n >= 0 steps.  Asynchronous, except that the
@@ -345,21 +349,21 @@ int lbpf_batch_create(const lbpf_params* p, const lbpf_seed* s, int count, void*
  * Instances re-initialised or restored since the last call are picked up;
  * instances stepped individually to a different buffer parity give
  * LBPF_ESTATE.  An error of any instance is reported here. */
-int lbpf_batch_step(lbpf_batch_t* b, int n);
+lbpf_status lbpf_batch_step(lbpf_batch_t* b, int n);
 
 /* lbpf_diagnostics of every instance into out[0..count-1].  Synchronising;
  * returns the first non-OK status (all entries are still filled). */
-int lbpf_batch_diagnostics(lbpf_batch_t* b, lbpf_diag* out);
+lbpf_status lbpf_batch_diagnostics(lbpf_batch_t* b, lbpf_diag* out);
 
 /* Borrowed handle of instance i (NULL if out of range); owned by the batch.
  * Use it for lbpf_read_fields, lbpf_diagnostics, lbpf_write_state. */
 lbpf_t* lbpf_batch_instance(lbpf_batch_t* b, int i);
-int lbpf_batch_count(const lbpf_batch_t* b);
+lbpf_status lbpf_batch_count(const lbpf_batch_t* b);
 
 /* The tile shape the tuner chose (rows of the 32-wide tile, pipeline stages)
  * and the measured ms per step of each compiled shape (ms[0..*nvar-1]); any
  * pointer may be NULL.  LBPF_ESTATE before tuning has run. */
-int lbpf_batch_tuning(const lbpf_batch_t* b, int* tile_rows, int* stages, float* ms, int* nvar);
+lbpf_status lbpf_batch_tuning(const lbpf_batch_t* b, int* tile_rows, int* stages, float* ms, int* nvar);
 const char* lbpf_batch_last_error(const lbpf_batch_t* b);
 void lbpf_batch_destroy(lbpf_batch_t* b);
 
@@ -387,17 +391,17 @@ typedef struct {
  * initialises the weights from cfg->seed.  stream: the CUDA stream its work
  * is queued on (NULL = legacy default).  LBPF_EINVAL for an unsupported
  * configuration (reason on stderr), LBPF_ENOMEM if an allocation fails. */
-int lbpf_unet_create(const lbpf_unet_cfg* cfg, void* stream, lbpf_unet_t** out);
+lbpf_status lbpf_unet_create(const lbpf_unet_cfg* cfg, void* stream, lbpf_unet_t** out);
 /* x: device FP32 [batch][height][width][in_ch]; y: device FP32 [..][out_ch];
  * both caller-owned, not overlapping.  Asynchronous on the network's stream. */
-int lbpf_unet_forward(lbpf_unet_t* n, const float* x, float* y);
+lbpf_status lbpf_unet_forward(lbpf_unet_t* n, const float* x, float* y);
 /* Loss (mean squared error against device FP32 targets t, same layout as y)
  * and the gradients of every parameter, without updating them; the loss is
  * written to *loss_host (synchronising) if loss_host is not NULL. */
-int lbpf_unet_grad(lbpf_unet_t* n, const float* x, const float* t, float* loss_host);
+lbpf_status lbpf_unet_grad(lbpf_unet_t* n, const float* x, const float* t, float* loss_host);
 /* One Adam step (beta 0.9 / 0.999, eps 1e-8) at learning rate lr; the loss
  * of the batch goes to the device float *loss_dev if not NULL.  Asynchronous. */
-int lbpf_unet_train_step(lbpf_unet_t* n, const float* x, const float* t, float lr,
+lbpf_status lbpf_unet_train_step(lbpf_unet_t* n, const float* x, const float* t, float lr,
                          float* loss_dev);
 /* The training loop of the block propagator's network, on pairs held on the
  * device: per step, a minibatch of pairs gathered (and mirrored) into the
@@ -422,7 +426,7 @@ int lbpf_unet_train_step(lbpf_unet_t* n, const float* x, const float* t, float l
  * not bit for bit).  The first call allocates two minibatch buffers
  * owned by the network.  LBPF_EINVAL for an index, flip or rate out of range
  * or a network that is not 4 -> 4 (nothing queued). */
-int lbpf_surrogate_train(lbpf_unet_t* net, const float* X, const float* T, int64_t n_pairs,
+lbpf_status lbpf_surrogate_train(lbpf_unet_t* net, const float* X, const float* T, int64_t n_pairs,
                          int steps, const int32_t* idx, const int32_t* flip, const float* lr,
                          int log_every, float* loss_log);
 
@@ -435,15 +439,15 @@ int lbpf_surrogate_train(lbpf_unet_t* net, const float* X, const float* T, int64
  * convolution has Cin = 16 (inputs zero-padded).  which: 0 weights,
  * 1 gradients; set = 1 writes weights.  Synchronising. */
 size_t lbpf_unet_param_count(const lbpf_unet_t* n);
-int lbpf_unet_params(lbpf_unet_t* n, int which, float* host, size_t count, int set);
+lbpf_status lbpf_unet_params(lbpf_unet_t* n, int which, float* host, size_t count, int set);
 /* Select the convolution kernels: 1 (default) the tcgen05 / TMEM / TMA
  * kernel wherever the layer's shape allows it, 0 the warp-level mma.sync
  * kernel everywhere.  Takes effect at the next pass. */
-int lbpf_unet_set_tensor_path(lbpf_unet_t* n, int use_tcgen05);
+lbpf_status lbpf_unet_set_tensor_path(lbpf_unet_t* n, int use_tcgen05);
 /* Synchronises the network's stream and returns LBPF_ETIMEDOUT if a
  * tensor-core kernel gave up waiting on one of its barriers since creation
  * (lbpf_unet_grad and lbpf_surrogate_advance check the same). */
-int lbpf_unet_status(lbpf_unet_t* n);
+lbpf_status lbpf_unet_status(lbpf_unet_t* n);
 size_t lbpf_unet_device_bytes(const lbpf_unet_t* n);
 const char* lbpf_unet_last_error(const lbpf_unet_t* n);
 void lbpf_unet_destroy(lbpf_unet_t* n);
@@ -498,11 +502,11 @@ typedef struct {
 } lbpf_surrogate_report;
 
 /* The network input of the current state: device FP32 [ny][nx][4]. */
-int lbpf_surrogate_sample(lbpf_t* h, const lbpf_surrogate_cfg* cfg, float* x);
+lbpf_status lbpf_surrogate_sample(lbpf_t* h, const lbpf_surrogate_cfg* cfg, float* x);
 /* Training target from the inputs x0 (state at t) and x1 (at t + block):
  * t = (x1 - x0) scale / res_scale per channel; device FP32 [npix][4];
  * queued on `stream`. */
-int lbpf_surrogate_target(const lbpf_surrogate_cfg* cfg, const float* x0, const float* x1,
+lbpf_status lbpf_surrogate_target(const lbpf_surrogate_cfg* cfg, const float* x0, const float* x1,
                           int64_t npix, float* t, void* stream);
 /* Advance `blocks` blocks (synchronising once per block); rep may be NULL.
  * The network's kernels run on the simulation's stream during the call.  The
@@ -515,7 +519,7 @@ int lbpf_surrogate_target(const lbpf_surrogate_cfg* cfg, const float* x0, const 
  * on unordered streams too; calls that share one network must not overlap
  * (from several host threads).  LBPF_ETIMEDOUT if a tensor-core kernel gave
  * up waiting; LBPF_EINVAL for a mismatched network or cfg. */
-int lbpf_surrogate_advance(lbpf_t* h, lbpf_unet_t* net, const lbpf_surrogate_cfg* cfg,
+lbpf_status lbpf_surrogate_advance(lbpf_t* h, lbpf_unet_t* net, const lbpf_surrogate_cfg* cfg,
                            int blocks, lbpf_surrogate_report* rep);
 
 /* ---- allocation-free reduction ------------------------------------------------
@@ -550,7 +554,7 @@ int lbpf_surrogate_advance(lbpf_t* h, lbpf_unet_t* net, const lbpf_surrogate_cfg
  * propagator does not use it (it reduces into its network's scratch). */
 #define LBPF_NOALLOC_MAX_BLOCKS 4096
 #define LBPF_NOALLOC_MAX_NODES ((int64_t)LBPF_NOALLOC_MAX_BLOCKS * 256 * 64)
-int lbpf_field_sums_noalloc(const void* phi, const void* phi_prev, const void* U,
+lbpf_status lbpf_field_sums_noalloc(const void* phi, const void* phi_prev, const void* U,
                             const void* rho, int64_t n, int fp64, double* out, void* stream);
 
 #ifdef __cplusplus

@@ -392,6 +392,10 @@ struct HaloArgs {
   const float* head_b;
   float* head_y;
   int head_out;
+  // fused 2 x 2 average pooling of the output (null pool_y: none; G even and
+  // no mask): pool_y [N][H/2][W/2][pool_Cy], channels pool_off + n0 + c
+  bf16* pool_y;
+  int pool_Cy, pool_off;
 };
 
 template <int BK, int BN, int G>
@@ -409,6 +413,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int ksteps = 3 * a.nchunks;
   const bool head = a.head_y != nullptr;
+  const bool pool = a.pool_y != nullptr;
   pdl_trigger();
   if (threadIdx.x == 0) {
     for (int s = 0; s < S; ++s) {
@@ -532,6 +537,80 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       tc_fence_after();
       int img, h0, w0, n0;
       tile_at(t, img, h0, w0, n0);
+      if constexpr (G % 2 == 0) {
+        if (pool) {
+          // rows in pairs: both rows' outputs are stored, and each even lane
+          // also writes the 2 x 2 average of its pixel, its right neighbour's
+          // (lane + 1) and the two below, in the order of the separate
+          // pooling kernel ((x00 + x01) + x10 + x11) / 4 over the bf16 values
+#pragma unroll 1
+          for (int g0 = 0; g0 < G; g0 += 2) {
+            const long long p0 = ((long long)img * a.H + h0 + g0) * a.W + w0 + m;
+            bf16* y0 = a.y + p0 * a.Cy + a.co_off + n0;
+            bf16* y1 = y0 + (long long)a.W * a.Cy;
+            const long long pp = ((long long)img * (a.H / 2) + (h0 + g0) / 2) * (a.W / 2) +
+                                 (w0 + m) / 2;
+            bf16* yp = a.pool_y + pp * a.pool_Cy + a.pool_off + n0;
+#pragma unroll 1
+            for (int c = 0; c < BN; c += 32) {
+              uint32_t o0[16], o1[16];
+#pragma unroll
+              for (int rr = 0; rr < 2; ++rr) {
+                uint32_t r[32];
+                tmem_ld32(tmem + (uint32_t(q * 32) << 16) +
+                              uint32_t(buf * Sh::ACC + (g0 + rr) * BN + c),
+                          r);
+                uint32_t* o = rr ? o1 : o0;
+#pragma unroll
+                for (int j = 0; j < 32; j += 2) {
+                  float v0 = __uint_as_float(r[j]) + sbias[n0 + c + j];
+                  float v1 = __uint_as_float(r[j + 1]) + sbias[n0 + c + j + 1];
+                  if (a.relu) {
+                    v0 = fmaxf(v0, 0.f);
+                    v1 = fmaxf(v1, 0.f);
+                  }
+                  const __nv_bfloat162 ob = __floats2bfloat162_rn(v0, v1);
+                  o[j / 2] = *reinterpret_cast<const uint32_t*>(&ob);
+                }
+              }
+#pragma unroll
+              for (int v = 0; v < 4; ++v) {
+                reinterpret_cast<uint4*>(y0 + c)[v] =
+                    make_uint4(o0[4 * v], o0[4 * v + 1], o0[4 * v + 2], o0[4 * v + 3]);
+                reinterpret_cast<uint4*>(y1 + c)[v] =
+                    make_uint4(o1[4 * v], o1[4 * v + 1], o1[4 * v + 2], o1[4 * v + 3]);
+              }
+              uint32_t pk[16];
+#pragma unroll
+              for (int k = 0; k < 16; ++k) {
+                const uint32_t n0v = __shfl_down_sync(0xffffffffu, o0[k], 1);
+                const uint32_t n1v = __shfl_down_sync(0xffffffffu, o1[k], 1);
+                const __nv_bfloat162 x00 = *reinterpret_cast<const __nv_bfloat162*>(&o0[k]);
+                const __nv_bfloat162 x01 = *reinterpret_cast<const __nv_bfloat162*>(&n0v);
+                const __nv_bfloat162 x10 = *reinterpret_cast<const __nv_bfloat162*>(&o1[k]);
+                const __nv_bfloat162 x11 = *reinterpret_cast<const __nv_bfloat162*>(&n1v);
+                float lo = __low2float(x00) + __low2float(x01);
+                float hi = __high2float(x00) + __high2float(x01);
+                lo += __low2float(x10);
+                hi += __high2float(x10);
+                lo = 0.25f * (lo + __low2float(x11));
+                hi = 0.25f * (hi + __high2float(x11));
+                const __nv_bfloat162 pb = __floats2bfloat162_rn(lo, hi);
+                pk[k] = *reinterpret_cast<const uint32_t*>(&pb);
+              }
+              if ((lane & 1) == 0)
+#pragma unroll
+                for (int v = 0; v < 4; ++v)
+                  reinterpret_cast<uint4*>(yp + c)[v] =
+                      make_uint4(pk[4 * v], pk[4 * v + 1], pk[4 * v + 2], pk[4 * v + 3]);
+            }
+          }
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&acc_empty[buf]);
+          continue;
+        }
+      }
 #pragma unroll 1
       for (int g = 0; g < G; ++g) {
         const long long p = ((long long)img * a.H + h0 + g) * a.W + w0 + m;
@@ -768,6 +847,13 @@ static cudaError_t conv3x3_tc_halo(const ConvArgs& a, unsigned* err, cudaStream_
   t.head_y = fuse ? a.head_y : nullptr;
   t.head_out = fuse ? a.head_out : 0;
   if (a.head_done) *a.head_done = fuse ? 1 : 0;
+  // the pooling of the next level rides along when a tile holds row pairs
+  const bool fpool = a.pool_y && G % 2 == 0 && !a.mask && a.H % 2 == 0 && a.pool_Cy % 8 == 0 &&
+                     a.pool_off % 8 == 0 && !fuse;
+  t.pool_y = fpool ? a.pool_y : nullptr;
+  t.pool_Cy = a.pool_Cy;
+  t.pool_off = a.pool_off;
+  if (a.pool_done) *a.pool_done = fpool ? 1 : 0;
   *used = true;
   switch (BK) {
     case 64: return launch_halo_bk<64>(BN, G, mx, mw, t, s);

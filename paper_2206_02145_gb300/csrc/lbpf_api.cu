@@ -301,7 +301,7 @@ static_assert(sizeof(StateHeader) == 128, "state header must be 128 bytes");
 
 extern "C" {
 
-int lbpf_params_default(lbpf_params* p) {
+lbpf_status lbpf_params_default(lbpf_params* p) {
   if (!p) return LBPF_EINVAL;
   std::memset(p, 0, sizeof(*p));
   p->dim = 2;
@@ -318,7 +318,7 @@ int lbpf_params_default(lbpf_params* p) {
   return LBPF_OK;
 }
 
-int lbpf_create(const lbpf_params* p, void* stream, lbpf_t** out) {
+lbpf_status lbpf_create(const lbpf_params* p, void* stream, lbpf_t** out) {
   if (!p || !out) return LBPF_EINVAL;
   *out = nullptr;
   char why[160];
@@ -375,7 +375,7 @@ int lbpf_create(const lbpf_params* p, void* stream, lbpf_t** out) {
   return LBPF_OK;
 }
 
-int lbpf_init_seed(lbpf_t* h, const lbpf_seed* s) {
+lbpf_status lbpf_init_seed(lbpf_t* h, const lbpf_seed* s) {
   int rc = check_handle(h);
   if (rc) return rc;
   if (!s || !(s->radius >= 0.0) || !std::isfinite(s->u0) || !std::isfinite(s->noise_amp) ||
@@ -403,7 +403,7 @@ int lbpf_init_seed(lbpf_t* h, const lbpf_seed* s) {
   return LBPF_OK;
 }
 
-int lbpf_init_polygon(lbpf_t* h, const lbpf_polygon_seed* s) {
+lbpf_status lbpf_init_polygon(lbpf_t* h, const lbpf_polygon_seed* s) {
   int rc = check_handle(h);
   if (rc) return rc;
   if (h->m.dim != 2) return fail(h, LBPF_EINVAL, "polygon seeds are 2D");
@@ -446,7 +446,7 @@ int lbpf_init_polygon(lbpf_t* h, const lbpf_polygon_seed* s) {
   return LBPF_OK;
 }
 
-int lbpf_init_fields(lbpf_t* h, const double* phi, const double* U, const double* rho,
+lbpf_status lbpf_init_fields(lbpf_t* h, const double* phi, const double* U, const double* rho,
                      const double* ux, const double* uy, const double* uz) {
   int rc = check_handle(h);
   if (rc) return rc;
@@ -491,7 +491,7 @@ int lbpf_init_fields(lbpf_t* h, const double* phi, const double* U, const double
   return LBPF_OK;
 }
 
-int lbpf_step(lbpf_t* h, int n) {
+lbpf_status lbpf_step(lbpf_t* h, int n) {
   int rc = check_handle(h);
   if (rc) return rc;
   if (n < 0) return fail(h, LBPF_EINVAL, "n must be >= 0");
@@ -531,7 +531,7 @@ size_t lbpf_state_bytes(const lbpf_t* h) {
   return sizeof(StateHeader) + q * n * h->es + n * h->rs + (h->m.rel_g ? 2 * n * 2 : 0);
 }
 
-int lbpf_read_fields(lbpf_t* h, unsigned mask, void* host_dst, size_t bytes, int as_fp64) {
+lbpf_status lbpf_read_fields(lbpf_t* h, unsigned mask, void* host_dst, size_t bytes, int as_fp64) {
   int rc = check_handle(h);
   if (rc) return rc;
   if (!host_dst) return fail(h, LBPF_EINVAL, "null destination");
@@ -587,7 +587,7 @@ int lbpf_read_fields(lbpf_t* h, unsigned mask, void* host_dst, size_t bytes, int
   return check_device_error(h);
 }
 
-int lbpf_write_state(lbpf_t* h, const void* host_src, size_t bytes) {
+lbpf_status lbpf_write_state(lbpf_t* h, const void* host_src, size_t bytes) {
   int rc = check_handle(h);
   if (rc) return rc;
   if (!host_src || bytes != lbpf_state_bytes(h))
@@ -631,7 +631,7 @@ int lbpf_write_state(lbpf_t* h, const void* host_src, size_t bytes) {
   return LBPF_OK;
 }
 
-int lbpf_diagnostics(lbpf_t* h, lbpf_diag* out) {
+lbpf_status lbpf_diagnostics(lbpf_t* h, lbpf_diag* out) {
   int rc = check_handle(h);
   if (rc) return rc;
   if (!out) return fail(h, LBPF_EINVAL, "null output");
@@ -656,7 +656,7 @@ int lbpf_diagnostics(lbpf_t* h, lbpf_diag* out) {
   return LBPF_OK;
 }
 
-int lbpf_facets_enqueue(lbpf_t* h, int k, const double* nx, const double* ny) {
+lbpf_status lbpf_facets_enqueue(lbpf_t* h, int k, const double* nx, const double* ny) {
   int rc = check_handle(h);
   if (rc) return rc;
   if (!nx || !ny) return fail(h, LBPF_EINVAL, "null argument");
@@ -699,7 +699,7 @@ int lbpf_facets_enqueue(lbpf_t* h, int k, const double* nx, const double* ny) {
   return LBPF_OK;
 }
 
-int lbpf_facets_collect(lbpf_t* h, lbpf_facets* out) {
+lbpf_status lbpf_facets_collect(lbpf_t* h, lbpf_facets* out) {
   int rc = check_handle(h);
   if (rc) return rc;
   if (!out) return fail(h, LBPF_EINVAL, "null argument");
@@ -783,13 +783,13 @@ int lbpf_facets_collect(lbpf_t* h, lbpf_facets* out) {
   return LBPF_OK;
 }
 
-int lbpf_measure_facets(lbpf_t* h, int k, const double* nx, const double* ny,
+lbpf_status lbpf_measure_facets(lbpf_t* h, int k, const double* nx, const double* ny,
                         lbpf_facets* out) {
   int rc = lbpf_facets_enqueue(h, k, nx, ny);
   return rc ? rc : lbpf_facets_collect(h, out);
 }
 
-int lbpf_growth_fit(const double* t, const double* L, int n, double* slope, double* intercept,
+lbpf_status lbpf_growth_fit(const double* t, const double* L, int n, double* slope, double* intercept,
                     double* r2) {
   if (!t || !L || !slope || !intercept || !r2 || n < 2) return LBPF_EINVAL;
   double tm = 0.0, Lm = 0.0;
@@ -819,7 +819,7 @@ int lbpf_growth_fit(const double* t, const double* L, int n, double* slope, doub
   return LBPF_OK;
 }
 
-int lbpf_set_solid(lbpf_t* h, const uint8_t* mask) {
+lbpf_status lbpf_set_solid(lbpf_t* h, const uint8_t* mask) {
   int rc = check_handle(h);
   if (rc) return rc;
   if (!mask) {
@@ -858,7 +858,7 @@ int lbpf_set_solid(lbpf_t* h, const uint8_t* mask) {
   return LBPF_OK;
 }
 
-int lbpf_set_stream(lbpf_t* h, void* stream) {
+lbpf_status lbpf_set_stream(lbpf_t* h, void* stream) {
   if (!h) return LBPF_EINVAL;
   h->stream = static_cast<cudaStream_t>(stream);
   return LBPF_OK;
@@ -978,7 +978,7 @@ int batch_build_graph(lbpf_batch* b) {
 
 extern "C" {
 
-int lbpf_batch_create(const lbpf_params* p, const lbpf_seed* s, int count, void* stream,
+lbpf_status lbpf_batch_create(const lbpf_params* p, const lbpf_seed* s, int count, void* stream,
                       lbpf_batch_t** out) {
   if (!p || !s || !out || count < 1 || count > 65535) return LBPF_EINVAL;
   *out = nullptr;
@@ -1019,7 +1019,7 @@ int lbpf_batch_create(const lbpf_params* p, const lbpf_seed* s, int count, void*
   return LBPF_OK;
 }
 
-int lbpf_batch_step(lbpf_batch_t* b, int n) {
+lbpf_status lbpf_batch_step(lbpf_batch_t* b, int n) {
   if (!b) return LBPF_EINVAL;
   if (b->status != LBPF_OK) return b->status;
   if (n < 0) return bfail(b, LBPF_EINVAL, "n must be >= 0");
@@ -1086,7 +1086,7 @@ int lbpf_batch_step(lbpf_batch_t* b, int n) {
   return LBPF_OK;
 }
 
-int lbpf_batch_diagnostics(lbpf_batch_t* b, lbpf_diag* out) {
+lbpf_status lbpf_batch_diagnostics(lbpf_batch_t* b, lbpf_diag* out) {
   if (!b || !out) return LBPF_EINVAL;
   int worst = LBPF_OK;
   for (size_t i = 0; i < b->kids.size(); ++i) {
@@ -1101,9 +1101,9 @@ lbpf_t* lbpf_batch_instance(lbpf_batch_t* b, int i) {
   return b->kids[i];
 }
 
-int lbpf_batch_count(const lbpf_batch_t* b) { return b ? int(b->kids.size()) : 0; }
+lbpf_status lbpf_batch_count(const lbpf_batch_t* b) { return b ? int(b->kids.size()) : 0; }
 
-int lbpf_batch_tuning(const lbpf_batch_t* b, int* tile_rows, int* stages, float* ms, int* nvar) {
+lbpf_status lbpf_batch_tuning(const lbpf_batch_t* b, int* tile_rows, int* stages, float* ms, int* nvar) {
   if (!b) return LBPF_EINVAL;
   if (nvar) *nvar = b->nplans;
   if (ms)

@@ -148,7 +148,7 @@ cudaError_t launch_field_sums(const void* phi, const void* phi_prev, const void*
 
 }  // namespace lbk
 
-extern "C" int lbpf_field_sums_noalloc(const void* phi, const void* phi_prev, const void* U,
+extern "C" lbpf_status lbpf_field_sums_noalloc(const void* phi, const void* phi_prev, const void* U,
                                        const void* rho, int64_t n, int fp64, double* out,
                                        void* stream) {
   if (!phi || !phi_prev || !U || !out || n < 0) return LBPF_EINVAL;

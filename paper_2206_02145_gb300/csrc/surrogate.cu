@@ -158,7 +158,7 @@ cudaError_t make_conv(lbpf_unet* n, ConvLayer* l, int cin, int cout, int real_ci
 // head: the 1x1 head to fuse into this layer's epilogue where the kernel can
 // (*head_done says whether it did)
 int conv_fwd(lbpf_unet* n, const ConvLayer& l, const Act& x, int xoff, const Act& y, int yoff,
-             int* head_done = nullptr) {
+             int* head_done = nullptr, const Act* pool = nullptr, int* pool_done = nullptr) {
   lbk::nn::ConvArgs a{};
   a.x = x.p;
   a.Cx = x.c;
@@ -183,6 +183,12 @@ int conv_fwd(lbpf_unet* n, const ConvLayer& l, const Act& x, int xoff, const Act
     a.head_y = n->y;
     a.head_out = n->cfg.out_ch;
     a.head_done = head_done;
+  }
+  if (pool && pool_done) {  // the next level's pooled input, channels 0 .. Cout
+    a.pool_y = pool->p;
+    a.pool_Cy = pool->c;
+    a.pool_off = 0;
+    a.pool_done = pool_done;
   }
   UCK(n, lbk::nn::conv3x3(a, n->stream));
   return LBPF_OK;
@@ -249,9 +255,14 @@ int forward(lbpf_unet* n) {
     const Act& in = l == 0 ? n->xin : n->pool[l];
     if ((rc = conv_fwd(n, n->enc_a[l], in, 0, n->ea[l], 0))) return rc;
     if (l < L - 1) {
-      if ((rc = conv_fwd(n, n->enc_b[l], n->ea[l], 0, n->cat[l], n->C[l]))) return rc;
-      UCK(n, lbk::nn::avgpool2(n->cat[l].p, n->cat[l].c, n->C[l], n->pool[l + 1].p, n->C[l], 0,
-                               n->C[l], n->cfg.batch, n->H[l], n->W[l], n->stream));
+      // the 2 x 2 pooling into the next level rides in the epilogue where it can
+      int pooled = 0;
+      if ((rc = conv_fwd(n, n->enc_b[l], n->ea[l], 0, n->cat[l], n->C[l], nullptr, &n->pool[l + 1],
+                         &pooled)))
+        return rc;
+      if (!pooled)
+        UCK(n, lbk::nn::avgpool2(n->cat[l].p, n->cat[l].c, n->C[l], n->pool[l + 1].p, n->C[l], 0,
+                                 n->C[l], n->cfg.batch, n->H[l], n->W[l], n->stream));
     } else {
       if ((rc = conv_fwd(n, n->enc_b[l], n->ea[l], 0, n->bottom, 0))) return rc;
     }
@@ -560,7 +571,7 @@ double ray_diff(const double* a, const double* b) {
 
 extern "C" {
 
-int lbpf_unet_create(const lbpf_unet_cfg* cfg, void* stream, lbpf_unet_t** out) {
+lbpf_status lbpf_unet_create(const lbpf_unet_cfg* cfg, void* stream, lbpf_unet_t** out) {
   if (!cfg || !out) return LBPF_EINVAL;
   *out = nullptr;
   const int L = cfg->levels;
@@ -666,7 +677,7 @@ int lbpf_unet_create(const lbpf_unet_cfg* cfg, void* stream, lbpf_unet_t** out) 
   return LBPF_OK;
 }
 
-int lbpf_unet_forward(lbpf_unet_t* n, const float* x, float* y) {
+lbpf_status lbpf_unet_forward(lbpf_unet_t* n, const float* x, float* y) {
   if (!n || !x || !y) return LBPF_EINVAL;
   int rc;
   if ((rc = pack_input(n, x))) return rc;
@@ -676,7 +687,7 @@ int lbpf_unet_forward(lbpf_unet_t* n, const float* x, float* y) {
   return LBPF_OK;
 }
 
-int lbpf_unet_grad(lbpf_unet_t* n, const float* x, const float* t, float* loss_host) {
+lbpf_status lbpf_unet_grad(lbpf_unet_t* n, const float* x, const float* t, float* loss_host) {
   if (!n || !x || !t) return LBPF_EINVAL;
   int rc;
   for (const ParamView& v : params(n)) UCK(n, cudaMemsetAsync(v.g, 0, v.n * 4, n->stream));
@@ -685,15 +696,15 @@ int lbpf_unet_grad(lbpf_unet_t* n, const float* x, const float* t, float* loss_h
   return check_err(n);
 }
 
-int lbpf_unet_set_tensor_path(lbpf_unet_t* n, int use_tcgen05) {
+lbpf_status lbpf_unet_set_tensor_path(lbpf_unet_t* n, int use_tcgen05) {
   if (!n) return LBPF_EINVAL;
   n->tensor_path = use_tcgen05 ? 1 : 0;
   return LBPF_OK;
 }
 
-int lbpf_unet_status(lbpf_unet_t* n) { return n ? check_err(n) : LBPF_EINVAL; }
+lbpf_status lbpf_unet_status(lbpf_unet_t* n) { return n ? check_err(n) : LBPF_EINVAL; }
 
-int lbpf_unet_train_step(lbpf_unet_t* n, const float* x, const float* t, float lr,
+lbpf_status lbpf_unet_train_step(lbpf_unet_t* n, const float* x, const float* t, float lr,
                          float* loss_dev) {
   if (!n || !x || !t) return LBPF_EINVAL;
   int rc;
@@ -705,7 +716,7 @@ int lbpf_unet_train_step(lbpf_unet_t* n, const float* x, const float* t, float l
   return LBPF_OK;
 }
 
-int lbpf_surrogate_train(lbpf_unet_t* n, const float* X, const float* T, int64_t n_pairs,
+lbpf_status lbpf_surrogate_train(lbpf_unet_t* n, const float* X, const float* T, int64_t n_pairs,
                          int steps, const int32_t* idx, const int32_t* flip, const float* lr,
                          int log_every, float* loss_log) {
   if (!n || !X || !T || n_pairs < 1 || steps < 0 || (steps > 0 && (!idx || !lr)) ||
@@ -780,7 +791,7 @@ size_t lbpf_unet_param_count(const lbpf_unet_t* n) {
   return s;
 }
 
-int lbpf_unet_params(lbpf_unet_t* n, int which, float* host, size_t count, int set) {
+lbpf_status lbpf_unet_params(lbpf_unet_t* n, int which, float* host, size_t count, int set) {
   if (!n || !host || count != lbpf_unet_param_count(n) || which < 0 || which > 1 ||
       (set && which != 0))
     return LBPF_EINVAL;
@@ -804,7 +815,7 @@ int lbpf_unet_params(lbpf_unet_t* n, int which, float* host, size_t count, int s
   return LBPF_OK;
 }
 
-int lbpf_surrogate_target(const lbpf_surrogate_cfg* cfg, const float* x0, const float* x1,
+lbpf_status lbpf_surrogate_target(const lbpf_surrogate_cfg* cfg, const float* x0, const float* x1,
                           int64_t npix, float* t, void* stream) {
   if (check_cfg(cfg) || !x0 || !x1 || !t || npix < 0) return LBPF_EINVAL;
   lbk::Vec4 g;
@@ -815,7 +826,7 @@ int lbpf_surrogate_target(const lbpf_surrogate_cfg* cfg, const float* x0, const 
   return cudaGetLastError() == cudaSuccess ? LBPF_OK : LBPF_ECUDA;
 }
 
-int lbpf_surrogate_sample(lbpf_t* h, const lbpf_surrogate_cfg* cfg, float* x) {
+lbpf_status lbpf_surrogate_sample(lbpf_t* h, const lbpf_surrogate_cfg* cfg, float* x) {
   if (!h || !x || check_cfg(cfg)) return LBPF_EINVAL;
   if (h->status != LBPF_OK) return h->status;
   if (!h->initialized) return sfail(h, LBPF_ESTATE, "sample before init");
@@ -908,7 +919,7 @@ int prediction_graph(lbpf* h, lbpf_unet* net, const lbpf_surrogate_cfg* cfg,
 
 extern "C" {
 
-int lbpf_surrogate_advance(lbpf_t* h, lbpf_unet_t* net, const lbpf_surrogate_cfg* cfg,
+lbpf_status lbpf_surrogate_advance(lbpf_t* h, lbpf_unet_t* net, const lbpf_surrogate_cfg* cfg,
                            int blocks, lbpf_surrogate_report* rep) {
   if (!h || !net || check_cfg(cfg) || blocks < 0) return LBPF_EINVAL;
   if (h->status != LBPF_OK) return h->status;

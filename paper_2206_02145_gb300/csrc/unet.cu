@@ -114,14 +114,17 @@ __global__ void __launch_bounds__(kThreads) conv3x3_kernel(const ConvArgs a) {
 
 // ---- weight gradient ---------------------------------------------------------------
 // dW[tap][co][ci] += sum_p dy[p][co] x[p + shift(tap)][ci] over a chunk of
-// pixels.  M = BM output channels, N = BN input channels, K = 16 pixels per
-// step; A and B come from row-major [pixel][channel] tiles through
-// ldmatrix.trans.  4 warps as 2 x 2.
-template <int BM, int BN>
+// pixels.  M = BM output channels, N = BN input channels; each pipeline stage
+// holds KP pixels of dy and of the tap-shifted x ([pixel][channel] tiles,
+// 16-byte cp.async, zero fill outside the image and past the chunk), S stages
+// deep so that S - 1 stages are in flight while one is multiplied; the MMA
+// steps K = 16 pixels through a stage with ldmatrix.trans.  4 warps as 2 x 2.
+template <int BM, int BN, int KP, int S>
 __global__ void __launch_bounds__(kThreads) wgrad3x3_kernel(const WgradArgs a) {
   constexpr int LDA = BM + 8, LDB = BN + 8;
-  __shared__ __align__(16) bf16 sA[2][16][LDA];
-  __shared__ __align__(16) bf16 sB[2][16][LDB];
+  extern __shared__ __align__(16) unsigned char wg_smem[];
+  bf16(*sA)[KP][LDA] = reinterpret_cast<bf16(*)[KP][LDA]>(wg_smem);
+  bf16(*sB)[KP][LDB] = reinterpret_cast<bf16(*)[KP][LDB]>(wg_smem + S * KP * LDA * 2);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int wm = warp & 1, wn = warp >> 1;
   constexpr int WM = BM / 2, WN = BN / 2;  // warp tile
@@ -131,7 +134,7 @@ __global__ void __launch_bounds__(kThreads) wgrad3x3_kernel(const WgradArgs a) {
   const long long p_begin = (long long)chunk * a.chunk;
   long long p_end = p_begin + a.chunk;
   if (p_end > a.npix) p_end = a.npix;
-  const int ksteps = int((p_end - p_begin) / 16);
+  const int ksteps = int((p_end - p_begin + KP - 1) / KP);
 
   float acc[WM / 16][WN / 8][4];
 #pragma unroll
@@ -142,47 +145,55 @@ __global__ void __launch_bounds__(kThreads) wgrad3x3_kernel(const WgradArgs a) {
       for (int k = 0; k < 4; ++k) acc[i][j][k] = 0.f;
 
   auto load = [&](int ks, int buf) {
-    const long long pb = p_begin + ks * 16;
-    for (int i = tid; i < 16 * (BM / 8); i += kThreads) {
+    const long long pb = p_begin + (long long)ks * KP;
+    for (int i = tid; i < KP * (BM / 8); i += kThreads) {
       const int r = i / (BM / 8), c = (i % (BM / 8)) * 8;
-      cp_async16(&sA[buf][r][c], a.dy + (pb + r) * a.Cdy + a.co_off + m0 + c, 16);
+      const bool in = pb + r < p_end;
+      cp_async16(&sA[buf][r][c], a.dy + (in ? pb + r : p_begin) * a.Cdy + a.co_off + m0 + c,
+                 in ? 16 : 0);
     }
-    for (int i = tid; i < 16 * (BN / 8); i += kThreads) {
+    for (int i = tid; i < KP * (BN / 8); i += kThreads) {
       const int r = i / (BN / 8), c = (i % (BN / 8)) * 8;
       const long long p = pb + r;
       const int w = int(p % a.W), h = int((p / a.W) % a.H);
       const long long img = p / ((long long)a.W * a.H);
       const int hh = h + ky - 1, ww = w + kx - 1;
-      const bool ok = hh >= 0 && hh < a.H && ww >= 0 && ww < a.W;
-      const long long q = (img * a.H + (ok ? hh : 0)) * a.W + (ok ? ww : 0);
+      const bool ok = p < p_end && hh >= 0 && hh < a.H && ww >= 0 && ww < a.W;
+      const long long q = ok ? (img * a.H + hh) * a.W + ww : 0;
       cp_async16(&sB[buf][r][c], a.x + q * a.Cx + a.ci_off + n0 + c, ok ? 16 : 0);
     }
-    cp_async_commit();
   };
-  if (ksteps > 0) load(0, 0);
-  for (int ks = 0; ks < ksteps; ++ks) {
-    const int buf = ks & 1;
-    if (ks + 1 < ksteps) {
-      load(ks + 1, buf ^ 1);
-      cp_async_wait<1>();
-    } else {
-      cp_async_wait<0>();
-    }
-    __syncthreads();
-    uint32_t af[WM / 16][4], bfr[WN / 8][2];
+  // prologue: stages 0 .. S - 2 in flight (one commit group per stage, empty
+  // groups past the end keep the counting uniform)
 #pragma unroll
-    for (int mt = 0; mt < WM / 16; ++mt)
-      ldmatrix_x4_t(af[mt], &sA[buf][(lane & 7) + ((lane >> 4) << 3)]
-                                [wm * WM + mt * 16 + ((lane >> 3) & 1) * 8]);
-#pragma unroll
-    for (int nt = 0; nt < WN / 8; ++nt)
-      ldmatrix_x2_t(bfr[nt], &sB[buf][lane & 15][wn * WN + nt * 8]);
-#pragma unroll
-    for (int mt = 0; mt < WM / 16; ++mt)
-#pragma unroll
-      for (int nt = 0; nt < WN / 8; ++nt) mma_bf16(acc[mt][nt], af[mt], bfr[nt]);
-    __syncthreads();
+  for (int st = 0; st < S - 1; ++st) {
+    if (st < ksteps) load(st, st);
+    cp_async_commit();
   }
+  for (int ks = 0; ks < ksteps; ++ks) {
+    cp_async_wait<S - 2>();  // stage ks has landed
+    __syncthreads();         // ... for every thread, and stage ks - 1 is free
+    const int nxt = ks + S - 1;
+    if (nxt < ksteps) load(nxt, nxt % S);
+    cp_async_commit();
+    const int buf = ks % S;
+#pragma unroll
+    for (int kk = 0; kk < KP; kk += 16) {
+      uint32_t af[WM / 16][4], bfr[WN / 8][2];
+#pragma unroll
+      for (int mt = 0; mt < WM / 16; ++mt)
+        ldmatrix_x4_t(af[mt], &sA[buf][kk + (lane & 7) + ((lane >> 4) << 3)]
+                                  [wm * WM + mt * 16 + ((lane >> 3) & 1) * 8]);
+#pragma unroll
+      for (int nt = 0; nt < WN / 8; ++nt)
+        ldmatrix_x2_t(bfr[nt], &sB[buf][kk + (lane & 15)][wn * WN + nt * 8]);
+#pragma unroll
+      for (int mt = 0; mt < WM / 16; ++mt)
+#pragma unroll
+        for (int nt = 0; nt < WN / 8; ++nt) mma_bf16(acc[mt][nt], af[mt], bfr[nt]);
+    }
+  }
+  cp_async_wait<0>();
 #pragma unroll
   for (int mt = 0; mt < WM / 16; ++mt)
 #pragma unroll
@@ -502,6 +513,7 @@ int blocks_for(long long n) {
 
 cudaError_t conv3x3(const ConvArgs& a, cudaStream_t s) {
   if (a.head_done) *a.head_done = 0;
+  if (a.pool_done) *a.pool_done = 0;
   if (a.tensor_path && a.err && conv3x3_tc_supported(a)) return conv3x3_tc(a, a.err, s);
   if (a.W % 64 || a.Cin % 16 || a.Cx % 8 || a.Cy % 8 || a.ci_off % 8 || a.co_off % 8)
     return cudaErrorInvalidValue;
@@ -527,14 +539,18 @@ cudaError_t wgrad3x3(const WgradArgs& args, cudaStream_t s) {
     a.chunk = int((c + 15) / 16 * 16);
   }
   const int chunks = int((a.npix + a.chunk - 1) / a.chunk);
-  const dim3 grid_z(1, 1, unsigned(9 * chunks));
-  if (a.Cout % 64 == 0 && a.Cin % 32 == 0)
-    wgrad3x3_kernel<64, 32><<<dim3(a.Cout / 64, a.Cin / 32, grid_z.z), kThreads, 0, s>>>(a);
-  else if (a.Cin % 32 == 0)
-    wgrad3x3_kernel<32, 32><<<dim3(a.Cout / 32, a.Cin / 32, grid_z.z), kThreads, 0, s>>>(a);
-  else
-    wgrad3x3_kernel<32, 16><<<dim3(a.Cout / 32, a.Cin / 16, grid_z.z), kThreads, 0, s>>>(a);
-  return cudaGetLastError();
+  const unsigned gz = unsigned(9 * chunks);
+  constexpr int KP = 64, S = 4;
+  auto go = [&](auto kern, int bm, int bn) {
+    const int smem = S * KP * ((bm + 8) + (bn + 8)) * 2;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    kern<<<dim3(a.Cout / bm, a.Cin / bn, gz), kThreads, smem, s>>>(a);
+    return cudaGetLastError();
+  };
+  if (a.Cout % 64 == 0 && a.Cin % 32 == 0) return go(wgrad3x3_kernel<64, 32, KP, S>, 64, 32);
+  if (a.Cin % 32 == 0) return go(wgrad3x3_kernel<32, 32, KP, S>, 32, 32);
+  return go(wgrad3x3_kernel<32, 16, KP, S>, 32, 16);
 }
 
 bool v8(int a) { return a % 8 == 0; }

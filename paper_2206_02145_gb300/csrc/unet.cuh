@@ -60,6 +60,12 @@ struct ConvArgs {
   float* head_y;
   int head_out;
   int* head_done;
+  // optional 2 x 2 average pooling of the output (pool_y null: none), in the
+  // epilogue where the tiling allows (*pool_done = 1): pool_y
+  // [N][H/2][W/2][pool_Cy], channels pool_off .. pool_off + Cout
+  bf16* pool_y;
+  int pool_Cy, pool_off;
+  int* pool_done;
 };
 // requirements: W % 64 == 0, Cin % 16 == 0, Cout % 32 == 0, strides/offsets % 8 == 0
 cudaError_t conv3x3(const ConvArgs& a, cudaStream_t s);
