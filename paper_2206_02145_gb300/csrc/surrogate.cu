@@ -11,6 +11,7 @@
 //   head: 1x1 convolution (C0 -> out channels), FP32, predicting the residual
 // Activations and weights are bf16 (weights keep an FP32 master copy for
 // Adam); every GEMM accumulates in FP32.  Inputs are padded to 16 channels.
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -67,6 +68,8 @@ struct lbpf_unet {
   Act g_bottom;
   float *y = nullptr, *gy = nullptr, *loss = nullptr;
   unsigned* d_err = nullptr;  // bit 2: a tensor-core kernel timed out
+  float* wpart = nullptr;     // partial sums of the nine-tap weight gradient
+  size_t wpart_cap = 0;       // ... in floats
   int tensor_path = 1;        // convolutions on the tcgen05 kernel where possible
   // block propagator scratch (allocated on first use): network input x,
   // output y, current planes F (phi, U, ux, uy, rho), predicted planes F1
@@ -214,6 +217,8 @@ int conv_bwd(lbpf_unet* n, const ConvLayer& l, const Act& x, int xoff, const Act
   wa.H = x.h;
   wa.W = x.w;
   wa.chunk = 4096;
+  wa.part = n->wpart;
+  wa.part_cap = n->wpart_cap;
   UCK(n, lbk::nn::wgrad3x3(wa, n->stream));
   UCK(n, lbk::nn::bias_grad(g.p, g.c, goff, l.cout, npix, l.gb, n->stream));
   if (gx) {
@@ -668,6 +673,23 @@ lbpf_status lbpf_unet_create(const lbpf_unet_cfg* cfg, void* stream, lbpf_unet_t
   chk(dalloc(n, &n->gy, ny));
   chk(dalloc(n, &n->loss, 1));
   chk(dalloc(n, &n->d_err, 1));
+  {  // scratch of the nine-tap weight gradient: the largest layer's need
+    size_t need = 0;
+    auto take = [&](const ConvLayer& cl, int l) {
+      need = std::max(need, lbk::nn::wgrad_scratch(cl.cout, cl.cin, cfg->batch, n->H[l], n->W[l]));
+    };
+    for (int l = 0; l < L; ++l) {
+      take(n->enc_a[l], l);
+      take(n->enc_b[l], l);
+    }
+    for (int l = 0; l < L - 1; ++l) {
+      take(n->up[l], l);
+      take(n->dec_a[l], l);
+      take(n->dec_b[l], l);
+    }
+    if (need) chk(dalloc(n, &n->wpart, need));
+    n->wpart_cap = need;
+  }
   if (e != cudaSuccess) {
     fprintf(stderr, "lbpf_unet_create: %s\n", cudaGetErrorString(e));
     lbpf_unet_destroy(n);

@@ -206,6 +206,114 @@ __global__ void __launch_bounds__(kThreads) wgrad3x3_kernel(const WgradArgs a) {
       }
 }
 
+// Nine taps at once: a CTA owns a 32 x 32 (co, ci) tile of every tap and a
+// run of `chunk` pixel patches of 2 image rows x 64 pixels.  Per patch it
+// loads dy once ([128 px][32 co]) and x once as the patch with a one-pixel
+// halo ([4 rows][66 px][32 ci], zero fill outside the image), both by
+// cp.async into a double buffer; each K step of 16 pixels loads the dy
+// fragment once and multiplies it by the nine tap-shifted x fragments (the
+// shift is a row offset into the halo tile).  The nine 32 x 32 partial sums
+// go to part[(tile * nchunks + chunk) * 9 * 1024 + ...]; wgrad_reduce_kernel
+// adds them over the chunks into dw in a fixed order (no atomics).
+constexpr int kWP = 128;                  // pixels per patch (2 rows x 64)
+constexpr int kWHalo = 4 * 66;            // halo pixels per patch
+constexpr int kWLD = 40;                  // smem row pitch (32 channels + 8)
+
+__global__ void __launch_bounds__(kThreads) wgrad_taps_kernel(const WgradArgs a, int chunk,
+                                                              int nchunks, int patches) {
+  extern __shared__ __align__(16) unsigned char wt_smem[];
+  bf16(*sA)[kWP][kWLD] = reinterpret_cast<bf16(*)[kWP][kWLD]>(wt_smem);
+  bf16(*sB)[kWHalo][kWLD] = reinterpret_cast<bf16(*)[kWHalo][kWLD]>(wt_smem + 2 * kWP * kWLD * 2);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int wm = warp & 1, wn = warp >> 1;  // warp tile: 16 co x 16 ci
+  const int ntn = a.Cin / 32;
+  const int tile = blockIdx.x / nchunks, ck = blockIdx.x % nchunks;
+  const int m0 = (tile / ntn) * 32, n0 = (tile % ntn) * 32;
+  const int pbeg = ck * chunk;
+  const int pend = min(pbeg + chunk, patches);
+  const int pw = a.W / 64, ph = a.H / 2;  // patches per image row pair, per image column
+
+  float acc[9][2][4];
+#pragma unroll
+  for (int t = 0; t < 9; ++t)
+#pragma unroll
+    for (int j = 0; j < 2; ++j)
+#pragma unroll
+      for (int k = 0; k < 4; ++k) acc[t][j][k] = 0.f;
+
+  auto load = [&](int pt, int buf) {
+    const int img = pt / (pw * ph), r = pt % (pw * ph);
+    const int h0 = (r / pw) * 2, w0 = (r % pw) * 64;
+    for (int i = tid; i < kWP * 4; i += kThreads) {  // dy: 128 px x 4 x 8 channels
+      const int px = i >> 2, c = (i & 3) * 8;
+      const long long p = ((long long)img * a.H + h0 + (px >> 6)) * a.W + w0 + (px & 63);
+      cp_async16(&sA[buf][px][c], a.dy + p * a.Cdy + a.co_off + m0 + c, 16);
+    }
+    for (int i = tid; i < kWHalo * 4; i += kThreads) {  // x halo: 4 x 66 px x 4 x 8
+      const int hp = i >> 2, c = (i & 3) * 8;
+      const int hh = h0 - 1 + hp / 66, ww = w0 - 1 + hp % 66;
+      const bool ok = hh >= 0 && hh < a.H && ww >= 0 && ww < a.W;
+      const long long q = ok ? ((long long)img * a.H + hh) * a.W + ww : 0;
+      cp_async16(&sB[buf][hp][c], a.x + q * a.Cx + a.ci_off + n0 + c, ok ? 16 : 0);
+    }
+  };
+  if (pbeg < pend) load(pbeg, 0);
+  cp_async_commit();
+  for (int pt = pbeg; pt < pend; ++pt) {
+    const int buf = (pt - pbeg) & 1;
+    if (pt + 1 < pend) load(pt + 1, buf ^ 1);
+    cp_async_commit();
+    cp_async_wait<1>();  // patch pt has landed
+    __syncthreads();
+#pragma unroll 1
+    for (int ks = 0; ks < kWP / 16; ++ks) {
+      const int rr = ks >> 2, c0 = (ks & 3) * 16;  // row of the patch, first column
+      uint32_t af[4];
+      ldmatrix_x4_t(af, &sA[buf][ks * 16 + (lane & 7) + ((lane >> 4) << 3)]
+                             [wm * 16 + ((lane >> 3) & 1) * 8]);
+#pragma unroll
+      for (int t = 0; t < 9; ++t) {
+        const int ky = t / 3, kx = t % 3;
+        const int hrow = (rr + ky) * 66 + c0 + kx;  // halo pixel of the first of the 16
+#pragma unroll
+        for (int nt = 0; nt < 2; ++nt) {
+          uint32_t bfr[2];
+          ldmatrix_x2_t(bfr, &sB[buf][hrow + (lane & 15)][wn * 16 + nt * 8]);
+          mma_bf16(acc[t][nt], af, bfr);
+        }
+      }
+    }
+    __syncthreads();  // buffer buf is free for the load two patches on
+  }
+  float* out = a.part + (size_t(tile) * nchunks + ck) * 9 * 1024;
+#pragma unroll
+  for (int t = 0; t < 9; ++t)
+#pragma unroll
+    for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int co = wm * 16 + (lane >> 2) + (k >> 1) * 8;
+        const int ci = wn * 16 + nt * 8 + (lane & 3) * 2 + (k & 1);
+        out[t * 1024 + co * 32 + ci] = acc[t][nt][k];
+      }
+}
+
+// dw[tap][co][ci] += sum over the chunks of the nine-tap kernel's partials
+__global__ void wgrad_reduce_kernel(const float* part, int nchunks, int ntiles, int ntn, int Cout,
+                                    int Cin, float* dw) {
+  const long long n = (long long)ntiles * 9 * 1024;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int tile = int(i / (9 * 1024)), r = int(i % (9 * 1024));
+    const int t = r / 1024, co = (tile / ntn) * 32 + (r % 1024) / 32,
+              ci = (tile % ntn) * 32 + r % 32;
+    const float* p = part + size_t(tile) * nchunks * 9 * 1024 + r;
+    float s = 0.f;
+    for (int c = 0; c < nchunks; ++c) s += p[size_t(c) * 9 * 1024];
+    dw[(size_t(t) * Cout + co) * Cin + ci] += s;
+  }
+}
+
 // ---- element-wise kernels -------------------------------------------------------------
 // All of them move 8 channels (16 bytes) per thread and iteration; channel
 // counts, strides and offsets are multiples of 8.
@@ -528,8 +636,49 @@ cudaError_t conv3x3(const ConvArgs& a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// the nine-tap kernel's launch shape: 32 x 32 tiles, pixel patches per CTA
+// chosen for about four CTAs per SM
+namespace {
+struct TapsShape {
+  int ntiles, ntn, patches, chunk, nchunks;
+};
+bool taps_shape(int Cout, int Cin, int N, int H, int W, TapsShape* t) {
+  if (Cout % 32 || Cin % 32 || W % 64 || H % 2) return false;
+  t->ntn = Cin / 32;
+  t->ntiles = (Cout / 32) * t->ntn;
+  t->patches = N * (H / 2) * (W / 64);
+  const long long want = 4 * 152;
+  t->chunk = int((t->patches * (long long)t->ntiles + want - 1) / want);
+  if (t->chunk < 1) t->chunk = 1;
+  t->nchunks = (t->patches + t->chunk - 1) / t->chunk;
+  return true;
+}
+}  // namespace
+
+size_t wgrad_scratch(int Cout, int Cin, int N, int H, int W) {
+  TapsShape t;
+  if (!taps_shape(Cout, Cin, N, H, W, &t)) return 0;
+  return size_t(t.ntiles) * t.nchunks * 9 * 1024;
+}
+
 cudaError_t wgrad3x3(const WgradArgs& args, cudaStream_t s) {
   WgradArgs a = args;
+  TapsShape ts;
+  const int N = int(a.npix / ((long long)a.H * a.W));
+  if (a.part && taps_shape(a.Cout, a.Cin, N, a.H, a.W, &ts) &&
+      size_t(ts.ntiles) * ts.nchunks * 9 * 1024 <= a.part_cap && a.Cdy % 8 == 0 &&
+      a.Cx % 8 == 0 && a.co_off % 8 == 0 && a.ci_off % 8 == 0) {
+    const int smem = 2 * (kWP + kWHalo) * kWLD * 2;
+    cudaError_t e =
+        cudaFuncSetAttribute(wgrad_taps_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    wgrad_taps_kernel<<<ts.ntiles * ts.nchunks, kThreads, smem, s>>>(a, ts.chunk, ts.nchunks,
+                                                                      ts.patches);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    wgrad_reduce_kernel<<<blocks_for((long long)ts.ntiles * 9 * 1024), 256, 0, s>>>(
+        a.part, ts.nchunks, ts.ntiles, ts.ntn, a.Cout, a.Cin, a.dw);
+    return cudaGetLastError();
+  }
   if (a.W % 16 || a.Cout % 32 || a.Cin % 16 || a.chunk < 16 || a.chunk % 16)
     return cudaErrorInvalidValue;
   // grid z = 9 x chunks must stay within 65535: enlarge the chunk if needed

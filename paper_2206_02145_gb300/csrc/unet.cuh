@@ -6,38 +6,18 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include "pdl.cuh"
+
 namespace lbk {
 namespace nn {
 
 using bf16 = __nv_bfloat16;
 
-// Programmatic dependent launch between the network's kernels: a kernel
-// launched by launch_pdl may be scheduled (and run its prologue: barrier
-// set-up, tensor-memory allocation) while the kernel before it on the stream
-// finishes.  Each such kernel signals pdl_trigger() at its start and calls
-// pdl_wait() before its first access to global memory; pdl_wait returns once
-// the kernel before it has completed and its writes are visible.  Without the
-// launch attribute both are no-ops.
-__device__ __forceinline__ void pdl_trigger() {
-  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-}
-__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
-
-template <typename... KArgs, typename... Args>
-inline cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem,
-                              cudaStream_t s, Args... args) {
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = grid;
-  cfg.blockDim = block;
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = s;
-  cudaLaunchAttribute at[1];
-  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  at[0].val.programmaticStreamSerializationAllowed = 1;
-  cfg.attrs = at;
-  cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, kern, args...);
-}
+// the network's kernels follow one another with programmatic dependent
+// launch (pdl.cuh)
+using lbk::launch_pdl;
+using lbk::pdl_trigger;
+using lbk::pdl_wait;
 
 struct ConvArgs {
   const bf16* x;   // [N][H][W][Cx], channels ci_off .. ci_off + Cin
@@ -79,12 +59,19 @@ struct WgradArgs {
   int Cx, ci_off, Cin;
   const bf16* dy;  // gradient of the layer's pre-activation [N][H][W][Cdy], channels co_off..
   int Cdy, co_off, Cout;
-  float* dw;       // [9][Cout][Cin] FP32, accumulated with atomics
+  float* dw;       // [9][Cout][Cin] FP32, accumulated (+=)
   long long npix;  // N * H * W
   int H, W;
-  int chunk;       // pixels per CTA (multiple of 16)
+  int chunk;       // pixels per CTA (multiple of 16) of the per-tap kernel
+  // scratch for the nine-tap kernel's partial sums (floats), owned by the
+  // caller; too small or null: the per-tap kernel with atomics runs instead
+  float* part;
+  size_t part_cap;
 };
 cudaError_t wgrad3x3(const WgradArgs& a, cudaStream_t s);
+// floats of scratch the nine-tap weight-gradient kernel needs for a layer
+// (0 where its shape does not allow that kernel)
+size_t wgrad_scratch(int Cout, int Cin, int N, int H, int W);
 
 cudaError_t bias_grad(const bf16* g, int Cg, int off, int C, long long npix, float* db,
                       cudaStream_t s);
