@@ -298,19 +298,33 @@ __global__ void __launch_bounds__(kThreads) wgrad_taps_kernel(const WgradArgs a,
       }
 }
 
-// dw[tap][co][ci] += sum over the chunks of the nine-tap kernel's partials
-__global__ void wgrad_reduce_kernel(const float* part, int nchunks, int ntiles, int ntn, int Cout,
-                                    int Cin, float* dw) {
+// dw[tap][co][ci] += sum over the chunks of the nine-tap kernel's partials.
+// A block takes 32 consecutive partial entries; its 8 warps sum every 8th
+// chunk each (lane = entry, 128-byte rows), then warp 0 adds the 8 warp sums
+// in a fixed order: deterministic, no atomics.
+__global__ void __launch_bounds__(256) wgrad_reduce_kernel(const float* part, int nchunks,
+                                                           int ntiles, int ntn, int Cout,
+                                                           int Cin, float* dw) {
+  __shared__ float red[8][32];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const long long n = (long long)ntiles * 9 * 1024;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-       i += (long long)gridDim.x * blockDim.x) {
+  for (long long base = (long long)blockIdx.x * 32; base < n; base += (long long)gridDim.x * 32) {
+    const long long i = base + lane;  // n is a multiple of 32
     const int tile = int(i / (9 * 1024)), r = int(i % (9 * 1024));
-    const int t = r / 1024, co = (tile / ntn) * 32 + (r % 1024) / 32,
-              ci = (tile % ntn) * 32 + r % 32;
     const float* p = part + size_t(tile) * nchunks * 9 * 1024 + r;
     float s = 0.f;
-    for (int c = 0; c < nchunks; ++c) s += p[size_t(c) * 9 * 1024];
-    dw[(size_t(t) * Cout + co) * Cin + ci] += s;
+    for (int c = warp; c < nchunks; c += 8) s += p[size_t(c) * 9 * 1024];
+    red[warp][lane] = s;
+    __syncthreads();
+    if (warp == 0) {
+      float t = 0.f;
+#pragma unroll
+      for (int w = 0; w < 8; ++w) t += red[w][lane];
+      const int tp = r / 1024, co = (tile / ntn) * 32 + (r % 1024) / 32,
+                ci = (tile % ntn) * 32 + r % 32;
+      dw[(size_t(tp) * Cout + co) * Cin + ci] += t;
+    }
+    __syncthreads();
   }
 }
 
@@ -357,14 +371,17 @@ __global__ void bias_grad_kernel(const bf16* g, int Cg, int off, int C, long lon
 #pragma unroll
   for (int i = 0; i < 8; ++i) red[threadIdx.x][i] = acc[i];
   __syncthreads();
-  if (threadIdx.x < groups) {
-    float s[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    for (int l = 0; l < lanes; ++l)
+  // tree over the pixel lanes (a power of two, set by the launcher), then one
+  // atomic per value
+  for (int half = lanes / 2; half > 0; half /= 2) {
+    if (pl < half)
 #pragma unroll
-      for (int i = 0; i < 8; ++i) s[i] += red[l * groups + threadIdx.x][i];
-#pragma unroll
-    for (int i = 0; i < 8; ++i) atomicAdd(db + threadIdx.x * 8 + i, s[i]);
+      for (int i = 0; i < 8; ++i) red[threadIdx.x][i] += red[threadIdx.x + half * groups][i];
+    __syncthreads();
   }
+  if (threadIdx.x < groups)
+#pragma unroll
+    for (int i = 0; i < 8; ++i) atomicAdd(db + threadIdx.x * 8 + i, red[threadIdx.x][i]);
 }
 
 // g = 0 where act <= 0
@@ -675,7 +692,8 @@ cudaError_t wgrad3x3(const WgradArgs& args, cudaStream_t s) {
     wgrad_taps_kernel<<<ts.ntiles * ts.nchunks, kThreads, smem, s>>>(a, ts.chunk, ts.nchunks,
                                                                       ts.patches);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    wgrad_reduce_kernel<<<blocks_for((long long)ts.ntiles * 9 * 1024), 256, 0, s>>>(
+    const long long groups = (long long)ts.ntiles * 9 * 1024 / 32;
+    wgrad_reduce_kernel<<<unsigned(groups < 152 * 16 ? groups : 152 * 16), 256, 0, s>>>(
         a.part, ts.nchunks, ts.ntiles, ts.ntn, a.Cout, a.Cin, a.dw);
     return cudaGetLastError();
   }
@@ -707,7 +725,10 @@ bool v8(int a) { return a % 8 == 0; }
 cudaError_t bias_grad(const bf16* g, int Cg, int off, int C, long long npix, float* db,
                       cudaStream_t s) {
   if (!v8(C) || !v8(Cg) || !v8(off) || C > 2048) return cudaErrorInvalidValue;
-  const int groups = C / 8, lanes = 256 / groups > 0 ? 256 / groups : 1;
+  // pixel lanes per block: a power of two (the kernel's tree reduction)
+  const int groups = C / 8;
+  int lanes = 1;
+  while (lanes * 2 * groups <= 256) lanes *= 2;
   long long blocks = (npix + lanes * 16 - 1) / (lanes * 16);
   if (blocks > 152 * 8) blocks = 152 * 8;
   if (blocks < 1) blocks = 1;
