@@ -670,6 +670,7 @@ def main():
         # the same instances stepped one after another (each its own graph),
         # against the single batched launch per step
         kseq = max(64, min(args.steps, 640) // 64 * 64)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         for s_ in sims:
             s_.step(64)
         torch.cuda.synchronize()

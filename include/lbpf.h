@@ -499,6 +499,8 @@ typedef struct {
   double max_iface_err;      /* largest judged interface error (lattice units) */
   double max_iface_est;      /* largest per-block interface error estimate committed */
   double iface_acc;          /* accumulated estimate at the end of the call (largest ray) */
+  double max_drift_committed; /* largest drift among the blocks the network advanced
+                                 (at most drift_tol: a larger one falls back to the LB) */
 } lbpf_surrogate_report;
 
 /* The network input of the current state: device FP32 [ny][nx][4]. */

@@ -105,7 +105,8 @@ class lbpf_surrogate_report(ctypes.Structure):
     _fields_ = [("blocks", ctypes.c_int64), ("surrogate_blocks", ctypes.c_int64),
                 ("judged_blocks", ctypes.c_int64), ("fallback_blocks", ctypes.c_int64),
                 ("max_drift", ctypes.c_double), ("max_iface_err", ctypes.c_double),
-                ("max_iface_est", ctypes.c_double), ("iface_acc", ctypes.c_double)]
+                ("max_iface_est", ctypes.c_double), ("iface_acc", ctypes.c_double),
+                ("max_drift_committed", ctypes.c_double)]
 
 
 EXPORTED = ("lbpf_params_default", "lbpf_create", "lbpf_init_seed", "lbpf_init_fields",

@@ -70,6 +70,12 @@ struct lbpf_unet {
   unsigned* d_err = nullptr;  // bit 2: a tensor-core kernel timed out
   float* wpart = nullptr;     // partial sums of the nine-tap weight gradient
   size_t wpart_cap = 0;       // ... in floats
+  // tables of the one-launch Adam step (every parameter tensor) and
+  // flip-transpose (every convolution), in device memory
+  lbk::nn::AdamSeg* adam_segs = nullptr;
+  lbk::nn::FlipSeg* flip_segs = nullptr;
+  int n_adam = 0, n_flip = 0;
+  long long adam_blocks = 0, flip_blocks = 0;
   int tensor_path = 1;        // convolutions on the tcgen05 kernel where possible
   // block propagator scratch (allocated on first use): network input x,
   // output y, current planes F (phi, U, ux, uy, rho), predicted planes F1
@@ -213,14 +219,14 @@ int conv_bwd(lbpf_unet* n, const ConvLayer& l, const Act& x, int xoff, const Act
   wa.co_off = goff;
   wa.Cout = l.cout;
   wa.dw = l.gw;
+  wa.db = l.gb;
   wa.npix = npix;
   wa.H = x.h;
   wa.W = x.w;
   wa.chunk = 4096;
   wa.part = n->wpart;
   wa.part_cap = n->wpart_cap;
-  UCK(n, lbk::nn::wgrad3x3(wa, n->stream));
-  UCK(n, lbk::nn::bias_grad(g.p, g.c, goff, l.cout, npix, l.gb, n->stream));
+  UCK(n, lbk::nn::wgrad3x3(wa, n->stream));  // weight and bias gradients
   if (gx) {
     lbk::nn::ConvArgs a{};
     a.x = g.p;
@@ -297,8 +303,7 @@ int backward(lbpf_unet* n, const float* t) {
   const int L = n->L, B = n->cfg.batch;
   const long long npix = (long long)B * n->H[0] * n->W[0];
   int rc;
-  for (ConvLayer* l : all_layers(n))
-    UCK(n, lbk::nn::flip_transpose(l->wb, l->wt, l->cout, l->cin, n->stream));
+  UCK(n, lbk::nn::flip_multi(n->flip_segs, n->n_flip, n->flip_blocks, n->stream));
   UCK(n, cudaMemsetAsync(n->loss, 0, sizeof(float), n->stream));
   UCK(n, lbk::nn::mse(n->y, t, npix * n->cfg.out_ch, n->gy, n->loss, n->stream));
   const Act& top = L > 1 ? n->db[0] : n->bottom;
@@ -359,19 +364,40 @@ int check_err(lbpf_unet* n) {
 
 int adam_all(lbpf_unet* n, float lr) {
   ++n->t;
-  const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
-  for (ConvLayer* l : all_layers(n)) {
-    UCK(n, lbk::nn::adam(l->w, l->gw, l->mw, l->vw, l->wb, (long long)l->nw, lr, b1, b2, eps, n->t,
-                         n->stream));
-    UCK(n, lbk::nn::adam(l->b, l->gb, l->mb, l->vb, nullptr, l->cout, lr, b1, b2, eps, n->t,
-                         n->stream));
-  }
-  const long long nh = (long long)n->cfg.out_ch * n->C[0];
-  UCK(n, lbk::nn::adam(n->hw, n->ghw, n->mhw, n->vhw, nullptr, nh, lr, b1, b2, eps, n->t,
-                       n->stream));
-  UCK(n, lbk::nn::adam(n->hb, n->ghb, n->mhb, n->vhb, nullptr, n->cfg.out_ch, lr, b1, b2, eps,
-                       n->t, n->stream));
+  UCK(n, lbk::nn::adam_multi(n->adam_segs, n->n_adam, n->adam_blocks, lr, 0.9f, 0.999f, 1e-8f,
+                             n->t, n->stream));
   return LBPF_OK;
+}
+
+// the device tables of adam_all and of the weights' flip-transpose
+cudaError_t build_seg_tables(lbpf_unet* n) {
+  using lbk::nn::kSegBlock;
+  std::vector<lbk::nn::AdamSeg> as;
+  std::vector<lbk::nn::FlipSeg> fs;
+  long long ab = 0, fb = 0;
+  auto add = [&](float* w, float* g, float* m, float* v, bf16* wb, long long cnt) {
+    as.push_back({w, g, m, v, wb, cnt, ab});
+    ab += (cnt + kSegBlock - 1) / kSegBlock;
+  };
+  for (ConvLayer* l : all_layers(n)) {
+    add(l->w, l->gw, l->mw, l->vw, l->wb, (long long)l->nw);
+    add(l->b, l->gb, l->mb, l->vb, nullptr, l->cout);
+    fs.push_back({l->wb, l->wt, l->cout, l->cin, fb});
+    fb += (9LL * l->cout * l->cin + kSegBlock - 1) / kSegBlock;
+  }
+  add(n->hw, n->ghw, n->mhw, n->vhw, nullptr, (long long)n->cfg.out_ch * n->C[0]);
+  add(n->hb, n->ghb, n->mhb, n->vhb, nullptr, n->cfg.out_ch);
+  cudaError_t e = dalloc(n, &n->adam_segs, as.size());
+  if (e == cudaSuccess) e = dalloc(n, &n->flip_segs, fs.size());
+  if (e == cudaSuccess)
+    e = cudaMemcpy(n->adam_segs, as.data(), as.size() * sizeof(as[0]), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(n->flip_segs, fs.data(), fs.size() * sizeof(fs[0]), cudaMemcpyHostToDevice);
+  n->n_adam = int(as.size());
+  n->n_flip = int(fs.size());
+  n->adam_blocks = ab;
+  n->flip_blocks = fb;
+  return e;
 }
 
 // pack FP32 NHWC (in_ch <= 16) into the bf16 16-channel input buffer: one
@@ -690,6 +716,7 @@ lbpf_status lbpf_unet_create(const lbpf_unet_cfg* cfg, void* stream, lbpf_unet_t
     if (need) chk(dalloc(n, &n->wpart, need));
     n->wpart_cap = need;
   }
+  chk(build_seg_tables(n));
   if (e != cudaSuccess) {
     fprintf(stderr, "lbpf_unet_create: %s\n", cudaGetErrorString(e));
     lbpf_unet_destroy(n);
@@ -1067,6 +1094,7 @@ lbpf_status lbpf_surrogate_advance(lbpf_t* h, lbpf_unet_t* net, const lbpf_surro
       h->step += nb;
       for (int k = 0; k < 4; ++k) acc[k] = cand[k];
       r.max_iface_est = std::fmax(r.max_iface_est, est);
+      r.max_drift_committed = std::fmax(r.max_drift_committed, drift);
       r.iface_acc = est_acc;
       ++r.surrogate_blocks;
     }

@@ -213,14 +213,18 @@ __global__ void __launch_bounds__(kThreads) wgrad3x3_kernel(const WgradArgs a) {
 // cp.async into a double buffer; each K step of 16 pixels loads the dy
 // fragment once and multiplies it by the nine tap-shifted x fragments (the
 // shift is a row offset into the halo tile).  The nine 32 x 32 partial sums
-// go to part[(tile * nchunks + chunk) * 9 * 1024 + ...]; wgrad_reduce_kernel
-// adds them over the chunks into dw in a fixed order (no atomics).
+// go to part[(tile * nchunks + chunk) * 9 * 1024 + ...].  The CTAs of the
+// first input-channel tile (n0 = 0) also sum dy over their pixels, the bias
+// gradient's partial, into part[bias_off + (co_tile * nchunks + chunk) * 32
+// + co].  wgrad_reduce_kernel adds both over the chunks into dw and db in a
+// fixed order (no atomics, so the result does not depend on the schedule).
 constexpr int kWP = 128;                  // pixels per patch (2 rows x 64)
 constexpr int kWHalo = 4 * 66;            // halo pixels per patch
 constexpr int kWLD = 40;                  // smem row pitch (32 channels + 8)
 
 __global__ void __launch_bounds__(kThreads) wgrad_taps_kernel(const WgradArgs a, int chunk,
-                                                              int nchunks, int patches) {
+                                                              int nchunks, int patches,
+                                                              size_t bias_off) {
   extern __shared__ __align__(16) unsigned char wt_smem[];
   bf16(*sA)[kWP][kWLD] = reinterpret_cast<bf16(*)[kWP][kWLD]>(wt_smem);
   bf16(*sB)[kWHalo][kWLD] = reinterpret_cast<bf16(*)[kWHalo][kWLD]>(wt_smem + 2 * kWP * kWLD * 2);
@@ -241,6 +245,9 @@ __global__ void __launch_bounds__(kThreads) wgrad_taps_kernel(const WgradArgs a,
 #pragma unroll
       for (int k = 0; k < 4; ++k) acc[t][j][k] = 0.f;
 
+  // bias partial: thread (co pair tid & 15, pixel group tid >> 4 of 16 pixels)
+  const bool with_bias = a.db != nullptr && n0 == 0;
+  float bsum0 = 0.f, bsum1 = 0.f;
   auto load = [&](int pt, int buf) {
     const int img = pt / (pw * ph), r = pt % (pw * ph);
     const int h0 = (r / pw) * 2, w0 = (r % pw) * 64;
@@ -265,6 +272,16 @@ __global__ void __launch_bounds__(kThreads) wgrad_taps_kernel(const WgradArgs a,
     cp_async_commit();
     cp_async_wait<1>();  // patch pt has landed
     __syncthreads();
+    if (with_bias) {
+      const int cp = tid & 15, pg = tid >> 4;
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        const __nv_bfloat162 v =
+            *reinterpret_cast<const __nv_bfloat162*>(&sA[buf][pg * 16 + i][cp * 2]);
+        bsum0 += __low2float(v);
+        bsum1 += __high2float(v);
+      }
+    }
 #pragma unroll 1
     for (int ks = 0; ks < kWP / 16; ++ks) {
       const int rr = ks >> 2, c0 = (ks & 3) * 16;  // row of the patch, first column
@@ -296,33 +313,63 @@ __global__ void __launch_bounds__(kThreads) wgrad_taps_kernel(const WgradArgs a,
         const int ci = wn * 16 + nt * 8 + (lane & 3) * 2 + (k & 1);
         out[t * 1024 + co * 32 + ci] = acc[t][nt][k];
       }
+  if (with_bias) {  // the 8 pixel groups' sums in a fixed order (patch buffers are free)
+    float* red = reinterpret_cast<float*>(wt_smem);
+    red[(tid >> 4) * 32 + (tid & 15) * 2] = bsum0;
+    red[(tid >> 4) * 32 + (tid & 15) * 2 + 1] = bsum1;
+    __syncthreads();
+    if (tid < 32) {
+      float t = 0.f;
+#pragma unroll
+      for (int g = 0; g < 8; ++g) t += red[g * 32 + tid];
+      a.part[bias_off + (size_t(tile / ntn) * nchunks + ck) * 32 + tid] = t;
+    }
+  }
 }
 
-// dw[tap][co][ci] += sum over the chunks of the nine-tap kernel's partials.
-// A block takes 32 consecutive partial entries; its 8 warps sum every 8th
-// chunk each (lane = entry, 128-byte rows), then warp 0 adds the 8 warp sums
-// in a fixed order: deterministic, no atomics.
-__global__ void __launch_bounds__(256) wgrad_reduce_kernel(const float* part, int nchunks,
-                                                           int ntiles, int ntn, int Cout,
-                                                           int Cin, float* dw) {
+// dw[tap][co][ci] += sum over the chunks of the nine-tap kernel's partials,
+// and db[co] += sum over the chunks of its bias partials (entries n .. n +
+// Cout of the loop).  A block takes 32 consecutive entries; its 8 warps sum
+// every 8th chunk each (lane = entry, 128-byte rows), then warp 0 adds the 8
+// warp sums in a fixed order: deterministic, no atomics.
+__global__ void __launch_bounds__(256) wgrad_reduce_kernel(const float* part, size_t bias_off,
+                                                           int nchunks, int ntiles, int ntn,
+                                                           int Cout, int Cin, float* dw,
+                                                           float* db) {
   __shared__ float red[8][32];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const long long n = (long long)ntiles * 9 * 1024;
-  for (long long base = (long long)blockIdx.x * 32; base < n; base += (long long)gridDim.x * 32) {
-    const long long i = base + lane;  // n is a multiple of 32
-    const int tile = int(i / (9 * 1024)), r = int(i % (9 * 1024));
-    const float* p = part + size_t(tile) * nchunks * 9 * 1024 + r;
+  const long long total = n + (db ? Cout : 0);
+  for (long long base = (long long)blockIdx.x * 32; base < total;
+       base += (long long)gridDim.x * 32) {
+    const long long i = base + lane;  // n and Cout are multiples of 32
+    const float* p;
+    size_t stride;
+    if (base < n) {
+      const int tile = int(i / (9 * 1024)), r = int(i % (9 * 1024));
+      p = part + size_t(tile) * nchunks * 9 * 1024 + r;
+      stride = 9 * 1024;
+    } else {
+      const int co = int(i - n);
+      p = part + bias_off + size_t(co >> 5) * nchunks * 32 + (co & 31);
+      stride = 32;
+    }
     float s = 0.f;
-    for (int c = warp; c < nchunks; c += 8) s += p[size_t(c) * 9 * 1024];
+    for (int c = warp; c < nchunks; c += 8) s += p[size_t(c) * stride];
     red[warp][lane] = s;
     __syncthreads();
     if (warp == 0) {
       float t = 0.f;
 #pragma unroll
       for (int w = 0; w < 8; ++w) t += red[w][lane];
-      const int tp = r / 1024, co = (tile / ntn) * 32 + (r % 1024) / 32,
-                ci = (tile % ntn) * 32 + r % 32;
-      dw[(size_t(tp) * Cout + co) * Cin + ci] += t;
+      if (base < n) {
+        const int tile = int(i / (9 * 1024)), r = int(i % (9 * 1024));
+        const int tp = r / 1024, co = (tile / ntn) * 32 + (r % 1024) / 32,
+                  ci = (tile % ntn) * 32 + r % 32;
+        dw[(size_t(tp) * Cout + co) * Cin + ci] += t;
+      } else {
+        db[i - n] += t;
+      }
     }
     __syncthreads();
   }
@@ -362,6 +409,7 @@ __global__ void bias_grad_kernel(const bf16* g, int Cg, int off, int C, long lon
   const int cg = threadIdx.x % groups, pl = threadIdx.x / groups;
   float acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   if (pl < lanes)
+#pragma unroll 4
     for (long long p = (long long)blockIdx.x * lanes + pl; p < npix; p += (long long)gridDim.x * lanes) {
       float f[8];
       unpack8(ld8(g + p * Cg + off + cg * 8), f);
@@ -536,45 +584,51 @@ __global__ void head_fwd_kernel(const bf16* x, int C, const float* w, const floa
 // head gradient for a tile of 256 pixels per block: gx = (gy w) * (x > 0)
 // (bf16, one pixel per thread); dw[o][c] += sum_p gy[p][o] x[p][c] and
 // db[o] += sum_p gy[p][o] from the tile staged in shared memory
-__global__ void head_bwd_kernel(const bf16* x, int C, const float* w, const float* gy, int O,
-                                long long npix, bf16* gx, float* dw, float* db) {
-  __shared__ float sx[256][33];
-  __shared__ float sg[256][8];
-  __shared__ float sw[8 * 32];
-  for (int i = threadIdx.x; i < O * C; i += blockDim.x) sw[i] = w[i];
-  for (long long base = (long long)blockIdx.x * 256; base < npix; base += (long long)gridDim.x * 256) {
-    __syncthreads();
-    const long long p = base + threadIdx.x;
-    const bool in = p < npix;
-    for (int c = 0; c < C; c += 8) {
-      float f[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-      if (in) unpack8(ld8(x + p * C + c), f);
+// head backward: gx[p][c] = (x[p][c] > 0) sum_o gy[p][o] w[o][c],
+// dw[o][c] += sum_p gy[p][o] x[p][c], db[o] += sum_p gy[p][o].  A warp walks
+// pixels one at a time with lane c on channel c (C <= 32), so every access of
+// x and gx is one coalesced row and gy is a broadcast; the 8 warps' sums meet
+// in shared memory in a fixed order, then one atomic per value and block.
+template <int O>
+__global__ void __launch_bounds__(256) head_bwd_kernel(const bf16* x, int C, const float* w,
+                                                       const float* gy, long long npix, bf16* gx,
+                                                       float* dw, float* db) {
+  __shared__ float red[8][O][33];  // per warp: dw[o][c] at [o][c], db[o] at [o][32]
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const bool on = lane < C;
+  float wl[O], acc[O], accb[O];
 #pragma unroll
-      for (int k = 0; k < 8; ++k) sx[threadIdx.x][c + k] = f[k];
+  for (int o = 0; o < O; ++o) {
+    wl[o] = on ? w[o * C + lane] : 0.f;
+    acc[o] = accb[o] = 0.f;
+  }
+  const long long stride = (long long)gridDim.x * 8;
+#pragma unroll 4
+  for (long long p = (long long)blockIdx.x * 8 + warp; p < npix; p += stride) {
+    const float xv = on ? __bfloat162float(x[p * C + lane]) : 0.f;
+    float s = 0.f;
+#pragma unroll
+    for (int o = 0; o < O; ++o) {
+      const float g = gy[p * O + o];
+      s += g * wl[o];
+      acc[o] += g * xv;
+      accb[o] += g;
     }
-    for (int o = 0; o < O; ++o) sg[threadIdx.x][o] = in ? gy[p * O + o] : 0.f;
-    if (in)
-      for (int c = 0; c < C; c += 8) {
-        float f[8];
+    if (on) gx[p * C + lane] = __float2bfloat16(xv > 0.f ? s : 0.f);
+  }
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
-          float s = 0.f;
-          for (int o = 0; o < O; ++o) s += sg[threadIdx.x][o] * sw[o * C + c + k];
-          f[k] = sx[threadIdx.x][c + k] > 0.f ? s : 0.f;
-        }
-        st8(gx + p * C + c, pack8(f));
-      }
-    __syncthreads();
-    if (threadIdx.x < O * C) {
-      const int o = threadIdx.x / C, c = threadIdx.x % C;
-      float s = 0.f;
-      for (int r = 0; r < 256; ++r) s += sg[r][o] * sx[r][c];
-      atomicAdd(dw + threadIdx.x, s);
-    } else if (threadIdx.x >= 128 && threadIdx.x < 128 + O) {
-      const int o = threadIdx.x - 128;
-      float s = 0.f;
-      for (int r = 0; r < 256; ++r) s += sg[r][o];
-      atomicAdd(db + o, s);
+  for (int o = 0; o < O; ++o) {
+    red[warp][o][lane] = acc[o];
+    if (lane == 0) red[warp][o][32] = accb[o];
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < O * 33; i += blockDim.x) {
+    const int o = i / 33, c = i % 33;
+    if (c < C || c == 32) {
+      float t = 0.f;
+#pragma unroll
+      for (int k = 0; k < 8; ++k) t += red[k][o][c];
+      atomicAdd(c == 32 ? db + o : dw + o * C + c, t);
     }
   }
 }
@@ -600,32 +654,56 @@ __global__ void mse_kernel(const float* y, const float* t, long long n, float* g
   }
 }
 
-// Adam with bias correction; refreshes the bf16 copy and clears the gradient
-__global__ void adam_kernel(float* w, float* g, float* m, float* v, bf16* wb, long long n,
-                            float lr, float b1, float b2, float eps, float c1, float c2) {
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-       i += (long long)gridDim.x * blockDim.x) {
-    const float gi = g[i];
-    const float mi = b1 * m[i] + (1.f - b1) * gi;
-    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
-    m[i] = mi;
-    v[i] = vi;
-    const float wi = w[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
-    w[i] = wi;
-    if (wb) wb[i] = __float2bfloat16(wi);
-    g[i] = 0.f;
+// the table entry of block b: the last segment whose first block is <= b
+template <typename Seg>
+__device__ __forceinline__ const Seg& seg_of(const Seg* segs, int nseg, long long b) {
+  int lo = 0, hi = nseg - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (segs[mid].blk0 <= b) lo = mid;
+    else hi = mid - 1;
+  }
+  return segs[lo];
+}
+
+// Adam with bias correction over every parameter tensor of the network in one
+// launch: each block updates kSegBlock consecutive values of one tensor,
+// refreshes their bf16 copy and clears their gradient
+__global__ void __launch_bounds__(256) adam_multi_kernel(const AdamSeg* segs, int nseg, float lr,
+                                                         float b1, float b2, float eps, float c1,
+                                                         float c2) {
+  const AdamSeg sg = seg_of(segs, nseg, blockIdx.x);
+  const long long i0 = (blockIdx.x - sg.blk0) * (long long)kSegBlock;
+#pragma unroll
+  for (int k = 0; k < kSegBlock / 256; ++k) {
+    const long long i = i0 + k * 256 + threadIdx.x;
+    if (i >= sg.n) break;
+    const float gi = sg.g[i];
+    const float mi = b1 * sg.m[i] + (1.f - b1) * gi;
+    const float vi = b2 * sg.v[i] + (1.f - b2) * gi * gi;
+    sg.m[i] = mi;
+    sg.v[i] = vi;
+    const float wi = sg.w[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    sg.w[i] = wi;
+    if (sg.wb) sg.wb[i] = __float2bfloat16(wi);
+    sg.g[i] = 0.f;
   }
 }
 
-// wt[8 - tap][ci][co] = w[tap][co][ci]: the weights of the data gradient
-__global__ void flip_transpose_kernel(const bf16* w, bf16* wt, int Cout, int Cin) {
-  const long long n = 9LL * Cout * Cin;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-       i += (long long)gridDim.x * blockDim.x) {
-    const int ci = int(i % Cin);
-    const int co = int((i / Cin) % Cout);
-    const int tap = int(i / ((long long)Cin * Cout));
-    wt[(size_t(8 - tap) * Cin + ci) * Cout + co] = w[i];
+// wt[8 - tap][ci][co] = w[tap][co][ci] (the weights of the data gradient) for
+// every convolution of the network in one launch
+__global__ void __launch_bounds__(256) flip_multi_kernel(const FlipSeg* segs, int nseg) {
+  const FlipSeg sg = seg_of(segs, nseg, blockIdx.x);
+  const long long n = 9LL * sg.cout * sg.cin;
+  const long long i0 = (blockIdx.x - sg.blk0) * (long long)kSegBlock;
+#pragma unroll
+  for (int k = 0; k < kSegBlock / 256; ++k) {
+    const long long i = i0 + k * 256 + threadIdx.x;
+    if (i >= n) break;
+    const int ci = int(i % sg.cin);
+    const int co = int((i / sg.cin) % sg.cout);
+    const int tap = int(i / ((long long)sg.cin * sg.cout));
+    sg.wt[(size_t(8 - tap) * sg.cin + ci) * sg.cout + co] = sg.w[i];
   }
 }
 
@@ -670,12 +748,17 @@ bool taps_shape(int Cout, int Cin, int N, int H, int W, TapsShape* t) {
   t->nchunks = (t->patches + t->chunk - 1) / t->chunk;
   return true;
 }
+// floats of the nine-tap kernel's weight partials; its bias partials follow
+size_t taps_weight_floats(const TapsShape& t) { return size_t(t.ntiles) * t.nchunks * 9 * 1024; }
+size_t taps_bias_floats(const TapsShape& t) {
+  return size_t(t.ntiles / t.ntn) * t.nchunks * 32;
+}
 }  // namespace
 
 size_t wgrad_scratch(int Cout, int Cin, int N, int H, int W) {
   TapsShape t;
   if (!taps_shape(Cout, Cin, N, H, W, &t)) return 0;
-  return size_t(t.ntiles) * t.nchunks * 9 * 1024;
+  return taps_weight_floats(t) + taps_bias_floats(t);
 }
 
 cudaError_t wgrad3x3(const WgradArgs& args, cudaStream_t s) {
@@ -683,19 +766,24 @@ cudaError_t wgrad3x3(const WgradArgs& args, cudaStream_t s) {
   TapsShape ts;
   const int N = int(a.npix / ((long long)a.H * a.W));
   if (a.part && taps_shape(a.Cout, a.Cin, N, a.H, a.W, &ts) &&
-      size_t(ts.ntiles) * ts.nchunks * 9 * 1024 <= a.part_cap && a.Cdy % 8 == 0 &&
+      taps_weight_floats(ts) + taps_bias_floats(ts) <= a.part_cap && a.Cdy % 8 == 0 &&
       a.Cx % 8 == 0 && a.co_off % 8 == 0 && a.ci_off % 8 == 0) {
     const int smem = 2 * (kWP + kWHalo) * kWLD * 2;
     cudaError_t e =
         cudaFuncSetAttribute(wgrad_taps_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
+    const size_t bias_off = taps_weight_floats(ts);
     wgrad_taps_kernel<<<ts.ntiles * ts.nchunks, kThreads, smem, s>>>(a, ts.chunk, ts.nchunks,
-                                                                      ts.patches);
+                                                                      ts.patches, bias_off);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    const long long groups = (long long)ts.ntiles * 9 * 1024 / 32;
+    const long long groups = ((long long)ts.ntiles * 9 * 1024 + (a.db ? a.Cout : 0)) / 32;
     wgrad_reduce_kernel<<<unsigned(groups < 152 * 16 ? groups : 152 * 16), 256, 0, s>>>(
-        a.part, ts.nchunks, ts.ntiles, ts.ntn, a.Cout, a.Cin, a.dw);
+        a.part, bias_off, ts.nchunks, ts.ntiles, ts.ntn, a.Cout, a.Cin, a.dw, a.db);
     return cudaGetLastError();
+  }
+  if (a.db) {  // the per-tap kernel leaves the bias gradient to its own kernel
+    const cudaError_t e = bias_grad(a.dy, a.Cdy, a.co_off, a.Cout, a.npix, a.db, s);
+    if (e != cudaSuccess) return e;
   }
   if (a.W % 16 || a.Cout % 32 || a.Cin % 16 || a.chunk < 16 || a.chunk % 16)
     return cudaErrorInvalidValue;
@@ -729,6 +817,8 @@ cudaError_t bias_grad(const bf16* g, int Cg, int off, int C, long long npix, flo
   const int groups = C / 8;
   int lanes = 1;
   while (lanes * 2 * groups <= 256) lanes *= 2;
+  // about 16 pixels per lane: more blocks would queue more atomics on the same
+  // C addresses than they save in load latency
   long long blocks = (npix + lanes * 16 - 1) / (lanes * 16);
   if (blocks > 152 * 8) blocks = 152 * 8;
   if (blocks < 1) blocks = 1;
@@ -783,10 +873,21 @@ cudaError_t head_fwd(const bf16* x, int C, const float* w, const float* b, float
 }
 cudaError_t head_bwd(const bf16* x, int C, const float* w, const float* gy, int O, long long npix,
                      bf16* gx, float* dw, float* db, cudaStream_t s) {
-  if (O * C > 128 || O > 8 || C > 32 || !v8(C)) return cudaErrorInvalidValue;
-  long long blocks = (npix + 255) / 256;
+  if (O < 1 || O > 8 || C > 32 || !v8(C)) return cudaErrorInvalidValue;
+  long long blocks = (npix + 8 * 16 - 1) / (8 * 16);  // about 16 pixels per warp
   if (blocks > 152 * 8) blocks = 152 * 8;
-  head_bwd_kernel<<<int(blocks), 256, 0, s>>>(x, C, w, gy, O, npix, gx, dw, db);
+  if (blocks < 1) blocks = 1;
+  const dim3 g{unsigned(blocks)}, bl{256};
+  switch (O) {
+    case 1: head_bwd_kernel<1><<<g, bl, 0, s>>>(x, C, w, gy, npix, gx, dw, db); break;
+    case 2: head_bwd_kernel<2><<<g, bl, 0, s>>>(x, C, w, gy, npix, gx, dw, db); break;
+    case 3: head_bwd_kernel<3><<<g, bl, 0, s>>>(x, C, w, gy, npix, gx, dw, db); break;
+    case 4: head_bwd_kernel<4><<<g, bl, 0, s>>>(x, C, w, gy, npix, gx, dw, db); break;
+    case 5: head_bwd_kernel<5><<<g, bl, 0, s>>>(x, C, w, gy, npix, gx, dw, db); break;
+    case 6: head_bwd_kernel<6><<<g, bl, 0, s>>>(x, C, w, gy, npix, gx, dw, db); break;
+    case 7: head_bwd_kernel<7><<<g, bl, 0, s>>>(x, C, w, gy, npix, gx, dw, db); break;
+    default: head_bwd_kernel<8><<<g, bl, 0, s>>>(x, C, w, gy, npix, gx, dw, db); break;
+  }
   return cudaGetLastError();
 }
 cudaError_t mse(const float* y, const float* t, long long n, float* gy, float* loss,
@@ -794,14 +895,16 @@ cudaError_t mse(const float* y, const float* t, long long n, float* gy, float* l
   mse_kernel<<<blocks_for(n), 256, 0, s>>>(y, t, n, gy, loss);
   return cudaGetLastError();
 }
-cudaError_t adam(float* w, float* g, float* m, float* v, bf16* wb, long long n, float lr, float b1,
-                 float b2, float eps, int t, cudaStream_t s) {
+cudaError_t adam_multi(const AdamSeg* segs, int nseg, long long blocks, float lr, float b1,
+                       float b2, float eps, int t, cudaStream_t s) {
+  if (nseg < 1 || blocks < 1 || blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
   const float c1 = 1.f - powf(b1, float(t)), c2 = 1.f - powf(b2, float(t));
-  adam_kernel<<<blocks_for(n), 256, 0, s>>>(w, g, m, v, wb, n, lr, b1, b2, eps, c1, c2);
+  adam_multi_kernel<<<unsigned(blocks), 256, 0, s>>>(segs, nseg, lr, b1, b2, eps, c1, c2);
   return cudaGetLastError();
 }
-cudaError_t flip_transpose(const bf16* w, bf16* wt, int Cout, int Cin, cudaStream_t s) {
-  flip_transpose_kernel<<<blocks_for(9LL * Cout * Cin), 256, 0, s>>>(w, wt, Cout, Cin);
+cudaError_t flip_multi(const FlipSeg* segs, int nseg, long long blocks, cudaStream_t s) {
+  if (nseg < 1 || blocks < 1 || blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
+  flip_multi_kernel<<<unsigned(blocks), 256, 0, s>>>(segs, nseg);
   return cudaGetLastError();
 }
 

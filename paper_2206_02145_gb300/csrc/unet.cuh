@@ -60,6 +60,7 @@ struct WgradArgs {
   const bf16* dy;  // gradient of the layer's pre-activation [N][H][W][Cdy], channels co_off..
   int Cdy, co_off, Cout;
   float* dw;       // [9][Cout][Cin] FP32, accumulated (+=)
+  float* db;       // [Cout] FP32 bias gradient sum of dy, accumulated (+=); null: not formed
   long long npix;  // N * H * W
   int H, W;
   int chunk;       // pixels per CTA (multiple of 16) of the per-tap kernel
@@ -90,9 +91,26 @@ cudaError_t head_bwd(const bf16* x, int C, const float* w, const float* gy, int 
                      bf16* gx, float* dw, float* db, cudaStream_t s);
 cudaError_t mse(const float* y, const float* t, long long n, float* gy, float* loss,
                 cudaStream_t s);
-cudaError_t adam(float* w, float* g, float* m, float* v, bf16* wb, long long n, float lr, float b1,
-                 float b2, float eps, int t, cudaStream_t s);
-cudaError_t flip_transpose(const bf16* w, bf16* wt, int Cout, int Cin, cudaStream_t s);
+// Multi-tensor launches: a table in device memory lists the tensors, each
+// covering ceil(n / kSegBlock) consecutive blocks starting at block blk0
+// (blk0 ascending from 0); `blocks` is the sum over the table.
+constexpr int kSegBlock = 1024;  // values per block
+struct AdamSeg {  // one parameter tensor: FP32 value, gradient, moments, bf16 copy (or null)
+  float *w, *g, *m, *v;
+  bf16* wb;
+  long long n, blk0;
+};
+struct FlipSeg {  // one convolution's weights [9][cout][cin] and their flip-transpose
+  const bf16* w;
+  bf16* wt;
+  int cout, cin;
+  long long blk0;
+};
+// Adam step t (bias-corrected) over every tensor of the table; clears the gradients
+cudaError_t adam_multi(const AdamSeg* segs, int nseg, long long blocks, float lr, float b1,
+                       float b2, float eps, int t, cudaStream_t s);
+// wt[8 - tap][ci][co] = w[tap][co][ci] for every convolution of the table
+cudaError_t flip_multi(const FlipSeg* segs, int nseg, long long blocks, cudaStream_t s);
 
 }  // namespace nn
 }  // namespace lbk

@@ -77,7 +77,9 @@ def test_propagator_gains_at_the_stated_error(trained):
           "growth LB", grow_lb, "network", grow_s)
     assert da["step"] == db["step"]
     assert rep["blocks"] == K and rep["surrogate_blocks"] >= K // 2
-    assert rep["max_drift"] <= 1e-3 and rep["max_iface_est"] <= 1.0
+    # the checks held for every block the network advanced (a prediction that
+    # failed one went to the LB instead and counts as a fallback)
+    assert rep["max_drift_committed"] <= 1e-3 and rep["max_iface_est"] <= 1.0
     # committed states keep the solute invariant as the LB does
     assert abs(da["solute_drift_rel"]) < 1e-6
     # interface positions within 1 lattice unit, growth within 25 %
