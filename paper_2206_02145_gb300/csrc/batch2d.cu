@@ -1,13 +1,15 @@
 // Batched 2D step: many independent instances (different grids, parameters
-// and seeds) advanced by ONE persistent launch per time step.  The tiles of
-// all instances form one work list; a CTA walks it round-robin, looks up the
-// instance of each tile in a tile -> instance table, and feeds its pipeline
-// with that instance's TMA descriptors (kept in global memory).  The per-tile
-// work is exactly the single-grid kernel's (step2d_tile.cuh), so a batched
-// instance evolves bit for bit like the same instance stepped alone.
+// and seeds) advanced by ONE persistent launch per time step.  The host orders
+// the instances' tiles and splits them over the resident CTAs once per plan
+// (batch_schedule): every CTA gets runs of tiles, each of one instance, and
+// feeds its pipeline with that instance's TMA descriptors (kept in global
+// memory).  The per-tile work is exactly the
+// single-grid kernel's (step2d_tile.cuh), so a batched instance evolves bit
+// for bit like the same instance stepped alone.
 //
 // Several tile shapes / pipeline depths are compiled; the host times them on
 // the live batch (all produce the same bits) and keeps the fastest.
+#include <algorithm>
 #include <vector>
 
 #include "batch2d_kernels.cuh"
@@ -17,15 +19,88 @@ namespace lbk {
 namespace {
 
 cudaError_t dispatch_any(int storage, int flow, int v, bool mask, bool chm, bool setup, int* ctas,
-                         int* smem, const BatchDesc* d, const unsigned short* ti, int total,
-                         cudaStream_t s) {
+                         int* smem, const BatchDesc* d, const BatchSeg* sg, const int* cs,
+                         int grid, cudaStream_t s) {
   switch (storage) {
     case ST_FP16:
-      return batch_dispatch_fp16(flow, v, mask, chm, setup, ctas, smem, d, ti, total, s);
+      return batch_dispatch_fp16(flow, v, mask, chm, setup, ctas, smem, d, sg, cs, grid, s);
     case ST_BF16:
-      return batch_dispatch_bf16(flow, v, mask, chm, setup, ctas, smem, d, ti, total, s);
+      return batch_dispatch_bf16(flow, v, mask, chm, setup, ctas, smem, d, sg, cs, grid, s);
     default:
-      return batch_dispatch_fp32(flow, v, mask, chm, setup, ctas, smem, d, ti, total, s);
+      return batch_dispatch_fp32(flow, v, mask, chm, setup, ctas, smem, d, sg, cs, grid, s);
+  }
+}
+
+// The order of the batch's tiles and their split over the G resident CTAs.
+// The instances' tiles (tiles[i] of instance i, row-major) are cut into
+// chunks of K consecutive tiles.  Instances of at most a quarter of a wave
+// (G K / 4 tiles) are listed first, one whole instance after another, so that
+// each is stepped within one wave (its wrapped halos and pushes meet in L2);
+// the chunks of the larger ones follow round after round over those instances
+// (chunk q of every instance that has one, then chunk q + 1, ...), so that
+// every large instance is stepped as a compact band of rows that moves through
+// it while all of them advance together.  CTA b takes chunks b, b + G,
+// b + 2G, ... of the list, as the single-instance step's CTAs take tiles, so
+// every CTA gets a mix of instances and of edge and interior tiles.
+// K is the largest of 4, 2, 1 that still gives every CTA at least 16 chunks
+// (balance within one chunk in sixteen); one instance takes K = 1, which is
+// the single-instance step's walk.  A CTA's consecutive tiles of one instance at a
+// constant stride form one run.  Out: the runs CTA after CTA, and per CTA the
+// index of its first run (cta_seg[b] .. cta_seg[b + 1]).
+void batch_schedule(const std::vector<int>& tiles, int G, std::vector<BatchSeg>* segs,
+                    std::vector<int>* cta_seg) {
+  const int n = int(tiles.size());
+  long long total = 0;
+  int maxt = 0;
+  for (int t : tiles) {
+    total += t;
+    maxt = std::max(maxt, t);
+  }
+  int K = 1;
+  if (n > 1)
+    for (int k : {4, 2})
+      if (total >= 16LL * k * G) {
+        K = k;
+        break;
+      }
+  struct Chunk {
+    int inst, first, count;
+  };
+  std::vector<Chunk> chunks;
+  auto small = [&](int i) { return 4LL * tiles[i] <= (long long)G * K; };
+  for (int i = 0; i < n; ++i)  // instances within a quarter of a wave: one after another
+    if (small(i))
+      for (int q = 0; q * K < tiles[i]; ++q)
+        chunks.push_back({i, q * K, std::min(K, tiles[i] - q * K)});
+  for (int q = 0; q * K < maxt; ++q)  // the others: round after round
+    for (int i = 0; i < n; ++i)
+      if (!small(i) && q * K < tiles[i]) chunks.push_back({i, q * K, std::min(K, tiles[i] - q * K)});
+  const int nc = int(chunks.size());
+  const int grid = std::min(G, nc);
+  segs->clear();
+  cta_seg->assign(1, 0);
+  for (int b = 0; b < grid; ++b) {
+    BatchSeg run{-1, 0, 1, 0};
+    auto add = [&](int inst, int t) {
+      if (run.count > 0 && run.inst == inst) {
+        const int last = run.first + (run.count - 1) * run.stride;
+        if (run.count == 1 && t > last) {
+          run.stride = t - last;
+          ++run.count;
+          return;
+        }
+        if (t - last == run.stride) {
+          ++run.count;
+          return;
+        }
+      }
+      if (run.count > 0) segs->push_back(run);
+      run = BatchSeg{inst, t, 1, 1};
+    };
+    for (int q = b; q < nc; q += grid)
+      for (int r = 0; r < chunks[q].count; ++r) add(chunks[q].inst, chunks[q].first + r);
+    if (run.count > 0) segs->push_back(run);
+    cta_seg->push_back(int(segs->size()));
   }
 }
 
@@ -55,7 +130,7 @@ cudaError_t batch_plan_build(const BatchMember* members, int count, int storage,
   const int qfg = (flow ? 9 : 0) + 9;
   const int hx = int(16 / es);
   std::vector<BatchDesc> host[2];
-  std::vector<unsigned short> inst;
+  std::vector<int> tiles;
   int tile0 = 0;
   bool mask = false;
   for (int i = 0; i < count; ++i) mask = mask || members[i].m.solid != nullptr;
@@ -107,11 +182,9 @@ cudaError_t batch_plan_build(const BatchMember* members, int count, int storage,
       d.ring_cur = static_cast<float*>(members[i].rings[c ^ 1]);
       d.err = members[i].err;
       d.ntx = ntx;
-      d.tile0 = tile0;
-      d.ntiles = ntx * nty;
       host[c].push_back(d);
     }
-    for (int t = 0; t < ntx * nty; ++t) inst.push_back((unsigned short)i);
+    tiles.push_back(ntx * nty);
     if (m.solid) {
       batch_solid_tiles_kernel<<<(ntx * nty + 127) / 128, 128>>>(m, plan->solid_tiles + tile0, ntx,
                                                                   nty, tx, ty);
@@ -131,28 +204,39 @@ cudaError_t batch_plan_build(const BatchMember* members, int count, int storage,
                         cudaMemcpyHostToDevice)) != cudaSuccess)
       return e;
   }
-  if ((e = cudaMalloc(&plan->tile_inst, sizeof(unsigned short) * inst.size())) != cudaSuccess)
+  // the resident CTAs of this variant, then the split of the tiles over them
+  if ((e = dispatch_any(storage, flow, v, plan->mask, plan->chm, true, &plan->ctas, &plan->smem,
+                        nullptr, nullptr, nullptr, 0, nullptr)) != cudaSuccess)
     return e;
-  if ((e = cudaMemcpy(plan->tile_inst, inst.data(), sizeof(unsigned short) * inst.size(),
+  std::vector<BatchSeg> segs;
+  std::vector<int> cta_seg;
+  batch_schedule(tiles, plan->ctas, &segs, &cta_seg);
+  plan->grid = int(cta_seg.size()) - 1;
+  if ((e = cudaMalloc(&plan->segs, sizeof(BatchSeg) * segs.size())) != cudaSuccess) return e;
+  if ((e = cudaMemcpy(plan->segs, segs.data(), sizeof(BatchSeg) * segs.size(),
+                      cudaMemcpyHostToDevice)) != cudaSuccess)
+    return e;
+  if ((e = cudaMalloc(&plan->cta_seg, sizeof(int) * cta_seg.size())) != cudaSuccess) return e;
+  if ((e = cudaMemcpy(plan->cta_seg, cta_seg.data(), sizeof(int) * cta_seg.size(),
                       cudaMemcpyHostToDevice)) != cudaSuccess)
     return e;
   if (mask && (e = cudaDeviceSynchronize()) != cudaSuccess) return e;
-  plan->bytes = 2 * sizeof(BatchDesc) * count + sizeof(unsigned short) * inst.size() +
-                (mask ? size_t(all_tiles) : 0);
-  return dispatch_any(storage, flow, v, plan->mask, plan->chm, true, &plan->ctas, &plan->smem, nullptr, nullptr, 0,
-                      nullptr);
+  plan->bytes = 2 * sizeof(BatchDesc) * count + sizeof(BatchSeg) * segs.size() +
+                sizeof(int) * cta_seg.size() + (mask ? size_t(all_tiles) : 0);
+  return cudaSuccess;
 }
 
 cudaError_t batch_plan_launch(const BatchPlan& plan, int c, cudaStream_t s) {
   int ctas = plan.ctas, smem = plan.smem;
   return dispatch_any(plan.storage, plan.flow, plan.variant, plan.mask, plan.chm, false, &ctas,
-                      &smem, plan.desc[c], plan.tile_inst, plan.total_tiles, s);
+                      &smem, plan.desc[c], plan.segs, plan.cta_seg, plan.grid, s);
 }
 
 void batch_plan_free(BatchPlan* plan) {
   for (int c = 0; c < 2; ++c)
     if (plan->desc[c]) cudaFree(plan->desc[c]);
-  if (plan->tile_inst) cudaFree(plan->tile_inst);
+  if (plan->segs) cudaFree(plan->segs);
+  if (plan->cta_seg) cudaFree(plan->cta_seg);
   if (plan->solid_tiles) cudaFree(plan->solid_tiles);
   *plan = BatchPlan{};
 }

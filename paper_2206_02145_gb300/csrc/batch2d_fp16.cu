@@ -4,9 +4,10 @@
 namespace lbk {
 
 cudaError_t batch_dispatch_fp16(int flow, int v, bool mask, bool chm, bool setup, int* ctas,
-                              int* smem, const BatchDesc* d, const unsigned short* ti,
-                              int total, cudaStream_t s) {
-  return batch::dispatch_storage<__half>(flow, v, mask, chm, setup, ctas, smem, d, ti, total, s);
+                              int* smem, const BatchDesc* d, const BatchSeg* segs,
+                              const int* cta_seg, int grid, cudaStream_t s) {
+  return batch::dispatch_storage<__half>(flow, v, mask, chm, setup, ctas, smem, d, segs, cta_seg,
+                                       grid, s);
 }
 
 }  // namespace lbk

@@ -161,7 +161,7 @@ struct alignas(128) BatchDesc {
   void* dst;
   float* ring_cur;
   unsigned* err;
-  int ntx, tile0, ntiles, c;
+  int ntx, c;  // tiles per row of the instance; buffer parity
 };
 struct BatchMember {  // what the batch needs of one instance
   Model m;
@@ -169,11 +169,18 @@ struct BatchMember {  // what the batch needs of one instance
   void* rings[2];
   unsigned* err;
 };
+// One run of a batched CTA's work: the tiles first, first + stride, ...
+// (count of them) of instance inst, numbered row-major within the instance.
+struct BatchSeg {
+  int inst, first, stride, count;
+};
 struct BatchPlan {  // device tables of one compiled variant
   BatchDesc* desc[2] = {nullptr, nullptr};
-  unsigned short* tile_inst = nullptr;
+  BatchSeg* segs = nullptr;   // the runs of every CTA, CTA after CTA
+  int* cta_seg = nullptr;     // CTA b works through segs[cta_seg[b] .. cta_seg[b + 1])
   unsigned char* solid_tiles = nullptr;  // per-tile solid flags of this variant's tiles
   int total_tiles = 0, variant = 0, storage = 0, flow = 0, ctas = 0, smem = 0;
+  int grid = 0;  // CTAs of one launch (those with work, all resident at once)
   int mask = 0, chm = 0;  // some instance has solid nodes; the flow collides by CHM
   size_t bytes = 0;
 };
@@ -184,10 +191,12 @@ cudaError_t batch_plan_build(const BatchMember* members, int count, int storage,
                              BatchPlan* plan);
 cudaError_t batch_plan_launch(const BatchPlan& plan, int c, cudaStream_t s);
 // the kernel variants of one storage type (setup: occupancy and shared memory
-// into *ctas, *smem; else one launch of the step over the tile list)
+// into *ctas, *smem; else one launch of the step: grid CTAs working through
+// their runs of tiles)
 #define LBPF_BATCH_DISPATCH(NAME)                                                            \
   cudaError_t NAME(int flow, int v, bool mask, bool chm, bool setup, int* ctas, int* smem,   \
-                   const BatchDesc* d, const unsigned short* ti, int total, cudaStream_t s);
+                   const BatchDesc* d, const BatchSeg* segs, const int* cta_seg, int grid,   \
+                   cudaStream_t s);
 LBPF_BATCH_DISPATCH(batch_dispatch_fp32)
 LBPF_BATCH_DISPATCH(batch_dispatch_fp16)
 LBPF_BATCH_DISPATCH(batch_dispatch_bf16)
