@@ -8,7 +8,7 @@ step over the whole grid; the metric is MLUPS (million node updates per
 second) with the HBM roofline of the step kernel beside it.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload c1|c2|c2_fp16|c3|c3s|c3_fp16|c3_bf16|c4|c4s|c5|c5net|f1|f2|f3|
+                  [--workload c1|c2|c2_fp16|c3|c3s|c3_fp16|c3s_fp16|c3_bf16|c4|c4s|c5|c5net|f1|f2|f3|
                               f3_3d|f3_3ds]
 
 Workloads f1 (the crystal-shape measurement with a hexagonal seed), f2 (a
@@ -102,6 +102,11 @@ WORKLOADS = {
                 desc="3D 128^3 case of c3 for profiler captures (D3Q19 flow, D3Q7 solute and "
                      "phase field), cubic eps 0.04, sphere R=12, U0=0.3, inflow 0.005",
                 desc_note="FP32"),
+    "c3s_fp16": dict(base="c3", nx=128, ny=128, nz=128, storage="fp16",
+                     seed=(64.0, 64.0, 64.0, 12.0, 0.3, 0.01, 1),
+                     desc="3D 128^3 case of c3_fp16 for profiler captures (D3Q19 flow, D3Q7 "
+                          "solute and phase field), cubic eps 0.04, sphere R=12, U0=0.3, inflow "
+                          "0.005, FP16 shifted storage", desc_note=True),
     "c3_bf16": dict(base="c3", storage="bf16"),
     "f3_3d": dict(base="c3", desc_note=True,
                   desc="3D 256^3 coupled LB (D3Q19 flow, D3Q7 solute and phase field), cubic "

@@ -35,6 +35,7 @@ def test_every_workload_resolves(bench):
     ("c1", 18 * 4 * 2 + 8),
     # 3D: 19 + 7 + 7 populations
     ("c3", 33 * 4 * 2 + 8), ("f3_3d", 33 * 4 * 2 + 8), ("c3_fp16", 33 * 2 * 2 + 8 + 6),
+    ("c3s_fp16", 33 * 2 * 2 + 8 + 6),
 ])
 def test_algorithmic_bytes_per_node_update(bench, name, bytes_per_lup):
     assert bench.workload(name)["bytes_per_lup"] == bytes_per_lup
