@@ -326,13 +326,14 @@ void lbpf_destroy(lbpf_t* h);
 /* ---- batched sweep ------------------------------------------------------------
  * Many independent 2D instances (the parametric sweeps of Sec. 3: supersaturation,
  * seed size, inflow) advanced together by ONE persistent kernel launch per time
- * step: the tiles of all instances form one work list.  Every instance is an
- * ordinary handle with its own state (lbpf_batch_instance); a batched instance
- * evolves bit for bit like the same instance stepped alone.  Several tile
- * shapes are compiled; the first lbpf_batch_step that is long enough
- * (>= 24 steps) times each of them on the live batch and keeps the fastest
- * (lbpf_batch_tuning); every shape produces the same bits.  Steps of 64 are
- * replayed from a CUDA graph. */
+ * step: the tiles of all instances are split over the resident CTAs once per
+ * plan.  Every instance is an ordinary handle with its own state
+ * (lbpf_batch_instance); a batched instance evolves bit for bit like the same
+ * instance stepped alone.  Several tile shapes are compiled, each with two tile
+ * orders (large instances interleaved, or instance after instance); the first
+ * lbpf_batch_step that is long enough (>= 48 steps) times every (order, shape)
+ * plan on the live batch and keeps the fastest (lbpf_batch_tuning); every plan
+ * produces the same bits.  Steps of 64 are replayed from a CUDA graph. */
 typedef struct lbpf_batch lbpf_batch_t;
 
 /* Create `count` instances (1..65535) from p[i] and seed them with s[i]
@@ -361,8 +362,10 @@ lbpf_t* lbpf_batch_instance(lbpf_batch_t* b, int i);
 lbpf_status lbpf_batch_count(const lbpf_batch_t* b);
 
 /* The tile shape the tuner chose (rows of the 32-wide tile, pipeline stages)
- * and the measured ms per step of each compiled shape (ms[0..*nvar-1]); any
- * pointer may be NULL.  LBPF_ESTATE before tuning has run. */
+ * and the measured ms per step of each plan (ms[0..*nvar-1], at most 8: plan
+ * p is tile order p / 4 (0 large instances interleaved, 1 instance after
+ * instance) with compiled shape p % 4); any pointer may be NULL.  LBPF_ESTATE
+ * before tuning has run. */
 lbpf_status lbpf_batch_tuning(const lbpf_batch_t* b, int* tile_rows, int* stages, float* ms, int* nvar);
 const char* lbpf_batch_last_error(const lbpf_batch_t* b);
 void lbpf_batch_destroy(lbpf_batch_t* b);

@@ -33,21 +33,25 @@ cudaError_t dispatch_any(int storage, int flow, int v, bool mask, bool chm, bool
 
 // The order of the batch's tiles and their split over the G resident CTAs.
 // The instances' tiles (tiles[i] of instance i, row-major) are cut into
-// chunks of K consecutive tiles.  Instances of at most a quarter of a wave
-// (G K / 4 tiles) are listed first, one whole instance after another, so that
-// each is stepped within one wave (its wrapped halos and pushes meet in L2);
-// the chunks of the larger ones follow round after round over those instances
-// (chunk q of every instance that has one, then chunk q + 1, ...), so that
-// every large instance is stepped as a compact band of rows that moves through
-// it while all of them advance together.  CTA b takes chunks b, b + G,
-// b + 2G, ... of the list, as the single-instance step's CTAs take tiles, so
-// every CTA gets a mix of instances and of edge and interior tiles.
-// K is the largest of 4, 2, 1 that still gives every CTA at least 16 chunks
-// (balance within one chunk in sixteen); one instance takes K = 1, which is
-// the single-instance step's walk.  A CTA's consecutive tiles of one instance at a
-// constant stride form one run.  Out: the runs CTA after CTA, and per CTA the
-// index of its first run (cta_seg[b] .. cta_seg[b + 1]).
-void batch_schedule(const std::vector<int>& tiles, int G, std::vector<BatchSeg>* segs,
+// chunks of K consecutive tiles, so that a CTA steps K neighbours in a row one
+// after another (the pushes across their common edges meet in L2 while the
+// sectors are still there).  order 1: the instances one after another.
+// order 0: instances of at most a quarter of a wave (G K / 4 tiles) one after
+// another, then the chunks of the larger ones round after round over those
+// instances (chunk q of every instance that has one, then chunk q + 1, ...),
+// so that every large instance is stepped as a band of rows that moves
+// through it while all of them advance together.  Which order is faster
+// depends on the mix (measured on 16 equal 512^2 FP16 instances: order 0;
+// on 64 uneven 256^2..768^2 ones: order 1); the tuner times both.  CTA b
+// takes chunks b, b + G, b + 2G, ... of the list, as the single-instance
+// step's CTAs take tiles, so every CTA gets a mix of instances and of edge
+// and interior tiles.  K is the largest of 8, 4, 2, 1 that still gives every
+// CTA at least 16 chunks (balance within one chunk in sixteen); one instance
+// takes K = 1, which is the single-instance step's walk.  A CTA's consecutive
+// tiles of one instance at a constant stride form one run.  Out: the runs CTA
+// after CTA, and per CTA the index of its first run (cta_seg[b] ..
+// cta_seg[b + 1]).
+void batch_schedule(const std::vector<int>& tiles, int G, int order, std::vector<BatchSeg>* segs,
                     std::vector<int>* cta_seg) {
   const int n = int(tiles.size());
   long long total = 0;
@@ -58,7 +62,7 @@ void batch_schedule(const std::vector<int>& tiles, int G, std::vector<BatchSeg>*
   }
   int K = 1;
   if (n > 1)
-    for (int k : {4, 2})
+    for (int k : {8, 4, 2})
       if (total >= 16LL * k * G) {
         K = k;
         break;
@@ -67,7 +71,7 @@ void batch_schedule(const std::vector<int>& tiles, int G, std::vector<BatchSeg>*
     int inst, first, count;
   };
   std::vector<Chunk> chunks;
-  auto small = [&](int i) { return 4LL * tiles[i] <= (long long)G * K; };
+  auto small = [&](int i) { return order == 1 || 4LL * tiles[i] <= (long long)G * K; };
   for (int i = 0; i < n; ++i)  // instances within a quarter of a wave: one after another
     if (small(i))
       for (int q = 0; q * K < tiles[i]; ++q)
@@ -124,7 +128,7 @@ int batch_variant_rows(int v) { return batch::kVariants[v].ty; }
 int batch_variant_stages(int v) { return batch::kVariants[v].stages; }
 
 cudaError_t batch_plan_build(const BatchMember* members, int count, int storage, int flow, int v,
-                             BatchPlan* plan) {
+                             int order, BatchPlan* plan) {
   const int ty = batch::kVariants[v].ty, tx = 32;
   const size_t es = storage == ST_FP32 ? 4 : 2;
   const int qfg = (flow ? 9 : 0) + 9;
@@ -210,7 +214,8 @@ cudaError_t batch_plan_build(const BatchMember* members, int count, int storage,
     return e;
   std::vector<BatchSeg> segs;
   std::vector<int> cta_seg;
-  batch_schedule(tiles, plan->ctas, &segs, &cta_seg);
+  batch_schedule(tiles, plan->ctas, order, &segs, &cta_seg);
+  plan->order = order;
   plan->grid = int(cta_seg.size()) - 1;
   if ((e = cudaMalloc(&plan->segs, sizeof(BatchSeg) * segs.size())) != cudaSuccess) return e;
   if ((e = cudaMemcpy(plan->segs, segs.data(), sizeof(BatchSeg) * segs.size(),

@@ -937,11 +937,15 @@ int batch_build(lbpf_batch* b) {
     mem[i].err = k->d_err;
     b->gens[i] = k->gen;
   }
-  b->nplans = lbk::batch_variant_count();
+  // one plan per (tile order, compiled variant): plan p = order * variants + variant
+  const int nvar = lbk::batch_variant_count();
+  b->nplans = lbk::kBatchOrders * nvar;
+  if (b->nplans > int(sizeof(b->plans) / sizeof(b->plans[0])))
+    return bfail(b, LBPF_EINVAL, "%d batch plans exceed the handle's table", b->nplans);
   const lbpf* k0 = b->kids[0];
-  for (int v = 0; v < b->nplans; ++v)
-    BCK(b, lbk::batch_plan_build(mem.data(), int(mem.size()), k0->m.storage, k0->m.flow, v,
-                                 &b->plans[v]));
+  for (int p = 0; p < b->nplans; ++p)
+    BCK(b, lbk::batch_plan_build(mem.data(), int(mem.size()), k0->m.storage, k0->m.flow,
+                                 p % nvar, p / nvar, &b->plans[p]));
   return LBPF_OK;
 }
 
@@ -1109,8 +1113,9 @@ lbpf_status lbpf_batch_tuning(const lbpf_batch_t* b, int* tile_rows, int* stages
   if (ms)
     for (int v = 0; v < b->nplans; ++v) ms[v] = b->tune_ms[v];
   const int v = b->chosen;
-  if (tile_rows) *tile_rows = v < 0 ? 0 : lbk::batch_variant_rows(v);
-  if (stages) *stages = v < 0 ? 0 : lbk::batch_variant_stages(v);
+  const int nv = lbk::batch_variant_count();
+  if (tile_rows) *tile_rows = v < 0 ? 0 : lbk::batch_variant_rows(v % nv);
+  if (stages) *stages = v < 0 ? 0 : lbk::batch_variant_stages(v % nv);
   return v < 0 ? LBPF_ESTATE : LBPF_OK;
 }
 

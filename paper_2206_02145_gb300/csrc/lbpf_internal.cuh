@@ -180,15 +180,19 @@ struct BatchPlan {  // device tables of one compiled variant
   int* cta_seg = nullptr;     // CTA b works through segs[cta_seg[b] .. cta_seg[b + 1])
   unsigned char* solid_tiles = nullptr;  // per-tile solid flags of this variant's tiles
   int total_tiles = 0, variant = 0, storage = 0, flow = 0, ctas = 0, smem = 0;
-  int grid = 0;  // CTAs of one launch (those with work, all resident at once)
+  int grid = 0;   // CTAs of one launch (those with work, all resident at once)
+  int order = 0;  // tile order of the schedule (batch_schedule)
   int mask = 0, chm = 0;  // some instance has solid nodes; the flow collides by CHM
   size_t bytes = 0;
 };
 int batch_variant_count();
 int batch_variant_rows(int v);
 int batch_variant_stages(int v);
+// the tile orders a plan can take (batch_schedule): 0 large instances
+// interleaved, 1 instance after instance
+constexpr int kBatchOrders = 2;
 cudaError_t batch_plan_build(const BatchMember* members, int count, int storage, int flow, int v,
-                             BatchPlan* plan);
+                             int order, BatchPlan* plan);
 cudaError_t batch_plan_launch(const BatchPlan& plan, int c, cudaStream_t s);
 // the kernel variants of one storage type (setup: occupancy and shared memory
 // into *ctas, *smem; else one launch of the step: grid CTAs working through

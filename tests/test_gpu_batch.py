@@ -36,7 +36,7 @@ def test_batch_equals_single_instances_bitwise(L, storage_name):
     storage = getattr(L, storage_name)
     params, seeds = sweep(storage)
     b = L.Batch(params, seeds)
-    b.step(131)  # tuning (24) + graph replays + remainder, odd total
+    b.step(131)  # tuning (48) + graph replays + remainder, odd total
     singles = []
     for p, s in zip(params, seeds):
         sim = L.Sim(**p)
@@ -46,7 +46,8 @@ def test_batch_equals_single_instances_bitwise(L, storage_name):
     for i, sim in enumerate(singles):
         assert np.array_equal(b.instance(i).state(), sim.state()), i
     t = b.tuning()
-    assert t["tuned"] and t["tile_rows"] in (2, 4, 8) and len(t["ms_per_step"]) == 4
+    # four tile shapes, each in the two tile orders
+    assert t["tuned"] and t["tile_rows"] in (2, 4, 8) and len(t["ms_per_step"]) == 8
     d = b.diagnostics()
     assert all(x["step"] == 131 and x["nonfinite"] == 0 for x in d)
 
