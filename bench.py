@@ -147,7 +147,7 @@ WORKLOADS = {
                # 50-step network needs the smaller rate (at 5e-4 its small
                # per-block bias accumulates to lattice units over 400 blocks)
                surrogate=dict(blocks=(50, 200), judge_every=8, traj=50, t_end=20000,
-                              every=500, crop=256, batch=8, start=1000,
+                              every=500, crop=256, batch=8, start=1000, min_steps=20000,
                               recipe={50: (8000, 2.5e-4), 200: (4000, 5e-4)}),
                sample=dict(nx=256, ny=256, channel=True)),
     "c5net": dict(desc="the c5 network alone: BF16 U-Net 32/64/128/256 channels on a 512x512 "
@@ -1059,7 +1059,9 @@ def surrogate_arm(args, w, nb, stream, dist, clk, rank):
     b.step(nb)
     torch.cuda.synchronize()
     d0 = b.diagnostics()
-    K = max(1, args.steps // nb)
+    # --steps is a minimum: the comparison spans at least c["min_steps"] LB steps,
+    # so that the judged blocks (one in judge_every) weigh as they do in a run
+    K = max(1, max(args.steps, c["min_steps"]) // nb)
     steps = K * nb
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
