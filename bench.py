@@ -148,6 +148,7 @@ WORKLOADS = {
                # per-block bias accumulates to lattice units over 400 blocks)
                surrogate=dict(blocks=(50, 200), judge_every=8, traj=50, t_end=20000,
                               every=500, crop=256, batch=8, start=1000, min_steps=20000,
+                              val_blocks=100, val_tol=0.5, val_seeds=3, iface_rel_tol=0.9,
                               recipe={50: (8000, 2.5e-4), 200: (4000, 5e-4)}),
                sample=dict(nx=256, ny=256, channel=True)),
     "c5net": dict(desc="the c5 network alone: BF16 U-Net 32/64/128/256 channels on a 512x512 "
@@ -1028,12 +1029,42 @@ def surrogate_arm(args, w, nb, stream, dist, clk, rank):
     X, T = S.generate_pairs(c["traj"], c["t_end"], c["every"], nx, ny, cfg, seed=100,
                             crop=c["crop"])
     t_data = time.perf_counter() - t0
-    tr = L.UNet(in_ch=4, out_ch=4, levels=4, batch=c["batch"], height=c["crop"], width=nx,
-                seed=1, stream=stream.cuda_stream)
     train_steps, lr = c["recipe"][nb]
+    # validation (a problem of its own, neither a training trajectory nor the
+    # held-out test problem): the network alone advances val_blocks blocks
+    # (only the first is judged) and its interface is compared with the LB's;
+    # a candidate that drifts by more than val_tol lattice units is replaced
+    # by one trained from the next initialisation seed (at most val_seeds)
+    vparams, vfields, _ = S.channel_problem(np.random.default_rng(5151 + rank), nx, ny)
+    vb = S.make_sim(vparams, vfields, stream.cuda_stream)
+    vb.step(c["start"] + c["val_blocks"] * nb)
+    v_ref = vb.diagnostics()["iface_pos"][:4]
+    vb.close()
+    vcfg = S.default_cfg(nb, judge_every=0, drift_tol=1.0, iface_tol=1e9)
     t0 = time.perf_counter()
-    hist = S.train(tr, X, T, train_steps, lr=lr, log_every=1000)
-    tr.status()
+    tries = []
+    tr = None
+    for nseed in range(1, c["val_seeds"] + 1):
+        cand = L.UNet(in_ch=4, out_ch=4, levels=4, batch=c["batch"], height=c["crop"],
+                      width=nx, seed=nseed, stream=stream.cuda_stream)
+        h_ = S.train(cand, X, T, train_steps, lr=lr, log_every=1000)
+        cand.status()
+        vnet = S.inference_net(cand, nx, ny, stream.cuda_stream)
+        va = S.make_sim(vparams, vfields, stream.cuda_stream)
+        va.step(c["start"])
+        L.lbpf_surrogate_advance(va, vnet, vcfg, c["val_blocks"])
+        verr = float(np.max(np.abs(va.diagnostics()["iface_pos"][:4] - v_ref)))
+        va.close()
+        vnet.close()
+        tries.append({"seed": nseed, "val_iface_err_lu": verr})
+        if tr is None or verr < best:
+            if tr is not None:
+                tr.close()
+            tr, hist, best = cand, h_, verr
+        else:
+            cand.close()
+        if verr <= c["val_tol"]:
+            break
     t_train = time.perf_counter() - t0
     npairs = int(X.shape[0])
     del X, T
@@ -1054,7 +1085,8 @@ def surrogate_arm(args, w, nb, stream, dist, clk, rank):
     b = S.make_sim(params, fields, stream.cuda_stream)
     a.step(c["start"])
     b.step(c["start"])
-    pcfg = S.default_cfg(nb, judge_every=c["judge_every"], drift_tol=1e-3, iface_tol=1.0)
+    pcfg = S.default_cfg(nb, judge_every=c["judge_every"], drift_tol=1e-3, iface_tol=1.0,
+                         iface_rel_tol=c["iface_rel_tol"])
     L.lbpf_surrogate_advance(a, net, pcfg, 1)  # warm-up: captures the prediction graph
     b.step(nb)
     torch.cuda.synchronize()
@@ -1088,7 +1120,7 @@ def surrogate_arm(args, w, nb, stream, dist, clk, rank):
     cb = S.make_sim(params, fields, stream.cuda_stream)
     cb.step(c["start"] + nb)
     bcfg = S.default_cfg(nb, judge_every=c["judge_every"], drift_tol=1e-3, iface_tol=1.0,
-                         iface_budget=1.0)
+                         iface_rel_tol=c["iface_rel_tol"], iface_budget=1.0)
     torch.cuda.synchronize()
     ev0.record(stream)
     rep_b = L.lbpf_surrogate_advance(cb, net, bcfg, K)
@@ -1118,6 +1150,8 @@ def surrogate_arm(args, w, nb, stream, dist, clk, rank):
         "training": {"pairs": npairs, "steps": train_steps, "lr": lr, "batch": c["batch"],
                      "band_rows": c["crop"], "data_s": round(t_data, 1),
                      "train_s": round(t_train, 1), "loss": [round(x[1], 5) for x in hist],
+                     "validation": {"blocks": c["val_blocks"], "tol_lu": c["val_tol"],
+                                    "candidates": tries},
                      "held_out_mse": mse_net, "held_out_mse_no_network": mse_none,
                      "held_out_ratio": mse_net / mse_none},
         "held_out_problem": info,
@@ -1230,7 +1264,8 @@ def run_surrogate(args, w):
             "with_accumulated_bound": head["with_accumulated_bound"],
             "block_lengths": {str(k): {kk: v for kk, v in r.items()
                                        if kk not in ("training", "held_out_problem")}
-                              | {"held_out_ratio": r["training"]["held_out_ratio"]}
+                              | {"held_out_ratio": r["training"]["held_out_ratio"],
+                                 "validation": r["training"]["validation"]}
                               for k, r in arms.items()},
             "roofline": {"bound": "tensor", "achieved": tflops, "peak": peak_tf,
                          "unit": "TFLOP/s", "frac": tflops / peak_tf, "peak_source": peak_kind,

@@ -475,7 +475,15 @@ void lbpf_unet_destroy(lbpf_unet_t* n);
  *     accumulated estimate stays within iface_budget: per ray, the signed
  *     sum of those differences over every block the call has committed (this
  *     one included), never reset, so that a biased network runs into the
- *     bound and the rest of the call falls back to the LB.
+ *     bound and the rest of the call falls back to the LB; and, if
+ *     iface_rel_tol > 0, the estimate is also at most iface_rel_tol times the
+ *     largest displacement of that LB block over the rays, so that a network
+ *     that freezes or doubles the growth fails even where the interface moves
+ *     far less than iface_tol per block.
+ * A judged prediction earns trust if its error against the LB block (the
+ * largest difference of the interface positions over the rays) is at most
+ * iface_tol and, if iface_rel_tol > 0, at most iface_rel_tol times the LB
+ * block's largest displacement.
  * An accepted prediction's remaining solute deficit is spread over the
  * liquid in proportion to (1 - phi)/2 before it is committed, so that the
  * committed state keeps the invariant exactly as the LB does.
@@ -489,6 +497,7 @@ typedef struct {
   double drift_tol;          /* relative solute drift bound (e.g. 1e-3) */
   double iface_tol;          /* per-block interface error bound, lattice units (e.g. 1.0) */
   double iface_budget;       /* bound on the accumulated estimate over a call (0: none) */
+  double iface_rel_tol;      /* bound relative to the LB's displacement per block (0: none) */
   float shift[4], scale[4];  /* input normalisation of (phi, U, ux, uy); scale != 0 */
   float res_scale[4];        /* output scale of the change of (phi, U, ux, uy) */
 } lbpf_surrogate_cfg;

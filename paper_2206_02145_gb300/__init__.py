@@ -97,7 +97,8 @@ class lbpf_unet_cfg(ctypes.Structure):
 class lbpf_surrogate_cfg(ctypes.Structure):
     _fields_ = [("steps_per_block", ctypes.c_int), ("judge_every", ctypes.c_int),
                 ("drift_tol", ctypes.c_double), ("iface_tol", ctypes.c_double),
-                ("iface_budget", ctypes.c_double), ("shift", ctypes.c_float * 4), ("scale", ctypes.c_float * 4),
+                ("iface_budget", ctypes.c_double), ("iface_rel_tol", ctypes.c_double),
+                ("shift", ctypes.c_float * 4), ("scale", ctypes.c_float * 4),
                 ("res_scale", ctypes.c_float * 4)]
 
 
@@ -630,12 +631,13 @@ class UNet:
 
 
 def surrogate_cfg(steps_per_block=50, judge_every=8, drift_tol=1e-3, iface_tol=1.0,
-                  iface_budget=0.0, shift=(0.0, 0.3, 0.0, 0.0), scale=(1.0, 0.2, 0.01, 0.01),
+                  iface_budget=0.0, iface_rel_tol=0.0, shift=(0.0, 0.3, 0.0, 0.0),
+                  scale=(1.0, 0.2, 0.01, 0.01),
                   res_scale=(0.05, 0.005, 0.001, 0.001)) -> lbpf_surrogate_cfg:
     c = lbpf_surrogate_cfg()
     c.steps_per_block, c.judge_every = int(steps_per_block), int(judge_every)
     c.drift_tol, c.iface_tol = float(drift_tol), float(iface_tol)
-    c.iface_budget = float(iface_budget)
+    c.iface_budget, c.iface_rel_tol = float(iface_budget), float(iface_rel_tol)
     c.shift[:], c.scale[:], c.res_scale[:] = list(shift), list(scale), list(res_scale)
     return c
 

@@ -575,7 +575,7 @@ int sfail(lbpf* h, int code, const char* fmt, ...) {
 
 int check_cfg(const lbpf_surrogate_cfg* c) {
   if (!c || c->steps_per_block < 1 || c->judge_every < 0 || !(c->drift_tol >= 0.0) ||
-      !(c->iface_tol >= 0.0) || !(c->iface_budget >= 0.0))
+      !(c->iface_tol >= 0.0) || !(c->iface_budget >= 0.0) || !(c->iface_rel_tol >= 0.0))
     return LBPF_EINVAL;
   for (int k = 0; k < 4; ++k)
     if (!(std::isfinite(c->shift[k]) && std::isfinite(c->scale[k]) && c->scale[k] != 0.f &&
@@ -1025,6 +1025,8 @@ lbpf_status lbpf_surrogate_advance(lbpf_t* h, lbpf_unet_t* net, const lbpf_surro
   bool lb_pending = false, judge_pending = false, pending_ok = false;
   double dref[4] = {0, 0, 0, 0}, lb_start[4] = {0, 0, 0, 0}, pred_pending[4] = {0, 0, 0, 0};
   double acc[4] = {0, 0, 0, 0};
+  double dref_max = 0.0;  // the most recent LB block's largest displacement over the rays
+  const double rel = cfg->iface_rel_tol;
   int rc;
   for (int b = 0; b <= blocks; ++b) {
     const bool last = b == blocks;  // only resolves the outcome of the final block
@@ -1039,13 +1041,16 @@ lbpf_status lbpf_surrogate_advance(lbpf_t* h, lbpf_unet_t* net, const lbpf_surro
     const double* posP = res + 3;
     const double* pos0 = res + 7;
     if (lb_pending) {
-      for (int k = 0; k < 4; ++k)
+      dref_max = 0.0;
+      for (int k = 0; k < 4; ++k) {
         dref[k] = (pos0[k] >= 0 && lb_start[k] >= 0) ? pos0[k] - lb_start[k] : -1e300;
+        if (dref[k] > -1e300) dref_max = std::fmax(dref_max, std::fabs(dref[k]));
+      }
       have_ref = true;
       if (judge_pending) {
         const double err = ray_diff(pred_pending, pos0);
         r.max_iface_err = std::fmax(r.max_iface_err, err);
-        trusted = pending_ok && err >= 0.0 && err <= tol;
+        trusted = pending_ok && err >= 0.0 && err <= tol && (rel <= 0.0 || err <= rel * dref_max);
       }
       lb_pending = false;
     }
@@ -1065,7 +1070,8 @@ lbpf_status lbpf_surrogate_advance(lbpf_t* h, lbpf_unet_t* net, const lbpf_surro
     const bool drift_ok = drift <= cfg->drift_tol;
     const bool judge = !trusted || !have_ref || (cfg->judge_every > 0 && b % cfg->judge_every == 0);
     const bool fails = !drift_ok || !(est >= 0.0 && est <= tol) ||
-                       (cfg->iface_budget > 0.0 && !(est_acc <= cfg->iface_budget));
+                       (cfg->iface_budget > 0.0 && !(est_acc <= cfg->iface_budget)) ||
+                       (rel > 0.0 && !(est <= rel * dref_max));
     if (judge || fails) {
       if ((rc = lbpf_step(h, nb))) return rc;
       lb_pending = true;

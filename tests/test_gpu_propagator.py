@@ -116,6 +116,32 @@ def test_frozen_network_is_caught_by_the_interface_estimate(L, S):
         s.close()
 
 
+def test_frozen_network_fails_the_relative_interface_check(L, S):
+    # the same frozen network: its estimate equals the LB's displacement, so a
+    # bound relative to that displacement rejects every prediction and the
+    # LB advances every block (judged or fallback), the result the plain LB's
+    rng = np.random.default_rng(6)
+    params, fields, _ = S.channel_problem(rng, NX, NY)
+    fields["U"][:] = 0.45
+    a = S.make_sim(params, fields)
+    b = S.make_sim(params, fields)
+    a.step(200)
+    b.step(200)
+    net = _net(L)
+    net.set_weights(np.zeros(net.param_count, np.float32))
+    cfg = L.surrogate_cfg(judge_every=0, iface_tol=1.0, iface_rel_tol=0.75)
+    rep = L.lbpf_surrogate_advance(a, net, cfg, 12)
+    assert rep["blocks"] == 12 and rep["surrogate_blocks"] == 0, rep
+    assert rep["judged_blocks"] + rep["fallback_blocks"] == 12, rep
+    b.step(12 * 50)
+    np.testing.assert_array_equal(a.state(), b.state())
+    # without the relative bound the same network is committed (absolute bound 1 lu)
+    rep0 = L.lbpf_surrogate_advance(b, net, L.surrogate_cfg(judge_every=0, iface_tol=1.0), 12)
+    assert rep0["surrogate_blocks"] > 0, rep0
+    for s_ in (a, b, net):
+        s_.close()
+
+
 def test_rejects_mismatched_network(L, S):
     params, fields, _ = _problem(S, 7)
     a = S.make_sim(params, fields)
@@ -125,6 +151,8 @@ def test_rejects_mismatched_network(L, S):
         L.lbpf_surrogate_advance(a, net, L.surrogate_cfg(), 1)
     with pytest.raises(L.LbpfError):
         L.lbpf_surrogate_advance(a, _net(L), L.surrogate_cfg(steps_per_block=0), 1)
+    with pytest.raises(L.LbpfError):
+        L.lbpf_surrogate_advance(a, _net(L), L.surrogate_cfg(iface_rel_tol=-1.0), 1)
     a.close()
     net.close()
 
