@@ -148,7 +148,7 @@ WORKLOADS = {
                # per-block bias accumulates to lattice units over 400 blocks)
                surrogate=dict(blocks=(50, 200), judge_every=8, traj=50, t_end=20000,
                               every=500, crop=256, batch=8, start=1000, min_steps=20000,
-                              val_blocks=100, val_tol=0.5, val_seeds=3, iface_rel_tol=0.9,
+                              val_steps=5000, val_tol=0.5, val_seeds=3, iface_rel_tol=0.9,
                               recipe={50: (8000, 2.5e-4), 200: (4000, 5e-4)}),
                sample=dict(nx=256, ny=256, channel=True)),
     "c5net": dict(desc="the c5 network alone: BF16 U-Net 32/64/128/256 channels on a 512x512 "
@@ -1031,13 +1031,15 @@ def surrogate_arm(args, w, nb, stream, dist, clk, rank):
     t_data = time.perf_counter() - t0
     train_steps, lr = c["recipe"][nb]
     # validation (a problem of its own, neither a training trajectory nor the
-    # held-out test problem): the network alone advances val_blocks blocks
-    # (only the first is judged) and its interface is compared with the LB's;
-    # a candidate that drifts by more than val_tol lattice units is replaced
-    # by one trained from the next initialisation seed (at most val_seeds)
+    # held-out test problem): the network alone advances val_steps LB steps
+    # worth of blocks (only the first is judged) and its interface is compared
+    # with the LB's; a candidate that drifts by more than val_tol lattice units
+    # is replaced by one trained from the next initialisation seed (at most
+    # val_seeds); the best candidate is kept
+    vblocks = max(4, c["val_steps"] // nb)
     vparams, vfields, _ = S.channel_problem(np.random.default_rng(5151 + rank), nx, ny)
     vb = S.make_sim(vparams, vfields, stream.cuda_stream)
-    vb.step(c["start"] + c["val_blocks"] * nb)
+    vb.step(c["start"] + vblocks * nb)
     v_ref = vb.diagnostics()["iface_pos"][:4]
     vb.close()
     vcfg = S.default_cfg(nb, judge_every=0, drift_tol=1.0, iface_tol=1e9)
@@ -1052,7 +1054,7 @@ def surrogate_arm(args, w, nb, stream, dist, clk, rank):
         vnet = S.inference_net(cand, nx, ny, stream.cuda_stream)
         va = S.make_sim(vparams, vfields, stream.cuda_stream)
         va.step(c["start"])
-        L.lbpf_surrogate_advance(va, vnet, vcfg, c["val_blocks"])
+        L.lbpf_surrogate_advance(va, vnet, vcfg, vblocks)
         verr = float(np.max(np.abs(va.diagnostics()["iface_pos"][:4] - v_ref)))
         va.close()
         vnet.close()
@@ -1150,7 +1152,7 @@ def surrogate_arm(args, w, nb, stream, dist, clk, rank):
         "training": {"pairs": npairs, "steps": train_steps, "lr": lr, "batch": c["batch"],
                      "band_rows": c["crop"], "data_s": round(t_data, 1),
                      "train_s": round(t_train, 1), "loss": [round(x[1], 5) for x in hist],
-                     "validation": {"blocks": c["val_blocks"], "tol_lu": c["val_tol"],
+                     "validation": {"blocks": vblocks, "tol_lu": c["val_tol"],
                                     "candidates": tries},
                      "held_out_mse": mse_net, "held_out_mse_no_network": mse_none,
                      "held_out_ratio": mse_net / mse_none},
