@@ -68,7 +68,7 @@ struct lbpf_unet {
   Act g_bottom;
   float *y = nullptr, *gy = nullptr, *loss = nullptr;
   unsigned* d_err = nullptr;  // bit 2: a tensor-core kernel timed out
-  float* wpart = nullptr;     // partial sums of the nine-tap weight gradient
+  float* wpart = nullptr;     // partial sums of the weight, bias and head gradients
   size_t wpart_cap = 0;       // ... in floats
   // tables of the one-launch Adam step (every parameter tensor) and
   // flip-transpose (every convolution), in device memory
@@ -98,6 +98,8 @@ struct lbpf_unet {
 };
 
 namespace {
+
+constexpr int kWgradChunk = 4096;  // pixels per chunk of the per-tap weight gradient
 
 int ufail(lbpf_unet* n, int code, const char* fmt, ...) {
   if (!n) return code;
@@ -223,7 +225,7 @@ int conv_bwd(lbpf_unet* n, const ConvLayer& l, const Act& x, int xoff, const Act
   wa.npix = npix;
   wa.H = x.h;
   wa.W = x.w;
-  wa.chunk = 4096;
+  wa.chunk = kWgradChunk;
   wa.part = n->wpart;
   wa.part_cap = n->wpart_cap;
   UCK(n, lbk::nn::wgrad3x3(wa, n->stream));  // weight and bias gradients
@@ -309,7 +311,7 @@ int backward(lbpf_unet* n, const float* t) {
   const Act& top = L > 1 ? n->db[0] : n->bottom;
   Act& g_top = L > 1 ? n->g_db[0] : n->g_bottom;
   UCK(n, lbk::nn::head_bwd(top.p, n->C[0], n->hw, n->gy, n->cfg.out_ch, npix, g_top.p, n->ghw,
-                           n->ghb, n->stream));
+                           n->ghb, n->wpart, n->wpart_cap, n->stream));
   // decoder, from the top level down to the bottom
   for (int l = 0; l < L - 1; ++l) {
     if ((rc = conv_bwd(n, n->dec_b[l], n->da[l], 0, n->g_db[l], 0, &n->g_da[l], 0, &n->da[l])))
@@ -699,10 +701,14 @@ lbpf_status lbpf_unet_create(const lbpf_unet_cfg* cfg, void* stream, lbpf_unet_t
   chk(dalloc(n, &n->gy, ny));
   chk(dalloc(n, &n->loss, 1));
   chk(dalloc(n, &n->d_err, 1));
-  {  // scratch of the nine-tap weight gradient: the largest layer's need
-    size_t need = 0;
+  {  // scratch of the gradients' partial sums: the largest need of a layer's
+     // weight and bias gradients and of the head's backward (used one after
+     // another on the network's stream)
+    size_t need = lbk::nn::head_bwd_scratch(n->C[0], cfg->out_ch,
+                                            (long long)cfg->batch * n->H[0] * n->W[0]);
     auto take = [&](const ConvLayer& cl, int l) {
-      need = std::max(need, lbk::nn::wgrad_scratch(cl.cout, cl.cin, cfg->batch, n->H[l], n->W[l]));
+      need = std::max(need, lbk::nn::wgrad_scratch(cl.cout, cl.cin, cfg->batch, n->H[l], n->W[l],
+                                                   kWgradChunk));
     };
     for (int l = 0; l < L; ++l) {
       take(n->enc_a[l], l);

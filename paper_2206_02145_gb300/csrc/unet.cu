@@ -202,8 +202,39 @@ __global__ void __launch_bounds__(kThreads) wgrad3x3_kernel(const WgradArgs a) {
       for (int k = 0; k < 4; ++k) {
         const int co = m0 + wm * WM + mt * 16 + (lane >> 2) + (k >> 1) * 8;
         const int ci = n0 + wn * WN + nt * 8 + (lane & 3) * 2 + (k & 1);
-        atomicAdd(a.dw + (size_t(tap) * a.Cout + co) * a.Cin + ci, acc[mt][nt][k]);
+        const size_t e = (size_t(tap) * a.Cout + co) * a.Cin + ci;
+        if (a.part)  // this chunk's partial; summed over the chunks in a fixed order
+          a.part[size_t(chunk) * 9 * a.Cout * a.Cin + e] = acc[mt][nt][k];
+        else
+          atomicAdd(a.dw + e, acc[mt][nt][k]);
       }
+}
+
+// out[i] += sum over p < nparts of part[p * stride + i], i < n, in a fixed
+// order: a block takes 32 consecutive outputs, its 8 warps sum every 8th
+// partial each, then warp 0 adds the 8 warp sums
+__global__ void __launch_bounds__(256) sum_partials_kernel(const float* part, long long stride,
+                                                           int nparts, int n, float* out) {
+  __shared__ float red[8][32];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int i = blockIdx.x * 32 + lane;
+  float t = 0.f;
+  if (i < n)
+    for (int p = warp; p < nparts; p += 8) t += part[p * stride + i];
+  red[warp][lane] = t;
+  __syncthreads();
+  if (warp == 0 && i < n) {
+    float u = 0.f;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) u += red[w][lane];
+    out[i] += u;
+  }
+}
+cudaError_t sum_partials(const float* part, long long stride, int nparts, int n, float* out,
+                         cudaStream_t s) {
+  if (n < 1 || nparts < 1) return cudaSuccess;
+  sum_partials_kernel<<<(n + 31) / 32, 256, 0, s>>>(part, stride, nparts, n, out);
+  return cudaGetLastError();
 }
 
 // Nine taps at once: a CTA owns a 32 x 32 (co, ci) tile of every tap and a
@@ -399,10 +430,10 @@ __device__ __forceinline__ const V8& ld8(const bf16* p) { return *reinterpret_ca
 __device__ __forceinline__ void st8(bf16* p, const V8& v) { *reinterpret_cast<V8*>(p) = v; }
 
 // bias gradient db[c] += sum over pixels of g[p][off + c]: each thread owns
-// one group of 8 channels and a stride of pixels; block reduction in shared
-// memory, one atomic per channel and block
+// one group of 8 channels and a stride of pixels; a tree in shared memory
+// per block, the blocks' sums added in a fixed order (sum_partials)
 __global__ void bias_grad_kernel(const bf16* g, int Cg, int off, int C, long long npix,
-                                 float* db) {
+                                 float* part) {
   __shared__ float red[256][8];
   const int groups = C / 8;
   const int lanes = blockDim.x / groups;  // pixel lanes per block
@@ -427,9 +458,9 @@ __global__ void bias_grad_kernel(const bf16* g, int Cg, int off, int C, long lon
       for (int i = 0; i < 8; ++i) red[threadIdx.x][i] += red[threadIdx.x + half * groups][i];
     __syncthreads();
   }
-  if (threadIdx.x < groups)
+  if (threadIdx.x < groups)  // this block's sums; summed over the blocks in a fixed order
 #pragma unroll
-    for (int i = 0; i < 8; ++i) atomicAdd(db + threadIdx.x * 8 + i, red[threadIdx.x][i]);
+    for (int i = 0; i < 8; ++i) part[size_t(blockIdx.x) * C + threadIdx.x * 8 + i] = red[threadIdx.x][i];
 }
 
 // g = 0 where act <= 0
@@ -588,11 +619,12 @@ __global__ void head_fwd_kernel(const bf16* x, int C, const float* w, const floa
 // dw[o][c] += sum_p gy[p][o] x[p][c], db[o] += sum_p gy[p][o].  A warp walks
 // pixels one at a time with lane c on channel c (C <= 32), so every access of
 // x and gx is one coalesced row and gy is a broadcast; the 8 warps' sums meet
-// in shared memory in a fixed order, then one atomic per value and block.
+// in shared memory in a fixed order, the blocks' sums are added in a fixed
+// order too (sum_partials).
 template <int O>
 __global__ void __launch_bounds__(256) head_bwd_kernel(const bf16* x, int C, const float* w,
                                                        const float* gy, long long npix, bf16* gx,
-                                                       float* dw, float* db) {
+                                                       float* part) {
   __shared__ float red[8][O][33];  // per warp: dw[o][c] at [o][c], db[o] at [o][32]
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const bool on = lane < C;
@@ -628,7 +660,8 @@ __global__ void __launch_bounds__(256) head_bwd_kernel(const bf16* x, int C, con
       float t = 0.f;
 #pragma unroll
       for (int k = 0; k < 8; ++k) t += red[k][o][c];
-      atomicAdd(c == 32 ? db + o : dw + o * C + c, t);
+      // this block's partial: dw entries o C + c, then the O db entries
+      part[size_t(blockIdx.x) * (O * C + O) + (c == 32 ? O * C + o : o * C + c)] = t;
     }
   }
 }
@@ -748,6 +781,16 @@ bool taps_shape(int Cout, int Cin, int N, int H, int W, TapsShape* t) {
   t->nchunks = (t->patches + t->chunk - 1) / t->chunk;
   return true;
 }
+// pixels per chunk of the per-tap kernel: the requested chunk, enlarged so
+// that its grid (9 x chunks) stays within 65535
+int pertap_chunk(long long npix, int chunk) {
+  const long long max_chunks = 65535 / 9;
+  if ((npix + chunk - 1) / chunk > max_chunks) {
+    const long long c = (npix + max_chunks - 1) / max_chunks;
+    chunk = int((c + 15) / 16 * 16);
+  }
+  return chunk;
+}
 // floats of the nine-tap kernel's weight partials; its bias partials follow
 size_t taps_weight_floats(const TapsShape& t) { return size_t(t.ntiles) * t.nchunks * 9 * 1024; }
 size_t taps_bias_floats(const TapsShape& t) {
@@ -755,10 +798,12 @@ size_t taps_bias_floats(const TapsShape& t) {
 }
 }  // namespace
 
-size_t wgrad_scratch(int Cout, int Cin, int N, int H, int W) {
+size_t wgrad_scratch(int Cout, int Cin, int N, int H, int W, int chunk) {
   TapsShape t;
-  if (!taps_shape(Cout, Cin, N, H, W, &t)) return 0;
-  return taps_weight_floats(t) + taps_bias_floats(t);
+  if (taps_shape(Cout, Cin, N, H, W, &t)) return taps_weight_floats(t) + taps_bias_floats(t);
+  const long long npix = (long long)N * H * W;
+  const int c = pertap_chunk(npix, chunk);
+  return size_t((npix + c - 1) / c) * 9 * Cout * Cin + bias_grad_scratch(Cout, npix);
 }
 
 cudaError_t wgrad3x3(const WgradArgs& args, cudaStream_t s) {
@@ -781,20 +826,17 @@ cudaError_t wgrad3x3(const WgradArgs& args, cudaStream_t s) {
         a.part, bias_off, ts.nchunks, ts.ntiles, ts.ntn, a.Cout, a.Cin, a.dw, a.db);
     return cudaGetLastError();
   }
-  if (a.db) {  // the per-tap kernel leaves the bias gradient to its own kernel
-    const cudaError_t e = bias_grad(a.dy, a.Cdy, a.co_off, a.Cout, a.npix, a.db, s);
-    if (e != cudaSuccess) return e;
-  }
   if (a.W % 16 || a.Cout % 32 || a.Cin % 16 || a.chunk < 16 || a.chunk % 16)
     return cudaErrorInvalidValue;
-  // grid z = 9 x chunks must stay within 65535: enlarge the chunk if needed
-  const long long max_chunks = 65535 / 9;
-  if ((a.npix + a.chunk - 1) / a.chunk > max_chunks) {
-    const long long c = (a.npix + max_chunks - 1) / max_chunks;
-    a.chunk = int((c + 15) / 16 * 16);
-  }
+  a.chunk = pertap_chunk(a.npix, a.chunk);
   const int chunks = int((a.npix + a.chunk - 1) / a.chunk);
   const unsigned gz = unsigned(9 * chunks);
+  // the per-tap kernel's partials per chunk, then the bias partials: both
+  // summed in a fixed order; without room for them, FP32 atomics
+  const size_t wfloats = size_t(chunks) * 9 * a.Cout * a.Cin;
+  const size_t bfloats = a.db ? bias_grad_scratch(a.Cout, a.npix) : 0;
+  const bool partials = a.part && wfloats + bfloats <= a.part_cap;
+  if (!partials) a.part = nullptr;
   constexpr int KP = 64, S = 4;
   auto go = [&](auto kern, int bm, int bn) {
     const int smem = S * KP * ((bm + 8) + (bn + 8)) * 2;
@@ -803,27 +845,48 @@ cudaError_t wgrad3x3(const WgradArgs& args, cudaStream_t s) {
     kern<<<dim3(a.Cout / bm, a.Cin / bn, gz), kThreads, smem, s>>>(a);
     return cudaGetLastError();
   };
-  if (a.Cout % 64 == 0 && a.Cin % 32 == 0) return go(wgrad3x3_kernel<64, 32, KP, S>, 64, 32);
-  if (a.Cin % 32 == 0) return go(wgrad3x3_kernel<32, 32, KP, S>, 32, 32);
-  return go(wgrad3x3_kernel<32, 16, KP, S>, 32, 16);
+  cudaError_t e;
+  if (a.Cout % 64 == 0 && a.Cin % 32 == 0) e = go(wgrad3x3_kernel<64, 32, KP, S>, 64, 32);
+  else if (a.Cin % 32 == 0) e = go(wgrad3x3_kernel<32, 32, KP, S>, 32, 32);
+  else e = go(wgrad3x3_kernel<32, 16, KP, S>, 32, 16);
+  if (e != cudaSuccess) return e;
+  if (partials) {
+    const long long n = 9LL * a.Cout * a.Cin;
+    if ((e = sum_partials(a.part, n, chunks, int(n), a.dw, s)) != cudaSuccess) return e;
+  }
+  if (!a.db) return cudaSuccess;
+  if (!partials) return cudaErrorInvalidValue;  // the bias gradient needs its scratch
+  return bias_grad(a.dy, a.Cdy, a.co_off, a.Cout, a.npix, a.db, args.part + wfloats,
+                   a.part_cap - wfloats, s);
 }
 
 bool v8(int a) { return a % 8 == 0; }
 
-cudaError_t bias_grad(const bf16* g, int Cg, int off, int C, long long npix, float* db,
-                      cudaStream_t s) {
-  if (!v8(C) || !v8(Cg) || !v8(off) || C > 2048) return cudaErrorInvalidValue;
-  // pixel lanes per block: a power of two (the kernel's tree reduction)
+int bias_grad_blocks(int C, long long npix, int* lanes_out) {
+  // pixel lanes per block: a power of two (the kernel's tree reduction),
+  // about 16 pixels per lane
   const int groups = C / 8;
   int lanes = 1;
   while (lanes * 2 * groups <= 256) lanes *= 2;
-  // about 16 pixels per lane: more blocks would queue more atomics on the same
-  // C addresses than they save in load latency
   long long blocks = (npix + lanes * 16 - 1) / (lanes * 16);
   if (blocks > 152 * 8) blocks = 152 * 8;
   if (blocks < 1) blocks = 1;
-  bias_grad_kernel<<<int(blocks), groups * lanes, 0, s>>>(g, Cg, off, C, npix, db);
-  return cudaGetLastError();
+  if (lanes_out) *lanes_out = lanes;
+  return int(blocks);
+}
+size_t bias_grad_scratch(int C, long long npix) {
+  return size_t(bias_grad_blocks(C, npix, nullptr)) * C;
+}
+cudaError_t bias_grad(const bf16* g, int Cg, int off, int C, long long npix, float* db,
+                      float* part, size_t part_cap, cudaStream_t s) {
+  if (!v8(C) || !v8(Cg) || !v8(off) || C > 2048 || !part) return cudaErrorInvalidValue;
+  int lanes = 1;
+  const int blocks = bias_grad_blocks(C, npix, &lanes);
+  if (size_t(blocks) * C > part_cap) return cudaErrorInvalidValue;
+  bias_grad_kernel<<<blocks, (C / 8) * lanes, 0, s>>>(g, Cg, off, C, npix, part);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return sum_partials(part, C, blocks, C, db, s);
 }
 cudaError_t relu_mask(bf16* g, int Cg, int goff, const bf16* act, int Ca, int aoff, int C,
                       long long npix, cudaStream_t s) {
@@ -871,24 +934,36 @@ cudaError_t head_fwd(const bf16* x, int C, const float* w, const float* b, float
     default: return launch_pdl(head_fwd_kernel<8>, g, bl, 0, s, x, C, w, b, y, npix);
   }
 }
-cudaError_t head_bwd(const bf16* x, int C, const float* w, const float* gy, int O, long long npix,
-                     bf16* gx, float* dw, float* db, cudaStream_t s) {
-  if (O < 1 || O > 8 || C > 32 || !v8(C)) return cudaErrorInvalidValue;
+int head_bwd_blocks(long long npix) {
   long long blocks = (npix + 8 * 16 - 1) / (8 * 16);  // about 16 pixels per warp
   if (blocks > 152 * 8) blocks = 152 * 8;
-  if (blocks < 1) blocks = 1;
+  return int(blocks < 1 ? 1 : blocks);
+}
+size_t head_bwd_scratch(int C, int O, long long npix) {
+  return size_t(head_bwd_blocks(npix)) * (size_t(O) * C + O);
+}
+cudaError_t head_bwd(const bf16* x, int C, const float* w, const float* gy, int O, long long npix,
+                     bf16* gx, float* dw, float* db, float* part, size_t part_cap,
+                     cudaStream_t s) {
+  if (O < 1 || O > 8 || C > 32 || !v8(C) || !part) return cudaErrorInvalidValue;
+  const int blocks = head_bwd_blocks(npix);
+  if (size_t(blocks) * (O * C + O) > part_cap) return cudaErrorInvalidValue;
   const dim3 g{unsigned(blocks)}, bl{256};
   switch (O) {
-    case 1: head_bwd_kernel<1><<<g, bl, 0, s>>>(x, C, w, gy, npix, gx, dw, db); break;
-    case 2: head_bwd_kernel<2><<<g, bl, 0, s>>>(x, C, w, gy, npix, gx, dw, db); break;
-    case 3: head_bwd_kernel<3><<<g, bl, 0, s>>>(x, C, w, gy, npix, gx, dw, db); break;
-    case 4: head_bwd_kernel<4><<<g, bl, 0, s>>>(x, C, w, gy, npix, gx, dw, db); break;
-    case 5: head_bwd_kernel<5><<<g, bl, 0, s>>>(x, C, w, gy, npix, gx, dw, db); break;
-    case 6: head_bwd_kernel<6><<<g, bl, 0, s>>>(x, C, w, gy, npix, gx, dw, db); break;
-    case 7: head_bwd_kernel<7><<<g, bl, 0, s>>>(x, C, w, gy, npix, gx, dw, db); break;
-    default: head_bwd_kernel<8><<<g, bl, 0, s>>>(x, C, w, gy, npix, gx, dw, db); break;
+    case 1: head_bwd_kernel<1><<<g, bl, 0, s>>>(x, C, w, gy, npix, gx, part); break;
+    case 2: head_bwd_kernel<2><<<g, bl, 0, s>>>(x, C, w, gy, npix, gx, part); break;
+    case 3: head_bwd_kernel<3><<<g, bl, 0, s>>>(x, C, w, gy, npix, gx, part); break;
+    case 4: head_bwd_kernel<4><<<g, bl, 0, s>>>(x, C, w, gy, npix, gx, part); break;
+    case 5: head_bwd_kernel<5><<<g, bl, 0, s>>>(x, C, w, gy, npix, gx, part); break;
+    case 6: head_bwd_kernel<6><<<g, bl, 0, s>>>(x, C, w, gy, npix, gx, part); break;
+    case 7: head_bwd_kernel<7><<<g, bl, 0, s>>>(x, C, w, gy, npix, gx, part); break;
+    default: head_bwd_kernel<8><<<g, bl, 0, s>>>(x, C, w, gy, npix, gx, part); break;
   }
-  return cudaGetLastError();
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const long long stride = (long long)O * C + O;
+  if ((e = sum_partials(part, stride, blocks, O * C, dw, s)) != cudaSuccess) return e;
+  return sum_partials(part + size_t(O) * C, stride, blocks, O, db, s);
 }
 cudaError_t mse(const float* y, const float* t, long long n, float* gy, float* loss,
                 cudaStream_t s) {

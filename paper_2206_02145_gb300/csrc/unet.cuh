@@ -64,18 +64,23 @@ struct WgradArgs {
   long long npix;  // N * H * W
   int H, W;
   int chunk;       // pixels per CTA (multiple of 16) of the per-tap kernel
-  // scratch for the nine-tap kernel's partial sums (floats), owned by the
-  // caller; too small or null: the per-tap kernel with atomics runs instead
+  // scratch for the partial sums (floats, wgrad_scratch of the layer), owned
+  // by the caller, so that dw and db are summed in a fixed order; too small
+  // or null: the per-tap kernel with atomics, and no bias gradient (error)
   float* part;
   size_t part_cap;
 };
 cudaError_t wgrad3x3(const WgradArgs& a, cudaStream_t s);
-// floats of scratch the nine-tap weight-gradient kernel needs for a layer
-// (0 where its shape does not allow that kernel)
-size_t wgrad_scratch(int Cout, int Cin, int N, int H, int W);
+// floats of scratch wgrad3x3 needs for a layer (the nine-tap kernel's
+// partials where its shape allows it, else the per-tap kernel's partials at
+// `chunk` pixels per chunk and the bias partials) for sums in a fixed order
+size_t wgrad_scratch(int Cout, int Cin, int N, int H, int W, int chunk);
 
+// db[c] += sum over the pixels of g[p][off + c], in a fixed order through
+// part (at least bias_grad_scratch(C, npix) floats)
+size_t bias_grad_scratch(int C, long long npix);
 cudaError_t bias_grad(const bf16* g, int Cg, int off, int C, long long npix, float* db,
-                      cudaStream_t s);
+                      float* part, size_t part_cap, cudaStream_t s);
 cudaError_t relu_mask(bf16* g, int Cg, int goff, const bf16* act, int Ca, int aoff, int C,
                       long long npix, cudaStream_t s);
 cudaError_t avgpool2(const bf16* x, int Cx, int xoff, bf16* y, int Cy, int yoff, int C, int B,
@@ -87,8 +92,11 @@ cudaError_t upsample2_bwd_mask(const bf16* g, bf16* gx, const bf16* act, int C, 
                                int W, cudaStream_t s);
 cudaError_t head_fwd(const bf16* x, int C, const float* w, const float* b, float* y, int O,
                      long long npix, cudaStream_t s);
+// scratch of head_bwd (floats): per block its dw and db sums
+size_t head_bwd_scratch(int C, int O, long long npix);
 cudaError_t head_bwd(const bf16* x, int C, const float* w, const float* gy, int O, long long npix,
-                     bf16* gx, float* dw, float* db, cudaStream_t s);
+                     bf16* gx, float* dw, float* db, float* part, size_t part_cap,
+                     cudaStream_t s);
 cudaError_t mse(const float* y, const float* t, long long n, float* gy, float* loss,
                 cudaStream_t s);
 // Multi-tensor launches: a table in device memory lists the tensors, each

@@ -31,8 +31,7 @@ def trained():
     net = L.UNet(in_ch=4, out_ch=4, levels=3, batch=8, height=128, width=NX, seed=1,
                  stream=L.current_stream())
     # measured across seeds: 2000 Adam steps at 3e-4 with mirror augmentation
-    # learn reliably (shorter schedules at 1e-3 sometimes do not: the weight
-    # gradient accumulates with FP32 atomics, so training is not bit-reproducible)
+    # learn reliably (shorter schedules at 1e-3 did not for some seeds)
     hist = S.train(net, X, T, 2000, lr=3e-4, log_every=500, augment=True)
     net.status()
     return L, S, cfg, net, (Xv, Tv), hist
