@@ -47,7 +47,8 @@ sys.path.insert(0, ROOT)
 SRC_2D = ["step2d.cu", "step2d_tile.cuh", "step2d_core.cuh", "lbpf_device.cuh", "tma.cuh"]
 SRC_3D = ["step3d.cu", "step3d_core.cuh", "lbpf_device.cuh"]
 SRC_BATCH = ["batch2d.cu", "batch2d_kernels.cuh", "batch2d_fp32.cu", "batch2d_fp16.cu",
-             "batch2d_bf16.cu", "step2d_tile.cuh", "step2d_core.cuh", "lbpf_device.cuh", "tma.cuh"]
+             "batch2d_bf16.cu", "batch_schedule.h", "step2d_tile.cuh", "step2d_core.cuh",
+             "lbpf_device.cuh", "tma.cuh"]
 SRC_CONV = ["conv_tc.cu", "tma.cuh"]
 SRC_FACETS = ["facets.cu"]
 

@@ -20,7 +20,7 @@ SOURCES = ["lbpf_api.cu", "step2d.cu", "step3d.cu", "batch2d.cu", "batch2d_fp32.
            "surrogate.cu", "facets.cu"]
 HEADERS = ["lbpf_internal.cuh", "lbpf_device.cuh", "step2d_core.cuh", "step2d_tile.cuh",
            "step3d_core.cuh", "batch2d_kernels.cuh", "tma_host.h", "tma.cuh", "unet.cuh",
-           "unet_ops.cuh", "lbpf_handle.cuh", "pdl.cuh"]
+           "unet_ops.cuh", "lbpf_handle.cuh", "pdl.cuh", "batch_schedule.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2",
               "--expt-relaxed-constexpr"]

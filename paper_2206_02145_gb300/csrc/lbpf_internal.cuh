@@ -10,6 +10,8 @@
 #include <cstdint>
 #include <type_traits>
 
+#include "batch_schedule.h"
+
 namespace lbk {
 
 enum { BC_PERIODIC = 0, BC_INOUT = 1, BC_WALL = 2 };
@@ -168,11 +170,6 @@ struct BatchMember {  // what the batch needs of one instance
   void* pops[2];
   void* rings[2];
   unsigned* err;
-};
-// One run of a batched CTA's work: the tiles first, first + stride, ...
-// (count of them) of instance inst, numbered row-major within the instance.
-struct BatchSeg {
-  int inst, first, stride, count;
 };
 struct BatchPlan {  // device tables of one compiled variant
   BatchDesc* desc[2] = {nullptr, nullptr};
