@@ -131,7 +131,8 @@ __global__ void __launch_bounds__(TX* TY)
 // MASK: the variant with the solid-node path (its extra registers held to
 // five CTAs per SM, which measured faster than four at more registers); CHM:
 // the central Hermite MRT flow collision (likewise)
-template <typename T, bool FLOW, int TX, int TY, int S, bool MASK, bool CHM>
+template <typename T, bool FLOW, int TX, int TY, int S, bool MASK, bool CHM,
+          bool CUR = sizeof(T) == 2>
 __global__ void __launch_bounds__(TX* TY, (MASK || CHM) ? 5 : LBPF_2D_MIN_CTAS)
     step2d_tma_kernel(const __grid_constant__ CUtensorMap tm_fg,
                       const __grid_constant__ CUtensorMap tm_h,
@@ -157,15 +158,48 @@ __global__ void __launch_bounds__(TX* TY, (MASK || CHM) ? 5 : LBPF_2D_MIN_CTAS)
     issue_tile_2d<T, FLOW, TX, TY>(&tm_fg, &tm_h, &tm_ring, &tm_uown, &tm_uhal, c, &full[s],
                                    smem + s * L::STAGE, (tile % ntx) * TX, (tile / ntx) * TY);
   };
+  // CUR: the CTA's tiles are first, first + G, first + 2G, ...: their column
+  // and row are stepped by (G mod ntx, G div ntx) with one carry, so that the
+  // loop divides by ntx only once; thread 0 loads the tile S steps ahead of
+  // the one being computed.  Measured on the 1024^2 coupled step: 3 % faster
+  // with 16-bit storage (38.3 against 39.6 us), 0.7 % slower in FP32 (49.0
+  // against 48.7 us, two more registers), so FP32 keeps the division.
+  struct Cursor {
+    int tile, col, row;
+  };
+  const int gcol = G % ntx, grow = G / ntx;
+  auto advance = [&](Cursor& q) {
+    q.tile += G;
+    q.col += gcol;
+    q.row += grow;
+    if (q.col >= ntx) {
+      q.col -= ntx;
+      ++q.row;
+    }
+  };
+  auto issue_at = [&](const Cursor& q, int s) {
+    issue_tile_2d<T, FLOW, TX, TY>(&tm_fg, &tm_h, &tm_ring, &tm_uown, &tm_uhal, c, &full[s],
+                                   smem + s * L::STAGE, q.col * TX, q.row * TY);
+  };
+  Cursor work{first, first % ntx, first / ntx};
 
   if (tid == 0) {
     for (int s = 0; s < S; ++s) mbar_init(&full[s], 1);
     fence_barrier_init();
   }
   __syncthreads();
-  if (tid == 0)
-    for (int k = 0; k < S; ++k)
-      if (first + k * G < ntiles) issue(first + k * G, k);
+  if (tid == 0) {
+    if constexpr (CUR) {
+      Cursor q = work;
+      for (int k = 0; k < S && q.tile < ntiles; ++k) {
+        issue_at(q, k);
+        advance(q);
+      }
+    } else {
+      for (int k = 0; k < S; ++k)
+        if (first + k * G < ntiles) issue(first + k * G, k);
+    }
+  }
 
   for (int k = 0;; ++k) {
     const int tile = first + k * G;
@@ -185,13 +219,26 @@ __global__ void __launch_bounds__(TX* TY, (MASK || CHM) ? 5 : LBPF_2D_MIN_CTAS)
       __syncthreads();
       return;
     }
-    const int x0 = (tile % ntx) * TX, y0 = (tile / ntx) * TY;
+    const int x0 = CUR ? work.col * TX : (tile % ntx) * TX;
+    const int y0 = CUR ? work.row * TY : (tile / ntx) * TY;
     tile_2d<T, FLOW, TX, TY, MASK, CHM>(m, src, dst, ring_cur, err, x0, y0, c,
                                         smem + s * L::STAGE, &sh_phi[0][0]);
     __syncthreads();  // stage s and sh_phi are free again
-    if (tid == 0 && tile + S * G < ntiles) {
-      fence_proxy_async_smem();
-      issue(tile + S * G, s);
+    if constexpr (CUR) {
+      if (tid == 0) {
+        Cursor q = work;
+        for (int j = 0; j < S; ++j) advance(q);
+        if (q.tile < ntiles) {
+          fence_proxy_async_smem();
+          issue_at(q, s);
+        }
+      }
+      advance(work);
+    } else {
+      if (tid == 0 && tile + S * G < ntiles) {
+        fence_proxy_async_smem();
+        issue(tile + S * G, s);
+      }
     }
   }
 }
