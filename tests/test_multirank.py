@@ -83,3 +83,13 @@ def test_reference_arm_runs_on_rank_zero_only(tmp_path):
     assert outs[0] == ""
     line = json.loads(outs[1].splitlines()[-1])
     assert line["impl"] == "reference" and line["n_gpus"] == 2 and line["value"] > 0
+    # the reference line describes its own run: the oracle on the host cores,
+    # the same metric as the GPU arm, no host-device copies
+    assert line["metric"] == "coupled-LB MLUPS" and line["unit"] == "MLUPS"
+    assert line["higher_is_better"] is True and line["steps"] == 3 and line["warmup"] == 3
+    cb = line["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["sample"]
+    assert cb["value"] == line["value"]
+    e2e = line["e2e"]
+    assert e2e["value"] == line["value"] and e2e["unit"] == line["unit"]
+    assert e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0
