@@ -189,6 +189,22 @@ def shard(members, rank: int, world: int):
     return params[rank::world], seeds[rank::world]
 
 
+def lup_bytes(w, storage):
+    """Algorithmic bytes of one node update of workload w with the given
+    population storage: every population read and written once, the phi ring
+    read and written, the solid mask read, and with 16-bit storage the per-node
+    g reference (the node's own read, its neighbours' encoding reference read,
+    the new one written)."""
+    q = (9 if w["dim"] == 2 else 19) * w["flow"] + 2 * (9 if w["dim"] == 2 else 7)
+    ring = 8 if storage == "fp64" else 4
+    b = 2 * q * ELEM[storage] + 2 * ring
+    if w.get("baffle"):
+        b += 1  # the solid mask
+    if ELEM[storage] == 2:
+        b += 3 * 2
+    return b
+
+
 def workload(name, rank: int = 0, world: int = 1):
     """The workload's settings for rank `rank` of `world`.  nodes: the nodes
     this rank steps; nodes_all: those of all ranks (replicas of one grid, or
@@ -201,15 +217,7 @@ def workload(name, rank: int = 0, world: int = 1):
         if not note:
             b["desc"] = b["desc"] + f", {b['storage'].upper()} shifted storage"
         w = b
-    q = (9 if w["dim"] == 2 else 19) * w["flow"] + 2 * (9 if w["dim"] == 2 else 7)
-    ring = 8 if w["storage"] == "fp64" else 4
-    w["bytes_per_lup"] = 2 * q * ELEM[w["storage"]] + 2 * ring
-    if w.get("baffle"):
-        w["bytes_per_lup"] += 1  # the solid mask
-    if ELEM[w["storage"]] == 2:
-        # the per-node g reference of 16-bit storage (FP16): the node's own
-        # read, its neighbours' encoding reference read, the new one written
-        w["bytes_per_lup"] += 3 * 2
+    w["bytes_per_lup"] = lup_bytes(w, w["storage"])
     w["nodes"] = w["nx"] * w["ny"] * w["nz"]
     w["nodes_all"] = w["nodes"] * world
     if w.get("batch"):
@@ -663,6 +671,12 @@ def main():
         e, rel = iface_compare(d_init[0], iface16, d["iface_pos"], w["dim"])
         fp16_form = {"fp16_ms_per_step": ms16 / args.steps, "speedup_over_fp32": ms_max / ms16,
                      "steps": total_steps, "iface_pos_err_lu": e, "growth_rel_err": rel}
+        # its own HBM roofline: algorithmic bytes of the FP16 node update over
+        # the same measured copy peak as the FP32 line
+        b16 = lup_bytes(w, "fp16")
+        gbs16 = b16 * w["nodes"] / (ms16 / args.steps * 1e-3) / 1e9
+        fp16_form.update({"bytes_per_lup": b16, "achieved_gbs": gbs16,
+                          "hbm_frac": gbs16 / measured_peaks()[0]})
 
     vs_bgk = None
     if batch is None and w.get("collision"):

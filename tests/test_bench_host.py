@@ -41,6 +41,14 @@ def test_algorithmic_bytes_per_node_update(bench, name, bytes_per_lup):
     assert bench.workload(name)["bytes_per_lup"] == bytes_per_lup
 
 
+def test_fp16_arm_counts_the_fp16_node_update(bench):
+    # the default line's FP16-storage arm takes the C2 grid's bytes in FP16
+    # storage for its own roofline, the bytes of the c2_fp16 workload
+    c2 = bench.workload("c2")
+    assert bench.lup_bytes(c2, "fp16") == bench.workload("c2_fp16")["bytes_per_lup"] == 122
+    assert bench.lup_bytes(c2, "fp32") == c2["bytes_per_lup"] == 224
+
+
 def test_sweep_is_seeded_and_within_its_ranges(bench):
     a = bench.sweep_members(64, 4)
     b = bench.sweep_members(64, 4)
