@@ -130,7 +130,8 @@ __global__ void __launch_bounds__(TX* TY)
 
 // MASK: the variant with the solid-node path (its extra registers held to
 // five CTAs per SM, which measured faster than four at more registers); CHM:
-// the central Hermite MRT flow collision (likewise)
+// the central Hermite MRT flow collision (likewise).  CUR: how the threads
+// learn the origin of their CTA's next tile (below).
 template <typename T, bool FLOW, int TX, int TY, int S, bool MASK, bool CHM,
           bool CUR = sizeof(T) == 2>
 __global__ void __launch_bounds__(TX* TY, (MASK || CHM) ? 5 : LBPF_2D_MIN_CTAS)
@@ -148,22 +149,24 @@ __global__ void __launch_bounds__(TX* TY, (MASK || CHM) ? 5 : LBPF_2D_MIN_CTAS)
   extern __shared__ unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t full[S];
   __shared__ R sh_phi[SY][SX];
+  __shared__ int2 org[S];  // !CUR: origin of the tile in each stage
   unsigned char* smem = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
 
   const int tid = threadIdx.x;
   const int first = blockIdx.x, G = gridDim.x;
 
-  auto issue = [&](int tile, int s) {
-    issue_tile_2d<T, FLOW, TX, TY>(&tm_fg, &tm_h, &tm_ring, &tm_uown, &tm_uhal, c, &full[s],
-                                   smem + s * L::STAGE, (tile % ntx) * TX, (tile / ntx) * TY);
-  };
-  // CUR: the CTA's tiles are first, first + G, first + 2G, ...: their column
-  // and row are stepped by (G mod ntx, G div ntx) with one carry, so that the
-  // loop divides by ntx only once; thread 0 loads the tile S steps ahead of
-  // the one being computed.  Measured on the 1024^2 coupled step: 3 % faster
-  // with 16-bit storage (38.3 against 39.6 us), 0.7 % slower in FP32 (49.0
-  // against 48.7 us, two more registers), so FP32 keeps the division.
+  // The CTA's tiles are first, first + G, first + 2G, ...  Their origins
+  // reach the threads without a division by ntx in every thread:
+  //  - CUR (16-bit storage): every thread steps the tile's column and row by
+  //    (G mod ntx, G div ntx) with one carry; thread 0 loads the tile S steps
+  //    ahead of the one being computed;
+  //  - otherwise (FP32): thread 0 divides once per tile it loads and writes the
+  //    origin into the stage's slot of org before it arrives on the stage's
+  //    mbarrier, whose completion publishes it to the other threads.
+  // Same-box timings of the 1024^2 coupled step (dividing in every thread /
+  // cursor / published origin): FP16 39.6 / 38.35 / 38.5 us, FP32 48.7 / 49.05
+  // (two more registers) / 48.5 us.
   struct Cursor {
     int tile, col, row;
   };
@@ -177,9 +180,14 @@ __global__ void __launch_bounds__(TX* TY, (MASK || CHM) ? 5 : LBPF_2D_MIN_CTAS)
       ++q.row;
     }
   };
-  auto issue_at = [&](const Cursor& q, int s) {
+  auto issue_xy = [&](int x0, int y0, int s) {
     issue_tile_2d<T, FLOW, TX, TY>(&tm_fg, &tm_h, &tm_ring, &tm_uown, &tm_uhal, c, &full[s],
-                                   smem + s * L::STAGE, q.col * TX, q.row * TY);
+                                   smem + s * L::STAGE, x0, y0);
+  };
+  auto issue_org = [&](int tile, int s) {  // thread 0, !CUR
+    const int2 o = make_int2((tile % ntx) * TX, (tile / ntx) * TY);
+    org[s] = o;
+    issue_xy(o.x, o.y, s);
   };
   Cursor work{first, first % ntx, first / ntx};
 
@@ -192,12 +200,12 @@ __global__ void __launch_bounds__(TX* TY, (MASK || CHM) ? 5 : LBPF_2D_MIN_CTAS)
     if constexpr (CUR) {
       Cursor q = work;
       for (int k = 0; k < S && q.tile < ntiles; ++k) {
-        issue_at(q, k);
+        issue_xy(q.col * TX, q.row * TY, k);
         advance(q);
       }
     } else {
       for (int k = 0; k < S; ++k)
-        if (first + k * G < ntiles) issue(first + k * G, k);
+        if (first + k * G < ntiles) issue_org(first + k * G, k);
     }
   }
 
@@ -219,25 +227,32 @@ __global__ void __launch_bounds__(TX* TY, (MASK || CHM) ? 5 : LBPF_2D_MIN_CTAS)
       __syncthreads();
       return;
     }
-    const int x0 = CUR ? work.col * TX : (tile % ntx) * TX;
-    const int y0 = CUR ? work.row * TY : (tile / ntx) * TY;
+    int x0, y0;
+    if constexpr (CUR) {
+      x0 = work.col * TX;
+      y0 = work.row * TY;
+    } else {
+      const int2 o = org[s];
+      x0 = o.x;
+      y0 = o.y;
+    }
     tile_2d<T, FLOW, TX, TY, MASK, CHM>(m, src, dst, ring_cur, err, x0, y0, c,
                                         smem + s * L::STAGE, &sh_phi[0][0]);
-    __syncthreads();  // stage s and sh_phi are free again
+    __syncthreads();  // stage s, its origin slot and sh_phi are free again
     if constexpr (CUR) {
       if (tid == 0) {
         Cursor q = work;
         for (int j = 0; j < S; ++j) advance(q);
         if (q.tile < ntiles) {
           fence_proxy_async_smem();
-          issue_at(q, s);
+          issue_xy(q.col * TX, q.row * TY, s);
         }
       }
       advance(work);
     } else {
       if (tid == 0 && tile + S * G < ntiles) {
         fence_proxy_async_smem();
-        issue(tile + S * G, s);
+        issue_org(tile + S * G, s);
       }
     }
   }
